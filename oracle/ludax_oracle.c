@@ -1,0 +1,523 @@
+/*
+ * ludax_oracle.c -- plain, slow CPU oracle for the Ludax board-game hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file: only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg use it.  It shares no code, header, table or constant
+ * generator with the CUDA path under paper_2506_22609_b300/csrc.
+ *
+ * What it computes (Ludax, arXiv 2506.22609):
+ *   - the rules of Tic-Tac-Toe, Connect Four, Hex and Reversi/Othello as the
+ *     paper's game appendix states them (App. C, "Benchmark Game
+ *     Descriptions"), over a row-major int8 cell array with row 0 at the top
+ *     (cell numbering as in the English Draughts listing of App. A, where P1
+ *     moves "up" and starts on cells 40..62);
+ *   - the action = destination-cell convention of Sec. 3.4 (Connect Four's
+ *     legal cells are the empty cells directly above an occupied cell or on
+ *     the bottom row), plus one pass action for Reversi (force_pass, App. B);
+ *   - ordered end rules, a win checked before a draw (Sec. 3.3);
+ *   - uniform-random playouts (the random-policy benchmark of Sec. 6) driven
+ *     by a counter-based splitmix64 keyed on (seed, env, ply).
+ *
+ * Every check is a direct scan of the cell array: lines are found by testing
+ * every start cell and direction, Reversi legality and flips walk each ray
+ * cell by cell, and Hex connectivity is a breadth-first search from the
+ * mover's first edge.  No bitboards, no incremental state.
+ *
+ * Readings where the paper is silent (they are listed in the design doc):
+ *   Hex neighbours of (r,c): (r-1,c) (r+1,c) (r,c-1) (r,c+1) (r-1,c+1) (r+1,c-1);
+ *   Reversi: P1 = black moves first; white on D4,E5 = cells 27,36, black on
+ *   D5,E4 = cells 35,28 (algebraic rows counted from the top); a pass is the
+ *   action id 64, legal only when no cell is; two consecutive passes end the
+ *   game; a tie in disc count is a draw;
+ *   an illegal action ends the game: the mover loses (reward -1, opponent +1);
+ *   ply caps 9 / 42 / 128 / n*n mark an env CAPPED (never reached by a correct
+ *   implementation of these games).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_TTT 0
+#define OR_C4 1
+#define OR_OTHELLO 2
+#define OR_HEX 3
+
+#define OR_ONGOING (-1)
+#define OR_DRAW 0
+#define OR_P1 1
+#define OR_P2 2
+#define OR_CAPPED 3
+
+#define OR_MAXCELLS 128
+
+typedef struct {
+    int32_t game, rows, cols, ncells;
+    int8_t cell[OR_MAXCELLS]; /* 0 empty, 1 P1, 2 P2; index r*cols + c, r = 0 top */
+    int32_t to_move;          /* 1 or 2 */
+    int32_t ply;              /* plies played so far, passes included */
+    int32_t passes;           /* consecutive passes (Reversi) */
+    int32_t outcome;          /* OR_ONGOING, OR_DRAW, OR_P1, OR_P2, OR_CAPPED */
+    int32_t illegal;          /* 1 when the game ended on an illegal action */
+} ogame;
+
+/* ------------------------------------------------------------------ RNG --
+ * splitmix64 (Steele, Lea and Flood, OOPSLA 2014; the form published by
+ * Vigna): add the golden-ratio increment, then the finaliser
+ * z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27; z *= 0x94D049BB133111EB;
+ * z ^= z>>31.  oracle_sm(x) is one output for the state x.                  */
+uint64_t oracle_sm(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* The counter-based draw for one ply of one env: the key of an env is
+ * sm(sm(seed) ^ env) with env the global env index; the draw for a ply is
+ * sm(key ^ ply).                                                           */
+uint64_t oracle_draw(uint64_t seed, uint64_t env, uint64_t ply) {
+    uint64_t key = oracle_sm(oracle_sm(seed) ^ env);
+    return oracle_sm(key ^ ply);
+}
+
+/* Uniform index in [0, n) from the top 32 bits of a draw (multiply-shift). */
+uint32_t oracle_pick(uint64_t r, uint32_t n) {
+    uint64_t hi = r >> 32;
+    return (uint32_t)((hi * (uint64_t)n) >> 32);
+}
+
+/* ------------------------------------------------------------ geometry -- */
+static int in_board(const ogame* g, int r, int c) {
+    return r >= 0 && r < g->rows && c >= 0 && c < g->cols;
+}
+static int at(const ogame* g, int r, int c) { return g->cell[r * g->cols + c]; }
+
+int oracle_ply_cap(int game, int rows, int cols) {
+    switch (game) {
+    case OR_TTT: return 9;
+    case OR_C4: return 42;
+    case OR_OTHELLO: return 128;
+    case OR_HEX: return rows * cols;
+    }
+    return 0;
+}
+
+/* Number of actions: one per cell, plus the pass for Reversi. */
+int oracle_num_actions(int game, int rows, int cols) {
+    return rows * cols + (game == OR_OTHELLO ? 1 : 0);
+}
+
+int oracle_check_params(int game, int rows, int cols) {
+    switch (game) {
+    case OR_TTT: return (rows == 3 && cols == 3) ? 0 : -1;
+    case OR_C4: return (rows == 6 && cols == 7) ? 0 : -1;
+    case OR_OTHELLO: return (rows == 8 && cols == 8) ? 0 : -1;
+    case OR_HEX: return (rows == cols && rows >= 2 && rows <= 11) ? 0 : -1;
+    }
+    return -1;
+}
+
+/* Start position: an empty board, except Reversi's four discs. */
+int oracle_init(ogame* g, int game, int rows, int cols) {
+    if (oracle_check_params(game, rows, cols) != 0) return -1;
+    memset(g, 0, sizeof(*g));
+    g->game = game;
+    g->rows = rows;
+    g->cols = cols;
+    g->ncells = rows * cols;
+    g->to_move = 1;
+    g->outcome = OR_ONGOING;
+    if (game == OR_OTHELLO) {
+        /* D4 and E5 white (P2); D5 and E4 black (P1); row 4 is index 3. */
+        g->cell[3 * 8 + 3] = 2; /* D4 = 27 */
+        g->cell[4 * 8 + 4] = 2; /* E5 = 36 */
+        g->cell[4 * 8 + 3] = 1; /* D5 = 35 */
+        g->cell[3 * 8 + 4] = 1; /* E4 = 28 */
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- lines --
+ * Does player p own L consecutive cells along any row, column or diagonal?
+ * Every start cell and every one of the four directions is tested.        */
+static int has_line(const ogame* g, int p, int L) {
+    static const int dr[4] = {0, 1, 1, 1};
+    static const int dc[4] = {1, 0, 1, -1};
+    for (int r = 0; r < g->rows; r++)
+        for (int c = 0; c < g->cols; c++)
+            for (int d = 0; d < 4; d++) {
+                int k = 0;
+                while (k < L && in_board(g, r + k * dr[d], c + k * dc[d]) &&
+                       at(g, r + k * dr[d], c + k * dc[d]) == p)
+                    k++;
+                if (k == L) return 1;
+            }
+    return 0;
+}
+
+static int board_full(const ogame* g) {
+    for (int i = 0; i < g->ncells; i++)
+        if (g->cell[i] == 0) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------- Reversi -- */
+static const int ODR[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+static const int ODC[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+
+/* Length of the run of opponent discs starting next to (r,c) in direction d
+ * that is closed by one of p's discs; 0 if there is no such custodial run. */
+static int custodial_run(const ogame* g, int p, int r, int c, int d) {
+    int q = 3 - p, k = 1;
+    while (in_board(g, r + k * ODR[d], c + k * ODC[d]) && at(g, r + k * ODR[d], c + k * ODC[d]) == q)
+        k++;
+    if (k == 1) return 0;
+    if (!in_board(g, r + k * ODR[d], c + k * ODC[d])) return 0;
+    return at(g, r + k * ODR[d], c + k * ODC[d]) == p ? k - 1 : 0;
+}
+
+static int othello_cell_legal(const ogame* g, int p, int i) {
+    int r = i / g->cols, c = i % g->cols;
+    if (g->cell[i] != 0) return 0;
+    for (int d = 0; d < 8; d++)
+        if (custodial_run(g, p, r, c, d) > 0) return 1;
+    return 0;
+}
+
+/* ----------------------------------------------------------------- Hex --
+ * Breadth-first search over p's stones from p's first edge; p connects
+ * when the search reaches p's second edge.  P1 joins row 0 to row n-1,
+ * P2 joins column 0 to column n-1.                                       */
+static const int HDR[6] = {-1, 1, 0, 0, -1, 1};
+static const int HDC[6] = {0, 0, -1, 1, 1, -1};
+
+static int hex_connects(const ogame* g, int p) {
+    int n = g->rows;
+    int seen[OR_MAXCELLS];
+    int queue[OR_MAXCELLS];
+    int head = 0, tail = 0;
+    memset(seen, 0, sizeof(seen));
+    for (int t = 0; t < n; t++) {
+        int r = (p == 1) ? 0 : t;
+        int c = (p == 1) ? t : 0;
+        int i = r * n + c;
+        if (g->cell[i] == p) {
+            seen[i] = 1;
+            queue[tail++] = i;
+        }
+    }
+    while (head < tail) {
+        int i = queue[head++];
+        int r = i / n, c = i % n;
+        if ((p == 1 && r == n - 1) || (p == 2 && c == n - 1)) return 1;
+        for (int d = 0; d < 6; d++) {
+            int rr = r + HDR[d], cc = c + HDC[d];
+            if (!in_board(g, rr, cc)) continue;
+            int j = rr * n + cc;
+            if (!seen[j] && g->cell[j] == p) {
+                seen[j] = 1;
+                queue[tail++] = j;
+            }
+        }
+    }
+    return 0;
+}
+
+/* For a full or partial Hex board: bit 0 set if P1 connects, bit 1 if P2. */
+int oracle_hex_connections(int n, const int8_t* cells) {
+    ogame g;
+    if (oracle_init(&g, OR_HEX, n, n) != 0) return -1;
+    memcpy(g.cell, cells, (size_t)(n * n));
+    return (hex_connects(&g, 1) ? 1 : 0) | (hex_connects(&g, 2) ? 2 : 0);
+}
+
+/* --------------------------------------------------------- legal actions --
+ * legal[a] = 1 for each legal action a in [0, num_actions); returns the
+ * count.  A finished game has no legal action.                           */
+int oracle_legal(const ogame* g, uint8_t* legal) {
+    int A = oracle_num_actions(g->game, g->rows, g->cols);
+    int n = 0;
+    memset(legal, 0, (size_t)A);
+    if (g->outcome != OR_ONGOING) return 0;
+    for (int i = 0; i < g->ncells; i++) {
+        int ok = 0;
+        if (g->cell[i] != 0) continue;
+        switch (g->game) {
+        case OR_TTT:
+        case OR_HEX: ok = 1; break;
+        case OR_C4: {
+            int r = i / g->cols, c = i % g->cols;
+            ok = (r == g->rows - 1) || (at(g, r + 1, c) != 0);
+            break;
+        }
+        case OR_OTHELLO: ok = othello_cell_legal(g, g->to_move, i); break;
+        }
+        legal[i] = (uint8_t)ok;
+        n += ok;
+    }
+    if (g->game == OR_OTHELLO && n == 0) {
+        legal[g->ncells] = 1; /* force_pass */
+        n = 1;
+    }
+    return n;
+}
+
+static void finish(ogame* g, int outcome) { g->outcome = outcome; }
+
+/* Rewards for [P1, P2] from the final outcome (PGX shape). */
+void oracle_rewards(const ogame* g, float* rew2) {
+    rew2[0] = rew2[1] = 0.0f;
+    if (g->outcome == OR_P1) { rew2[0] = 1.0f; rew2[1] = -1.0f; }
+    if (g->outcome == OR_P2) { rew2[0] = -1.0f; rew2[1] = 1.0f; }
+}
+
+/* ----------------------------------------------------------------- step --
+ * Apply one action for the player to move.  Returns 0 on success, 1 when the
+ * game was already over (a no-op), -1 for an illegal action (the game ends
+ * and the mover loses).                                                   */
+int oracle_apply(ogame* g, int action) {
+    uint8_t legal[OR_MAXCELLS + 1];
+    int A, p;
+    if (g->outcome != OR_ONGOING) return 1;
+    A = oracle_num_actions(g->game, g->rows, g->cols);
+    oracle_legal(g, legal);
+    p = g->to_move;
+    if (action < 0 || action >= A || !legal[action]) {
+        g->illegal = 1;
+        finish(g, 3 - p);
+        return -1;
+    }
+    if (g->game == OR_OTHELLO && action == g->ncells) {
+        g->passes += 1;
+    } else {
+        int r = action / g->cols, c = action % g->cols;
+        g->cell[action] = (int8_t)p;
+        if (g->game == OR_OTHELLO) {
+            int runs[8];
+            for (int d = 0; d < 8; d++) runs[d] = custodial_run(g, p, r, c, d);
+            for (int d = 0; d < 8; d++)
+                for (int k = 1; k <= runs[d]; k++) g->cell[(r + k * ODR[d]) * g->cols + c + k * ODC[d]] = (int8_t)p;
+            g->passes = 0;
+        }
+    }
+    g->ply += 1;
+    g->to_move = 3 - p;
+    /* end rules, in order: win first, then draw */
+    switch (g->game) {
+    case OR_TTT:
+        if (has_line(g, p, 3)) finish(g, p);
+        else if (board_full(g)) finish(g, OR_DRAW);
+        break;
+    case OR_C4:
+        if (has_line(g, p, 4)) finish(g, p);
+        else if (board_full(g)) finish(g, OR_DRAW);
+        break;
+    case OR_HEX:
+        if (hex_connects(g, p)) finish(g, p);
+        break;
+    case OR_OTHELLO:
+        if (g->passes >= 2) {
+            int n1 = 0, n2 = 0;
+            for (int i = 0; i < g->ncells; i++) {
+                n1 += g->cell[i] == 1;
+                n2 += g->cell[i] == 2;
+            }
+            finish(g, n1 > n2 ? OR_P1 : (n2 > n1 ? OR_P2 : OR_DRAW));
+        }
+        break;
+    }
+    if (g->outcome == OR_ONGOING && g->ply >= oracle_ply_cap(g->game, g->rows, g->cols)) finish(g, OR_CAPPED);
+    return 0;
+}
+
+/* -------------------------------------------------------------- playout --
+ * Uniform-random playout of one env.  Each ply: collect the legal actions
+ * in ascending id; if the only one is the forced pass, play it without a
+ * draw; otherwise draw r = draw(seed, env, ply) and play the k-th legal
+ * action with k = pick(r, count).  Stops at the end of the game or, when
+ * stop_ply >= 0, once ply == stop_ply.                                    */
+void oracle_playout(ogame* g, uint64_t seed, uint64_t env, int stop_ply) {
+    uint8_t legal[OR_MAXCELLS + 1];
+    int A = oracle_num_actions(g->game, g->rows, g->cols);
+    while (g->outcome == OR_ONGOING && (stop_ply < 0 || g->ply < stop_ply)) {
+        int n = oracle_legal(g, legal);
+        int action = -1;
+        if (g->game == OR_OTHELLO && legal[g->ncells]) {
+            action = g->ncells;
+        } else {
+            uint32_t k = oracle_pick(oracle_draw(seed, env, (uint64_t)g->ply), (uint32_t)n);
+            for (int a = 0; a < A; a++)
+                if (legal[a]) {
+                    if (k == 0) { action = a; break; }
+                    k--;
+                }
+        }
+        oracle_apply(g, action);
+    }
+}
+
+/* -------------------------------------------------------- batch helpers --
+ * State arrays used to move positions in and out of the oracle:
+ *   board[e*ncells + i]  int8 cell values
+ *   to_move[e] (1/2), ply[e], passes[e], outcome[e] (-1 ongoing)            */
+static void load_state(ogame* g, int game, int rows, int cols, int64_t e, const int8_t* board, const int8_t* to_move,
+                       const int16_t* ply, const int8_t* passes, const int8_t* outcome) {
+    oracle_init(g, game, rows, cols);
+    memcpy(g->cell, board + e * g->ncells, (size_t)g->ncells);
+    g->to_move = to_move[e];
+    g->ply = ply[e];
+    g->passes = passes[e];
+    g->outcome = outcome[e];
+}
+
+static void store_state(const ogame* g, int64_t e, int8_t* board, int8_t* to_move, int16_t* ply, int8_t* passes,
+                        int8_t* outcome) {
+    if (board) memcpy(board + e * g->ncells, g->cell, (size_t)g->ncells);
+    if (to_move) to_move[e] = (int8_t)g->to_move;
+    if (ply) ply[e] = (int16_t)g->ply;
+    if (passes) passes[e] = (int8_t)g->passes;
+    if (outcome) outcome[e] = (int8_t)g->outcome;
+}
+
+/* Playouts from the start position for envs env_offset .. env_offset+n-1.
+ * Outputs (each nullable): final boards, outcome, final ply.               */
+int oracle_rollout_start(int game, int rows, int cols, int64_t n, int64_t env_offset, uint64_t seed, int8_t* board,
+                         int8_t* outcome, int16_t* plies) {
+    ogame g;
+    if (oracle_check_params(game, rows, cols) != 0) return -1;
+    for (int64_t e = 0; e < n; e++) {
+        oracle_init(&g, game, rows, cols);
+        oracle_playout(&g, seed, (uint64_t)(env_offset + e), -1);
+        store_state(&g, e, board, NULL, plies, NULL, outcome);
+    }
+    return 0;
+}
+
+/* Playouts (or partial playouts up to stop_ply[e] when stop_ply is given)
+ * from the given states, which are updated in place.                      */
+int oracle_rollout_from(int game, int rows, int cols, int64_t n, int64_t env_offset, uint64_t seed, int8_t* board,
+                        int8_t* to_move, int16_t* ply, int8_t* passes, int8_t* outcome, const int16_t* stop_ply) {
+    ogame g;
+    if (oracle_check_params(game, rows, cols) != 0) return -1;
+    for (int64_t e = 0; e < n; e++) {
+        load_state(&g, game, rows, cols, e, board, to_move, ply, passes, outcome);
+        oracle_playout(&g, seed, (uint64_t)(env_offset + e), stop_ply ? stop_ply[e] : -1);
+        store_state(&g, e, board, to_move, ply, passes, outcome);
+    }
+    return 0;
+}
+
+/* One step for each env with the given actions; rewards [n][2] float,
+ * terminated [n] (1 when the game is over after the step), error [n] (1 for
+ * an illegal action).  States are updated in place.                        */
+int oracle_step_batch(int game, int rows, int cols, int64_t n, int8_t* board, int8_t* to_move, int16_t* ply,
+                      int8_t* passes, int8_t* outcome, const int32_t* actions, float* rewards, uint8_t* terminated,
+                      uint8_t* error) {
+    ogame g;
+    if (oracle_check_params(game, rows, cols) != 0) return -1;
+    for (int64_t e = 0; e < n; e++) {
+        int st;
+        load_state(&g, game, rows, cols, e, board, to_move, ply, passes, outcome);
+        st = oracle_apply(&g, actions[e]);
+        if (st == 1) {
+            rewards[2 * e] = rewards[2 * e + 1] = 0.0f;
+        } else if (g.outcome == OR_ONGOING || g.outcome == OR_CAPPED) {
+            rewards[2 * e] = rewards[2 * e + 1] = 0.0f;
+        } else {
+            oracle_rewards(&g, rewards + 2 * e);
+        }
+        terminated[e] = (uint8_t)(g.outcome != OR_ONGOING);
+        error[e] = (uint8_t)(st == -1);
+        store_state(&g, e, board, to_move, ply, passes, outcome);
+    }
+    return 0;
+}
+
+/* Legal-action masks for a batch of states: legal[e*A + a]. */
+int oracle_legal_batch(int game, int rows, int cols, int64_t n, const int8_t* board, const int8_t* to_move,
+                       const int16_t* ply, const int8_t* passes, const int8_t* outcome, uint8_t* legal) {
+    ogame g;
+    int A = oracle_num_actions(game, rows, cols);
+    if (oracle_check_params(game, rows, cols) != 0) return -1;
+    for (int64_t e = 0; e < n; e++) {
+        load_state(&g, game, rows, cols, e, board, to_move, ply, passes, outcome);
+        oracle_legal(&g, legal + e * A);
+    }
+    return 0;
+}
+
+/* Start positions for a batch (board, to_move, ply, passes, outcome). */
+int oracle_reset_batch(int game, int rows, int cols, int64_t n, int8_t* board, int8_t* to_move, int16_t* ply,
+                       int8_t* passes, int8_t* outcome) {
+    ogame g;
+    if (oracle_init(&g, game, rows, cols) != 0) return -1;
+    for (int64_t e = 0; e < n; e++) store_state(&g, e, board, to_move, ply, passes, outcome);
+    return 0;
+}
+
+/* Mixed batch: desc[e] packs game | rows << 8 | cols << 16 for env e. */
+int oracle_rollout_mixed(const int32_t* desc, int64_t n, int64_t env_offset, uint64_t seed, int8_t* outcome,
+                         int16_t* plies) {
+    ogame g;
+    for (int64_t e = 0; e < n; e++) {
+        int game = desc[e] & 0xFF, rows = (desc[e] >> 8) & 0xFF, cols = (desc[e] >> 16) & 0xFF;
+        if (oracle_init(&g, game, rows, cols) != 0) return -1;
+        oracle_playout(&g, seed, (uint64_t)(env_offset + e), -1);
+        outcome[e] = (int8_t)g.outcome;
+        plies[e] = (int16_t)g.ply;
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- perft --
+ * Number of action sequences of length depth from the start position in
+ * which no position before the last action is finished.                    */
+static uint64_t perft_rec(const ogame* g, int depth) {
+    uint8_t legal[OR_MAXCELLS + 1];
+    int A, n;
+    uint64_t total = 0;
+    if (depth == 0) return 1;
+    if (g->outcome != OR_ONGOING) return 0;
+    A = oracle_num_actions(g->game, g->rows, g->cols);
+    n = oracle_legal(g, legal);
+    (void)n;
+    for (int a = 0; a < A; a++) {
+        if (!legal[a]) continue;
+        ogame child = *g;
+        oracle_apply(&child, a);
+        total += perft_rec(&child, depth - 1);
+    }
+    return total;
+}
+
+uint64_t oracle_perft(int game, int rows, int cols, int depth) {
+    ogame g;
+    if (oracle_init(&g, game, rows, cols) != 0) return 0;
+    return perft_rec(&g, depth);
+}
+
+/* ------------------------------------------------- Tic-Tac-Toe enumeration --
+ * Walks every complete game; counts[length*3 + outcome] with outcome
+ * 0 draw, 1 X (P1) win, 2 O (P2) win, length in 0..9.                      */
+static void ttt_walk(const ogame* g, uint64_t* counts) {
+    uint8_t legal[16];
+    if (g->outcome != OR_ONGOING) {
+        counts[g->ply * 3 + g->outcome] += 1;
+        return;
+    }
+    oracle_legal(g, legal);
+    for (int a = 0; a < 9; a++) {
+        if (!legal[a]) continue;
+        ogame child = *g;
+        oracle_apply(&child, a);
+        ttt_walk(&child, counts);
+    }
+}
+
+void oracle_ttt_enumerate(uint64_t* counts /* [10*3] */) {
+    ogame g;
+    memset(counts, 0, sizeof(uint64_t) * 30);
+    oracle_init(&g, OR_TTT, 3, 3);
+    ttt_walk(&g, counts);
+}

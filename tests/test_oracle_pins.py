@@ -1,0 +1,308 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU needed).
+
+Each test checks the oracle against something it does not compute itself: a
+published value, a closed form, an invariant of the game, or brute force with
+an independent method.  A plausible slip in the oracle (a dropped direction,
+a wrong neighbour, a swapped start disc, the draw checked before the win)
+fails at least one of them.
+"""
+import numpy as np
+import pytest
+
+from conftest import golden
+from oracle import games as G
+
+
+# ---------------------------------------------------------------- RNG ----
+def test_splitmix64_published_sequence():
+    # state s_i = i * golden; output i = sm(s_{i}) with sm adding the golden
+    # increment first, i.e. output i = mix((i+1)*golden).
+    gamma = 0x9E3779B97F4A7C15
+    for idx, hexval in golden("splitmix64.txt"):
+        state = (int(idx) * gamma) % 2**64
+        assert G.sm(state) == int(hexval, 16)
+
+
+def test_pick_is_uniform_multiply_shift():
+    # k = floor(u * n / 2^32) for the top 32 bits u of the draw: check the
+    # extreme draws and that every index in [0, n) is reachable and balanced.
+    for n in (1, 2, 3, 7, 42, 64, 121):
+        assert G.pick(0, n) == 0
+        assert G.pick(2**64 - 1, n) == n - 1
+        ks = [G.pick(((u * 2**32) // n + 1) << 32, n) for u in range(n)]
+        assert ks == list(range(n))
+    # empirical uniformity over many draws
+    n, cnt = 7, np.zeros(7, int)
+    for ply in range(7000):
+        cnt[G.pick(G.draw(5, 11, ply), n)] += 1
+    assert cnt.min() > 850 and cnt.max() < 1150
+
+
+# ---------------------------------------------------------- Tic-Tac-Toe --
+def test_ttt_exhaustive_enumeration():
+    counts = G.ttt_enumerate()
+    want = np.zeros((10, 3), np.uint64)
+    for length, d, x, o in golden("ttt_enumeration.txt"):
+        want[int(length)] = [int(d), int(x), int(o)]
+    assert (counts == want).all()
+    assert int(counts.sum()) == 255168
+
+
+# ------------------------------------------------------------------ perft --
+@pytest.mark.parametrize("row", golden("perft.txt"), ids=lambda r: f"{r[0]}-d{r[1]}")
+def test_perft(row):
+    game, depth, count = row
+    gid, rows, cols = {"c4": (G.C4, 6, 7), "othello": (G.OTHELLO, 8, 8)}[game]
+    assert G.perft(gid, rows, cols, int(depth)) == int(count)
+
+
+def test_c4_perft_closed_form():
+    for d in range(1, 7):
+        assert G.perft(G.C4, 6, 7, d) == 7**d
+    assert G.perft(G.C4, 6, 7, 7) == 7**7 - 7
+
+
+# -------------------------------------------------------------------- Hex --
+def _hex_conn_numpy(n, cells):
+    """Independent connectivity check: iterative label propagation with
+    numpy over the six hex neighbours (r±1,c), (r,c±1), (r-1,c+1), (r+1,c-1)."""
+    b = np.asarray(cells, np.int8).reshape(n, n)
+    res = 0
+    for p, bit in ((1, 1), (2, 2)):
+        own = b == p
+        reach = np.zeros_like(own)
+        if p == 1:
+            reach[0, :] = own[0, :]
+        else:
+            reach[:, 0] = own[:, 0]
+        while True:
+            nb = reach.copy()
+            nb[1:, :] |= reach[:-1, :]
+            nb[:-1, :] |= reach[1:, :]
+            nb[:, 1:] |= reach[:, :-1]
+            nb[:, :-1] |= reach[:, 1:]
+            nb[:-1, 1:] |= reach[1:, :-1]   # (r+1,c-1) -> (r,c): source is down-left
+            nb[1:, :-1] |= reach[:-1, 1:]   # (r-1,c+1) -> (r,c)
+            nb &= own
+            if (nb == reach).all():
+                break
+            reach = nb
+        if (p == 1 and reach[n - 1, :].any()) or (p == 2 and reach[:, n - 1].any()):
+            res |= bit
+    return res
+
+
+@pytest.mark.parametrize("n", [2, 3, 4])
+def test_hex_every_full_board_has_one_winner_exhaustive(n):
+    cells = n * n
+    for code in range(2**cells):
+        b = np.array([1 + ((code >> i) & 1) for i in range(cells)], np.int8)
+        c = G.hex_connections(n, b)
+        assert c in (1, 2), (n, code, c)
+        if code % 97 == 0:
+            assert c == _hex_conn_numpy(n, b)
+
+
+@pytest.mark.parametrize("n", [7, 9, 11])
+def test_hex_random_full_boards_one_winner(n):
+    rng = np.random.default_rng(1234 + n)
+    for _ in range(1500):
+        b = rng.integers(1, 3, n * n).astype(np.int8)
+        c = G.hex_connections(n, b)
+        assert c in (1, 2)
+        assert c == _hex_conn_numpy(n, b)
+
+
+@pytest.mark.parametrize("n", [5, 7, 11])
+def test_hex_early_winner_equals_full_board_winner(n):
+    # Play random games to the end, then fill every empty cell alternately:
+    # the unique winner of the full board is the player who won early.
+    out, plies, boards = G.rollout_start(G.HEX, n, n, 200, seed=77, want_boards=True)
+    rng = np.random.default_rng(n)
+    for e in range(200):
+        assert out[e] in (1, 2)
+        b = boards[e].copy()
+        assert _hex_conn_numpy(n, b) == out[e]   # only the winner connects
+        empty = np.flatnonzero(b == 0)
+        rng.shuffle(empty)
+        nxt = 3 - out[e] if plies[e] % 2 == 1 else out[e]
+        for i in empty:
+            b[i] = nxt
+            nxt = 3 - nxt
+        assert G.hex_connections(n, b) == out[e]
+        # the winner moved last: P1 moves on odd final ply counts
+        assert out[e] == (1 if plies[e] % 2 == 1 else 2)
+
+
+@pytest.mark.parametrize("n", [3, 7, 11])
+def test_hex_earliest_win_and_diagonal_reading(n):
+    # P1 plays down column 0 while P2 plays down column n-1: P1 connects
+    # top-bottom at ply 2n-1 and not before.
+    s = G.reset(G.HEX, n, n, 1)
+    for k in range(n):
+        G.step(s, [k * n + 0])
+        if k < n - 1:
+            assert s.outcome[0] == -1
+            G.step(s, [k * n + n - 1] if k * n + n - 1 != k * n else [(k + 1) * n - 1])
+            assert s.outcome[0] == -1
+    assert s.outcome[0] == 1 and s.ply[0] == 2 * n - 1
+    # Reading of the rhombus: (r,c)-(r+1,c-1) are neighbours, (r,c)-(r+1,c+1) are not.
+    b = np.zeros(n * n, np.int8)
+    for r in range(n):
+        b[r * n + (n - 1 - r)] = 1          # anti-diagonal chain
+    assert G.hex_connections(n, b) & 1
+    b[:] = 0
+    for r in range(n):
+        b[r * n + r] = 1                    # main diagonal: no connection for n > 1
+    assert not (G.hex_connections(n, b) & 1)
+
+
+# ---------------------------------------------------------------- Othello --
+def test_othello_start_position():
+    s = G.reset(G.OTHELLO, 8, 8, 1)
+    b = s.board[0]
+    assert b[27] == 2 and b[36] == 2 and b[28] == 1 and b[35] == 1
+    assert (b != 0).sum() == 4
+    # black (P1) to move has the four standard openings d3, c4, f5, e6
+    assert sorted(np.flatnonzero(G.legal(s)[0])) == [19, 26, 37, 44]
+
+
+def test_othello_forced_pass_and_end_by_count():
+    s = G.States(G.OTHELLO, 8, 8, 1)
+    s.to_move[:] = 2
+    s.outcome[:] = -1
+    s.board[0, [0, 1, 9]] = 1            # P1 discs only: P2 cannot move
+    m = G.legal(s)[0]
+    assert m[64] == 1 and m[:64].sum() == 0
+    rew, term, err = G.step(s, [64])
+    assert not term[0] and s.passes[0] == 1 and s.to_move[0] == 1
+    m = G.legal(s)[0]
+    assert m[64] == 1 and m[:64].sum() == 0   # P1 has no custodial move either
+    rew, term, err = G.step(s, [64])
+    assert term[0] and s.outcome[0] == 1 and tuple(rew[0]) == (1.0, -1.0)
+    assert s.ply[0] == 2
+
+
+def test_othello_tie_is_draw_and_pass_resets():
+    s = G.States(G.OTHELLO, 8, 8, 1)
+    s.to_move[:] = 1
+    s.outcome[:] = -1
+    s.board[0, 0] = 1
+    s.board[0, 63] = 2
+    G.step(s, [64])
+    G.step(s, [64])
+    assert s.outcome[0] == 0
+    # a move after a pass resets the pass counter
+    s = G.reset(G.OTHELLO, 8, 8, 1)
+    s.passes[:] = 1
+    G.step(s, [19])
+    assert s.passes[0] == 0 and s.board[0, 27] == 1  # d3 flips d4
+
+
+def test_othello_flips_all_directions():
+    # P1 at the centre surrounded by rays of P2 discs closed by P1 discs in
+    # all eight directions: every P2 disc on the rays flips.
+    s = G.States(G.OTHELLO, 8, 8, 1)
+    s.to_move[:] = 1
+    s.outcome[:] = -1
+    r0, c0 = 3, 3
+    for dr in (-1, 0, 1):
+        for dc in (-1, 0, 1):
+            if dr == dc == 0:
+                continue
+            s.board[0, (r0 + dr) * 8 + c0 + dc] = 2
+            s.board[0, (r0 + 2 * dr) * 8 + c0 + 2 * dc] = 1
+    G.step(s, [r0 * 8 + c0])
+    assert (s.board[0] == 2).sum() == 0 and (s.board[0] == 1).sum() == 17
+
+
+def test_othello_disc_conservation_random():
+    out, plies, boards = G.rollout_start(G.OTHELLO, 8, 8, 300, seed=2, want_boards=True)
+    s = G.reset(G.OTHELLO, 8, 8, 300)
+    G.rollout_from(s, seed=2)
+    assert (s.outcome == out).all() and (s.ply == plies).all()
+    discs = (boards != 0).sum(1)
+    assert (discs <= 64).all()
+    # passes are plies that place nothing; the game ends with exactly two
+    placements = discs - 4
+    npass = plies.astype(int) - placements
+    assert (npass >= 2).all()
+    n1, n2 = (boards == 1).sum(1), (boards == 2).sum(1)
+    want = np.where(n1 > n2, 1, np.where(n2 > n1, 2, 0))
+    assert (out == want).all()
+
+
+# ------------------------------------------------------------ Connect Four --
+def _lines(board, p, L, rows, cols):
+    b = (np.asarray(board).reshape(rows, cols) == p)
+    for dr, dc in ((0, 1), (1, 0), (1, 1), (1, -1)):
+        for r in range(rows):
+            for c in range(cols):
+                rr, cc = r + (L - 1) * dr, c + (L - 1) * dc
+                if 0 <= rr < rows and 0 <= cc < cols and all(b[r + k * dr, c + k * dc] for k in range(L)):
+                    return True
+    return False
+
+
+def test_c4_random_games_consistent():
+    out, plies, boards = G.rollout_start(G.C4, 6, 7, 400, seed=1, want_boards=True)
+    for e in range(400):
+        b = boards[e].reshape(6, 7)
+        # gravity: no empty cell under a stone
+        for c in range(7):
+            col = b[:, c]
+            filled = np.flatnonzero(col)
+            if filled.size:
+                assert (col[filled.min():] != 0).all()
+        assert (b != 0).sum() == plies[e]
+        if out[e] == 0:
+            assert plies[e] == 42
+            assert not _lines(b, 1, 4, 6, 7) and not _lines(b, 2, 4, 6, 7)
+        else:
+            assert _lines(b, out[e], 4, 6, 7) and not _lines(b, 3 - out[e], 4, 6, 7)
+            assert out[e] == (1 if plies[e] % 2 == 1 else 2)
+    assert set(np.unique(out)) <= {0, 1, 2}
+
+
+def test_c4_legal_cells_gravity():
+    s = G.reset(G.C4, 6, 7, 1)
+    assert list(np.flatnonzero(G.legal(s)[0])) == list(range(35, 42))
+    G.step(s, [38])
+    assert list(np.flatnonzero(G.legal(s)[0])) == [31, 35, 36, 37, 39, 40, 41]
+    for _ in range(5):
+        G.step(s, [int(np.flatnonzero(G.legal(s)[0])[0])])  # fill column 3 upward
+    assert s.board[0, 3] != 0 and not G.legal(s)[0, 3]      # column 3 full
+
+
+def test_ttt_win_beats_draw_on_last_move():
+    # X O O / O X X / X O X: X's ninth-ply move at 8 fills the board and
+    # completes the diagonal 0-4-8, so the game is a win, not a draw (Sec. 3.3).
+    s = G.reset(G.TTT, 3, 3, 1)
+    for i, a in enumerate((0, 1, 4, 2, 5, 3, 6, 7, 8)):
+        assert s.outcome[0] == -1, i
+        G.step(s, [a])
+    assert s.board[0].tolist() == [1, 2, 2, 2, 1, 1, 1, 2, 1]
+    assert s.outcome[0] == 1 and s.ply[0] == 9
+
+
+# ------------------------------------------------------------- step API ---
+@pytest.mark.parametrize("game,rows,cols", [(G.TTT, 3, 3), (G.C4, 6, 7), (G.OTHELLO, 8, 8), (G.HEX, 5, 5)])
+def test_illegal_action_mover_loses(game, rows, cols):
+    s = G.reset(game, rows, cols, 2)
+    if game in (G.TTT, G.HEX):
+        G.step(s, [0, 0])                 # P1 takes cell 0, then P2 repeats it
+        bad, mover = 0, 2
+    elif game == G.C4:
+        bad, mover = 0, 1                 # top-left cell: nothing below it
+    else:
+        bad, mover = 27, 1                # occupied start disc
+    rew, term, err = G.step(s, [bad, -5])
+    assert err.tolist() == [1, 1] and term.tolist() == [1, 1]
+    for e in range(2):
+        assert s.outcome[e] == 3 - mover
+        assert rew[e, mover - 1] == -1.0 and rew[e, 2 - mover] == 1.0
+    # stepping a finished env is a no-op with zero reward
+    before = s.copy()
+    rew, term, err = G.step(s, [1, 1])
+    assert (rew == 0).all() and term.all() and not err.any()
+    assert (s.board == before.board).all() and (s.ply == before.ply).all()
