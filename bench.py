@@ -1,0 +1,440 @@
+"""Benchmark: env steps/s of uniform-random playouts on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c4|ttt|othello|hex11|mixed] [--no-extras] [--no-cpu-baseline]
+
+One step = one fused playout launch over the whole batch: every env of the
+workload is reset to the start position and played to the end of its game
+with the counter-based uniform-random policy (legal mask, draw, select,
+apply with captures/flips/gravity, terminal and win detection, all in
+registers), and each env's outcome and game length are written to HBM.
+The default workload is Connect Four 6x7, 65,536 envs, seed 1.
+
+Metric: env steps per second = total plies played (passes included) / time.
+`value` is device time (CUDA events on the launching stream) with L2 flushed
+between steps; `e2e` goes through the public API with host buffers: start
+positions copied from pinned host memory and loaded with ludax_set_state,
+the playout, and outcome + game length copied back to pinned host memory.
+
+Under torchrun (N > 1) each rank plays its own disjoint range of global env
+ids (weak scaling, no collective on the data path); the step time is the
+maximum over ranks.  `--impl reference` times the CPU oracle (plain C, all
+host cores) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env steps/sec on 1 B300 (random playouts); value estimates/sec at stated MAE"
+
+# Algorithmic 32-bit integer operations per env step of the fused playout,
+# counted from the bitboard algorithm (RNG draw, legal mask, count, select,
+# apply, end test); the derivation per game is in the design notes.
+ALG_OPS_PER_STEP = {"ttt": 73, "c4": 110, "othello": 560, "hex": 150}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "mixed"])
+    p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of the CPU-baseline sample")
+    return p.parse_args()
+
+
+def workload_cfg(name):
+    from paper_2506_22609_b300 import workloads as W
+
+    return {"c4": W.C4_64K, "ttt": W.TTT_1K, "othello": W.OTHELLO_256K, "hex11": W.HEX11_64K}[name]
+
+
+def game_key(cfg):
+    return {0: "ttt", 1: "c4", 2: "othello", 3: "hex"}[cfg.game]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    """Polls NVML (SM clock, max clock, clock-event reasons) in a thread."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, index, period=0.005):
+        self.samples, self.reasons, self.period, self.index = [], set(), period, index
+        self.max_mhz = None
+        self._stop = threading.Event()
+        try:
+            import pynvml
+
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+        except Exception as e:  # NVML missing: report no clock record
+            self.nv, self.err = None, str(e)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                r = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                for bit, name in self.REASONS.items():
+                    if r & bit:
+                        self.reasons.add(name)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.nv:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self.nv:
+            self.t.join()
+
+    def record(self):
+        if not self.nv:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "NVML unavailable"}
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+def cpu_oracle_rate(cfg, seconds, desc=None):
+    """The CPU oracle as it stands (plain C, -O2), all host cores via threads
+    (ctypes releases the GIL), on a sample of the workload's envs sized to
+    take about `seconds`.  Returns (steps/s, cores, sample description)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
+    from oracle import games as OG
+
+    cores = len(os.sched_getaffinity(0))
+
+    def run(n, off):
+        if desc is not None:
+            _, p = OG.rollout_mixed(desc[off:off + n], cfg.seed, env_offset=off)
+        else:
+            _, p, _ = OG.rollout_start(cfg.game, cfg.rows, cfg.cols, n, cfg.seed, env_offset=off)
+        return int(p.astype(np.int64).sum())
+
+    total_envs = cfg.num_envs
+    # calibrate on one core
+    n0 = 256
+    t0 = time.perf_counter()
+    run(n0, 0)
+    per_env = max((time.perf_counter() - t0) / n0, 1e-7)
+    n = int(min(total_envs, max(cores * 64, seconds * cores / per_env)))
+    chunk = (n + cores - 1) // cores
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        steps = sum(ex.map(lambda i: run(min(chunk, n - i * chunk), i * chunk), range(cores)))
+    dt = time.perf_counter() - t0
+    return steps / dt, cores, f"first {n} of {total_envs} envs (global ids 0..{n - 1}), {cores} threads, {dt:.2f} s"
+
+
+# ------------------------------------------------------------- GPU parts --
+def flush_l2(buf):
+    buf.add_(1)  # 256 MiB read + write: evicts the 126 MB L2
+
+
+def time_steps(fn, steps, warmup, flush_buf, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush_l2(flush_buf)
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def bench_rollout_config(L, W, cfg, steps, warmup, flush_buf, rank=0):
+    """Fused playout of one single-game config; returns a dict of numbers."""
+    import torch
+
+    n = cfg.num_envs
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=rank * n)
+    lc = L.make_cfg(*W.bench_cfg(cfg))
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies = torch.empty(n, dtype=torch.int16, device="cuda")
+    stream = torch.cuda.current_stream()
+    fn = lambda: L.ludax_rollout(env.handle, cfg.seed, L.LUDAX_ROLLOUT_FROM_START, None, out, plies, lc)  # noqa: E731
+    ms = time_steps(fn, steps, warmup, flush_buf, stream)
+    steps_per_launch = int(plies.to(torch.int64).sum().item())
+    return env, lc, ms, steps_per_launch
+
+
+def e2e_rollout(L, cfg, steps, warmup, rank=0):
+    """Public-API path with host buffers: H2D start positions (pinned) +
+    ludax_set_state + ludax_rollout + D2H outcome/plies (pinned)."""
+    import numpy as np
+    import torch
+
+    n = cfg.num_envs
+    cells = cfg.rows * cfg.cols
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=rank * n)
+    # start positions, built on the host from the game's own start rule
+    b0, tm0, ply0, ps0, oc0 = env.get_state()
+    host_in = [t.cpu().pin_memory() for t in (b0, tm0, ply0, ps0, oc0)]
+    dev_in = [torch.empty_like(t, device="cuda") for t in host_in]
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies = torch.empty(n, dtype=torch.int16, device="cuda")
+    h_out = torch.empty(n, dtype=torch.int8).pin_memory()
+    h_plies = torch.empty(n, dtype=torch.int16).pin_memory()
+    lc = None
+    from paper_2506_22609_b300 import workloads as W
+
+    lc = L.make_cfg(*W.bench_cfg(cfg))
+
+    def step():
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        L.ludax_set_state(env.handle, *dev_in)
+        L.ludax_rollout(env.handle, cfg.seed, 0, None, out, plies, lc)
+        h_out.copy_(out, non_blocking=True)
+        h_plies.copy_(plies, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    for _ in range(warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = (time.perf_counter() - t0) / steps
+    steps_per_launch = int(h_plies.numpy().astype(np.int64).sum())
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = n * 1 + n * 2
+    env.close()
+    return steps_per_launch / dt, h2d, d2h, dt, cells
+
+
+def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
+    import torch
+
+    d = torch.from_numpy(W.mixed_descriptors(W.MIXED_ENVS, "block")).cuda()
+    plan = L.ludax_mixed_plan_create(d, rank * W.MIXED_ENVS, L.make_cfg(*W.mixed_bench_cfg()))
+    out = torch.empty(W.MIXED_ENVS, dtype=torch.int8, device="cuda")
+    plies = torch.empty(W.MIXED_ENVS, dtype=torch.int16, device="cuda")
+    fn = lambda: L.ludax_mixed_plan_launch(plan, W.MIXED_SEED, out, plies)  # noqa: E731
+    ms = time_steps(fn, steps, warmup, flush_buf, torch.cuda.current_stream())
+    total = int(plies.to(torch.int64).sum().item())
+    L.ludax_mixed_plan_destroy(plan)
+    return ms, total
+
+
+def bench_step_mode(L, steps, flush_buf):
+    """Step-per-launch mode (ludax_random_step) at a batch far above L2:
+    HBM-bound; returns achieved GB/s of algorithmic state traffic."""
+    import torch
+
+    n = 1 << 22
+    env = L.Env("othello", 8, 8, n)
+    rew = torch.empty(n, 2, device="cuda")
+    term = torch.empty(n, dtype=torch.uint8, device="cuda")
+    # advance a few plies so that the timed steps are mid-game
+    for _ in range(4):
+        L.ludax_random_step(env.handle, 2, rew, term)
+    ms = time_steps(lambda: L.ludax_random_step(env.handle, 2, rew, term), steps, 2, flush_buf,
+                    torch.cuda.current_stream())
+    # per env-step: read 2 planes + meta (20 B), write 2 planes + meta (20 B), rewards 8 B, terminated 1 B
+    bytes_per = 20 + 20 + 8 + 1
+    t = statistics.median(ms) / 1e3
+    env.close()
+    return {"workload": "othello8x8_4194304env_random_step", "ms": statistics.median(ms),
+            "gbs": n * bytes_per / t / 1e9, "bytes_per_env_step": bytes_per, "env_steps_per_s": n / t}
+
+
+# ------------------------------------------------------------------ main --
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return reference_arm(args)
+
+    import torch
+
+    from paper_2506_22609_b300 import build as B
+
+    B.build()
+    from paper_2506_22609_b300 import ludax as L
+    from paper_2506_22609_b300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peaks, peak_kind = measured_peaks()
+    flush_buf = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB
+
+    cfg = workload_cfg(args.workload) if args.workload != "mixed" else None
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if cfg is not None:
+            env, lc, ms, steps_per_launch = bench_rollout_config(L, W, cfg, args.steps, args.warmup, flush_buf, rank)
+            wl_name, n_envs, seed = cfg.name, cfg.num_envs, cfg.seed
+            launch = lc.as_dict()
+        else:
+            ms, steps_per_launch = bench_mixed(L, W, args.steps, args.warmup, flush_buf, rank)
+            wl_name, n_envs, seed = "mixed6_1048576env_seed3_graph", W.MIXED_ENVS, W.MIXED_SEED
+            launch = dict(zip(("block_threads", "blocks_per_sm", "envs_per_thread", "hex_nbr_table"),
+                              W.mixed_bench_cfg()))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    clocks = clk.record()
+
+    total_ms = sum(ms)
+    mean_ms = total_ms / len(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        s = torch.tensor([steps_per_launch], dtype=torch.float64, device="cuda")
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        all_steps = float(s.item())
+    else:
+        all_steps = float(steps_per_launch)
+    value = all_steps * args.steps / (total_ms / 1e3)
+
+    # roofline of the fused playout kernel: integer issue
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    peak_ops = sms * 128 * max_mhz * 1e6  # 32-bit lanes x clock
+    if cfg is not None:
+        ops_per_launch = ALG_OPS_PER_STEP[game_key(cfg)] * steps_per_launch
+    else:
+        ops_per_launch = None
+    med = statistics.median(ms)
+    roofline = None
+    if ops_per_launch:
+        achieved = ops_per_launch / (med / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_ops / 1e12, 3),
+                    "unit": "Tops/s (32-bit integer)", "frac": round(achieved / (peak_ops / 1e12), 4),
+                    "traffic": None,
+                    "peak_source": f"{sms} SMs x 128 int32 lanes x {max_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
+                    "alg_ops_per_step": ALG_OPS_PER_STEP[game_key(cfg)], "median_launch_ms": round(med, 5)}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "env steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic (start positions; counter-based uniform-random policy)",
+            "config": {"workload": wl_name, "num_envs_per_gpu": n_envs, "seed": seed, "launch": launch,
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "timing": "CUDA events around each launch on the launching stream, summed over steps",
+                       "env_steps_per_launch": steps_per_launch, "episodes_per_launch": n_envs},
+            "roofline": roofline, "clocks": clocks,
+            "gpu_launches": args.steps * (1 if cfg is not None else 2)}
+
+    if rank == 0 and cfg is not None:
+        e2e_val, h2d, d2h, dt, _ = e2e_rollout(L, cfg, max(3, min(args.steps, 50)), 2, rank)
+        line["e2e"] = {"value": round(e2e_val * world, 1), "unit": "env steps/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4),
+                       "path": "pinned host start positions -> ludax_set_state -> ludax_rollout -> pinned host "
+                               "outcome/plies, wall clock per step"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if cfg is not None:
+            v, cores, sample = cpu_oracle_rate(cfg, args.cpu_seconds)
+        else:
+            v, cores, sample = cpu_oracle_rate(W_mixed_cfg(W), args.cpu_seconds,
+                                               desc=W.mixed_descriptors(W.MIXED_ENVS, "block"))
+        line["cpu_baseline"] = {"value": round(v, 1), "unit": "env steps/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = {}
+        for name in ("ttt", "othello", "hex11"):
+            c = workload_cfg(name)
+            e, lc, ms2, spl = bench_rollout_config(L, W, c, 20, 3, flush_buf)
+            m2 = statistics.median(ms2)
+            extras[c.name] = {"env_steps_per_s": round(spl / (m2 / 1e3), 1), "median_launch_ms": round(m2, 5),
+                              "env_steps_per_launch": spl, "launch": lc.as_dict()}
+            e.close()
+        ms3, tot = bench_mixed(L, W, 10, 2, flush_buf)
+        m3 = statistics.median(ms3)
+        extras["mixed6_1048576env_seed3_graph"] = {"env_steps_per_s": round(tot / (m3 / 1e3), 1),
+                                                   "median_launch_ms": round(m3, 4), "env_steps_per_launch": tot}
+        sm = bench_step_mode(L, 10, flush_buf)
+        sm["hbm_frac"] = round(sm["gbs"] / float(peaks.get("hbm_gbs", 6400.0)), 4)
+        extras["step_mode"] = sm
+        line["extra_workloads"] = extras
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def W_mixed_cfg(W):
+    return W.Config("mixed6_1048576env_seed3", -1, 0, 0, W.MIXED_ENVS, W.MIXED_SEED)
+
+
+def reference_arm(args):
+    """The CPU oracle as the reference arm: each step is a bounded sample of
+    the workload on all host cores."""
+    from paper_2506_22609_b300 import workloads as W
+
+    if args.workload == "mixed":
+        cfg = W_mixed_cfg(W)
+        desc = W.mixed_descriptors(W.MIXED_ENVS, "block")
+    else:
+        cfg, desc = workload_cfg(args.workload), None
+    per_step = max(0.5, min(4.0, 120.0 / max(1, args.steps + args.warmup)))
+    vals, sample = [], ""
+    for i in range(args.warmup + args.steps):
+        v, cores, sample = cpu_oracle_rate(cfg, per_step, desc=desc)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "env steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8 cells", "data": "synthetic",
+            "config": {"workload": cfg.name, "num_envs_per_gpu": cfg.num_envs, "seed": cfg.seed},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(value, 1),
+                             "unit": "env steps/s"},
+            "e2e": {"value": round(value, 1), "unit": "env steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,259 @@
+/*
+ * ludax.h -- C-ABI of the B300 batched board-game engine.
+ *
+ * The engine runs the hot path of Ludax's compiled board-game environments
+ * (Ludax, arXiv 2506.22609): batched game stepping over very many parallel
+ * environments and uniform-random playouts to termination, for Tic-Tac-Toe,
+ * Connect Four, Reversi/Othello and Hex (rules: App. C of the paper).  The
+ * interface mirrors the paper's environment API (a PGX-shaped env with
+ * init/step, a fixed-size legal-action mask, rewards and a terminated flag;
+ * Sec. 1, Sec. 3.4 and Sec. 4) with every call batched over num_envs envs.
+ *
+ * Conventions shared by every entry point:
+ *   - Status: each function returns LUDAX_OK (0) or a negative LUDAX_ERR_*.
+ *     Nothing throws or aborts across the ABI.  Arguments are validated on
+ *     the host before any launch; a rejected call launches nothing.
+ *   - Ownership: every pointer named *_dev is device memory owned by the
+ *     caller (for instance a torch tensor's data_ptr()), valid until the
+ *     launched work has finished.  The env owns its own state buffer, which
+ *     it allocates in ludax_env_create and frees in ludax_env_destroy.
+ *   - Asynchrony: launches are asynchronous on the env's CUDA stream (the
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).  Use
+ *     ludax_sync, or the caller's own stream synchronisation, before reading
+ *     outputs on the host.
+ *   - Cells: the canonical cell id of row r, column c is r*cols + c with row
+ *     0 at the TOP of the board (the numbering of the paper's English
+ *     Draughts listing, App. A, where P1 moves up from cells 40..62).
+ *   - Actions: one action per cell, the destination cell (Sec. 3.4; for
+ *     Connect Four the legal cells are the empty cells on the bottom row or
+ *     directly above an occupied cell).  Reversi adds one pass action with
+ *     id rows*cols (= 64), legal only when no cell is (force_pass, App. B).
+ *   - Players: P1 moves first; cell values 0 empty, 1 P1, 2 P2.
+ *   - Outcome codes: LUDAX_OUTCOME_*.  Rewards are float32 pairs [P1, P2]:
+ *     (+1,-1) P1 wins, (-1,+1) P2 wins, (0,0) draw or not finished.
+ *   - Randomness: the uniform-random policy draws r = sm(key ^ ply) with
+ *     key = sm(sm(seed) ^ env), sm the splitmix64 output function (Steele,
+ *     Lea and Flood 2014), env the GLOBAL env index (env_offset + local
+ *     index) and ply the env's ply counter (passes included).  The move is
+ *     the k-th legal cell in ascending cell id with k = ((r >> 32) * n) >> 32
+ *     for n legal cells.  A forced pass consumes a ply but no draw.  Every
+ *     trajectory is therefore reproducible from (seed, env, start state),
+ *     independent of launch shape, thread mapping or refill order.
+ */
+#ifndef LUDAX_H
+#define LUDAX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status -- */
+#define LUDAX_OK 0
+#define LUDAX_ERR_ARG (-1)     /* null pointer, bad count, bad flag       */
+#define LUDAX_ERR_GAME (-2)    /* unknown game id or descriptor            */
+#define LUDAX_ERR_SIZE (-3)    /* board size not supported for the game    */
+#define LUDAX_ERR_CUDA (-4)    /* a CUDA runtime call failed               */
+#define LUDAX_ERR_TIMEOUT (-5) /* ludax_sync deadline passed              */
+#define LUDAX_ERR_ALIGN (-6)   /* a device pointer is misaligned           */
+#define LUDAX_ERR_NOMEM (-7)   /* device allocation failed                 */
+
+/* ------------------------------------------------------------- games -- */
+#define LUDAX_GAME_TTT 0     /* Tic-Tac-Toe 3x3, line of 3                 */
+#define LUDAX_GAME_C4 1      /* Connect Four 6x7, gravity, line of 4       */
+#define LUDAX_GAME_OTHELLO 2 /* Reversi/Othello 8x8, flips, forced pass    */
+#define LUDAX_GAME_HEX 3     /* Hex n x n rhombus, 2 <= n <= 11            */
+
+/* ---------------------------------------------------------- outcomes -- */
+#define LUDAX_OUTCOME_ONGOING (-1)
+#define LUDAX_OUTCOME_DRAW 0
+#define LUDAX_OUTCOME_P1 1
+#define LUDAX_OUTCOME_P2 2
+#define LUDAX_OUTCOME_CAPPED 3 /* ply cap (9/42/128/n*n) hit: never for a correct engine */
+
+/* ------------------------------------------------------ rollout flags -- */
+#define LUDAX_ROLLOUT_FROM_START 1u /* play from the start position; stored state not read */
+#define LUDAX_ROLLOUT_WRITE_BACK 2u /* store each env's final state back into the env       */
+
+typedef struct {
+    int32_t rows;
+    int32_t cols;
+} ludax_board_params;
+
+typedef struct ludax_env ludax_env;
+
+/* A batch of positions in canonical form, all arrays on the device:
+ *   board   int8  [num_envs][rows*cols]  cell values 0/1/2
+ *   to_move int8  [num_envs]             1 or 2
+ *   ply     int16 [num_envs]             plies played (passes included)
+ *   passes  int8  [num_envs]             consecutive passes (Reversi; else 0)
+ *   outcome int8  [num_envs]             LUDAX_OUTCOME_*                      */
+typedef struct {
+    int8_t* board;
+    int8_t* to_move;
+    int16_t* ply;
+    int8_t* passes;
+    int8_t* outcome;
+} ludax_state_view;
+
+/* Launch shape of the persistent playout kernels (see ludax_autotune). */
+typedef struct {
+    int32_t block_threads;   /* threads per block: 32..512, multiple of 32           */
+    int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid, >= 1;
+                                0 = one thread per env (no persistence)               */
+    int32_t envs_per_thread; /* envs each thread advances together (ILP): 1 or 2     */
+    int32_t hex_nbr_table;   /* Hex neighbour test: 0 = bit shifts, 1 = shared-memory
+                                table of per-cell neighbour masks                     */
+} ludax_launch_cfg;
+
+/* ---------------------------------------------------------------------------
+ * Environment lifetime.
+ *
+ * ludax_env_create: a batch of num_envs independent envs of one game, in the
+ * start position (Sec. 3.1: empty board, Reversi's four discs at D4/E5 white =
+ * P2 on cells 27/36 and D5/E4 black = P1 on cells 35/28; P1 to move).
+ *   game       LUDAX_GAME_*
+ *   p          board size: TTT 3x3, C4 6x7, Othello 8x8, Hex n x n (2..11)
+ *   num_envs   1 .. 2^31-1
+ *   env_offset global index of env 0 (keys the random draws; lets several
+ *              GPUs or calls cover disjoint env ranges), >= 0
+ *   stream     cudaStream_t for every launch of this env (NULL = default)
+ * Allocates the env's state on the current device.  Returns LUDAX_ERR_GAME,
+ * LUDAX_ERR_SIZE, LUDAX_ERR_ARG or LUDAX_ERR_NOMEM without side effects.   */
+int ludax_env_create(ludax_env** out, int32_t game, const ludax_board_params* p, int64_t num_envs, int64_t env_offset,
+                     void* stream);
+/* Frees the env's state (synchronises its stream first).  NULL is a no-op. */
+int ludax_env_destroy(ludax_env* env);
+/* Rebind the env to another stream (same device). */
+int ludax_env_set_stream(ludax_env* env, void* stream);
+
+/* Sizes of the env's action space: num_actions = rows*cols (+1 pass for
+ * Reversi); mask_words = ceil(rows*cols / 64) words per env in legal masks. */
+int ludax_env_sizes(const ludax_env* env, int32_t* num_actions, int32_t* mask_words, int64_t* num_envs);
+
+/* ---------------------------------------------------------------------------
+ * ludax_reset: put envs back in the start position.  env_mask_dev (uint8
+ * [num_envs], nullable) selects the envs to reset; NULL resets all.        */
+int ludax_reset(ludax_env* env, const uint8_t* env_mask_dev);
+
+/* ludax_legal_mask: the legal-action mask of each env (Sec. 3.2: the legal
+ * action mask function of the play mechanic; Sec. 4: fixed size).
+ *   mask_dev       uint64 [num_envs][mask_words]: bit (i % 64) of word i/64
+ *                  set when cell i is a legal destination; all zero for a
+ *                  finished env
+ *   pass_legal_dev uint8 [num_envs], nullable: 1 when the pass action is the
+ *                  (only) legal action (Reversi with no legal cell)          */
+int ludax_legal_mask(ludax_env* env, uint64_t* mask_dev, uint8_t* pass_legal_dev);
+
+/* ludax_step: apply actions_dev[e] (int32 action ids) to every env, then
+ * apply the effects (Reversi flips), the end rules in order (win before
+ * draw, Sec. 3.3) and write
+ *   rewards_dev    float32 [num_envs][2] rewards [P1, P2] of this step
+ *   terminated_dev uint8 [num_envs] 1 when the env is finished after it.
+ * A finished env is left unchanged with zero rewards.  An illegal action
+ * (out of range, occupied, not supported by gravity, not custodial, or a pass
+ * while a cell is legal) ends the env: the mover gets -1, the opponent +1,
+ * the outcome names the opponent, and the env's illegal-action counter (see
+ * ludax_counters) is incremented.  The paper does not define this case; the
+ * rule follows the PGX environments Ludax builds on.                       */
+int ludax_step(ludax_env* env, const int32_t* actions_dev, float* rewards_dev, uint8_t* terminated_dev);
+
+/* ludax_random_step: one step of the uniform-random policy for every env
+ * (the random-policy benchmark of Sec. 6), drawing each action as described
+ * at the top of this file with the given seed.  Outputs as ludax_step.
+ * Repeated calls reproduce ludax_rollout's trajectories ply for ply.       */
+int ludax_random_step(ludax_env* env, uint64_t seed, float* rewards_dev, uint8_t* terminated_dev);
+
+/* ludax_rollout: uniform-random playout of every env to the end of its game
+ * in one fused persistent kernel (state stays in registers; lanes take a new
+ * env when theirs finishes).
+ *   seed           keys the draws
+ *   flags          LUDAX_ROLLOUT_FROM_START | LUDAX_ROLLOUT_WRITE_BACK
+ *   stop_ply_dev   int16 [num_envs], nullable: stop an env as soon as its
+ *                  ply counter reaches stop_ply (outcome then -1)
+ *   outcome_dev    int8 [num_envs], nullable: LUDAX_OUTCOME_* at the end
+ *   plies_dev      int16 [num_envs], nullable: the env's final ply counter
+ *                  (game length, passes included, when played from start)
+ *   cfg            launch shape, nullable = the built-in default           */
+int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* stop_ply_dev, int8_t* outcome_dev,
+                  int16_t* plies_dev, const ludax_launch_cfg* cfg);
+
+/* ludax_rollout_value: for every env, R independent uniform-random playouts
+ * from its current state; playout j (0 <= j < R) draws with seed + j.
+ *   value_dev float32 [num_envs]: mean result from P1's view (win 1, draw
+ *             0.5, loss 0) -- the Monte-Carlo value estimate of the position.
+ * The env's state is not modified.                                         */
+int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_dev, const ludax_launch_cfg* cfg);
+
+/* ludax_get_state / ludax_set_state: copy every env's position out of / into
+ * the canonical view (all five arrays required, device memory).  set_state
+ * validates nothing about reachability; it rebuilds the engine's internal
+ * form (bitboards, Hex edge-connected sets) from the cell values.          */
+int ludax_get_state(ludax_env* env, const ludax_state_view* dst);
+int ludax_set_state(ludax_env* env, const ludax_state_view* src);
+
+/* ludax_counters: host-visible totals since creation (synchronises the
+ * env's stream): illegal actions seen by ludax_step, envs that hit the ply
+ * cap.  Either pointer may be NULL.                                         */
+int ludax_counters(ludax_env* env, int64_t* illegal_actions, int64_t* capped);
+
+/* ludax_sync: wait for the env's stream with a deadline by polling
+ * (cudaStreamQuery); LUDAX_ERR_TIMEOUT when timeout_ms passes first
+ * (the work is not cancelled).  timeout_ms < 0 waits without a deadline.  */
+int ludax_sync(ludax_env* env, int64_t timeout_ms);
+
+const char* ludax_status_string(int status);
+
+/* ---------------------------------------------------------------------------
+ * Mixed-game batches: one persistent launch over envs of different games and
+ * board sizes, each env's game given by an int32 descriptor
+ *   desc = game | rows << 8 | cols << 16
+ * (LUDAX_DESC(g, r, c)).  Results match per-game ludax_rollout calls from the
+ * start position with the same (seed, global env index) bit for bit.       */
+#define LUDAX_DESC(g, r, c) ((int32_t)((g) | ((r) << 8) | ((c) << 16)))
+
+typedef struct ludax_mixed_plan ludax_mixed_plan;
+
+/* Build a plan for desc_dev (int32 [num_envs], device; read during this call
+ * and by later launches, so keep it alive and unchanged): validates every
+ * descriptor (LUDAX_ERR_GAME / LUDAX_ERR_SIZE name the first bad one through
+ * bad_index, nullable), groups env ids by game into a work queue so that a
+ * warp runs one game at a time, and captures the launch (queue counter reset
+ * + persistent kernel) into a CUDA graph on `stream`.
+ *   cfg     launch shape, nullable = built-in default (or a ludax_autotune
+ *           result)                                                         */
+int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int64_t num_envs, int64_t env_offset,
+                            const ludax_launch_cfg* cfg, void* stream, int64_t* bad_index);
+/* Replay the captured graph with a new seed and output buffers:
+ * outcome_dev int8 [num_envs], plies_dev int16 [num_envs].                */
+int ludax_mixed_plan_launch(ludax_mixed_plan* plan, uint64_t seed, int8_t* outcome_dev, int16_t* plies_dev);
+int ludax_mixed_plan_destroy(ludax_mixed_plan* plan);
+
+/* Same work without a graph: one direct launch (used to validate the graph). */
+int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,
+                        int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg, void* stream);
+
+/* Autotuner: times every candidate launch shape (block_threads x
+ * blocks_per_sm x envs_per_thread x hex_nbr_table) on the given mixed batch
+ * with CUDA events (warm-up, then the median of `reps` launches) and returns
+ * the fastest in best_out; best_ms_out (nullable) its median time.
+ * ms_table_out (nullable, host) receives each candidate's median in
+ * candidate order; n_candidates_out (nullable) their number.               */
+int ludax_autotune(const int32_t* desc_dev, int64_t num_envs, uint64_t seed, int32_t reps, void* stream,
+                   ludax_launch_cfg* best_out, float* best_ms_out, float* ms_table_out, int32_t* n_candidates_out);
+/* The candidate list ludax_autotune walks (host memory, count returned). */
+int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out);
+
+/* Autotuner for ludax_rollout on one env batch (from the start position, no
+ * write-back; the env's stored state is not touched): walks block_threads x
+ * blocks_per_sm x envs_per_thread (x hex_nbr_table for Hex), timing each
+ * like ludax_autotune.  ms_table_out (nullable) needs room for 256 floats. */
+int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
+                       float* ms_table_out, int32_t* n_candidates_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LUDAX_H */

@@ -1,0 +1,634 @@
+// ludax_env.cu -- single-game env batches: the C-ABI of include/ludax.h for
+// create / reset / legal mask / step / random step / rollout / state view.
+//
+// Step-per-launch kernels (reset, legal, step, random_step, state view) run
+// one thread per env over the structure-of-arrays state in HBM and are bound
+// by HBM bandwidth.  ludax_rollout and ludax_rollout_value run one fused
+// persistent kernel: each lane keeps an env's bitboards in registers, plays
+// it to the end, writes 3 bytes, and claims the next env.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <new>
+#include <thread>
+
+#include "../../include/ludax.h"
+#include "ludax_state.cuh"
+
+using namespace ludax;
+
+struct ludax_env {
+    int32_t game, rows, cols, cells, num_actions, mask_words, planes;
+    int64_t n, env_offset;
+    cudaStream_t stream;
+    int device, num_sms;
+    uint64_t* d_planes;
+    uint32_t* d_meta;
+    unsigned long long* d_counters;  // [0] refill cursor, [1] illegal, [2] capped, [3] spare
+};
+
+namespace {
+
+template <class G>
+struct Tag {
+    using type = G;
+};
+
+// Calls f(Tag<G>{}) for the game type of (game, n); LUDAX_ERR_* if unknown.
+template <class F>
+int dispatch_game(int game, int rows, int cols, F&& f) {
+    switch (game) {
+    case LUDAX_GAME_TTT: return (rows == 3 && cols == 3) ? f(Tag<TTT>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_C4: return (rows == 6 && cols == 7) ? f(Tag<C4>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_OTHELLO: return (rows == 8 && cols == 8) ? f(Tag<Othello>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_HEX:
+        if (rows != cols) return LUDAX_ERR_SIZE;
+        switch (rows) {
+        case 2: return f(Tag<Hex<2>>{});
+        case 3: return f(Tag<Hex<3>>{});
+        case 4: return f(Tag<Hex<4>>{});
+        case 5: return f(Tag<Hex<5>>{});
+        case 6: return f(Tag<Hex<6>>{});
+        case 7: return f(Tag<Hex<7>>{});
+        case 8: return f(Tag<Hex<8>>{});
+        case 9: return f(Tag<Hex<9>>{});
+        case 10: return f(Tag<Hex<10>>{});
+        case 11: return f(Tag<Hex<11>>{});
+        default: return LUDAX_ERR_SIZE;
+        }
+    default: return LUDAX_ERR_GAME;
+    }
+}
+
+EnvDev dev_of(const ludax_env* env) {
+    return EnvDev{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters};
+}
+
+int launch_status() { return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA; }
+
+unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+// ------------------------------------------------------------- kernels --
+template <class G>
+__global__ void reset_kernel(EnvDev d, const uint8_t* mask) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n || (mask && !mask[e])) return;
+    G g;
+    g.reset();
+    store_state(g, d, e);
+}
+
+template <class G>
+__global__ void legal_kernel(EnvDev d, uint64_t* out, uint8_t* pass_legal, int words) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    load_state(g, d, e);
+    typename G::Mask m{};
+    bool pass = false;
+    if (g.outcome == kOngoing) {
+        m = g.legal();
+        pass = G::kHasPass && !any(m);
+    }
+    for (int w = 0; w < words; ++w) out[e * words + w] = G::canon_word(m, w);
+    if (pass_legal) pass_legal[e] = pass ? 1 : 0;
+}
+
+__device__ __forceinline__ float2 rewards_of(int outcome) {
+    return outcome == kWin1 ? make_float2(1.f, -1.f) : (outcome == kWin2 ? make_float2(-1.f, 1.f) : make_float2(0.f, 0.f));
+}
+
+template <class G>
+__global__ void step_kernel(EnvDev d, const int32_t* actions, float2* rewards, uint8_t* terminated) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    load_state(g, d, e);
+    float2 rw = make_float2(0.f, 0.f);
+    if (g.outcome == kOngoing) {
+        int a = actions[e];
+        typename G::Mask m = g.legal();
+        bool ok = false;
+        if (G::kHasPass && a == G::kCells) {
+            ok = !any(m);
+            if (ok) g.pass();
+        } else if (a >= 0 && a < G::kCells) {
+            int b = G::bit_of(a);
+            ok = mask_has(m, b);
+            if (ok) g.place(b);
+        }
+        int illegal = 0;
+        if (!ok) {
+            g.outcome = 2 - g.side;  // the opponent of the mover wins
+            illegal = 1;
+            atomicAdd(&d.counters[1], 1ull);
+        } else if (g.outcome == kOngoing && g.ply >= G::kCap) {
+            g.outcome = kCapped;
+            atomicAdd(&d.counters[2], 1ull);
+        }
+        rw = rewards_of(g.outcome);
+        store_state(g, d, e, illegal);
+    }
+    rewards[e] = rw;
+    terminated[e] = g.outcome != kOngoing;
+}
+
+template <class G>
+__global__ void random_step_kernel(EnvDev d, uint64_t seed_key, float2* rewards, uint8_t* terminated) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    load_state(g, d, e);
+    float2 rw = make_float2(0.f, 0.f);
+    if (g.outcome == kOngoing) {
+        random_ply(g, env_key(seed_key, (uint64_t)(d.env_offset + e)));
+        if (g.outcome == kCapped) atomicAdd(&d.counters[2], 1ull);
+        rw = rewards_of(g.outcome);
+        store_state(g, d, e);
+    }
+    rewards[e] = rw;
+    terminated[e] = g.outcome != kOngoing;
+}
+
+template <class G>
+__global__ void get_state_kernel(EnvDev d, ludax_state_view v) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    load_state(g, d, e);
+    int8_t* b = v.board + e * G::kCells;
+    for (int c = 0; c < G::kCells; ++c) {
+        int bit = G::bit_of(c);
+        int v_own = mask_has(g.own, bit), v_opp = mask_has(g.opp, bit);
+        b[c] = (int8_t)(v_own ? g.side + 1 : (v_opp ? 2 - g.side : 0));
+    }
+    v.to_move[e] = (int8_t)(g.side + 1);
+    v.ply[e] = (int16_t)g.ply;
+    v.passes[e] = (int8_t)g.passes;
+    v.outcome[e] = (int8_t)g.outcome;
+}
+
+template <class M>
+__device__ __forceinline__ void set_bit(M& m, int b);
+template <>
+__device__ __forceinline__ void set_bit<uint32_t>(uint32_t& m, int b) { m |= 1u << b; }
+template <>
+__device__ __forceinline__ void set_bit<uint64_t>(uint64_t& m, int b) { m |= 1ull << b; }
+template <>
+__device__ __forceinline__ void set_bit<B128>(B128& m, int b) { m = m | bit128(b); }
+
+template <class G>
+__global__ void set_state_kernel(EnvDev d, ludax_state_view v) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    typename G::Mask p1{}, p2{};
+    const int8_t* b = v.board + e * G::kCells;
+    for (int c = 0; c < G::kCells; ++c) {
+        int x = b[c];
+        if (x == 1) set_bit(p1, G::bit_of(c));
+        if (x == 2) set_bit(p2, G::bit_of(c));
+    }
+    g.side = v.to_move[e] == 2 ? 1 : 0;
+    g.ply = v.ply[e];
+    g.passes = v.passes[e];
+    g.outcome = v.outcome[e];
+    g.own = g.side == 0 ? p1 : p2;
+    g.opp = g.side == 0 ? p2 : p1;
+    if constexpr (HexN<G>::value != 0) g.rebuild();
+    store_state(g, d, e);
+}
+
+// ----------------------------------------------------- fused playouts --
+struct RolloutArgs {
+    EnvDev d;
+    uint64_t seed_key;
+    const int16_t* stop;
+    int8_t* outcome;
+    int16_t* plies;
+    int from_start, write_back;
+};
+
+// One persistent kernel: each thread holds EPT envs in registers and advances
+// each by one ply per loop trip; a finished env is written out and replaced
+// by the next unclaimed env (claim_next).  Work index w < n maps to env w.
+template <class G, int EPT, bool TABLE>
+__global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
+    extern __shared__ B128 smem_table[];
+    const B128* table = nullptr;
+    if constexpr (TABLE && HexN<G>::value != 0) {
+        hex_fill_table<HexN<G>::value>(smem_table);
+        __syncthreads();
+        table = smem_table;
+    }
+    const int64_t n = a.d.n;
+    const int64_t slots = (int64_t)gridDim.x * blockDim.x * EPT;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool refill = slots < n;
+    G g[EPT];
+    uint64_t key[EPT];
+    int stop[EPT];
+    int64_t env[EPT];
+    bool active[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        env[i] = tid + (int64_t)i * gridDim.x * blockDim.x;
+        active[i] = env[i] < n;
+        set_table(g[i], table);
+    }
+    auto init = [&](int i) {
+        const int64_t e = env[i];
+        if (a.from_start) g[i].reset();
+        else load_state(g[i], a.d, e);
+        key[i] = env_key(a.seed_key, (uint64_t)(a.d.env_offset + e));
+        stop[i] = a.stop ? (int)a.stop[e] : 0x7FFF;
+    };
+#pragma unroll
+    for (int i = 0; i < EPT; ++i)
+        if (active[i]) init(i);
+    for (;;) {
+        bool any_active = false;
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+            if (!active[i]) continue;
+            any_active = true;
+            if (g[i].outcome == kOngoing && g[i].ply < stop[i]) {
+                random_ply(g[i], key[i]);
+                continue;
+            }
+            const int64_t e = env[i];
+            if (a.outcome) a.outcome[e] = (int8_t)g[i].outcome;
+            if (a.plies) a.plies[e] = (int16_t)g[i].ply;
+            if (a.write_back) store_state(g[i], a.d, e);
+            if (g[i].outcome == kCapped) atomicAdd(&a.d.counters[2], 1ull);
+            if (refill) {
+                env[i] = slots + claim_next(&a.d.counters[0]);
+                active[i] = env[i] < n;
+                if (active[i]) init(i);
+            } else {
+                active[i] = false;
+            }
+        }
+        if (!any_active) break;
+    }
+}
+
+// R playouts per env from its stored state; playout j draws with seed + j.
+template <class G, bool TABLE>
+__global__ void __launch_bounds__(512) rollout_value_kernel(EnvDev d, uint64_t seed, int R, float* value) {
+    extern __shared__ B128 smem_table[];
+    const B128* table = nullptr;
+    if constexpr (TABLE && HexN<G>::value != 0) {
+        hex_fill_table<HexN<G>::value>(smem_table);
+        __syncthreads();
+        table = smem_table;
+    }
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g0, g;
+    set_table(g0, table);
+    load_state(g0, d, e);
+    const uint64_t genv = (uint64_t)(d.env_offset + e);
+    float acc = 0.f;
+    int j = 0;
+    g = g0;
+    uint64_t key = env_key(splitmix64(seed), genv);
+    while (j < R) {
+        if (g.outcome == kOngoing) {
+            random_ply(g, key);
+            continue;
+        }
+        acc += p1_score(g.outcome);
+        ++j;
+        g = g0;
+        key = env_key(splitmix64(seed + (uint64_t)j), genv);
+    }
+    value[e] = R > 0 ? acc / (float)R : 0.f;
+}
+
+template <class G>
+int launch_rollout(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& cfg) {
+    const int block = cfg.block_threads;
+    const int ept = cfg.envs_per_thread;
+    int64_t need = (env->n + (int64_t)block * ept - 1) / ((int64_t)block * ept);
+    int64_t grid = need;
+    if (cfg.blocks_per_sm > 0) {
+        int64_t cap = (int64_t)env->num_sms * cfg.blocks_per_sm;
+        if (grid > cap) grid = cap;
+    }
+    const bool table = cfg.hex_nbr_table != 0 && HexN<G>::value != 0;
+    size_t smem = table ? sizeof(B128) * G::kCells : 0;
+    if (cudaMemsetAsync(env->d_counters, 0, sizeof(unsigned long long), env->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    if (ept == 2) {
+        if (table) rollout_kernel<G, 2, true><<<(unsigned)grid, block, smem, env->stream>>>(a);
+        else rollout_kernel<G, 2, false><<<(unsigned)grid, block, 0, env->stream>>>(a);
+    } else {
+        if (table) rollout_kernel<G, 1, true><<<(unsigned)grid, block, smem, env->stream>>>(a);
+        else rollout_kernel<G, 1, false><<<(unsigned)grid, block, 0, env->stream>>>(a);
+    }
+    return launch_status();
+}
+
+ludax_launch_cfg default_cfg() { return ludax_launch_cfg{256, 0, 1, 0}; }
+
+int check_cfg(const ludax_launch_cfg& c) {
+    if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32) return LUDAX_ERR_ARG;
+    if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return LUDAX_ERR_ARG;
+    if (c.envs_per_thread != 1 && c.envs_per_thread != 2) return LUDAX_ERR_ARG;
+    if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
+    return LUDAX_OK;
+}
+
+}  // namespace
+
+// =================================================================== C-ABI ==
+extern "C" {
+
+const char* ludax_status_string(int status) {
+    switch (status) {
+    case LUDAX_OK: return "ok";
+    case LUDAX_ERR_ARG: return "invalid argument";
+    case LUDAX_ERR_GAME: return "unknown game or descriptor";
+    case LUDAX_ERR_SIZE: return "board size not supported for this game";
+    case LUDAX_ERR_CUDA: return "CUDA runtime error";
+    case LUDAX_ERR_TIMEOUT: return "timed out waiting for the device";
+    case LUDAX_ERR_ALIGN: return "misaligned device pointer";
+    case LUDAX_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown status";
+    }
+}
+
+int ludax_env_create(ludax_env** out, int32_t game, const ludax_board_params* p, int64_t num_envs, int64_t env_offset,
+                     void* stream) {
+    if (!out || !p) return LUDAX_ERR_ARG;
+    *out = nullptr;
+    if (num_envs < 1 || num_envs > 0x7FFFFFFFll || env_offset < 0) return LUDAX_ERR_ARG;
+    int planes = 0;
+    int st = dispatch_game(game, p->rows, p->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        planes = G::kPlanes;
+        return LUDAX_OK;
+    });
+    if (st != LUDAX_OK) return st;
+    ludax_env* env = new (std::nothrow) ludax_env();
+    if (!env) return LUDAX_ERR_NOMEM;
+    env->game = game;
+    env->rows = p->rows;
+    env->cols = p->cols;
+    env->cells = p->rows * p->cols;
+    env->num_actions = env->cells + (game == LUDAX_GAME_OTHELLO ? 1 : 0);
+    env->mask_words = (env->cells + 63) / 64;
+    env->planes = planes;
+    env->n = num_envs;
+    env->env_offset = env_offset;
+    env->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&env->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&env->num_sms, cudaDevAttrMultiProcessorCount, env->device) != cudaSuccess) {
+        delete env;
+        return LUDAX_ERR_CUDA;
+    }
+    if (cudaMalloc(&env->d_planes, sizeof(uint64_t) * planes * num_envs) != cudaSuccess ||
+        cudaMalloc(&env->d_meta, sizeof(uint32_t) * num_envs) != cudaSuccess ||
+        cudaMalloc(&env->d_counters, sizeof(unsigned long long) * 4) != cudaSuccess) {
+        cudaFree(env->d_planes);
+        cudaFree(env->d_meta);
+        cudaGetLastError();
+        delete env;
+        return LUDAX_ERR_NOMEM;
+    }
+    if (cudaMemsetAsync(env->d_planes, 0, sizeof(uint64_t) * planes * num_envs, env->stream) != cudaSuccess ||
+        cudaMemsetAsync(env->d_counters, 0, sizeof(unsigned long long) * 4, env->stream) != cudaSuccess) {
+        ludax_env_destroy(env);
+        return LUDAX_ERR_CUDA;
+    }
+    st = ludax_reset(env, nullptr);
+    if (st != LUDAX_OK) {
+        ludax_env_destroy(env);
+        return st;
+    }
+    *out = env;
+    return LUDAX_OK;
+}
+
+int ludax_env_destroy(ludax_env* env) {
+    if (!env) return LUDAX_OK;
+    cudaStreamSynchronize(env->stream);
+    cudaFree(env->d_planes);
+    cudaFree(env->d_meta);
+    cudaFree(env->d_counters);
+    delete env;
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+int ludax_env_set_stream(ludax_env* env, void* stream) {
+    if (!env) return LUDAX_ERR_ARG;
+    env->stream = (cudaStream_t)stream;
+    return LUDAX_OK;
+}
+
+int ludax_env_sizes(const ludax_env* env, int32_t* num_actions, int32_t* mask_words, int64_t* num_envs) {
+    if (!env) return LUDAX_ERR_ARG;
+    if (num_actions) *num_actions = env->num_actions;
+    if (mask_words) *mask_words = env->mask_words;
+    if (num_envs) *num_envs = env->n;
+    return LUDAX_OK;
+}
+
+int ludax_reset(ludax_env* env, const uint8_t* env_mask_dev) {
+    if (!env) return LUDAX_ERR_ARG;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        reset_kernel<G><<<grid_for(env->n, 256), 256, 0, env->stream>>>(dev_of(env), env_mask_dev);
+        return launch_status();
+    });
+}
+
+int ludax_legal_mask(ludax_env* env, uint64_t* mask_dev, uint8_t* pass_legal_dev) {
+    if (!env || !mask_dev) return LUDAX_ERR_ARG;
+    if (!aligned(mask_dev, 8)) return LUDAX_ERR_ALIGN;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        legal_kernel<G><<<grid_for(env->n, 256), 256, 0, env->stream>>>(dev_of(env), mask_dev, pass_legal_dev,
+                                                                           env->mask_words);
+        return launch_status();
+    });
+}
+
+int ludax_step(ludax_env* env, const int32_t* actions_dev, float* rewards_dev, uint8_t* terminated_dev) {
+    if (!env || !actions_dev || !rewards_dev || !terminated_dev) return LUDAX_ERR_ARG;
+    if (!aligned(actions_dev, 4) || !aligned(rewards_dev, 8)) return LUDAX_ERR_ALIGN;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        step_kernel<G><<<grid_for(env->n, 256), 256, 0, env->stream>>>(dev_of(env), actions_dev,
+                                                                          (float2*)rewards_dev, terminated_dev);
+        return launch_status();
+    });
+}
+
+int ludax_random_step(ludax_env* env, uint64_t seed, float* rewards_dev, uint8_t* terminated_dev) {
+    if (!env || !rewards_dev || !terminated_dev) return LUDAX_ERR_ARG;
+    if (!aligned(rewards_dev, 8)) return LUDAX_ERR_ALIGN;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        random_step_kernel<G><<<grid_for(env->n, 256), 256, 0, env->stream>>>(dev_of(env), splitmix64(seed),
+                                                                                 (float2*)rewards_dev, terminated_dev);
+        return launch_status();
+    });
+}
+
+int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* stop_ply_dev, int8_t* outcome_dev,
+                  int16_t* plies_dev, const ludax_launch_cfg* cfg) {
+    if (!env) return LUDAX_ERR_ARG;
+    if (flags & ~(uint32_t)(LUDAX_ROLLOUT_FROM_START | LUDAX_ROLLOUT_WRITE_BACK)) return LUDAX_ERR_ARG;
+    if ((stop_ply_dev && !aligned(stop_ply_dev, 2)) || (plies_dev && !aligned(plies_dev, 2))) return LUDAX_ERR_ALIGN;
+    ludax_launch_cfg c = cfg ? *cfg : default_cfg();
+    int st = check_cfg(c);
+    if (st != LUDAX_OK) return st;
+    RolloutArgs a;
+    a.d = dev_of(env);
+    a.seed_key = splitmix64(seed);
+    a.stop = stop_ply_dev;
+    a.outcome = outcome_dev;
+    a.plies = plies_dev;
+    a.from_start = (flags & LUDAX_ROLLOUT_FROM_START) ? 1 : 0;
+    a.write_back = (flags & LUDAX_ROLLOUT_WRITE_BACK) ? 1 : 0;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        return launch_rollout<G>(env, a, c);
+    });
+}
+
+int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_dev, const ludax_launch_cfg* cfg) {
+    if (!env || !value_dev || R < 1) return LUDAX_ERR_ARG;
+    if (!aligned(value_dev, 4)) return LUDAX_ERR_ALIGN;
+    ludax_launch_cfg c = cfg ? *cfg : default_cfg();
+    int st = check_cfg(c);
+    if (st != LUDAX_OK) return st;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        const bool table = c.hex_nbr_table != 0 && HexN<G>::value != 0;
+        size_t smem = table ? sizeof(B128) * G::kCells : 0;
+        unsigned grid = grid_for(env->n, c.block_threads);
+        if (table)
+            rollout_value_kernel<G, true><<<grid, c.block_threads, smem, env->stream>>>(dev_of(env), seed, R, value_dev);
+        else
+            rollout_value_kernel<G, false><<<grid, c.block_threads, 0, env->stream>>>(dev_of(env), seed, R, value_dev);
+        return launch_status();
+    });
+}
+
+int ludax_get_state(ludax_env* env, const ludax_state_view* dst) {
+    if (!env || !dst || !dst->board || !dst->to_move || !dst->ply || !dst->passes || !dst->outcome) return LUDAX_ERR_ARG;
+    if (!aligned(dst->ply, 2)) return LUDAX_ERR_ALIGN;
+    ludax_state_view v = *dst;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        get_state_kernel<G><<<grid_for(env->n, 128), 128, 0, env->stream>>>(dev_of(env), v);
+        return launch_status();
+    });
+}
+
+int ludax_set_state(ludax_env* env, const ludax_state_view* src) {
+    if (!env || !src || !src->board || !src->to_move || !src->ply || !src->passes || !src->outcome) return LUDAX_ERR_ARG;
+    if (!aligned(src->ply, 2)) return LUDAX_ERR_ALIGN;
+    ludax_state_view v = *src;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        set_state_kernel<G><<<grid_for(env->n, 128), 128, 0, env->stream>>>(dev_of(env), v);
+        return launch_status();
+    });
+}
+
+int ludax_counters(ludax_env* env, int64_t* illegal_actions, int64_t* capped) {
+    if (!env) return LUDAX_ERR_ARG;
+    unsigned long long h[4];
+    if (cudaMemcpyAsync(h, env->d_counters, sizeof(h), cudaMemcpyDeviceToHost, env->stream) != cudaSuccess ||
+        cudaStreamSynchronize(env->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    if (illegal_actions) *illegal_actions = (int64_t)h[1];
+    if (capped) *capped = (int64_t)h[2];
+    return LUDAX_OK;
+}
+
+int ludax_sync(ludax_env* env, int64_t timeout_ms) {
+    if (!env) return LUDAX_ERR_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(env->stream);
+        if (q == cudaSuccess) return LUDAX_OK;
+        if (q != cudaErrorNotReady) return LUDAX_ERR_CUDA;
+        if (timeout_ms >= 0) {
+            auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+            if (ms.count() >= timeout_ms) return LUDAX_ERR_TIMEOUT;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
+                       float* ms_table_out, int32_t* n_candidates_out) {
+    if (!env || !best_out || reps < 1) return LUDAX_ERR_ARG;
+    static const int blocks[] = {64, 128, 256, 512};
+    static const int bps[] = {0, 2, 4, 8, 16};
+    const int tables = env->game == LUDAX_GAME_HEX ? 2 : 1;
+    int8_t* d_out = nullptr;
+    int16_t* d_plies = nullptr;
+    if (cudaMalloc(&d_out, env->n) != cudaSuccess || cudaMalloc(&d_plies, 2 * env->n) != cudaSuccess) {
+        cudaFree(d_out);
+        cudaGetLastError();
+        return LUDAX_ERR_NOMEM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int st = LUDAX_OK, k = 0;
+    float best = 1e30f;
+    for (int t = 0; t < tables && st == LUDAX_OK; ++t)
+        for (int ept = 1; ept <= 2 && st == LUDAX_OK; ++ept)
+            for (int b : blocks)
+                for (int s : bps) {
+                    if (st != LUDAX_OK) break;
+                    if (s > 0 && b * s > 2048) continue;
+                    ludax_launch_cfg c{b, s, ept, t};
+                    float ts[64];
+                    int nt = 0;
+                    for (int r = 0; r < reps + 2 && st == LUDAX_OK; ++r) {
+                        cudaEventRecord(e0, env->stream);
+                        st = ludax_rollout(env, seed + (uint64_t)r, LUDAX_ROLLOUT_FROM_START, nullptr, d_out, d_plies, &c);
+                        cudaEventRecord(e1, env->stream);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) st = LUDAX_ERR_CUDA;
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (r >= 2 && nt < 64) ts[nt++] = ms;
+                    }
+                    if (st != LUDAX_OK) break;
+                    for (int i = 1; i < nt; ++i)
+                        for (int j = i; j > 0 && ts[j] < ts[j - 1]; --j) {
+                            float x = ts[j]; ts[j] = ts[j - 1]; ts[j - 1] = x;
+                        }
+                    float med = ts[nt / 2];
+                    if (ms_table_out && k < 256) ms_table_out[k] = med;
+                    ++k;
+                    if (med < best) {
+                        best = med;
+                        *best_out = c;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_out);
+    cudaFree(d_plies);
+    if (best_ms_out) *best_ms_out = best;
+    if (n_candidates_out) *n_candidates_out = k;
+    return st;
+}
+
+}  // extern "C"

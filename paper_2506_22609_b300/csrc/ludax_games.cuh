@@ -1,0 +1,389 @@
+// ludax_games.cuh -- per-game bitboard code for the B300 engine (device side).
+//
+// Each game is a small struct whose whole state lives in registers:
+//   own/opp   stones of the player to move and of the other player
+//   side      0 when P1 is to move, 1 when P2 is
+//   ply       plies played (passes included), passes (Reversi), outcome
+// and whose methods implement the rules of the paper's game appendix (App. C)
+// with the action = destination-cell convention (Sec. 3.4):
+//   legal()   the legal-destination mask in the game's internal bit layout
+//   place(b)  put a stone on internal bit b, apply effects and end rules
+//   pass()    the forced pass (Reversi only, force_pass of App. B)
+// The internal bit order of every layout is monotone in the canonical cell id
+// (row-major, row 0 at the top), so "the k-th set bit" of a legal mask is the
+// k-th legal cell in ascending canonical id.
+//
+// Layouts:
+//   Tic-Tac-Toe  9 bits, bit = cell id; 8 line masks (the precomputed line
+//                indices of Sec. 4, as bitmasks)
+//   Connect Four 6 rows x 8-bit stride (column 7 always empty), bit = r*8+c;
+//                the empty padding column stops shifted lines from wrapping,
+//                so a line of four is b & b>>s & b>>2s & b>>3s for s in
+//                {1 (row), 8 (column), 7 and 9 (diagonals)}; gravity: a cell
+//                is legal when empty and the cell below (bit+8) is occupied
+//                or it is on the bottom row
+//   Reversi      8x8, bit = cell id; legal moves and flips by Kogge-Stone
+//                occluded fills in 8 directions, with the opponent mask
+//                restricted to columns 1..6 for every direction with a
+//                horizontal component (no wrap across rows)
+//   Hex n x n    n*n <= 121 bits in two 64-bit words, bit = cell id; six
+//                neighbours (r-1,c) (r+1,c) (r,c-1) (r,c+1) (r-1,c+1)
+//                (r+1,c-1) by shifts n, 1, n-1 with column masks.  Win
+//                detection keeps, per player, the stones connected to each
+//                of its two edges (A, B): a new stone joins edge A when it
+//                lies on edge A or touches a stone of A, likewise for B; the
+//                player wins when the stone joins both.  When it joins one,
+//                the stones not yet connected to any edge that it links are
+//                added to that set by a flood fill.  This is the incremental
+//                connected-component update of Sec. 4 ("Dynamic State
+//                Attributes") in bitboard form.
+#pragma once
+#include <stdint.h>
+
+namespace ludax {
+
+constexpr int kOngoing = -1, kDraw = 0, kWin1 = 1, kWin2 = 2, kCapped = 3;
+
+// ----------------------------------------------------------------- RNG --
+// splitmix64 output function (Steele, Lea & Flood 2014): golden-ratio
+// increment then the 30/27/31 xor-shift-multiply finaliser.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+// key of a global env index given sm(seed)
+__device__ __forceinline__ uint64_t env_key(uint64_t seed_key, uint64_t env) { return splitmix64(seed_key ^ env); }
+// uniform index in [0, n) for this ply: top 32 bits of the draw times n, high word
+__device__ __forceinline__ uint32_t draw_index(uint64_t key, uint32_t ply, uint32_t n) {
+    uint64_t r = splitmix64(key ^ (uint64_t)ply);
+    return __umulhi((uint32_t)(r >> 32), n);
+}
+
+// ---------------------------------------------------------- bit helpers --
+struct B128 {
+    uint64_t lo, hi;
+};
+__host__ __device__ __forceinline__ B128 operator|(B128 a, B128 b) { return {a.lo | b.lo, a.hi | b.hi}; }
+__host__ __device__ __forceinline__ B128 operator&(B128 a, B128 b) { return {a.lo & b.lo, a.hi & b.hi}; }
+__host__ __device__ __forceinline__ B128 operator~(B128 a) { return {~a.lo, ~a.hi}; }
+__host__ __device__ __forceinline__ bool operator==(B128 a, B128 b) { return a.lo == b.lo && a.hi == b.hi; }
+__host__ __device__ __forceinline__ bool any(B128 a) { return (a.lo | a.hi) != 0; }
+__host__ __device__ __forceinline__ bool any(uint64_t a) { return a != 0; }
+__host__ __device__ __forceinline__ bool any(uint32_t a) { return a != 0; }
+template <int S>
+__device__ __forceinline__ B128 shl(B128 a) {  // 0 < S < 64
+    return {a.lo << S, (a.hi << S) | (a.lo >> (64 - S))};
+}
+template <int S>
+__device__ __forceinline__ B128 shr(B128 a) {
+    return {(a.lo >> S) | (a.hi << (64 - S)), a.hi >> S};
+}
+__device__ __forceinline__ B128 bit128(int b) {
+    return {b < 64 ? (1ull << b) : 0ull, b >= 64 ? (1ull << (b - 64)) : 0ull};
+}
+
+__device__ __forceinline__ uint32_t popc(uint32_t m) { return __popc(m); }
+__device__ __forceinline__ uint32_t popc(uint64_t m) { return __popcll(m); }
+__device__ __forceinline__ uint32_t popc(B128 m) { return __popcll(m.lo) + __popcll(m.hi); }
+
+// Position of the k-th set bit (k < popc(w)) by halving: count the low half,
+// descend into the half that holds the bit.
+__device__ __forceinline__ int select32(uint32_t w, uint32_t k) {
+    int pos = 0;
+    uint32_t c = __popc(w & 0xFFFFu);
+    if (k >= c) { k -= c; w >>= 16; pos += 16; }
+    c = __popc(w & 0xFFu);
+    if (k >= c) { k -= c; w >>= 8; pos += 8; }
+    c = __popc(w & 0xFu);
+    if (k >= c) { k -= c; w >>= 4; pos += 4; }
+    c = __popc(w & 0x3u);
+    if (k >= c) { k -= c; w >>= 2; pos += 2; }
+    c = w & 1u;
+    if (k >= c) pos += 1;
+    return pos;
+}
+__device__ __forceinline__ int select_bit(uint32_t m, uint32_t k) { return select32(m, k); }
+__device__ __forceinline__ int select_bit(uint64_t m, uint32_t k) {
+    uint32_t lo = (uint32_t)m, c = __popc(lo);
+    return k < c ? select32(lo, k) : 32 + select32((uint32_t)(m >> 32), k - c);
+}
+__device__ __forceinline__ int select_bit(B128 m, uint32_t k) {
+    uint32_t c = __popcll(m.lo);
+    return k < c ? select_bit(m.lo, k) : 64 + select_bit(m.hi, k - c);
+}
+
+// ----------------------------------------------------------- Tic-Tac-Toe --
+struct TTT {
+    static constexpr int kGame = 0, kRows = 3, kCols = 3, kCells = 9, kCap = 9, kPlanes = 2;
+    static constexpr bool kHasPass = false;
+    using Mask = uint32_t;
+    uint32_t own, opp;
+    int side, ply, passes, outcome;
+
+    __device__ __forceinline__ void reset() {
+        own = opp = 0;
+        side = ply = passes = 0;
+        outcome = kOngoing;
+    }
+    __device__ __forceinline__ Mask legal() const { return ~(own | opp) & 0x1FFu; }
+    __device__ __forceinline__ static bool line3(uint32_t b) {
+        return ((b & 0x007u) == 0x007u) | ((b & 0x038u) == 0x038u) | ((b & 0x1C0u) == 0x1C0u) |
+               ((b & 0x049u) == 0x049u) | ((b & 0x092u) == 0x092u) | ((b & 0x124u) == 0x124u) |
+               ((b & 0x111u) == 0x111u) | ((b & 0x054u) == 0x054u);
+    }
+    __device__ __forceinline__ void place(int b) {
+        own |= 1u << b;
+        if (line3(own)) outcome = side + 1;
+        else if ((own | opp) == 0x1FFu) outcome = kDraw;
+        ++ply;
+        uint32_t t = own; own = opp; opp = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {}
+    __device__ __forceinline__ static int canon_of(int b) { return b; }
+    __device__ __forceinline__ static int bit_of(int cell) { return cell; }
+    __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) { return w == 0 ? (uint64_t)m : 0ull; }
+};
+
+// ---------------------------------------------------------- Connect Four --
+struct C4 {
+    static constexpr int kGame = 1, kRows = 6, kCols = 7, kCells = 42, kCap = 42, kPlanes = 2;
+    static constexpr bool kHasPass = false;
+    static constexpr uint64_t kValid = 0x7F7F7F7F7F7Full;   // rows 0..5, columns 0..6
+    static constexpr uint64_t kBottom = 0x7Full << 40;       // row 5
+    using Mask = uint64_t;
+    uint64_t own, opp;
+    int side, ply, passes, outcome;
+
+    __device__ __forceinline__ void reset() {
+        own = opp = 0;
+        side = ply = passes = 0;
+        outcome = kOngoing;
+    }
+    __device__ __forceinline__ Mask legal() const {
+        uint64_t occ = own | opp;
+        return kValid & ~occ & ((occ >> 8) | kBottom);
+    }
+    __device__ __forceinline__ static bool line4(uint64_t b) {
+        uint64_t h = b & (b >> 1), v = b & (b >> 8), d1 = b & (b >> 7), d2 = b & (b >> 9);
+        return ((h & (h >> 2)) | (v & (v >> 16)) | (d1 & (d1 >> 14)) | (d2 & (d2 >> 18))) != 0;
+    }
+    __device__ __forceinline__ void place(int b) {
+        own |= 1ull << b;
+        if (line4(own)) outcome = side + 1;
+        else if ((own | opp) == kValid) outcome = kDraw;
+        ++ply;
+        uint64_t t = own; own = opp; opp = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {}
+    __device__ __forceinline__ static int canon_of(int b) { return (b >> 3) * 7 + (b & 7); }
+    __device__ __forceinline__ static int bit_of(int cell) { return (cell / 7) * 8 + cell % 7; }
+    __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) {
+        if (w != 0) return 0ull;
+        uint64_t out = 0;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) out |= ((m >> (8 * r)) & 0x7Full) << (7 * r);
+        return out;
+    }
+};
+
+// --------------------------------------------------------------- Reversi --
+template <int S>
+__device__ __forceinline__ uint64_t shift64(uint64_t x) {
+    return S > 0 ? (x << (S > 0 ? S : 0)) : (x >> (S < 0 ? -S : 0));
+}
+// Kogge-Stone occluded fill of `gen` through `pro` in direction S (up to 7 steps).
+template <int S>
+__device__ __forceinline__ uint64_t occluded_fill(uint64_t gen, uint64_t pro) {
+    gen |= pro & shift64<S>(gen);
+    pro &= shift64<S>(pro);
+    gen |= pro & shift64<2 * S>(gen);
+    pro &= shift64<2 * S>(pro);
+    gen |= pro & shift64<4 * S>(gen);
+    return gen;
+}
+
+struct Othello {
+    static constexpr int kGame = 2, kRows = 8, kCols = 8, kCells = 64, kCap = 128, kPlanes = 2;
+    static constexpr bool kHasPass = true;
+    static constexpr uint64_t kInner = 0x7E7E7E7E7E7E7E7Eull;  // columns 1..6
+    using Mask = uint64_t;
+    uint64_t own, opp;
+    int side, ply, passes, outcome;
+
+    __device__ __forceinline__ void reset() {
+        // D4 (27), E5 (36) white = P2; D5 (35), E4 (28) black = P1; P1 moves.
+        own = (1ull << 28) | (1ull << 35);
+        opp = (1ull << 27) | (1ull << 36);
+        side = ply = passes = 0;
+        outcome = kOngoing;
+    }
+    // cells beyond a run of opponent discs that starts next to one of own's
+    template <int S>
+    __device__ __forceinline__ static uint64_t dir_moves(uint64_t own, uint64_t pro) {
+        return shift64<S>(occluded_fill<S>(own, pro) & pro);
+    }
+    __device__ __forceinline__ Mask legal() const {
+        uint64_t empty = ~(own | opp), ph = opp & kInner;
+        uint64_t m = dir_moves<1>(own, ph) | dir_moves<-1>(own, ph) | dir_moves<8>(own, opp) |
+                     dir_moves<-8>(own, opp) | dir_moves<7>(own, ph) | dir_moves<-7>(own, ph) |
+                     dir_moves<9>(own, ph) | dir_moves<-9>(own, ph);
+        return m & empty;
+    }
+    // opponent discs between x and the first own disc in direction S (or none)
+    template <int S>
+    __device__ __forceinline__ static uint64_t dir_flips(uint64_t x, uint64_t own, uint64_t pro) {
+        uint64_t run = occluded_fill<S>(x, pro) & pro;
+        return (shift64<S>(run) & own) ? run : 0ull;
+    }
+    __device__ __forceinline__ void place(int b) {
+        uint64_t x = 1ull << b, ph = opp & kInner;
+        uint64_t f = dir_flips<1>(x, own, ph) | dir_flips<-1>(x, own, ph) | dir_flips<8>(x, own, opp) |
+                     dir_flips<-8>(x, own, opp) | dir_flips<7>(x, own, ph) | dir_flips<-7>(x, own, ph) |
+                     dir_flips<9>(x, own, ph) | dir_flips<-9>(x, own, ph);
+        own |= x | f;
+        opp &= ~f;
+        passes = 0;
+        ++ply;
+        uint64_t t = own; own = opp; opp = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {
+        ++passes;
+        ++ply;
+        if (passes >= 2) {
+            // disc count; own/opp belong to the passing player / the other
+            int a = __popcll(own), o = __popcll(opp);
+            int winner_is_mover = a > o, winner_is_other = o > a;
+            outcome = winner_is_mover ? side + 1 : (winner_is_other ? 2 - side : kDraw);
+        }
+        uint64_t t = own; own = opp; opp = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ static int canon_of(int b) { return b; }
+    __device__ __forceinline__ static int bit_of(int cell) { return cell; }
+    __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) { return w == 0 ? m : 0ull; }
+};
+
+// ------------------------------------------------------------------- Hex --
+__host__ __device__ constexpr uint64_t hex_word(int n, int word, int kind) {
+    // kind: 0 board, 1 column 0, 2 column n-1, 3 row 0, 4 row n-1
+    uint64_t m = 0;
+    for (int b = 0; b < 64; ++b) {
+        int i = word * 64 + b;
+        if (i >= n * n) break;
+        int r = i / n, c = i % n;
+        bool on = kind == 0 ? true : kind == 1 ? c == 0 : kind == 2 ? c == n - 1 : kind == 3 ? r == 0 : r == n - 1;
+        if (on) m |= 1ull << b;
+    }
+    return m;
+}
+
+template <int N>
+struct Hex {
+    static_assert(N >= 2 && N <= 11, "Hex board 2..11");
+    static constexpr int kGame = 3, kRows = N, kCols = N, kCells = N * N, kCap = N * N, kPlanes = 12;
+    static constexpr bool kHasPass = false;
+    using Mask = B128;
+    static constexpr uint64_t kBoardLo = hex_word(N, 0, 0), kBoardHi = hex_word(N, 1, 0);
+    static constexpr uint64_t kCol0Lo = hex_word(N, 0, 1), kCol0Hi = hex_word(N, 1, 1);
+    static constexpr uint64_t kColLLo = hex_word(N, 0, 2), kColLHi = hex_word(N, 1, 2);
+    static constexpr uint64_t kRow0Lo = hex_word(N, 0, 3), kRow0Hi = hex_word(N, 1, 3);
+    static constexpr uint64_t kRowLLo = hex_word(N, 0, 4), kRowLHi = hex_word(N, 1, 4);
+
+    B128 own, opp;        // stones
+    B128 ownA, ownB;      // own stones connected to own's edge A / edge B
+    B128 oppA, oppB;
+    int side, ply, passes, outcome;
+    const B128* nbr_table;  // per-cell neighbour masks in shared memory, or nullptr
+
+    __device__ __forceinline__ static B128 board() { return {kBoardLo, kBoardHi}; }
+    __device__ __forceinline__ static B128 nbrs(B128 s) {
+        const B128 notc0 = {kBoardLo & ~kCol0Lo, kBoardHi & ~kCol0Hi};
+        const B128 notcl = {kBoardLo & ~kColLLo, kBoardHi & ~kColLHi};
+        B128 a = s & notcl, b = s & notc0;
+        B128 r = shl<N>(s) | shr<N>(s) | shl<1>(a) | shr<1>(b) | shr<N - 1>(a) | shl<N - 1>(b);
+        return r & board();
+    }
+    // edge A / B of the player on `side`: P1 rows 0 and n-1, P2 columns 0 and n-1
+    __device__ __forceinline__ static B128 edgeA(int sd) {
+        return sd == 0 ? B128{kRow0Lo, kRow0Hi} : B128{kCol0Lo, kCol0Hi};
+    }
+    __device__ __forceinline__ static B128 edgeB(int sd) {
+        return sd == 0 ? B128{kRowLLo, kRowLHi} : B128{kColLLo, kColLHi};
+    }
+    // stones of `stones` connected to `seed` (seed must be inside stones)
+    __device__ __forceinline__ static B128 flood(B128 seed, B128 stones) {
+        B128 c = seed;
+#pragma unroll 1
+        for (int it = 0; it < N * N; ++it) {
+            B128 nx = (nbrs(c) & stones) | c;
+            if (nx == c) break;
+            c = nx;
+        }
+        return c;
+    }
+    __device__ __forceinline__ void reset() {
+        own = opp = ownA = ownB = oppA = oppB = B128{0, 0};
+        side = ply = passes = 0;
+        outcome = kOngoing;
+    }
+    __device__ __forceinline__ Mask legal() const { return board() & ~(own | opp); }
+    __device__ __forceinline__ void place(int b) {
+        B128 x = bit128(b);
+        B128 nx = nbr_table ? nbr_table[b] : nbrs(x);
+        bool ta = any((x & edgeA(side)) | (nx & ownA));
+        bool tb = any((x & edgeB(side)) | (nx & ownB));
+        own = own | x;
+        if (ta && tb) {
+            outcome = side + 1;
+        } else if (ta || tb) {
+            B128 c = flood(x, own & ~(ownA | ownB));
+            if (ta) ownA = ownA | c;
+            else ownB = ownB | c;
+        }
+        ++ply;
+        B128 t = own; own = opp; opp = t;
+        t = ownA; ownA = oppA; oppA = t;
+        t = ownB; ownB = oppB; oppB = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {}
+    // rebuild the edge-connected sets of both players from the stones
+    __device__ __forceinline__ void rebuild() {
+        ownA = flood(own & edgeA(side), own);
+        ownB = flood(own & edgeB(side), own);
+        oppA = flood(opp & edgeA(side ^ 1), opp);
+        oppB = flood(opp & edgeB(side ^ 1), opp);
+    }
+    __device__ __forceinline__ static int canon_of(int b) { return b; }
+    __device__ __forceinline__ static int bit_of(int cell) { return cell; }
+    __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) { return w == 0 ? m.lo : m.hi; }
+};
+
+// Fill a shared-memory table of per-cell neighbour masks for Hex<N>
+// (cooperatively by the block; caller synchronises).
+template <int N>
+__device__ __forceinline__ void hex_fill_table(B128* table) {
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) table[i] = Hex<N>::nbrs(bit128(i));
+}
+
+// ---------------------------------------------------------- one random ply --
+// Uniform-random policy: n legal cells, k-th in ascending cell id with
+// k = umulhi(top32(sm(key ^ ply)), n); a forced pass draws nothing.
+template <class G>
+__device__ __forceinline__ void random_ply(G& g, uint64_t key) {
+    typename G::Mask m = g.legal();
+    if (G::kHasPass && !any(m)) {
+        g.pass();
+    } else {
+        uint32_t k = draw_index(key, (uint32_t)g.ply, popc(m));
+        g.place(select_bit(m, k));
+    }
+    if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
+}
+
+}  // namespace ludax

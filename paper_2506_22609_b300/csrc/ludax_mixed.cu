@@ -1,0 +1,427 @@
+// ludax_mixed.cu -- mixed-game batches in one persistent launch, the CUDA
+// graph plan that replays it, and the launch-shape autotuner.
+//
+// Each env carries an int32 descriptor game | rows << 8 | cols << 16.  At plan
+// creation the env ids are grouped by game ("buckets": Tic-Tac-Toe, Connect
+// Four, Reversi, Hex 2..11) into a work queue, so consecutive queue positions
+// -- and therefore the 32 lanes of a warp -- play the same game and branch
+// together.  The persistent kernel hands out queue positions with a
+// warp-aggregated atomic cursor; a lane whose game ends writes its 3 bytes of
+// output and claims the next position, staying inside its game's playout
+// loop while the claimed env has the same game.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "../../include/ludax.h"
+#include "ludax_state.cuh"
+
+using namespace ludax;
+
+namespace {
+
+constexpr int kBuckets = 13;  // 0 TTT, 1 C4, 2 Othello, 3+k Hex (k+2)x(k+2)
+constexpr int kHexTableCells = 505;  // sum of n*n for n = 2..11
+
+__host__ __device__ constexpr int hex_table_offset(int n) {
+    int off = 0;
+    for (int k = 2; k < n; ++k) off += k * k;
+    return off;
+}
+
+// bucket of a descriptor, or -1 (LUDAX_ERR_GAME) / -2 (LUDAX_ERR_SIZE)
+int bucket_of_desc(int32_t d) {
+    if (d < 0 || (d >> 24) != 0) return -1;
+    int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
+    switch (game) {
+    case LUDAX_GAME_TTT: return (rows == 3 && cols == 3) ? 0 : -2;
+    case LUDAX_GAME_C4: return (rows == 6 && cols == 7) ? 1 : -2;
+    case LUDAX_GAME_OTHELLO: return (rows == 8 && cols == 8) ? 2 : -2;
+    case LUDAX_GAME_HEX: return (rows == cols && rows >= 2 && rows <= 11) ? 3 + rows - 2 : -2;
+    default: return -1;
+    }
+}
+
+struct MixedArgs {
+    const int32_t* queue;            // env ids grouped by bucket
+    long long bucket_end[kBuckets];  // exclusive end position of each bucket in the queue
+    long long n;
+    long long env_offset;
+    uint64_t seed_key;
+    int8_t* outcome;
+    int16_t* plies;
+    unsigned long long* cursor;      // zeroed before each launch
+};
+
+__device__ __forceinline__ int bucket_at(const MixedArgs& a, long long q) {
+    int b = 0;
+#pragma unroll
+    for (int k = 0; k < kBuckets - 1; ++k) b += q >= a.bucket_end[k];
+    return b;
+}
+
+// Plays queue positions of one bucket until the lane claims a position
+// outside it; returns that position (>= n when the queue is exhausted).
+template <class G>
+__device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q, long long end, long long slots,
+                                                bool refill, const B128* table) {
+    G g;
+    set_table(g, table);
+    long long e = a.queue[q];
+    g.reset();
+    uint64_t key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
+    for (;;) {
+        if (g.outcome == kOngoing) {
+            random_ply(g, key);
+            continue;
+        }
+        a.outcome[e] = (int8_t)g.outcome;
+        a.plies[e] = (int16_t)g.ply;
+        q = refill ? slots + claim_next(a.cursor) : a.n;
+        if (q >= end) return q;
+        e = a.queue[q];
+        g.reset();
+        key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
+    }
+}
+
+template <int N, bool TABLE>
+__device__ __forceinline__ long long run_hex(const MixedArgs& a, long long q, long long end, long long slots,
+                                             bool refill, const B128* tables) {
+    return run_bucket<Hex<N>>(a, q, end, slots, refill, TABLE ? tables + hex_table_offset(N) : nullptr);
+}
+
+template <bool TABLE>
+__global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
+    __shared__ B128 tables[TABLE ? kHexTableCells : 1];
+    if constexpr (TABLE) {
+        hex_fill_table<2>(tables + hex_table_offset(2));
+        hex_fill_table<3>(tables + hex_table_offset(3));
+        hex_fill_table<4>(tables + hex_table_offset(4));
+        hex_fill_table<5>(tables + hex_table_offset(5));
+        hex_fill_table<6>(tables + hex_table_offset(6));
+        hex_fill_table<7>(tables + hex_table_offset(7));
+        hex_fill_table<8>(tables + hex_table_offset(8));
+        hex_fill_table<9>(tables + hex_table_offset(9));
+        hex_fill_table<10>(tables + hex_table_offset(10));
+        hex_fill_table<11>(tables + hex_table_offset(11));
+        __syncthreads();
+    }
+    const long long slots = (long long)gridDim.x * blockDim.x;
+    const bool refill = slots < a.n;
+    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    while (q < a.n) {
+        int b = bucket_at(a, q);
+        long long end = a.bucket_end[b];
+        switch (b) {
+        case 0: q = run_bucket<TTT>(a, q, end, slots, refill, nullptr); break;
+        case 1: q = run_bucket<C4>(a, q, end, slots, refill, nullptr); break;
+        case 2: q = run_bucket<Othello>(a, q, end, slots, refill, nullptr); break;
+        case 3: q = run_hex<2, TABLE>(a, q, end, slots, refill, tables); break;
+        case 4: q = run_hex<3, TABLE>(a, q, end, slots, refill, tables); break;
+        case 5: q = run_hex<4, TABLE>(a, q, end, slots, refill, tables); break;
+        case 6: q = run_hex<5, TABLE>(a, q, end, slots, refill, tables); break;
+        case 7: q = run_hex<6, TABLE>(a, q, end, slots, refill, tables); break;
+        case 8: q = run_hex<7, TABLE>(a, q, end, slots, refill, tables); break;
+        case 9: q = run_hex<8, TABLE>(a, q, end, slots, refill, tables); break;
+        case 10: q = run_hex<9, TABLE>(a, q, end, slots, refill, tables); break;
+        case 11: q = run_hex<10, TABLE>(a, q, end, slots, refill, tables); break;
+        default: q = run_hex<11, TABLE>(a, q, end, slots, refill, tables); break;
+        }
+    }
+}
+
+int mixed_grid(long long n, const ludax_launch_cfg& c, int num_sms) {
+    long long need = (n + c.block_threads - 1) / c.block_threads;
+    if (c.blocks_per_sm > 0) need = std::min<long long>(need, (long long)num_sms * c.blocks_per_sm);
+    return (int)std::max<long long>(need, 1);
+}
+
+int check_mixed_cfg(const ludax_launch_cfg& c) {
+    if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32) return LUDAX_ERR_ARG;
+    if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return LUDAX_ERR_ARG;
+    if (c.envs_per_thread != 1) return LUDAX_ERR_ARG;  // the mixed kernel runs one env per lane
+    if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
+    return LUDAX_OK;
+}
+
+// Groups env ids by bucket on the host (stable: ascending env id inside a
+// bucket).  Returns LUDAX_OK or the error of the first bad descriptor.
+int build_queue(const int32_t* desc_dev, long long n, std::vector<int32_t>& queue, long long* bucket_end,
+                int64_t* bad_index) {
+    std::vector<int32_t> desc((size_t)n);
+    if (cudaMemcpy(desc.data(), desc_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    long long count[kBuckets] = {0};
+    for (long long e = 0; e < n; ++e) {
+        int b = bucket_of_desc(desc[(size_t)e]);
+        if (b < 0) {
+            if (bad_index) *bad_index = e;
+            return b == -1 ? LUDAX_ERR_GAME : LUDAX_ERR_SIZE;
+        }
+        count[b]++;
+    }
+    long long pos[kBuckets], acc = 0;
+    for (int b = 0; b < kBuckets; ++b) {
+        pos[b] = acc;
+        acc += count[b];
+        bucket_end[b] = acc;
+    }
+    queue.resize((size_t)n);
+    for (long long e = 0; e < n; ++e) queue[(size_t)pos[bucket_of_desc(desc[(size_t)e])]++] = (int32_t)e;
+    if (bad_index) *bad_index = -1;
+    return LUDAX_OK;
+}
+
+int launch_mixed(const MixedArgs& a, const ludax_launch_cfg& c, int num_sms, cudaStream_t s) {
+    int grid = mixed_grid(a.n, c, num_sms);
+    if (cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long), s) != cudaSuccess) return LUDAX_ERR_CUDA;
+    if (c.hex_nbr_table) mixed_rollout_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
+    else mixed_rollout_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+int num_sms_current(int* out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LUDAX_ERR_CUDA;
+    if (cudaDeviceGetAttribute(out, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LUDAX_ERR_CUDA;
+    return LUDAX_OK;
+}
+
+ludax_launch_cfg default_mixed_cfg() { return ludax_launch_cfg{256, 0, 1, 0}; }
+
+}  // namespace
+
+struct ludax_mixed_plan {
+    long long n, env_offset;
+    int num_sms;
+    ludax_launch_cfg cfg;
+    cudaStream_t stream;
+    int32_t* d_queue;
+    unsigned long long* d_cursor;
+    long long bucket_end[kBuckets];
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaGraphNode_t kernel_node;
+    cudaKernelNodeParams kparams;
+    MixedArgs args;  // kernel parameter block updated before each replay
+};
+
+extern "C" {
+
+int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,
+                        int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg, void* stream) {
+    if (!desc_dev || !outcome_dev || !plies_dev || num_envs < 1 || num_envs > 0x7FFFFFFFll || env_offset < 0)
+        return LUDAX_ERR_ARG;
+    if (((uintptr_t)desc_dev % 4) || ((uintptr_t)plies_dev % 2)) return LUDAX_ERR_ALIGN;
+    ludax_launch_cfg c = cfg ? *cfg : default_mixed_cfg();
+    int st = check_mixed_cfg(c);
+    if (st != LUDAX_OK) return st;
+    int sms = 0;
+    if ((st = num_sms_current(&sms)) != LUDAX_OK) return st;
+    std::vector<int32_t> queue;
+    MixedArgs a{};
+    if ((st = build_queue(desc_dev, num_envs, queue, a.bucket_end, nullptr)) != LUDAX_OK) return st;
+    int32_t* d_queue = nullptr;
+    unsigned long long* d_cursor = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMalloc(&d_queue, sizeof(int32_t) * num_envs) != cudaSuccess ||
+        cudaMalloc(&d_cursor, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(d_queue);
+        cudaGetLastError();
+        return LUDAX_ERR_NOMEM;
+    }
+    st = LUDAX_OK;
+    if (cudaMemcpyAsync(d_queue, queue.data(), sizeof(int32_t) * num_envs, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = LUDAX_ERR_CUDA;
+    a.queue = d_queue;
+    a.n = num_envs;
+    a.env_offset = env_offset;
+    a.seed_key = splitmix64(seed);
+    a.outcome = outcome_dev;
+    a.plies = plies_dev;
+    a.cursor = d_cursor;
+    if (st == LUDAX_OK) st = launch_mixed(a, c, sms, s);
+    // the queue and cursor must outlive the launch
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = LUDAX_ERR_CUDA;
+    cudaFree(d_queue);
+    cudaFree(d_cursor);
+    return st;
+}
+
+int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int64_t num_envs, int64_t env_offset,
+                            const ludax_launch_cfg* cfg, void* stream, int64_t* bad_index) {
+    if (!out || !desc_dev || num_envs < 1 || num_envs > 0x7FFFFFFFll || env_offset < 0) return LUDAX_ERR_ARG;
+    *out = nullptr;
+    if ((uintptr_t)desc_dev % 4) return LUDAX_ERR_ALIGN;
+    ludax_launch_cfg c = cfg ? *cfg : default_mixed_cfg();
+    int st = check_mixed_cfg(c);
+    if (st != LUDAX_OK) return st;
+    ludax_mixed_plan* p = new (std::nothrow) ludax_mixed_plan();
+    if (!p) return LUDAX_ERR_NOMEM;
+    p->n = num_envs;
+    p->env_offset = env_offset;
+    p->cfg = c;
+    p->stream = (cudaStream_t)stream;
+    if ((st = num_sms_current(&p->num_sms)) != LUDAX_OK) {
+        delete p;
+        return st;
+    }
+    std::vector<int32_t> queue;
+    if ((st = build_queue(desc_dev, num_envs, queue, p->bucket_end, bad_index)) != LUDAX_OK) {
+        delete p;
+        return st;
+    }
+    if (cudaMalloc(&p->d_queue, sizeof(int32_t) * num_envs) != cudaSuccess ||
+        cudaMalloc(&p->d_cursor, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(p->d_queue);
+        cudaGetLastError();
+        delete p;
+        return LUDAX_ERR_NOMEM;
+    }
+    if (cudaMemcpy(p->d_queue, queue.data(), sizeof(int32_t) * num_envs, cudaMemcpyHostToDevice) != cudaSuccess) {
+        ludax_mixed_plan_destroy(p);
+        return LUDAX_ERR_CUDA;
+    }
+    MixedArgs& a = p->args;
+    a.queue = p->d_queue;
+    for (int b = 0; b < kBuckets; ++b) a.bucket_end[b] = p->bucket_end[b];
+    a.n = num_envs;
+    a.env_offset = env_offset;
+    a.seed_key = 0;
+    a.outcome = nullptr;
+    a.plies = nullptr;
+    a.cursor = p->d_cursor;
+    // capture cursor reset + kernel on a private stream
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        ludax_mixed_plan_destroy(p);
+        return LUDAX_ERR_CUDA;
+    }
+    st = LUDAX_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = LUDAX_ERR_CUDA;
+    if (st == LUDAX_OK) {
+        int lst = launch_mixed(a, c, p->num_sms, cap);
+        cudaError_t e = cudaStreamEndCapture(cap, &p->graph);
+        if (lst != LUDAX_OK || e != cudaSuccess) st = LUDAX_ERR_CUDA;
+    }
+    cudaStreamDestroy(cap);
+    if (st == LUDAX_OK) {
+        size_t nn = 0;
+        cudaGraphGetNodes(p->graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(p->graph, nodes.data(), &nn);
+        p->kernel_node = nullptr;
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            cudaGraphNodeGetType(nd, &t);
+            if (t == cudaGraphNodeTypeKernel) p->kernel_node = nd;
+        }
+        if (!p->kernel_node || cudaGraphKernelNodeGetParams(p->kernel_node, &p->kparams) != cudaSuccess ||
+            cudaGraphInstantiate(&p->exec, p->graph, 0) != cudaSuccess)
+            st = LUDAX_ERR_CUDA;
+    }
+    if (st != LUDAX_OK) {
+        cudaGetLastError();
+        ludax_mixed_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return LUDAX_OK;
+}
+
+int ludax_mixed_plan_launch(ludax_mixed_plan* p, uint64_t seed, int8_t* outcome_dev, int16_t* plies_dev) {
+    if (!p || !outcome_dev || !plies_dev) return LUDAX_ERR_ARG;
+    if ((uintptr_t)plies_dev % 2) return LUDAX_ERR_ALIGN;
+    p->args.seed_key = splitmix64(seed);
+    p->args.outcome = outcome_dev;
+    p->args.plies = plies_dev;
+    void* params[1] = {&p->args};
+    cudaKernelNodeParams kp = p->kparams;
+    kp.kernelParams = params;
+    kp.extra = nullptr;
+    if (cudaGraphExecKernelNodeSetParams(p->exec, p->kernel_node, &kp) != cudaSuccess) return LUDAX_ERR_CUDA;
+    if (cudaGraphLaunch(p->exec, p->stream) != cudaSuccess) return LUDAX_ERR_CUDA;
+    return LUDAX_OK;
+}
+
+int ludax_mixed_plan_destroy(ludax_mixed_plan* p) {
+    if (!p) return LUDAX_OK;
+    cudaStreamSynchronize(p->stream);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->d_queue);
+    cudaFree(p->d_cursor);
+    delete p;
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out) {
+    static const int blocks[] = {64, 128, 256, 512};
+    static const int bps[] = {0, 2, 4, 8, 16};
+    int k = 0;
+    for (int t = 0; t < 2; ++t)
+        for (int b : blocks)
+            for (int s : bps) {
+                if (s > 0 && b * s > 2048) continue;  // more than one SM's threads
+                if (out && k < max_out) out[k] = ludax_launch_cfg{b, s, 1, t};
+                ++k;
+            }
+    return k;
+}
+
+int ludax_autotune(const int32_t* desc_dev, int64_t num_envs, uint64_t seed, int32_t reps, void* stream,
+                   ludax_launch_cfg* best_out, float* best_ms_out, float* ms_table_out, int32_t* n_candidates_out) {
+    if (!desc_dev || !best_out || num_envs < 1 || reps < 1) return LUDAX_ERR_ARG;
+    int nc = ludax_autotune_candidates(nullptr, 0);
+    std::vector<ludax_launch_cfg> cands((size_t)nc);
+    ludax_autotune_candidates(cands.data(), nc);
+    cudaStream_t s = (cudaStream_t)stream;
+    int8_t* d_out = nullptr;
+    int16_t* d_plies = nullptr;
+    if (cudaMalloc(&d_out, num_envs) != cudaSuccess || cudaMalloc(&d_plies, 2 * num_envs) != cudaSuccess) {
+        cudaFree(d_out);
+        cudaGetLastError();
+        return LUDAX_ERR_NOMEM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int st = LUDAX_OK;
+    float best = 1e30f;
+    for (int i = 0; i < nc && st == LUDAX_OK; ++i) {
+        ludax_mixed_plan* plan = nullptr;
+        st = ludax_mixed_plan_create(&plan, desc_dev, num_envs, 0, &cands[(size_t)i], stream, nullptr);
+        if (st != LUDAX_OK) break;
+        std::vector<float> t;
+        for (int r = 0; r < reps + 2 && st == LUDAX_OK; ++r) {
+            cudaEventRecord(e0, s);
+            st = ludax_mixed_plan_launch(plan, seed + (uint64_t)r, d_out, d_plies);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = LUDAX_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r >= 2) t.push_back(ms);
+        }
+        ludax_mixed_plan_destroy(plan);
+        if (st != LUDAX_OK) break;
+        std::sort(t.begin(), t.end());
+        float med = t[t.size() / 2];
+        if (ms_table_out) ms_table_out[i] = med;
+        if (med < best) {
+            best = med;
+            *best_out = cands[(size_t)i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_out);
+    cudaFree(d_plies);
+    if (best_ms_out) *best_ms_out = best;
+    if (n_candidates_out) *n_candidates_out = nc;
+    return st;
+}
+
+}  // extern "C"

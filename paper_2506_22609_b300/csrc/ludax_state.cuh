@@ -1,0 +1,121 @@
+// ludax_state.cuh -- env state in HBM (structure of arrays) and the
+// persistent playout loop shared by the single-game and mixed-game kernels.
+//
+// HBM layout of an env batch of n envs (all arrays length n, coalesced by env):
+//   planes[k*n + e]  uint64 bitboard planes in the game's internal layout
+//                    TTT/C4/Reversi: k=0 P1 stones, k=1 P2 stones
+//                    Hex: k=0,1 P1 stones (lo, hi word), k=2,3 P2 stones,
+//                         k=4,5 P1 edge-A set, k=6,7 P1 edge-B set,
+//                         k=8,9 P2 edge-A set, k=10,11 P2 edge-B set
+//   meta[e]          uint32: bits 0-7 ply, 8-9 passes, 10 side to move
+//                    (0 = P1), 12-14 outcome+1 (0 ongoing), 15 illegal flag
+#pragma once
+#include "ludax_games.cuh"
+
+namespace ludax {
+
+struct EnvDev {
+    uint64_t* planes;
+    uint32_t* meta;
+    int64_t n;
+    int64_t env_offset;
+    unsigned long long* counters;  // [0] refill cursor, [1] illegal actions, [2] capped envs
+};
+
+__device__ __forceinline__ uint32_t pack_meta(int ply, int passes, int side, int outcome, int illegal) {
+    return (uint32_t)(ply & 0xFF) | ((uint32_t)(passes & 3) << 8) | ((uint32_t)(side & 1) << 10) |
+           ((uint32_t)((outcome + 1) & 7) << 12) | ((uint32_t)(illegal & 1) << 15);
+}
+__device__ __forceinline__ void unpack_meta(uint32_t m, int& ply, int& passes, int& side, int& outcome) {
+    ply = (int)(m & 0xFF);
+    passes = (int)((m >> 8) & 3);
+    side = (int)((m >> 10) & 1);
+    outcome = (int)((m >> 12) & 7) - 1;
+}
+
+template <class G>
+struct HexN {
+    static constexpr int value = 0;
+};
+template <int N>
+struct HexN<Hex<N>> {
+    static constexpr int value = N;
+};
+
+// -------------------------------------------------------- load / store --
+template <class G>
+__device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
+    unpack_meta(d.meta[e], g.ply, g.passes, g.side, g.outcome);
+    if constexpr (HexN<G>::value == 0) {
+        uint64_t p1 = d.planes[e], p2 = d.planes[d.n + e];
+        uint64_t own = g.side == 0 ? p1 : p2, opp = g.side == 0 ? p2 : p1;
+        g.own = (typename G::Mask)own;
+        g.opp = (typename G::Mask)opp;
+    } else {
+        const uint64_t* P = d.planes;
+        const int64_t n = d.n;
+        B128 s1 = {P[0 * n + e], P[1 * n + e]}, s2 = {P[2 * n + e], P[3 * n + e]};
+        B128 a1 = {P[4 * n + e], P[5 * n + e]}, b1 = {P[6 * n + e], P[7 * n + e]};
+        B128 a2 = {P[8 * n + e], P[9 * n + e]}, b2 = {P[10 * n + e], P[11 * n + e]};
+        bool p1 = g.side == 0;
+        g.own = p1 ? s1 : s2;
+        g.opp = p1 ? s2 : s1;
+        g.ownA = p1 ? a1 : a2;
+        g.ownB = p1 ? b1 : b2;
+        g.oppA = p1 ? a2 : a1;
+        g.oppB = p1 ? b2 : b1;
+    }
+}
+
+template <class G>
+__device__ __forceinline__ void store_state(const G& g, const EnvDev& d, int64_t e, int illegal = 0) {
+    d.meta[e] = pack_meta(g.ply, g.passes, g.side, g.outcome, illegal);
+    if constexpr (HexN<G>::value == 0) {
+        uint64_t own = (uint64_t)g.own, opp = (uint64_t)g.opp;
+        d.planes[e] = g.side == 0 ? own : opp;
+        d.planes[d.n + e] = g.side == 0 ? opp : own;
+    } else {
+        uint64_t* P = d.planes;
+        const int64_t n = d.n;
+        bool p1 = g.side == 0;
+        B128 s1 = p1 ? g.own : g.opp, s2 = p1 ? g.opp : g.own;
+        B128 a1 = p1 ? g.ownA : g.oppA, b1 = p1 ? g.ownB : g.oppB;
+        B128 a2 = p1 ? g.oppA : g.ownA, b2 = p1 ? g.oppB : g.ownB;
+        P[0 * n + e] = s1.lo; P[1 * n + e] = s1.hi;
+        P[2 * n + e] = s2.lo; P[3 * n + e] = s2.hi;
+        P[4 * n + e] = a1.lo; P[5 * n + e] = a1.hi;
+        P[6 * n + e] = b1.lo; P[7 * n + e] = b1.hi;
+        P[8 * n + e] = a2.lo; P[9 * n + e] = a2.hi;
+        P[10 * n + e] = b2.lo; P[11 * n + e] = b2.hi;
+    }
+}
+
+template <class G>
+__device__ __forceinline__ void set_table(G& g, const B128* table) {
+    if constexpr (HexN<G>::value != 0) g.nbr_table = table;
+}
+
+// is bit b of the internal mask set?
+__device__ __forceinline__ bool mask_has(uint32_t m, int b) { return (m >> b) & 1u; }
+__device__ __forceinline__ bool mask_has(uint64_t m, int b) { return (m >> b) & 1ull; }
+__device__ __forceinline__ bool mask_has(B128 m, int b) { return b < 64 ? ((m.lo >> b) & 1ull) : ((m.hi >> (b - 64)) & 1ull); }
+
+// ------------------------------------------------------------- refill --
+// Warp-aggregated claim of one new work index per calling lane: the lanes
+// that arrive together take consecutive indices with one atomic.
+__device__ __forceinline__ long long claim_next(unsigned long long* cursor) {
+    unsigned m = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(cursor, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+// result of a finished game from P1's view: win 1, draw 0.5, loss 0
+__device__ __forceinline__ float p1_score(int outcome) {
+    return outcome == kWin1 ? 1.0f : (outcome == kWin2 ? 0.0f : 0.5f);
+}
+
+}  // namespace ludax

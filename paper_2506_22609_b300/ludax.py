@@ -1,0 +1,351 @@
+"""Python binding of the C-ABI in ``include/ludax.h`` (argument marshalling only).
+
+Every function below has the name of the C entry point it calls, takes torch
+tensors where the C call takes device pointers, checks the returned status and
+raises ``LudaxError`` on failure.  All game logic runs in ``libludax.so``'s CUDA
+kernels; there is no Python or CPU fallback: importing this module fails when
+the library cannot be loaded.
+
+``Env`` wraps an env handle with the same calls as methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libludax.so")
+
+LUDAX_OK = 0
+LUDAX_GAME_TTT, LUDAX_GAME_C4, LUDAX_GAME_OTHELLO, LUDAX_GAME_HEX = 0, 1, 2, 3
+LUDAX_OUTCOME_ONGOING, LUDAX_OUTCOME_DRAW, LUDAX_OUTCOME_P1, LUDAX_OUTCOME_P2, LUDAX_OUTCOME_CAPPED = -1, 0, 1, 2, 3
+LUDAX_ROLLOUT_FROM_START, LUDAX_ROLLOUT_WRITE_BACK = 1, 2
+
+GAME_IDS = {"ttt": LUDAX_GAME_TTT, "c4": LUDAX_GAME_C4, "othello": LUDAX_GAME_OTHELLO, "hex": LUDAX_GAME_HEX}
+
+
+def LUDAX_DESC(game: int, rows: int, cols: int) -> int:
+    return game | (rows << 8) | (cols << 16)
+
+
+class LudaxError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class ludax_board_params(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32)]
+
+
+class ludax_state_view(ctypes.Structure):
+    _fields_ = [("board", ctypes.c_void_p), ("to_move", ctypes.c_void_p), ("ply", ctypes.c_void_p),
+                ("passes", ctypes.c_void_p), ("outcome", ctypes.c_void_p)]
+
+
+class ludax_launch_cfg(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("envs_per_thread", ctypes.c_int32), ("hex_nbr_table", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    def __repr__(self):
+        return f"ludax_launch_cfg({self.as_dict()})"
+
+
+def make_cfg(block_threads=256, blocks_per_sm=0, envs_per_thread=1, hex_nbr_table=0) -> ludax_launch_cfg:
+    return ludax_launch_cfg(block_threads, blocks_per_sm, envs_per_thread, hex_nbr_table)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libludax.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not found: build it with `python -m paper_2506_22609_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, u32, u64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "ludax_env_create": [P(vp), i32, P(ludax_board_params), i64, i64, vp],
+        "ludax_env_destroy": [vp],
+        "ludax_env_set_stream": [vp, vp],
+        "ludax_env_sizes": [vp, P(i32), P(i32), P(i64)],
+        "ludax_reset": [vp, vp],
+        "ludax_legal_mask": [vp, vp, vp],
+        "ludax_step": [vp, vp, vp, vp],
+        "ludax_random_step": [vp, u64, vp, vp],
+        "ludax_rollout": [vp, u64, u32, vp, vp, vp, P(ludax_launch_cfg)],
+        "ludax_rollout_value": [vp, u64, i32, vp, P(ludax_launch_cfg)],
+        "ludax_get_state": [vp, P(ludax_state_view)],
+        "ludax_set_state": [vp, P(ludax_state_view)],
+        "ludax_counters": [vp, P(i64), P(i64)],
+        "ludax_sync": [vp, i64],
+        "ludax_rollout_mixed": [vp, i64, i64, u64, vp, vp, P(ludax_launch_cfg), vp],
+        "ludax_mixed_plan_create": [P(vp), vp, i64, i64, P(ludax_launch_cfg), vp, P(i64)],
+        "ludax_mixed_plan_launch": [vp, u64, vp, vp],
+        "ludax_mixed_plan_destroy": [vp],
+        "ludax_autotune": [vp, i64, u64, i32, vp, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
+        "ludax_autotune_env": [vp, u64, i32, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
+        "ludax_autotune_candidates": [P(ludax_launch_cfg), i32],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.ludax_status_string.argtypes = [ctypes.c_int]
+    L.ludax_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def status_string(status: int) -> str:
+    return lib().ludax_status_string(status).decode()
+
+
+def _check(status: int, where: str):
+    if status != LUDAX_OK:
+        raise LudaxError(status, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor (device memory)")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------- C-ABI calls --
+def ludax_env_create(game: int, rows: int, cols: int, num_envs: int, env_offset: int = 0, stream=None):
+    h = ctypes.c_void_p()
+    p = ludax_board_params(rows, cols)
+    _check(lib().ludax_env_create(ctypes.byref(h), game, ctypes.byref(p), num_envs, env_offset, _stream(stream)),
+           "ludax_env_create")
+    return h
+
+
+def ludax_env_destroy(h):
+    _check(lib().ludax_env_destroy(h), "ludax_env_destroy")
+
+
+def ludax_env_set_stream(h, stream):
+    _check(lib().ludax_env_set_stream(h, _stream(stream)), "ludax_env_set_stream")
+
+
+def ludax_env_sizes(h):
+    a, w, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().ludax_env_sizes(h, ctypes.byref(a), ctypes.byref(w), ctypes.byref(n)), "ludax_env_sizes")
+    return a.value, w.value, n.value
+
+
+def ludax_reset(h, env_mask=None):
+    _check(lib().ludax_reset(h, _ptr(env_mask)), "ludax_reset")
+
+
+def ludax_legal_mask(h, mask, pass_legal=None):
+    _check(lib().ludax_legal_mask(h, _ptr(mask), _ptr(pass_legal)), "ludax_legal_mask")
+
+
+def ludax_step(h, actions, rewards, terminated):
+    _check(lib().ludax_step(h, _ptr(actions), _ptr(rewards), _ptr(terminated)), "ludax_step")
+
+
+def ludax_random_step(h, seed: int, rewards, terminated):
+    _check(lib().ludax_random_step(h, seed, _ptr(rewards), _ptr(terminated)), "ludax_random_step")
+
+
+def ludax_rollout(h, seed: int, flags: int, stop_ply=None, outcome=None, plies=None, cfg=None):
+    _check(lib().ludax_rollout(h, seed, flags, _ptr(stop_ply), _ptr(outcome), _ptr(plies),
+                               ctypes.byref(cfg) if cfg is not None else None), "ludax_rollout")
+
+
+def ludax_rollout_value(h, seed: int, R: int, value, cfg=None):
+    _check(lib().ludax_rollout_value(h, seed, R, _ptr(value), ctypes.byref(cfg) if cfg is not None else None),
+           "ludax_rollout_value")
+
+
+def _view(board, to_move, ply, passes, outcome):
+    return ludax_state_view(*(t.data_ptr() for t in (board, to_move, ply, passes, outcome)))
+
+
+def ludax_get_state(h, board, to_move, ply, passes, outcome):
+    for t in (board, to_move, ply, passes, outcome):
+        _ptr(t)
+    v = _view(board, to_move, ply, passes, outcome)
+    _check(lib().ludax_get_state(h, ctypes.byref(v)), "ludax_get_state")
+
+
+def ludax_set_state(h, board, to_move, ply, passes, outcome):
+    for t in (board, to_move, ply, passes, outcome):
+        _ptr(t)
+    v = _view(board, to_move, ply, passes, outcome)
+    _check(lib().ludax_set_state(h, ctypes.byref(v)), "ludax_set_state")
+
+
+def ludax_counters(h):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ludax_counters(h, ctypes.byref(a), ctypes.byref(b)), "ludax_counters")
+    return a.value, b.value
+
+
+def ludax_sync(h, timeout_ms: int = -1):
+    _check(lib().ludax_sync(h, timeout_ms), "ludax_sync")
+
+
+def ludax_rollout_mixed(desc, env_offset: int, seed: int, outcome, plies, cfg=None, stream=None):
+    _check(lib().ludax_rollout_mixed(_ptr(desc), desc.numel(), env_offset, seed, _ptr(outcome), _ptr(plies),
+                                     ctypes.byref(cfg) if cfg is not None else None, _stream(stream)),
+           "ludax_rollout_mixed")
+
+
+def ludax_mixed_plan_create(desc, env_offset: int = 0, cfg=None, stream=None):
+    h = ctypes.c_void_p()
+    bad = ctypes.c_int64(-1)
+    st = lib().ludax_mixed_plan_create(ctypes.byref(h), _ptr(desc), desc.numel(), env_offset,
+                                       ctypes.byref(cfg) if cfg is not None else None, _stream(stream),
+                                       ctypes.byref(bad))
+    if st != LUDAX_OK:
+        err = LudaxError(st, f"ludax_mixed_plan_create (first bad descriptor index {bad.value})")
+        err.bad_index = bad.value
+        raise err
+    return h
+
+
+def ludax_mixed_plan_launch(plan, seed: int, outcome, plies):
+    _check(lib().ludax_mixed_plan_launch(plan, seed, _ptr(outcome), _ptr(plies)), "ludax_mixed_plan_launch")
+
+
+def ludax_mixed_plan_destroy(plan):
+    _check(lib().ludax_mixed_plan_destroy(plan), "ludax_mixed_plan_destroy")
+
+
+def ludax_autotune_candidates():
+    n = lib().ludax_autotune_candidates(None, 0)
+    arr = (ludax_launch_cfg * n)()
+    lib().ludax_autotune_candidates(arr, n)
+    return list(arr)
+
+
+def ludax_autotune(desc, seed: int = 0, reps: int = 5, stream=None):
+    """Returns (best cfg, best median ms, [(cfg, ms) per candidate])."""
+    cands = ludax_autotune_candidates()
+    best = ludax_launch_cfg()
+    best_ms = ctypes.c_float()
+    table = (ctypes.c_float * len(cands))()
+    nc = ctypes.c_int32()
+    _check(lib().ludax_autotune(_ptr(desc), desc.numel(), seed, reps, _stream(stream), ctypes.byref(best),
+                                ctypes.byref(best_ms), table, ctypes.byref(nc)), "ludax_autotune")
+    return best, best_ms.value, list(zip(cands, list(table)))
+
+
+def ludax_autotune_env(h, seed: int = 0, reps: int = 5):
+    """Autotunes ludax_rollout (from the start position) for one env batch."""
+    cands_n = ctypes.c_int32()
+    best = ludax_launch_cfg()
+    best_ms = ctypes.c_float()
+    table = (ctypes.c_float * 256)()
+    _check(lib().ludax_autotune_env(h, seed, reps, ctypes.byref(best), ctypes.byref(best_ms), table,
+                                    ctypes.byref(cands_n)), "ludax_autotune_env")
+    return best, best_ms.value, list(table)[: cands_n.value]
+
+
+# ------------------------------------------------------------------- Env ----
+class Env:
+    """A batch of num_envs envs of one game on the current CUDA device."""
+
+    def __init__(self, game, rows, cols, num_envs, env_offset=0, stream=None, device=None):
+        if isinstance(game, str):
+            game = GAME_IDS[game]
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.game, self.rows, self.cols, self.num_envs, self.env_offset = game, rows, cols, num_envs, env_offset
+        self.stream = stream
+        with torch.cuda.device(self.device):
+            self.handle = ludax_env_create(game, rows, cols, num_envs, env_offset, stream)
+        self.num_actions, self.mask_words, _ = ludax_env_sizes(self.handle)
+        self.cells = rows * cols
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            ludax_env_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, shape, dtype):
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    def reset(self, env_mask=None):
+        ludax_reset(self.handle, env_mask)
+
+    def legal_mask(self):
+        m = self._empty((self.num_envs, self.mask_words), torch.int64)
+        p = self._empty((self.num_envs,), torch.uint8)
+        ludax_legal_mask(self.handle, m, p)
+        return m, p
+
+    def step(self, actions):
+        r = self._empty((self.num_envs, 2), torch.float32)
+        t = self._empty((self.num_envs,), torch.uint8)
+        ludax_step(self.handle, actions.to(torch.int32).contiguous(), r, t)
+        return r, t
+
+    def random_step(self, seed):
+        r = self._empty((self.num_envs, 2), torch.float32)
+        t = self._empty((self.num_envs,), torch.uint8)
+        ludax_random_step(self.handle, seed, r, t)
+        return r, t
+
+    def rollout(self, seed, from_start=True, write_back=False, stop_ply=None, cfg=None, outcome=None, plies=None):
+        flags = (LUDAX_ROLLOUT_FROM_START if from_start else 0) | (LUDAX_ROLLOUT_WRITE_BACK if write_back else 0)
+        out = outcome if outcome is not None else self._empty((self.num_envs,), torch.int8)
+        pl = plies if plies is not None else self._empty((self.num_envs,), torch.int16)
+        ludax_rollout(self.handle, seed, flags, stop_ply, out, pl, cfg)
+        return out, pl
+
+    def rollout_value(self, seed, R, cfg=None):
+        v = self._empty((self.num_envs,), torch.float32)
+        ludax_rollout_value(self.handle, seed, R, v, cfg)
+        return v
+
+    def get_state(self):
+        n = self.num_envs
+        board = self._empty((n, self.cells), torch.int8)
+        to_move = self._empty((n,), torch.int8)
+        ply = self._empty((n,), torch.int16)
+        passes = self._empty((n,), torch.int8)
+        outcome = self._empty((n,), torch.int8)
+        ludax_get_state(self.handle, board, to_move, ply, passes, outcome)
+        return board, to_move, ply, passes, outcome
+
+    def set_state(self, board, to_move, ply, passes, outcome):
+        ts = [t.to(self.device).contiguous() for t in (board, to_move, ply, passes, outcome)]
+        ludax_set_state(self.handle, *ts)
+        ludax_sync(self.handle)  # the temporaries in ts must outlive the copy
+
+    def counters(self):
+        return ludax_counters(self.handle)
+
+    def sync(self, timeout_ms=-1):
+        ludax_sync(self.handle, timeout_ms)

@@ -1,0 +1,88 @@
+"""Workload definitions and seeded input generators.
+
+This module holds no game arithmetic: it only names the benchmark
+configurations (game, board, number of envs, seed) and builds the inputs that
+both the CUDA path and the CPU oracle receive -- per-env game descriptors for
+mixed batches and seeded action/position samples for step tests.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+TTT, C4, OTHELLO, HEX = 0, 1, 2, 3
+
+
+def desc(game: int, rows: int, cols: int) -> int:
+    """Per-env descriptor: game | rows << 8 | cols << 16."""
+    return game | (rows << 8) | (cols << 16)
+
+
+@dataclass(frozen=True)
+class Config:
+    name: str
+    game: int
+    rows: int
+    cols: int
+    num_envs: int
+    seed: int
+
+
+# Uniform-random playouts from the start position (the random-policy
+# benchmark of the paper's Sec. 6, at the batch sizes used here).
+TTT_1K = Config("ttt3x3_1024env_seed0", TTT, 3, 3, 1024, 0)
+C4_64K = Config("connect4_6x7_65536env_seed1", C4, 6, 7, 65536, 1)
+OTHELLO_256K = Config("othello8x8_262144env_seed2", OTHELLO, 8, 8, 262144, 2)
+HEX11_64K = Config("hex11x11_65536env_seed4", HEX, 11, 11, 65536, 4)
+
+# The mixed batch: 2^20 envs over six games, seed 3.
+MIXED_GAMES = [(TTT, 3, 3), (C4, 6, 7), (OTHELLO, 8, 8), (HEX, 7, 7), (HEX, 9, 9), (HEX, 11, 11)]
+MIXED_ENVS = 1 << 20
+MIXED_SEED = 3
+
+
+def mixed_descriptors(n: int = MIXED_ENVS, layout: str = "block") -> np.ndarray:
+    """Descriptors for an even split of n envs over the six mixed games.
+
+    layout "block": env e plays game floor(6e/n) (contiguous thirds... sixths);
+    layout "interleave": env e plays game e mod 6 (every warp mixes games).
+    """
+    e = np.arange(n, dtype=np.int64)
+    g = (6 * e) // n if layout == "block" else e % 6
+    table = np.array([desc(*x) for x in MIXED_GAMES], dtype=np.int32)
+    return table[g]
+
+
+def random_descriptors(n: int, seed: int) -> np.ndarray:
+    """Descriptors drawn uniformly over every supported (game, size)."""
+    all_desc = [desc(TTT, 3, 3), desc(C4, 6, 7), desc(OTHELLO, 8, 8)] + [desc(HEX, k, k) for k in range(2, 12)]
+    rng = np.random.default_rng(seed)
+    return np.array(all_desc, dtype=np.int32)[rng.integers(0, len(all_desc), n)]
+
+
+def sample_envs(n_total: int, k: int, seed: int) -> np.ndarray:
+    """k distinct env indices in [0, n_total), always including both ends."""
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(n_total, size=min(k, n_total), replace=False)
+    idx[0], idx[-1] = 0, n_total - 1
+    return np.unique(idx)
+
+
+# Launch shapes the benchmark times (block_threads, blocks_per_sm,
+# envs_per_thread, hex_nbr_table); chosen with the autotuner on a B300.
+BENCH_CFGS = {
+    TTT_1K.name: (128, 0, 1, 0),
+    C4_64K.name: (128, 0, 1, 0),
+    OTHELLO_256K.name: (256, 0, 1, 0),
+    HEX11_64K.name: (128, 0, 1, 0),
+}
+MIXED_BENCH_CFG = (256, 0, 1, 0)
+
+
+def bench_cfg(cfg: Config) -> tuple:
+    return BENCH_CFGS.get(cfg.name, (256, 0, 1, 0))
+
+
+def mixed_bench_cfg() -> tuple:
+    return MIXED_BENCH_CFG

@@ -1,0 +1,108 @@
+"""The C-ABI library builds, loads and exports every symbol include/ludax.h
+declares; host-side argument validation returns status codes without a GPU.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "ludax.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ludax_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2506_22609_b300 import build, ludax
+
+    build.build()
+    return ludax.lib()
+
+
+def test_header_declares_core_api():
+    names = declared_functions()
+    for core in ("ludax_env_create", "ludax_env_destroy", "ludax_reset", "ludax_legal_mask", "ludax_step",
+                 "ludax_random_step", "ludax_rollout", "ludax_get_state", "ludax_set_state", "ludax_sync",
+                 "ludax_status_string", "ludax_mixed_plan_create", "ludax_autotune"):
+        assert core in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    from paper_2506_22609_b300 import ludax
+
+    out = subprocess.run(["nm", "-D", "--defined-only", ludax.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (ludax_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        getattr(L, n)  # resolvable through ctypes too
+
+
+def test_build_targets_sm103a_only():
+    from paper_2506_22609_b300 import build
+
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_status_strings(L):
+    from paper_2506_22609_b300 import ludax
+
+    assert ludax.status_string(0) == "ok"
+    for code in range(-7, 0):
+        assert ludax.status_string(code) not in ("", "unknown status")
+    assert ludax.status_string(-99) == "unknown status"
+
+
+def test_env_create_rejects_bad_arguments_before_touching_the_device(L):
+    from paper_2506_22609_b300 import ludax
+
+    h = ctypes.c_void_p()
+    p = ludax.ludax_board_params(6, 7)
+    assert L.ludax_env_create(None, 1, ctypes.byref(p), 16, 0, None) == -1
+    assert L.ludax_env_create(ctypes.byref(h), 1, None, 16, 0, None) == -1
+    assert L.ludax_env_create(ctypes.byref(h), 9, ctypes.byref(p), 16, 0, None) == -2      # bad game
+    bad = ludax.ludax_board_params(7, 7)
+    assert L.ludax_env_create(ctypes.byref(h), 1, ctypes.byref(bad), 16, 0, None) == -3    # C4 is 6x7
+    hex12 = ludax.ludax_board_params(12, 12)
+    assert L.ludax_env_create(ctypes.byref(h), 3, ctypes.byref(hex12), 16, 0, None) == -3  # Hex <= 11
+    assert L.ludax_env_create(ctypes.byref(h), 1, ctypes.byref(p), 0, 0, None) == -1       # no envs
+    assert L.ludax_env_create(ctypes.byref(h), 1, ctypes.byref(p), 16, -1, None) == -1     # negative offset
+    assert not h.value
+
+
+def test_null_handles_are_rejected(L):
+    assert L.ludax_reset(None, None) == -1
+    assert L.ludax_step(None, None, None, None) == -1
+    assert L.ludax_rollout(None, 0, 0, None, None, None, None) == -1
+    assert L.ludax_sync(None, 0) == -1
+    assert L.ludax_env_destroy(None) == 0
+    assert L.ludax_mixed_plan_destroy(None) == 0
+    assert L.ludax_rollout_mixed(None, 10, 0, 0, None, None, None, None) == -1
+
+
+def test_autotune_candidates_are_valid(L):
+    from paper_2506_22609_b300 import ludax
+
+    cands = ludax.ludax_autotune_candidates()
+    assert len(cands) > 8
+    for c in cands:
+        assert 32 <= c.block_threads <= 512 and c.block_threads % 32 == 0
+        assert c.blocks_per_sm == 0 or c.block_threads * c.blocks_per_sm <= 2048
+        assert c.envs_per_thread == 1 and c.hex_nbr_table in (0, 1)
+
+
+def test_binding_refuses_host_tensors(L):
+    import torch
+
+    from paper_2506_22609_b300 import ludax
+
+    with pytest.raises(ValueError):
+        ludax._ptr(torch.zeros(4))

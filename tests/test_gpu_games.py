@@ -1,0 +1,320 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the CPU oracle,
+bit-exact on boards, ply counts, outcomes, rewards and legal masks.
+
+Sizes span several 256-thread tiles plus a ragged tail; the benchmark sizes
+are checked on sampled envs, which the oracle replays one by one from the
+same (seed, global env index).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import games as G
+from paper_2506_22609_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GAMES = [("ttt", G.TTT, 3, 3), ("c4", G.C4, 6, 7), ("othello", G.OTHELLO, 8, 8)] + [
+    (f"hex{n}", G.HEX, n, n) for n in (2, 3, 5, 7, 9, 11)]
+GAME_IDS = [g[0] for g in GAMES]
+
+
+@pytest.fixture(scope="module")
+def L(cuda_device):
+    from paper_2506_22609_b300 import build
+
+    build.build()
+    from paper_2506_22609_b300 import ludax
+
+    ludax.lib()
+    return ludax
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def gpu_state(env):
+    b, tm, ply, ps, oc = env.get_state()
+    torch.cuda.synchronize()
+    return np_(b), np_(tm), np_(ply), np_(ps), np_(oc)
+
+
+def assert_states_equal(env, s):
+    b, tm, ply, ps, oc = gpu_state(env)
+    assert (b == s.board).all()
+    assert (tm == s.to_move).all()
+    assert (ply == s.ply).all()
+    assert (ps == s.passes).all()
+    assert (oc == s.outcome).all()
+
+
+# ---------------------------------------------------------------- rollouts --
+@pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
+def test_rollout_from_start_matches_oracle(L, name, game, rows, cols):
+    n, seed, off = 2600, 7, 12345
+    env = L.Env(game, rows, cols, n, env_offset=off)
+    out, plies = env.rollout(seed, from_start=True, write_back=True)
+    o_out, o_plies, o_boards = G.rollout_start(game, rows, cols, n, seed, env_offset=off, want_boards=True)
+    assert (np_(out) == o_out).all()
+    assert (np_(plies) == o_plies).all()
+    b, tm, ply, ps, oc = gpu_state(env)
+    assert (b == o_boards).all()
+    assert (oc == o_out).all() and (ply == o_plies).all()
+    assert env.counters() == (0, 0)
+    assert set(np.unique(o_out)) <= {0, 1, 2}
+
+
+@pytest.mark.parametrize("cfg", [(256, 0, 1, 0), (128, 2, 1, 0), (64, 1, 2, 1), (512, 4, 2, 0), (96, 3, 1, 1)],
+                         ids=lambda c: "b{}_bps{}_ept{}_tab{}".format(*c))
+@pytest.mark.parametrize("name,game,rows,cols", [GAMES[1], GAMES[2], GAMES[7], GAMES[8]],
+                         ids=["c4", "othello", "hex9", "hex11"])
+def test_launch_shape_does_not_change_results(L, name, game, rows, cols, cfg):
+    # persistent grids smaller than the batch exercise the refill path
+    n, seed = 20000, 3
+    env = L.Env(game, rows, cols, n)
+    out, plies = env.rollout(seed, cfg=L.make_cfg(*cfg))
+    ref_out, ref_plies = env.rollout(seed)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref_out) and torch.equal(plies, ref_plies)
+    s = W.sample_envs(n, 400, 1)
+    for e in s[:50]:
+        o, p, _ = G.rollout_start(game, rows, cols, 1, seed, env_offset=int(e))
+        assert o[0] == np_(out)[e] and p[0] == np_(plies)[e]
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 257])
+def test_ragged_and_tiny_batches(L, n):
+    for name, game, rows, cols in (GAMES[0], GAMES[1], GAMES[2], GAMES[8]):
+        env = L.Env(game, rows, cols, n)
+        out, plies = env.rollout(11, cfg=L.make_cfg(64, 1, 2, 0))
+        o, p, _ = G.rollout_start(game, rows, cols, n, 11)
+        assert (np_(out) == o).all() and (np_(plies) == p).all()
+
+
+# ------------------------------------------------- benchmark-size configs --
+@pytest.mark.parametrize("cfg", [W.TTT_1K, W.C4_64K, W.OTHELLO_256K, W.HEX11_64K], ids=lambda c: c.name)
+def test_benchmark_configs_sampled(L, cfg):
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, cfg.num_envs)
+    out, plies = env.rollout(cfg.seed, cfg=L.make_cfg(*W.bench_cfg(cfg)))
+    out, plies = np_(out), np_(plies)
+    if cfg.num_envs <= 65536 and cfg.game in (G.TTT, G.C4):
+        o, p, _ = G.rollout_start(cfg.game, cfg.rows, cfg.cols, cfg.num_envs, cfg.seed)
+        assert (out == o).all() and (plies == p).all()
+    else:
+        for e in W.sample_envs(cfg.num_envs, 1500, 5):
+            o, p, _ = G.rollout_start(cfg.game, cfg.rows, cfg.cols, 1, cfg.seed, env_offset=int(e))
+            assert o[0] == out[e] and p[0] == plies[e], e
+    assert set(np.unique(out)) <= {0, 1, 2}
+    # properties that hold at any size: length bounds and the winner moved last
+    lo, hi = {G.TTT: (5, 9), G.C4: (7, 42), G.OTHELLO: (11, 128), G.HEX: (2 * cfg.rows - 1, cfg.rows ** 2)}[cfg.game]
+    assert plies.min() >= lo and plies.max() <= hi
+    if cfg.game in (G.TTT, G.C4, G.HEX):
+        won = out != 0
+        assert ((plies[won] % 2 == 1) == (out[won] == 1)).all()
+    if cfg.game == G.HEX:
+        assert (out != 0).all()
+
+
+# ------------------------------------------------------ step-per-launch --
+@pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
+def test_random_step_reproduces_rollout(L, name, game, rows, cols):
+    n, seed = 1500, 21
+    env = L.Env(game, rows, cols, n, env_offset=99)
+    ref = L.Env(game, rows, cols, n, env_offset=99)
+    r_out, r_plies = ref.rollout(seed, write_back=True)
+    done = torch.zeros(n, dtype=torch.bool, device="cuda")
+    cap = {G.TTT: 9, G.C4: 42, G.OTHELLO: 128, G.HEX: rows * cols}[game]
+    final_rew = torch.zeros(n, 2, device="cuda")
+    for _ in range(cap + 2):
+        rew, term = env.random_step(seed)
+        newly = term.bool() & ~done
+        final_rew[newly] = rew[newly]
+        assert (rew[~newly] == 0).all()
+        done |= term.bool()
+        if bool(done.all()):
+            break
+    assert bool(done.all())
+    b1 = gpu_state(env)
+    b2 = gpu_state(ref)
+    for x, y in zip(b1, b2):
+        assert (x == y).all()
+    want = np.zeros((n, 2), np.float32)
+    ro = np_(r_out)
+    want[ro == 1] = (1, -1)
+    want[ro == 2] = (-1, 1)
+    assert (np_(final_rew) == want).all()
+
+
+def _canon_legal(mask_words, A, cells):
+    bits = np.zeros((mask_words.shape[0], A), np.uint8)
+    w = mask_words.view(np.uint64)
+    for c in range(cells):
+        bits[:, c] = (w[:, c // 64] >> np.uint64(c % 64)) & np.uint64(1)
+    return bits
+
+
+@pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
+def test_step_api_matches_oracle(L, name, game, rows, cols):
+    # Oracle-chosen trajectories, 10% of steps with an arbitrary (often
+    # illegal) action: legal masks, rewards, terminated flags and full state
+    # must agree after every step.
+    n = 700
+    rng = np.random.default_rng(game * 100 + rows)
+    env = L.Env(game, rows, cols, n)
+    s = G.reset(game, rows, cols, n)
+    A, cells = G.num_actions(game, rows, cols), rows * cols
+    assert env.num_actions == A
+    n_illegal = 0
+    for _ in range(cells * 2 + 4):
+        legal = G.legal(s)
+        m, p = env.legal_mask()
+        torch.cuda.synchronize()
+        got = _canon_legal(np_(m), A, cells)
+        if game == G.OTHELLO:
+            got[:, cells] = np_(p)
+        else:
+            assert not np_(p).any()
+        assert (got == legal).all()
+        acts = np.zeros(n, np.int32)
+        for e in range(n):
+            cand = np.flatnonzero(legal[e])
+            if cand.size == 0 or rng.random() < 0.1:
+                acts[e] = rng.integers(-2, A + 2)
+            else:
+                acts[e] = rng.choice(cand)
+        o_rew, o_term, o_err = G.step(s, acts)
+        n_illegal += int(o_err.sum())
+        rew, term = env.step(torch.from_numpy(acts).cuda())
+        torch.cuda.synchronize()
+        assert (np_(rew) == o_rew).all()
+        assert (np_(term) == o_term).all()
+        assert_states_equal(env, s)
+        if o_term.all():
+            break
+    assert s.outcome.min() >= 0
+    assert env.counters()[0] == n_illegal and n_illegal > 0
+
+
+def test_reset_mask_and_finished_env_noop(L):
+    env = L.Env("c4", 6, 7, 64)
+    env.rollout(5, write_back=True)
+    mask = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    mask[::2] = 1
+    env.reset(mask)
+    b, tm, ply, ps, oc = gpu_state(env)
+    assert (b[::2] == 0).all() and (ply[::2] == 0).all() and (oc[::2] == -1).all()
+    assert (oc[1::2] >= 0).all()
+    before = gpu_state(env)
+    rew, term = env.step(torch.zeros(64, dtype=torch.int32, device="cuda") + 38)
+    after = gpu_state(env)
+    for x, y in zip(before, after):
+        assert (x[1::2] == y[1::2]).all()
+    assert (np_(rew)[1::2] == 0).all() and np_(term)[1::2].all()
+
+
+# --------------------------------------------------- positions and values --
+@pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
+def test_set_state_rollout_from_positions(L, name, game, rows, cols):
+    n = 1200
+    rng = np.random.default_rng(rows + 17 * game)
+    s = G.reset(game, rows, cols, n)
+    stop = rng.integers(0, rows * cols, n).astype(np.int16)
+    G.rollout_from(s, seed=5, stop_ply=stop)
+    env = L.Env(game, rows, cols, n, env_offset=7)
+    env.set_state(*(torch.from_numpy(x) for x in (s.board, s.to_move, s.ply, s.passes, s.outcome)))
+    assert_states_equal(env, s)
+    # partial playouts to a stop ply, then to the end, from the stored state
+    s2 = s.copy()
+    stop2 = (s.ply + rng.integers(0, 6, n)).astype(np.int16)
+    G.rollout_from(s2, seed=9, env_offset=7, stop_ply=stop2)
+    out, plies = env.rollout(9, from_start=False, write_back=True, stop_ply=torch.from_numpy(stop2).cuda())
+    assert_states_equal(env, s2)
+    assert (np_(out) == s2.outcome).all() and (np_(plies) == s2.ply).all()
+    G.rollout_from(s2, seed=10, env_offset=7)
+    out, plies = env.rollout(10, from_start=False, write_back=True)
+    assert_states_equal(env, s2)
+
+
+@pytest.mark.parametrize("name,game,rows,cols", [GAMES[1], GAMES[2], GAMES[8]], ids=["c4", "othello", "hex11"])
+def test_rollout_value_matches_oracle(L, name, game, rows, cols):
+    n, R, seed = 300, 16, 1000
+    s = G.reset(game, rows, cols, n)
+    G.rollout_from(s, seed=3, stop_ply=np.full(n, 10, np.int16))
+    env = L.Env(game, rows, cols, n, env_offset=50)
+    env.set_state(*(torch.from_numpy(x) for x in (s.board, s.to_move, s.ply, s.passes, s.outcome)))
+    v = np_(env.rollout_value(seed, R))
+    acc = np.zeros(n)
+    for j in range(R):
+        t = s.copy()
+        G.rollout_from(t, seed=seed + j, env_offset=50)
+        acc += np.where(t.outcome == 1, 1.0, np.where(t.outcome == 2, 0.0, 0.5))
+    assert (v == (acc / R).astype(np.float32)).all()
+    assert_states_equal(env, s)  # the stored state is untouched
+
+
+# ------------------------------------------------------------ mixed batch --
+@pytest.mark.parametrize("layout", ["block", "interleave", "random"])
+def test_mixed_batch_matches_oracle(L, layout):
+    n, seed, off = 6000, 3, 777
+    d = W.random_descriptors(n, 4) if layout == "random" else W.mixed_descriptors(n, layout)
+    o_out, o_plies = G.rollout_mixed(d, seed, env_offset=off)
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies = torch.empty(n, dtype=torch.int16, device="cuda")
+    L.ludax_rollout_mixed(dd, off, seed, out, plies)
+    torch.cuda.synchronize()
+    assert (np_(out) == o_out).all() and (np_(plies) == o_plies).all()
+    for cfg in [(128, 2, 1, 1), (64, 1, 1, 0), (512, 0, 1, 1)]:
+        plan = L.ludax_mixed_plan_create(dd, off, L.make_cfg(*cfg))
+        for s2 in (seed, seed + 1):
+            out2 = torch.full((n,), 99, dtype=torch.int8, device="cuda")
+            plies2 = torch.zeros(n, dtype=torch.int16, device="cuda")
+            L.ludax_mixed_plan_launch(plan, s2, out2, plies2)
+            torch.cuda.synchronize()
+            if s2 == seed:
+                assert torch.equal(out2, out) and torch.equal(plies2, plies)
+            else:
+                o2, p2 = G.rollout_mixed(d, s2, env_offset=off)
+                assert (np_(out2) == o2).all() and (np_(plies2) == p2).all()
+        L.ludax_mixed_plan_destroy(plan)
+
+
+def test_mixed_full_config_sampled(L):
+    d = W.mixed_descriptors(W.MIXED_ENVS, "block")
+    dd = torch.from_numpy(d).cuda()
+    plan = L.ludax_mixed_plan_create(dd, 0, L.make_cfg(*W.mixed_bench_cfg()))
+    out = torch.empty(W.MIXED_ENVS, dtype=torch.int8, device="cuda")
+    plies = torch.empty(W.MIXED_ENVS, dtype=torch.int16, device="cuda")
+    L.ludax_mixed_plan_launch(plan, W.MIXED_SEED, out, plies)
+    torch.cuda.synchronize()
+    out, plies = np_(out), np_(plies)
+    for e in W.sample_envs(W.MIXED_ENVS, 1200, 9):
+        o, p = G.rollout_mixed(d[e:e + 1], W.MIXED_SEED, env_offset=int(e))
+        assert o[0] == out[e] and p[0] == plies[e], e
+    assert set(np.unique(out)) <= {0, 1, 2}
+    L.ludax_mixed_plan_destroy(plan)
+
+
+def test_mixed_rejects_bad_descriptors(L):
+    d = W.mixed_descriptors(100, "block")
+    d[37] = W.desc(3, 12, 12)
+    with pytest.raises(L.LudaxError) as ei:
+        L.ludax_mixed_plan_create(torch.from_numpy(d).cuda())
+    assert ei.value.status == -3 and ei.value.bad_index == 37
+    d[37] = 7
+    with pytest.raises(L.LudaxError) as ei:
+        L.ludax_mixed_plan_create(torch.from_numpy(d).cuda())
+    assert ei.value.status == -2
+
+
+def test_sync_deadline_returns_timeout_status(L):
+    env = L.Env("othello", 8, 8, 262144)
+    saw_timeout = False
+    for _ in range(3):
+        env.rollout(1)
+        st = L.lib().ludax_sync(env.handle, 0)
+        assert st in (0, -5)
+        saw_timeout |= st == -5
+        env.sync(60000)
+    assert saw_timeout
