@@ -119,7 +119,7 @@ class ClockSampler:
 
     def record(self):
         if not self.nv:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "NVML unavailable"}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "note": "NVML unavailable: " + self.err}
         return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
                 "reasons": sorted(self.reasons), "samples": len(self.samples)}
 
@@ -316,8 +316,8 @@ def main():
         else:
             ms, steps_per_launch = bench_mixed(L, W, args.steps, args.warmup, flush_buf, rank)
             wl_name, n_envs, seed = "mixed6_1048576env_seed3_graph", W.MIXED_ENVS, W.MIXED_SEED
-            launch = dict(zip(("block_threads", "blocks_per_sm", "envs_per_thread", "hex_nbr_table"),
-                              W.mixed_bench_cfg()))
+            launch = dict(zip(("block_threads", "blocks_per_sm", "envs_per_thread", "hex_nbr_table",
+                               "compact_every"), W.mixed_bench_cfg()))
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()

@@ -280,6 +280,112 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
     }
 }
 
+// Persistent playouts with block-level compaction.  Each round every live env
+// plays up to R plies in registers; then the block packs its unfinished envs
+// (kWords+2 words each) into shared memory at consecutive slots, so live envs
+// occupy the lowest warps and warps with no live env skip the next round's
+// plies (they only meet the barriers).  Freed slots take new envs from the
+// queue.  Results are independent of the packing: every draw is keyed by
+// (seed, global env, ply).
+template <class G>
+__device__ __forceinline__ void slot_store(uint64_t* buf, int stride, int pos, const G& g, uint64_t key,
+                                           long long env, int stop) {
+    uint64_t w[G::kWords];
+    g.save(w);
+#pragma unroll
+    for (int i = 0; i < G::kWords; ++i) buf[i * stride + pos] = w[i];
+    buf[G::kWords * stride + pos] = key;
+    buf[(G::kWords + 1) * stride + pos] = (uint64_t)(uint32_t)env | ((uint64_t)(uint32_t)stop << 32);
+}
+template <class G>
+__device__ __forceinline__ void slot_load(const uint64_t* buf, int stride, int pos, G& g, uint64_t& key,
+                                          long long& env, int& stop) {
+    uint64_t w[G::kWords];
+#pragma unroll
+    for (int i = 0; i < G::kWords; ++i) w[i] = buf[i * stride + pos];
+    g.load(w);
+    key = buf[G::kWords * stride + pos];
+    uint64_t x = buf[(G::kWords + 1) * stride + pos];
+    env = (long long)(uint32_t)x;
+    stop = (int)(x >> 32);
+}
+
+template <class G, bool TABLE>
+__global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int R) {
+    extern __shared__ __align__(16) uint64_t smem64[];
+    const int B = blockDim.x;
+    uint64_t* buf = smem64;                                        // [kWords+2][B]
+    int* warp_cnt = reinterpret_cast<int*>(smem64 + (G::kWords + 2) * B);  // [16] + exhausted flag
+    const B128* table = nullptr;
+    if constexpr (TABLE && HexN<G>::value != 0) {
+        B128* t = reinterpret_cast<B128*>(warp_cnt + 32);
+        hex_fill_table<HexN<G>::value>(t);
+        table = t;
+    }
+    if (threadIdx.x == 0) warp_cnt[16] = 0;
+    __syncthreads();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
+    const long long n = a.d.n;
+    const long long slots = (long long)gridDim.x * B;
+    const bool refill = slots < n;
+    G g;
+    set_table(g, table);
+    uint64_t key = 0;
+    long long env = (long long)blockIdx.x * B + tid;
+    int stop = 0;
+    bool active = env < n;
+    auto init = [&]() {
+        if (a.from_start) g.reset();
+        else load_state(g, a.d, env);
+        key = env_key(a.seed_key, (uint64_t)(a.d.env_offset + env));
+        stop = a.stop ? (int)a.stop[env] : 0x7FFF;
+    };
+    if (active) init();
+    for (;;) {
+        if (active) {
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+                if (g.outcome != kOngoing || g.ply >= stop) break;
+                random_ply(g, key);
+            }
+            if (g.outcome != kOngoing || g.ply >= stop) {
+                if (a.outcome) a.outcome[env] = (int8_t)g.outcome;
+                if (a.plies) a.plies[env] = (int16_t)g.ply;
+                if (a.write_back) store_state(g, a.d, env);
+                if (g.outcome == kCapped) atomicAdd(&a.d.counters[2], 1ull);
+                active = false;
+            }
+        }
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, active);
+        if (lane == 0) warp_cnt[warp] = __popc(ball);
+        __syncthreads();
+        int prefix = 0, total = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            int c = warp_cnt[w];
+            prefix += w < warp ? c : 0;
+            total += c;
+        }
+        if (active) slot_store(buf, B, prefix + __popc(ball & ((1u << lane) - 1u)), g, key, env, stop);
+        __syncthreads();
+        if (tid < total) {
+            slot_load(buf, B, tid, g, key, env, stop);
+            active = true;
+        } else {
+            active = false;
+            if (refill && !warp_cnt[16]) {
+                env = slots + claim_next(&a.d.counters[0]);
+                if (env < n) {
+                    init();
+                    active = true;
+                } else {
+                    warp_cnt[16] = 1;  // queue exhausted: stop claiming
+                }
+            }
+        }
+        if (!__syncthreads_or(active)) break;
+    }
+}
+
 // R playouts per env from its stored state; playout j draws with seed + j.
 template <class G, bool TABLE>
 __global__ void __launch_bounds__(512) rollout_value_kernel(EnvDev d, uint64_t seed, int R, float* value) {
@@ -325,8 +431,25 @@ int launch_rollout(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg&
     }
     const bool table = cfg.hex_nbr_table != 0 && HexN<G>::value != 0;
     size_t smem = table ? sizeof(B128) * G::kCells : 0;
-    if (cudaMemsetAsync(env->d_counters, 0, sizeof(unsigned long long), env->stream) != cudaSuccess)
+    // the refill cursor is only read when the grid holds fewer slots than envs
+    if (grid * block * ept < env->n &&
+        cudaMemsetAsync(env->d_counters, 0, sizeof(unsigned long long), env->stream) != cudaSuccess)
         return LUDAX_ERR_CUDA;
+    if (cfg.compact_every > 0) {
+        size_t cs = sizeof(uint64_t) * (G::kWords + 2) * block + 32 * sizeof(int) + smem;
+        if (table) {
+            auto k = rollout_compact_kernel<G, true>;
+            if (cs > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs) != cudaSuccess)
+                return LUDAX_ERR_CUDA;
+            k<<<(unsigned)grid, block, cs, env->stream>>>(a, cfg.compact_every);
+        } else {
+            auto k = rollout_compact_kernel<G, false>;
+            if (cs > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs) != cudaSuccess)
+                return LUDAX_ERR_CUDA;
+            k<<<(unsigned)grid, block, cs, env->stream>>>(a, cfg.compact_every);
+        }
+        return launch_status();
+    }
     if (ept == 2) {
         if (table) rollout_kernel<G, 2, true><<<(unsigned)grid, block, smem, env->stream>>>(a);
         else rollout_kernel<G, 2, false><<<(unsigned)grid, block, 0, env->stream>>>(a);
@@ -337,13 +460,15 @@ int launch_rollout(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg&
     return launch_status();
 }
 
-ludax_launch_cfg default_cfg() { return ludax_launch_cfg{256, 0, 1, 0}; }
+ludax_launch_cfg default_cfg() { return ludax_launch_cfg{256, 0, 1, 0, 0}; }
 
 int check_cfg(const ludax_launch_cfg& c) {
     if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32) return LUDAX_ERR_ARG;
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return LUDAX_ERR_ARG;
     if (c.envs_per_thread != 1 && c.envs_per_thread != 2) return LUDAX_ERR_ARG;
     if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
+    if (c.compact_every < 0 || c.compact_every > 256) return LUDAX_ERR_ARG;
+    if (c.compact_every > 0 && c.envs_per_thread != 1) return LUDAX_ERR_ARG;
     return LUDAX_OK;
 }
 
@@ -591,13 +716,16 @@ int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch
     cudaEventCreate(&e1);
     int st = LUDAX_OK, k = 0;
     float best = 1e30f;
+    static const int compacts[] = {0, 4, 8, 16};
     for (int t = 0; t < tables && st == LUDAX_OK; ++t)
+        for (int ce : compacts)
         for (int ept = 1; ept <= 2 && st == LUDAX_OK; ++ept)
             for (int b : blocks)
                 for (int s : bps) {
                     if (st != LUDAX_OK) break;
                     if (s > 0 && b * s > 2048) continue;
-                    ludax_launch_cfg c{b, s, ept, t};
+                    if (ce > 0 && ept != 1) continue;
+                    ludax_launch_cfg c{b, s, ept, t, ce};
                     float ts[64];
                     int nt = 0;
                     for (int r = 0; r < reps + 2 && st == LUDAX_OK; ++r) {

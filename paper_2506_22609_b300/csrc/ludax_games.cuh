@@ -114,6 +114,18 @@ __device__ __forceinline__ int select_bit(B128 m, uint32_t k) {
     return k < c ? select_bit(m.lo, k) : 64 + select_bit(m.hi, k - c);
 }
 
+// per-env scalars packed into one word for the shared-memory slot of an env
+__device__ __forceinline__ uint64_t pack_small(int ply, int passes, int side, int outcome) {
+    return (uint64_t)(ply & 0xFFFF) | ((uint64_t)(passes & 0xFF) << 16) | ((uint64_t)(side & 1) << 24) |
+           ((uint64_t)(outcome + 1) << 32);
+}
+__device__ __forceinline__ void unpack_small(uint64_t w, int& ply, int& passes, int& side, int& outcome) {
+    ply = (int)(w & 0xFFFF);
+    passes = (int)((w >> 16) & 0xFF);
+    side = (int)((w >> 24) & 1);
+    outcome = (int)(w >> 32) - 1;
+}
+
 // ----------------------------------------------------------- Tic-Tac-Toe --
 struct TTT {
     static constexpr int kGame = 0, kRows = 3, kCols = 3, kCells = 9, kCap = 9, kPlanes = 2;
@@ -145,6 +157,17 @@ struct TTT {
     __device__ __forceinline__ static int canon_of(int b) { return b; }
     __device__ __forceinline__ static int bit_of(int cell) { return cell; }
     __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) { return w == 0 ? (uint64_t)m : 0ull; }
+    // register state as kWords 64-bit words (shared-memory slots)
+    static constexpr int kWords = 2;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = (uint64_t)own | ((uint64_t)opp << 32);
+        w[1] = pack_small(ply, passes, side, outcome);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        own = (uint32_t)w[0];
+        opp = (uint32_t)(w[0] >> 32);
+        unpack_small(w[1], ply, passes, side, outcome);
+    }
 };
 
 // ---------------------------------------------------------- Connect Four --
@@ -187,6 +210,17 @@ struct C4 {
 #pragma unroll
         for (int r = 0; r < 6; ++r) out |= ((m >> (8 * r)) & 0x7Full) << (7 * r);
         return out;
+    }
+    static constexpr int kWords = 3;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = own;
+        w[1] = opp;
+        w[2] = pack_small(ply, passes, side, outcome);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        own = w[0];
+        opp = w[1];
+        unpack_small(w[2], ply, passes, side, outcome);
     }
 };
 
@@ -266,6 +300,17 @@ struct Othello {
     __device__ __forceinline__ static int canon_of(int b) { return b; }
     __device__ __forceinline__ static int bit_of(int cell) { return cell; }
     __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) { return w == 0 ? m : 0ull; }
+    static constexpr int kWords = 3;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = own;
+        w[1] = opp;
+        w[2] = pack_small(ply, passes, side, outcome);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        own = w[0];
+        opp = w[1];
+        unpack_small(w[2], ply, passes, side, outcome);
+    }
 };
 
 // ------------------------------------------------------------------- Hex --
@@ -362,6 +407,19 @@ struct Hex {
     __device__ __forceinline__ static int canon_of(int b) { return b; }
     __device__ __forceinline__ static int bit_of(int cell) { return cell; }
     __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) { return w == 0 ? m.lo : m.hi; }
+    static constexpr int kWords = 13;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = own.lo; w[1] = own.hi; w[2] = opp.lo; w[3] = opp.hi;
+        w[4] = ownA.lo; w[5] = ownA.hi; w[6] = ownB.lo; w[7] = ownB.hi;
+        w[8] = oppA.lo; w[9] = oppA.hi; w[10] = oppB.lo; w[11] = oppB.hi;
+        w[12] = pack_small(ply, passes, side, outcome);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        own = {w[0], w[1]}; opp = {w[2], w[3]};
+        ownA = {w[4], w[5]}; ownB = {w[6], w[7]};
+        oppA = {w[8], w[9]}; oppB = {w[10], w[11]};
+        unpack_small(w[12], ply, passes, side, outcome);
+    }
 };
 
 // Fill a shared-memory table of per-cell neighbour masks for Hex<N>

@@ -47,7 +47,8 @@ class ludax_state_view(ctypes.Structure):
 
 class ludax_launch_cfg(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("envs_per_thread", ctypes.c_int32), ("hex_nbr_table", ctypes.c_int32)]
+                ("envs_per_thread", ctypes.c_int32), ("hex_nbr_table", ctypes.c_int32),
+                ("compact_every", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -56,8 +57,8 @@ class ludax_launch_cfg(ctypes.Structure):
         return f"ludax_launch_cfg({self.as_dict()})"
 
 
-def make_cfg(block_threads=256, blocks_per_sm=0, envs_per_thread=1, hex_nbr_table=0) -> ludax_launch_cfg:
-    return ludax_launch_cfg(block_threads, blocks_per_sm, envs_per_thread, hex_nbr_table)
+def make_cfg(block_threads=256, blocks_per_sm=0, envs_per_thread=1, hex_nbr_table=0, compact_every=0):
+    return ludax_launch_cfg(block_threads, blocks_per_sm, envs_per_thread, hex_nbr_table, compact_every)
 
 
 _lib = None

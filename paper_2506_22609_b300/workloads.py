@@ -70,18 +70,19 @@ def sample_envs(n_total: int, k: int, seed: int) -> np.ndarray:
 
 
 # Launch shapes the benchmark times (block_threads, blocks_per_sm,
-# envs_per_thread, hex_nbr_table); chosen with the autotuner on a B300.
+# envs_per_thread, hex_nbr_table, compact_every): the fastest candidates of
+# ludax_autotune_env / ludax_autotune on a B300.
 BENCH_CFGS = {
-    TTT_1K.name: (128, 0, 1, 0),
-    C4_64K.name: (128, 0, 1, 0),
-    OTHELLO_256K.name: (256, 0, 1, 0),
-    HEX11_64K.name: (128, 0, 1, 0),
+    TTT_1K.name: (64, 0, 1, 0, 16),
+    C4_64K.name: (256, 4, 1, 0, 16),
+    OTHELLO_256K.name: (256, 0, 1, 0, 0),
+    HEX11_64K.name: (512, 4, 1, 1, 16),
 }
-MIXED_BENCH_CFG = (256, 0, 1, 0)
+MIXED_BENCH_CFG = (128, 0, 1, 1, 0)
 
 
 def bench_cfg(cfg: Config) -> tuple:
-    return BENCH_CFGS.get(cfg.name, (256, 0, 1, 0))
+    return BENCH_CFGS.get(cfg.name, (256, 0, 1, 0, 0))
 
 
 def mixed_bench_cfg() -> tuple:

@@ -65,8 +65,10 @@ def test_rollout_from_start_matches_oracle(L, name, game, rows, cols):
     assert set(np.unique(o_out)) <= {0, 1, 2}
 
 
-@pytest.mark.parametrize("cfg", [(256, 0, 1, 0), (128, 2, 1, 0), (64, 1, 2, 1), (512, 4, 2, 0), (96, 3, 1, 1)],
-                         ids=lambda c: "b{}_bps{}_ept{}_tab{}".format(*c))
+@pytest.mark.parametrize("cfg", [(256, 0, 1, 0, 0), (128, 2, 1, 0, 0), (64, 1, 2, 1, 0), (512, 4, 2, 0, 0),
+                                 (96, 3, 1, 1, 0), (256, 0, 1, 0, 4), (128, 2, 1, 1, 8), (448, 1, 1, 0, 16),
+                                 (64, 1, 1, 0, 1)],
+                         ids=lambda c: "b{}_bps{}_ept{}_tab{}_cmp{}".format(*c))
 @pytest.mark.parametrize("name,game,rows,cols", [GAMES[1], GAMES[2], GAMES[7], GAMES[8]],
                          ids=["c4", "othello", "hex9", "hex11"])
 def test_launch_shape_does_not_change_results(L, name, game, rows, cols, cfg):
@@ -87,9 +89,10 @@ def test_launch_shape_does_not_change_results(L, name, game, rows, cols, cfg):
 def test_ragged_and_tiny_batches(L, n):
     for name, game, rows, cols in (GAMES[0], GAMES[1], GAMES[2], GAMES[8]):
         env = L.Env(game, rows, cols, n)
-        out, plies = env.rollout(11, cfg=L.make_cfg(64, 1, 2, 0))
         o, p, _ = G.rollout_start(game, rows, cols, n, 11)
-        assert (np_(out) == o).all() and (np_(plies) == p).all()
+        for cfg in [(64, 1, 2, 0, 0), (64, 1, 1, 0, 4), (32, 1, 1, 1, 2)]:
+            out, plies = env.rollout(11, cfg=L.make_cfg(*cfg))
+            assert (np_(out) == o).all() and (np_(plies) == p).all()
 
 
 # ------------------------------------------------- benchmark-size configs --
@@ -265,7 +268,8 @@ def test_mixed_batch_matches_oracle(L, layout):
     L.ludax_rollout_mixed(dd, off, seed, out, plies)
     torch.cuda.synchronize()
     assert (np_(out) == o_out).all() and (np_(plies) == o_plies).all()
-    for cfg in [(128, 2, 1, 1), (64, 1, 1, 0), (512, 0, 1, 1)]:
+    for cfg in [(128, 2, 1, 1, 0), (64, 1, 1, 0, 0), (512, 0, 1, 1, 0), (256, 2, 1, 0, 8), (128, 1, 1, 1, 16),
+                (64, 3, 1, 0, 1)]:
         plan = L.ludax_mixed_plan_create(dd, off, L.make_cfg(*cfg))
         for s2 in (seed, seed + 1):
             out2 = torch.full((n,), 99, dtype=torch.int8, device="cuda")
