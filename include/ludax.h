@@ -256,6 +256,54 @@ int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out);
 int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
                        float* ms_table_out, int32_t* n_candidates_out);
 
+/* ---------------------------------------------------------------------------
+ * Value network that truncates playouts (the learned part built on the
+ * engine; the paper's own agents, Sec. 7, are AlphaZero ResNets, which this
+ * library does not provide).
+ *
+ * Input row of a position: bf16 1.0 at column c for each P1 stone on cell c,
+ * at column cells + c for each P2 stone, at column 2*cells when P1 is to
+ * move; zero up to in_pad = round_up(2*cells + 1, 128) columns.  Layers:
+ * in_pad -> 512 ReLU -> 512 ReLU -> 1, v = tanh(z), predicted probability that
+ * P1 wins p = (v + 1) / 2.  BF16 weights and activations, FP32 accumulation;
+ * FP32 master weights and Adam (beta1 0.9, beta2 0.999, eps 1e-8).  Loss:
+ * mean over the batch of (p - y)^2.
+ *
+ * Parameters are one flat FP32 vector in the order
+ *   W1 [512][in_pad], b1 [512], W2 [512][512], b2 [512], w3 [512], b3 [1].
+ * Batches B must be multiples of 128 and at most max_batch.  All pointers are
+ * device memory; the net works on its own stream.                           */
+typedef struct ludax_net ludax_net;
+
+int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* stream);
+int ludax_net_destroy(ludax_net* net);
+int ludax_net_sizes(const ludax_net* net, int32_t* in_pad, int32_t* hidden, int64_t* num_params);
+/* set_params copies params_dev (float [num_params]) and resets Adam's moments
+ * and step count; get_params copies the FP32 masters out. */
+int ludax_net_set_params(ludax_net* net, const float* params_dev);
+int ludax_net_get_params(ludax_net* net, float* params_dev);
+/* p_dev float [B]: predicted P(P1 wins) for the input rows x_dev (bf16 bits,
+ * uint16 [B][in_pad], 16-byte aligned). */
+int ludax_net_forward(ludax_net* net, const uint16_t* x_dev, int64_t B, float* p_dev);
+/* Gradient of the loss against labels y_dev (float [B]) into grad_dev (float
+ * [num_params], nullable) and the loss into loss_dev (float [1], nullable);
+ * the parameters are not changed. */
+int ludax_net_grad(ludax_net* net, const uint16_t* x_dev, const float* y_dev, int64_t B, float* grad_dev,
+                   float* loss_dev);
+/* One Adam step with learning rate lr on the batch; loss_dev as above. */
+int ludax_net_train_step(ludax_net* net, const uint16_t* x_dev, const float* y_dev, int64_t B, float lr,
+                         float* loss_dev);
+/* The net input row of every env's current position into x_dev (uint16
+ * [num_envs][ld], ld >= 2*cells+1, ld % 8 == 0, 16-byte aligned). */
+int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld);
+/* Truncated value estimate of every env's current position: K continuations
+ * of up to `plies` uniform-random plies (continuation j draws as playout j of
+ * ludax_rollout_value with this seed); a continuation that ends the game
+ * counts its result (win 1, draw 0.5, loss 0 for P1), otherwise the net's p
+ * at the leaf.  value_dev float [num_envs] = mean over the K continuations.
+ * The env and the net must share a stream and the env's board size. */
+int ludax_truncated_value(ludax_env* env, ludax_net* net, uint64_t seed, int32_t K, int32_t plies, float* value_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,52 @@
+// ludax_internal.cuh -- host-side definitions shared by the library's
+// translation units (the env handle and the game dispatcher).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/ludax.h"
+#include "ludax_state.cuh"
+
+struct ludax_env {
+    int32_t game, rows, cols, cells, num_actions, mask_words, planes;
+    int64_t n, env_offset;
+    cudaStream_t stream;
+    int device, num_sms;
+    uint64_t* d_planes;
+    uint32_t* d_meta;
+    unsigned long long* d_counters;  // [0] refill cursor, [1] illegal, [2] capped, [3] spare
+};
+
+namespace ludax {
+
+template <class G>
+struct Tag {
+    using type = G;
+};
+
+// Calls f(Tag<G>{}) for the game type of (game, n); LUDAX_ERR_* if unknown.
+template <class F>
+int dispatch_game(int game, int rows, int cols, F&& f) {
+    switch (game) {
+    case LUDAX_GAME_TTT: return (rows == 3 && cols == 3) ? f(Tag<TTT>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_C4: return (rows == 6 && cols == 7) ? f(Tag<C4>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_OTHELLO: return (rows == 8 && cols == 8) ? f(Tag<Othello>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_HEX:
+        if (rows != cols) return LUDAX_ERR_SIZE;
+        switch (rows) {
+        case 2: return f(Tag<Hex<2>>{});
+        case 3: return f(Tag<Hex<3>>{});
+        case 4: return f(Tag<Hex<4>>{});
+        case 5: return f(Tag<Hex<5>>{});
+        case 6: return f(Tag<Hex<6>>{});
+        case 7: return f(Tag<Hex<7>>{});
+        case 8: return f(Tag<Hex<8>>{});
+        case 9: return f(Tag<Hex<9>>{});
+        case 10: return f(Tag<Hex<10>>{});
+        case 11: return f(Tag<Hex<11>>{});
+        default: return LUDAX_ERR_SIZE;
+        }
+    default: return LUDAX_ERR_GAME;
+    }
+}
+
+}  // namespace ludax

@@ -1,0 +1,662 @@
+// ludax_net.cu -- the value network that truncates playouts: BF16 MLP
+// (inputs [P1 plane, P2 plane, side to move] -> 512 ReLU -> 512 ReLU -> tanh),
+// FP32 accumulation, hand-written forward, backward and Adam kernels, input
+// packing from env state, and the truncated value estimator (a few random
+// plies, then the net).
+//
+// Precision: weights live as FP32 masters with BF16 copies used by every
+// GEMM; activations H1, H2 and the hidden-layer gradients dZ2, dZ1 are stored
+// in BF16; every product accumulates in FP32; the output layer, loss,
+// gradient reductions and Adam run in FP32.
+//
+// GEMMs run on the tensor cores: one templated kernel computes
+// C[m][n] = sum_k A(m,k) B(n,k) over 128x128 tiles with BK = 32, three
+// cp.async stages, ldmatrix (transposing where an operand is stored
+// M- or N-major) and mma.m16n8k16 BF16 -> FP32, with a fused epilogue.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "ludax_internal.cuh"
+
+using namespace ludax;
+
+namespace {
+
+constexpr int kH = 512;  // hidden width
+constexpr int BM = 128, BN = 128, BKT = 32, STAGES = 3, GEMM_THREADS = 256;
+constexpr int KMAJ_LD = BKT + 8;   // smem row length of a K-major tile (halves)
+constexpr int MMAJ_LD = BM + 8;    // smem row length of an M/N-major tile (halves)
+constexpr int TILE_HALVES = (BM * KMAJ_LD > BKT * MMAJ_LD) ? BM * KMAJ_LD : BKT * MMAJ_LD;
+constexpr size_t GEMM_SMEM = sizeof(__nv_bfloat16) * TILE_HALVES * 2 * STAGES;
+
+enum { EPI_BIAS_RELU = 0, EPI_MASK = 1, EPI_PARTIAL = 2 };
+
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    const __nv_bfloat16* B;
+    int M, N, K, lda, ldb, k_per_split;
+    const float* bias;          // EPI_BIAS_RELU: [N]
+    const __nv_bfloat16* mask;  // EPI_MASK: [M][ldo], multiply by (mask > 0)
+    __nv_bfloat16* out;         // EPI_BIAS_RELU / EPI_MASK: [M][ldo]
+    int ldo;
+    float* partial;             // EPI_PARTIAL: [splits][M][N]
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Copy one BK-deep stage of an operand tile into shared memory.
+//   KMAJOR: global X[row][k] (row = m or n), tile sm[row][k] with row length KMAJ_LD
+//   else  : global X[k][row],               tile sm[k][row] with row length MMAJ_LD
+template <bool KMAJOR>
+__device__ __forceinline__ void load_tile(__nv_bfloat16* sm, const __nv_bfloat16* g, int ld, int row0, int k0) {
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        int c = t + i * GEMM_THREADS;  // 512 chunks of 8 halves
+        if (KMAJOR) {
+            int r = c >> 2, kc = (c & 3) * 8;
+            cp_async16(sm + r * KMAJ_LD + kc, g + (size_t)(row0 + r) * ld + k0 + kc);
+        } else {
+            int r = c >> 4, mc = (c & 15) * 8;
+            cp_async16(sm + r * MMAJ_LD + mc, g + (size_t)(k0 + r) * ld + row0 + mc);
+        }
+    }
+}
+
+template <bool AK, bool BK_, int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS) gemm_bf16_kernel(GemmArgs g) {
+    extern __shared__ __align__(16) __nv_bfloat16 gsm[];
+    __nv_bfloat16* sA = gsm;
+    __nv_bfloat16* sB = gsm + TILE_HALVES * STAGES;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * g.k_per_split;
+    const int ktiles = g.k_per_split / BKT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, warp tile 64 x 32
+
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+    auto issue = [&](int kt) {
+        int s = kt % STAGES;
+        load_tile<AK>(sA + s * TILE_HALVES, g.A, g.lda, m0, kbeg + kt * BKT);
+        load_tile<BK_>(sB + s * TILE_HALVES, g.B, g.ldb, n0, kbeg + kt * BKT);
+    };
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (s < ktiles) issue(s);
+        cp_async_commit();
+    }
+    for (int kt = 0; kt < ktiles; ++kt) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();
+        if (kt + STAGES - 1 < ktiles) issue(kt + STAGES - 1);
+        cp_async_commit();
+        const __nv_bfloat16* a = sA + (kt % STAGES) * TILE_HALVES;
+        const __nv_bfloat16* b = sB + (kt % STAGES) * TILE_HALVES;
+#pragma unroll
+        for (int kk = 0; kk < BKT; kk += 16) {
+            uint32_t af[4][4], bfr[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi) {
+                int mr = wm * 64 + mi * 16;
+                if (AK) {
+                    ldsm_x4(af[mi], a + (mr + (lane & 15)) * KMAJ_LD + kk + (lane >> 4) * 8);
+                } else {
+                    ldsm_x4_t(af[mi], a + (kk + (lane & 7) + (lane >> 4) * 8) * MMAJ_LD + mr + ((lane >> 3) & 1) * 8);
+                }
+            }
+#pragma unroll
+            for (int nj = 0; nj < 2; ++nj) {
+                int nr = wn * 32 + nj * 16;
+                uint32_t r[4];
+                if (BK_) {
+                    ldsm_x4(r, b + (nr + (lane & 7) + (lane >> 4) * 8) * KMAJ_LD + kk + ((lane >> 3) & 1) * 8);
+                } else {
+                    ldsm_x4_t(r, b + (kk + (lane & 7) + ((lane >> 3) & 1) * 8) * MMAJ_LD + nr + (lane >> 4) * 8);
+                }
+                bfr[nj * 2][0] = r[0];
+                bfr[nj * 2][1] = r[1];
+                bfr[nj * 2 + 1][0] = r[2];
+                bfr[nj * 2 + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bfr[ni]);
+        }
+    }
+    cp_async_wait<0>();
+
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int row = m0 + wm * 64 + mi * 16 + gid + h * 8;
+                int col = n0 + wn * 32 + ni * 8 + tig * 2;
+                float v0 = acc[mi][ni][2 * h], v1 = acc[mi][ni][2 * h + 1];
+                if (EPI == EPI_BIAS_RELU) {
+                    v0 = fmaxf(v0 + g.bias[col], 0.f);
+                    v1 = fmaxf(v1 + g.bias[col + 1], 0.f);
+                    *reinterpret_cast<__nv_bfloat162*>(g.out + (size_t)row * g.ldo + col) = __floats2bfloat162_rn(v0, v1);
+                } else if (EPI == EPI_MASK) {
+                    __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(g.mask + (size_t)row * g.ldo + col);
+                    v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+                    v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+                    *reinterpret_cast<__nv_bfloat162*>(g.out + (size_t)row * g.ldo + col) = __floats2bfloat162_rn(v0, v1);
+                } else {
+                    float* p = g.partial + (size_t)blockIdx.z * g.M * g.N + (size_t)row * g.N + col;
+                    *reinterpret_cast<float2*>(p) = make_float2(v0, v1);
+                }
+            }
+}
+
+template <bool AK, bool BK_, int EPI>
+int launch_gemm(const GemmArgs& a, int splits, cudaStream_t s) {
+    if (a.M % BM || a.N % BN || a.K % (BKT * splits) || a.lda % 8 || a.ldb % 8) return LUDAX_ERR_SIZE;
+    auto k = gemm_bf16_kernel<AK, BK_, EPI>;
+    static bool attr = false;  // per instantiation
+    if (!attr) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess)
+            return LUDAX_ERR_CUDA;
+        attr = true;
+    }
+    GemmArgs g = a;
+    g.k_per_split = a.K / splits;
+    dim3 grid(a.N / BN, a.M / BM, splits);
+    k<<<grid, GEMM_THREADS, GEMM_SMEM, s>>>(g);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ head layer --
+// One warp per row: z = H2[b] . w3 + b3, v = tanh(z), p = (v + 1) / 2.  With
+// labels: g3[b] = dL/dz for L = mean (p - y)^2, and the row's squared error.
+__global__ void head_forward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16* w3, const float* b3, int B,
+                                    float* p_out, const float* y, float* g3, float* sqerr) {
+    int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (row >= B) return;
+    const uint4* h = reinterpret_cast<const uint4*>(H2 + (size_t)row * kH);
+    const uint4* w = reinterpret_cast<const uint4*>(w3);
+    float z = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        uint4 hv = h[lane + 32 * i], wv = w[lane + 32 * i];
+        const __nv_bfloat162* hp = reinterpret_cast<const __nv_bfloat162*>(&hv);
+        const __nv_bfloat162* wp = reinterpret_cast<const __nv_bfloat162*>(&wv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float2 a = __bfloat1622float2(hp[j]), c = __bfloat1622float2(wp[j]);
+            z = fmaf(a.x, c.x, z);
+            z = fmaf(a.y, c.y, z);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xFFFFFFFFu, z, o);
+    if (lane == 0) {
+        z += b3[0];
+        float v = tanhf(z);
+        float p = 0.5f * (v + 1.f);
+        if (p_out) p_out[row] = p;
+        if (y) {
+            float d = p - y[row];
+            g3[row] = d * (1.f - v * v) / (float)B;  // 2 (p-y)/B * (1/2) (1 - v^2)
+            sqerr[row] = d * d;
+        }
+    }
+}
+
+// dZ2[b][j] = g3[b] w3[j] [H2[b][j] > 0] (stored bf16), plus per-chunk column
+// partials of dw3 = sum_b g3 H2 and db2 = sum_b dZ2, and of db3 = sum_b g3.
+constexpr int HB_ROWS = 256;
+__global__ void head_backward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16* w3, const float* g3, int B,
+                                     __nv_bfloat16* dZ2, float* part_w3, float* part_b2, float* part_b3) {
+    const int j = threadIdx.x * 2;  // 256 threads x 2 columns
+    const int r0 = blockIdx.x * HB_ROWS;
+    float2 w = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(w3 + j));
+    float aw0 = 0, aw1 = 0, ab0 = 0, ab1 = 0, ag = 0;
+    for (int r = r0; r < min(r0 + HB_ROWS, B); ++r) {
+        float gr = g3[r];
+        float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(H2 + (size_t)r * kH + j));
+        float d0 = h.x > 0.f ? gr * w.x : 0.f, d1 = h.y > 0.f ? gr * w.y : 0.f;
+        *reinterpret_cast<__nv_bfloat162*>(dZ2 + (size_t)r * kH + j) = __floats2bfloat162_rn(d0, d1);
+        aw0 = fmaf(gr, h.x, aw0);
+        aw1 = fmaf(gr, h.y, aw1);
+        ab0 += d0;
+        ab1 += d1;
+        ag += gr;
+    }
+    part_w3[(size_t)blockIdx.x * kH + j] = aw0;
+    part_w3[(size_t)blockIdx.x * kH + j + 1] = aw1;
+    part_b2[(size_t)blockIdx.x * kH + j] = ab0;
+    part_b2[(size_t)blockIdx.x * kH + j + 1] = ab1;
+    if (threadIdx.x == 0) part_b3[blockIdx.x] = ag;
+}
+
+// per-chunk column sums of a [B][kH] bf16 matrix (db1 = sum_b dZ1)
+__global__ void colsum_kernel(const __nv_bfloat16* X, int B, float* part) {
+    const int j = threadIdx.x * 2;
+    const int r0 = blockIdx.x * HB_ROWS;
+    float a0 = 0, a1 = 0;
+    for (int r = r0; r < min(r0 + HB_ROWS, B); ++r) {
+        float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(X + (size_t)r * kH + j));
+        a0 += v.x;
+        a1 += v.y;
+    }
+    part[(size_t)blockIdx.x * kH + j] = a0;
+    part[(size_t)blockIdx.x * kH + j + 1] = a1;
+}
+
+// out[i] = sum_s part[s*n + i] (in a fixed order)
+__global__ void reduce_parts_kernel(const float* part, int splits, int n, float* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a = 0.f;
+    for (int s = 0; s < splits; ++s) a += part[(size_t)s * n + i];
+    out[i] = a;
+}
+
+// Adam (Kingma & Ba, Algorithm 1) on the flat FP32 parameters, then the BF16
+// copies the GEMMs read.  bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
+__global__ void adam_kernel(float* p, float* m, float* v, const float* g, long long n, float lr, float bc1, float bc2) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.f - b1) * gi;
+    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+__global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+__global__ void sum_kernel(const float* x, int n, float scale, float* out) {
+    __shared__ float sh[32];
+    float a = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        a = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        if (threadIdx.x == 0) *out = a * scale;
+    }
+}
+
+// ---------------------------------------------------------- env -> input --
+// Row of the net input for a position: bf16 1.0 at column c for each P1 stone
+// on cell c, at column cells + c for each P2 stone, at column 2*cells when P1
+// is to move; zero elsewhere up to ld.
+template <class G>
+__device__ __forceinline__ void write_input_row(const G& g, __nv_bfloat16* row, int ld) {
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+    for (int c0 = 0; c0 < ld; c0 += 8) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int c = c0 + i;
+            bool on = false;
+            if (c < G::kCells) {
+                int b = G::bit_of(c);
+                on = g.side == 0 ? mask_has(g.own, b) : mask_has(g.opp, b);
+            } else if (c < 2 * G::kCells) {
+                int b = G::bit_of(c - G::kCells);
+                on = g.side == 0 ? mask_has(g.opp, b) : mask_has(g.own, b);
+            } else if (c == 2 * G::kCells) {
+                on = g.side == 0;
+            }
+            v[i] = on ? one : zero;
+        }
+        *reinterpret_cast<uint4*>(row + c0) = *reinterpret_cast<const uint4*>(v);
+    }
+}
+
+template <class G>
+__global__ void pack_inputs_kernel(EnvDev d, __nv_bfloat16* X, int ld) {
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    load_state(g, d, e);
+    write_input_row(g, X + (size_t)e * ld, ld);
+}
+
+// Continuation j of env e0+i (i < n_chunk): up to `plies` uniform-random plies
+// from the stored state with the draws of playout seed + j, then either the
+// final result (score, done = 1) or the leaf's input row (done = 0).
+template <class G>
+__global__ void leaf_kernel(EnvDev d, long long e0, long long n_chunk, int K, uint64_t seed, int plies,
+                            __nv_bfloat16* X, int ld, float* score, uint8_t* done) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_chunk * K) return;
+    long long e = e0 + t / K;
+    int j = (int)(t % K);
+    G g;
+    set_table(g, nullptr);
+    load_state(g, d, e);
+    uint64_t key = env_key(splitmix64(seed + (uint64_t)j), (uint64_t)(d.env_offset + e));
+    int stop = g.ply + plies;
+    while (g.outcome == kOngoing && g.ply < stop) random_ply(g, key);
+    if (g.outcome != kOngoing) {
+        score[t] = p1_score(g.outcome);
+        done[t] = 1;
+    } else {
+        done[t] = 0;
+    }
+    write_input_row(g, X + (size_t)t * ld, ld);
+}
+
+// value[e0+i] = mean over j of (done ? score : p_net)
+__global__ void combine_kernel(long long e0, long long n_chunk, int K, const float* score, const uint8_t* done,
+                               const float* p, float* value) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_chunk) return;
+    float a = 0.f;
+    for (int j = 0; j < K; ++j) {
+        long long t = i * K + j;
+        a += done[t] ? score[t] : p[t];
+    }
+    value[e0 + i] = a / (float)K;
+}
+
+unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+struct ludax_net {
+    int cells, kin, kpad;
+    long long max_batch;
+    cudaStream_t stream;
+    long long nparams;
+    long long oW1, ob1, oW2, ob2, ow3, ob3;
+    int t;  // Adam steps taken
+    float *p, *m, *v, *g;
+    __nv_bfloat16 *W1b, *W2b, *w3b;
+    __nv_bfloat16 *H1, *H2, *dZ2, *dZ1, *Xleaf;
+    float *pout, *g3, *sqerr, *part, *score;
+    uint8_t* done;
+    long long part_floats;
+};
+
+namespace {
+
+int net_check(const ludax_net* n, long long B) {
+    if (!n || B < 1 || B > n->max_batch) return LUDAX_ERR_ARG;
+    if (B % BM) return LUDAX_ERR_SIZE;
+    return LUDAX_OK;
+}
+
+int refresh_bf16(ludax_net* n) {
+    to_bf16_kernel<<<blocks_for((long long)kH * n->kpad, 256), 256, 0, n->stream>>>(n->p + n->oW1, n->W1b,
+                                                                                   (long long)kH * n->kpad);
+    to_bf16_kernel<<<blocks_for((long long)kH * kH, 256), 256, 0, n->stream>>>(n->p + n->oW2, n->W2b, (long long)kH * kH);
+    to_bf16_kernel<<<blocks_for(kH, 256), 256, 0, n->stream>>>(n->p + n->ow3, n->w3b, kH);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+// Forward pass to p (and, with labels y, the per-row gradient g3 of the loss).
+int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, const float* y) {
+    cudaStream_t s = n->stream;
+    GemmArgs a{};
+    a.A = X; a.B = n->W1b; a.M = (int)B; a.N = kH; a.K = n->kpad; a.lda = n->kpad; a.ldb = n->kpad;
+    a.bias = n->p + n->ob1; a.out = n->H1; a.ldo = kH;
+    int st = launch_gemm<true, true, EPI_BIAS_RELU>(a, 1, s);
+    if (st) return st;
+    a.A = n->H1; a.B = n->W2b; a.K = kH; a.lda = kH; a.ldb = kH; a.bias = n->p + n->ob2; a.out = n->H2;
+    if ((st = launch_gemm<true, true, EPI_BIAS_RELU>(a, 1, s))) return st;
+    head_forward_kernel<<<blocks_for(B, 8), 256, 0, s>>>(n->H2, n->w3b, n->p + n->ob3, (int)B, p, y, n->g3, n->sqerr);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+// Full gradient into n->g (flat, FP32) and the mean loss into loss_out (nullable).
+int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, float* loss_out) {
+    cudaStream_t s = n->stream;
+    const int chunks = (int)((B + HB_ROWS - 1) / HB_ROWS);
+    float* pw3 = n->part;
+    float* pb2 = pw3 + (size_t)chunks * kH;
+    float* pb3 = pb2 + (size_t)chunks * kH;
+    head_backward_kernel<<<chunks, 256, 0, s>>>(n->H2, n->w3b, n->g3, (int)B, n->dZ2, pw3, pb2, pb3);
+    reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pw3, chunks, kH, n->g + n->ow3);
+    reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pb2, chunks, kH, n->g + n->ob2);
+    reduce_parts_kernel<<<1, 32, 0, s>>>(pb3, chunks, 1, n->g + n->ob3);
+    // dZ1 = (dZ2 . W2) * [H1 > 0]
+    GemmArgs a{};
+    a.A = n->dZ2; a.B = n->W2b; a.M = (int)B; a.N = kH; a.K = kH; a.lda = kH; a.ldb = kH;
+    a.mask = n->H1; a.out = n->dZ1; a.ldo = kH;
+    int st = launch_gemm<true, false, EPI_MASK>(a, 1, s);
+    if (st) return st;
+    colsum_kernel<<<chunks, 256, 0, s>>>(n->dZ1, (int)B, pw3);
+    reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pw3, chunks, kH, n->g + n->ob1);
+    // dW2 = dZ2^T . H1 and dW1 = dZ1^T . X, split over the batch
+    int splits = (int)std::min<long long>(32, B / BKT);
+    while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
+    a = GemmArgs{};
+    a.A = n->dZ2; a.B = n->H1; a.M = kH; a.N = kH; a.K = (int)B; a.lda = kH; a.ldb = kH; a.partial = n->part;
+    if ((st = launch_gemm<false, false, EPI_PARTIAL>(a, splits, s))) return st;
+    reduce_parts_kernel<<<blocks_for((long long)kH * kH, 256), 256, 0, s>>>(n->part, splits, kH * kH, n->g + n->oW2);
+    a.A = n->dZ1; a.B = X; a.N = n->kpad; a.ldb = n->kpad;
+    if ((st = launch_gemm<false, false, EPI_PARTIAL>(a, splits, s))) return st;
+    reduce_parts_kernel<<<blocks_for((long long)kH * n->kpad, 256), 256, 0, s>>>(n->part, splits, kH * n->kpad,
+                                                                                 n->g + n->oW1);
+    if (loss_out) sum_kernel<<<1, 1024, 0, s>>>(n->sqerr, (int)B, 1.f / (float)B, loss_out);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* stream) {
+    if (!out || cells < 1 || cells > 127 || max_batch < BM || max_batch % BM || max_batch > (1ll << 24))
+        return LUDAX_ERR_ARG;
+    *out = nullptr;
+    ludax_net* n = new (std::nothrow) ludax_net();
+    if (!n) return LUDAX_ERR_NOMEM;
+    n->cells = cells;
+    n->kin = 2 * cells + 1;
+    n->kpad = ((n->kin + 127) / 128) * 128;
+    n->max_batch = max_batch;
+    n->stream = (cudaStream_t)stream;
+    n->oW1 = 0;
+    n->ob1 = n->oW1 + (long long)kH * n->kpad;
+    n->oW2 = n->ob1 + kH;
+    n->ob2 = n->oW2 + (long long)kH * kH;
+    n->ow3 = n->ob2 + kH;
+    n->ob3 = n->ow3 + kH;
+    n->nparams = n->ob3 + 1;
+    const long long B = max_batch;
+    const int max_splits = 32;
+    n->part_floats = std::max<long long>((long long)max_splits * kH * std::max(kH, n->kpad),
+                                         3ll * ((B + HB_ROWS - 1) / HB_ROWS) * kH + 64);
+    bool ok = cudaMalloc(&n->p, 4 * n->nparams * sizeof(float)) == cudaSuccess;
+    if (ok) {
+        n->m = n->p + n->nparams;
+        n->v = n->m + n->nparams;
+        n->g = n->v + n->nparams;
+    }
+    ok = ok && cudaMalloc(&n->W1b, sizeof(__nv_bfloat16) * ((size_t)kH * n->kpad + (size_t)kH * kH + kH)) == cudaSuccess;
+    if (ok) {
+        n->W2b = n->W1b + (size_t)kH * n->kpad;
+        n->w3b = n->W2b + (size_t)kH * kH;
+    }
+    ok = ok && cudaMalloc(&n->H1, sizeof(__nv_bfloat16) * (size_t)B * (4 * kH + n->kpad)) == cudaSuccess;
+    if (ok) {
+        n->H2 = n->H1 + (size_t)B * kH;
+        n->dZ2 = n->H2 + (size_t)B * kH;
+        n->dZ1 = n->dZ2 + (size_t)B * kH;
+        n->Xleaf = n->dZ1 + (size_t)B * kH;
+    }
+    ok = ok && cudaMalloc(&n->pout, sizeof(float) * (4 * (size_t)B + n->part_floats)) == cudaSuccess;
+    if (ok) {
+        n->g3 = n->pout + B;
+        n->sqerr = n->g3 + B;
+        n->score = n->sqerr + B;
+        n->part = n->score + B;
+    }
+    ok = ok && cudaMalloc(&n->done, (size_t)B) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        ludax_net_destroy(n);
+        return LUDAX_ERR_NOMEM;
+    }
+    if (cudaMemsetAsync(n->p, 0, 4 * n->nparams * sizeof(float), n->stream) != cudaSuccess ||
+        refresh_bf16(n) != LUDAX_OK) {
+        ludax_net_destroy(n);
+        return LUDAX_ERR_CUDA;
+    }
+    *out = n;
+    return LUDAX_OK;
+}
+
+int ludax_net_destroy(ludax_net* n) {
+    if (!n) return LUDAX_OK;
+    cudaStreamSynchronize(n->stream);
+    cudaFree(n->p);
+    cudaFree(n->W1b);
+    cudaFree(n->H1);
+    cudaFree(n->pout);
+    cudaFree(n->done);
+    delete n;
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+int ludax_net_sizes(const ludax_net* n, int32_t* in_pad, int32_t* hidden, int64_t* num_params) {
+    if (!n) return LUDAX_ERR_ARG;
+    if (in_pad) *in_pad = n->kpad;
+    if (hidden) *hidden = kH;
+    if (num_params) *num_params = n->nparams;
+    return LUDAX_OK;
+}
+
+int ludax_net_set_params(ludax_net* n, const float* params_dev) {
+    if (!n || !params_dev) return LUDAX_ERR_ARG;
+    if (cudaMemcpyAsync(n->p, params_dev, sizeof(float) * n->nparams, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess ||
+        cudaMemsetAsync(n->m, 0, 2 * sizeof(float) * n->nparams, n->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    n->t = 0;
+    return refresh_bf16(n);
+}
+
+int ludax_net_get_params(ludax_net* n, float* params_dev) {
+    if (!n || !params_dev) return LUDAX_ERR_ARG;
+    return cudaMemcpyAsync(params_dev, n->p, sizeof(float) * n->nparams, cudaMemcpyDeviceToDevice, n->stream) == cudaSuccess
+               ? LUDAX_OK
+               : LUDAX_ERR_CUDA;
+}
+
+int ludax_net_forward(ludax_net* n, const uint16_t* x_dev, int64_t B, float* p_dev) {
+    int st = net_check(n, B);
+    if (st) return st;
+    if (!x_dev || !p_dev) return LUDAX_ERR_ARG;
+    if ((uintptr_t)x_dev % 16) return LUDAX_ERR_ALIGN;
+    return net_forward(n, reinterpret_cast<const __nv_bfloat16*>(x_dev), B, p_dev, nullptr);
+}
+
+int ludax_net_grad(ludax_net* n, const uint16_t* x_dev, const float* y_dev, int64_t B, float* grad_dev, float* loss_dev) {
+    int st = net_check(n, B);
+    if (st) return st;
+    if (!x_dev || !y_dev) return LUDAX_ERR_ARG;
+    if ((uintptr_t)x_dev % 16) return LUDAX_ERR_ALIGN;
+    const __nv_bfloat16* X = reinterpret_cast<const __nv_bfloat16*>(x_dev);
+    if ((st = net_forward(n, X, B, n->pout, y_dev))) return st;
+    if ((st = net_backward(n, X, B, loss_dev))) return st;
+    if (grad_dev && cudaMemcpyAsync(grad_dev, n->g, sizeof(float) * n->nparams, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    return LUDAX_OK;
+}
+
+int ludax_net_train_step(ludax_net* n, const uint16_t* x_dev, const float* y_dev, int64_t B, float lr, float* loss_dev) {
+    int st = ludax_net_grad(n, x_dev, y_dev, B, nullptr, loss_dev);
+    if (st) return st;
+    n->t += 1;
+    const float bc1 = 1.f - powf(0.9f, (float)n->t), bc2 = 1.f - powf(0.999f, (float)n->t);
+    adam_kernel<<<blocks_for(n->nparams, 256), 256, 0, n->stream>>>(n->p, n->m, n->v, n->g, n->nparams, lr, bc1, bc2);
+    if (cudaGetLastError() != cudaSuccess) return LUDAX_ERR_CUDA;
+    return refresh_bf16(n);
+}
+
+int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld) {
+    if (!env || !x_dev || ld < 2 * env->cells + 1 || ld % 8) return LUDAX_ERR_ARG;
+    if ((uintptr_t)x_dev % 16) return LUDAX_ERR_ALIGN;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        pack_inputs_kernel<G><<<blocks_for(env->n, 128), 128, 0, env->stream>>>(
+            EnvDev{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters},
+            reinterpret_cast<__nv_bfloat16*>(x_dev), ld);
+        return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    });
+}
+
+int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K, int32_t plies, float* value_dev) {
+    if (!env || !n || !value_dev || K < 1 || plies < 0) return LUDAX_ERR_ARG;
+    if (n->cells != env->cells) return LUDAX_ERR_SIZE;
+    if (n->stream != env->stream) return LUDAX_ERR_ARG;
+    long long chunk = (n->max_batch / K);
+    if (chunk < 1) return LUDAX_ERR_SIZE;
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        EnvDev d{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters};
+        for (long long e0 = 0; e0 < env->n; e0 += chunk) {
+            long long nc = std::min(chunk, env->n - e0);
+            long long rows = nc * K, rows_pad = ((rows + BM - 1) / BM) * BM;
+            if (rows_pad > rows &&
+                cudaMemsetAsync(n->Xleaf + (size_t)rows * n->kpad, 0,
+                                sizeof(__nv_bfloat16) * (size_t)(rows_pad - rows) * n->kpad, env->stream) != cudaSuccess)
+                return LUDAX_ERR_CUDA;
+            leaf_kernel<G><<<blocks_for(rows, 128), 128, 0, env->stream>>>(d, e0, nc, K, seed, plies, n->Xleaf,
+                                                                             n->kpad, n->score, n->done);
+            int st = net_forward(n, n->Xleaf, rows_pad, n->pout, nullptr);
+            if (st) return st;
+            combine_kernel<<<blocks_for(nc, 256), 256, 0, env->stream>>>(e0, nc, K, n->score, n->done, n->pout, value_dev);
+        }
+        return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    });
+}
+
+}  // extern "C"

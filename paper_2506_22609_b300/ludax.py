@@ -96,6 +96,16 @@ def lib() -> ctypes.CDLL:
         "ludax_autotune": [vp, i64, u64, i32, vp, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
         "ludax_autotune_env": [vp, u64, i32, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
         "ludax_autotune_candidates": [P(ludax_launch_cfg), i32],
+        "ludax_net_create": [P(vp), i32, i64, vp],
+        "ludax_net_destroy": [vp],
+        "ludax_net_sizes": [vp, P(i32), P(i32), P(i64)],
+        "ludax_net_set_params": [vp, vp],
+        "ludax_net_get_params": [vp, vp],
+        "ludax_net_forward": [vp, vp, i64, vp],
+        "ludax_net_grad": [vp, vp, vp, i64, vp, vp],
+        "ludax_net_train_step": [vp, vp, vp, i64, ctypes.c_float, vp],
+        "ludax_pack_inputs": [vp, vp, i32],
+        "ludax_truncated_value": [vp, vp, u64, i32, i32, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -266,6 +276,94 @@ def ludax_autotune_env(h, seed: int = 0, reps: int = 5):
     _check(lib().ludax_autotune_env(h, seed, reps, ctypes.byref(best), ctypes.byref(best_ms), table,
                                     ctypes.byref(cands_n)), "ludax_autotune_env")
     return best, best_ms.value, list(table)[: cands_n.value]
+
+
+def ludax_net_create(cells: int, max_batch: int, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().ludax_net_create(ctypes.byref(h), cells, max_batch, _stream(stream)), "ludax_net_create")
+    return h
+
+
+def ludax_net_destroy(h):
+    _check(lib().ludax_net_destroy(h), "ludax_net_destroy")
+
+
+def ludax_net_sizes(h):
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(lib().ludax_net_sizes(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "ludax_net_sizes")
+    return a.value, b.value, c.value
+
+
+def ludax_net_set_params(h, params):
+    _check(lib().ludax_net_set_params(h, _ptr(params)), "ludax_net_set_params")
+
+
+def ludax_net_get_params(h, params):
+    _check(lib().ludax_net_get_params(h, _ptr(params)), "ludax_net_get_params")
+
+
+def ludax_net_forward(h, x, p):
+    _check(lib().ludax_net_forward(h, _ptr(x), x.shape[0], _ptr(p)), "ludax_net_forward")
+
+
+def ludax_net_grad(h, x, y, grad=None, loss=None):
+    _check(lib().ludax_net_grad(h, _ptr(x), _ptr(y), x.shape[0], _ptr(grad), _ptr(loss)), "ludax_net_grad")
+
+
+def ludax_net_train_step(h, x, y, lr: float, loss=None):
+    _check(lib().ludax_net_train_step(h, _ptr(x), _ptr(y), x.shape[0], lr, _ptr(loss)), "ludax_net_train_step")
+
+
+def ludax_pack_inputs(env_h, x, ld: int):
+    _check(lib().ludax_pack_inputs(env_h, _ptr(x), ld), "ludax_pack_inputs")
+
+
+def ludax_truncated_value(env_h, net_h, seed: int, K: int, plies: int, value):
+    _check(lib().ludax_truncated_value(env_h, net_h, seed, K, plies, _ptr(value)), "ludax_truncated_value")
+
+
+class Net:
+    """The value network (bf16 inputs are passed as int16 tensors holding the bits)."""
+
+    def __init__(self, cells, max_batch, stream=None):
+        self.handle = ludax_net_create(cells, max_batch, stream)
+        self.in_pad, self.hidden, self.num_params = ludax_net_sizes(self.handle)
+        self.cells, self.max_batch = cells, max_batch
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            ludax_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        ludax_net_set_params(self.handle, params.to(torch.float32).contiguous())
+
+    def get_params(self):
+        p = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        ludax_net_get_params(self.handle, p)
+        return p
+
+    def forward(self, x):
+        p = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")
+        ludax_net_forward(self.handle, x, p)
+        return p
+
+    def grad(self, x, y):
+        g = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        ludax_net_grad(self.handle, x, y, g, loss)
+        return g, loss
+
+    def train_step(self, x, y, lr):
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        ludax_net_train_step(self.handle, x, y, lr, loss)
+        return loss
 
 
 # ------------------------------------------------------------------- Env ----

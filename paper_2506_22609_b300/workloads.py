@@ -87,3 +87,32 @@ def bench_cfg(cfg: Config) -> tuple:
 
 def mixed_bench_cfg() -> tuple:
     return MIXED_BENCH_CFG
+
+
+# ------------------------------------------------------------ value net --
+NET_HIDDEN = 512
+
+
+def net_in_pad(cells: int) -> int:
+    return ((2 * cells + 1 + 127) // 128) * 128
+
+
+def init_params(cells: int, seed: int) -> np.ndarray:
+    """Initial flat parameter vector (float32) for the value network:
+    Kaiming-uniform hidden weights (bound sqrt(6 / fan_in), fan_in counting
+    the real inputs 2*cells+1), output weights uniform within 1/sqrt(512),
+    zero biases.  Layout W1 [512][in_pad], b1, W2 [512][512], b2, w3, b3."""
+    rng = np.random.default_rng(seed)
+    H, K, kin = NET_HIDDEN, net_in_pad(cells), 2 * cells + 1
+    W1 = np.zeros((H, K), np.float32)
+    W1[:, :kin] = rng.uniform(-1, 1, (H, kin)) * np.sqrt(6.0 / kin)
+    W2 = rng.uniform(-1, 1, (H, H)) * np.sqrt(6.0 / H)
+    w3 = rng.uniform(-1, 1, H) / np.sqrt(H)
+    z = np.zeros(H)
+    return np.concatenate([W1.reshape(-1), z, W2.reshape(-1), z, w3, [0.0]]).astype(np.float32)
+
+
+def ply_samples(n: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """n plies drawn uniformly from lo..hi (inclusive): where each sampled
+    playout stops to yield a training position."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, n).astype(np.int16)

@@ -1,0 +1,179 @@
+"""GPU parity of the value network kernels against the fp64 oracle.
+
+Tolerances follow from the precision the kernels use: BF16 weights, BF16
+hidden activations and hidden-layer gradients (unit roundoff 2^-8), FP32
+accumulation.  Against an fp64 evaluation that applies the same BF16
+rounding to weights and activations, outputs agree to ~1e-4; against the
+plain fp64 definition the gradients agree to a few percent.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import games as G
+from oracle import mlp as M
+from paper_2506_22609_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L(cuda_device):
+    from paper_2506_22609_b300 import build
+
+    build.build()
+    from paper_2506_22609_b300 import ludax
+
+    ludax.lib()
+    return ludax
+
+
+def bf16_bits(x):
+    """float array -> int16 tensor holding bf16 bits (round to nearest even)."""
+    t = torch.from_numpy(np.asarray(x, np.float32))
+    return t.to(torch.bfloat16).view(torch.int16).cuda()
+
+
+def rounded_theta(theta, K):
+    """Weights rounded to bf16 as the GEMMs see them; biases stay fp32."""
+    P = M.unflatten(theta, K)
+    for k in ("W1", "W2", "w3"):
+        P[k] = M.bf16_round(P[k])
+    return M.flatten(P, K)
+
+
+def forward_bf16(theta, X, K):
+    """fp64 forward with the kernels' rounding points (bf16 weights and hidden activations)."""
+    P = M.unflatten(rounded_theta(theta, K), K)
+    h1 = M.bf16_round(np.maximum(X @ P["W1"].T + P["b1"], 0))
+    h2 = M.bf16_round(np.maximum(h1 @ P["W2"].T + P["b2"], 0))
+    return 0.5 * (np.tanh(h2 @ P["w3"] + P["b3"][0]) + 1)
+
+
+def positions(game, rows, cols, n, seed):
+    s = G.reset(game, rows, cols, n)
+    G.rollout_from(s, seed=seed, stop_ply=W.ply_samples(n, 3, rows * cols // 2, seed))
+    return s
+
+
+@pytest.mark.parametrize("name,game,rows,cols", [("othello", G.OTHELLO, 8, 8), ("hex11", G.HEX, 11, 11),
+                                                 ("c4", G.C4, 6, 7)])
+def test_pack_inputs_matches_encoding(L, name, game, rows, cols):
+    n = 300
+    s = positions(game, rows, cols, n, 1)
+    env = L.Env(game, rows, cols, n)
+    env.set_state(*(torch.from_numpy(x) for x in (s.board, s.to_move, s.ply, s.passes, s.outcome)))
+    K = W.net_in_pad(rows * cols)
+    x = torch.empty(n, K, dtype=torch.int16, device="cuda")
+    L.ludax_pack_inputs(env.handle, x, K)
+    got = x.view(torch.bfloat16).float().cpu().numpy()
+    assert (got == M.encode(s.board, s.to_move, K)).all()
+
+
+@pytest.mark.parametrize("cells,B", [(64, 256), (121, 384), (64, 1280)])
+def test_forward_matches_oracle(L, cells, B):
+    K = W.net_in_pad(cells)
+    theta = W.init_params(cells, 7)
+    theta[M.num_params(K) - 1] = 0.1                      # nonzero output bias
+    rng = np.random.default_rng(cells)
+    X = np.zeros((B, K))
+    X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
+    net = L.Net(cells, 2048)
+    assert (net.in_pad, net.hidden, net.num_params) == (K, 512, M.num_params(K))
+    net.set_params(torch.from_numpy(theta).cuda())
+    p = net.forward(bf16_bits(X)).cpu().numpy()
+    ref = forward_bf16(theta, X, K)
+    assert np.abs(p - ref).max() < 5e-4
+    exact, _ = M.forward(theta.astype(np.float64), X, K)
+    assert np.abs(p - exact).max() < 2e-2
+    assert np.allclose(net.get_params().cpu().numpy(), theta)
+
+
+@pytest.mark.parametrize("cells,B", [(64, 512), (121, 256)])
+def test_gradient_matches_oracle(L, cells, B):
+    K = W.net_in_pad(cells)
+    theta = W.init_params(cells, 3)
+    rng = np.random.default_rng(5)
+    X = np.zeros((B, K))
+    X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
+    y = rng.random(B)
+    net = L.Net(cells, 1024)
+    net.set_params(torch.from_numpy(theta).cuda())
+    g, loss = net.grad(bf16_bits(X), torch.from_numpy(y.astype(np.float32)).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    th = rounded_theta(theta, K)
+    want = M.grad(th, X, y, K)
+    assert abs(loss.item() - M.loss(th, X, y, K)) < 1e-3 * max(1.0, M.loss(th, X, y, K))
+    G_ = M.unflatten(g, K)
+    Wt = M.unflatten(want, K)
+    for name, _ in M.param_shapes(K):
+        a, b = G_[name].ravel(), Wt[name].ravel()
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+        assert rel < 3e-2 and cos > 0.999, (name, rel, cos)
+    # padded input columns never receive gradient
+    assert np.abs(G_["W1"][:, 2 * cells + 1:]).max() == 0.0
+
+
+def test_adam_step_matches_oracle(L):
+    cells, B = 64, 256
+    K = W.net_in_pad(cells)
+    theta = W.init_params(cells, 11)
+    rng = np.random.default_rng(2)
+    X = np.zeros((B, K))
+    X[:, :129] = rng.random((B, 129)) < 0.3
+    y = rng.random(B)
+    net = L.Net(cells, 256)
+    net.set_params(torch.from_numpy(theta).cuda())
+    xb, yb = bf16_bits(X), torch.from_numpy(y.astype(np.float32)).cuda()
+    th, m, v = theta.astype(np.float64), np.zeros(theta.size), np.zeros(theta.size)
+    for t in (1, 2, 3):
+        g, _ = net.grad(xb, yb)
+        net.train_step(xb, yb, 1e-3)
+        th, m, v = M.adam_step(th, m, v, g.cpu().numpy().astype(np.float64), t, 1e-3)
+        got = net.get_params().cpu().numpy()
+        assert np.abs(got - th).max() < 2e-6, t
+        th = got.astype(np.float64)  # follow the fp32 trajectory
+
+
+def test_training_fits_a_fixed_target(L):
+    # A learnable target: the label is the fraction of P1 stones among the
+    # first 16 cells, so the loss must fall well below the label variance.
+    cells, B = 64, 2048
+    K = W.net_in_pad(cells)
+    rng = np.random.default_rng(0)
+    X = np.zeros((B, K))
+    X[:, :129] = rng.random((B, 129)) < 0.5
+    y = X[:, :16].mean(1)
+    net = L.Net(cells, B)
+    net.set_params(torch.from_numpy(W.init_params(cells, 1)).cuda())
+    xb, yb = bf16_bits(X), torch.from_numpy(y.astype(np.float32)).cuda()
+    first = net.train_step(xb, yb, 1e-3).item()
+    for _ in range(300):
+        last = net.train_step(xb, yb, 1e-3).item()
+    assert last < 0.1 * first and last < 0.1 * y.var()
+
+
+@pytest.mark.parametrize("name,game,rows,cols", [("othello", G.OTHELLO, 8, 8), ("hex7", G.HEX, 7, 7)])
+def test_truncated_value_matches_oracle(L, name, game, rows, cols):
+    n, Kc, plies, seed = 200, 4, 8, 99
+    cells = rows * cols
+    K = W.net_in_pad(cells)
+    s = positions(game, rows, cols, n, 4)
+    env = L.Env(game, rows, cols, n, env_offset=10)
+    env.set_state(*(torch.from_numpy(x) for x in (s.board, s.to_move, s.ply, s.passes, s.outcome)))
+    theta = W.init_params(cells, 8)
+    net = L.Net(cells, 1024)
+    net.set_params(torch.from_numpy(theta).cuda())
+    val = torch.empty(n, dtype=torch.float32, device="cuda")
+    L.ludax_truncated_value(env.handle, net.handle, seed, Kc, plies, val)
+    val = val.cpu().numpy()
+    want = np.zeros(n)
+    for j in range(Kc):
+        t = s.copy()
+        G.rollout_from(t, seed=seed + j, env_offset=10, stop_ply=(t.ply + plies).astype(np.int16))
+        p = forward_bf16(theta, M.encode(t.board, t.to_move, K), K)
+        res = np.where(t.outcome == 1, 1.0, np.where(t.outcome == 2, 0.0, 0.5))
+        want += np.where(t.outcome >= 0, res, p)
+    want /= Kc
+    assert np.abs(val - want).max() < 5e-4
