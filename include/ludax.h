@@ -238,6 +238,32 @@ int ludax_mixed_plan_destroy(ludax_mixed_plan* plan);
 int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,
                         int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg, void* stream);
 
+/* Allocation-free variant of ludax_rollout_mixed, for callers that cannot
+ * allocate device memory: code running while a CUDA graph is being captured,
+ * where cudaMalloc is not permitted, or serving loops and embedders where
+ * cudaMalloc/cudaFree would synchronise the device, stall other streams or
+ * break a fixed memory budget.  (The paper has no counterpart: this is a
+ * deployment entry point of this library.)
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *     Its scratch -- the game-grouped work queue and the claim cursors -- is a
+ *     static device array of 4 MiB plus 512 bytes, held by every GPU that
+ *     loads this library until the process exits.
+ *   - num_envs at most 1,048,576 (2^20): larger batches return LUDAX_ERR_SIZE
+ *     before anything is launched.
+ *   - The first call on a device looks up the array's device address (which
+ *     may load the library's device code); make that first call before any
+ *     stream capture on the device.
+ *   - Every call shares the one array: the call resets the counters it needs
+ *     and overwrites the queue, so calls whose work overlaps on the GPU (other
+ *     streams or threads) race and must be serialised by the caller.
+ *   - Blocks until the descriptors are validated (one small device-to-host
+ *     read); the playout itself stays asynchronous on `stream`.
+ * Arguments, results and errors as ludax_rollout_mixed; bad_index (nullable)
+ * receives the index of the first invalid descriptor, else -1.            */
+int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,
+                                int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg, void* stream,
+                                int64_t* bad_index);
+
 /* Autotuner: times every candidate launch shape (block_threads x
  * blocks_per_sm x envs_per_thread x hex_nbr_table) on the given mixed batch
  * with CUDA events (warm-up, then the median of `reps` launches) and returns

@@ -591,3 +591,139 @@ int ludax_autotune(const int32_t* desc_dev, int64_t num_envs, uint64_t seed, int
 }
 
 }  // extern "C"
+
+// ===================================================== allocation-free path ==
+// ludax_rollout_mixed_noalloc: the same mixed-batch playout as
+// ludax_rollout_mixed, for callers that must not allocate device memory --
+// for example code that runs while another thread captures work into a CUDA
+// graph, or a serving loop where cudaMalloc/cudaFree would synchronise the
+// device and stall other streams.  Its scratch (the game-grouped work queue
+// and the claim cursors) lives in the static device array below, which every
+// GPU that loads this library keeps until the process exits.
+namespace {
+
+constexpr long long kNoAllocMaxEnvs = 1ll << 20;  // 4 MiB of queue entries
+constexpr int kNoAllocCounterWords = 64;         // cursors, bucket counts and fill positions, first bad index
+// layout in 32-bit words: [0, kNoAllocMaxEnvs) queue, then 64 uint64 counters
+// (words 0..15 cursors, 16..31 bucket counts, 32..47 fill positions, 48 first bad index)
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocMaxEnvs + 2 * kNoAllocCounterWords];
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+__device__ __forceinline__ int bucket_of_desc_dev(int32_t d) {
+    if (d < 0 || (d >> 24) != 0) return -1;
+    int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
+    if (game == LUDAX_GAME_TTT) return (rows == 3 && cols == 3) ? 0 : -2;
+    if (game == LUDAX_GAME_C4) return (rows == 6 && cols == 7) ? 1 : -2;
+    if (game == LUDAX_GAME_OTHELLO) return (rows == 8 && cols == 8) ? 2 : -2;
+    if (game == LUDAX_GAME_HEX) return (rows == cols && rows >= 2 && rows <= 11) ? 3 + rows - 2 : -2;
+    return -1;
+}
+
+__global__ void noalloc_reset_kernel(unsigned long long* ctr, long long n) {
+    int i = threadIdx.x;
+    if (i < kNoAllocCounterWords) ctr[i] = (i == 48) ? (unsigned long long)n : 0ull;
+}
+
+// bucket histogram (block-local, then one atomic per bucket per block) and
+// the smallest index of an invalid descriptor
+__global__ void noalloc_count_kernel(const int32_t* desc, long long n, unsigned long long* ctr) {
+    __shared__ unsigned int hist[kBuckets];
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) {
+        int b = bucket_of_desc_dev(desc[e]);
+        if (b < 0) atomicMin(&ctr[48], (unsigned long long)e);
+        else atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kBuckets && hist[threadIdx.x]) atomicAdd(&ctr[16 + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+}
+
+struct BucketBegins {
+    long long begin[kBuckets];
+};
+
+// queue[begin[b] + k] = env ids of bucket b (order inside a bucket follows
+// the blocks' reservation order; results do not depend on it)
+__global__ void noalloc_scatter_kernel(const int32_t* desc, long long n, BucketBegins bb, unsigned long long* ctr,
+                                       int32_t* queue) {
+    __shared__ unsigned int hist[kBuckets];
+    __shared__ unsigned long long base[kBuckets];
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int b = -1;
+    unsigned int rank = 0;
+    if (e < n) {
+        b = bucket_of_desc_dev(desc[e]);
+        if (b >= 0) rank = atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kBuckets && hist[threadIdx.x])
+        base[threadIdx.x] = atomicAdd(&ctr[32 + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+    __syncthreads();
+    if (b >= 0) queue[bb.begin[b] + (long long)base[b] + rank] = (int32_t)e;
+}
+
+}  // namespace
+
+extern "C" int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,
+                                           int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg,
+                                           void* stream, int64_t* bad_index) {
+    if (!desc_dev || !outcome_dev || !plies_dev || num_envs < 1 || env_offset < 0) return LUDAX_ERR_ARG;
+    if (num_envs > kNoAllocMaxEnvs) return LUDAX_ERR_SIZE;  // more envs than the static queue holds
+    if (((uintptr_t)desc_dev % 4) || ((uintptr_t)plies_dev % 2)) return LUDAX_ERR_ALIGN;
+    ludax_launch_cfg c = cfg ? *cfg : default_mixed_cfg();
+    int st = check_mixed_cfg(c);
+    if (st != LUDAX_OK) return st;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LUDAX_ERR_CUDA;
+    if ((st = num_sms_current(&sms)) != LUDAX_OK) return st;
+    // once per device, with that device current: the scratch array's device address
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LUDAX_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    uint32_t* base = static_cast<uint32_t*>(g_noalloc_ptr[dev]);
+    int32_t* queue = reinterpret_cast<int32_t*>(base);
+    unsigned long long* ctr = reinterpret_cast<unsigned long long*>(base + kNoAllocMaxEnvs);
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned grid = (unsigned)((num_envs + 255) / 256);
+    noalloc_reset_kernel<<<1, kNoAllocCounterWords, 0, s>>>(ctr, num_envs);
+    noalloc_count_kernel<<<grid, 256, 0, s>>>(desc_dev, num_envs, ctr);
+    unsigned long long h[kNoAllocCounterWords];
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    if ((long long)h[48] < num_envs) {
+        long long e = (long long)h[48];
+        int32_t d = 0;
+        if (bad_index) *bad_index = e;
+        if (cudaMemcpy(&d, desc_dev + e, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) return LUDAX_ERR_CUDA;
+        return bucket_of_desc(d) == -2 ? LUDAX_ERR_SIZE : LUDAX_ERR_GAME;
+    }
+    if (bad_index) *bad_index = -1;
+    BucketBegins bb;
+    MixedArgs a{};
+    long long acc = 0;
+    for (int b = 0; b < kBuckets; ++b) {
+        bb.begin[b] = acc;
+        acc += (long long)h[16 + b];
+        a.bucket_end[b] = acc;
+    }
+    noalloc_scatter_kernel<<<grid, 256, 0, s>>>(desc_dev, num_envs, bb, ctr, queue);
+    if (cudaGetLastError() != cudaSuccess) return LUDAX_ERR_CUDA;
+    a.queue = queue;
+    a.n = num_envs;
+    a.env_offset = env_offset;
+    a.seed_key = splitmix64(seed);
+    a.outcome = outcome_dev;
+    a.plies = plies_dev;
+    a.cursor = ctr;  // words 0..12: zeroed by launch_mixed before the kernel
+    return launch_mixed(a, c, sms, s);
+}

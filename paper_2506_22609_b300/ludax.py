@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "ludax_sync": [vp, i64],
         "ludax_rollout_mixed": [vp, i64, i64, u64, vp, vp, P(ludax_launch_cfg), vp],
         "ludax_mixed_plan_create": [P(vp), vp, i64, i64, P(ludax_launch_cfg), vp, P(i64)],
+        "ludax_rollout_mixed_noalloc": [vp, i64, i64, u64, vp, vp, P(ludax_launch_cfg), vp, P(i64)],
         "ludax_mixed_plan_launch": [vp, u64, vp, vp],
         "ludax_mixed_plan_destroy": [vp],
         "ludax_autotune": [vp, i64, u64, i32, vp, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
@@ -225,6 +226,19 @@ def ludax_rollout_mixed(desc, env_offset: int, seed: int, outcome, plies, cfg=No
     _check(lib().ludax_rollout_mixed(_ptr(desc), desc.numel(), env_offset, seed, _ptr(outcome), _ptr(plies),
                                      ctypes.byref(cfg) if cfg is not None else None, _stream(stream)),
            "ludax_rollout_mixed")
+
+
+def ludax_rollout_mixed_noalloc(desc, env_offset: int, seed: int, outcome, plies, cfg=None, stream=None):
+    """Allocation-free mixed-batch playout (at most 2^20 envs; calls share one
+    static scratch array and must not overlap on the GPU)."""
+    bad = ctypes.c_int64(-1)
+    st = lib().ludax_rollout_mixed_noalloc(_ptr(desc), desc.numel(), env_offset, seed, _ptr(outcome), _ptr(plies),
+                                           ctypes.byref(cfg) if cfg is not None else None, _stream(stream),
+                                           ctypes.byref(bad))
+    if st != LUDAX_OK:
+        err = LudaxError(st, f"ludax_rollout_mixed_noalloc (first bad descriptor index {bad.value})")
+        err.bad_index = bad.value
+        raise err
 
 
 def ludax_mixed_plan_create(desc, env_offset: int = 0, cfg=None, stream=None):
