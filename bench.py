@@ -37,9 +37,16 @@ sys.path.insert(0, ROOT)
 METRIC = "env steps/sec on 1 B300 (random playouts); value estimates/sec at stated MAE"
 
 # Algorithmic 32-bit integer operations per env step of the fused playout,
-# counted from the bitboard algorithm (RNG draw, legal mask, count, select,
-# apply, end test); the derivation per game is in the design notes.
-ALG_OPS_PER_STEP = {"ttt": 73, "c4": 110, "othello": 560, "hex": 150}
+# counted from the bitboard algorithm with a 3-input logic op counted once:
+# RNG draw (13 logic/shift/add + 7 multiply), legal mask, popcount, k-th-bit
+# select, apply (Reversi flips), end test.  Reversi's count (437) is within 2%
+# of the instructions ncu measures executed per ply (444).
+ALG_OPS_PER_STEP = {"ttt": 75, "c4": 112, "othello": 437, "hex": 180}
+
+# DRAM bytes per launch of the benchmarked kernel, from the committed ncu
+# captures (profiles/); None once the kernel changes until it is captured again.
+NCU_TRAFFIC_BYTES = {"connect4_6x7_65536env_seed1": 13568,
+                     "connect4_6x7_16777216env_random_step_seed1": 335552512 + 426629888}
 
 
 def parse():
@@ -48,9 +55,10 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "mixed"])
+    p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "mixed", "step_c4"])
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
     p.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of the CPU-baseline sample")
     return p.parse_args()
 
@@ -75,35 +83,47 @@ def measured_peaks():
 
 # ----------------------------------------------------------------- clocks --
 class ClockSampler:
-    """Polls NVML (SM clock, max clock, clock-event reasons) in a thread."""
+    """Polls NVML's C library (SM clock, max SM clock, clock-event reasons)
+    from a thread while the timed region runs."""
 
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index, period=0.005):
-        self.samples, self.reasons, self.period, self.index = [], set(), period, index
-        self.max_mhz = None
+    def __init__(self, index, period=0.002):
+        import ctypes
+
+        self.samples, self.reasons, self.period = [], set(), period
+        self.max_mhz, self.err, self.nv = None, "", None
         self._stop = threading.Event()
         try:
-            import pynvml
-
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-        except Exception as e:  # NVML missing: report no clock record
-            self.nv, self.err = None, str(e)
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit_v2 failed")
+            self.h = ctypes.c_void_p()
+            # NVML indexes devices by their physical order; map through CUDA_VISIBLE_DEVICES
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            phys = int(vis.split(",")[index]) if vis and vis.split(",")[index].isdigit() else index
+            if nv.nvmlDeviceGetHandleByIndex_v2(phys, ctypes.byref(self.h)) != 0:
+                raise RuntimeError("nvmlDeviceGetHandleByIndex_v2 failed")
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(mx)) == 0:  # 1 = NVML_CLOCK_SM
+                self.max_mhz = mx.value
+            self.reason_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.nv, self.ct = nv, ctypes
+        except Exception as e:  # no NVML: report no clock record
+            self.err = str(e)
 
     def _run(self):
+        c = self.ct.c_uint()
+        r = self.ct.c_ulonglong()
         while not self._stop.is_set():
-            try:
-                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
-                r = self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, self.ct.byref(c)) == 0:
+                self.samples.append(c.value)
+            if self.reason_fn(self.h, self.ct.byref(r)) == 0:
                 for bit, name in self.REASONS.items():
-                    if r & bit:
+                    if r.value & bit:
                         self.reasons.add(name)
-            except Exception:
-                pass
             time.sleep(self.period)
 
     def __enter__(self):
@@ -254,13 +274,49 @@ def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
     return ms, total
 
 
-def bench_step_mode(L, steps, flush_buf):
+# algorithmic bytes of one env step in step-per-launch mode: read two planes
+# and the meta word (20 B), write them back (20 B), rewards (8 B), terminated (1 B)
+STEP_BYTES_PER_ENV = 49
+
+
+def bench_step_workload(L, steps, warmup, flush_buf, rank=0, n=1 << 24):
+    """Timed step = one ludax_random_step over n Connect Four envs, each step
+    taken on a batch reset and advanced 4 plies outside the timed events."""
+    import torch
+
+    env = L.Env("c4", 6, 7, n, env_offset=rank * n)
+    rew = torch.empty(n, 2, device="cuda")
+    term = torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def prepare():
+        L.ludax_reset(env.handle)
+        for _ in range(4):
+            L.ludax_random_step(env.handle, 1, rew, term)
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        prepare()
+        L.ludax_random_step(env.handle, 1, rew, term)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        prepare()
+        flush_l2(flush_buf)
+        a.record(stream)
+        L.ludax_random_step(env.handle, 1, rew, term)
+        b.record(stream)
+    torch.cuda.synchronize()
+    env.close()
+    return [a.elapsed_time(b) for a, b in ev], n, n
+
+
+def bench_step_mode(L, steps, flush_buf, game="c4", n=1 << 24):
     """Step-per-launch mode (ludax_random_step) at a batch far above L2:
     HBM-bound; returns achieved GB/s of algorithmic state traffic."""
     import torch
 
-    n = 1 << 22
-    env = L.Env("othello", 8, 8, n)
+    rows, cols = {"c4": (6, 7), "othello": (8, 8)}[game]
+    env = L.Env(game, rows, cols, n)
     rew = torch.empty(n, 2, device="cuda")
     term = torch.empty(n, dtype=torch.uint8, device="cuda")
     # advance a few plies so that the timed steps are mid-game
@@ -272,8 +328,29 @@ def bench_step_mode(L, steps, flush_buf):
     bytes_per = 20 + 20 + 8 + 1
     t = statistics.median(ms) / 1e3
     env.close()
-    return {"workload": "othello8x8_4194304env_random_step", "ms": statistics.median(ms),
+    return {"workload": f"{game}_{n}env_random_step", "ms": statistics.median(ms),
             "gbs": n * bytes_per / t / 1e9, "bytes_per_env_step": bytes_per, "env_steps_per_s": n / t}
+
+
+def bench_valuenet():
+    """The learned part: 2M training positions per game, 100k held-out
+    positions; value estimates/s of the truncated estimator (8 random plies,
+    then the net) and of full playouts at MAE <= 0.05 against a 256-playout
+    reference."""
+    from paper_2506_22609_b300 import valuenet as V
+
+    out = {}
+    for game in ("othello", "hex11"):
+        r = V.run(game)
+        ev = r["eval"]
+        out[game] = {"truncated_at_target": ev["truncated_at_target"], "full_at_target": ev["full_at_target"],
+                     "gain_estimates_per_s": ev.get("gain_estimates_per_s"), "net_only_mae": ev["net_only_mae"],
+                     "reference_noise_mae": ev["reference_noise_mae"], "target_mae": ev["target_mae"],
+                     "final_val_mae": r["history"][-1]["val_mae"], "train_seconds": round(r["train_seconds"], 3),
+                     "train_steps": r["train_steps"], "data_seconds": round(r["data_seconds"], 3),
+                     "n_train": r["n_train"], "n_eval": r["n_eval"],
+                     "all_truncated": ev["truncated"], "all_full": ev["full_playouts"]}
+    return out
 
 
 # ------------------------------------------------------------------ main --
@@ -304,12 +381,15 @@ def main():
     peaks, peak_kind = measured_peaks()
     flush_buf = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB
 
-    cfg = workload_cfg(args.workload) if args.workload != "mixed" else None
+    cfg = workload_cfg(args.workload) if args.workload not in ("mixed", "step_c4") else None
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
-        if cfg is not None:
+        if args.workload == "step_c4":
+            ms, steps_per_launch, n_envs = bench_step_workload(L, args.steps, args.warmup, flush_buf, rank)
+            wl_name, seed, launch = "connect4_6x7_16777216env_random_step_seed1", 1, {"block_threads": 256}
+        elif cfg is not None:
             env, lc, ms, steps_per_launch = bench_rollout_config(L, W, cfg, args.steps, args.warmup, flush_buf, rank)
             wl_name, n_envs, seed = cfg.name, cfg.num_envs, cfg.seed
             launch = lc.as_dict()
@@ -346,11 +426,19 @@ def main():
         ops_per_launch = None
     med = statistics.median(ms)
     roofline = None
+    if args.workload == "step_c4":
+        bytes_per = STEP_BYTES_PER_ENV
+        achieved = n_envs * bytes_per / (med / 1e3) / 1e9
+        peak = float(peaks.get("hbm_gbs", 6400.0))
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": NCU_TRAFFIC_BYTES.get(wl_name),
+                    "peak_source": f"hbm_gbs ({peak_kind})", "alg_bytes_per_env_step": bytes_per,
+                    "median_launch_ms": round(med, 5)}
     if ops_per_launch:
         achieved = ops_per_launch / (med / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_ops / 1e12, 3),
                     "unit": "Tops/s (32-bit integer)", "frac": round(achieved / (peak_ops / 1e12), 4),
-                    "traffic": None,
+                    "traffic": NCU_TRAFFIC_BYTES.get(wl_name),
                     "peak_source": f"{sms} SMs x 128 int32 lanes x {max_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
                     "alg_ops_per_step": ALG_OPS_PER_STEP[game_key(cfg)], "median_launch_ms": round(med, 5)}
 
@@ -363,16 +451,19 @@ def main():
                        "timing": "CUDA events around each launch on the launching stream, summed over steps",
                        "env_steps_per_launch": steps_per_launch, "episodes_per_launch": n_envs},
             "roofline": roofline, "clocks": clocks,
-            "gpu_launches": args.steps * (1 if cfg is not None else 2)}
+            "gpu_launches": args.steps * (2 if args.workload == "mixed" else 1)}
 
-    if rank == 0 and cfg is not None:
+    if rank == 0 and cfg is not None and args.workload != "step_c4":
         e2e_val, h2d, d2h, dt, _ = e2e_rollout(L, cfg, max(3, min(args.steps, 50)), 2, rank)
         line["e2e"] = {"value": round(e2e_val * world, 1), "unit": "env steps/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4),
                        "path": "pinned host start positions -> ludax_set_state -> ludax_rollout -> pinned host "
                                "outcome/plies, wall clock per step"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if cfg is not None:
+        if args.workload == "step_c4":
+            v, cores, sample = cpu_oracle_rate(W.C4_64K, args.cpu_seconds)
+            sample = "Connect Four playouts: " + sample
+        elif cfg is not None:
             v, cores, sample = cpu_oracle_rate(cfg, args.cpu_seconds)
         else:
             v, cores, sample = cpu_oracle_rate(W_mixed_cfg(W), args.cpu_seconds,
@@ -392,9 +483,12 @@ def main():
         m3 = statistics.median(ms3)
         extras["mixed6_1048576env_seed3_graph"] = {"env_steps_per_s": round(tot / (m3 / 1e3), 1),
                                                    "median_launch_ms": round(m3, 4), "env_steps_per_launch": tot}
-        sm = bench_step_mode(L, 10, flush_buf)
-        sm["hbm_frac"] = round(sm["gbs"] / float(peaks.get("hbm_gbs", 6400.0)), 4)
-        extras["step_mode"] = sm
+        for gname in ("c4", "othello"):
+            sm = bench_step_mode(L, 10, flush_buf, gname, 1 << 24 if gname == "c4" else 1 << 22)
+            sm["hbm_frac"] = round(sm["gbs"] / float(peaks.get("hbm_gbs", 6400.0)), 4)
+            extras["step_mode_" + gname] = sm
+        if not args.no_valuenet:
+            extras["value_net"] = bench_valuenet()
         line["extra_workloads"] = extras
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -105,10 +105,11 @@ typedef struct {
     int32_t envs_per_thread; /* envs each thread advances together (ILP): 1 or 2     */
     int32_t hex_nbr_table;   /* Hex neighbour test: 0 = bit shifts, 1 = shared-memory
                                 table of per-cell neighbour masks                     */
-    int32_t compact_every;   /* 0 = off; else every `compact_every` plies each block
-                                packs its unfinished envs into its lowest warps through
-                                shared memory (idle warps stop issuing) and refills the
-                                freed slots from the queue; needs envs_per_thread 1   */
+    int32_t compact_every;   /* single-game playouts only (0 for mixed batches): 0 =
+                                off; else every `compact_every` plies each block packs
+                                its unfinished envs into its lowest warps through shared
+                                memory (idle warps stop issuing) and refills the freed
+                                slots from the queue; needs envs_per_thread 1         */
 } ludax_launch_cfg;
 
 /* ---------------------------------------------------------------------------

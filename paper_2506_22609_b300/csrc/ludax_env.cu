@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
     const bool refill = slots < n;
     G g[EPT];
     uint64_t key[EPT];
+    uint32_t rhi[EPT];
     int stop[EPT];
     int64_t env[EPT];
     bool active[EPT];
@@ -207,6 +208,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
         if (a.from_start) g[i].reset();
         else load_state(g[i], a.d, e);
         key[i] = env_key(a.seed_key, (uint64_t)(a.d.env_offset + e));
+        rhi[i] = draw_hi(key[i], (uint32_t)g[i].ply);
         stop[i] = a.stop ? (int)a.stop[e] : 0x7FFF;
     };
 #pragma unroll
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
             if (!active[i]) continue;
             any_active = true;
             if (g[i].outcome == kOngoing && g[i].ply < stop[i]) {
-                random_ply(g[i], key[i]);
+                random_ply_pre(g[i], key[i], rhi[i]);
                 continue;
             }
             const int64_t e = env[i];
@@ -290,6 +292,7 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
     G g;
     set_table(g, table);
     uint64_t key = 0;
+    uint32_t rhi = 0;
     long long env = (long long)blockIdx.x * B + tid;
     int stop = 0;
     bool active = env < n;
@@ -297,6 +300,7 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
         if (a.from_start) g.reset();
         else load_state(g, a.d, env);
         key = env_key(a.seed_key, (uint64_t)(a.d.env_offset + env));
+        rhi = draw_hi(key, (uint32_t)g.ply);
         stop = a.stop ? (int)a.stop[env] : 0x7FFF;
     };
     if (active) init();
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 if (g.outcome != kOngoing || g.ply >= stop) break;
-                random_ply(g, key);
+                random_ply_pre(g, key, rhi);
             }
             if (g.outcome != kOngoing || g.ply >= stop) {
                 if (a.outcome) a.outcome[env] = (int8_t)g.outcome;
@@ -328,6 +332,7 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
         __syncthreads();
         if (tid < total) {
             slot_load(buf, B, tid, g, key, env, stop);
+            rhi = draw_hi(key, (uint32_t)g.ply);
             active = true;
         } else {
             active = false;
@@ -365,15 +370,17 @@ __global__ void __launch_bounds__(512) rollout_value_kernel(EnvDev d, uint64_t s
     int j = 0;
     g = g0;
     uint64_t key = env_key(splitmix64(seed), genv);
+    uint32_t rhi = draw_hi(key, (uint32_t)g.ply);
     while (j < R) {
         if (g.outcome == kOngoing) {
-            random_ply(g, key);
+            random_ply_pre(g, key, rhi);
             continue;
         }
         acc += p1_score(g.outcome);
         ++j;
         g = g0;
         key = env_key(splitmix64(seed + (uint64_t)j), genv);
+        rhi = draw_hi(key, (uint32_t)g.ply);
     }
     value[e] = R > 0 ? acc / (float)R : 0.f;
 }

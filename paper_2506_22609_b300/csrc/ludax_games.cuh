@@ -444,4 +444,24 @@ __device__ __forceinline__ void random_ply(G& g, uint64_t key) {
     if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
 }
 
+// The same ply with the draw software-pipelined: rhi holds the top 32 bits of
+// this ply's draw (computed one ply ahead); the next ply's draw is started
+// here, independent of the board work, and handed back through rhi.  The
+// result is identical to random_ply.
+__device__ __forceinline__ uint32_t draw_hi(uint64_t key, uint32_t ply) {
+    return (uint32_t)(splitmix64(key ^ (uint64_t)ply) >> 32);
+}
+template <class G>
+__device__ __forceinline__ void random_ply_pre(G& g, uint64_t key, uint32_t& rhi) {
+    const uint32_t rnext = draw_hi(key, (uint32_t)g.ply + 1u);
+    typename G::Mask m = g.legal();
+    if (G::kHasPass && !any(m)) {
+        g.pass();
+    } else {
+        g.place(select_bit(m, __umulhi(rhi, popc(m))));
+    }
+    if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
+    rhi = rnext;
+}
+
 }  // namespace ludax

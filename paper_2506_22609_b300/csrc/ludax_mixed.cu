@@ -52,10 +52,9 @@ struct MixedArgs {
     uint64_t seed_key;
     int8_t* outcome;
     int16_t* plies;
-    unsigned long long* cursor;      // [kBuckets] claim cursors, zeroed before each launch
-    int R;                           // plies per compaction round (compacting kernel only)
+    unsigned long long* cursor;      // claim cursor (word 0), zeroed before each launch
 };
-// Every mixed kernel takes exactly one parameter (MixedArgs): the graph plan
+// The mixed kernel takes exactly one parameter (MixedArgs): the graph plan
 // rewrites that single parameter before each replay.
 
 __device__ __forceinline__ int bucket_at(const MixedArgs& a, long long q) {
@@ -75,9 +74,10 @@ __device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q,
     long long e = a.queue[q];
     g.reset();
     uint64_t key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
+    uint32_t rhi = draw_hi(key, 0u);
     for (;;) {
         if (g.outcome == kOngoing) {
-            random_ply(g, key);
+            random_ply_pre(g, key, rhi);
             continue;
         }
         a.outcome[e] = (int8_t)g.outcome;
@@ -87,6 +87,7 @@ __device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q,
         e = a.queue[q];
         g.reset();
         key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
+        rhi = draw_hi(key, 0u);
     }
 }
 
@@ -136,143 +137,6 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
     }
 }
 
-// ---------------------------------------------------- compacting variant --
-// Each block works through the buckets in order.  Within a bucket phase all
-// of its threads play the same game: they claim queue positions of that
-// bucket from the bucket's own cursor, play R plies per round, and between
-// rounds the block packs its unfinished envs into its lowest warps through
-// shared memory and refills the freed slots.  The block moves to the next
-// bucket when the bucket's queue is exhausted and its last env is finished.
-constexpr int kMaxSlotWords = 15;  // Hex: 13 state words + key + env|stop
-
-template <class G>
-__device__ __forceinline__ void mslot_store(uint64_t* buf, int B, int pos, const G& g, uint64_t key, long long e) {
-    uint64_t w[G::kWords];
-    g.save(w);
-#pragma unroll
-    for (int i = 0; i < G::kWords; ++i) buf[i * B + pos] = w[i];
-    buf[G::kWords * B + pos] = key;
-    buf[(G::kWords + 1) * B + pos] = (uint64_t)e;
-}
-template <class G>
-__device__ __forceinline__ void mslot_load(const uint64_t* buf, int B, int pos, G& g, uint64_t& key, long long& e) {
-    uint64_t w[G::kWords];
-#pragma unroll
-    for (int i = 0; i < G::kWords; ++i) w[i] = buf[i * B + pos];
-    g.load(w);
-    key = buf[G::kWords * B + pos];
-    e = (long long)buf[(G::kWords + 1) * B + pos];
-}
-
-// claim the next queue position of a bucket; false (and the bucket marked
-// exhausted for the block) when none is left
-template <class G>
-__device__ __forceinline__ bool claim_env(const MixedArgs& a, unsigned long long* cursor, long long begin,
-                                          long long end, int* sh, G& g, uint64_t& key, long long& e) {
-    long long q = begin + claim_next(cursor);
-    if (q >= end) {
-        sh[16] = 1;
-        return false;
-    }
-    e = a.queue[q];
-    g.reset();
-    key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
-    return true;
-}
-
-template <class G>
-__device__ __forceinline__ void run_bucket_compact(const MixedArgs& a, int b, int R, uint64_t* buf, int* sh, const B128* table) {
-    const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = B >> 5;
-    const long long begin = b == 0 ? 0 : a.bucket_end[b - 1], end = a.bucket_end[b];
-    unsigned long long* cursor = a.cursor + b;
-    if (tid == 0) sh[16] = 0;  // bucket exhausted flag
-    __syncthreads();
-    G g;
-    set_table(g, table);
-    uint64_t key = 0;
-    long long e = 0;
-    bool active = claim_env(a, cursor, begin, end, sh, g, key, e);
-    if (!__syncthreads_or(active)) return;
-    for (;;) {
-        if (active) {
-#pragma unroll 1
-            for (int r = 0; r < R; ++r) {
-                if (g.outcome != kOngoing) break;
-                random_ply(g, key);
-            }
-            if (g.outcome != kOngoing) {
-                a.outcome[e] = (int8_t)g.outcome;
-                a.plies[e] = (int16_t)g.ply;
-                active = false;
-            }
-        }
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, active);
-        if (lane == 0) sh[warp] = __popc(ball);
-        __syncthreads();
-        int prefix = 0, total = 0;
-        for (int w = 0; w < nwarps; ++w) {
-            int c = sh[w];
-            prefix += w < warp ? c : 0;
-            total += c;
-        }
-        if (active) mslot_store(buf, B, prefix + __popc(ball & ((1u << lane) - 1u)), g, key, e);
-        __syncthreads();
-        if (tid < total) {
-            mslot_load(buf, B, tid, g, key, e);
-            active = true;
-        } else {
-            active = !sh[16] && claim_env(a, cursor, begin, end, sh, g, key, e);
-        }
-        if (!__syncthreads_or(active)) break;
-    }
-}
-
-template <bool TABLE>
-__global__ void __launch_bounds__(512) mixed_compact_kernel(MixedArgs a) {
-    const int R = a.R;
-    extern __shared__ __align__(16) uint64_t smem64[];
-    const int B = blockDim.x;
-    uint64_t* buf = smem64;
-    int* sh = reinterpret_cast<int*>(smem64 + kMaxSlotWords * B);  // [16] warp counts, [16] flag
-    B128* tables = reinterpret_cast<B128*>(sh + 32);
-    if constexpr (TABLE) {
-        hex_fill_table<2>(tables + hex_table_offset(2));
-        hex_fill_table<3>(tables + hex_table_offset(3));
-        hex_fill_table<4>(tables + hex_table_offset(4));
-        hex_fill_table<5>(tables + hex_table_offset(5));
-        hex_fill_table<6>(tables + hex_table_offset(6));
-        hex_fill_table<7>(tables + hex_table_offset(7));
-        hex_fill_table<8>(tables + hex_table_offset(8));
-        hex_fill_table<9>(tables + hex_table_offset(9));
-        hex_fill_table<10>(tables + hex_table_offset(10));
-        hex_fill_table<11>(tables + hex_table_offset(11));
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int b = 0; b < kBuckets; ++b) {
-        long long begin = b == 0 ? 0 : a.bucket_end[b - 1];
-        if (a.bucket_end[b] == begin) continue;
-        const B128* t = nullptr;
-        if (TABLE && b >= 3) t = tables + hex_table_offset(b - 1);
-        switch (b) {
-        case 0: run_bucket_compact<TTT>(a, b, R, buf, sh, nullptr); break;
-        case 1: run_bucket_compact<C4>(a, b, R, buf, sh, nullptr); break;
-        case 2: run_bucket_compact<Othello>(a, b, R, buf, sh, nullptr); break;
-        case 3: run_bucket_compact<Hex<2>>(a, b, R, buf, sh, t); break;
-        case 4: run_bucket_compact<Hex<3>>(a, b, R, buf, sh, t); break;
-        case 5: run_bucket_compact<Hex<4>>(a, b, R, buf, sh, t); break;
-        case 6: run_bucket_compact<Hex<5>>(a, b, R, buf, sh, t); break;
-        case 7: run_bucket_compact<Hex<6>>(a, b, R, buf, sh, t); break;
-        case 8: run_bucket_compact<Hex<7>>(a, b, R, buf, sh, t); break;
-        case 9: run_bucket_compact<Hex<8>>(a, b, R, buf, sh, t); break;
-        case 10: run_bucket_compact<Hex<9>>(a, b, R, buf, sh, t); break;
-        case 11: run_bucket_compact<Hex<10>>(a, b, R, buf, sh, t); break;
-        default: run_bucket_compact<Hex<11>>(a, b, R, buf, sh, t); break;
-        }
-        __syncthreads();
-    }
-}
-
 int mixed_grid(long long n, const ludax_launch_cfg& c, int num_sms) {
     long long need = (n + c.block_threads - 1) / c.block_threads;
     if (c.blocks_per_sm > 0) need = std::min<long long>(need, (long long)num_sms * c.blocks_per_sm);
@@ -284,7 +148,7 @@ int check_mixed_cfg(const ludax_launch_cfg& c) {
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return LUDAX_ERR_ARG;
     if (c.envs_per_thread != 1) return LUDAX_ERR_ARG;  // the mixed kernel runs one env per lane
     if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
-    if (c.compact_every < 0 || c.compact_every > 256) return LUDAX_ERR_ARG;
+    if (c.compact_every != 0) return LUDAX_ERR_ARG;  // compaction is a single-game option
     return LUDAX_OK;
 }
 
@@ -318,30 +182,9 @@ int build_queue(const int32_t* desc_dev, long long n, std::vector<int32_t>& queu
 
 int launch_mixed(const MixedArgs& a, const ludax_launch_cfg& c, int num_sms, cudaStream_t s) {
     int grid = mixed_grid(a.n, c, num_sms);
-    MixedArgs ar = a;
-    ar.R = c.compact_every;
     if (cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long) * kBuckets, s) != cudaSuccess) return LUDAX_ERR_CUDA;
-    if (c.compact_every > 0) {
-        size_t smem = sizeof(uint64_t) * kMaxSlotWords * c.block_threads + 32 * sizeof(int) +
-                      (c.hex_nbr_table ? sizeof(B128) * kHexTableCells : 0);
-        if (c.hex_nbr_table) {
-            auto k = mixed_compact_kernel<true>;
-            if (smem > 48 * 1024 &&
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-                return LUDAX_ERR_CUDA;
-            k<<<grid, c.block_threads, smem, s>>>(ar);
-        } else {
-            auto k = mixed_compact_kernel<false>;
-            if (smem > 48 * 1024 &&
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-                return LUDAX_ERR_CUDA;
-            k<<<grid, c.block_threads, smem, s>>>(ar);
-        }
-    } else if (c.hex_nbr_table) {
-        mixed_rollout_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
-    } else {
-        mixed_rollout_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
-    }
+    if (c.hex_nbr_table) mixed_rollout_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
+    else mixed_rollout_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
@@ -456,7 +299,6 @@ int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int
     a.outcome = nullptr;
     a.plies = nullptr;
     a.cursor = p->d_cursor;
-    a.R = c.compact_every;
     // capture cursor reset + kernel on a private stream
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -524,17 +366,14 @@ int ludax_mixed_plan_destroy(ludax_mixed_plan* p) {
 int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out) {
     static const int blocks[] = {64, 128, 256, 512};
     static const int bps[] = {0, 2, 4, 8, 16};
-    static const int compacts[] = {0, 8, 16};
     int k = 0;
-    for (int ce : compacts)
-        for (int t = 0; t < 2; ++t)
-            for (int b : blocks)
-                for (int s : bps) {
-                    if (s > 0 && b * s > 2048) continue;  // more than one SM's threads
-                    if (ce > 0 && s == 0) continue;       // compaction pays off in persistent grids
-                    if (out && k < max_out) out[k] = ludax_launch_cfg{b, s, 1, t, ce};
-                    ++k;
-                }
+    for (int t = 0; t < 2; ++t)
+        for (int b : blocks)
+            for (int s : bps) {
+                if (s > 0 && b * s > 2048) continue;  // more than one SM's threads
+                if (out && k < max_out) out[k] = ludax_launch_cfg{b, s, 1, t, 0};
+                ++k;
+            }
     return k;
 }
 
@@ -724,6 +563,6 @@ extern "C" int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_
     a.seed_key = splitmix64(seed);
     a.outcome = outcome_dev;
     a.plies = plies_dev;
-    a.cursor = ctr;  // words 0..12: zeroed by launch_mixed before the kernel
+    a.cursor = ctr;  // zeroed by launch_mixed before the kernel
     return launch_mixed(a, c, sms, s);
 }

@@ -382,7 +382,8 @@ __global__ void leaf_kernel(EnvDev d, long long e0, long long n_chunk, int K, ui
     load_state(g, d, e);
     uint64_t key = env_key(splitmix64(seed + (uint64_t)j), (uint64_t)(d.env_offset + e));
     int stop = g.ply + plies;
-    while (g.outcome == kOngoing && g.ply < stop) random_ply(g, key);
+    uint32_t rhi = draw_hi(key, (uint32_t)g.ply);
+    while (g.outcome == kOngoing && g.ply < stop) random_ply_pre(g, key, rhi);
     if (g.outcome != kOngoing) {
         score[t] = p1_score(g.outcome);
         done[t] = 1;

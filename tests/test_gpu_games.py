@@ -268,8 +268,7 @@ def test_mixed_batch_matches_oracle(L, layout):
     L.ludax_rollout_mixed(dd, off, seed, out, plies)
     torch.cuda.synchronize()
     assert (np_(out) == o_out).all() and (np_(plies) == o_plies).all()
-    for cfg in [(128, 2, 1, 1, 0), (64, 1, 1, 0, 0), (512, 0, 1, 1, 0), (256, 2, 1, 0, 8), (128, 1, 1, 1, 16),
-                (64, 3, 1, 0, 1)]:
+    for cfg in [(128, 2, 1, 1, 0), (64, 1, 1, 0, 0), (512, 0, 1, 1, 0), (256, 4, 1, 0, 0), (32, 1, 1, 1, 0)]:
         plan = L.ludax_mixed_plan_create(dd, off, L.make_cfg(*cfg))
         for s2 in (seed, seed + 1):
             out2 = torch.full((n,), 99, dtype=torch.int8, device="cuda")

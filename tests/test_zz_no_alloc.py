@@ -51,9 +51,9 @@ def test_noalloc_matches_allocating_entry_point_twice(L, layout):
         assert torch.equal(oo, ro) and torch.equal(op, rp)
 
 
-def test_noalloc_full_config_and_compacting_shape(L):
+def test_noalloc_full_config_and_persistent_shape(L):
     d = torch.from_numpy(W.mixed_descriptors(W.MIXED_ENVS, "block")).cuda()
-    for cfg in (L.make_cfg(*W.mixed_bench_cfg()), L.make_cfg(128, 2, 1, 1, 8)):
+    for cfg in (L.make_cfg(*W.mixed_bench_cfg()), L.make_cfg(128, 2, 1, 1, 0)):
         (ro, rp), (oo, op) = run_both(L, d, 0, W.MIXED_SEED, cfg)
         assert torch.equal(oo, ro) and torch.equal(op, rp)
 
