@@ -180,6 +180,12 @@ def cpu_oracle_rate(cfg, seconds, desc=None):
 
 
 # ------------------------------------------------------------- GPU parts --
+def D_shard(rank, n):
+    from paper_2506_22609_b300 import dist as D
+
+    return D.shard_offset(rank, n)
+
+
 def flush_l2(buf):
     buf.add_(1)  # 256 MiB read + write: evicts the 126 MB L2
 
@@ -205,7 +211,7 @@ def bench_rollout_config(L, W, cfg, steps, warmup, flush_buf, rank=0):
     import torch
 
     n = cfg.num_envs
-    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=rank * n)
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=D_shard(rank, n))
     lc = L.make_cfg(*W.bench_cfg(cfg))
     out = torch.empty(n, dtype=torch.int8, device="cuda")
     plies = torch.empty(n, dtype=torch.int16, device="cuda")
@@ -224,7 +230,7 @@ def e2e_rollout(L, cfg, steps, warmup, rank=0):
 
     n = cfg.num_envs
     cells = cfg.rows * cfg.cols
-    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=rank * n)
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=D_shard(rank, n))
     # start positions, built on the host from the game's own start rule
     b0, tm0, ply0, ps0, oc0 = env.get_state()
     host_in = [t.cpu().pin_memory() for t in (b0, tm0, ply0, ps0, oc0)]
@@ -264,7 +270,7 @@ def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
     import torch
 
     d = torch.from_numpy(W.mixed_descriptors(W.MIXED_ENVS, "block")).cuda()
-    plan = L.ludax_mixed_plan_create(d, rank * W.MIXED_ENVS, L.make_cfg(*W.mixed_bench_cfg()))
+    plan = L.ludax_mixed_plan_create(d, D_shard(rank, W.MIXED_ENVS), L.make_cfg(*W.mixed_bench_cfg()))
     out = torch.empty(W.MIXED_ENVS, dtype=torch.int8, device="cuda")
     plies = torch.empty(W.MIXED_ENVS, dtype=torch.int16, device="cuda")
     fn = lambda: L.ludax_mixed_plan_launch(plan, W.MIXED_SEED, out, plies)  # noqa: E731
@@ -284,7 +290,7 @@ def bench_step_workload(L, steps, warmup, flush_buf, rank=0, n=1 << 24):
     taken on a batch reset and advanced 4 plies outside the timed events."""
     import torch
 
-    env = L.Env("c4", 6, 7, n, env_offset=rank * n)
+    env = L.Env("c4", 6, 7, n, env_offset=D_shard(rank, n))
     rew = torch.empty(n, 2, device="cuda")
     term = torch.empty(n, dtype=torch.uint8, device="cuda")
 
@@ -356,9 +362,9 @@ def bench_valuenet():
 # ------------------------------------------------------------------ main --
 def main():
     args = parse()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2506_22609_b300 import dist as D
+
+    rank, world, local = D.world_info()
 
     if args.impl == "reference":
         if rank != 0:
@@ -403,17 +409,7 @@ def main():
             dist.barrier()
     clocks = clk.record()
 
-    total_ms = sum(ms)
-    mean_ms = total_ms / len(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        s = torch.tensor([steps_per_launch], dtype=torch.float64, device="cuda")
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        all_steps = float(s.item())
-    else:
-        all_steps = float(steps_per_launch)
+    total_ms, all_steps = D.aggregate(sum(ms), steps_per_launch, device="cuda")
     value = all_steps * args.steps / (total_ms / 1e3)
 
     # roofline of the fused playout kernel: integer issue
