@@ -338,6 +338,35 @@ def bench_step_mode(L, steps, flush_buf, game="c4", n=1 << 24):
             "gbs": n * bytes_per / t / 1e9, "bytes_per_env_step": bytes_per, "env_steps_per_s": n / t}
 
 
+def bench_dense(L, peaks, flush_buf, M=65536, N=512, K=512):
+    """The value net's hidden layer (M x N x K BF16 -> FP32 -> bias, ReLU, BF16)
+    on the tcgen05 kernel, and the full net forward on both tensor paths."""
+    import torch
+
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a = (torch.randn(M, K, device="cuda", generator=g) * 0.5).to(torch.bfloat16).view(torch.int16)
+    b = (torch.randn(N, K, device="cuda", generator=g) * 0.05).to(torch.bfloat16).view(torch.int16)
+    bias = torch.zeros(N, device="cuda")
+    out = torch.empty(M, N, dtype=torch.int16, device="cuda")
+    ms = time_steps(lambda: L.ludax_dense_bf16_relu(a, b, bias, out), 20, 3, flush_buf, torch.cuda.current_stream())
+    t = statistics.median(ms) / 1e3
+    tflops = 2.0 * M * N * K / t / 1e12
+    res = {"shape": [M, N, K], "median_ms": round(t * 1e3, 4), "tflops": round(tflops, 1),
+           "frac_of_bf16_peak": round(tflops / float(peaks.get("bf16_tflops", 1800.0)), 4),
+           "device_error": L.ludax_device_error()}
+    net = L.Net(64, M)
+    x = torch.zeros(M, net.in_pad, dtype=torch.int16, device="cuda")
+    flops = 2.0 * M * (net.in_pad * 512 + 512 * 512 + 512)
+    for path in (True, False):
+        net.set_tensor_path(path)
+        msf = time_steps(lambda: net.forward(x), 10, 2, flush_buf, torch.cuda.current_stream())
+        tf = statistics.median(msf) / 1e3
+        res["net_forward_" + ("tcgen05" if path else "mma_sync")] = {"median_ms": round(tf * 1e3, 4),
+                                                                    "tflops": round(flops / tf / 1e12, 1)}
+    net.close()
+    return res
+
+
 def bench_valuenet():
     """The learned part: 2M training positions per game, 100k held-out
     positions; value estimates/s of the truncated estimator (8 random plies,
@@ -483,6 +512,7 @@ def main():
             sm = bench_step_mode(L, 10, flush_buf, gname, 1 << 24 if gname == "c4" else 1 << 22)
             sm["hbm_frac"] = round(sm["gbs"] / float(peaks.get("hbm_gbs", 6400.0)), 4)
             extras["step_mode_" + gname] = sm
+        extras["dense_layer"] = bench_dense(L, peaks, flush_buf)
         if not args.no_valuenet:
             extras["value_net"] = bench_valuenet()
         line["extra_workloads"] = extras

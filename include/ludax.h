@@ -309,6 +309,10 @@ int ludax_net_sizes(const ludax_net* net, int32_t* in_pad, int32_t* hidden, int6
  * and step count; get_params copies the FP32 masters out. */
 int ludax_net_set_params(ludax_net* net, const float* params_dev);
 int ludax_net_get_params(ludax_net* net, float* params_dev);
+/* Which kernel runs the forward hidden layers: 1 (default) the tcgen05/TMEM
+ * kernel of ludax_dense_bf16_relu, 0 the mma.sync kernel (kept for
+ * comparison; the backward pass uses the mma.sync kernel). */
+int ludax_net_set_tensor_path(ludax_net* net, int32_t use_tcgen05);
 /* p_dev float [B]: predicted P(P1 wins) for the input rows x_dev (bf16 bits,
  * uint16 [B][in_pad], 16-byte aligned). */
 int ludax_net_forward(ludax_net* net, const uint16_t* x_dev, int64_t B, float* p_dev);
@@ -330,6 +334,20 @@ int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld);
  * at the leaf.  value_dev float [num_envs] = mean over the K continuations.
  * The env and the net must share a stream and the env's board size. */
 int ludax_truncated_value(ludax_env* env, ludax_net* net, uint64_t seed, int32_t K, int32_t plies, float* value_dev);
+
+/* Dense BF16 layer on the tcgen05 tensor cores (the value net's forward
+ * layers): out[m][n] = bf16(relu(sum_k a[m][k] * b[n][k] + bias[n])), FP32
+ * accumulation.  a uint16 (bf16 bits) [M][K], b [N][K], bias float [N], out
+ * [M][ld_out]; M % 128 == 0, N % 256 == 0, K % 64 == 0, 16-byte aligned
+ * pointers, ld_out % 8 == 0 (LUDAX_ERR_SIZE otherwise).  Asynchronous on
+ * `stream`.  The kernel bounds every internal wait; an expired wait is
+ * reported by ludax_device_error. */
+int ludax_dense_bf16_relu(const uint16_t* a_dev, const uint16_t* b_dev, const float* bias_dev, uint16_t* out_dev,
+                          int32_t M, int32_t N, int32_t K, int32_t ld_out, void* stream);
+/* Reads and clears the device error word of the tensor-core kernels
+ * (synchronising): LUDAX_OK, or LUDAX_ERR_TIMEOUT when a kernel gave up on
+ * an internal wait since the last call; error_out (nullable) gets the word. */
+int ludax_device_error(int32_t* error_out);
 
 #ifdef __cplusplus
 }

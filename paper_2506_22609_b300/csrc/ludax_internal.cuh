@@ -49,4 +49,10 @@ int dispatch_game(int game, int rows, int cols, F&& f) {
     }
 }
 
+// dense BF16 layer on tcgen05 tensor cores (ludax_umma.cu):
+// out = bf16(relu(A . B^T + bias)), A [M][K], B [N][K] row-major
+bool umma_dense_supported(int M, int N, int K);
+int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, int M, int N, int K, int ldo,
+                    cudaStream_t s);
+
 }  // namespace ludax

@@ -412,6 +412,7 @@ unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 struct ludax_net {
     int cells, kin, kpad;
+    int use_tcgen05;  // forward layers on tcgen05 (1, default) or mma.sync (0)
     long long max_batch;
     cudaStream_t stream;
     long long nparams;
@@ -441,16 +442,23 @@ int refresh_bf16(ludax_net* n) {
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
+// One hidden layer out = bf16(relu(A . W^T + b)): on the tcgen05 tensor
+// cores (TMA + TMEM) when the shape allows, else the mma.sync kernel.
+int dense_layer(ludax_net* n, const __nv_bfloat16* A, const __nv_bfloat16* W, const float* b, __nv_bfloat16* out,
+                long long B, int K) {
+    if (n->use_tcgen05 && umma_dense_supported((int)B, kH, K))
+        return umma_dense_relu(A, W, b, out, (int)B, kH, K, kH, n->stream);
+    GemmArgs a{};
+    a.A = A; a.B = W; a.M = (int)B; a.N = kH; a.K = K; a.lda = K; a.ldb = K; a.bias = b; a.out = out; a.ldo = kH;
+    return launch_gemm<true, true, EPI_BIAS_RELU>(a, 1, n->stream);
+}
+
 // Forward pass to p (and, with labels y, the per-row gradient g3 of the loss).
 int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, const float* y) {
     cudaStream_t s = n->stream;
-    GemmArgs a{};
-    a.A = X; a.B = n->W1b; a.M = (int)B; a.N = kH; a.K = n->kpad; a.lda = n->kpad; a.ldb = n->kpad;
-    a.bias = n->p + n->ob1; a.out = n->H1; a.ldo = kH;
-    int st = launch_gemm<true, true, EPI_BIAS_RELU>(a, 1, s);
+    int st = dense_layer(n, X, n->W1b, n->p + n->ob1, n->H1, B, n->kpad);
     if (st) return st;
-    a.A = n->H1; a.B = n->W2b; a.K = kH; a.lda = kH; a.ldb = kH; a.bias = n->p + n->ob2; a.out = n->H2;
-    if ((st = launch_gemm<true, true, EPI_BIAS_RELU>(a, 1, s))) return st;
+    if ((st = dense_layer(n, n->H1, n->W2b, n->p + n->ob2, n->H2, B, kH))) return st;
     head_forward_kernel<<<blocks_for(B, 8), 256, 0, s>>>(n->H2, n->w3b, n->p + n->ob3, (int)B, p, y, n->g3, n->sqerr);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
@@ -504,6 +512,7 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
     n->kpad = ((n->kin + 127) / 128) * 128;
     n->max_batch = max_batch;
     n->stream = (cudaStream_t)stream;
+    n->use_tcgen05 = 1;
     n->oW1 = 0;
     n->ob1 = n->oW1 + (long long)kH * n->kpad;
     n->oW2 = n->ob1 + kH;
@@ -582,6 +591,12 @@ int ludax_net_set_params(ludax_net* n, const float* params_dev) {
         return LUDAX_ERR_CUDA;
     n->t = 0;
     return refresh_bf16(n);
+}
+
+int ludax_net_set_tensor_path(ludax_net* n, int32_t use_tcgen05) {
+    if (!n || (use_tcgen05 != 0 && use_tcgen05 != 1)) return LUDAX_ERR_ARG;
+    n->use_tcgen05 = use_tcgen05;
+    return LUDAX_OK;
 }
 
 int ludax_net_get_params(ludax_net* n, float* params_dev) {

@@ -1,0 +1,311 @@
+// ludax_umma.cu -- dense BF16 layer on the 5th-generation tensor cores:
+//   out[m][n] = bf16( relu( sum_k A[m][k] * B[n][k] + bias[n] ) )
+// A [M][K] and B [N][K] are row-major (K contiguous) BF16, FP32 accumulation.
+//
+// Persistent, warp-specialised kernel: one CTA per SM walks 128 x 256 output
+// tiles (tile t covers rows 128*(t / (N/256)) and columns 256*(t % (N/256))).
+//   warp 0    : TMA producer -- streams 128x64 (A) and 256x64 (B) K-slices
+//               (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage
+//               shared-memory ring guarded by full/empty mbarriers;
+//   warp 1    : MMA issuer -- one thread issues tcgen05.mma (kind::f16,
+//               M=128, N=256, K=16) into one of two 256-column FP32
+//               accumulators in TMEM, frees ring stages with tcgen05.commit
+//               and signals the finished accumulator;
+//   warps 2-5 : epilogue -- drain the finished accumulator with tcgen05.ld
+//               (each warp its quarter of the 128 TMEM lanes = rows), add the
+//               bias, ReLU, round to BF16, store; then hand the accumulator
+//               back, so the epilogue of tile i overlaps the MMAs of tile i+1.
+// Every mbarrier wait is bounded (about a second of clock); on expiry the
+// kernel records an error in a device word and stops issuing work, so a
+// fault in the pipeline surfaces as a status instead of a hang.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ludax_internal.cuh"
+
+namespace {
+
+constexpr int TM = 128, TN = 256, TK = 64, TSTAGES = 4, UMMA_THREADS = 192;
+constexpr int A_TILE = TM * TK * 2, B_TILE = TN * TK * 2, STAGE = A_TILE + B_TILE;
+constexpr int TMEM_COLS = 2 * TN;  // two accumulators
+constexpr size_t UMMA_SMEM = (size_t)TSTAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
+constexpr long long kWaitLimit = 2000000000ll;  // clock cycles (~1 s at 2 GHz)
+
+static __device__ int g_umma_error;  // nonzero after a wait expired
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase with the given parity to complete; false after kWaitLimit cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitLimit) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];\n" ::
+            "r"(saddr(dst)),
+        "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA
+// with 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, N = TN, M = TM.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(UMMA_THREADS, 1)
+    umma_dense_relu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+                           int N, int K, const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int ldo) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + TSTAGES * STAGE);
+    uint64_t* empty = full + TSTAGES;
+    uint64_t* acc_full = empty + TSTAGES;  // [2] MMA -> epilogue
+    uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ktiles = K / TK, ntn = N / TN, ntiles = (M / TM) * ntn;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TSTAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 128);  // every epilogue thread arrives
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int m0 = (t / ntn) * TM, n0 = (t % ntn) * TN;
+                for (int kt = 0; kt < ktiles && ok; ++kt, ++it) {
+                    const int s = it % TSTAGES;
+                    if (it >= TSTAGES) ok = mbar_wait(&empty[s], (uint32_t)(((it / TSTAGES) & 1) ^ 1));
+                    if (!ok) break;
+                    uint8_t* st = smem + s * STAGE;
+                    mbar_expect_tx(&full[s], STAGE);
+                    tma_load_2d(st, &tmA, &full[s], kt * TK, m0);
+                    tma_load_2d(st + A_TILE, &tmB, &full[s], kt * TK, n0);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int it = 0, local = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++local) {
+                const int a = local & 1;
+                if (local >= 2) ok = mbar_wait(&acc_empty[a], (uint32_t)(((local >> 1) & 1) ^ 1));
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * TN);
+                for (int kt = 0; kt < ktiles && ok; ++kt, ++it) {
+                    const int s = it % TSTAGES;
+                    ok = mbar_wait(&full[s], (uint32_t)((it / TSTAGES) & 1));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t sa = saddr(smem + s * STAGE);
+                    const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_TILE);
+#pragma unroll
+                    for (int kk = 0; kk < TK / 16; ++kk)  // 16 elements = 32 bytes = 2 descriptor units
+                        umma_bf16(d, ad + 2 * kk, bd + 2 * kk, (kt | kk) != 0);
+                    umma_commit(&empty[s]);
+                }
+                umma_commit(&acc_full[a]);
+            }
+        }
+    } else {  // epilogue warps 2..5: TMEM lane quarter = warp % 4
+        const int q = warp & 3;
+        int local = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++local) {
+            const int a = local & 1;
+            if (ok) ok = mbar_wait(&acc_full[a], (uint32_t)((local >> 1) & 1));
+            ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            const int row = (t / ntn) * TM + q * 32 + lane, n0 = (t % ntn) * TN;
+            __nv_bfloat16* orow = out + (size_t)row * ldo + n0;
+            const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < TN / 32; ++c) {
+                uint32_t r[32];
+                tmem_ld32(base + (uint32_t)(c * 32), r);
+                __align__(16) __nv_bfloat162 v[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c * 32 + 2 * j;
+                    float x0 = fmaxf(__uint_as_float(r[2 * j]) + __ldg(bias + col), 0.f);
+                    float x1 = fmaxf(__uint_as_float(r[2 * j + 1]) + __ldg(bias + col + 1), 0.f);
+                    v[j] = __floats2bfloat162_rn(x0, x1);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(orow + c * 32);
+                const uint4* src = reinterpret_cast<const uint4*>(v);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dst[k] = src[k];
+            }
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
+        }
+    }
+    if (!ok) atomicOr(&g_umma_error, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// ------------------------------------------------------------ host side --
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][cols] matrix with a box of
+// box_rows x 64 columns and 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows) {
+    EncodeTiled fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+namespace ludax {
+
+bool umma_dense_supported(int M, int N, int K) { return M > 0 && N > 0 && K > 0 && M % TM == 0 && N % TN == 0 && K % TK == 0; }
+
+int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, int M, int N, int K, int ldo,
+                    cudaStream_t s) {
+    if (!umma_dense_supported(M, N, K) || ldo % 8 || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)out % 16))
+        return LUDAX_ERR_SIZE;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K, TM) || !make_map(&mb, B, N, K, TN)) return LUDAX_ERR_CUDA;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(umma_dense_relu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UMMA_SMEM) !=
+            cudaSuccess)
+            return LUDAX_ERR_CUDA;
+        attr = true;
+    }
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return LUDAX_ERR_CUDA;
+    }
+    const int ntiles = (M / TM) * (N / TN);
+    const int grid = ntiles < sms ? ntiles : sms;
+    umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, M, N, K, bias,
+                                                                 reinterpret_cast<__nv_bfloat16*>(out), ldo);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+}  // namespace ludax
+
+extern "C" {
+
+int ludax_dense_bf16_relu(const uint16_t* a_dev, const uint16_t* b_dev, const float* bias_dev, uint16_t* out_dev,
+                          int32_t M, int32_t N, int32_t K, int32_t ld_out, void* stream) {
+    if (!a_dev || !b_dev || !bias_dev || !out_dev) return LUDAX_ERR_ARG;
+    return ludax::umma_dense_relu(a_dev, b_dev, bias_dev, out_dev, M, N, K, ld_out, (cudaStream_t)stream);
+}
+
+int ludax_device_error(int32_t* error_out) {
+    int h = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&h, g_umma_error, sizeof(int)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_umma_error, &z, sizeof(int)) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    if (error_out) *error_out = h;
+    return h ? LUDAX_ERR_TIMEOUT : LUDAX_OK;
+}
+
+}  // extern "C"

@@ -102,11 +102,14 @@ def lib() -> ctypes.CDLL:
         "ludax_net_sizes": [vp, P(i32), P(i32), P(i64)],
         "ludax_net_set_params": [vp, vp],
         "ludax_net_get_params": [vp, vp],
+        "ludax_net_set_tensor_path": [vp, i32],
         "ludax_net_forward": [vp, vp, i64, vp],
         "ludax_net_grad": [vp, vp, vp, i64, vp, vp],
         "ludax_net_train_step": [vp, vp, vp, i64, ctypes.c_float, vp],
         "ludax_pack_inputs": [vp, vp, i32],
         "ludax_truncated_value": [vp, vp, u64, i32, i32, vp],
+        "ludax_dense_bf16_relu": [vp, vp, vp, vp, i32, i32, i32, i32, vp],
+        "ludax_device_error": [P(i32)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -336,6 +339,19 @@ def ludax_truncated_value(env_h, net_h, seed: int, K: int, plies: int, value):
     _check(lib().ludax_truncated_value(env_h, net_h, seed, K, plies, _ptr(value)), "ludax_truncated_value")
 
 
+def ludax_dense_bf16_relu(a, b, bias, out, stream=None):
+    M, K = a.shape
+    N = b.shape[0]
+    _check(lib().ludax_dense_bf16_relu(_ptr(a), _ptr(b), _ptr(bias), _ptr(out), M, N, K, out.shape[1],
+                                       _stream(stream)), "ludax_dense_bf16_relu")
+
+
+def ludax_device_error():
+    e = ctypes.c_int32()
+    lib().ludax_device_error(ctypes.byref(e))
+    return e.value
+
+
 class Net:
     """The value network (bf16 inputs are passed as int16 tensors holding the bits)."""
 
@@ -357,6 +373,9 @@ class Net:
 
     def set_params(self, params):
         ludax_net_set_params(self.handle, params.to(torch.float32).contiguous())
+
+    def set_tensor_path(self, use_tcgen05: bool):
+        _check(lib().ludax_net_set_tensor_path(self.handle, 1 if use_tcgen05 else 0), "ludax_net_set_tensor_path")
 
     def get_params(self):
         p = torch.empty(self.num_params, dtype=torch.float32, device="cuda")

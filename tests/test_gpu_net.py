@@ -81,11 +81,14 @@ def test_forward_matches_oracle(L, cells, B):
     net = L.Net(cells, 2048)
     assert (net.in_pad, net.hidden, net.num_params) == (K, 512, M.num_params(K))
     net.set_params(torch.from_numpy(theta).cuda())
-    p = net.forward(bf16_bits(X)).cpu().numpy()
     ref = forward_bf16(theta, X, K)
-    assert np.abs(p - ref).max() < 5e-4
     exact, _ = M.forward(theta.astype(np.float64), X, K)
-    assert np.abs(p - exact).max() < 2e-2
+    for tcgen05 in (True, False):
+        net.set_tensor_path(tcgen05)
+        p = net.forward(bf16_bits(X)).cpu().numpy()
+        assert np.abs(p - ref).max() < 5e-4
+        assert np.abs(p - exact).max() < 2e-2
+    assert L.ludax_device_error() == 0
     assert np.allclose(net.get_params().cpu().numpy(), theta)
 
 
