@@ -88,30 +88,59 @@ __device__ __forceinline__ uint32_t popc(uint32_t m) { return __popc(m); }
 __device__ __forceinline__ uint32_t popc(uint64_t m) { return __popcll(m); }
 __device__ __forceinline__ uint32_t popc(B128 m) { return __popcll(m.lo) + __popcll(m.hi); }
 
-// Position of the k-th set bit (k < popc(w)) by halving: count the low half,
-// descend into the half that holds the bit.
-__device__ __forceinline__ int select32(uint32_t w, uint32_t k) {
-    int pos = 0;
-    uint32_t c = __popc(w & 0xFFFFu);
-    if (k >= c) { k -= c; w >>= 16; pos += 16; }
-    c = __popc(w & 0xFFu);
-    if (k >= c) { k -= c; w >>= 8; pos += 8; }
-    c = __popc(w & 0xFu);
-    if (k >= c) { k -= c; w >>= 4; pos += 4; }
-    c = __popc(w & 0x3u);
-    if (k >= c) { k -= c; w >>= 2; pos += 2; }
-    c = w & 1u;
-    if (k >= c) pos += 1;
-    return pos;
+// Position of the k-th set bit (k < popc(w)), branch-free and without
+// popcount instructions on the dependent path (popcount and count-leading-
+// zeros take ~19 cycles on sm_103a against ~5 for logic ops).  Nested SWAR
+// counts give every 2-, 4- and 8-bit field's population at once; one
+// multiply turns the byte counts into inclusive byte prefix sums; the byte
+// holding the bit is found with three independent compares, then two
+// field-halving steps and the last bit finish the search.
+struct Swar32 {
+    uint32_t w, a, b, p;  // word; 2-bit counts; 4-bit counts; byte prefix sums
+};
+__device__ __forceinline__ Swar32 swar32(uint32_t w) {
+    Swar32 s;
+    s.w = w;
+    s.a = w - ((w >> 1) & 0x55555555u);
+    s.b = (s.a & 0x33333333u) + ((s.a >> 2) & 0x33333333u);
+    s.p = ((s.b + (s.b >> 4)) & 0x0F0F0F0Fu) * 0x01010101u;
+    return s;
 }
-__device__ __forceinline__ int select_bit(uint32_t m, uint32_t k) { return select32(m, k); }
+__device__ __forceinline__ uint32_t swar_select(const Swar32& s, uint32_t k) {
+    const uint32_t p0 = s.p & 0xFFu, p1 = (s.p >> 8) & 0xFFu, p2 = (s.p >> 16) & 0xFFu;
+    const uint32_t g0 = k >= p0, g1 = k >= p1, g2 = k >= p2;
+    const uint32_t before = g2 ? p2 : (g1 ? p1 : (g0 ? p0 : 0u));
+    uint32_t pos = (g0 + g1 + g2) << 3;
+    k -= before;
+    uint32_t c = (s.b >> pos) & 0xFu, t = k >= c;
+    k -= t ? c : 0u;
+    pos += t << 2;
+    c = (s.a >> pos) & 3u;
+    t = k >= c;
+    k -= t ? c : 0u;
+    pos += t << 1;
+    c = (s.w >> pos) & 1u;
+    return pos + (k >= c ? 1u : 0u);
+}
+__device__ __forceinline__ int select_bit(uint32_t m, uint32_t k) { return (int)swar_select(swar32(m), k); }
+// the SWAR counts of both 32-bit halves do not depend on k, so they are
+// formed while k is still being drawn; one search runs in the chosen half
 __device__ __forceinline__ int select_bit(uint64_t m, uint32_t k) {
-    uint32_t lo = (uint32_t)m, c = __popc(lo);
-    return k < c ? select32(lo, k) : 32 + select32((uint32_t)(m >> 32), k - c);
+    const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
+    const uint32_t nlo = __popc(lo);
+    const Swar32 sl = swar32(lo), sh = swar32(hi);
+    const bool low = k < nlo;
+    Swar32 s;
+    s.w = low ? sl.w : sh.w;
+    s.a = low ? sl.a : sh.a;
+    s.b = low ? sl.b : sh.b;
+    s.p = low ? sl.p : sh.p;
+    return (int)((low ? 0u : 32u) + swar_select(s, low ? k : k - nlo));
 }
 __device__ __forceinline__ int select_bit(B128 m, uint32_t k) {
-    uint32_t c = __popcll(m.lo);
-    return k < c ? select_bit(m.lo, k) : 64 + select_bit(m.hi, k - c);
+    const uint32_t c = __popcll(m.lo);
+    const bool low = k < c;
+    return (low ? 0 : 64) + select_bit(low ? m.lo : m.hi, low ? k : k - c);
 }
 
 // per-env scalars packed into one word for the shared-memory slot of an env
