@@ -2,7 +2,8 @@
 
 Builds ``libludax_oracle.so`` next to the source with plain ``gcc -O2`` (no
 intrinsics, no vector pragmas) on first use, then exposes numpy-friendly
-functions.  Game ids: 0 Tic-Tac-Toe, 1 Connect Four, 2 Reversi/Othello, 3 Hex.
+functions.  Game ids: 0 Tic-Tac-Toe, 1 Connect Four, 2 Reversi/Othello, 3 Hex,
+4 Gomoku, 5 Pente, 6 Yavalath.
 Outcome codes: -1 ongoing, 0 draw, 1 P1 win, 2 P2 win, 3 capped.
 """
 from __future__ import annotations
@@ -17,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "ludax_oracle.c")
 LIB = os.path.join(HERE, "libludax_oracle.so")
 
-TTT, C4, OTHELLO, HEX = 0, 1, 2, 3
+TTT, C4, OTHELLO, HEX, GOMOKU, PENTE, YAVALATH = 0, 1, 2, 3, 4, 5, 6
 ONGOING, DRAW, P1, P2, CAPPED = -1, 0, 1, 2, 3
 
 _lib = None
@@ -46,6 +47,7 @@ def lib():
         L.oracle_pick.restype = u32
         L.oracle_pick.argtypes = [u64, u32]
         L.oracle_num_actions.argtypes = [i32, i32, i32]
+        L.oracle_num_cells.argtypes = [i32, i32, i32]
         L.oracle_ply_cap.argtypes = [i32, i32, i32]
         L.oracle_hex_connections.argtypes = [i32, vp]
         L.oracle_rollout_start.argtypes = [i32, i32, i32, i64, i64, u64, vp, vp, vp]
@@ -81,6 +83,10 @@ def num_actions(game, rows, cols) -> int:
     return lib().oracle_num_actions(game, rows, cols)
 
 
+def num_cells(game, rows, cols) -> int:
+    return lib().oracle_num_cells(game, rows, cols)
+
+
 def ply_cap(game, rows, cols) -> int:
     return lib().oracle_ply_cap(game, rows, cols)
 
@@ -92,12 +98,13 @@ def hex_connections(n: int, cells) -> int:
 
 class States:
     """A batch of positions in the canonical layout shared with the C-ABI's
-    state view: board[n, rows*cols] int8, to_move/passes/outcome int8,
-    ply int16."""
+    state view: board[n, cells] int8, to_move/passes/outcome int8, ply int16
+    (for Pente, passes holds the captured pairs: P1's in the low 4 bits, P2's
+    in the high 4 bits)."""
 
     def __init__(self, game, rows, cols, n):
         self.game, self.rows, self.cols, self.n = game, rows, cols, n
-        self.board = np.zeros((n, rows * cols), np.int8)
+        self.board = np.zeros((n, num_cells(game, rows, cols)), np.int8)
         self.to_move = np.zeros(n, np.int8)
         self.ply = np.zeros(n, np.int16)
         self.passes = np.zeros(n, np.int8)
@@ -141,7 +148,7 @@ def rollout_start(game, rows, cols, n, seed, env_offset=0, want_boards=False):
     Returns (outcome int8[n], plies int16[n], boards int8[n, cells] or None)."""
     out = np.zeros(n, np.int8)
     plies = np.zeros(n, np.int16)
-    boards = np.zeros((n, rows * cols), np.int8) if want_boards else None
+    boards = np.zeros((n, num_cells(game, rows, cols)), np.int8) if want_boards else None
     assert lib().oracle_rollout_start(game, rows, cols, n, env_offset, seed, _p(boards), _p(out), _p(plies)) == 0
     return out, plies, boards
 

@@ -24,6 +24,13 @@
  * cell by cell, and Hex connectivity is a breadth-first search from the
  * mover's first edge.  No bitboards, no incremental state.
  *
+ * The line-game family (App. C): Gomoku 15x15 (a line of exactly five wins,
+ * six or more does not), Pente 19x19 (five or more in a row wins; placing a
+ * stone that closes own-opp-opp-own along any of 8 directions removes the two
+ * opponent stones; ten captured stones win; P1's first move is the centre),
+ * Yavalath on the 61-cell hexagon (four in a row wins, otherwise three in a
+ * row loses); all three end in a draw on a full board.
+ *
  * Readings where the paper is silent (they are listed in the design doc):
  *   Hex neighbours of (r,c): (r-1,c) (r+1,c) (r,c-1) (r,c+1) (r-1,c+1) (r+1,c-1);
  *   Reversi: P1 = black moves first; white on D4,E5 = cells 27,36, black on
@@ -42,6 +49,9 @@
 #define OR_C4 1
 #define OR_OTHELLO 2
 #define OR_HEX 3
+#define OR_GOMOKU 4
+#define OR_PENTE 5
+#define OR_YAVALATH 6
 
 #define OR_ONGOING (-1)
 #define OR_DRAW 0
@@ -49,16 +59,18 @@
 #define OR_P2 2
 #define OR_CAPPED 3
 
-#define OR_MAXCELLS 128
+#define OR_MAXCELLS 512
 
 typedef struct {
     int32_t game, rows, cols, ncells;
-    int8_t cell[OR_MAXCELLS]; /* 0 empty, 1 P1, 2 P2; index r*cols + c, r = 0 top */
+    int8_t cell[OR_MAXCELLS]; /* 0 empty, 1 P1, 2 P2; index r*cols + c, r = 0 top
+                                 (Yavalath: row-major over the 61 cells of the hexagon) */
     int32_t to_move;          /* 1 or 2 */
     int32_t ply;              /* plies played so far, passes included */
     int32_t passes;           /* consecutive passes (Reversi) */
     int32_t outcome;          /* OR_ONGOING, OR_DRAW, OR_P1, OR_P2, OR_CAPPED */
     int32_t illegal;          /* 1 when the game ended on an illegal action */
+    int32_t captures[3];      /* Pente: opponent stones captured by player 1 / 2 */
 } ogame;
 
 /* ------------------------------------------------------------------ RNG --
@@ -88,10 +100,39 @@ uint32_t oracle_pick(uint64_t r, uint32_t n) {
 }
 
 /* ------------------------------------------------------------ geometry -- */
-static int in_board(const ogame* g, int r, int c) {
-    return r >= 0 && r < g->rows && c >= 0 && c < g->cols;
+/* Yavalath's hexagon (side 5, 61 cells, the long diagonal drawn left to
+ * right) in axial coordinates: rows r = 0..8, columns c = 0..8 with
+ * |r - c| <= 4; neighbours differ by (0,+-1), (+-1,0) or (+-1,+-1).  Cells are
+ * numbered row by row, left to right. */
+static int yav_valid(int r, int c) { return r >= 0 && r < 9 && c >= 0 && c < 9 && (r - c <= 4) && (c - r <= 4); }
+static int yav_id(int r, int c) {
+    int id = 0;
+    for (int rr = 0; rr < r; ++rr) id += 9 - (rr > 4 ? rr - 4 : 4 - rr);
+    return id + c - (r > 4 ? r - 4 : 0);
 }
-static int at(const ogame* g, int r, int c) { return g->cell[r * g->cols + c]; }
+static void yav_rc(int id, int* r, int* c) {
+    int rr = 0;
+    for (;;) {
+        int len = 9 - (rr > 4 ? rr - 4 : 4 - rr);
+        if (id < len) break;
+        id -= len;
+        rr++;
+    }
+    *r = rr;
+    *c = id + (rr > 4 ? rr - 4 : 0);
+}
+
+/* canonical id of (r, c), or -1 off the board */
+static int cell_id(const ogame* g, int r, int c) {
+    if (g->game == OR_YAVALATH) return yav_valid(r, c) ? yav_id(r, c) : -1;
+    return (r >= 0 && r < g->rows && c >= 0 && c < g->cols) ? r * g->cols + c : -1;
+}
+static void cell_rc(const ogame* g, int id, int* r, int* c) {
+    if (g->game == OR_YAVALATH) yav_rc(id, r, c);
+    else { *r = id / g->cols; *c = id % g->cols; }
+}
+static int in_board(const ogame* g, int r, int c) { return cell_id(g, r, c) >= 0; }
+static int at(const ogame* g, int r, int c) { return g->cell[cell_id(g, r, c)]; }
 
 int oracle_ply_cap(int game, int rows, int cols) {
     switch (game) {
@@ -99,13 +140,18 @@ int oracle_ply_cap(int game, int rows, int cols) {
     case OR_C4: return 42;
     case OR_OTHELLO: return 128;
     case OR_HEX: return rows * cols;
+    case OR_GOMOKU: return rows * cols;
+    case OR_PENTE: return 2000;
+    case OR_YAVALATH: return 61;
     }
     return 0;
 }
 
 /* Number of actions: one per cell, plus the pass for Reversi. */
+int oracle_num_cells(int game, int rows, int cols) { return game == OR_YAVALATH ? 61 : rows * cols; }
+
 int oracle_num_actions(int game, int rows, int cols) {
-    return rows * cols + (game == OR_OTHELLO ? 1 : 0);
+    return oracle_num_cells(game, rows, cols) + (game == OR_OTHELLO ? 1 : 0);
 }
 
 int oracle_check_params(int game, int rows, int cols) {
@@ -114,6 +160,9 @@ int oracle_check_params(int game, int rows, int cols) {
     case OR_C4: return (rows == 6 && cols == 7) ? 0 : -1;
     case OR_OTHELLO: return (rows == 8 && cols == 8) ? 0 : -1;
     case OR_HEX: return (rows == cols && rows >= 2 && rows <= 11) ? 0 : -1;
+    case OR_GOMOKU: return (rows == 15 && cols == 15) ? 0 : -1;
+    case OR_PENTE: return (rows == 19 && cols == 19) ? 0 : -1;
+    case OR_YAVALATH: return (rows == 9 && cols == 9) ? 0 : -1;
     }
     return -1;
 }
@@ -125,7 +174,7 @@ int oracle_init(ogame* g, int game, int rows, int cols) {
     g->game = game;
     g->rows = rows;
     g->cols = cols;
-    g->ncells = rows * cols;
+    g->ncells = oracle_num_cells(game, rows, cols);
     g->to_move = 1;
     g->outcome = OR_ONGOING;
     if (game == OR_OTHELLO) {
@@ -144,13 +193,31 @@ int oracle_init(ogame* g, int game, int rows, int cols) {
 static int has_line(const ogame* g, int p, int L) {
     static const int dr[4] = {0, 1, 1, 1};
     static const int dc[4] = {1, 0, 1, -1};
+    int nd = g->game == OR_YAVALATH ? 3 : 4; /* the hexagon's three axes: (0,1) (1,0) (1,1) */
     for (int r = 0; r < g->rows; r++)
         for (int c = 0; c < g->cols; c++)
-            for (int d = 0; d < 4; d++) {
+            for (int d = 0; d < nd; d++) {
                 int k = 0;
                 while (k < L && in_board(g, r + k * dr[d], c + k * dc[d]) &&
                        at(g, r + k * dr[d], c + k * dc[d]) == p)
                     k++;
+                if (k == L) return 1;
+            }
+    return 0;
+}
+
+/* Does player p own a maximal run of exactly L cells in a row (the cells
+ * just before and just after the run are not p's)? */
+static int has_line_exact(const ogame* g, int p, int L) {
+    static const int dr[4] = {0, 1, 1, 1};
+    static const int dc[4] = {1, 0, 1, -1};
+    for (int r = 0; r < g->rows; r++)
+        for (int c = 0; c < g->cols; c++)
+            for (int d = 0; d < 4; d++) {
+                int pr = r - dr[d], pc = c - dc[d];
+                if (in_board(g, pr, pc) && at(g, pr, pc) == p) continue; /* not the start of a run */
+                int k = 0;
+                while (in_board(g, r + k * dr[d], c + k * dc[d]) && at(g, r + k * dr[d], c + k * dc[d]) == p) k++;
                 if (k == L) return 1;
             }
     return 0;
@@ -245,7 +312,10 @@ int oracle_legal(const ogame* g, uint8_t* legal) {
         if (g->cell[i] != 0) continue;
         switch (g->game) {
         case OR_TTT:
-        case OR_HEX: ok = 1; break;
+        case OR_HEX:
+        case OR_GOMOKU:
+        case OR_YAVALATH: ok = 1; break;
+        case OR_PENTE: ok = g->ply > 0 || i == (g->rows / 2) * g->cols + g->cols / 2; break; /* first move: centre */
         case OR_C4: {
             int r = i / g->cols, c = i % g->cols;
             ok = (r == g->rows - 1) || (at(g, r + 1, c) != 0);
@@ -291,8 +361,23 @@ int oracle_apply(ogame* g, int action) {
     if (g->game == OR_OTHELLO && action == g->ncells) {
         g->passes += 1;
     } else {
-        int r = action / g->cols, c = action % g->cols;
+        int r, c;
+        cell_rc(g, action, &r, &c);
         g->cell[action] = (int8_t)p;
+        if (g->game == OR_PENTE) {
+            /* custodial capture of exactly two opponent stones: the new stone,
+             * two opponent stones, then one of the mover's, along any of the
+             * eight directions; the two are removed and counted */
+            for (int d = 0; d < 8; d++) {
+                int r1 = r + ODR[d], c1 = c + ODC[d], r2 = r + 2 * ODR[d], c2 = c + 2 * ODC[d];
+                int r3 = r + 3 * ODR[d], c3 = c + 3 * ODC[d];
+                if (in_board(g, r3, c3) && at(g, r1, c1) == 3 - p && at(g, r2, c2) == 3 - p && at(g, r3, c3) == p) {
+                    g->cell[cell_id(g, r1, c1)] = 0;
+                    g->cell[cell_id(g, r2, c2)] = 0;
+                    g->captures[p] += 2;
+                }
+            }
+        }
         if (g->game == OR_OTHELLO) {
             int runs[8];
             for (int d = 0; d < 8; d++) runs[d] = custodial_run(g, p, r, c, d);
@@ -315,6 +400,19 @@ int oracle_apply(ogame* g, int action) {
         break;
     case OR_HEX:
         if (hex_connects(g, p)) finish(g, p);
+        break;
+    case OR_GOMOKU:
+        if (has_line_exact(g, p, 5)) finish(g, p);
+        else if (board_full(g)) finish(g, OR_DRAW);
+        break;
+    case OR_PENTE:
+        if (has_line(g, p, 5) || g->captures[p] >= 10) finish(g, p);
+        else if (board_full(g)) finish(g, OR_DRAW);
+        break;
+    case OR_YAVALATH:
+        if (has_line(g, p, 4)) finish(g, p);
+        else if (has_line(g, p, 3)) finish(g, 3 - p);
+        else if (board_full(g)) finish(g, OR_DRAW);
         break;
     case OR_OTHELLO:
         if (g->passes >= 2) {
@@ -361,14 +459,23 @@ void oracle_playout(ogame* g, uint64_t seed, uint64_t env, int stop_ply) {
  * State arrays used to move positions in and out of the oracle:
  *   board[e*ncells + i]  int8 cell values
  *   to_move[e] (1/2), ply[e], passes[e], outcome[e] (-1 ongoing)            */
+/* Pente keeps its capture counts in the passes slot of the state arrays:
+ * passes[e] = captures by P1 + 16 * (captures by P2) / 2 ... stored as
+ * (captures by P1 / 2) | (captures by P2 / 2) << 4 (pairs, at most 15). */
 static void load_state(ogame* g, int game, int rows, int cols, int64_t e, const int8_t* board, const int8_t* to_move,
                        const int16_t* ply, const int8_t* passes, const int8_t* outcome) {
     oracle_init(g, game, rows, cols);
     memcpy(g->cell, board + e * g->ncells, (size_t)g->ncells);
     g->to_move = to_move[e];
     g->ply = ply[e];
-    g->passes = passes[e];
     g->outcome = outcome[e];
+    if (game == OR_PENTE) {
+        int v = (uint8_t)passes[e];
+        g->captures[1] = 2 * (v & 15);
+        g->captures[2] = 2 * (v >> 4);
+    } else {
+        g->passes = passes[e];
+    }
 }
 
 static void store_state(const ogame* g, int64_t e, int8_t* board, int8_t* to_move, int16_t* ply, int8_t* passes,
@@ -376,7 +483,14 @@ static void store_state(const ogame* g, int64_t e, int8_t* board, int8_t* to_mov
     if (board) memcpy(board + e * g->ncells, g->cell, (size_t)g->ncells);
     if (to_move) to_move[e] = (int8_t)g->to_move;
     if (ply) ply[e] = (int16_t)g->ply;
-    if (passes) passes[e] = (int8_t)g->passes;
+    if (passes) {
+        if (g->game == OR_PENTE) {
+            int a = g->captures[1] / 2, b = g->captures[2] / 2;
+            passes[e] = (int8_t)((a > 15 ? 15 : a) | ((b > 15 ? 15 : b) << 4));
+        } else {
+            passes[e] = (int8_t)g->passes;
+        }
+    }
     if (outcome) outcome[e] = (int8_t)g->outcome;
 }
 
