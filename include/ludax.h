@@ -64,6 +64,11 @@ extern "C" {
 #define LUDAX_GAME_C4 1      /* Connect Four 6x7, gravity, line of 4       */
 #define LUDAX_GAME_OTHELLO 2 /* Reversi/Othello 8x8, flips, forced pass    */
 #define LUDAX_GAME_HEX 3     /* Hex n x n rhombus, 2 <= n <= 11            */
+#define LUDAX_GAME_GOMOKU 4  /* Gomoku 15x15, a line of exactly five wins  */
+#define LUDAX_GAME_PENTE 5   /* Pente 19x19, five in a row or ten captured
+                                stones win; P1's first move is the centre  */
+#define LUDAX_GAME_YAVALATH 6 /* Yavalath, 61-cell hexagon (board params
+                                 9x9): four in a row wins, three loses     */
 
 /* ---------------------------------------------------------- outcomes -- */
 #define LUDAX_OUTCOME_ONGOING (-1)
@@ -84,10 +89,14 @@ typedef struct {
 typedef struct ludax_env ludax_env;
 
 /* A batch of positions in canonical form, all arrays on the device:
- *   board   int8  [num_envs][rows*cols]  cell values 0/1/2
+ *   board   int8  [num_envs][cells]      cell values 0/1/2 (cells = rows*cols;
+ *                                        Yavalath: the 61 cells of the hexagon,
+ *                                        row by row, left to right)
  *   to_move int8  [num_envs]             1 or 2
  *   ply     int16 [num_envs]             plies played (passes included)
- *   passes  int8  [num_envs]             consecutive passes (Reversi; else 0)
+ *   passes  int8  [num_envs]             consecutive passes (Reversi); Pente:
+ *                                        captured pairs, P1's in the low 4 bits,
+ *                                        P2's in the high 4 bits; else 0
  *   outcome int8  [num_envs]             LUDAX_OUTCOME_*                      */
 typedef struct {
     int8_t* board;
@@ -119,7 +128,8 @@ typedef struct {
  * start position (Sec. 3.1: empty board, Reversi's four discs at D4/E5 white =
  * P2 on cells 27/36 and D5/E4 black = P1 on cells 35/28; P1 to move).
  *   game       LUDAX_GAME_*
- *   p          board size: TTT 3x3, C4 6x7, Othello 8x8, Hex n x n (2..11)
+ *   p          board size: TTT 3x3, C4 6x7, Othello 8x8, Hex n x n (2..11),
+ *              Gomoku 15x15, Pente 19x19, Yavalath 9x9 (the hexagon's axial grid)
  *   num_envs   1 .. 2^31-1
  *   env_offset global index of env 0 (keys the random draws; lets several
  *              GPUs or calls cover disjoint env ranges), >= 0

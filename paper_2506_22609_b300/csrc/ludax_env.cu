@@ -52,7 +52,7 @@ __global__ void legal_kernel(EnvDev d, uint64_t* out, uint8_t* pass_legal, int w
         m = g.legal();
         pass = G::kHasPass && !any(m);
     }
-    for (int w = 0; w < words; ++w) out[e * words + w] = G::canon_word(m, w);
+    for (int w = 0; w < words; ++w) out[e * words + w] = canon_mask_word<G>(m, w);
     if (pass_legal) pass_legal[e] = pass ? 1 : 0;
 }
 
@@ -130,6 +130,10 @@ __global__ void get_state_kernel(EnvDev d, ludax_state_view v) {
     v.to_move[e] = (int8_t)(g.side + 1);
     v.ply[e] = (int16_t)g.ply;
     v.passes[e] = (int8_t)g.passes;
+    if constexpr (G::kGame == Pente::kGame) {  // captured pairs: P1 low nibble, P2 high nibble
+        const int c1 = g.side == 0 ? g.caps_own : g.caps_opp, c2 = g.side == 0 ? g.caps_opp : g.caps_own;
+        v.passes[e] = (int8_t)((c1 & 15) | ((c2 & 15) << 4));
+    }
     v.outcome[e] = (int8_t)g.outcome;
 }
 
@@ -141,6 +145,8 @@ template <>
 __device__ __forceinline__ void set_bit<uint64_t>(uint64_t& m, int b) { m |= 1ull << b; }
 template <>
 __device__ __forceinline__ void set_bit<B128>(B128& m, int b) { m = m | bit128(b); }
+template <int W>
+__device__ __forceinline__ void set_bit(BitsW<W>& m, int b) { set_bit_w(m, b); }
 
 template <class G>
 __global__ void set_state_kernel(EnvDev d, ludax_state_view v) {
@@ -161,6 +167,12 @@ __global__ void set_state_kernel(EnvDev d, ludax_state_view v) {
     g.outcome = v.outcome[e];
     g.own = g.side == 0 ? p1 : p2;
     g.opp = g.side == 0 ? p2 : p1;
+    if constexpr (G::kGame == Pente::kGame) {
+        const int x = (uint8_t)v.passes[e], c1 = x & 15, c2 = x >> 4;
+        g.passes = 0;
+        g.caps_own = g.side == 0 ? c1 : c2;
+        g.caps_opp = g.side == 0 ? c2 : c1;
+    }
     if constexpr (HexN<G>::value != 0) g.rebuild();
     store_state(g, d, e);
 }
@@ -462,10 +474,11 @@ int ludax_env_create(ludax_env** out, int32_t game, const ludax_board_params* p,
     if (!out || !p) return LUDAX_ERR_ARG;
     *out = nullptr;
     if (num_envs < 1 || num_envs > 0x7FFFFFFFll || env_offset < 0) return LUDAX_ERR_ARG;
-    int planes = 0;
+    int planes = 0, cells = 0;
     int st = dispatch_game(game, p->rows, p->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         planes = G::kPlanes;
+        cells = G::kCells;
         return LUDAX_OK;
     });
     if (st != LUDAX_OK) return st;
@@ -474,7 +487,7 @@ int ludax_env_create(ludax_env** out, int32_t game, const ludax_board_params* p,
     env->game = game;
     env->rows = p->rows;
     env->cols = p->cols;
-    env->cells = p->rows * p->cols;
+    env->cells = cells;
     env->num_actions = env->cells + (game == LUDAX_GAME_OTHELLO ? 1 : 0);
     env->mask_words = (env->cells + 63) / 64;
     env->planes = planes;

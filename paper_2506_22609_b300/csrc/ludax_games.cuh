@@ -37,6 +37,11 @@
 //                added to that set by a flood fill.  This is the incremental
 //                connected-component update of Sec. 4 ("Dynamic State
 //                Attributes") in bitboard form.
+//   Gomoku 15x15 / Pente 19x19 / Yavalath: W-word bitboards (BitsW) with one
+//                empty padding column per row (strides 16, 20 and 10), so
+//                shifted line and capture patterns cannot wrap across rows;
+//                Yavalath's 61-cell hexagon sits in axial coordinates (row r,
+//                column c, |r - c| <= 4) of a 9x9 grid.
 #pragma once
 #include <stdint.h>
 
@@ -457,6 +462,339 @@ template <int N>
 __device__ __forceinline__ void hex_fill_table(B128* table) {
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) table[i] = Hex<N>::nbrs(bit128(i));
 }
+
+// ------------------------------------------------- multi-word bitboards --
+template <int W>
+struct BitsW {
+    uint64_t w[W];
+};
+template <int W>
+__device__ __forceinline__ BitsW<W> operator|(const BitsW<W>& a, const BitsW<W>& b) {
+    BitsW<W> o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) o.w[i] = a.w[i] | b.w[i];
+    return o;
+}
+template <int W>
+__device__ __forceinline__ BitsW<W> operator&(const BitsW<W>& a, const BitsW<W>& b) {
+    BitsW<W> o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) o.w[i] = a.w[i] & b.w[i];
+    return o;
+}
+template <int W>
+__device__ __forceinline__ BitsW<W> operator~(const BitsW<W>& a) {
+    BitsW<W> o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) o.w[i] = ~a.w[i];
+    return o;
+}
+template <int W>
+__device__ __forceinline__ bool any(const BitsW<W>& a) {
+    uint64_t x = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) x |= a.w[i];
+    return x != 0;
+}
+template <int W>
+__device__ __forceinline__ uint32_t popc(const BitsW<W>& a) {
+    uint32_t n = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) n += __popcll(a.w[i]);
+    return n;
+}
+// bit i of the result = bit i + S of a (S >= 0, compile time)
+template <int S, int W>
+__device__ __forceinline__ BitsW<W> shr(const BitsW<W>& a) {
+    constexpr int q = S / 64, r = S % 64;
+    BitsW<W> o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint64_t lo = (i + q < W) ? a.w[i + q] : 0ull;
+        const uint64_t hi = (i + q + 1 < W) ? a.w[i + q + 1] : 0ull;
+        o.w[i] = r == 0 ? lo : ((lo >> (r == 0 ? 1 : r)) | (hi << (r == 0 ? 1 : 64 - r)));
+    }
+    return o;
+}
+// bit i of the result = bit i - S of a
+template <int S, int W>
+__device__ __forceinline__ BitsW<W> shl(const BitsW<W>& a) {
+    constexpr int q = S / 64, r = S % 64;
+    BitsW<W> o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint64_t hi = (i - q >= 0) ? a.w[i - q] : 0ull;
+        const uint64_t lo = (i - q - 1 >= 0) ? a.w[i - q - 1] : 0ull;
+        o.w[i] = r == 0 ? hi : ((hi << (r == 0 ? 1 : r)) | (lo >> (r == 0 ? 1 : 64 - r)));
+    }
+    return o;
+}
+// dynamic single-bit access without indexing the register array (p may lie
+// outside the board: the test then reads 0)
+template <int W>
+__device__ __forceinline__ bool test_bit(const BitsW<W>& a, int p) {
+    uint64_t word = 0;
+    const int q = p >> 6;
+#pragma unroll
+    for (int i = 0; i < W; ++i) word = q == i ? a.w[i] : word;
+    return p >= 0 && ((word >> (p & 63)) & 1ull);
+}
+template <int W>
+__device__ __forceinline__ void set_bit_w(BitsW<W>& a, int p) {
+    const int q = p >> 6;
+    const uint64_t b = 1ull << (p & 63);
+#pragma unroll
+    for (int i = 0; i < W; ++i) a.w[i] |= q == i ? b : 0ull;
+}
+template <int W>
+__device__ __forceinline__ void clear_bit_w(BitsW<W>& a, int p) {
+    const int q = p >> 6;
+    const uint64_t b = 1ull << (p & 63);
+#pragma unroll
+    for (int i = 0; i < W; ++i) a.w[i] &= q == i ? ~b : ~0ull;
+}
+template <int W>
+__device__ __forceinline__ int select_bit(const BitsW<W>& m, uint32_t k) {
+    uint32_t pre = 0, base = 0;
+    uint64_t word = m.w[0];
+    int widx = 0;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint32_t c = __popcll(m.w[i]);
+        const bool here = k >= pre && k < pre + c;
+        word = here ? m.w[i] : word;
+        base = here ? pre : base;
+        widx = here ? i : widx;
+        pre += c;
+    }
+    return widx * 64 + select_bit(word, k - base);
+}
+template <int W>
+__device__ __forceinline__ BitsW<W> bits_from(const uint64_t (&v)[W]) {
+    BitsW<W> o;
+#pragma unroll
+    for (int i = 0; i < W; ++i) o.w[i] = v[i];
+    return o;
+}
+
+// word `word` of the mask of cells (r < R, c < C) in a row-stride-S layout,
+// optionally restricted to the hexagon |r - c| <= 4
+__host__ __device__ constexpr uint64_t grid_word(int R, int C, int S, bool hexagon, int word) {
+    uint64_t m = 0;
+    for (int b = 0; b < 64; ++b) {
+        int i = word * 64 + b, r = i / S, c = i % S;
+        if (r < R && c < C && (!hexagon || (r - c <= 4 && c - r <= 4))) m |= 1ull << b;
+    }
+    return m;
+}
+
+// any run of >= 5 (L5) / >= 4 / >= 3 stones along stride D, full board
+template <int D, int W>
+__device__ __forceinline__ BitsW<W> runs2(const BitsW<W>& b) { return b & shr<D>(b); }
+template <int D, int W>
+__device__ __forceinline__ bool has_run5(const BitsW<W>& b) {
+    const BitsW<W> m2 = runs2<D>(b), m4 = m2 & shr<2 * D>(m2);
+    return any(m4 & shr<4 * D>(b));
+}
+// a maximal run of exactly five: starts of >= 5 windows with no stone before
+// the window and none right after it
+template <int D, int W>
+__device__ __forceinline__ bool has_exact5(const BitsW<W>& b) {
+    const BitsW<W> m2 = runs2<D>(b), m4 = m2 & shr<2 * D>(m2), m5 = m4 & shr<4 * D>(b);
+    return any(m5 & ~shl<D>(b) & ~shr<5 * D>(b));
+}
+
+// ------------------------------------------------------------- Gomoku --
+struct Gomoku {
+    static constexpr int kGame = 4, kRows = 15, kCols = 15, kCells = 225, kCap = 225, W = 4, kStride = 16;
+    static constexpr int kPlanes = 2 * W;
+    static constexpr bool kHasPass = false;
+    using Mask = BitsW<W>;
+    Mask own, opp;
+    int side, ply, passes, outcome;
+
+    __device__ __forceinline__ static Mask valid() {
+        return Mask{{grid_word(15, 15, 16, false, 0), grid_word(15, 15, 16, false, 1), grid_word(15, 15, 16, false, 2),
+                     grid_word(15, 15, 16, false, 3)}};
+    }
+    __device__ __forceinline__ void reset() {
+        own = opp = Mask{{0, 0, 0, 0}};
+        side = ply = passes = 0;
+        outcome = kOngoing;
+    }
+    __device__ __forceinline__ Mask legal() const { return valid() & ~(own | opp); }
+    __device__ __forceinline__ static bool five(const Mask& b) {
+        return has_exact5<1>(b) | has_exact5<16>(b) | has_exact5<17>(b) | has_exact5<15>(b);
+    }
+    __device__ __forceinline__ void place(int b) {
+        set_bit_w(own, b);
+        if (five(own)) outcome = side + 1;
+        else if (ply + 1 >= kCells) outcome = kDraw;
+        ++ply;
+        Mask t = own; own = opp; opp = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {}
+    __device__ __forceinline__ static int canon_of(int b) { return (b >> 4) * 15 + (b & 15); }
+    __device__ __forceinline__ static int bit_of(int cell) { return (cell / 15) * 16 + cell % 15; }
+    static constexpr int kWords = 2 * W + 1;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+#pragma unroll
+        for (int i = 0; i < W; ++i) { w[i] = own.w[i]; w[W + i] = opp.w[i]; }
+        w[2 * W] = pack_small(ply, passes, side, outcome);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) { own.w[i] = w[i]; opp.w[i] = w[W + i]; }
+        unpack_small(w[2 * W], ply, passes, side, outcome);
+    }
+};
+
+// --------------------------------------------------------------- Pente --
+struct Pente {
+    static constexpr int kGame = 5, kRows = 19, kCols = 19, kCells = 361, kCap = 2000, W = 6, kStride = 20;
+    static constexpr int kPlanes = 2 * W;
+    static constexpr bool kHasPass = false;
+    static constexpr int kCentre = 9 * 20 + 9;
+    using Mask = BitsW<W>;
+    Mask own, opp;
+    int side, ply, passes, outcome;
+    int caps_own, caps_opp;  // pairs captured by the player to move / by the other
+
+    __device__ __forceinline__ static Mask valid() {
+        return Mask{{grid_word(19, 19, 20, false, 0), grid_word(19, 19, 20, false, 1), grid_word(19, 19, 20, false, 2),
+                     grid_word(19, 19, 20, false, 3), grid_word(19, 19, 20, false, 4), grid_word(19, 19, 20, false, 5)}};
+    }
+    __device__ __forceinline__ void reset() {
+        own = opp = Mask{{0, 0, 0, 0, 0, 0}};
+        side = ply = passes = 0;
+        caps_own = caps_opp = 0;
+        outcome = kOngoing;
+    }
+    __device__ __forceinline__ Mask legal() const {
+        if (ply == 0) {
+            Mask c = Mask{{0, 0, 0, 0, 0, 0}};
+            set_bit_w(c, kCentre);
+            return c & ~(own | opp);
+        }
+        return valid() & ~(own | opp);
+    }
+    // own - opp - opp - own along D from the new stone b: remove the pair
+    template <int D>
+    __device__ __forceinline__ void capture(int b) {
+        if (test_bit(opp, b + D) && test_bit(opp, b + 2 * D) && test_bit(own, b + 3 * D)) {
+            clear_bit_w(opp, b + D);
+            clear_bit_w(opp, b + 2 * D);
+            ++caps_own;
+        }
+    }
+    __device__ __forceinline__ static bool five(const Mask& b) {
+        return has_run5<1>(b) | has_run5<20>(b) | has_run5<21>(b) | has_run5<19>(b);
+    }
+    __device__ __forceinline__ void place(int b) {
+        set_bit_w(own, b);
+        capture<1>(b);
+        capture<-1>(b);
+        capture<20>(b);
+        capture<-20>(b);
+        capture<21>(b);
+        capture<-21>(b);
+        capture<19>(b);
+        capture<-19>(b);
+        if (five(own) || caps_own >= 5) outcome = side + 1;
+        else if (!any(valid() & ~(own | opp))) outcome = kDraw;
+        ++ply;
+        Mask t = own; own = opp; opp = t;
+        int c = caps_own; caps_own = caps_opp; caps_opp = c;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {}
+    __device__ __forceinline__ static int canon_of(int b) { return (b / 20) * 19 + b % 20; }
+    __device__ __forceinline__ static int bit_of(int cell) { return (cell / 19) * 20 + cell % 19; }
+    static constexpr int kWords = 2 * W + 1;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+#pragma unroll
+        for (int i = 0; i < W; ++i) { w[i] = own.w[i]; w[W + i] = opp.w[i]; }
+        w[2 * W] = pack_small(ply, passes, side, outcome) | ((uint64_t)(caps_own & 15) << 40) |
+                   ((uint64_t)(caps_opp & 15) << 44);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) { own.w[i] = w[i]; opp.w[i] = w[W + i]; }
+        unpack_small(w[2 * W] & 0xFFFFFFFFFFull, ply, passes, side, outcome);
+        caps_own = (int)((w[2 * W] >> 40) & 15);
+        caps_opp = (int)((w[2 * W] >> 44) & 15);
+    }
+};
+
+// ------------------------------------------------------------ Yavalath --
+struct Yavalath {
+    static constexpr int kGame = 6, kRows = 9, kCols = 9, kCells = 61, kCap = 61, W = 2, kStride = 10;
+    static constexpr int kPlanes = 2 * W;
+    static constexpr bool kHasPass = false;
+    using Mask = BitsW<W>;
+    Mask own, opp;
+    int side, ply, passes, outcome;
+
+    __device__ __forceinline__ static Mask valid() {
+        return Mask{{grid_word(9, 9, 10, true, 0), grid_word(9, 9, 10, true, 1)}};
+    }
+    __device__ __forceinline__ void reset() {
+        own = opp = Mask{{0, 0}};
+        side = ply = passes = 0;
+        outcome = kOngoing;
+    }
+    __device__ __forceinline__ Mask legal() const { return valid() & ~(own | opp); }
+    template <int D>
+    __device__ __forceinline__ static bool run4(const Mask& b) {
+        const Mask m2 = runs2<D>(b);
+        return any(m2 & shr<2 * D>(m2));
+    }
+    template <int D>
+    __device__ __forceinline__ static bool run3(const Mask& b) {
+        return any(runs2<D>(b) & shr<2 * D>(b));
+    }
+    __device__ __forceinline__ void place(int b) {
+        set_bit_w(own, b);
+        // the hexagon's three axes: strides 1, 10 and 11 in the axial layout
+        if (run4<1>(own) | run4<10>(own) | run4<11>(own)) outcome = side + 1;
+        else if (run3<1>(own) | run3<10>(own) | run3<11>(own)) outcome = 2 - side;  // three without four loses
+        else if (ply + 1 >= kCells) outcome = kDraw;
+        ++ply;
+        Mask t = own; own = opp; opp = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {}
+    // canonical id <-> axial (r, c): rows of 5,6,7,8,9,8,7,6,5 cells; c starts at max(0, r-4)
+    __device__ __forceinline__ static int bit_of(int cell) {
+        int r = 0, start = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int len = 9 - (i > 4 ? i - 4 : 4 - i);
+            const bool past = cell >= start + len && r == i;
+            start += past ? len : 0;
+            r += past ? 1 : 0;
+        }
+        return r * 10 + (cell - start) + (r > 4 ? r - 4 : 0);
+    }
+    __device__ __forceinline__ static int canon_of(int b) {
+        const int r = b / 10, c = b % 10;
+        int start = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) start += i < r ? 9 - (i > 4 ? i - 4 : 4 - i) : 0;
+        return start + c - (r > 4 ? r - 4 : 0);
+    }
+    static constexpr int kWords = 2 * W + 1;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = own.w[0]; w[1] = own.w[1]; w[2] = opp.w[0]; w[3] = opp.w[1];
+        w[4] = pack_small(ply, passes, side, outcome);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        own = Mask{{w[0], w[1]}};
+        opp = Mask{{w[2], w[3]}};
+        unpack_small(w[4], ply, passes, side, outcome);
+    }
+};
 
 // ---------------------------------------------------------- one random ply --
 // Uniform-random policy: n legal cells, k-th in ascending cell id with

@@ -45,6 +45,9 @@ int dispatch_game(int game, int rows, int cols, F&& f) {
         case 11: return f(Tag<Hex<11>>{});
         default: return LUDAX_ERR_SIZE;
         }
+    case LUDAX_GAME_GOMOKU: return (rows == 15 && cols == 15) ? f(Tag<Gomoku>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_PENTE: return (rows == 19 && cols == 19) ? f(Tag<Pente>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_YAVALATH: return (rows == 9 && cols == 9) ? f(Tag<Yavalath>{}) : LUDAX_ERR_SIZE;
     default: return LUDAX_ERR_GAME;
     }
 }

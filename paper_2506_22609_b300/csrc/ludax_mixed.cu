@@ -22,7 +22,7 @@ using namespace ludax;
 
 namespace {
 
-constexpr int kBuckets = 13;  // 0 TTT, 1 C4, 2 Othello, 3+k Hex (k+2)x(k+2)
+constexpr int kBuckets = 16;  // 0 TTT, 1 C4, 2 Othello, 3+k Hex (k+2)x(k+2), 13 Gomoku, 14 Pente, 15 Yavalath
 constexpr int kHexTableCells = 505;  // sum of n*n for n = 2..11
 
 __host__ __device__ constexpr int hex_table_offset(int n) {
@@ -40,6 +40,9 @@ int bucket_of_desc(int32_t d) {
     case LUDAX_GAME_C4: return (rows == 6 && cols == 7) ? 1 : -2;
     case LUDAX_GAME_OTHELLO: return (rows == 8 && cols == 8) ? 2 : -2;
     case LUDAX_GAME_HEX: return (rows == cols && rows >= 2 && rows <= 11) ? 3 + rows - 2 : -2;
+    case LUDAX_GAME_GOMOKU: return (rows == 15 && cols == 15) ? 13 : -2;
+    case LUDAX_GAME_PENTE: return (rows == 19 && cols == 19) ? 14 : -2;
+    case LUDAX_GAME_YAVALATH: return (rows == 9 && cols == 9) ? 15 : -2;
     default: return -1;
     }
 }
@@ -132,7 +135,10 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         case 9: q = run_hex<8, TABLE>(a, q, end, slots, refill, tables); break;
         case 10: q = run_hex<9, TABLE>(a, q, end, slots, refill, tables); break;
         case 11: q = run_hex<10, TABLE>(a, q, end, slots, refill, tables); break;
-        default: q = run_hex<11, TABLE>(a, q, end, slots, refill, tables); break;
+        case 12: q = run_hex<11, TABLE>(a, q, end, slots, refill, tables); break;
+        case 13: q = run_bucket<Gomoku>(a, q, end, slots, refill, nullptr); break;
+        case 14: q = run_bucket<Pente>(a, q, end, slots, refill, nullptr); break;
+        default: q = run_bucket<Yavalath>(a, q, end, slots, refill, nullptr); break;
         }
     }
 }
@@ -457,6 +463,9 @@ __device__ __forceinline__ int bucket_of_desc_dev(int32_t d) {
     if (game == LUDAX_GAME_C4) return (rows == 6 && cols == 7) ? 1 : -2;
     if (game == LUDAX_GAME_OTHELLO) return (rows == 8 && cols == 8) ? 2 : -2;
     if (game == LUDAX_GAME_HEX) return (rows == cols && rows >= 2 && rows <= 11) ? 3 + rows - 2 : -2;
+    if (game == LUDAX_GAME_GOMOKU) return (rows == 15 && cols == 15) ? 13 : -2;
+    if (game == LUDAX_GAME_PENTE) return (rows == 19 && cols == 19) ? 14 : -2;
+    if (game == LUDAX_GAME_YAVALATH) return (rows == 9 && cols == 9) ? 15 : -2;
     return -1;
 }
 

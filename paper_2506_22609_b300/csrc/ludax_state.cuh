@@ -7,8 +7,11 @@
 //                    Hex: k=0,1 P1 stones (lo, hi word), k=2,3 P2 stones,
 //                         k=4,5 P1 edge-A set, k=6,7 P1 edge-B set,
 //                         k=8,9 P2 edge-A set, k=10,11 P2 edge-B set
-//   meta[e]          uint32: bits 0-7 ply, 8-9 passes, 10 side to move
-//                    (0 = P1), 12-14 outcome+1 (0 ongoing), 15 illegal flag
+//                    Gomoku/Pente/Yavalath: k = 0..W-1 P1 words, W..2W-1 P2 words
+//   meta[e]          uint32: bits 0-7 ply (low byte), 8-9 passes, 10 side to
+//                    move (0 = P1), 12-14 outcome+1 (0 ongoing), 15 illegal
+//                    flag, 16-23 ply (high byte), 24-27 / 28-31 pairs captured
+//                    by P1 / P2 (Pente)
 #pragma once
 #include "ludax_games.cuh"
 
@@ -22,12 +25,14 @@ struct EnvDev {
     unsigned long long* counters;  // [0] refill cursor, [1] illegal actions, [2] capped envs
 };
 
-__device__ __forceinline__ uint32_t pack_meta(int ply, int passes, int side, int outcome, int illegal) {
+__device__ __forceinline__ uint32_t pack_meta(int ply, int passes, int side, int outcome, int illegal, int caps1 = 0,
+                                              int caps2 = 0) {
     return (uint32_t)(ply & 0xFF) | ((uint32_t)(passes & 3) << 8) | ((uint32_t)(side & 1) << 10) |
-           ((uint32_t)((outcome + 1) & 7) << 12) | ((uint32_t)(illegal & 1) << 15);
+           ((uint32_t)((outcome + 1) & 7) << 12) | ((uint32_t)(illegal & 1) << 15) |
+           ((uint32_t)((ply >> 8) & 0xFF) << 16) | ((uint32_t)(caps1 & 15) << 24) | ((uint32_t)(caps2 & 15) << 28);
 }
 __device__ __forceinline__ void unpack_meta(uint32_t m, int& ply, int& passes, int& side, int& outcome) {
-    ply = (int)(m & 0xFF);
+    ply = (int)(m & 0xFF) | (int)(((m >> 16) & 0xFF) << 8);
     passes = (int)((m >> 8) & 3);
     side = (int)((m >> 10) & 1);
     outcome = (int)((m >> 12) & 7) - 1;
@@ -41,12 +46,45 @@ template <int N>
 struct HexN<Hex<N>> {
     static constexpr int value = N;
 };
+// number of 64-bit words per player for the multi-word bitboard games
+template <class G>
+struct WideW {
+    static constexpr int value = 0;
+};
+template <>
+struct WideW<Gomoku> {
+    static constexpr int value = Gomoku::W;
+};
+template <>
+struct WideW<Pente> {
+    static constexpr int value = Pente::W;
+};
+template <>
+struct WideW<Yavalath> {
+    static constexpr int value = Yavalath::W;
+};
 
 // -------------------------------------------------------- load / store --
 template <class G>
 __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
-    unpack_meta(d.meta[e], g.ply, g.passes, g.side, g.outcome);
-    if constexpr (HexN<G>::value == 0) {
+    const uint32_t meta = d.meta[e];
+    unpack_meta(meta, g.ply, g.passes, g.side, g.outcome);
+    if constexpr (WideW<G>::value != 0) {
+        constexpr int W = WideW<G>::value;
+        typename G::Mask p1, p2;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            p1.w[i] = d.planes[(int64_t)i * d.n + e];
+            p2.w[i] = d.planes[(int64_t)(W + i) * d.n + e];
+        }
+        g.own = g.side == 0 ? p1 : p2;
+        g.opp = g.side == 0 ? p2 : p1;
+        if constexpr (G::kGame == Pente::kGame) {
+            const int c1 = (int)((meta >> 24) & 15), c2 = (int)((meta >> 28) & 15);
+            g.caps_own = g.side == 0 ? c1 : c2;
+            g.caps_opp = g.side == 0 ? c2 : c1;
+        }
+    } else if constexpr (HexN<G>::value == 0) {
         uint64_t p1 = d.planes[e], p2 = d.planes[d.n + e];
         uint64_t own = g.side == 0 ? p1 : p2, opp = g.side == 0 ? p2 : p1;
         g.own = (typename G::Mask)own;
@@ -69,12 +107,26 @@ __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
 
 template <class G>
 __device__ __forceinline__ void store_state(const G& g, const EnvDev& d, int64_t e, int illegal = 0) {
-    d.meta[e] = pack_meta(g.ply, g.passes, g.side, g.outcome, illegal);
-    if constexpr (HexN<G>::value == 0) {
+    if constexpr (WideW<G>::value != 0) {
+        constexpr int W = WideW<G>::value;
+        int c1 = 0, c2 = 0;
+        if constexpr (G::kGame == Pente::kGame) {
+            c1 = g.side == 0 ? g.caps_own : g.caps_opp;
+            c2 = g.side == 0 ? g.caps_opp : g.caps_own;
+        }
+        d.meta[e] = pack_meta(g.ply, g.passes, g.side, g.outcome, illegal, c1, c2);
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            d.planes[(int64_t)i * d.n + e] = g.side == 0 ? g.own.w[i] : g.opp.w[i];
+            d.planes[(int64_t)(W + i) * d.n + e] = g.side == 0 ? g.opp.w[i] : g.own.w[i];
+        }
+    } else if constexpr (HexN<G>::value == 0) {
+        d.meta[e] = pack_meta(g.ply, g.passes, g.side, g.outcome, illegal);
         uint64_t own = (uint64_t)g.own, opp = (uint64_t)g.opp;
         d.planes[e] = g.side == 0 ? own : opp;
         d.planes[d.n + e] = g.side == 0 ? opp : own;
     } else {
+        d.meta[e] = pack_meta(g.ply, g.passes, g.side, g.outcome, illegal);
         uint64_t* P = d.planes;
         const int64_t n = d.n;
         bool p1 = g.side == 0;
@@ -99,6 +151,23 @@ __device__ __forceinline__ void set_table(G& g, const B128* table) {
 __device__ __forceinline__ bool mask_has(uint32_t m, int b) { return (m >> b) & 1u; }
 __device__ __forceinline__ bool mask_has(uint64_t m, int b) { return (m >> b) & 1ull; }
 __device__ __forceinline__ bool mask_has(B128 m, int b) { return b < 64 ? ((m.lo >> b) & 1ull) : ((m.hi >> (b - 64)) & 1ull); }
+template <int W>
+__device__ __forceinline__ bool mask_has(const BitsW<W>& m, int b) { return test_bit(m, b); }
+
+// word w of a legal mask in canonical cell order
+template <class G>
+__device__ __forceinline__ uint64_t canon_mask_word(const typename G::Mask& m, int w) {
+    if constexpr (WideW<G>::value == 0) {
+        return G::canon_word(m, w);
+    } else {
+        uint64_t out = 0;
+        for (int j = 0; j < 64; ++j) {
+            const int c = w * 64 + j;
+            if (c < G::kCells && mask_has(m, G::bit_of(c))) out |= 1ull << j;
+        }
+        return out;
+    }
+}
 
 // ------------------------------------------------------------- refill --
 // Warp-aggregated claim of one new work index per calling lane: the lanes

@@ -20,10 +20,12 @@ LIB_PATH = os.path.join(HERE, "libludax.so")
 
 LUDAX_OK = 0
 LUDAX_GAME_TTT, LUDAX_GAME_C4, LUDAX_GAME_OTHELLO, LUDAX_GAME_HEX = 0, 1, 2, 3
+LUDAX_GAME_GOMOKU, LUDAX_GAME_PENTE, LUDAX_GAME_YAVALATH = 4, 5, 6
 LUDAX_OUTCOME_ONGOING, LUDAX_OUTCOME_DRAW, LUDAX_OUTCOME_P1, LUDAX_OUTCOME_P2, LUDAX_OUTCOME_CAPPED = -1, 0, 1, 2, 3
 LUDAX_ROLLOUT_FROM_START, LUDAX_ROLLOUT_WRITE_BACK = 1, 2
 
-GAME_IDS = {"ttt": LUDAX_GAME_TTT, "c4": LUDAX_GAME_C4, "othello": LUDAX_GAME_OTHELLO, "hex": LUDAX_GAME_HEX}
+GAME_IDS = {"ttt": LUDAX_GAME_TTT, "c4": LUDAX_GAME_C4, "othello": LUDAX_GAME_OTHELLO, "hex": LUDAX_GAME_HEX,
+            "gomoku": LUDAX_GAME_GOMOKU, "pente": LUDAX_GAME_PENTE, "yavalath": LUDAX_GAME_YAVALATH}
 
 
 def LUDAX_DESC(game: int, rows: int, cols: int) -> int:
@@ -412,7 +414,7 @@ class Env:
         with torch.cuda.device(self.device):
             self.handle = ludax_env_create(game, rows, cols, num_envs, env_offset, stream)
         self.num_actions, self.mask_words, _ = ludax_env_sizes(self.handle)
-        self.cells = rows * cols
+        self.cells = self.num_actions - (1 if game == LUDAX_GAME_OTHELLO else 0)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

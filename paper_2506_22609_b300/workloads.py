@@ -11,7 +11,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-TTT, C4, OTHELLO, HEX = 0, 1, 2, 3
+TTT, C4, OTHELLO, HEX, GOMOKU, PENTE, YAVALATH = 0, 1, 2, 3, 4, 5, 6
 
 
 def desc(game: int, rows: int, cols: int) -> int:
@@ -35,6 +35,10 @@ TTT_1K = Config("ttt3x3_1024env_seed0", TTT, 3, 3, 1024, 0)
 C4_64K = Config("connect4_6x7_65536env_seed1", C4, 6, 7, 65536, 1)
 OTHELLO_256K = Config("othello8x8_262144env_seed2", OTHELLO, 8, 8, 262144, 2)
 HEX11_64K = Config("hex11x11_65536env_seed4", HEX, 11, 11, 65536, 4)
+# the line-game family (Gomoku, Pente, Yavalath)
+GOMOKU_64K = Config("gomoku15x15_65536env_seed5", GOMOKU, 15, 15, 65536, 5)
+PENTE_64K = Config("pente19x19_65536env_seed6", PENTE, 19, 19, 65536, 6)
+YAVALATH_64K = Config("yavalath61_65536env_seed7", YAVALATH, 9, 9, 65536, 7)
 
 # The mixed batch: 2^20 envs over six games, seed 3.
 MIXED_GAMES = [(TTT, 3, 3), (C4, 6, 7), (OTHELLO, 8, 8), (HEX, 7, 7), (HEX, 9, 9), (HEX, 11, 11)]
@@ -56,7 +60,8 @@ def mixed_descriptors(n: int = MIXED_ENVS, layout: str = "block") -> np.ndarray:
 
 def random_descriptors(n: int, seed: int) -> np.ndarray:
     """Descriptors drawn uniformly over every supported (game, size)."""
-    all_desc = [desc(TTT, 3, 3), desc(C4, 6, 7), desc(OTHELLO, 8, 8)] + [desc(HEX, k, k) for k in range(2, 12)]
+    all_desc = [desc(TTT, 3, 3), desc(C4, 6, 7), desc(OTHELLO, 8, 8)] + [desc(HEX, k, k) for k in range(2, 12)] + [
+        desc(GOMOKU, 15, 15), desc(PENTE, 19, 19), desc(YAVALATH, 9, 9)]
     rng = np.random.default_rng(seed)
     return np.array(all_desc, dtype=np.int32)[rng.integers(0, len(all_desc), n)]
 

@@ -15,7 +15,13 @@ from paper_2506_22609_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 GAMES = [("ttt", G.TTT, 3, 3), ("c4", G.C4, 6, 7), ("othello", G.OTHELLO, 8, 8)] + [
-    (f"hex{n}", G.HEX, n, n) for n in (2, 3, 5, 7, 9, 11)]
+    (f"hex{n}", G.HEX, n, n) for n in (2, 3, 5, 7, 9, 11)] + [
+    ("gomoku", G.GOMOKU, 15, 15), ("pente", G.PENTE, 19, 19), ("yavalath", G.YAVALATH, 9, 9)]
+BIG = (G.GOMOKU, G.PENTE)
+
+
+def cells_of(game, rows, cols):
+    return G.num_cells(game, rows, cols)
 GAME_IDS = [g[0] for g in GAMES]
 
 
@@ -52,7 +58,7 @@ def assert_states_equal(env, s):
 # ---------------------------------------------------------------- rollouts --
 @pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
 def test_rollout_from_start_matches_oracle(L, name, game, rows, cols):
-    n, seed, off = 2600, 7, 12345
+    n, seed, off = (700 if game in BIG else 2600), 7, 12345
     env = L.Env(game, rows, cols, n, env_offset=off)
     out, plies = env.rollout(seed, from_start=True, write_back=True)
     o_out, o_plies, o_boards = G.rollout_start(game, rows, cols, n, seed, env_offset=off, want_boards=True)
@@ -69,11 +75,11 @@ def test_rollout_from_start_matches_oracle(L, name, game, rows, cols):
                                  (96, 3, 1, 1, 0), (256, 0, 1, 0, 4), (128, 2, 1, 1, 8), (448, 1, 1, 0, 16),
                                  (64, 1, 1, 0, 1)],
                          ids=lambda c: "b{}_bps{}_ept{}_tab{}_cmp{}".format(*c))
-@pytest.mark.parametrize("name,game,rows,cols", [GAMES[1], GAMES[2], GAMES[7], GAMES[8]],
-                         ids=["c4", "othello", "hex9", "hex11"])
+@pytest.mark.parametrize("name,game,rows,cols", [GAMES[1], GAMES[2], GAMES[7], GAMES[8], GAMES[10], GAMES[11]],
+                         ids=["c4", "othello", "hex9", "hex11", "pente", "yavalath"])
 def test_launch_shape_does_not_change_results(L, name, game, rows, cols, cfg):
     # persistent grids smaller than the batch exercise the refill path
-    n, seed = 20000, 3
+    n, seed = (6000 if game in BIG else 20000), 3
     env = L.Env(game, rows, cols, n)
     out, plies = env.rollout(seed, cfg=L.make_cfg(*cfg))
     ref_out, ref_plies = env.rollout(seed)
@@ -87,7 +93,7 @@ def test_launch_shape_does_not_change_results(L, name, game, rows, cols, cfg):
 
 @pytest.mark.parametrize("n", [1, 31, 33, 257])
 def test_ragged_and_tiny_batches(L, n):
-    for name, game, rows, cols in (GAMES[0], GAMES[1], GAMES[2], GAMES[8]):
+    for name, game, rows, cols in (GAMES[0], GAMES[1], GAMES[2], GAMES[8], GAMES[9], GAMES[11]):
         env = L.Env(game, rows, cols, n)
         o, p, _ = G.rollout_start(game, rows, cols, n, 11)
         for cfg in [(64, 1, 2, 0, 0), (64, 1, 1, 0, 4), (32, 1, 1, 1, 2)]:
@@ -96,7 +102,8 @@ def test_ragged_and_tiny_batches(L, n):
 
 
 # ------------------------------------------------- benchmark-size configs --
-@pytest.mark.parametrize("cfg", [W.TTT_1K, W.C4_64K, W.OTHELLO_256K, W.HEX11_64K], ids=lambda c: c.name)
+@pytest.mark.parametrize("cfg", [W.TTT_1K, W.C4_64K, W.OTHELLO_256K, W.HEX11_64K, W.GOMOKU_64K, W.PENTE_64K,
+                                 W.YAVALATH_64K], ids=lambda c: c.name)
 def test_benchmark_configs_sampled(L, cfg):
     env = L.Env(cfg.game, cfg.rows, cfg.cols, cfg.num_envs)
     out, plies = env.rollout(cfg.seed, cfg=L.make_cfg(*W.bench_cfg(cfg)))
@@ -105,14 +112,15 @@ def test_benchmark_configs_sampled(L, cfg):
         o, p, _ = G.rollout_start(cfg.game, cfg.rows, cfg.cols, cfg.num_envs, cfg.seed)
         assert (out == o).all() and (plies == p).all()
     else:
-        for e in W.sample_envs(cfg.num_envs, 1500, 5):
+        for e in W.sample_envs(cfg.num_envs, 300 if cfg.game in BIG else 1500, 5):
             o, p, _ = G.rollout_start(cfg.game, cfg.rows, cfg.cols, 1, cfg.seed, env_offset=int(e))
             assert o[0] == out[e] and p[0] == plies[e], e
     assert set(np.unique(out)) <= {0, 1, 2}
     # properties that hold at any size: length bounds and the winner moved last
-    lo, hi = {G.TTT: (5, 9), G.C4: (7, 42), G.OTHELLO: (11, 128), G.HEX: (2 * cfg.rows - 1, cfg.rows ** 2)}[cfg.game]
+    lo, hi = {G.TTT: (5, 9), G.C4: (7, 42), G.OTHELLO: (11, 128), G.HEX: (2 * cfg.rows - 1, cfg.rows ** 2),
+              G.GOMOKU: (9, 225), G.PENTE: (9, 2000), G.YAVALATH: (5, 61)}[cfg.game]
     assert plies.min() >= lo and plies.max() <= hi
-    if cfg.game in (G.TTT, G.C4, G.HEX):
+    if cfg.game in (G.TTT, G.C4, G.HEX, G.GOMOKU, G.PENTE):
         won = out != 0
         assert ((plies[won] % 2 == 1) == (out[won] == 1)).all()
     if cfg.game == G.HEX:
@@ -122,12 +130,12 @@ def test_benchmark_configs_sampled(L, cfg):
 # ------------------------------------------------------ step-per-launch --
 @pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
 def test_random_step_reproduces_rollout(L, name, game, rows, cols):
-    n, seed = 1500, 21
+    n, seed = (300 if game in BIG else 1500), 21
     env = L.Env(game, rows, cols, n, env_offset=99)
     ref = L.Env(game, rows, cols, n, env_offset=99)
     r_out, r_plies = ref.rollout(seed, write_back=True)
     done = torch.zeros(n, dtype=torch.bool, device="cuda")
-    cap = {G.TTT: 9, G.C4: 42, G.OTHELLO: 128, G.HEX: rows * cols}[game]
+    cap = G.ply_cap(game, rows, cols)
     final_rew = torch.zeros(n, 2, device="cuda")
     for _ in range(cap + 2):
         rew, term = env.random_step(seed)
@@ -162,11 +170,11 @@ def test_step_api_matches_oracle(L, name, game, rows, cols):
     # Oracle-chosen trajectories, 10% of steps with an arbitrary (often
     # illegal) action: legal masks, rewards, terminated flags and full state
     # must agree after every step.
-    n = 700
+    n = 128 if game in BIG else 700
     rng = np.random.default_rng(game * 100 + rows)
     env = L.Env(game, rows, cols, n)
     s = G.reset(game, rows, cols, n)
-    A, cells = G.num_actions(game, rows, cols), rows * cols
+    A, cells = G.num_actions(game, rows, cols), cells_of(game, rows, cols)
     assert env.num_actions == A
     n_illegal = 0
     for _ in range(cells * 2 + 4):
@@ -219,10 +227,10 @@ def test_reset_mask_and_finished_env_noop(L):
 # --------------------------------------------------- positions and values --
 @pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
 def test_set_state_rollout_from_positions(L, name, game, rows, cols):
-    n = 1200
+    n = 300 if game in BIG else 1200
     rng = np.random.default_rng(rows + 17 * game)
     s = G.reset(game, rows, cols, n)
-    stop = rng.integers(0, rows * cols, n).astype(np.int16)
+    stop = rng.integers(0, cells_of(game, rows, cols), n).astype(np.int16)
     G.rollout_from(s, seed=5, stop_ply=stop)
     env = L.Env(game, rows, cols, n, env_offset=7)
     env.set_state(*(torch.from_numpy(x) for x in (s.board, s.to_move, s.ply, s.passes, s.outcome)))
