@@ -41,7 +41,8 @@ METRIC = "env steps/sec on 1 B300 (random playouts); value estimates/sec at stat
 # RNG draw (13 logic/shift/add + 7 multiply), legal mask, popcount, k-th-bit
 # select, apply (Reversi flips), end test.  Reversi's count (437) is within 2%
 # of the instructions ncu measures executed per ply (444).
-ALG_OPS_PER_STEP = {"ttt": 75, "c4": 112, "othello": 437, "hex": 180}
+ALG_OPS_PER_STEP = {"ttt": 75, "c4": 112, "othello": 437, "hex": 180, "gomoku": 330, "pente": 700,
+                    "yavalath": 150}
 
 # DRAM bytes per launch of the benchmarked kernel, from the committed ncu
 # captures (profiles/); None once the kernel changes until it is captured again.
@@ -55,7 +56,8 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "mixed", "step_c4"])
+    p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "gomoku", "pente", "yavalath",
+                                                        "mixed", "step_c4"])
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
@@ -66,11 +68,12 @@ def parse():
 def workload_cfg(name):
     from paper_2506_22609_b300 import workloads as W
 
-    return {"c4": W.C4_64K, "ttt": W.TTT_1K, "othello": W.OTHELLO_256K, "hex11": W.HEX11_64K}[name]
+    return {"c4": W.C4_64K, "ttt": W.TTT_1K, "othello": W.OTHELLO_256K, "hex11": W.HEX11_64K, "gomoku": W.GOMOKU_64K,
+            "pente": W.PENTE_64K, "yavalath": W.YAVALATH_64K}[name]
 
 
 def game_key(cfg):
-    return {0: "ttt", 1: "c4", 2: "othello", 3: "hex"}[cfg.game]
+    return {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente", 6: "yavalath"}[cfg.game]
 
 
 def measured_peaks():
@@ -497,12 +500,14 @@ def main():
                                 "sample": sample}
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {}
-        for name in ("ttt", "othello", "hex11"):
+        for name in ("ttt", "othello", "hex11", "gomoku", "pente", "yavalath"):
             c = workload_cfg(name)
             e, lc, ms2, spl = bench_rollout_config(L, W, c, 20, 3, flush_buf)
             m2 = statistics.median(ms2)
-            extras[c.name] = {"env_steps_per_s": round(spl / (m2 / 1e3), 1), "median_launch_ms": round(m2, 5),
-                              "env_steps_per_launch": spl, "launch": lc.as_dict()}
+            rate = spl / (m2 / 1e3)
+            extras[c.name] = {"env_steps_per_s": round(rate, 1), "median_launch_ms": round(m2, 5),
+                              "env_steps_per_launch": spl, "launch": lc.as_dict(),
+                              "alu_frac": round(ALG_OPS_PER_STEP[game_key(c)] * rate / peak_ops, 4)}
             e.close()
         ms3, tot = bench_mixed(L, W, 10, 2, flush_buf)
         m3 = statistics.median(ms3)

@@ -289,7 +289,7 @@ int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out);
 /* Autotuner for ludax_rollout on one env batch (from the start position, no
  * write-back; the env's stored state is not touched): walks block_threads x
  * blocks_per_sm x envs_per_thread (x hex_nbr_table for Hex), timing each
- * like ludax_autotune.  ms_table_out (nullable) needs room for 256 floats. */
+ * like ludax_autotune.  ms_table_out (nullable) needs room for 512 floats. */
 int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
                        float* ms_table_out, int32_t* n_candidates_out);
 

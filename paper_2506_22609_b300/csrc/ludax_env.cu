@@ -680,7 +680,7 @@ int ludax_sync(ludax_env* env, int64_t timeout_ms) {
 int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
                        float* ms_table_out, int32_t* n_candidates_out) {
     if (!env || !best_out || reps < 1) return LUDAX_ERR_ARG;
-    static const int blocks[] = {64, 128, 256, 512};
+    static const int blocks[] = {64, 128, 192, 256, 384, 448, 512};
     static const int bps[] = {0, 2, 4, 8, 16};
     const int tables = env->game == LUDAX_GAME_HEX ? 2 : 1;
     int8_t* d_out = nullptr;
@@ -722,7 +722,7 @@ int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch
                             float x = ts[j]; ts[j] = ts[j - 1]; ts[j - 1] = x;
                         }
                     float med = ts[nt / 2];
-                    if (ms_table_out && k < 256) ms_table_out[k] = med;
+                    if (ms_table_out && k < 512) ms_table_out[k] = med;
                     ++k;
                     if (med < best) {
                         best = med;

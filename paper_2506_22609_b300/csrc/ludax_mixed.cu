@@ -370,7 +370,7 @@ int ludax_mixed_plan_destroy(ludax_mixed_plan* p) {
 }
 
 int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out) {
-    static const int blocks[] = {64, 128, 256, 512};
+    static const int blocks[] = {64, 128, 192, 256, 384, 448, 512};
     static const int bps[] = {0, 2, 4, 8, 16};
     int k = 0;
     for (int t = 0; t < 2; ++t)

@@ -291,7 +291,7 @@ def ludax_autotune_env(h, seed: int = 0, reps: int = 5):
     cands_n = ctypes.c_int32()
     best = ludax_launch_cfg()
     best_ms = ctypes.c_float()
-    table = (ctypes.c_float * 256)()
+    table = (ctypes.c_float * 512)()
     _check(lib().ludax_autotune_env(h, seed, reps, ctypes.byref(best), ctypes.byref(best_ms), table,
                                     ctypes.byref(cands_n)), "ludax_autotune_env")
     return best, best_ms.value, list(table)[: cands_n.value]

@@ -79,9 +79,12 @@ def sample_envs(n_total: int, k: int, seed: int) -> np.ndarray:
 # ludax_autotune_env / ludax_autotune on a B300.
 BENCH_CFGS = {
     TTT_1K.name: (64, 0, 1, 0, 16),
-    C4_64K.name: (256, 4, 1, 0, 16),
-    OTHELLO_256K.name: (256, 0, 1, 0, 0),
-    HEX11_64K.name: (512, 4, 1, 1, 16),
+    C4_64K.name: (448, 4, 1, 0, 16),
+    OTHELLO_256K.name: (448, 0, 1, 0, 0),
+    HEX11_64K.name: (448, 2, 1, 1, 16),
+    GOMOKU_64K.name: (448, 0, 1, 0, 16),
+    PENTE_64K.name: (448, 4, 1, 0, 16),
+    YAVALATH_64K.name: (448, 0, 1, 0, 16),
 }
 MIXED_BENCH_CFG = (128, 0, 1, 1, 0)
 
