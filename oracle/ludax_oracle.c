@@ -29,7 +29,11 @@
  * stone that closes own-opp-opp-own along any of 8 directions removes the two
  * opponent stones; ten captured stones win; P1's first move is the centre),
  * Yavalath on the 61-cell hexagon (four in a row wins, otherwise three in a
- * row loses); all three end in a draw on a full board.
+ * row loses); all three end in a draw on a full board.  The parametric line
+ * game (place on an empty cell, optionally with Connect-Four gravity; a line
+ * of at least -- or exactly -- L wins, or loses in the misere variant; a full
+ * board draws) covers Tic-Tac-Toe, Connect Four and their variants on any
+ * board of up to 128 padded cells.
  *
  * Readings where the paper is silent (they are listed in the design doc):
  *   Hex neighbours of (r,c): (r-1,c) (r+1,c) (r,c-1) (r,c+1) (r-1,c+1) (r+1,c-1);
@@ -52,6 +56,10 @@
 #define OR_GOMOKU 4
 #define OR_PENTE 5
 #define OR_YAVALATH 6
+#define OR_LINE 7 /* parametric line game; the game argument packs 7 | L << 8 | flags << 12 */
+#define OR_LINE_EXACT 1
+#define OR_LINE_GRAVITY 2
+#define OR_LINE_MISERE 4
 
 #define OR_ONGOING (-1)
 #define OR_DRAW 0
@@ -71,6 +79,7 @@ typedef struct {
     int32_t outcome;          /* OR_ONGOING, OR_DRAW, OR_P1, OR_P2, OR_CAPPED */
     int32_t illegal;          /* 1 when the game ended on an illegal action */
     int32_t captures[3];      /* Pente: opponent stones captured by player 1 / 2 */
+    int32_t line, flags;      /* parametric line game: line length, OR_LINE_* flags */
 } ogame;
 
 /* ------------------------------------------------------------------ RNG --
@@ -135,7 +144,8 @@ static int in_board(const ogame* g, int r, int c) { return cell_id(g, r, c) >= 0
 static int at(const ogame* g, int r, int c) { return g->cell[cell_id(g, r, c)]; }
 
 int oracle_ply_cap(int game, int rows, int cols) {
-    switch (game) {
+    switch (game & 0xFF) {
+    case OR_LINE: return rows * cols;
     case OR_TTT: return 9;
     case OR_C4: return 42;
     case OR_OTHELLO: return 128;
@@ -148,13 +158,20 @@ int oracle_ply_cap(int game, int rows, int cols) {
 }
 
 /* Number of actions: one per cell, plus the pass for Reversi. */
-int oracle_num_cells(int game, int rows, int cols) { return game == OR_YAVALATH ? 61 : rows * cols; }
+int oracle_num_cells(int game, int rows, int cols) { return (game & 0xFF) == OR_YAVALATH ? 61 : rows * cols; }
 
 int oracle_num_actions(int game, int rows, int cols) {
     return oracle_num_cells(game, rows, cols) + (game == OR_OTHELLO ? 1 : 0);
 }
 
 int oracle_check_params(int game, int rows, int cols) {
+    if ((game & 0xFF) == OR_LINE) {
+        int L = (game >> 8) & 15, fl = (game >> 12) & 7;
+        if (game >> 15) return -1;
+        (void)fl;
+        return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128 && L >= 2 && L <= (rows > cols ? rows : cols)) ? 0
+                                                                                                               : -1;
+    }
     switch (game) {
     case OR_TTT: return (rows == 3 && cols == 3) ? 0 : -1;
     case OR_C4: return (rows == 6 && cols == 7) ? 0 : -1;
@@ -171,6 +188,11 @@ int oracle_check_params(int game, int rows, int cols) {
 int oracle_init(ogame* g, int game, int rows, int cols) {
     if (oracle_check_params(game, rows, cols) != 0) return -1;
     memset(g, 0, sizeof(*g));
+    if ((game & 0xFF) == OR_LINE) {
+        g->line = (game >> 8) & 15;
+        g->flags = (game >> 12) & 7;
+        game = OR_LINE;
+    }
     g->game = game;
     g->rows = rows;
     g->cols = cols;
@@ -316,6 +338,11 @@ int oracle_legal(const ogame* g, uint8_t* legal) {
         case OR_GOMOKU:
         case OR_YAVALATH: ok = 1; break;
         case OR_PENTE: ok = g->ply > 0 || i == (g->rows / 2) * g->cols + g->cols / 2; break; /* first move: centre */
+        case OR_LINE: {
+            int r = i / g->cols, c = i % g->cols;
+            ok = !(g->flags & OR_LINE_GRAVITY) || r == g->rows - 1 || at(g, r + 1, c) != 0;
+            break;
+        }
         case OR_C4: {
             int r = i / g->cols, c = i % g->cols;
             ok = (r == g->rows - 1) || (at(g, r + 1, c) != 0);
@@ -409,6 +436,12 @@ int oracle_apply(ogame* g, int action) {
         if (has_line(g, p, 5) || g->captures[p] >= 10) finish(g, p);
         else if (board_full(g)) finish(g, OR_DRAW);
         break;
+    case OR_LINE: {
+        int made = (g->flags & OR_LINE_EXACT) ? has_line_exact(g, p, g->line) : has_line(g, p, g->line);
+        if (made) finish(g, (g->flags & OR_LINE_MISERE) ? 3 - p : p);
+        else if (board_full(g)) finish(g, OR_DRAW);
+        break;
+    }
     case OR_YAVALATH:
         if (has_line(g, p, 4)) finish(g, p);
         else if (has_line(g, p, 3)) finish(g, 3 - p);
@@ -576,6 +609,7 @@ int oracle_rollout_mixed(const int32_t* desc, int64_t n, int64_t env_offset, uin
     ogame g;
     for (int64_t e = 0; e < n; e++) {
         int game = desc[e] & 0xFF, rows = (desc[e] >> 8) & 0xFF, cols = (desc[e] >> 16) & 0xFF;
+        if (game == OR_LINE) game |= ((desc[e] >> 24) & 15) << 8 | ((desc[e] >> 28) & 7) << 12;
         if (oracle_init(&g, game, rows, cols) != 0) return -1;
         oracle_playout(&g, seed, (uint64_t)(env_offset + e), -1);
         outcome[e] = (int8_t)g.outcome;

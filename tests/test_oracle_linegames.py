@@ -182,3 +182,42 @@ def test_pente_random_games_consistent():
         placed_by_loser = plies[e] // 2
         captured_by_w = placed_by_loser - stones[3 - w]
         assert max(_runs(b, w)) >= 5 or captured_by_w >= 10
+
+
+# ---------------------------------------------- parametric line game (m,n,k) --
+LINE = 7
+
+
+def line_game(L, exact=False, gravity=False, misere=False):
+    return LINE | (L << 8) | ((1 if exact else 0) | (2 if gravity else 0) | (4 if misere else 0)) << 12
+
+
+def test_line_game_closed_form_perft():
+    # 4x4, line of 4: no game ends before ply 7, so perft = falling factorial
+    want = 1
+    for d in range(1, 6):
+        want *= 16 - (d - 1)
+        assert G.perft(line_game(4), 4, 4, d) == want
+    # gravity on 5 columns of height 4: every column stays open for 4 plies
+    for d in range(1, 5):
+        assert G.perft(line_game(4, gravity=True), 4, 5, d) == 5 ** d
+
+
+def test_misere_tic_tac_toe_loser_made_the_line():
+    out, plies, boards = G.rollout_start(line_game(3, misere=True), 3, 3, 500, seed=8, want_boards=True)
+    for e in range(500):
+        b = boards[e].reshape(3, 3)
+        mover = 1 if plies[e] % 2 == 1 else 2
+        if out[e] == 0:
+            assert plies[e] == 9 and max(_runs(b, 1)) < 3 and max(_runs(b, 2)) < 3
+        else:
+            assert out[e] == 3 - mover and max(_runs(b, mover)) >= 3
+
+
+def test_exact_line_game_matches_gomoku_rule_on_small_board():
+    # exactly-4 on 7x7: the winner has a maximal run of exactly 4 and the loser none
+    out, plies, boards = G.rollout_start(line_game(4, exact=True), 7, 7, 300, seed=2, want_boards=True)
+    for e in range(300):
+        b = boards[e].reshape(7, 7)
+        if out[e] in (1, 2):
+            assert 4 in _runs(b, out[e]) and 4 not in _runs(b, 3 - out[e])
