@@ -69,6 +69,15 @@ extern "C" {
                                 stones win; P1's first move is the centre  */
 #define LUDAX_GAME_YAVALATH 6 /* Yavalath, 61-cell hexagon (board params
                                  9x9): four in a row wins, three loses     */
+#define LUDAX_GAME_LINE 7     /* parametric line game on any rows x cols board
+                                 with rows*(cols+1) <= 128: place on an empty
+                                 cell (with gravity if LUDAX_LINE_GRAVITY); a
+                                 line of at least `line` stones (exactly, with
+                                 LUDAX_LINE_EXACT) wins -- loses, with
+                                 LUDAX_LINE_MISERE; a full board draws    */
+#define LUDAX_LINE_EXACT 1
+#define LUDAX_LINE_GRAVITY 2
+#define LUDAX_LINE_MISERE 4
 
 /* ---------------------------------------------------------- outcomes -- */
 #define LUDAX_OUTCOME_ONGOING (-1)
@@ -84,6 +93,8 @@ extern "C" {
 typedef struct {
     int32_t rows;
     int32_t cols;
+    int32_t line;  /* LUDAX_GAME_LINE: line length, 2..min(15, max(rows, cols)); else 0 */
+    int32_t flags; /* LUDAX_GAME_LINE: LUDAX_LINE_* bits; else 0                   */
 } ludax_board_params;
 
 typedef struct ludax_env ludax_env;
@@ -227,6 +238,9 @@ const char* ludax_status_string(int status);
  * (LUDAX_DESC(g, r, c)).  Results match per-game ludax_rollout calls from the
  * start position with the same (seed, global env index) bit for bit.       */
 #define LUDAX_DESC(g, r, c) ((int32_t)((g) | ((r) << 8) | ((c) << 16)))
+/* descriptor of the parametric line game: line length in bits 24-27, flags in 28-30 */
+#define LUDAX_DESC_LINE(r, c, line, flags) \
+    ((int32_t)(LUDAX_GAME_LINE | ((r) << 8) | ((c) << 16) | ((line) << 24) | ((flags) << 28)))
 
 typedef struct ludax_mixed_plan ludax_mixed_plan;
 
@@ -257,7 +271,7 @@ int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_o
  * deployment entry point of this library.)
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  *     Its scratch -- the game-grouped work queue and the claim cursors -- is a
- *     static device array of 4 MiB plus 512 bytes, held by every GPU that
+ *     static device array of 4 MiB plus 1 KiB, held by every GPU that
  *     loads this library until the process exits.
  *   - num_envs at most 1,048,576 (2^20): larger batches return LUDAX_ERR_SIZE
  *     before anything is launched.

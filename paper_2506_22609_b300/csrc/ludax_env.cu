@@ -20,7 +20,7 @@ using namespace ludax;
 namespace {
 
 EnvDev dev_of(const ludax_env* env) {
-    return EnvDev{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters};
+    return EnvDev{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters, env->desc, env->cells};
 }
 
 int launch_status() { return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA; }
@@ -52,7 +52,7 @@ __global__ void legal_kernel(EnvDev d, uint64_t* out, uint8_t* pass_legal, int w
         m = g.legal();
         pass = G::kHasPass && !any(m);
     }
-    for (int w = 0; w < words; ++w) out[e * words + w] = canon_mask_word<G>(m, w);
+    for (int w = 0; w < words; ++w) out[e * words + w] = canon_mask_word(g, m, w);
     if (pass_legal) pass_legal[e] = pass ? 1 : 0;
 }
 
@@ -75,8 +75,8 @@ __global__ void step_kernel(EnvDev d, const int32_t* actions, float2* rewards, u
         if (G::kHasPass && a == G::kCells) {
             ok = !any(m);
             if (ok) g.pass();
-        } else if (a >= 0 && a < G::kCells) {
-            int b = G::bit_of(a);
+        } else if (a >= 0 && a < cells_of(g)) {
+            int b = g.bit_of(a);
             ok = mask_has(m, b);
             if (ok) g.place(b);
         }
@@ -121,9 +121,9 @@ __global__ void get_state_kernel(EnvDev d, ludax_state_view v) {
     G g;
     set_table(g, nullptr);
     load_state(g, d, e);
-    int8_t* b = v.board + e * G::kCells;
-    for (int c = 0; c < G::kCells; ++c) {
-        int bit = G::bit_of(c);
+    int8_t* b = v.board + e * d.cells;
+    for (int c = 0; c < d.cells; ++c) {
+        int bit = g.bit_of(c);
         int v_own = mask_has(g.own, bit), v_opp = mask_has(g.opp, bit);
         b[c] = (int8_t)(v_own ? g.side + 1 : (v_opp ? 2 - g.side : 0));
     }
@@ -154,12 +154,13 @@ __global__ void set_state_kernel(EnvDev d, ludax_state_view v) {
     if (e >= d.n) return;
     G g;
     set_table(g, nullptr);
+    configure(g, d.desc);
     typename G::Mask p1{}, p2{};
-    const int8_t* b = v.board + e * G::kCells;
-    for (int c = 0; c < G::kCells; ++c) {
+    const int8_t* b = v.board + e * d.cells;
+    for (int c = 0; c < d.cells; ++c) {
         int x = b[c];
-        if (x == 1) set_bit(p1, G::bit_of(c));
-        if (x == 2) set_bit(p2, G::bit_of(c));
+        if (x == 1) set_bit(p1, g.bit_of(c));
+        if (x == 2) set_bit(p2, g.bit_of(c));
     }
     g.side = v.to_move[e] == 2 ? 1 : 0;
     g.ply = v.ply[e];
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
     }
     auto init = [&](int i) {
         const int64_t e = env[i];
+        configure(g[i], a.d.desc);
         if (a.from_start) g[i].reset();
         else load_state(g[i], a.d, e);
         key[i] = env_key(a.seed_key, (uint64_t)(a.d.env_offset + e));
@@ -309,6 +311,7 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
     int stop = 0;
     bool active = env < n;
     auto init = [&]() {
+        configure(g, a.d.desc);
         if (a.from_start) g.reset();
         else load_state(g, a.d, env);
         key = env_key(a.seed_key, (uint64_t)(a.d.env_offset + env));
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
         __syncthreads();
         if (tid < total) {
             slot_load(buf, B, tid, g, key, env, stop);
+            configure(g, a.d.desc);
             rhi = draw_hi(key, (uint32_t)g.ply);
             active = true;
         } else {
@@ -478,16 +482,25 @@ int ludax_env_create(ludax_env** out, int32_t game, const ludax_board_params* p,
     int st = dispatch_game(game, p->rows, p->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         planes = G::kPlanes;
-        cells = G::kCells;
+        cells = G::kGame == LineGame::kGame ? p->rows * p->cols : G::kCells;
         return LUDAX_OK;
     });
     if (st != LUDAX_OK) return st;
+    int32_t desc = game | (p->rows << 8) | (p->cols << 16);
+    if (game == LUDAX_GAME_LINE) {
+        const int mx = p->rows > p->cols ? p->rows : p->cols;
+        if (p->line < 2 || p->line > 15 || p->line > mx || (p->flags & ~7)) return LUDAX_ERR_SIZE;
+        desc |= (p->line << 24) | (p->flags << 28);
+    } else if (p->line != 0 || p->flags != 0) {
+        return LUDAX_ERR_ARG;
+    }
     ludax_env* env = new (std::nothrow) ludax_env();
     if (!env) return LUDAX_ERR_NOMEM;
     env->game = game;
     env->rows = p->rows;
     env->cols = p->cols;
     env->cells = cells;
+    env->desc = desc;
     env->num_actions = env->cells + (game == LUDAX_GAME_OTHELLO ? 1 : 0);
     env->mask_words = (env->cells + 63) / 64;
     env->planes = planes;

@@ -796,6 +796,114 @@ struct Yavalath {
     }
 };
 
+// ------------------------------------------------ parametric line game --
+// Any R x C board with R * (C + 1) <= 128 in a stride C + 1 layout (two
+// words): place on an empty cell -- with Connect-Four gravity if asked -- and
+// a line of at least L (or exactly L) stones along a row, column or diagonal
+// wins, or loses in the misere variant; a full board draws.  All parameters
+// come from the env's descriptor at run time.
+__device__ __forceinline__ uint64_t shr64c(uint64_t x, int s) { return s >= 64 ? 0ull : (x >> s); }
+__device__ __forceinline__ uint64_t shl64c(uint64_t x, int s) { return s >= 64 ? 0ull : (x << s); }
+// bit i of the result = bit i + s of a (0 <= s, run-time)
+__device__ __forceinline__ BitsW<2> shr_rt(const BitsW<2>& a, int s) {
+    BitsW<2> o;
+    if (s >= 64) {
+        o.w[0] = shr64c(a.w[1], s - 64);
+        o.w[1] = 0;
+    } else {
+        o.w[0] = (a.w[0] >> s) | (s == 0 ? 0ull : a.w[1] << (64 - s));
+        o.w[1] = a.w[1] >> s;
+    }
+    return o;
+}
+// bit i of the result = bit i - s of a
+__device__ __forceinline__ BitsW<2> shl_rt(const BitsW<2>& a, int s) {
+    BitsW<2> o;
+    if (s >= 64) {
+        o.w[1] = shl64c(a.w[0], s - 64);
+        o.w[0] = 0;
+    } else {
+        o.w[1] = (a.w[1] << s) | (s == 0 ? 0ull : a.w[0] >> (64 - s));
+        o.w[0] = a.w[0] << s;
+    }
+    return o;
+}
+
+struct LineGame {
+    static constexpr int kGame = 7, kRows = 0, kCols = 0, kCells = 128, kCap = 128, W = 2, kPlanes = 4;
+    static constexpr bool kHasPass = false;
+    static constexpr int kExact = 1, kGravity = 2, kMisere = 4;
+    using Mask = BitsW<2>;
+    Mask own, opp;
+    int side, ply, passes, outcome;
+    int R, C, S, L, flags;
+    Mask valid, bottom;
+
+    // parameters from a descriptor: game | R << 8 | C << 16 | L << 24 | flags << 28
+    __device__ __forceinline__ void configure(int32_t desc) {
+        R = (desc >> 8) & 0xFF;
+        C = (desc >> 16) & 0xFF;
+        L = (desc >> 24) & 15;
+        flags = (desc >> 28) & 7;
+        S = C + 1;
+        const uint64_t row = (C >= 64) ? ~0ull : ((1ull << C) - 1ull);
+        valid = Mask{{0, 0}};
+        for (int r = 0; r < R; ++r) valid = valid | shl_rt(Mask{{row, 0}}, r * S);
+        bottom = shl_rt(Mask{{row, 0}}, (R - 1) * S);
+    }
+    __device__ __forceinline__ int cells() const { return R * C; }
+    __device__ __forceinline__ void reset() {
+        own = opp = Mask{{0, 0}};
+        side = ply = passes = 0;
+        outcome = kOngoing;
+    }
+    __device__ __forceinline__ Mask legal() const {
+        const Mask occ = own | opp;
+        Mask m = valid & ~occ;
+        if (flags & kGravity) m = m & (shr_rt(occ, S) | bottom);
+        return m;
+    }
+    __device__ __forceinline__ bool line_dir(const Mask& b, int d) const {
+        Mask m = b;
+        for (int i = 1; i < L; ++i) m = m & shr_rt(b, i * d);
+        if (flags & kExact) m = m & ~shl_rt(b, d) & ~shr_rt(b, L * d);
+        return any(m);
+    }
+    __device__ __forceinline__ void place(int b) {
+        set_bit_w(own, b);
+        const bool made = line_dir(own, 1) | line_dir(own, S) | line_dir(own, S + 1) | line_dir(own, S - 1);
+        if (made) outcome = (flags & kMisere) ? 2 - side : side + 1;
+        else if (!any(valid & ~(own | opp))) outcome = kDraw;
+        ++ply;
+        Mask t = own; own = opp; opp = t;
+        side ^= 1;
+    }
+    __device__ __forceinline__ void pass() {}
+    __device__ __forceinline__ int canon_of(int b) const { return (b / S) * C + b % S; }
+    __device__ __forceinline__ int bit_of(int cell) const { return (cell / C) * S + cell % C; }
+    static constexpr int kWords = 5;
+    __device__ __forceinline__ void save(uint64_t* w) const {
+        w[0] = own.w[0]; w[1] = own.w[1]; w[2] = opp.w[0]; w[3] = opp.w[1];
+        w[4] = pack_small(ply, passes, side, outcome);
+    }
+    __device__ __forceinline__ void load(const uint64_t* w) {
+        own = Mask{{w[0], w[1]}};
+        opp = Mask{{w[2], w[3]}};
+        unpack_small(w[4], ply, passes, side, outcome);
+    }
+};
+
+// parameters of a game instance: no-ops except for the parametric line game
+template <class G>
+__device__ __forceinline__ void configure(G& g, int32_t desc) {
+    if constexpr (G::kGame == LineGame::kGame) g.configure(desc);
+}
+template <class G>
+__device__ __forceinline__ int cells_of(const G& g) {
+    if constexpr (G::kGame == LineGame::kGame) return g.cells();
+    else return G::kCells;
+}
+
 // ---------------------------------------------------------- one random ply --
 // Uniform-random policy: n legal cells, k-th in ascending cell id with
 // k = umulhi(top32(sm(key ^ ply)), n); a forced pass draws nothing.

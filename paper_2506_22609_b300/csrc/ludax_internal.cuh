@@ -14,6 +14,7 @@ struct ludax_env {
     uint64_t* d_planes;
     uint32_t* d_meta;
     unsigned long long* d_counters;  // [0] refill cursor, [1] illegal, [2] capped, [3] spare
+    int32_t desc;                    // game descriptor (with the line game's parameters)
 };
 
 namespace ludax {
@@ -48,6 +49,8 @@ int dispatch_game(int game, int rows, int cols, F&& f) {
     case LUDAX_GAME_GOMOKU: return (rows == 15 && cols == 15) ? f(Tag<Gomoku>{}) : LUDAX_ERR_SIZE;
     case LUDAX_GAME_PENTE: return (rows == 19 && cols == 19) ? f(Tag<Pente>{}) : LUDAX_ERR_SIZE;
     case LUDAX_GAME_YAVALATH: return (rows == 9 && cols == 9) ? f(Tag<Yavalath>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_LINE:
+        return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128) ? f(Tag<LineGame>{}) : LUDAX_ERR_SIZE;
     default: return LUDAX_ERR_GAME;
     }
 }

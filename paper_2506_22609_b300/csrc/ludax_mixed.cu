@@ -22,7 +22,8 @@ using namespace ludax;
 
 namespace {
 
-constexpr int kBuckets = 16;  // 0 TTT, 1 C4, 2 Othello, 3+k Hex (k+2)x(k+2), 13 Gomoku, 14 Pente, 15 Yavalath
+constexpr int kBuckets = 17;  // 0 TTT, 1 C4, 2 Othello, 3+k Hex (k+2)x(k+2), 13 Gomoku, 14 Pente, 15 Yavalath,
+                               // 16 the parametric line game (any parameters)
 constexpr int kHexTableCells = 505;  // sum of n*n for n = 2..11
 
 __host__ __device__ constexpr int hex_table_offset(int n) {
@@ -33,8 +34,13 @@ __host__ __device__ constexpr int hex_table_offset(int n) {
 
 // bucket of a descriptor, or -1 (LUDAX_ERR_GAME) / -2 (LUDAX_ERR_SIZE)
 int bucket_of_desc(int32_t d) {
-    if (d < 0 || (d >> 24) != 0) return -1;
+    if (d < 0) return -1;
     int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
+    if (game == LUDAX_GAME_LINE) {
+        const int L = (d >> 24) & 15, mx = rows > cols ? rows : cols;
+        return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128 && L >= 2 && L <= mx) ? 16 : -2;
+    }
+    if ((d >> 24) != 0) return -1;
     switch (game) {
     case LUDAX_GAME_TTT: return (rows == 3 && cols == 3) ? 0 : -2;
     case LUDAX_GAME_C4: return (rows == 6 && cols == 7) ? 1 : -2;
@@ -49,6 +55,7 @@ int bucket_of_desc(int32_t d) {
 
 struct MixedArgs {
     const int32_t* queue;            // env ids grouped by bucket
+    const int32_t* desc;             // per-env descriptors (parameters of the line game)
     long long bucket_end[kBuckets];  // exclusive end position of each bucket in the queue
     long long n;
     long long env_offset;
@@ -75,6 +82,7 @@ __device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q,
     G g;
     set_table(g, table);
     long long e = a.queue[q];
+    configure(g, a.desc[e]);
     g.reset();
     uint64_t key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
     uint32_t rhi = draw_hi(key, 0u);
@@ -88,6 +96,7 @@ __device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q,
         q = refill ? slots + claim_next(a.cursor) : a.n;
         if (q >= end) return q;
         e = a.queue[q];
+        configure(g, a.desc[e]);
         g.reset();
         key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
         rhi = draw_hi(key, 0u);
@@ -138,7 +147,8 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         case 12: q = run_hex<11, TABLE>(a, q, end, slots, refill, tables); break;
         case 13: q = run_bucket<Gomoku>(a, q, end, slots, refill, nullptr); break;
         case 14: q = run_bucket<Pente>(a, q, end, slots, refill, nullptr); break;
-        default: q = run_bucket<Yavalath>(a, q, end, slots, refill, nullptr); break;
+        case 15: q = run_bucket<Yavalath>(a, q, end, slots, refill, nullptr); break;
+        default: q = run_bucket<LineGame>(a, q, end, slots, refill, nullptr); break;
         }
     }
 }
@@ -248,6 +258,7 @@ int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_o
     if (cudaMemcpyAsync(d_queue, queue.data(), sizeof(int32_t) * num_envs, cudaMemcpyHostToDevice, s) != cudaSuccess)
         st = LUDAX_ERR_CUDA;
     a.queue = d_queue;
+    a.desc = desc_dev;
     a.n = num_envs;
     a.env_offset = env_offset;
     a.seed_key = splitmix64(seed);
@@ -298,6 +309,7 @@ int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int
     }
     MixedArgs& a = p->args;
     a.queue = p->d_queue;
+    a.desc = desc_dev;
     for (int b = 0; b < kBuckets; ++b) a.bucket_end[b] = p->bucket_end[b];
     a.n = num_envs;
     a.env_offset = env_offset;
@@ -448,17 +460,23 @@ int ludax_autotune(const int32_t* desc_dev, int64_t num_envs, uint64_t seed, int
 namespace {
 
 constexpr long long kNoAllocMaxEnvs = 1ll << 20;  // 4 MiB of queue entries
-constexpr int kNoAllocCounterWords = 64;         // cursors, bucket counts and fill positions, first bad index
-// layout in 32-bit words: [0, kNoAllocMaxEnvs) queue, then 64 uint64 counters
-// (words 0..15 cursors, 16..31 bucket counts, 32..47 fill positions, 48 first bad index)
+constexpr int kNoAllocCounterWords = 128;        // cursors, bucket counts and fill positions, first bad index
+// layout in 32-bit words: [0, kNoAllocMaxEnvs) queue, then 128 uint64 counters
+// (words 0..31 cursors, 32..63 bucket counts, 64..95 fill positions, 96 first bad index)
+constexpr int kCtrCount = 32, kCtrPos = 64, kCtrBad = 96;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocMaxEnvs + 2 * kNoAllocCounterWords];
 
 constexpr int kMaxDevices = 64;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
 __device__ __forceinline__ int bucket_of_desc_dev(int32_t d) {
-    if (d < 0 || (d >> 24) != 0) return -1;
+    if (d < 0) return -1;
     int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
+    if (game == LUDAX_GAME_LINE) {
+        const int L = (d >> 24) & 15, mx = rows > cols ? rows : cols;
+        return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128 && L >= 2 && L <= mx) ? 16 : -2;
+    }
+    if ((d >> 24) != 0) return -1;
     if (game == LUDAX_GAME_TTT) return (rows == 3 && cols == 3) ? 0 : -2;
     if (game == LUDAX_GAME_C4) return (rows == 6 && cols == 7) ? 1 : -2;
     if (game == LUDAX_GAME_OTHELLO) return (rows == 8 && cols == 8) ? 2 : -2;
@@ -471,7 +489,7 @@ __device__ __forceinline__ int bucket_of_desc_dev(int32_t d) {
 
 __global__ void noalloc_reset_kernel(unsigned long long* ctr, long long n) {
     int i = threadIdx.x;
-    if (i < kNoAllocCounterWords) ctr[i] = (i == 48) ? (unsigned long long)n : 0ull;
+    if (i < kNoAllocCounterWords) ctr[i] = (i == kCtrBad) ? (unsigned long long)n : 0ull;
 }
 
 // bucket histogram (block-local, then one atomic per bucket per block) and
@@ -483,11 +501,12 @@ __global__ void noalloc_count_kernel(const int32_t* desc, long long n, unsigned 
     long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e < n) {
         int b = bucket_of_desc_dev(desc[e]);
-        if (b < 0) atomicMin(&ctr[48], (unsigned long long)e);
+        if (b < 0) atomicMin(&ctr[kCtrBad], (unsigned long long)e);
         else atomicAdd(&hist[b], 1u);
     }
     __syncthreads();
-    if (threadIdx.x < kBuckets && hist[threadIdx.x]) atomicAdd(&ctr[16 + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+    if (threadIdx.x < kBuckets && hist[threadIdx.x])
+        atomicAdd(&ctr[kCtrCount + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
 }
 
 struct BucketBegins {
@@ -511,7 +530,7 @@ __global__ void noalloc_scatter_kernel(const int32_t* desc, long long n, BucketB
     }
     __syncthreads();
     if (threadIdx.x < kBuckets && hist[threadIdx.x])
-        base[threadIdx.x] = atomicAdd(&ctr[32 + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+        base[threadIdx.x] = atomicAdd(&ctr[kCtrPos + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
     __syncthreads();
     if (b >= 0) queue[bb.begin[b] + (long long)base[b] + rank] = (int32_t)e;
 }
@@ -548,8 +567,8 @@ extern "C" int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_
         cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return LUDAX_ERR_CUDA;
-    if ((long long)h[48] < num_envs) {
-        long long e = (long long)h[48];
+    if ((long long)h[kCtrBad] < num_envs) {
+        long long e = (long long)h[kCtrBad];
         int32_t d = 0;
         if (bad_index) *bad_index = e;
         if (cudaMemcpy(&d, desc_dev + e, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) return LUDAX_ERR_CUDA;
@@ -561,12 +580,13 @@ extern "C" int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_
     long long acc = 0;
     for (int b = 0; b < kBuckets; ++b) {
         bb.begin[b] = acc;
-        acc += (long long)h[16 + b];
+        acc += (long long)h[kCtrCount + b];
         a.bucket_end[b] = acc;
     }
     noalloc_scatter_kernel<<<grid, 256, 0, s>>>(desc_dev, num_envs, bb, ctr, queue);
     if (cudaGetLastError() != cudaSuccess) return LUDAX_ERR_CUDA;
     a.queue = queue;
+    a.desc = desc_dev;
     a.n = num_envs;
     a.env_offset = env_offset;
     a.seed_key = splitmix64(seed);

@@ -336,19 +336,20 @@ __global__ void sum_kernel(const float* x, int n, float scale, float* out) {
 template <class G>
 __device__ __forceinline__ void write_input_row(const G& g, __nv_bfloat16* row, int ld) {
     const __nv_bfloat16 one = __float2bfloat16_rn(1.f), zero = __float2bfloat16_rn(0.f);
+    const int cells = cells_of(g);
     for (int c0 = 0; c0 < ld; c0 += 8) {
         __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             int c = c0 + i;
             bool on = false;
-            if (c < G::kCells) {
-                int b = G::bit_of(c);
+            if (c < cells) {
+                int b = g.bit_of(c);
                 on = g.side == 0 ? mask_has(g.own, b) : mask_has(g.opp, b);
-            } else if (c < 2 * G::kCells) {
-                int b = G::bit_of(c - G::kCells);
+            } else if (c < 2 * cells) {
+                int b = g.bit_of(c - cells);
                 on = g.side == 0 ? mask_has(g.opp, b) : mask_has(g.own, b);
-            } else if (c == 2 * G::kCells) {
+            } else if (c == 2 * cells) {
                 on = g.side == 0;
             }
             v[i] = on ? one : zero;
@@ -643,7 +644,7 @@ int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld) {
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         pack_inputs_kernel<G><<<blocks_for(env->n, 128), 128, 0, env->stream>>>(
-            EnvDev{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters},
+            EnvDev{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters, env->desc, env->cells},
             reinterpret_cast<__nv_bfloat16*>(x_dev), ld);
         return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
     });
@@ -657,7 +658,7 @@ int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K
     if (chunk < 1) return LUDAX_ERR_SIZE;
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
-        EnvDev d{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters};
+        EnvDev d{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters, env->desc, env->cells};
         for (long long e0 = 0; e0 < env->n; e0 += chunk) {
             long long nc = std::min(chunk, env->n - e0);
             long long rows = nc * K, rows_pad = ((rows + BM - 1) / BM) * BM;

@@ -23,6 +23,8 @@ struct EnvDev {
     int64_t n;
     int64_t env_offset;
     unsigned long long* counters;  // [0] refill cursor, [1] illegal actions, [2] capped envs
+    int32_t desc;                  // the env's game descriptor (parameters of the line game)
+    int32_t cells;                 // cells per board in canonical views
 };
 
 __device__ __forceinline__ uint32_t pack_meta(int ply, int passes, int side, int outcome, int illegal, int caps1 = 0,
@@ -63,10 +65,15 @@ template <>
 struct WideW<Yavalath> {
     static constexpr int value = Yavalath::W;
 };
+template <>
+struct WideW<LineGame> {
+    static constexpr int value = LineGame::W;
+};
 
 // -------------------------------------------------------- load / store --
 template <class G>
 __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
+    configure(g, d.desc);
     const uint32_t meta = d.meta[e];
     unpack_meta(meta, g.ply, g.passes, g.side, g.outcome);
     if constexpr (WideW<G>::value != 0) {
@@ -156,14 +163,15 @@ __device__ __forceinline__ bool mask_has(const BitsW<W>& m, int b) { return test
 
 // word w of a legal mask in canonical cell order
 template <class G>
-__device__ __forceinline__ uint64_t canon_mask_word(const typename G::Mask& m, int w) {
+__device__ __forceinline__ uint64_t canon_mask_word(const G& g, const typename G::Mask& m, int w) {
     if constexpr (WideW<G>::value == 0) {
         return G::canon_word(m, w);
     } else {
         uint64_t out = 0;
+        const int cells = cells_of(g);
         for (int j = 0; j < 64; ++j) {
             const int c = w * 64 + j;
-            if (c < G::kCells && mask_has(m, G::bit_of(c))) out |= 1ull << j;
+            if (c < cells && mask_has(m, g.bit_of(c))) out |= 1ull << j;
         }
         return out;
     }

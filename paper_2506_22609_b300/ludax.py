@@ -20,16 +20,22 @@ LIB_PATH = os.path.join(HERE, "libludax.so")
 
 LUDAX_OK = 0
 LUDAX_GAME_TTT, LUDAX_GAME_C4, LUDAX_GAME_OTHELLO, LUDAX_GAME_HEX = 0, 1, 2, 3
-LUDAX_GAME_GOMOKU, LUDAX_GAME_PENTE, LUDAX_GAME_YAVALATH = 4, 5, 6
+LUDAX_GAME_GOMOKU, LUDAX_GAME_PENTE, LUDAX_GAME_YAVALATH, LUDAX_GAME_LINE = 4, 5, 6, 7
+LUDAX_LINE_EXACT, LUDAX_LINE_GRAVITY, LUDAX_LINE_MISERE = 1, 2, 4
 LUDAX_OUTCOME_ONGOING, LUDAX_OUTCOME_DRAW, LUDAX_OUTCOME_P1, LUDAX_OUTCOME_P2, LUDAX_OUTCOME_CAPPED = -1, 0, 1, 2, 3
 LUDAX_ROLLOUT_FROM_START, LUDAX_ROLLOUT_WRITE_BACK = 1, 2
 
 GAME_IDS = {"ttt": LUDAX_GAME_TTT, "c4": LUDAX_GAME_C4, "othello": LUDAX_GAME_OTHELLO, "hex": LUDAX_GAME_HEX,
-            "gomoku": LUDAX_GAME_GOMOKU, "pente": LUDAX_GAME_PENTE, "yavalath": LUDAX_GAME_YAVALATH}
+            "gomoku": LUDAX_GAME_GOMOKU, "pente": LUDAX_GAME_PENTE, "yavalath": LUDAX_GAME_YAVALATH,
+            "line": LUDAX_GAME_LINE}
 
 
 def LUDAX_DESC(game: int, rows: int, cols: int) -> int:
     return game | (rows << 8) | (cols << 16)
+
+
+def LUDAX_DESC_LINE(rows: int, cols: int, line: int, flags: int = 0) -> int:
+    return LUDAX_GAME_LINE | (rows << 8) | (cols << 16) | (line << 24) | (flags << 28)
 
 
 class LudaxError(RuntimeError):
@@ -39,7 +45,8 @@ class LudaxError(RuntimeError):
 
 
 class ludax_board_params(ctypes.Structure):
-    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32)]
+    _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32), ("line", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
 
 
 class ludax_state_view(ctypes.Structure):
@@ -151,9 +158,10 @@ def _stream(stream):
 
 
 # ------------------------------------------------------------- C-ABI calls --
-def ludax_env_create(game: int, rows: int, cols: int, num_envs: int, env_offset: int = 0, stream=None):
+def ludax_env_create(game: int, rows: int, cols: int, num_envs: int, env_offset: int = 0, stream=None, line: int = 0,
+                     flags: int = 0):
     h = ctypes.c_void_p()
-    p = ludax_board_params(rows, cols)
+    p = ludax_board_params(rows, cols, line, flags)
     _check(lib().ludax_env_create(ctypes.byref(h), game, ctypes.byref(p), num_envs, env_offset, _stream(stream)),
            "ludax_env_create")
     return h
@@ -405,14 +413,14 @@ class Net:
 class Env:
     """A batch of num_envs envs of one game on the current CUDA device."""
 
-    def __init__(self, game, rows, cols, num_envs, env_offset=0, stream=None, device=None):
+    def __init__(self, game, rows, cols, num_envs, env_offset=0, stream=None, device=None, line=0, flags=0):
         if isinstance(game, str):
             game = GAME_IDS[game]
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.game, self.rows, self.cols, self.num_envs, self.env_offset = game, rows, cols, num_envs, env_offset
         self.stream = stream
         with torch.cuda.device(self.device):
-            self.handle = ludax_env_create(game, rows, cols, num_envs, env_offset, stream)
+            self.handle = ludax_env_create(game, rows, cols, num_envs, env_offset, stream, line, flags)
         self.num_actions, self.mask_words, _ = ludax_env_sizes(self.handle)
         self.cells = self.num_actions - (1 if game == LUDAX_GAME_OTHELLO else 0)
 

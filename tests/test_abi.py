@@ -106,3 +106,16 @@ def test_binding_refuses_host_tensors(L):
 
     with pytest.raises(ValueError):
         ludax._ptr(torch.zeros(4))
+
+
+def test_line_game_parameters_validated_on_host(L):
+    from paper_2506_22609_b300 import ludax
+
+    h = ctypes.c_void_p()
+    ok = ludax.ludax_board_params(6, 7, 4, 2)
+    assert L.ludax_env_create(ctypes.byref(h), 7, ctypes.byref(ludax.ludax_board_params(12, 12, 5, 0)), 4, 0, None) == -3
+    assert L.ludax_env_create(ctypes.byref(h), 7, ctypes.byref(ludax.ludax_board_params(6, 7, 9, 0)), 4, 0, None) == -3
+    assert L.ludax_env_create(ctypes.byref(h), 7, ctypes.byref(ludax.ludax_board_params(6, 7, 4, 8)), 4, 0, None) == -3
+    # the other games take no line parameters
+    assert L.ludax_env_create(ctypes.byref(h), 1, ctypes.byref(ludax.ludax_board_params(6, 7, 4, 0)), 4, 0, None) == -1
+    assert not h.value and ok.line == 4

@@ -313,10 +313,14 @@ def test_mixed_rejects_bad_descriptors(L):
     with pytest.raises(L.LudaxError) as ei:
         L.ludax_mixed_plan_create(torch.from_numpy(d).cuda())
     assert ei.value.status == -3 and ei.value.bad_index == 37
-    d[37] = 7
+    d[37] = W.desc(9, 3, 3)                       # no game has id 9
     with pytest.raises(L.LudaxError) as ei:
         L.ludax_mixed_plan_create(torch.from_numpy(d).cuda())
     assert ei.value.status == -2
+    d[37] = W.desc(7, 6, 7)                       # line game without a line length
+    with pytest.raises(L.LudaxError) as ei:
+        L.ludax_mixed_plan_create(torch.from_numpy(d).cuda())
+    assert ei.value.status == -3
 
 
 def test_sync_deadline_returns_timeout_status(L):
@@ -329,3 +333,63 @@ def test_sync_deadline_returns_timeout_status(L):
         saw_timeout |= st == -5
         env.sync(60000)
     assert saw_timeout
+
+
+# ------------------------------------------------- parametric line game --
+LINE_CASES = [(3, 3, 3, 0), (6, 7, 4, 2), (4, 4, 3, 4), (7, 7, 4, 1), (9, 12, 5, 0), (8, 9, 5, 3), (1, 8, 3, 0)]
+
+
+def line_gid(line, flags):
+    """The oracle's id for a parametric line game."""
+    return 7 | (line << 8) | (flags << 12)
+
+
+@pytest.mark.parametrize("rows,cols,line,flags", LINE_CASES, ids=lambda *a: None)
+def test_line_game_matches_oracle(L, rows, cols, line, flags):
+    n, seed, off = 2000, 13, 5
+    env = L.Env("line", rows, cols, n, env_offset=off, line=line, flags=flags)
+    assert env.num_actions == rows * cols
+    out, plies = env.rollout(seed, write_back=True)
+    o, p, b = G.rollout_start(line_gid(line, flags), rows, cols, n, seed, env_offset=off, want_boards=True)
+    assert (np_(out) == o).all() and (np_(plies) == p).all()
+    assert (gpu_state(env)[0] == b).all()
+    # oracle-driven trajectories through the step API, legal masks each ply
+    m = 200
+    env2 = L.Env("line", rows, cols, m, line=line, flags=flags)
+    s = G.reset(line_gid(line, flags), rows, cols, m)
+    rng = np.random.default_rng(rows * 31 + cols)
+    for _ in range(rows * cols + 1):
+        legal = G.legal(s)
+        mk, _pass = env2.legal_mask()
+        torch.cuda.synchronize()
+        assert (_canon_legal(np_(mk), rows * cols, rows * cols) == legal).all()
+        acts = np.array([rng.choice(np.flatnonzero(lg)) if lg.any() else 0 for lg in legal], np.int32)
+        o_rew, o_term, _ = G.step(s, acts)
+        rew, term = env2.step(torch.from_numpy(acts).cuda())
+        torch.cuda.synchronize()
+        assert (np_(rew) == o_rew).all() and (np_(term) == o_term).all()
+        assert_states_equal(env2, s)
+        if o_term.all():
+            break
+
+
+def test_mixed_batch_with_line_games(L):
+    n, seed = 4000, 21
+    rng = np.random.default_rng(3)
+    pool = [L.LUDAX_DESC_LINE(r, c, ln, fl) for r, c, ln, fl in LINE_CASES] + [
+        W.desc(0, 3, 3), W.desc(1, 6, 7), W.desc(3, 7, 7), W.desc(6, 9, 9)]
+    d = np.array(pool, np.int32)[rng.integers(0, len(pool), n)]
+    o, p = G.rollout_mixed(d, seed)
+    dd = torch.from_numpy(d).cuda()
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies = torch.empty(n, dtype=torch.int16, device="cuda")
+    plan = L.ludax_mixed_plan_create(dd)
+    L.ludax_mixed_plan_launch(plan, seed, out, plies)
+    torch.cuda.synchronize()
+    assert (np_(out) == o).all() and (np_(plies) == p).all()
+    L.ludax_mixed_plan_destroy(plan)
+    bad = d.copy()
+    bad[7] = L.LUDAX_DESC_LINE(12, 12, 5, 0)       # 12 x 13 > 128 padded cells
+    with pytest.raises(L.LudaxError) as ei:
+        L.ludax_mixed_plan_create(torch.from_numpy(bad).cuda())
+    assert ei.value.status == -3 and ei.value.bad_index == 7
