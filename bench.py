@@ -41,12 +41,16 @@ METRIC = "env steps/sec on 1 B300 (random playouts); value estimates/sec at stat
 # RNG draw (13 logic/shift/add + 7 multiply), legal mask, popcount, k-th-bit
 # select, apply (Reversi flips), end test.  Reversi's count (437) is within 2%
 # of the instructions ncu measures executed per ply (444).
+# The parametric line game's count is for its benchmarked instance (9 x 12,
+# exactly five, gravity): RNG 20, legal with gravity 18, popcount 5, select 30,
+# place 4, four directions x (three doubling shift-ANDs + the two exact-length
+# shifts) 248, outcome and turn 9.
 ALG_OPS_PER_STEP = {"ttt": 75, "c4": 112, "othello": 437, "hex": 180, "gomoku": 330, "pente": 700,
-                    "yavalath": 150}
+                    "yavalath": 150, "line": 334}
 
 # DRAM bytes per launch of the benchmarked kernel, from the committed ncu
 # captures (profiles/); None once the kernel changes until it is captured again.
-NCU_TRAFFIC_BYTES = {"connect4_6x7_65536env_seed1": 13568,
+NCU_TRAFFIC_BYTES = {"connect4_6x7_65536env_seed1": 13824,
                      "connect4_6x7_16777216env_random_step_seed1": 335552512 + 426629888}
 
 
@@ -57,7 +61,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "gomoku", "pente", "yavalath",
-                                                        "mixed", "step_c4"])
+                                                        "line_c5", "mixed", "step_c4"])
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
@@ -69,11 +73,11 @@ def workload_cfg(name):
     from paper_2506_22609_b300 import workloads as W
 
     return {"c4": W.C4_64K, "ttt": W.TTT_1K, "othello": W.OTHELLO_256K, "hex11": W.HEX11_64K, "gomoku": W.GOMOKU_64K,
-            "pente": W.PENTE_64K, "yavalath": W.YAVALATH_64K}[name]
+            "pente": W.PENTE_64K, "yavalath": W.YAVALATH_64K, "line_c5": W.CONNECT5_9X12_64K}[name]
 
 
 def game_key(cfg):
-    return {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente", 6: "yavalath"}[cfg.game]
+    return {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente", 6: "yavalath", 7: "line"}[cfg.game]
 
 
 def measured_peaks():
@@ -164,7 +168,8 @@ def cpu_oracle_rate(cfg, seconds, desc=None):
         if desc is not None:
             _, p = OG.rollout_mixed(desc[off:off + n], cfg.seed, env_offset=off)
         else:
-            _, p, _ = OG.rollout_start(cfg.game, cfg.rows, cfg.cols, n, cfg.seed, env_offset=off)
+            gid = cfg.game if cfg.game != 7 else 7 | (cfg.line << 8) | (cfg.flags << 12)
+            _, p, _ = OG.rollout_start(gid, cfg.rows, cfg.cols, n, cfg.seed, env_offset=off)
         return int(p.astype(np.int64).sum())
 
     total_envs = cfg.num_envs
@@ -214,7 +219,7 @@ def bench_rollout_config(L, W, cfg, steps, warmup, flush_buf, rank=0):
     import torch
 
     n = cfg.num_envs
-    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=D_shard(rank, n))
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=D_shard(rank, n), line=cfg.line, flags=cfg.flags)
     lc = L.make_cfg(*W.bench_cfg(cfg))
     out = torch.empty(n, dtype=torch.int8, device="cuda")
     plies = torch.empty(n, dtype=torch.int16, device="cuda")
@@ -233,7 +238,7 @@ def e2e_rollout(L, cfg, steps, warmup, rank=0):
 
     n = cfg.num_envs
     cells = cfg.rows * cfg.cols
-    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=D_shard(rank, n))
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, n, env_offset=D_shard(rank, n), line=cfg.line, flags=cfg.flags)
     # start positions, built on the host from the game's own start rule
     b0, tm0, ply0, ps0, oc0 = env.get_state()
     host_in = [t.cpu().pin_memory() for t in (b0, tm0, ply0, ps0, oc0)]
@@ -281,6 +286,32 @@ def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
     total = int(plies.to(torch.int64).sum().item())
     L.ludax_mixed_plan_destroy(plan)
     return ms, total
+
+
+def bench_compiled_library(L, steps, warmup, flush_buf, n=1 << 20, seed=3):
+    """A mixed batch of every game description in the package's library,
+    compiled to descriptors (env e plays library game e mod G), through the
+    graph-captured mixed plan with the autotuned launch shape."""
+    import numpy as np
+    import torch
+
+    from paper_2506_22609_b300 import dsl
+
+    descs = [dsl.descriptor(t) for t in dsl.library().values()]
+    d = torch.from_numpy(np.array(descs, np.int32)[np.arange(n) % len(descs)]).cuda()
+    cfg, _, _ = L.ludax_autotune(d, seed, reps=3)
+    plan = L.ludax_mixed_plan_create(d, 0, cfg)
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies = torch.empty(n, dtype=torch.int16, device="cuda")
+    fn = lambda: L.ludax_mixed_plan_launch(plan, seed, out, plies)  # noqa: E731
+    ms = time_steps(fn, steps, warmup, flush_buf, torch.cuda.current_stream())
+    total = int(plies.to(torch.int64).sum().item())
+    L.ludax_mixed_plan_destroy(plan)
+    m = statistics.median(ms)
+    return {"env_steps_per_s": round(total / (m / 1e3), 1), "median_launch_ms": round(m, 4),
+            "env_steps_per_launch": total, "games": len(descs), "num_envs": n,
+            "launch": {k: getattr(cfg, k) for k in ("block_threads", "blocks_per_sm", "envs_per_thread",
+                                                     "hex_nbr_table", "compact_every")}}
 
 
 # algorithmic bytes of one env step in step-per-launch mode: read two planes
@@ -448,7 +479,7 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_ops = sms * 128 * max_mhz * 1e6  # 32-bit lanes x clock
-    if cfg is not None:
+    if cfg is not None and game_key(cfg) in ALG_OPS_PER_STEP:
         ops_per_launch = ALG_OPS_PER_STEP[game_key(cfg)] * steps_per_launch
     else:
         ops_per_launch = None
@@ -500,19 +531,21 @@ def main():
                                 "sample": sample}
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {}
-        for name in ("ttt", "othello", "hex11", "gomoku", "pente", "yavalath"):
+        for name in ("ttt", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5"):
             c = workload_cfg(name)
             e, lc, ms2, spl = bench_rollout_config(L, W, c, 20, 3, flush_buf)
             m2 = statistics.median(ms2)
             rate = spl / (m2 / 1e3)
             extras[c.name] = {"env_steps_per_s": round(rate, 1), "median_launch_ms": round(m2, 5),
                               "env_steps_per_launch": spl, "launch": lc.as_dict(),
-                              "alu_frac": round(ALG_OPS_PER_STEP[game_key(c)] * rate / peak_ops, 4)}
+                              "alu_frac": (round(ALG_OPS_PER_STEP[game_key(c)] * rate / peak_ops, 4)
+                                           if game_key(c) in ALG_OPS_PER_STEP else None)}
             e.close()
         ms3, tot = bench_mixed(L, W, 10, 2, flush_buf)
         m3 = statistics.median(ms3)
         extras["mixed6_1048576env_seed3_graph"] = {"env_steps_per_s": round(tot / (m3 / 1e3), 1),
                                                    "median_launch_ms": round(m3, 4), "env_steps_per_launch": tot}
+        extras["compiled_library_1048576env_seed3"] = bench_compiled_library(L, 10, 2, flush_buf)
         for gname in ("c4", "othello"):
             sm = bench_step_mode(L, 10, flush_buf, gname, 1 << 24 if gname == "c4" else 1 << 22)
             sm["hbm_frac"] = round(sm["gbs"] / float(peaks.get("hbm_gbs", 6400.0)), 4)

@@ -802,30 +802,33 @@ struct Yavalath {
 // a line of at least L (or exactly L) stones along a row, column or diagonal
 // wins, or loses in the misere variant; a full board draws.  All parameters
 // come from the env's descriptor at run time.
-__device__ __forceinline__ uint64_t shr64c(uint64_t x, int s) { return s >= 64 ? 0ull : (x >> s); }
-__device__ __forceinline__ uint64_t shl64c(uint64_t x, int s) { return s >= 64 ? 0ull : (x << s); }
-// bit i of the result = bit i + s of a (0 <= s, run-time)
+// 64-bit shifts with PTX semantics: an amount of 64 or more (as unsigned)
+// gives 0, so the 128-bit shifts below need no branch on the amount
+__device__ __forceinline__ uint64_t shr64c(uint64_t x, uint32_t s) {
+    uint64_t r;
+    asm("shr.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+__device__ __forceinline__ uint64_t shl64c(uint64_t x, uint32_t s) {
+    uint64_t r;
+    asm("shl.b64 %0, %1, %2;" : "=l"(r) : "l"(x), "r"(s));
+    return r;
+}
+// bit i of the result = bit i + s of a (0 <= s, run-time; 64 - s and s - 64
+// wrap to large unsigned amounts, which give 0)
 __device__ __forceinline__ BitsW<2> shr_rt(const BitsW<2>& a, int s) {
+    const uint32_t u = (uint32_t)s;
     BitsW<2> o;
-    if (s >= 64) {
-        o.w[0] = shr64c(a.w[1], s - 64);
-        o.w[1] = 0;
-    } else {
-        o.w[0] = (a.w[0] >> s) | (s == 0 ? 0ull : a.w[1] << (64 - s));
-        o.w[1] = a.w[1] >> s;
-    }
+    o.w[0] = shr64c(a.w[0], u) | shl64c(a.w[1], 64u - u) | shr64c(a.w[1], u - 64u);
+    o.w[1] = shr64c(a.w[1], u);
     return o;
 }
 // bit i of the result = bit i - s of a
 __device__ __forceinline__ BitsW<2> shl_rt(const BitsW<2>& a, int s) {
+    const uint32_t u = (uint32_t)s;
     BitsW<2> o;
-    if (s >= 64) {
-        o.w[1] = shl64c(a.w[0], s - 64);
-        o.w[0] = 0;
-    } else {
-        o.w[1] = (a.w[1] << s) | (s == 0 ? 0ull : a.w[0] >> (64 - s));
-        o.w[0] = a.w[0] << s;
-    }
+    o.w[1] = shl64c(a.w[1], u) | shr64c(a.w[0], 64u - u) | shl64c(a.w[0], u - 64u);
+    o.w[0] = shl64c(a.w[0], u);
     return o;
 }
 
@@ -863,17 +866,23 @@ struct LineGame {
         if (flags & kGravity) m = m & (shr_rt(occ, S) | bottom);
         return m;
     }
+    // a run of L stones along step d, by doubling: after the loop bit i of m
+    // is set iff cells i, i+d, ..., i+(k-1)d all hold a stone (k < L < 2k),
+    // and the last shift by (L-k)d closes the window to L cells
     __device__ __forceinline__ bool line_dir(const Mask& b, int d) const {
         Mask m = b;
-        for (int i = 1; i < L; ++i) m = m & shr_rt(b, i * d);
+        int k = 1;
+        for (; 2 * k <= L; k *= 2) m = m & shr_rt(m, k * d);
+        if (k < L) m = m & shr_rt(m, (L - k) * d);
         if (flags & kExact) m = m & ~shl_rt(b, d) & ~shr_rt(b, L * d);
         return any(m);
     }
     __device__ __forceinline__ void place(int b) {
         set_bit_w(own, b);
         const bool made = line_dir(own, 1) | line_dir(own, S) | line_dir(own, S + 1) | line_dir(own, S - 1);
+        // no stone is ever removed, so the board is full at ply R*C
         if (made) outcome = (flags & kMisere) ? 2 - side : side + 1;
-        else if (!any(valid & ~(own | opp))) outcome = kDraw;
+        else if (ply + 1 == R * C) outcome = kDraw;
         ++ply;
         Mask t = own; own = opp; opp = t;
         side ^= 1;

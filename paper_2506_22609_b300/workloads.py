@@ -27,6 +27,8 @@ class Config:
     cols: int
     num_envs: int
     seed: int
+    line: int = 0      # parametric line game: line length
+    flags: int = 0     # parametric line game: exact / gravity / misere bits
 
 
 # Uniform-random playouts from the start position (the random-policy
@@ -77,6 +79,9 @@ def sample_envs(n_total: int, k: int, seed: int) -> np.ndarray:
 # Launch shapes the benchmark times (block_threads, blocks_per_sm,
 # envs_per_thread, hex_nbr_table, compact_every): the fastest candidates of
 # ludax_autotune_env / ludax_autotune on a B300.
+# the parametric line-game kernel: exactly five in a row, with gravity, on 9 x 12
+CONNECT5_9X12_64K = Config("connect5exact_gravity_9x12_65536env_seed8", 7, 9, 12, 65536, 8, line=5, flags=3)
+
 BENCH_CFGS = {
     TTT_1K.name: (64, 0, 1, 0, 16),
     C4_64K.name: (448, 4, 1, 0, 16),
@@ -85,6 +90,7 @@ BENCH_CFGS = {
     GOMOKU_64K.name: (448, 0, 1, 0, 16),
     PENTE_64K.name: (448, 4, 1, 0, 16),
     YAVALATH_64K.name: (448, 0, 1, 0, 16),
+    CONNECT5_9X12_64K.name: (448, 0, 1, 0, 16),
 }
 MIXED_BENCH_CFG = (128, 0, 1, 1, 0)
 
