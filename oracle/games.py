@@ -28,7 +28,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle into a shared library (plain scalar C, -O2)."""
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -59,6 +59,9 @@ def lib():
         L.oracle_perft.restype = u64
         L.oracle_perft.argtypes = [i32, i32, i32, i32]
         L.oracle_ttt_enumerate.argtypes = [vp]
+        f64 = ctypes.c_double
+        L.oracle_mcts_search.argtypes = [i32, i32, i32, i64, i64, u64, i32, f64, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.oracle_mcts_play.argtypes = [i32, i32, i32, i64, i64, u64, i32, i32, f64, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -168,6 +171,33 @@ def rollout_mixed(desc, seed, env_offset=0):
     plies = np.zeros(n, np.int16)
     assert lib().oracle_rollout_mixed(_p(d), n, env_offset, seed, _p(out), _p(plies)) == 0
     return out, plies
+
+
+def mcts_search(s: States, seed, iters, c=2 ** 0.5, env_offset=0):
+    """One UCT search per state (see the oracle's MCTS section).  Returns
+    (action int32[n] (-1 if over), visits uint32[n, A], wins uint32[n, A])
+    with the root children's visit counts and half-point rewards by action."""
+    A = num_actions(s.game, s.rows, s.cols)
+    act = np.zeros(s.n, np.int32)
+    vis = np.zeros((s.n, A), np.uint32)
+    win = np.zeros((s.n, A), np.uint32)
+    assert lib().oracle_mcts_search(s.game, s.rows, s.cols, s.n, env_offset, seed, iters, c, *s._args(), _p(act),
+                                    _p(vis), _p(win)) == 0
+    return act, vis, win
+
+
+def mcts_play(game, rows, cols, n, seed, iters_p1, iters_p2, c=2 ** 0.5, env_offset=0):
+    """Matches between UCT agents from the start position.  Returns
+    (outcome int8, plies int16, agency int16, coverage int16), each [n]:
+    agency = turns with more than one legal action, coverage = cells that
+    were occupied at some point."""
+    out = np.zeros(n, np.int8)
+    plies = np.zeros(n, np.int16)
+    agency = np.zeros(n, np.int16)
+    cov = np.zeros(n, np.int16)
+    assert lib().oracle_mcts_play(game, rows, cols, n, env_offset, seed, iters_p1, iters_p2, c, _p(out), _p(plies),
+                                  _p(agency), _p(cov)) == 0
+    return out, plies, agency, cov
 
 
 def perft(game, rows, cols, depth) -> int:

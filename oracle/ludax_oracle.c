@@ -45,6 +45,7 @@
  *   ply caps 9 / 42 / 128 / n*n mark an env CAPPED (never reached by a correct
  *   implementation of these games).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -668,4 +669,200 @@ void oracle_ttt_enumerate(uint64_t* counts /* [10*3] */) {
     memset(counts, 0, sizeof(uint64_t) * 30);
     oracle_init(&g, OR_TTT, 3, 3);
     ttt_walk(&g, counts);
+}
+
+/* ================================================================ MCTS ==
+ * UCT (Kocsis and Szepesvari, ECML 2006): Monte-Carlo tree search with the
+ * UCB1 rule in the tree and a uniform-random playout from each new leaf, the
+ * agent of App. F's GAVEL-like evaluation ("MCTS with UCB1", a number of
+ * iterations per move, each = traversal, expansion, random rollout).
+ *
+ * The paper leaves the details open; this is the definition both sides
+ * implement (the readings are listed in the design doc):
+ *   - a node holds N (visits) and W (reward in half points, for the player
+ *     who made the move into the node: win 2, draw or capped 1, loss 0);
+ *   - iteration i of a search with key K: key_i = sm(K ^ i); from the root,
+ *     while the game is not over: if the node has untried legal actions, draw
+ *     k = pick(sm(~key_i), count) and expand the k-th untried action in
+ *     ascending action id (a forced pass is the only legal action), then stop
+ *     descending; otherwise go to the child with the largest
+ *     UCB1 = W / (2N) + T[N_parent] / sqrt(N), T[m] = c * sqrt(ln m),
+ *     the smallest action id on a tie;
+ *   - from the reached node, a uniform-random playout with draws
+ *     sm(key_i ^ ply) (as the benchmark's playouts, with key_i as the env key);
+ *   - every node on the path from the reached node up to, not including, the
+ *     root gets N += 1 and its mover's reward; the root gets N += 1;
+ *   - the move: the root child with the most visits, then the largest W, then
+ *     the smallest action id.
+ * A match plays such searches for both sides: match m (global index) has the
+ * key K_m = sm(sm(seed) ^ m); the search at ply t has key sm(K_m ^ (t+1) << 32);
+ * a position with a single legal action is played without a search.       */
+typedef struct {
+    int parent, action, mover, first_child, next_sibling;
+    uint32_t N, W;
+} onode;
+
+static void playout_key(ogame* g, uint64_t key) {
+    uint8_t legal[OR_MAXCELLS + 1];
+    int A = oracle_num_actions(g->game, g->rows, g->cols);
+    while (g->outcome == OR_ONGOING) {
+        int n = oracle_legal(g, legal), action = -1;
+        if (g->game == OR_OTHELLO && legal[g->ncells]) {
+            action = g->ncells;
+        } else {
+            uint32_t k = oracle_pick(oracle_sm(key ^ (uint64_t)g->ply), (uint32_t)n);
+            for (int a = 0; a < A; a++)
+                if (legal[a]) {
+                    if (k == 0) { action = a; break; }
+                    k--;
+                }
+        }
+        oracle_apply(g, action);
+    }
+}
+
+static uint32_t reward_half_points(int outcome, int mover) {
+    if (outcome == mover) return 2;
+    if (outcome == OR_DRAW || outcome == OR_CAPPED) return 1;
+    return 0;
+}
+
+/* One search from *root; returns the chosen action.  visits / wins, when
+ * not NULL, receive the root children's N and W by action id. */
+static int mcts_search(const ogame* root, uint64_t key, int iters, double c, uint32_t* visits, uint32_t* wins) {
+    int A = oracle_num_actions(root->game, root->rows, root->cols);
+    onode* nd = (onode*)calloc((size_t)iters + 1, sizeof(onode));
+    uint8_t* tried = (uint8_t*)calloc(((size_t)iters + 1) * (size_t)A, 1);
+    double* T = (double*)calloc((size_t)iters + 2, sizeof(double));
+    uint8_t legal[OR_MAXCELLS + 1];
+    int count = 1, best = -1;
+    for (int m = 1; m <= iters + 1; m++) T[m] = c * sqrt(log((double)m));
+    nd[0].parent = -1;
+    nd[0].action = -1;
+    nd[0].first_child = -1;
+    nd[0].next_sibling = -1;
+    for (int i = 0; i < iters; i++) {
+        uint64_t ki = oracle_sm(key ^ (uint64_t)i);
+        ogame g = *root;
+        int x = 0;
+        while (g.outcome == OR_ONGOING) {
+            int untried = 0;
+            oracle_legal(&g, legal);
+            for (int a = 0; a < A; a++) untried += legal[a] && !tried[(size_t)x * A + a];
+            if (untried > 0) {
+                uint32_t k = oracle_pick(oracle_sm(~ki), (uint32_t)untried);
+                int a = 0, y = count++;
+                for (a = 0; a < A; a++)
+                    if (legal[a] && !tried[(size_t)x * A + a]) {
+                        if (k == 0) break;
+                        k--;
+                    }
+                tried[(size_t)x * A + a] = 1;
+                nd[y].parent = x;
+                nd[y].action = a;
+                nd[y].mover = g.to_move;
+                nd[y].first_child = -1;
+                nd[y].next_sibling = nd[x].first_child;
+                nd[x].first_child = y;
+                oracle_apply(&g, a);
+                x = y;
+                break;
+            } else {
+                int pick = -1;
+                double bq = 0.0;
+                for (int y = nd[x].first_child; y >= 0; y = nd[y].next_sibling) {
+                    double q = (double)nd[y].W / (2.0 * (double)nd[y].N) + T[nd[x].N] / sqrt((double)nd[y].N);
+                    if (pick < 0 || q > bq || (q == bq && nd[y].action < nd[pick].action)) {
+                        pick = y;
+                        bq = q;
+                    }
+                }
+                oracle_apply(&g, nd[pick].action);
+                x = pick;
+            }
+        }
+        playout_key(&g, ki);
+        for (int y = x; y > 0; y = nd[y].parent) {
+            nd[y].N += 1;
+            nd[y].W += reward_half_points(g.outcome, nd[y].mover);
+        }
+        nd[0].N += 1;
+    }
+    for (int y = nd[0].first_child; y >= 0; y = nd[y].next_sibling) {
+        if (visits) visits[nd[y].action] = nd[y].N;
+        if (wins) wins[nd[y].action] = nd[y].W;
+        if (best < 0 || nd[y].N > nd[best].N || (nd[y].N == nd[best].N && nd[y].W > nd[best].W) ||
+            (nd[y].N == nd[best].N && nd[y].W == nd[best].W && nd[y].action < nd[best].action))
+            best = y;
+    }
+    {
+        int action = best >= 0 ? nd[best].action : -1;
+        free(nd);
+        free(tried);
+        free(T);
+        return action;
+    }
+}
+
+static uint64_t search_key(uint64_t seed, int64_t match, int ply) {
+    uint64_t km = oracle_sm(oracle_sm(seed) ^ (uint64_t)match);
+    return km ^ ((uint64_t)(ply + 1) << 32);
+}
+
+/* One search per state of the batch (states in the batch-helper layout);
+ * action[e] = chosen action (-1 when the game is over); visits / wins
+ * [e*A + a] = N / W of the root child for action a (0 if not expanded). */
+int oracle_mcts_search(int game, int rows, int cols, int64_t n, int64_t env_offset, uint64_t seed, int iters, double c,
+                       const int8_t* board, const int8_t* to_move, const int16_t* ply, const int8_t* passes,
+                       const int8_t* outcome, int32_t* action, uint32_t* visits, uint32_t* wins) {
+    int A;
+    if (oracle_check_params(game, rows, cols) != 0 || iters < 1) return -1;
+    A = oracle_num_actions(game, rows, cols);
+    for (int64_t e = 0; e < n; e++) {
+        ogame g;
+        load_state(&g, game, rows, cols, e, board, to_move, ply, passes, outcome);
+        if (visits) memset(visits + e * A, 0, (size_t)A * sizeof(uint32_t));
+        if (wins) memset(wins + e * A, 0, (size_t)A * sizeof(uint32_t));
+        action[e] = g.outcome != OR_ONGOING
+                        ? -1
+                        : mcts_search(&g, oracle_sm(search_key(seed, env_offset + e, g.ply)), iters, c,
+                                      visits ? visits + e * A : NULL, wins ? wins + e * A : NULL);
+    }
+    return 0;
+}
+
+/* Matches between two agents (iters_p1 for P1's moves, iters_p2 for P2's)
+ * from the start position.  Per match: the outcome, the plies, the turns with
+ * more than one legal action, and the cells occupied at some point. */
+int oracle_mcts_play(int game, int rows, int cols, int64_t n, int64_t env_offset, uint64_t seed, int iters_p1,
+                     int iters_p2, double c, int8_t* outcome, int16_t* plies, int16_t* agency, int16_t* coverage) {
+    uint8_t legal[OR_MAXCELLS + 1];
+    if (oracle_check_params(game, rows, cols) != 0 || iters_p1 < 1 || iters_p2 < 1) return -1;
+    for (int64_t e = 0; e < n; e++) {
+        ogame g;
+        uint8_t ever[OR_MAXCELLS];
+        int turns = 0, covered = 0, A;
+        oracle_init(&g, game, rows, cols);
+        A = oracle_num_actions(g.game, rows, cols);
+        for (int i = 0; i < g.ncells; i++) ever[i] = g.cell[i] != 0;
+        while (g.outcome == OR_ONGOING) {
+            int k = oracle_legal(&g, legal), a = -1;
+            if (k > 1) {
+                turns++;
+                a = mcts_search(&g, oracle_sm(search_key(seed, env_offset + e, g.ply)),
+                                g.to_move == 1 ? iters_p1 : iters_p2, c, NULL, NULL);
+            } else {
+                for (int j = 0; j < A; j++)
+                    if (legal[j]) a = j;
+            }
+            oracle_apply(&g, a);
+            for (int i = 0; i < g.ncells; i++) ever[i] |= g.cell[i] != 0;
+        }
+        for (int i = 0; i < g.ncells; i++) covered += ever[i];
+        outcome[e] = (int8_t)g.outcome;
+        plies[e] = (int16_t)g.ply;
+        agency[e] = (int16_t)turns;
+        coverage[e] = (int16_t)covered;
+    }
+    return 0;
 }
