@@ -359,6 +359,56 @@ int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld);
  * The env and the net must share a stream and the env's board size. */
 int ludax_truncated_value(ludax_env* env, ludax_net* net, uint64_t seed, int32_t K, int32_t plies, float* value_dev);
 
+/* ------------------------------------------------------------- MCTS --
+ * UCT agents (Kocsis and Szepesvari 2006): Monte-Carlo tree search with the
+ * UCB1 rule and one uniform-random playout per iteration, and whole matches
+ * between two such agents -- the agents of the GAVEL-like evaluation of
+ * App. F (which fixes "MCTS with UCB1" and iterations = traversal,
+ * expansion, random rollout; the rest is defined here):
+ *   - a node holds N (visits) and W (reward in half points for the player
+ *     who moved into it: win 2, draw or capped game 1, loss 0);
+ *   - iteration i of a search with key K uses key_i = sm(K ^ i); from the
+ *     root, while the game is not over: a node with untried legal actions
+ *     expands the k-th of them in ascending action id, k = umulhi(top32(
+ *     sm(~key_i)), count), and the descent stops; otherwise the descent
+ *     follows the child with the largest W/(2N) + T[N_parent]/sqrt(N),
+ *     T[m] = c * sqrt(ln m) (double, correctly rounded), the smallest action
+ *     on a tie; a forced pass is the only action of its node;
+ *   - a uniform-random playout from the reached node draws sm(key_i ^ ply)
+ *     per ply (as ludax_rollout with key_i as the env key);
+ *   - the reached node and its ancestors below the root get N += 1 and their
+ *     mover's reward; the root gets N += 1;
+ *   - the move played: the root child with the most visits, then the
+ *     largest W, then the smallest action id.
+ * The search of env / match m (global index, env_offset included) at ply t
+ * has K = sm(sm(sm(seed) ^ m) ^ ((t + 1) << 32)), sm = splitmix64.  The
+ * tree lives in a scratch buffer the env owns (grown on demand: num_envs *
+ * (iterations + 1) * (16 + 8 * mask words) bytes; LUDAX_ERR_NOMEM if it
+ * cannot be allocated).  One thread runs one search or one match. */
+#define LUDAX_MCTS_MAX_ITERS 4096
+
+/* One search per env from its current state (the env is not modified).
+ *   iterations  1 .. LUDAX_MCTS_MAX_ITERS;  c >= 0 (UCB1's exploration
+ *               constant; sqrt(2) is the textbook value)
+ *   action_dev  int32 [num_envs]: the chosen action id (-1 if the game is
+ *               over; the pass id for a forced pass)
+ *   visits_dev, wins_dev  uint32 [num_envs][num_actions], nullable: N and W
+ *               of the root's children by action id (0 for no child)      */
+int ludax_mcts_search(ludax_env* env, uint64_t seed, int32_t iterations, double c, int32_t* action_dev,
+                      uint32_t* visits_dev, uint32_t* wins_dev);
+
+/* One match per env between two UCT agents: P1 searches with iters_p1
+ * iterations per move, P2 with iters_p2; a position with a single legal
+ * action is played without a search.  flags: LUDAX_ROLLOUT_FROM_START
+ * (start position; otherwise the env's current state) | LUDAX_ROLLOUT_
+ * WRITE_BACK (store the final positions).  Per env, each output nullable:
+ *   outcome_dev   int8  LUDAX_OUTCOME_* at the end (CAPPED: not completed)
+ *   plies_dev     int16 final ply counter
+ *   agency_dev    int16 turns that had more than one legal action
+ *   coverage_dev  int16 cells that held a piece at some point of the match */
+int ludax_mcts_play(ludax_env* env, uint64_t seed, uint32_t flags, int32_t iters_p1, int32_t iters_p2, double c,
+                    int8_t* outcome_dev, int16_t* plies_dev, int16_t* agency_dev, int16_t* coverage_dev);
+
 /* Dense BF16 layer on the tcgen05 tensor cores (the value net's forward
  * layers): out[m][n] = bf16(relu(sum_k a[m][k] * b[n][k] + bias[n])), FP32
  * accumulation.  a uint16 (bf16 bits) [M][K], b [N][K], bias float [N], out

@@ -541,6 +541,8 @@ int ludax_env_destroy(ludax_env* env) {
     cudaFree(env->d_planes);
     cudaFree(env->d_meta);
     cudaFree(env->d_counters);
+    cudaFree(env->d_tree);
+    cudaFree(env->d_ucb);
     delete env;
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }

@@ -15,6 +15,11 @@ struct ludax_env {
     uint32_t* d_meta;
     unsigned long long* d_counters;  // [0] refill cursor, [1] illegal, [2] capped, [3] spare
     int32_t desc;                    // game descriptor (with the line game's parameters)
+    void* d_tree;                    // MCTS node slabs (grown on demand)
+    size_t tree_bytes;
+    double* d_ucb;                   // UCB1 table T[m] = c * sqrt(ln m)
+    int ucb_len;
+    double ucb_c;
 };
 
 namespace ludax {

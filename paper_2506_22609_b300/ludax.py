@@ -24,6 +24,7 @@ LUDAX_GAME_GOMOKU, LUDAX_GAME_PENTE, LUDAX_GAME_YAVALATH, LUDAX_GAME_LINE = 4, 5
 LUDAX_LINE_EXACT, LUDAX_LINE_GRAVITY, LUDAX_LINE_MISERE = 1, 2, 4
 LUDAX_OUTCOME_ONGOING, LUDAX_OUTCOME_DRAW, LUDAX_OUTCOME_P1, LUDAX_OUTCOME_P2, LUDAX_OUTCOME_CAPPED = -1, 0, 1, 2, 3
 LUDAX_ROLLOUT_FROM_START, LUDAX_ROLLOUT_WRITE_BACK = 1, 2
+LUDAX_MCTS_MAX_ITERS = 4096
 
 GAME_IDS = {"ttt": LUDAX_GAME_TTT, "c4": LUDAX_GAME_C4, "othello": LUDAX_GAME_OTHELLO, "hex": LUDAX_GAME_HEX,
             "gomoku": LUDAX_GAME_GOMOKU, "pente": LUDAX_GAME_PENTE, "yavalath": LUDAX_GAME_YAVALATH,
@@ -119,6 +120,8 @@ def lib() -> ctypes.CDLL:
         "ludax_truncated_value": [vp, vp, u64, i32, i32, vp],
         "ludax_dense_bf16_relu": [vp, vp, vp, vp, i32, i32, i32, i32, vp],
         "ludax_device_error": [P(i32)],
+        "ludax_mcts_search": [vp, u64, i32, ctypes.c_double, vp, vp, vp],
+        "ludax_mcts_play": [vp, u64, u32, i32, i32, ctypes.c_double, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -252,6 +255,17 @@ def ludax_rollout_mixed_noalloc(desc, env_offset: int, seed: int, outcome, plies
         err = LudaxError(st, f"ludax_rollout_mixed_noalloc (first bad descriptor index {bad.value})")
         err.bad_index = bad.value
         raise err
+
+
+def ludax_mcts_search(h, seed: int, iterations: int, c: float, action, visits=None, wins=None):
+    _check(lib().ludax_mcts_search(h, seed, iterations, c, _ptr(action), _ptr(visits), _ptr(wins)),
+           "ludax_mcts_search")
+
+
+def ludax_mcts_play(h, seed: int, flags: int, iters_p1: int, iters_p2: int, c: float, outcome=None, plies=None,
+                    agency=None, coverage=None):
+    _check(lib().ludax_mcts_play(h, seed, flags, iters_p1, iters_p2, c, _ptr(outcome), _ptr(plies), _ptr(agency),
+                                 _ptr(coverage)), "ludax_mcts_play")
 
 
 def ludax_mixed_plan_create(desc, env_offset: int = 0, cfg=None, stream=None):
@@ -470,6 +484,26 @@ class Env:
         v = self._empty((self.num_envs,), torch.float32)
         ludax_rollout_value(self.handle, seed, R, v, cfg)
         return v
+
+    def mcts_search(self, seed, iterations, c=2 ** 0.5, stats=False):
+        """One UCT search per env from its current state: the chosen action
+        ids, and with stats=True the root children's visits and half-point
+        rewards by action id."""
+        act = self._empty((self.num_envs,), torch.int32)
+        vis = self._empty((self.num_envs, self.num_actions), torch.int32) if stats else None
+        win = self._empty((self.num_envs, self.num_actions), torch.int32) if stats else None
+        ludax_mcts_search(self.handle, seed, iterations, c, act, vis, win)
+        return (act, vis, win) if stats else act
+
+    def mcts_play(self, seed, iters_p1, iters_p2, c=2 ** 0.5, from_start=True, write_back=False):
+        """One match per env between UCT agents: (outcome, plies, agency,
+        coverage) per env."""
+        flags = (LUDAX_ROLLOUT_FROM_START if from_start else 0) | (LUDAX_ROLLOUT_WRITE_BACK if write_back else 0)
+        n = self.num_envs
+        out = self._empty((n,), torch.int8)
+        pl, ag, cov = (self._empty((n,), torch.int16) for _ in range(3))
+        ludax_mcts_play(self.handle, seed, flags, iters_p1, iters_p2, c, out, pl, ag, cov)
+        return out, pl, ag, cov
 
     def get_state(self):
         n = self.num_envs

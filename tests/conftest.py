@@ -30,3 +30,15 @@ def cuda_device():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def L(cuda_device):
+    """The CUDA library's binding, built in tree and loaded (GPU tests only)."""
+    from paper_2506_22609_b300 import build
+
+    build.build()
+    from paper_2506_22609_b300 import ludax
+
+    ludax.lib()
+    return ludax
