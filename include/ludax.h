@@ -384,8 +384,16 @@ int ludax_truncated_value(ludax_env* env, ludax_net* net, uint64_t seed, int32_t
  * has K = sm(sm(sm(seed) ^ m) ^ ((t + 1) << 32)), sm = splitmix64.  The
  * tree lives in a scratch buffer the env owns (grown on demand: num_envs *
  * (iterations + 1) * (16 + 8 * mask words) bytes; LUDAX_ERR_NOMEM if it
- * cannot be allocated).  One thread runs one search or one match. */
+ * cannot be allocated).  One warp runs one search or one match; while the
+ * root has untried actions the warp's lanes play up to 32 iterations at
+ * once, with the result of the sequential definition above. */
 #define LUDAX_MCTS_MAX_ITERS 4096
+
+/* Allocates the env's tree scratch for searches of up to `iterations` and
+ * uploads the UCB1 table for c (synchronising), so that later
+ * ludax_mcts_search / ludax_mcts_play calls with at most that many
+ * iterations and the same c allocate nothing and stay asynchronous. */
+int ludax_mcts_reserve(ludax_env* env, int32_t iterations, double c);
 
 /* One search per env from its current state (the env is not modified).
  *   iterations  1 .. LUDAX_MCTS_MAX_ITERS;  c >= 0 (UCB1's exploration
@@ -408,6 +416,19 @@ int ludax_mcts_search(ludax_env* env, uint64_t seed, int32_t iterations, double 
  *   coverage_dev  int16 cells that held a piece at some point of the match */
 int ludax_mcts_play(ludax_env* env, uint64_t seed, uint32_t flags, int32_t iters_p1, int32_t iters_p2, double c,
                     int8_t* outcome_dev, int16_t* plies_dev, int16_t* agency_dev, int16_t* coverage_dev);
+
+/* Matches of any mix of games in one launch (one warp per match): env e
+ * plays the game of desc_host[e] (LUDAX_DESC / LUDAX_DESC_LINE) from its
+ * start position, P1 searching with iters_host[2e] iterations per move and
+ * P2 with iters_host[2e + 1]; match e has the global index env_offset + e
+ * (its keys as in ludax_mcts_play).  desc_host and iters_host are HOST
+ * arrays, validated (the first bad index goes to bad_index, nullable) and
+ * copied before the call returns; the outputs are device arrays [n] as in
+ * ludax_mcts_play.  Scratch is allocated and freed in stream order on
+ * `stream`; the call returns once the launch is enqueued. */
+int ludax_mcts_play_mixed(const int32_t* desc_host, const int32_t* iters_host, int64_t n, int64_t env_offset,
+                          uint64_t seed, double c, int8_t* outcome_dev, int16_t* plies_dev, int16_t* agency_dev,
+                          int16_t* coverage_dev, void* stream, int64_t* bad_index);
 
 /* Dense BF16 layer on the tcgen05 tensor cores (the value net's forward
  * layers): out[m][n] = bf16(relu(sum_k a[m][k] * b[n][k] + bias[n])), FP32

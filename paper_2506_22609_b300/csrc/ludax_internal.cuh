@@ -60,6 +60,32 @@ int dispatch_game(int game, int rows, int cols, F&& f) {
     }
 }
 
+// Per-env descriptors (game | rows << 8 | cols << 16 | line << 24 | flags << 28)
+// grouped by kernel instance ("buckets"): 0 TTT, 1 C4, 2 Othello, 3 + k Hex
+// (k + 2) x (k + 2), 13 Gomoku, 14 Pente, 15 Yavalath, 16 the parametric line
+// game (any parameters).  Returns the bucket, -1 for an unknown game or
+// -2 for a board size the game's kernel does not take.
+constexpr int kDescBuckets = 17;
+__host__ __device__ inline int desc_bucket(int32_t d) {
+    if (d < 0) return -1;
+    const int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
+    if (game == LUDAX_GAME_LINE) {
+        const int L = (d >> 24) & 15, mx = rows > cols ? rows : cols;
+        return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128 && L >= 2 && L <= mx) ? 16 : -2;
+    }
+    if ((d >> 24) != 0) return -1;
+    switch (game) {
+    case LUDAX_GAME_TTT: return (rows == 3 && cols == 3) ? 0 : -2;
+    case LUDAX_GAME_C4: return (rows == 6 && cols == 7) ? 1 : -2;
+    case LUDAX_GAME_OTHELLO: return (rows == 8 && cols == 8) ? 2 : -2;
+    case LUDAX_GAME_HEX: return (rows == cols && rows >= 2 && rows <= 11) ? 3 + rows - 2 : -2;
+    case LUDAX_GAME_GOMOKU: return (rows == 15 && cols == 15) ? 13 : -2;
+    case LUDAX_GAME_PENTE: return (rows == 19 && cols == 19) ? 14 : -2;
+    case LUDAX_GAME_YAVALATH: return (rows == 9 && cols == 9) ? 15 : -2;
+    default: return -1;
+    }
+}
+
 // dense BF16 layer on tcgen05 tensor cores (ludax_umma.cu):
 // out = bf16(relu(A . B^T + bias)), A [M][K], B [N][K] row-major
 bool umma_dense_supported(int M, int N, int K);

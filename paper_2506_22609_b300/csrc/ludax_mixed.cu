@@ -15,15 +15,13 @@
 #include <new>
 #include <vector>
 
-#include "../../include/ludax.h"
-#include "ludax_state.cuh"
+#include "ludax_internal.cuh"
 
 using namespace ludax;
 
 namespace {
 
-constexpr int kBuckets = 17;  // 0 TTT, 1 C4, 2 Othello, 3+k Hex (k+2)x(k+2), 13 Gomoku, 14 Pente, 15 Yavalath,
-                               // 16 the parametric line game (any parameters)
+constexpr int kBuckets = kDescBuckets;
 constexpr int kHexTableCells = 505;  // sum of n*n for n = 2..11
 
 __host__ __device__ constexpr int hex_table_offset(int n) {
@@ -32,26 +30,7 @@ __host__ __device__ constexpr int hex_table_offset(int n) {
     return off;
 }
 
-// bucket of a descriptor, or -1 (LUDAX_ERR_GAME) / -2 (LUDAX_ERR_SIZE)
-int bucket_of_desc(int32_t d) {
-    if (d < 0) return -1;
-    int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
-    if (game == LUDAX_GAME_LINE) {
-        const int L = (d >> 24) & 15, mx = rows > cols ? rows : cols;
-        return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128 && L >= 2 && L <= mx) ? 16 : -2;
-    }
-    if ((d >> 24) != 0) return -1;
-    switch (game) {
-    case LUDAX_GAME_TTT: return (rows == 3 && cols == 3) ? 0 : -2;
-    case LUDAX_GAME_C4: return (rows == 6 && cols == 7) ? 1 : -2;
-    case LUDAX_GAME_OTHELLO: return (rows == 8 && cols == 8) ? 2 : -2;
-    case LUDAX_GAME_HEX: return (rows == cols && rows >= 2 && rows <= 11) ? 3 + rows - 2 : -2;
-    case LUDAX_GAME_GOMOKU: return (rows == 15 && cols == 15) ? 13 : -2;
-    case LUDAX_GAME_PENTE: return (rows == 19 && cols == 19) ? 14 : -2;
-    case LUDAX_GAME_YAVALATH: return (rows == 9 && cols == 9) ? 15 : -2;
-    default: return -1;
-    }
-}
+int bucket_of_desc(int32_t d) { return desc_bucket(d); }
 
 struct MixedArgs {
     const int32_t* queue;            // env ids grouped by bucket
@@ -469,23 +448,7 @@ static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocMaxEnvs + 2 
 constexpr int kMaxDevices = 64;
 void* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-__device__ __forceinline__ int bucket_of_desc_dev(int32_t d) {
-    if (d < 0) return -1;
-    int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
-    if (game == LUDAX_GAME_LINE) {
-        const int L = (d >> 24) & 15, mx = rows > cols ? rows : cols;
-        return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128 && L >= 2 && L <= mx) ? 16 : -2;
-    }
-    if ((d >> 24) != 0) return -1;
-    if (game == LUDAX_GAME_TTT) return (rows == 3 && cols == 3) ? 0 : -2;
-    if (game == LUDAX_GAME_C4) return (rows == 6 && cols == 7) ? 1 : -2;
-    if (game == LUDAX_GAME_OTHELLO) return (rows == 8 && cols == 8) ? 2 : -2;
-    if (game == LUDAX_GAME_HEX) return (rows == cols && rows >= 2 && rows <= 11) ? 3 + rows - 2 : -2;
-    if (game == LUDAX_GAME_GOMOKU) return (rows == 15 && cols == 15) ? 13 : -2;
-    if (game == LUDAX_GAME_PENTE) return (rows == 19 && cols == 19) ? 14 : -2;
-    if (game == LUDAX_GAME_YAVALATH) return (rows == 9 && cols == 9) ? 15 : -2;
-    return -1;
-}
+__device__ __forceinline__ int bucket_of_desc_dev(int32_t d) { return desc_bucket(d); }
 
 __global__ void noalloc_reset_kernel(unsigned long long* ctr, long long n) {
     int i = threadIdx.x;

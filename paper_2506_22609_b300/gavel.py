@@ -77,7 +77,7 @@ def heuristics(selfplay: Matches, strong_as_p1: Matches, strong_as_p2: Matches) 
 
 def play(spec: dsl.GameSpec, matches: int, iters_p1: int, iters_p2: int, seed: int, c: float = math.sqrt(2.0),
          env_offset: int = 0) -> Matches:
-    """One batch of matches between UCT agents on the GPU."""
+    """One batch of matches of one game between UCT agents on the GPU."""
     env = dsl.make_env(spec, matches, env_offset=env_offset)
     try:
         out, plies, agency, cov = env.mcts_play(seed, iters_p1, iters_p2, c)
@@ -87,24 +87,68 @@ def play(spec: dsl.GameSpec, matches: int, iters_p1: int, iters_p2: int, seed: i
     return res
 
 
+def cells_of(spec: dsl.GameSpec) -> int:
+    return 61 if spec.game == dsl.GAME_YAVALATH else spec.rows * spec.cols
+
+
+def evaluate_many(games, matches: int = 100, iters: int = 100, weak_iters: int = 50, seed: int = 0,
+                  c: float = math.sqrt(2.0)) -> dict:
+    """Evaluate several games in ONE launch (``ludax_mcts_play_mixed``, one
+    warp per match).  Game g's matches take consecutive global match
+    indices: first ``matches`` between equal agents, then ``matches // 2``
+    with the stronger agent as P1, then the rest with it as P2.  ``games``
+    maps names to descriptions (text or compiled spec); returns {name:
+    heuristics and details} plus "_seconds" (wall time of the launch)."""
+    import torch
+
+    from . import ludax
+
+    results, parts, desc, iters_pp = {}, [], [], []
+    half = max(1, matches // 2)
+    sizes = ((matches, iters, iters), (half, iters, weak_iters), (max(1, matches - half), weak_iters, iters))
+    for name, game in games.items():
+        try:
+            spec = game if isinstance(game, dsl.GameSpec) else dsl.compile_game(game)
+        except dsl.DslError as err:
+            results[name] = {"playable": False, "error": str(err), "gavel_score": 0.0, "interesting": False}
+            continue
+        spans = []
+        for n, i1, i2 in sizes:
+            spans.append((len(desc), n))
+            desc += [spec.desc] * n
+            iters_pp += [(i1, i2)] * n
+        parts.append((name, spec, spans))
+    n = len(desc)
+    if n == 0:
+        results["_seconds"] = 0.0
+        return results
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty(n, dtype=torch.int8, device=dev)
+    plies, agency, cov = (torch.empty(n, dtype=torch.int16, device=dev) for _ in range(3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ludax.ludax_mcts_play_mixed(np.array(desc, np.int32), np.array(iters_pp, np.int32), 0, seed, c, out, plies, agency,
+                                cov)
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    o, p, a, v = (t.cpu().numpy() for t in (out, plies, agency, cov))
+    for name, spec, spans in parts:
+        ms = [Matches(o[s:s + k], p[s:s + k], a[s:s + k], v[s:s + k], cells_of(spec)) for s, k in spans]
+        res = heuristics(*ms)
+        res.update({"playable": True, "game": spec.name, "descriptor": spec.desc, "matches": matches, "iters": iters,
+                    "weak_iters": weak_iters, "mean_plies": float(ms[0].plies.mean()),
+                    "searches": int(sum(int(m.agency.astype(np.int64).sum()) for m in ms)),
+                    "first_match": spans[0][0]})
+        results[name] = res
+    results["_seconds"] = seconds
+    return results
+
+
 def evaluate(game, matches: int = 100, iters: int = 100, weak_iters: int = 50, seed: int = 0,
              c: float = math.sqrt(2.0)) -> dict:
-    """Evaluate a game description (text or compiled spec) as App. F does.
+    """Evaluate one game description (text or compiled spec) as App. F does.
     A description that does not compile is not playable and scores 0."""
-    if isinstance(game, dsl.GameSpec):
-        spec = game
-    else:
-        try:
-            spec = dsl.compile_game(game)
-        except dsl.DslError as err:
-            return {"playable": False, "error": str(err), "gavel_score": 0.0, "interesting": False}
-    t0 = time.perf_counter()
-    half = max(1, matches // 2)
-    selfplay = play(spec, matches, iters, iters, seed, c)
-    strong_p1 = play(spec, half, iters, weak_iters, seed + 1, c)
-    strong_p2 = play(spec, matches - half if matches > 1 else 1, weak_iters, iters, seed + 2, c)
-    res = heuristics(selfplay, strong_p1, strong_p2)
-    res.update({"playable": True, "game": spec.name, "descriptor": spec.desc, "matches": matches, "iters": iters,
-                "weak_iters": weak_iters, "seconds": time.perf_counter() - t0,
-                "mean_plies": float(selfplay.plies.mean())})
-    return res
+    res = evaluate_many({"game": game}, matches, iters, weak_iters, seed, c)
+    out = res["game"]
+    out["seconds"] = res["_seconds"]
+    return out

@@ -120,8 +120,10 @@ def lib() -> ctypes.CDLL:
         "ludax_truncated_value": [vp, vp, u64, i32, i32, vp],
         "ludax_dense_bf16_relu": [vp, vp, vp, vp, i32, i32, i32, i32, vp],
         "ludax_device_error": [P(i32)],
+        "ludax_mcts_reserve": [vp, i32, ctypes.c_double],
         "ludax_mcts_search": [vp, u64, i32, ctypes.c_double, vp, vp, vp],
         "ludax_mcts_play": [vp, u64, u32, i32, i32, ctypes.c_double, vp, vp, vp, vp],
+        "ludax_mcts_play_mixed": [vp, vp, i64, i64, u64, ctypes.c_double, vp, vp, vp, vp, vp, P(i64)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -257,6 +259,10 @@ def ludax_rollout_mixed_noalloc(desc, env_offset: int, seed: int, outcome, plies
         raise err
 
 
+def ludax_mcts_reserve(h, iterations: int, c: float):
+    _check(lib().ludax_mcts_reserve(h, iterations, c), "ludax_mcts_reserve")
+
+
 def ludax_mcts_search(h, seed: int, iterations: int, c: float, action, visits=None, wins=None):
     _check(lib().ludax_mcts_search(h, seed, iterations, c, _ptr(action), _ptr(visits), _ptr(wins)),
            "ludax_mcts_search")
@@ -266,6 +272,25 @@ def ludax_mcts_play(h, seed: int, flags: int, iters_p1: int, iters_p2: int, c: f
                     agency=None, coverage=None):
     _check(lib().ludax_mcts_play(h, seed, flags, iters_p1, iters_p2, c, _ptr(outcome), _ptr(plies), _ptr(agency),
                                  _ptr(coverage)), "ludax_mcts_play")
+
+
+def ludax_mcts_play_mixed(desc, iters, env_offset: int, seed: int, c: float, outcome=None, plies=None, agency=None,
+                          coverage=None, stream=None):
+    """desc: host int32 [n] descriptors; iters: host int32 [n, 2] (P1, P2)."""
+    import numpy as np
+
+    d = np.ascontiguousarray(desc, dtype=np.int32)
+    it = np.ascontiguousarray(iters, dtype=np.int32)
+    if it.shape != (d.shape[0], 2):
+        raise ValueError("iters must have shape [n, 2]")
+    bad = ctypes.c_int64(-1)
+    st = lib().ludax_mcts_play_mixed(d.ctypes.data_as(ctypes.c_void_p), it.ctypes.data_as(ctypes.c_void_p), d.shape[0],
+                                     env_offset, seed, c, _ptr(outcome), _ptr(plies), _ptr(agency), _ptr(coverage),
+                                     _stream(stream), ctypes.byref(bad))
+    if st != LUDAX_OK:
+        err = LudaxError(st, f"ludax_mcts_play_mixed (first bad index {bad.value})")
+        err.bad_index = bad.value
+        raise err
 
 
 def ludax_mixed_plan_create(desc, env_offset: int = 0, cfg=None, stream=None):
@@ -494,6 +519,9 @@ class Env:
         win = self._empty((self.num_envs, self.num_actions), torch.int32) if stats else None
         ludax_mcts_search(self.handle, seed, iterations, c, act, vis, win)
         return (act, vis, win) if stats else act
+
+    def mcts_reserve(self, iterations, c=2 ** 0.5):
+        ludax_mcts_reserve(self.handle, iterations, c)
 
     def mcts_play(self, seed, iters_p1, iters_p2, c=2 ** 0.5, from_start=True, write_back=False):
         """One match per env between UCT agents: (outcome, plies, agency,

@@ -120,3 +120,69 @@ def test_gavel_evaluation_runs_on_the_gpu(L):
         assert -1.0 <= res[k] <= 1.0
     # TTT between equal agents: complete, every cell coverable, agency high
     assert res["completion"] == 1.0 and res["agency"] > 0.8
+
+
+def test_mixed_matches_match_oracle(L):
+    from paper_2506_22609_b300 import workloads as W
+
+    groups = [(G.TTT, 3, 3, 12), (G.C4, 6, 7, 6), (G.HEX, 5, 5, 4), (LINE_4X4_MISERE, 4, 4, 6),
+              (G.OTHELLO, 8, 8, 3), (G.YAVALATH, 9, 9, 2), (G.GOMOKU, 15, 15, 1), (G.PENTE, 19, 19, 1),
+              (LINE_4X5_GRAVITY, 4, 5, 4)]
+
+    def desc_of(game, rows, cols):
+        if game & 0xFF == 7:
+            return L.LUDAX_DESC_LINE(rows, cols, (game >> 8) & 15, (game >> 12) & 7)
+        return W.desc(game, rows, cols)
+
+    desc, iters, who = [], [], []
+    rng = np.random.default_rng(4)
+    for game, rows, cols, k in groups:
+        for _ in range(k):
+            desc.append(desc_of(game, rows, cols))
+            iters.append((int(rng.integers(2, 30)), int(rng.integers(2, 30))))
+            who.append((game, rows, cols))
+    # shuffle so that neighbouring warps play different games
+    order = rng.permutation(len(desc))
+    desc = [desc[i] for i in order]
+    iters = [iters[i] for i in order]
+    who = [who[i] for i in order]
+    n, off, seed = len(desc), 40, 12
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies, agency, cov = (torch.empty(n, dtype=torch.int16, device="cuda") for _ in range(3))
+    L.ludax_mcts_play_mixed(np.array(desc, np.int32), np.array(iters, np.int32), off, seed, 2 ** 0.5, out, plies,
+                            agency, cov)
+    torch.cuda.synchronize()
+    got = [t.cpu().numpy() for t in (out, plies, agency, cov)]
+    for e in range(n):
+        game, rows, cols = who[e]
+        want = G.mcts_play(game, rows, cols, 1, seed, iters[e][0], iters[e][1], env_offset=off + e)
+        for g_arr, w_arr in zip(got, want):
+            assert g_arr[e] == w_arr[0], (e, who[e])
+    # invalid descriptors and iteration counts are caught on the host
+    bad = np.array(desc, np.int32)
+    bad[3] = W.desc(3, 12, 12)
+    with pytest.raises(L.LudaxError) as ei:
+        L.ludax_mcts_play_mixed(bad, np.array(iters, np.int32), 0, 1, 1.0, out)
+    assert ei.value.status == -3 and ei.value.bad_index == 3
+    it = np.array(iters, np.int32)
+    it[5, 1] = 0
+    with pytest.raises(L.LudaxError) as ei:
+        L.ludax_mcts_play_mixed(np.array(desc, np.int32), it, 0, 1, 1.0, out)
+    assert ei.value.status == -1 and ei.value.bad_index == 5
+
+
+def test_gavel_single_and_many_agree(L):
+    from paper_2506_22609_b300 import dsl
+
+    lib = dsl.library()
+    one = gavel.evaluate(lib["connect_four"], matches=8, iters=20, weak_iters=5, seed=3)
+    many = gavel.evaluate_many({"a": lib["tic_tac_toe"], "c4": lib["connect_four"]}, 8, 20, 5, 3)
+    # the same game at different global match indices gives different matches; at the
+    # same indices, the same ones
+    first = many["c4"]["first_match"]
+    desc = [dsl.descriptor(lib["connect_four"])] * 8
+    out = torch.empty(8, dtype=torch.int8, device="cuda")
+    L.ludax_mcts_play_mixed(np.array(desc, np.int32), np.array([(20, 20)] * 8, np.int32), first, 3, 2 ** 0.5, out)
+    o = G.mcts_play(G.C4, 6, 7, 8, 3, 20, 20, env_offset=first)[0]
+    assert (out.cpu().numpy() == o).all()
+    assert 0.0 <= one["gavel_score"] <= 1.0
