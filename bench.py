@@ -314,6 +314,33 @@ def bench_compiled_library(L, steps, warmup, flush_buf, n=1 << 20, seed=3):
                                                      "hex_nbr_table", "compact_every")}}
 
 
+def bench_gavel(matches=100, iters=100, weak_iters=50):
+    """App. F's GAVEL-like evaluation of every game in the package's library
+    (matches between UCT agents: equal agents, then the stronger agent in
+    each seat against a weaker one), all games in one launch; beside it the
+    oracle's time for one Connect Four match between the same agents (one
+    host thread, a bounded sample of 4 matches)."""
+    from oracle import games as OG
+    from paper_2506_22609_b300 import dsl, gavel
+
+    lib = dsl.library()
+    gavel.evaluate_many({"warm": lib["tic_tac_toe"]}, 4, 8, 4, 0)
+    r = gavel.evaluate_many(lib, matches, iters, weak_iters, 0)
+    secs = r.pop("_seconds")
+    searches = sum(v["searches"] for v in r.values())
+    scores = {k: round(v["gavel_score"], 3) for k, v in sorted(r.items())}
+    t0 = time.perf_counter()
+    OG.mcts_play(1, 6, 7, 4, 0, iters, iters)
+    cpu_c4 = (time.perf_counter() - t0) / 4
+    return {"seconds": round(secs, 4), "games": len(r), "matches": len(r) * (matches + matches), "iters": iters,
+            "weak_iters": weak_iters, "searches": searches, "searches_per_s": round(searches / secs, 1),
+            "iterations_per_s_lower_bound": round(searches * weak_iters / secs, 1), "gavel_scores": scores,
+            "median_gavel_score": round(float(statistics.median(scores.values())), 3),
+            "interesting": sorted(k for k, v in r.items() if v["interesting"]),
+            "cpu_oracle": {"connect_four_seconds_per_match": round(cpu_c4, 4), "threads": 1,
+                           "sample": "4 Connect Four matches between 100-iteration agents"}}
+
+
 # algorithmic bytes of one env step in step-per-launch mode: read two planes
 # and the meta word (20 B), write them back (20 B), rewards (8 B), terminated (1 B)
 STEP_BYTES_PER_ENV = 49
@@ -551,6 +578,7 @@ def main():
             sm["hbm_frac"] = round(sm["gbs"] / float(peaks.get("hbm_gbs", 6400.0)), 4)
             extras["step_mode_" + gname] = sm
         extras["dense_layer"] = bench_dense(L, peaks, flush_buf)
+        extras["gavel_library"] = bench_gavel()
         if not args.no_valuenet:
             extras["value_net"] = bench_valuenet()
         line["extra_workloads"] = extras
