@@ -3,7 +3,11 @@
 Builds ``libludax_oracle.so`` next to the source with plain ``gcc -O2`` (no
 intrinsics, no vector pragmas) on first use, then exposes numpy-friendly
 functions.  Game ids: 0 Tic-Tac-Toe, 1 Connect Four, 2 Reversi/Othello, 3 Hex,
-4 Gomoku, 5 Pente, 6 Yavalath.
+4 Gomoku, 5 Pente, 6 Yavalath, 7 | L << 8 | flags << 12 the parametric line
+game, 8 Wolf and Sheep, 9 English Draughts, 10 Dai Hasami Shogi (move games:
+action = from * cells + to; board values 1 / 2 a piece of P1 / P2, 3 / 4 a
+Draughts king of P1 / P2; Draughts keeps the cell of a piece that must keep
+capturing, plus one, in the passes slot).
 Outcome codes: -1 ongoing, 0 draw, 1 P1 win, 2 P2 win, 3 capped.
 """
 from __future__ import annotations
@@ -19,6 +23,7 @@ SRC = os.path.join(HERE, "ludax_oracle.c")
 LIB = os.path.join(HERE, "libludax_oracle.so")
 
 TTT, C4, OTHELLO, HEX, GOMOKU, PENTE, YAVALATH = 0, 1, 2, 3, 4, 5, 6
+WOLF_SHEEP, DRAUGHTS, HASAMI_SHOGI = 8, 9, 10    # move games: action = from * cells + to
 ONGOING, DRAW, P1, P2, CAPPED = -1, 0, 1, 2, 3
 
 _lib = None
@@ -58,6 +63,8 @@ def lib():
         L.oracle_rollout_mixed.argtypes = [vp, i64, i64, u64, vp, vp]
         L.oracle_perft.restype = u64
         L.oracle_perft.argtypes = [i32, i32, i32, i32]
+        L.oracle_perft_turns.restype = u64
+        L.oracle_perft_turns.argtypes = [i32, i32, i32, i32]
         L.oracle_ttt_enumerate.argtypes = [vp]
         f64 = ctypes.c_double
         L.oracle_mcts_search.argtypes = [i32, i32, i32, i64, i64, u64, i32, f64, vp, vp, vp, vp, vp, vp, vp, vp]
@@ -202,6 +209,12 @@ def mcts_play(game, rows, cols, n, seed, iters_p1, iters_p2, c=2 ** 0.5, env_off
 
 def perft(game, rows, cols, depth) -> int:
     return lib().oracle_perft(game, rows, cols, depth)
+
+
+def perft_turns(game, rows, cols, depth) -> int:
+    """Perft where a continuation by the same player (a Draughts multi-capture)
+    stays at the same depth."""
+    return lib().oracle_perft_turns(game, rows, cols, depth)
 
 
 def ttt_enumerate() -> np.ndarray:

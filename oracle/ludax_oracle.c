@@ -58,6 +58,9 @@
 #define OR_PENTE 5
 #define OR_YAVALATH 6
 #define OR_LINE 7 /* parametric line game; the game argument packs 7 | L << 8 | flags << 12 */
+#define OR_WOLF 8     /* Wolf and Sheep, 8x8 */
+#define OR_DRAUGHTS 9 /* English Draughts, 8x8 */
+#define OR_HASAMI 10  /* Dai Hasami Shogi, 9x9 */
 #define OR_LINE_EXACT 1
 #define OR_LINE_GRAVITY 2
 #define OR_LINE_MISERE 4
@@ -69,6 +72,7 @@
 #define OR_CAPPED 3
 
 #define OR_MAXCELLS 512
+#define OR_MAXACTIONS (81 * 81 + 1) /* move games: action = from * cells + to */
 
 typedef struct {
     int32_t game, rows, cols, ncells;
@@ -81,6 +85,7 @@ typedef struct {
     int32_t illegal;          /* 1 when the game ended on an illegal action */
     int32_t captures[3];      /* Pente: opponent stones captured by player 1 / 2 */
     int32_t line, flags;      /* parametric line game: line length, OR_LINE_* flags */
+    int32_t pending;          /* Draughts: cell of the piece that must capture again, -1 if none */
 } ogame;
 
 /* ------------------------------------------------------------------ RNG --
@@ -154,6 +159,9 @@ int oracle_ply_cap(int game, int rows, int cols) {
     case OR_GOMOKU: return rows * cols;
     case OR_PENTE: return 2000;
     case OR_YAVALATH: return 61;
+    case OR_WOLF:
+    case OR_DRAUGHTS:
+    case OR_HASAMI: return 200; /* Sec. 6: unbounded games stop after 200 turns */
     }
     return 0;
 }
@@ -161,8 +169,12 @@ int oracle_ply_cap(int game, int rows, int cols) {
 /* Number of actions: one per cell, plus the pass for Reversi. */
 int oracle_num_cells(int game, int rows, int cols) { return (game & 0xFF) == OR_YAVALATH ? 61 : rows * cols; }
 
+static int is_move_game(int game) { return game == OR_WOLF || game == OR_DRAUGHTS || game == OR_HASAMI; }
+
 int oracle_num_actions(int game, int rows, int cols) {
-    return oracle_num_cells(game, rows, cols) + (game == OR_OTHELLO ? 1 : 0);
+    int n = oracle_num_cells(game, rows, cols);
+    if (is_move_game(game)) return n * n; /* action = from * cells + to */
+    return n + (game == OR_OTHELLO ? 1 : 0);
 }
 
 int oracle_check_params(int game, int rows, int cols) {
@@ -181,6 +193,9 @@ int oracle_check_params(int game, int rows, int cols) {
     case OR_GOMOKU: return (rows == 15 && cols == 15) ? 0 : -1;
     case OR_PENTE: return (rows == 19 && cols == 19) ? 0 : -1;
     case OR_YAVALATH: return (rows == 9 && cols == 9) ? 0 : -1;
+    case OR_WOLF:
+    case OR_DRAUGHTS: return (rows == 8 && cols == 8) ? 0 : -1;
+    case OR_HASAMI: return (rows == 9 && cols == 9) ? 0 : -1;
     }
     return -1;
 }
@@ -200,6 +215,26 @@ int oracle_init(ogame* g, int game, int rows, int cols) {
     g->ncells = oracle_num_cells(game, rows, cols);
     g->to_move = 1;
     g->outcome = OR_ONGOING;
+    g->pending = -1;
+    if (game == OR_WOLF) {
+        /* four sheep (P1) on the dark cells of the bottom row, the wolf (P2)
+         * on the left one of the two central dark cells of the top row */
+        for (int c = 0; c < 8; c += 2) g->cell[7 * 8 + c] = 1;
+        g->cell[3] = 2;
+    }
+    if (game == OR_DRAUGHTS) {
+        /* men on the dark cells ((r + c) odd): P1 on rows 5-7, P2 on rows 0-2 */
+        for (int r = 0; r < 8; r++)
+            for (int c = 0; c < 8; c++)
+                if ((r + c) % 2 == 1 && (r >= 5 || r <= 2)) g->cell[r * 8 + c] = (int8_t)(r >= 5 ? 1 : 2);
+    }
+    if (game == OR_HASAMI) {
+        /* P1 fills the bottom two rows, P2 the top two */
+        for (int c = 0; c < 9; c++) {
+            g->cell[0 * 9 + c] = g->cell[1 * 9 + c] = 2;
+            g->cell[7 * 9 + c] = g->cell[8 * 9 + c] = 1;
+        }
+    }
     if (game == OR_OTHELLO) {
         /* D4 and E5 white (P2); D5 and E4 black (P1); row 4 is index 3. */
         g->cell[3 * 8 + 3] = 2; /* D4 = 27 */
@@ -322,6 +357,177 @@ int oracle_hex_connections(int n, const int8_t* cells) {
     return (hex_connects(&g, 1) ? 1 : 0) | (hex_connects(&g, 2) ? 2 : 0);
 }
 
+/* ---------------------------------------------------------- move games --
+ * Wolf and Sheep, English Draughts, Dai Hasami Shogi (App. C): pieces move
+ * from one cell to another, so an action is from * cells + to.  Cell values:
+ * 1 / 2 a piece of P1 / P2; 3 / 4 a king of P1 / P2 (Draughts).  P1 starts at
+ * the bottom and its "forward" is up (row 0 is the top).
+ *   Wolf and Sheep: sheep (P1) step diagonally forward, the wolf (P2)
+ *   diagonally in any direction, always onto an empty cell; the wolf wins on
+ *   reaching the bottom row.
+ *   Draughts: men step diagonally forward onto an empty cell or hop over an
+ *   adjacent opposing piece diagonally forward onto the empty cell beyond,
+ *   removing it; kings do both in all four diagonal directions; when any hop
+ *   exists, only hops are legal; a man ending on the far row becomes a king;
+ *   after a hop, if the moved piece (promoted or not) can hop again, the same
+ *   player moves again and only that piece's hops are legal.
+ *   Dai Hasami Shogi: a piece slides any distance orthogonally over empty
+ *   cells, or hops orthogonally over one adjacent piece of either side onto
+ *   the empty cell beyond (no capture); after the move, every straight
+ *   orthogonal run of opposing pieces that starts next to the moved piece and
+ *   ends at another piece of the mover is removed, and an opposing piece in a
+ *   corner whose two orthogonal neighbours are then both the mover's, one of
+ *   them the moved piece, is removed; five or more in a row, horizontally or
+ *   vertically, with none of the five on the mover's two starting rows, wins.
+ * In all three, the mover also wins when the player to move next has no
+ * legal action (as the Draughts listing of App. A ends its games). */
+static void finish(ogame* g, int outcome);
+
+static int owner_of(int v) { return v == 0 ? 0 : ((v == 1 || v == 3) ? 1 : 2); }
+
+static int on_board(const ogame* g, int r, int c) { return r >= 0 && r < g->rows && c >= 0 && c < g->cols; }
+
+static int cell_at(const ogame* g, int r, int c) { return g->cell[r * g->cols + c]; }
+
+/* the diagonal directions a Draughts piece of value v moves in */
+static int draughts_dirs(int v, int dr[4], int dc[4]) {
+    int n = 0, king = v >= 3, p = owner_of(v);
+    for (int sr = -1; sr <= 1; sr += 2)
+        for (int sc = -1; sc <= 1; sc += 2)
+            if (king || (p == 1 && sr == -1) || (p == 2 && sr == 1)) {
+                dr[n] = sr;
+                dc[n] = sc;
+                n++;
+            }
+    return n;
+}
+
+/* hops of the Draughts piece on cell i into legal[] (NULL: count only) */
+static int draughts_hops(const ogame* g, int i, uint8_t* legal) {
+    int dr[4], dc[4], r = i / 8, c = i % 8, v = g->cell[i], p = owner_of(v), n = 0;
+    int k = draughts_dirs(v, dr, dc);
+    for (int d = 0; d < k; d++) {
+        int r1 = r + dr[d], c1 = c + dc[d], r2 = r + 2 * dr[d], c2 = c + 2 * dc[d];
+        if (on_board(g, r2, c2) && owner_of(cell_at(g, r1, c1)) == 3 - p && cell_at(g, r2, c2) == 0) {
+            if (legal) legal[i * 64 + r2 * 8 + c2] = 1;
+            n++;
+        }
+    }
+    return n;
+}
+
+static int move_legal(const ogame* g, int p, uint8_t* legal) {
+    int N = g->ncells, n = 0;
+    if (legal) memset(legal, 0, (size_t)N * N);
+    if (g->game == OR_WOLF) {
+        for (int i = 0; i < N; i++) {
+            int r = i / 8, c = i % 8;
+            if (g->cell[i] != p) continue;
+            for (int sr = -1; sr <= 1; sr += 2)
+                for (int sc = -1; sc <= 1; sc += 2) {
+                    if (p == 1 && sr == 1) continue; /* sheep only go forward (up) */
+                    if (on_board(g, r + sr, c + sc) && cell_at(g, r + sr, c + sc) == 0) {
+                        if (legal) legal[i * N + (r + sr) * 8 + c + sc] = 1;
+                        n++;
+                    }
+                }
+        }
+        return n;
+    }
+    if (g->game == OR_DRAUGHTS) {
+        if (g->pending >= 0) return draughts_hops(g, g->pending, legal);
+        for (int i = 0; i < N; i++)
+            if (owner_of(g->cell[i]) == p) n += draughts_hops(g, i, legal);
+        if (n > 0) return n; /* captures take priority over steps */
+        for (int i = 0; i < N; i++) {
+            int dr[4], dc[4], r = i / 8, c = i % 8, k;
+            if (owner_of(g->cell[i]) != p) continue;
+            k = draughts_dirs(g->cell[i], dr, dc);
+            for (int d = 0; d < k; d++)
+                if (on_board(g, r + dr[d], c + dc[d]) && cell_at(g, r + dr[d], c + dc[d]) == 0) {
+                    if (legal) legal[i * N + (r + dr[d]) * 8 + c + dc[d]] = 1;
+                    n++;
+                }
+        }
+        return n;
+    }
+    /* Dai Hasami Shogi */
+    for (int i = 0; i < N; i++) {
+        static const int DR[4] = {-1, 1, 0, 0}, DC[4] = {0, 0, -1, 1};
+        int r = i / 9, c = i % 9;
+        if (g->cell[i] != p) continue;
+        for (int d = 0; d < 4; d++) {
+            int k = 1;
+            while (on_board(g, r + k * DR[d], c + k * DC[d]) && cell_at(g, r + k * DR[d], c + k * DC[d]) == 0) {
+                if (legal) legal[i * N + (r + k * DR[d]) * 9 + c + k * DC[d]] = 1;
+                n++;
+                k++;
+            }
+            if (k == 1 && on_board(g, r + 2 * DR[d], c + 2 * DC[d]) && cell_at(g, r + 2 * DR[d], c + 2 * DC[d]) == 0) {
+                if (legal) legal[i * N + (r + 2 * DR[d]) * 9 + c + 2 * DC[d]] = 1; /* hop the adjacent piece */
+                n++;
+            }
+        }
+    }
+    return n;
+}
+
+/* Hasami: does p own five in a row (row or column) outside its two starting rows? */
+static int hasami_line(const ogame* g, int p) {
+    int lo = p == 1 ? 0 : 2, hi = p == 1 ? 6 : 8; /* rows that count */
+    for (int r = lo; r <= hi; r++)
+        for (int c = 0; c < 9; c++) {
+            int h = 0, v = 0;
+            for (int k = 0; k < 5; k++) {
+                h += c + k < 9 && cell_at(g, r, c + k) == p;
+                v += r + k <= hi && cell_at(g, r + k, c) == p;
+            }
+            if (h == 5 || v == 5) return 1;
+        }
+    return 0;
+}
+
+static void move_apply(ogame* g, int action) {
+    int N = g->ncells, from = action / N, to = action % N, p = g->to_move, v = g->cell[from];
+    int rf = from / g->cols, cf = from % g->cols, rt = to / g->cols, ct = to % g->cols, again = 0;
+    g->cell[from] = 0;
+    g->cell[to] = (int8_t)v;
+    if (g->game == OR_DRAUGHTS) {
+        int hop = rt - rf == 2 || rf - rt == 2;
+        if (hop) g->cell[((rf + rt) / 2) * 8 + (cf + ct) / 2] = 0;
+        if (v < 3 && ((p == 1 && rt == 0) || (p == 2 && rt == 7))) g->cell[to] = (int8_t)(v + 2);
+        again = hop && draughts_hops(g, to, NULL) > 0;
+        g->pending = again ? to : -1;
+    }
+    if (g->game == OR_HASAMI) {
+        static const int DR[4] = {-1, 1, 0, 0}, DC[4] = {0, 0, -1, 1};
+        for (int d = 0; d < 4; d++) {
+            int k = 1;
+            while (on_board(g, rt + k * DR[d], ct + k * DC[d]) && cell_at(g, rt + k * DR[d], ct + k * DC[d]) == 3 - p) k++;
+            if (k > 1 && on_board(g, rt + k * DR[d], ct + k * DC[d]) && cell_at(g, rt + k * DR[d], ct + k * DC[d]) == p)
+                for (int j = 1; j < k; j++) g->cell[(rt + j * DR[d]) * 9 + ct + j * DC[d]] = 0;
+        }
+        for (int cr = 0; cr <= 8; cr += 8)
+            for (int cc = 0; cc <= 8; cc += 8) {
+                int vr = cr == 0 ? 1 : 7, hc = cc == 0 ? 1 : 7; /* the corner's two neighbours */
+                if (cell_at(g, cr, cc) == 3 - p && cell_at(g, vr, cc) == p && cell_at(g, cr, hc) == p &&
+                    (to == vr * 9 + cc || to == cr * 9 + hc))
+                    g->cell[cr * 9 + cc] = 0;
+            }
+    }
+    g->ply += 1;
+    if (!again) g->to_move = 3 - p;
+    if (g->game == OR_WOLF && p == 2 && rt == 7) {
+        finish(g, 2);
+        return;
+    }
+    if (g->game == OR_HASAMI && hasami_line(g, p)) {
+        finish(g, p);
+        return;
+    }
+    if (move_legal(g, g->to_move, NULL) == 0) finish(g, p);
+}
+
 /* --------------------------------------------------------- legal actions --
  * legal[a] = 1 for each legal action a in [0, num_actions); returns the
  * count.  A finished game has no legal action.                           */
@@ -330,6 +536,7 @@ int oracle_legal(const ogame* g, uint8_t* legal) {
     int n = 0;
     memset(legal, 0, (size_t)A);
     if (g->outcome != OR_ONGOING) return 0;
+    if (is_move_game(g->game)) return move_legal(g, g->to_move, legal);
     for (int i = 0; i < g->ncells; i++) {
         int ok = 0;
         if (g->cell[i] != 0) continue;
@@ -375,7 +582,7 @@ void oracle_rewards(const ogame* g, float* rew2) {
  * game was already over (a no-op), -1 for an illegal action (the game ends
  * and the mover loses).                                                   */
 int oracle_apply(ogame* g, int action) {
-    uint8_t legal[OR_MAXCELLS + 1];
+    uint8_t legal[OR_MAXACTIONS];
     int A, p;
     if (g->outcome != OR_ONGOING) return 1;
     A = oracle_num_actions(g->game, g->rows, g->cols);
@@ -385,6 +592,11 @@ int oracle_apply(ogame* g, int action) {
         g->illegal = 1;
         finish(g, 3 - p);
         return -1;
+    }
+    if (is_move_game(g->game)) {
+        move_apply(g, action);
+        if (g->outcome == OR_ONGOING && g->ply >= oracle_ply_cap(g->game, g->rows, g->cols)) finish(g, OR_CAPPED);
+        return 0;
     }
     if (g->game == OR_OTHELLO && action == g->ncells) {
         g->passes += 1;
@@ -470,7 +682,7 @@ int oracle_apply(ogame* g, int action) {
  * action with k = pick(r, count).  Stops at the end of the game or, when
  * stop_ply >= 0, once ply == stop_ply.                                    */
 void oracle_playout(ogame* g, uint64_t seed, uint64_t env, int stop_ply) {
-    uint8_t legal[OR_MAXCELLS + 1];
+    uint8_t legal[OR_MAXACTIONS];
     int A = oracle_num_actions(g->game, g->rows, g->cols);
     while (g->outcome == OR_ONGOING && (stop_ply < 0 || g->ply < stop_ply)) {
         int n = oracle_legal(g, legal);
@@ -507,6 +719,8 @@ static void load_state(ogame* g, int game, int rows, int cols, int64_t e, const 
         int v = (uint8_t)passes[e];
         g->captures[1] = 2 * (v & 15);
         g->captures[2] = 2 * (v >> 4);
+    } else if (game == OR_DRAUGHTS) {
+        g->pending = passes[e] - 1; /* the passes slot holds pending + 1 */
     } else {
         g->passes = passes[e];
     }
@@ -521,6 +735,8 @@ static void store_state(const ogame* g, int64_t e, int8_t* board, int8_t* to_mov
         if (g->game == OR_PENTE) {
             int a = g->captures[1] / 2, b = g->captures[2] / 2;
             passes[e] = (int8_t)((a > 15 ? 15 : a) | ((b > 15 ? 15 : b) << 4));
+        } else if (g->game == OR_DRAUGHTS) {
+            passes[e] = (int8_t)(g->pending + 1);
         } else {
             passes[e] = (int8_t)g->passes;
         }
@@ -623,7 +839,7 @@ int oracle_rollout_mixed(const int32_t* desc, int64_t n, int64_t env_offset, uin
  * Number of action sequences of length depth from the start position in
  * which no position before the last action is finished.                    */
 static uint64_t perft_rec(const ogame* g, int depth) {
-    uint8_t legal[OR_MAXCELLS + 1];
+    uint8_t legal[OR_MAXACTIONS];
     int A, n;
     uint64_t total = 0;
     if (depth == 0) return 1;
@@ -638,6 +854,33 @@ static uint64_t perft_rec(const ogame* g, int depth) {
         total += perft_rec(&child, depth - 1);
     }
     return total;
+}
+
+/* Perft by turns: an action after which the same player moves again (a
+ * Draughts capture that must continue) does not use up a level, so a whole
+ * multi-capture counts as one move, as published Draughts perft counts do. */
+static uint64_t perft_turns_rec(const ogame* g, int depth) {
+    uint8_t legal[OR_MAXACTIONS];
+    int A;
+    uint64_t total = 0;
+    if (depth == 0) return 1;
+    if (g->outcome != OR_ONGOING) return 0;
+    A = oracle_num_actions(g->game, g->rows, g->cols);
+    oracle_legal(g, legal);
+    for (int a = 0; a < A; a++) {
+        if (!legal[a]) continue;
+        ogame child = *g;
+        oracle_apply(&child, a);
+        if (child.outcome == OR_ONGOING && child.to_move == g->to_move) total += perft_turns_rec(&child, depth);
+        else total += perft_turns_rec(&child, depth - 1);
+    }
+    return total;
+}
+
+uint64_t oracle_perft_turns(int game, int rows, int cols, int depth) {
+    ogame g;
+    if (oracle_init(&g, game, rows, cols) != 0) return 0;
+    return perft_turns_rec(&g, depth);
 }
 
 uint64_t oracle_perft(int game, int rows, int cols, int depth) {
@@ -703,7 +946,7 @@ typedef struct {
 } onode;
 
 static void playout_key(ogame* g, uint64_t key) {
-    uint8_t legal[OR_MAXCELLS + 1];
+    uint8_t legal[OR_MAXACTIONS];
     int A = oracle_num_actions(g->game, g->rows, g->cols);
     while (g->outcome == OR_ONGOING) {
         int n = oracle_legal(g, legal), action = -1;
@@ -734,7 +977,7 @@ static int mcts_search(const ogame* root, uint64_t key, int iters, double c, uin
     onode* nd = (onode*)calloc((size_t)iters + 1, sizeof(onode));
     uint8_t* tried = (uint8_t*)calloc(((size_t)iters + 1) * (size_t)A, 1);
     double* T = (double*)calloc((size_t)iters + 2, sizeof(double));
-    uint8_t legal[OR_MAXCELLS + 1];
+    uint8_t legal[OR_MAXACTIONS];
     int count = 1, best = -1;
     for (int m = 1; m <= iters + 1; m++) T[m] = c * sqrt(log((double)m));
     nd[0].parent = -1;
@@ -836,7 +1079,7 @@ int oracle_mcts_search(int game, int rows, int cols, int64_t n, int64_t env_offs
  * more than one legal action, and the cells occupied at some point. */
 int oracle_mcts_play(int game, int rows, int cols, int64_t n, int64_t env_offset, uint64_t seed, int iters_p1,
                      int iters_p2, double c, int8_t* outcome, int16_t* plies, int16_t* agency, int16_t* coverage) {
-    uint8_t legal[OR_MAXCELLS + 1];
+    uint8_t legal[OR_MAXACTIONS];
     if (oracle_check_params(game, rows, cols) != 0 || iters_p1 < 1 || iters_p2 < 1) return -1;
     for (int64_t e = 0; e < n; e++) {
         ogame g;
