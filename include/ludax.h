@@ -78,13 +78,30 @@ extern "C" {
 #define LUDAX_LINE_EXACT 1
 #define LUDAX_LINE_GRAVITY 2
 #define LUDAX_LINE_MISERE 4
+/* Games whose pieces move (App. C): an action is from * cells + to, so
+ * num_actions = cells^2; P1 starts at the bottom; the mover wins when the
+ * player to move next has no legal action; capped (OUTCOME_CAPPED) after 200
+ * plies (Sec. 6 stops unbounded games after 200 turns).                   */
+#define LUDAX_GAME_WOLF_SHEEP 8    /* 8x8: four sheep (P1, cells 56/58/60/62) step
+                                      diagonally up, the wolf (P2, cell 3) steps
+                                      diagonally either way; the wolf wins on
+                                      the bottom row                          */
+#define LUDAX_GAME_DRAUGHTS 9      /* English Draughts 8x8: men on the dark cells
+                                      of rows 5-7 (P1) and 0-2 (P2); forced
+                                      hops, multi-hops as extra turns of the
+                                      same piece, crowning on the far row     */
+#define LUDAX_GAME_HASAMI_SHOGI 10 /* Dai Hasami Shogi 9x9: rook slides or hops
+                                      over an adjacent piece; custodial and
+                                      corner captures; five in a row outside
+                                      the mover's two home rows wins          */
 
 /* ---------------------------------------------------------- outcomes -- */
 #define LUDAX_OUTCOME_ONGOING (-1)
 #define LUDAX_OUTCOME_DRAW 0
 #define LUDAX_OUTCOME_P1 1
 #define LUDAX_OUTCOME_P2 2
-#define LUDAX_OUTCOME_CAPPED 3 /* ply cap (9/42/128/n*n) hit: never for a correct engine */
+#define LUDAX_OUTCOME_CAPPED 3 /* ply cap hit: 9/42/128/n*n never for a correct engine; Pente
+                                  2,000 and the move games 200 (games of unbounded length) */
 
 /* ------------------------------------------------------ rollout flags -- */
 #define LUDAX_ROLLOUT_FROM_START 1u /* play from the start position; stored state not read */
@@ -102,12 +119,15 @@ typedef struct ludax_env ludax_env;
 /* A batch of positions in canonical form, all arrays on the device:
  *   board   int8  [num_envs][cells]      cell values 0/1/2 (cells = rows*cols;
  *                                        Yavalath: the 61 cells of the hexagon,
- *                                        row by row, left to right)
+ *                                        row by row, left to right); Draughts
+ *                                        kings are 3 (P1) and 4 (P2)
  *   to_move int8  [num_envs]             1 or 2
  *   ply     int16 [num_envs]             plies played (passes included)
  *   passes  int8  [num_envs]             consecutive passes (Reversi); Pente:
  *                                        captured pairs, P1's in the low 4 bits,
- *                                        P2's in the high 4 bits; else 0
+ *                                        P2's in the high 4 bits; Draughts: 1 +
+ *                                        the cell of the piece that must hop
+ *                                        again (0 if none); else 0
  *   outcome int8  [num_envs]             LUDAX_OUTCOME_*                      */
 typedef struct {
     int8_t* board;
@@ -140,7 +160,8 @@ typedef struct {
  * P2 on cells 27/36 and D5/E4 black = P1 on cells 35/28; P1 to move).
  *   game       LUDAX_GAME_*
  *   p          board size: TTT 3x3, C4 6x7, Othello 8x8, Hex n x n (2..11),
- *              Gomoku 15x15, Pente 19x19, Yavalath 9x9 (the hexagon's axial grid)
+ *              Gomoku 15x15, Pente 19x19, Yavalath 9x9 (the hexagon's axial grid),
+ *              Wolf and Sheep 8x8, Draughts 8x8, Dai Hasami Shogi 9x9
  *   num_envs   1 .. 2^31-1
  *   env_offset global index of env 0 (keys the random draws; lets several
  *              GPUs or calls cover disjoint env ranges), >= 0
@@ -154,8 +175,9 @@ int ludax_env_destroy(ludax_env* env);
 /* Rebind the env to another stream (same device). */
 int ludax_env_set_stream(ludax_env* env, void* stream);
 
-/* Sizes of the env's action space: num_actions = rows*cols (+1 pass for
- * Reversi); mask_words = ceil(rows*cols / 64) words per env in legal masks. */
+/* Sizes of the env's action space: num_actions = cells (+1 pass for
+ * Reversi; cells^2 for the move games); mask_words = ceil(cells / 64) words
+ * per env in legal masks (ceil(cells^2 / 64) for the move games).          */
 int ludax_env_sizes(const ludax_env* env, int32_t* num_actions, int32_t* mask_words, int64_t* num_envs);
 
 /* ---------------------------------------------------------------------------

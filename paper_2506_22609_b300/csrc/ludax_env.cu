@@ -52,7 +52,13 @@ __global__ void legal_kernel(EnvDev d, uint64_t* out, uint8_t* pass_legal, int w
         m = g.legal();
         pass = G::kHasPass && !any(m);
     }
-    for (int w = 0; w < words; ++w) out[e * words + w] = canon_mask_word(g, m, w);
+    if constexpr (IsMove<G>::value) {
+        uint64_t* row = out + e * words;
+        for (int w = 0; w < words; ++w) row[w] = 0;
+        if (g.outcome == kOngoing) g.for_each_move([&](int a) { row[a >> 6] |= 1ull << (a & 63); });
+    } else {
+        for (int w = 0; w < words; ++w) out[e * words + w] = canon_mask_word(g, m, w);
+    }
     if (pass_legal) pass_legal[e] = pass ? 1 : 0;
 }
 
@@ -75,9 +81,9 @@ __global__ void step_kernel(EnvDev d, const int32_t* actions, float2* rewards, u
         if (G::kHasPass && a == G::kCells) {
             ok = !any(m);
             if (ok) g.pass();
-        } else if (a >= 0 && a < cells_of(g)) {
-            int b = g.bit_of(a);
-            ok = mask_has(m, b);
+        } else if (a >= 0 && a < actions_of(g) - (G::kHasPass ? 1 : 0)) {
+            int b = g.bit_of(a);  // move games: the action's ordinal, -1 if not legal
+            ok = b >= 0 && mask_has(m, b);
             if (ok) g.place(b);
         }
         int illegal = 0;
@@ -122,14 +128,19 @@ __global__ void get_state_kernel(EnvDev d, ludax_state_view v) {
     set_table(g, nullptr);
     load_state(g, d, e);
     int8_t* b = v.board + e * d.cells;
-    for (int c = 0; c < d.cells; ++c) {
-        int bit = g.bit_of(c);
-        int v_own = mask_has(g.own, bit), v_opp = mask_has(g.opp, bit);
-        b[c] = (int8_t)(v_own ? g.side + 1 : (v_opp ? 2 - g.side : 0));
+    if constexpr (IsMove<G>::value) {
+        for (int c = 0; c < d.cells; ++c) b[c] = (int8_t)g.cell_value(c);
+    } else {
+        for (int c = 0; c < d.cells; ++c) {
+            int bit = g.bit_of(c);
+            int v_own = mask_has(g.own, bit), v_opp = mask_has(g.opp, bit);
+            b[c] = (int8_t)(v_own ? g.side + 1 : (v_opp ? 2 - g.side : 0));
+        }
     }
     v.to_move[e] = (int8_t)(g.side + 1);
     v.ply[e] = (int16_t)g.ply;
     v.passes[e] = (int8_t)g.passes;
+    if constexpr (IsMove<G>::value) v.passes[e] = (int8_t)g.extra();
     if constexpr (G::kGame == Pente::kGame) {  // captured pairs: P1 low nibble, P2 high nibble
         const int c1 = g.side == 0 ? g.caps_own : g.caps_opp, c2 = g.side == 0 ? g.caps_opp : g.caps_own;
         v.passes[e] = (int8_t)((c1 & 15) | ((c2 & 15) << 4));
@@ -155,27 +166,40 @@ __global__ void set_state_kernel(EnvDev d, ludax_state_view v) {
     G g;
     set_table(g, nullptr);
     configure(g, d.desc);
-    typename G::Mask p1{}, p2{};
-    const int8_t* b = v.board + e * d.cells;
-    for (int c = 0; c < d.cells; ++c) {
-        int x = b[c];
-        if (x == 1) set_bit(p1, g.bit_of(c));
-        if (x == 2) set_bit(p2, g.bit_of(c));
-    }
-    g.side = v.to_move[e] == 2 ? 1 : 0;
-    g.ply = v.ply[e];
-    g.passes = v.passes[e];
-    g.outcome = v.outcome[e];
-    g.own = g.side == 0 ? p1 : p2;
-    g.opp = g.side == 0 ? p2 : p1;
-    if constexpr (G::kGame == Pente::kGame) {
-        const int x = (uint8_t)v.passes[e], c1 = x & 15, c2 = x >> 4;
+    if constexpr (IsMove<G>::value) {
+        g.reset();
+        g.clear();
+        g.side = v.to_move[e] == 2 ? 1 : 0;  // the pieces are kept relative to the side to move
+        const int8_t* b = v.board + e * d.cells;
+        for (int c = 0; c < d.cells; ++c) g.set_cell(c, b[c]);
+        g.ply = v.ply[e];
         g.passes = 0;
-        g.caps_own = g.side == 0 ? c1 : c2;
-        g.caps_opp = g.side == 0 ? c2 : c1;
+        g.outcome = v.outcome[e];
+        g.set_extra((uint8_t)v.passes[e]);
+        store_state(g, d, e);
+    } else {
+        typename G::Mask p1{}, p2{};
+        const int8_t* b = v.board + e * d.cells;
+        for (int c = 0; c < d.cells; ++c) {
+            int x = b[c];
+            if (x == 1) set_bit(p1, g.bit_of(c));
+            if (x == 2) set_bit(p2, g.bit_of(c));
+        }
+        g.side = v.to_move[e] == 2 ? 1 : 0;
+        g.ply = v.ply[e];
+        g.passes = v.passes[e];
+        g.outcome = v.outcome[e];
+        g.own = g.side == 0 ? p1 : p2;
+        g.opp = g.side == 0 ? p2 : p1;
+        if constexpr (G::kGame == Pente::kGame) {
+            const int x = (uint8_t)v.passes[e], c1 = x & 15, c2 = x >> 4;
+            g.passes = 0;
+            g.caps_own = g.side == 0 ? c1 : c2;
+            g.caps_opp = g.side == 0 ? c2 : c1;
+        }
+        if constexpr (HexN<G>::value != 0) g.rebuild();
+        store_state(g, d, e);
     }
-    if constexpr (HexN<G>::value != 0) g.rebuild();
-    store_state(g, d, e);
 }
 
 // ----------------------------------------------------- fused playouts --
@@ -479,10 +503,12 @@ int ludax_env_create(ludax_env** out, int32_t game, const ludax_board_params* p,
     *out = nullptr;
     if (num_envs < 1 || num_envs > 0x7FFFFFFFll || env_offset < 0) return LUDAX_ERR_ARG;
     int planes = 0, cells = 0;
+    bool move_game = false;
     int st = dispatch_game(game, p->rows, p->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         planes = G::kPlanes;
         cells = G::kGame == LineGame::kGame ? p->rows * p->cols : G::kCells;
+        move_game = IsMove<G>::value;
         return LUDAX_OK;
     });
     if (st != LUDAX_OK) return st;
@@ -501,8 +527,8 @@ int ludax_env_create(ludax_env** out, int32_t game, const ludax_board_params* p,
     env->cols = p->cols;
     env->cells = cells;
     env->desc = desc;
-    env->num_actions = env->cells + (game == LUDAX_GAME_OTHELLO ? 1 : 0);
-    env->mask_words = (env->cells + 63) / 64;
+    env->num_actions = move_game ? env->cells * env->cells : env->cells + (game == LUDAX_GAME_OTHELLO ? 1 : 0);
+    env->mask_words = move_game ? (env->num_actions + 63) / 64 : (env->cells + 63) / 64;
     env->planes = planes;
     env->n = num_envs;
     env->env_offset = env_offset;

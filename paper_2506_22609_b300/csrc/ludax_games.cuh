@@ -902,6 +902,10 @@ struct LineGame {
     }
 };
 
+}  // namespace ludax
+#include "ludax_movegames.cuh"
+namespace ludax {
+
 // parameters of a game instance: no-ops except for the parametric line game
 template <class G>
 __device__ __forceinline__ void configure(G& g, int32_t desc) {

@@ -56,6 +56,9 @@ int dispatch_game(int game, int rows, int cols, F&& f) {
     case LUDAX_GAME_YAVALATH: return (rows == 9 && cols == 9) ? f(Tag<Yavalath>{}) : LUDAX_ERR_SIZE;
     case LUDAX_GAME_LINE:
         return (rows >= 1 && cols >= 1 && rows * (cols + 1) <= 128) ? f(Tag<LineGame>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_WOLF_SHEEP: return (rows == 8 && cols == 8) ? f(Tag<WolfSheep>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_DRAUGHTS: return (rows == 8 && cols == 8) ? f(Tag<Draughts>{}) : LUDAX_ERR_SIZE;
+    case LUDAX_GAME_HASAMI_SHOGI: return (rows == 9 && cols == 9) ? f(Tag<HasamiShogi>{}) : LUDAX_ERR_SIZE;
     default: return LUDAX_ERR_GAME;
     }
 }
@@ -63,9 +66,10 @@ int dispatch_game(int game, int rows, int cols, F&& f) {
 // Per-env descriptors (game | rows << 8 | cols << 16 | line << 24 | flags << 28)
 // grouped by kernel instance ("buckets"): 0 TTT, 1 C4, 2 Othello, 3 + k Hex
 // (k + 2) x (k + 2), 13 Gomoku, 14 Pente, 15 Yavalath, 16 the parametric line
-// game (any parameters).  Returns the bucket, -1 for an unknown game or
-// -2 for a board size the game's kernel does not take.
-constexpr int kDescBuckets = 17;
+// game (any parameters), 17 Wolf and Sheep, 18 Draughts, 19 Dai Hasami Shogi.
+// Returns the bucket, -1 for an unknown game or -2 for a board size the
+// game's kernel does not take.
+constexpr int kDescBuckets = 20;
 __host__ __device__ inline int desc_bucket(int32_t d) {
     if (d < 0) return -1;
     const int game = d & 0xFF, rows = (d >> 8) & 0xFF, cols = (d >> 16) & 0xFF;
@@ -82,6 +86,9 @@ __host__ __device__ inline int desc_bucket(int32_t d) {
     case LUDAX_GAME_GOMOKU: return (rows == 15 && cols == 15) ? 13 : -2;
     case LUDAX_GAME_PENTE: return (rows == 19 && cols == 19) ? 14 : -2;
     case LUDAX_GAME_YAVALATH: return (rows == 9 && cols == 9) ? 15 : -2;
+    case LUDAX_GAME_WOLF_SHEEP: return (rows == 8 && cols == 8) ? 17 : -2;
+    case LUDAX_GAME_DRAUGHTS: return (rows == 8 && cols == 8) ? 18 : -2;
+    case LUDAX_GAME_HASAMI_SHOGI: return (rows == 9 && cols == 9) ? 19 : -2;
     default: return -1;
     }
 }

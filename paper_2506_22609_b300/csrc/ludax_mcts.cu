@@ -32,8 +32,10 @@ namespace {
 using namespace ludax;
 
 struct TNode {
-    int16_t parent, action, first_child, next_sibling;  // action: internal bit, -1 = pass
-    uint32_t N, W;
+    int16_t parent, action, first_child, next_sibling;  // action: internal bit (move games: ordinal), -1 = pass
+    uint16_t N, W;                                      // N <= 4096 iterations, W <= 2N half points
+    int8_t mover;                                       // side that made the move into the node (0 = P1)
+    int8_t pad[3];
 };
 static_assert(sizeof(TNode) == 16, "tree node is 16 bytes");
 
@@ -100,6 +102,12 @@ __device__ __forceinline__ uint32_t half_points(int outcome, int mover) {
     return (outcome == kDraw || outcome == kCapped) ? 1u : 0u;
 }
 
+__device__ __forceinline__ TNode make_node(int parent, int action, int first_child, int next_sibling, uint32_t N,
+                                           uint32_t W, int mover) {
+    return TNode{(int16_t)parent, (int16_t)action, (int16_t)first_child, (int16_t)next_sibling, (uint16_t)N,
+                 (uint16_t)W, (int8_t)mover, {0, 0, 0}};
+}
+
 __device__ __forceinline__ double ucb1(uint32_t W, uint32_t N, double t) {
     const double n = (double)N;
     return __dadd_rn(__ddiv_rn((double)W, __dmul_rn(2.0, n)), __ddiv_rn(t, __dsqrt_rn(n)));
@@ -125,23 +133,21 @@ __device__ void uct_iteration(const G& root, uint64_t ki, const double* __restri
     using M = typename G::Mask;
     constexpr int MW = MaskWords<M>::value;
     G g = root;
-    int x = 0, depth = 0;
+    int x = 0;
     while (g.outcome == kOngoing) {
         const M legal = g.legal();
         if (G::kHasPass && !any(legal)) {  // the forced pass is the only action
             if (nd[x].first_child < 0) {
                 const int y = count++;
-                nd[y] = TNode{(int16_t)x, -1, -1, -1, 0u, 0u};
+                nd[y] = make_node(x, -1, -1, -1, 0u, 0u, g.side);
                 mask_zero(mk + (size_t)y * MW, MW);
                 nd[x].first_child = (int16_t)y;
                 play(g, -1);
                 x = y;
-                ++depth;
                 break;
             }
             x = nd[x].first_child;
             play(g, -1);
-            ++depth;
             continue;
         }
         M tried;
@@ -153,12 +159,11 @@ __device__ void uct_iteration(const G& root, uint64_t ki, const double* __restri
             mask_add(tried, b);
             mask_put(mk + (size_t)x * MW, tried);
             const int y = count++;
-            nd[y] = TNode{(int16_t)x, (int16_t)b, -1, nd[x].first_child, 0u, 0u};
+            nd[y] = make_node(x, b, -1, nd[x].first_child, 0u, 0u, g.side);
             mask_zero(mk + (size_t)y * MW, MW);
             nd[x].first_child = (int16_t)y;
             play(g, b);
             x = y;
-            ++depth;
             break;
         }
         // every legal action has a child: UCB1, the smallest action on a tie
@@ -176,16 +181,13 @@ __device__ void uct_iteration(const G& root, uint64_t ki, const double* __restri
         }
         play(g, best_a);
         x = best;
-        ++depth;
     }
     while (g.outcome == kOngoing) random_ply(g, ki);
-    // every ply alternates the side to move, so the node at depth d was
-    // entered by side (side0 + d - 1) mod 2
-    for (int y = x, d = depth; y > 0; y = nd[y].parent, --d) {
-        nd[y].N += 1u;
-        nd[y].W += half_points(g.outcome, (root.side + d - 1) & 1);
+    for (int y = x; y > 0; y = nd[y].parent) {
+        nd[y].N = (uint16_t)(nd[y].N + 1u);
+        nd[y].W = (uint16_t)(nd[y].W + half_points(g.outcome, nd[y].mover));
     }
-    nd[0].N += 1u;
+    nd[0].N = (uint16_t)(nd[0].N + 1u);
 }
 
 // the move: most visits, then largest W, then smallest action
@@ -211,7 +213,7 @@ __device__ int uct_search_warp(const G& root, uint64_t key, int iters, const dou
     using M = typename G::Mask;
     constexpr int MW = MaskWords<M>::value;
     if (lane == 0) {
-        nd[0] = TNode{-1, -1, -1, -1, 0u, 0u};
+        nd[0] = make_node(-1, -1, -1, -1, 0u, 0u, 0);
         mask_zero(mk, MW);
     }
     __syncwarp();
@@ -243,13 +245,13 @@ __device__ int uct_search_warp(const G& root, uint64_t key, int iters, const dou
                 const uint64_t ki = splitmix64(key ^ (uint64_t)(i + lane));
                 while (g.outcome == kOngoing) random_ply(g, ki);
                 const int y = count + lane;
-                nd[y] = TNode{0, (int16_t)mine, -1, (int16_t)(lane == 0 ? head : y - 1), 1u,
-                              half_points(g.outcome, root.side)};
+                nd[y] = make_node(0, mine, -1, lane == 0 ? head : y - 1, 1u, half_points(g.outcome, root.side),
+                                  root.side);
                 mask_zero(mk + (size_t)y * MW, MW);
             }
             if (lane == 0) {
                 nd[0].first_child = (int16_t)(count + R - 1);
-                nd[0].N += (uint32_t)R;
+                nd[0].N = (uint16_t)(nd[0].N + R);
                 mask_put(mk, tried | (untried & ~u));
             }
             count += R;
@@ -299,7 +301,7 @@ __device__ void play_match(G& g, const MctsArgs& a, int64_t e, int64_t match, in
     constexpr int MW = MaskWords<typename G::Mask>::value;
     TNode* nd = a.nodes + (size_t)e * a.cap_nodes;
     uint64_t* mk = a.masks + (size_t)e * a.cap_nodes * a.slab_words;
-    typename G::Mask ever = g.own | g.opp;
+    auto ever = occupied_of(g);
     int turns = 0;
     (void)MW;
     while (g.outcome == kOngoing) {
@@ -315,7 +317,7 @@ __device__ void play_match(G& g, const MctsArgs& a, int64_t e, int64_t match, in
             }
         }
         play(g, b);
-        ever = ever | g.own | g.opp;
+        ever = ever | occupied_of(g);
     }
     if (lane == 0) {
         if (a.outcome) a.outcome[e] = (int8_t)g.outcome;
@@ -413,6 +415,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) uct_match_mixed_kernel(Mc
     case 14: mixed_match<Pente>(a, e, lane); break;
     case 15: mixed_match<Yavalath>(a, e, lane); break;
     case 16: mixed_match<LineGame>(a, e, lane); break;
+    case 17: mixed_match<WolfSheep>(a, e, lane); break;
+    case 18: mixed_match<Draughts>(a, e, lane); break;
+    case 19: mixed_match<HasamiShogi>(a, e, lane); break;
     default: break;  // validated on the host
     }
 }

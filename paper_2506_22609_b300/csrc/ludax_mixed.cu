@@ -127,7 +127,10 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         case 13: q = run_bucket<Gomoku>(a, q, end, slots, refill, nullptr); break;
         case 14: q = run_bucket<Pente>(a, q, end, slots, refill, nullptr); break;
         case 15: q = run_bucket<Yavalath>(a, q, end, slots, refill, nullptr); break;
-        default: q = run_bucket<LineGame>(a, q, end, slots, refill, nullptr); break;
+        case 16: q = run_bucket<LineGame>(a, q, end, slots, refill, nullptr); break;
+        case 17: q = run_bucket<WolfSheep>(a, q, end, slots, refill, nullptr); break;
+        case 18: q = run_bucket<Draughts>(a, q, end, slots, refill, nullptr); break;
+        default: q = run_bucket<HasamiShogi>(a, q, end, slots, refill, nullptr); break;
         }
     }
 }

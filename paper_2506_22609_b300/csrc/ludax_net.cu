@@ -643,10 +643,14 @@ int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld) {
     if ((uintptr_t)x_dev % 16) return LUDAX_ERR_ALIGN;
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
+        if constexpr (IsMove<G>::value) {
+            return LUDAX_ERR_GAME;  // the value net encodes placement boards (two stone planes)
+        } else {
         pack_inputs_kernel<G><<<blocks_for(env->n, 128), 128, 0, env->stream>>>(
             EnvDev{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters, env->desc, env->cells},
             reinterpret_cast<__nv_bfloat16*>(x_dev), ld);
         return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+        }
     });
 }
 
@@ -656,8 +660,11 @@ int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K
     if (n->stream != env->stream) return LUDAX_ERR_ARG;
     long long chunk = (n->max_batch / K);
     if (chunk < 1) return LUDAX_ERR_SIZE;
-    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) -> int {
         using G = typename decltype(tag)::type;
+        if constexpr (IsMove<G>::value) {
+            return LUDAX_ERR_GAME;  // the value net encodes placement boards (two stone planes)
+        } else {
         EnvDev d{env->d_planes, env->d_meta, env->n, env->env_offset, env->d_counters, env->desc, env->cells};
         for (long long e0 = 0; e0 < env->n; e0 += chunk) {
             long long nc = std::min(chunk, env->n - e0);
@@ -673,6 +680,7 @@ int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K
             combine_kernel<<<blocks_for(nc, 256), 256, 0, env->stream>>>(e0, nc, K, n->score, n->done, n->pout, value_dev);
         }
         return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+        }
     });
 }
 

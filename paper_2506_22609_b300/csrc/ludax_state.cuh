@@ -8,10 +8,13 @@
 //                         k=4,5 P1 edge-A set, k=6,7 P1 edge-B set,
 //                         k=8,9 P2 edge-A set, k=10,11 P2 edge-B set
 //                    Gomoku/Pente/Yavalath: k = 0..W-1 P1 words, W..2W-1 P2 words
+//                    Wolf and Sheep: P1, P2 pieces; Draughts: P1 men, P1
+//                    kings, P2 men, P2 kings; Dai Hasami Shogi: P1 lo/hi, P2 lo/hi
 //   meta[e]          uint32: bits 0-7 ply (low byte), 8-9 passes, 10 side to
 //                    move (0 = P1), 12-14 outcome+1 (0 ongoing), 15 illegal
 //                    flag, 16-23 ply (high byte), 24-27 / 28-31 pairs captured
-//                    by P1 / P2 (Pente)
+//                    by P1 / P2 (Pente); 24-31 Draughts: 1 + the cell of the
+//                    piece that must hop again (0 if none)
 #pragma once
 #include "ludax_games.cuh"
 
@@ -76,7 +79,13 @@ __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
     configure(g, d.desc);
     const uint32_t meta = d.meta[e];
     unpack_meta(meta, g.ply, g.passes, g.side, g.outcome);
-    if constexpr (WideW<G>::value != 0) {
+    if constexpr (IsMove<G>::value) {
+        uint64_t w[G::kPlanes];
+#pragma unroll
+        for (int k = 0; k < G::kPlanes; ++k) w[k] = d.planes[(int64_t)k * d.n + e];
+        g.planes_in(w);
+        g.set_extra((int)((meta >> 24) & 0xFF));
+    } else if constexpr (WideW<G>::value != 0) {
         constexpr int W = WideW<G>::value;
         typename G::Mask p1, p2;
 #pragma unroll
@@ -114,7 +123,14 @@ __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
 
 template <class G>
 __device__ __forceinline__ void store_state(const G& g, const EnvDev& d, int64_t e, int illegal = 0) {
-    if constexpr (WideW<G>::value != 0) {
+    if constexpr (IsMove<G>::value) {
+        const int x = g.extra();
+        d.meta[e] = pack_meta(g.ply, g.passes, g.side, g.outcome, illegal, x & 15, (x >> 4) & 15);
+        uint64_t w[G::kPlanes];
+        g.planes_out(w);
+#pragma unroll
+        for (int k = 0; k < G::kPlanes; ++k) d.planes[(int64_t)k * d.n + e] = w[k];
+    } else if constexpr (WideW<G>::value != 0) {
         constexpr int W = WideW<G>::value;
         int c1 = 0, c2 = 0;
         if constexpr (G::kGame == Pente::kGame) {
@@ -188,6 +204,20 @@ __device__ __forceinline__ long long claim_next(unsigned long long* cursor) {
     if (lane == leader) base = atomicAdd(cursor, (unsigned long long)__popc(m));
     base = __shfl_sync(m, base, leader);
     return (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+// cells holding a piece (any player)
+template <class G>
+__device__ __forceinline__ auto occupied_of(const G& g) {
+    if constexpr (IsMove<G>::value) return g.occupied();
+    else return g.own | g.opp;
+}
+
+// number of canonical actions (move games: from * cells + to)
+template <class G>
+__device__ __forceinline__ int actions_of(const G& g) {
+    if constexpr (IsMove<G>::value) return G::kActions;
+    else return cells_of(g) + (G::kHasPass ? 1 : 0);
 }
 
 // result of a finished game from P1's view: win 1, draw 0.5, loss 0

@@ -68,6 +68,8 @@ GAME_TTT, GAME_C4, GAME_OTHELLO, GAME_HEX = (_ludax.LUDAX_GAME_TTT, _ludax.LUDAX
                                              _ludax.LUDAX_GAME_HEX)
 GAME_GOMOKU, GAME_PENTE, GAME_YAVALATH, GAME_LINE = (_ludax.LUDAX_GAME_GOMOKU, _ludax.LUDAX_GAME_PENTE,
                                                      _ludax.LUDAX_GAME_YAVALATH, _ludax.LUDAX_GAME_LINE)
+GAME_WOLF_SHEEP, GAME_DRAUGHTS, GAME_HASAMI_SHOGI = (_ludax.LUDAX_GAME_WOLF_SHEEP, _ludax.LUDAX_GAME_DRAUGHTS,
+                                                     _ludax.LUDAX_GAME_HASAMI_SHOGI)
 GAME_NAMES = {v: k for k, v in _ludax.GAME_IDS.items()}
 LINE_MAX_PADDED_CELLS = 128     # rows * (cols + 1) of the parametric line-game kernel
 LINE_MAX_LENGTH = 15            # four bits of the descriptor

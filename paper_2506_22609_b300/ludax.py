@@ -22,13 +22,16 @@ LUDAX_OK = 0
 LUDAX_GAME_TTT, LUDAX_GAME_C4, LUDAX_GAME_OTHELLO, LUDAX_GAME_HEX = 0, 1, 2, 3
 LUDAX_GAME_GOMOKU, LUDAX_GAME_PENTE, LUDAX_GAME_YAVALATH, LUDAX_GAME_LINE = 4, 5, 6, 7
 LUDAX_LINE_EXACT, LUDAX_LINE_GRAVITY, LUDAX_LINE_MISERE = 1, 2, 4
+LUDAX_GAME_WOLF_SHEEP, LUDAX_GAME_DRAUGHTS, LUDAX_GAME_HASAMI_SHOGI = 8, 9, 10
+MOVE_GAMES = (LUDAX_GAME_WOLF_SHEEP, LUDAX_GAME_DRAUGHTS, LUDAX_GAME_HASAMI_SHOGI)
 LUDAX_OUTCOME_ONGOING, LUDAX_OUTCOME_DRAW, LUDAX_OUTCOME_P1, LUDAX_OUTCOME_P2, LUDAX_OUTCOME_CAPPED = -1, 0, 1, 2, 3
 LUDAX_ROLLOUT_FROM_START, LUDAX_ROLLOUT_WRITE_BACK = 1, 2
 LUDAX_MCTS_MAX_ITERS = 4096
 
 GAME_IDS = {"ttt": LUDAX_GAME_TTT, "c4": LUDAX_GAME_C4, "othello": LUDAX_GAME_OTHELLO, "hex": LUDAX_GAME_HEX,
             "gomoku": LUDAX_GAME_GOMOKU, "pente": LUDAX_GAME_PENTE, "yavalath": LUDAX_GAME_YAVALATH,
-            "line": LUDAX_GAME_LINE}
+            "line": LUDAX_GAME_LINE, "wolf_sheep": LUDAX_GAME_WOLF_SHEEP, "draughts": LUDAX_GAME_DRAUGHTS,
+            "hasami_shogi": LUDAX_GAME_HASAMI_SHOGI}
 
 
 def LUDAX_DESC(game: int, rows: int, cols: int) -> int:
@@ -461,7 +464,10 @@ class Env:
         with torch.cuda.device(self.device):
             self.handle = ludax_env_create(game, rows, cols, num_envs, env_offset, stream, line, flags)
         self.num_actions, self.mask_words, _ = ludax_env_sizes(self.handle)
-        self.cells = self.num_actions - (1 if game == LUDAX_GAME_OTHELLO else 0)
+        if game in MOVE_GAMES:  # action = from * cells + to
+            self.cells = int(round(self.num_actions ** 0.5))
+        else:
+            self.cells = self.num_actions - (1 if game == LUDAX_GAME_OTHELLO else 0)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

@@ -68,7 +68,7 @@ def test_env_create_rejects_bad_arguments_before_touching_the_device(L):
     p = ludax.ludax_board_params(6, 7)
     assert L.ludax_env_create(None, 1, ctypes.byref(p), 16, 0, None) == -1
     assert L.ludax_env_create(ctypes.byref(h), 1, None, 16, 0, None) == -1
-    assert L.ludax_env_create(ctypes.byref(h), 9, ctypes.byref(p), 16, 0, None) == -2      # bad game
+    assert L.ludax_env_create(ctypes.byref(h), 11, ctypes.byref(p), 16, 0, None) == -2      # bad game
     bad = ludax.ludax_board_params(7, 7)
     assert L.ludax_env_create(ctypes.byref(h), 1, ctypes.byref(bad), 16, 0, None) == -3    # C4 is 6x7
     hex12 = ludax.ludax_board_params(12, 12)

@@ -313,7 +313,7 @@ def test_mixed_rejects_bad_descriptors(L):
     with pytest.raises(L.LudaxError) as ei:
         L.ludax_mixed_plan_create(torch.from_numpy(d).cuda())
     assert ei.value.status == -3 and ei.value.bad_index == 37
-    d[37] = W.desc(9, 3, 3)                       # no game has id 9
+    d[37] = W.desc(11, 3, 3)                      # no game has id 11
     with pytest.raises(L.LudaxError) as ei:
         L.ludax_mixed_plan_create(torch.from_numpy(d).cuda())
     assert ei.value.status == -2
