@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "gomoku", "pente", "yavalath",
-                                                        "line_c5", "mixed", "step_c4"])
+                                                        "line_c5", "wolf_sheep", "draughts", "hasami_shogi", "mixed",
+                                                        "step_c4"])
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
@@ -73,11 +74,13 @@ def workload_cfg(name):
     from paper_2506_22609_b300 import workloads as W
 
     return {"c4": W.C4_64K, "ttt": W.TTT_1K, "othello": W.OTHELLO_256K, "hex11": W.HEX11_64K, "gomoku": W.GOMOKU_64K,
-            "pente": W.PENTE_64K, "yavalath": W.YAVALATH_64K, "line_c5": W.CONNECT5_9X12_64K}[name]
+            "pente": W.PENTE_64K, "yavalath": W.YAVALATH_64K, "line_c5": W.CONNECT5_9X12_64K,
+            "wolf_sheep": W.WOLF_SHEEP_64K, "draughts": W.DRAUGHTS_64K, "hasami_shogi": W.HASAMI_64K}[name]
 
 
 def game_key(cfg):
-    return {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente", 6: "yavalath", 7: "line"}[cfg.game]
+    return {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente", 6: "yavalath", 7: "line",
+            8: "wolf_sheep", 9: "draughts", 10: "hasami_shogi"}[cfg.game]
 
 
 def measured_peaks():
@@ -558,7 +561,8 @@ def main():
                                 "sample": sample}
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {}
-        for name in ("ttt", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5"):
+        for name in ("ttt", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5", "wolf_sheep", "draughts",
+                     "hasami_shogi"):
             c = workload_cfg(name)
             e, lc, ms2, spl = bench_rollout_config(L, W, c, 20, 3, flush_buf)
             m2 = statistics.median(ms2)

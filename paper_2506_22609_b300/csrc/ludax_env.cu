@@ -176,6 +176,7 @@ __global__ void set_state_kernel(EnvDev d, ludax_state_view v) {
         g.passes = 0;
         g.outcome = v.outcome[e];
         g.set_extra((uint8_t)v.passes[e]);
+        g.refresh();
         store_state(g, d, e);
     } else {
         typename G::Mask p1{}, p2{};

@@ -143,6 +143,7 @@ struct WolfSheep {
     }
     __device__ __forceinline__ int extra() const { return 0; }
     __device__ __forceinline__ void set_extra(int) {}
+    __device__ __forceinline__ void refresh() {}
     __device__ __forceinline__ void planes_out(uint64_t* w) const {
         w[0] = p1();
         w[1] = p2();
@@ -180,6 +181,8 @@ struct Draughts {
     using Mask = uint64_t;  // ordinals: at most 48 legal actions (12 pieces x 4 directions)
     uint64_t men_own, kings_own, men_opp, kings_opp;  // relative to the side to move
     int side, ply, passes, outcome, pending;           // pending: cell of the piece that must hop again, -1 if none
+    int ncache;                                        // legal actions of the position (refresh())
+    bool capcache;                                     // whether they are hops
 
     __device__ __forceinline__ void reset() {
         men_own = 0x55AA550000000000ull;  // P1: dark cells of rows 5-7
@@ -188,6 +191,7 @@ struct Draughts {
         side = ply = passes = 0;
         pending = -1;
         outcome = kOngoing;
+        refresh();
     }
     __device__ __forceinline__ uint64_t own() const { return men_own | kings_own; }
     __device__ __forceinline__ uint64_t opp() const { return men_opp | kings_opp; }
@@ -225,15 +229,18 @@ struct Draughts {
         return r != 0;
     }
     __device__ __forceinline__ uint64_t movers() const { return pending >= 0 ? (1ull << pending) : own(); }
-    __device__ __forceinline__ bool capture_mode() const { return pending >= 0 || any_hop(); }
     __device__ __forceinline__ uint64_t dests(int i, bool cap) const { return cap ? hops_of(i) : steps_of(i); }
-    __device__ __forceinline__ int count() const {
-        const bool cap = capture_mode();
+    // the position's legal-action count and capture mode, kept with the state
+    // (the count is also the end test of the previous ply)
+    __device__ __forceinline__ void refresh() {
+        capcache = pending >= 0 || any_hop();
         int n = 0;
-        for (uint64_t m = movers(); m; m &= m - 1) n += __popcll(dests(lowest(m), cap));
-        return n;
+        for (uint64_t m = movers(); m; m &= m - 1) n += __popcll(dests(lowest(m), capcache));
+        ncache = n;
     }
-    __device__ __forceinline__ Mask legal() const { return ordinals64(count()); }
+    __device__ __forceinline__ bool capture_mode() const { return capcache; }
+    __device__ __forceinline__ int count() const { return ncache; }
+    __device__ __forceinline__ Mask legal() const { return ordinals64(ncache); }
     __device__ __forceinline__ void find(int k, int& from, int& to) const {
         const bool cap = capture_mode();
         from = to = -1;
@@ -281,7 +288,8 @@ struct Draughts {
             kings_opp = x;
             side ^= 1;
         }
-        if (count() == 0) outcome = p + 1;
+        refresh();
+        if (ncache == 0) outcome = p + 1;
     }
     __device__ __forceinline__ void pass() {}
     __device__ __forceinline__ int canon_of(int k) const {
@@ -326,7 +334,7 @@ struct Draughts {
         else (king ? kings_opp : men_opp) |= b;
     }
     __device__ __forceinline__ int extra() const { return pending + 1; }
-    __device__ __forceinline__ void set_extra(int x) { pending = x - 1; }
+    __device__ __forceinline__ void set_extra(int x) { pending = x - 1; }  // call refresh() once the position is complete
     __device__ __forceinline__ void planes_out(uint64_t* w) const {  // P1 men, P1 kings, P2 men, P2 kings
         w[0] = side == 0 ? men_own : men_opp;
         w[1] = side == 0 ? kings_own : kings_opp;
@@ -356,6 +364,7 @@ struct Draughts {
         unpack_small(w[4], ply, x, side, outcome);
         pending = x - 1;
         passes = 0;
+        refresh();
     }
 };
 template <>
@@ -560,6 +569,7 @@ struct HasamiShogi {
     }
     __device__ __forceinline__ int extra() const { return 0; }
     __device__ __forceinline__ void set_extra(int) {}
+    __device__ __forceinline__ void refresh() {}
     __device__ __forceinline__ void planes_out(uint64_t* w) const {  // P1 lo, hi, P2 lo, hi
         const B128 a = side == 0 ? own : opp, b = side == 0 ? opp : own;
         w[0] = a.lo;

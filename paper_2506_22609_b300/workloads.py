@@ -79,6 +79,11 @@ def sample_envs(n_total: int, k: int, seed: int) -> np.ndarray:
 # Launch shapes the benchmark times (block_threads, blocks_per_sm,
 # envs_per_thread, hex_nbr_table, compact_every): the fastest candidates of
 # ludax_autotune_env / ludax_autotune on a B300.
+# move games (action = from * cells + to), 200-ply cap
+WOLF_SHEEP_64K = Config("wolf_sheep8x8_65536env_seed9", 8, 8, 8, 65536, 9)
+DRAUGHTS_64K = Config("draughts8x8_65536env_seed10", 9, 8, 8, 65536, 10)
+HASAMI_64K = Config("hasami_shogi9x9_65536env_seed11", 10, 9, 9, 65536, 11)
+
 # the parametric line-game kernel: exactly five in a row, with gravity, on 9 x 12
 CONNECT5_9X12_64K = Config("connect5exact_gravity_9x12_65536env_seed8", 7, 9, 12, 65536, 8, line=5, flags=3)
 
@@ -91,6 +96,9 @@ BENCH_CFGS = {
     PENTE_64K.name: (448, 4, 1, 0, 16),
     YAVALATH_64K.name: (448, 0, 1, 0, 16),
     CONNECT5_9X12_64K.name: (448, 0, 1, 0, 16),
+    WOLF_SHEEP_64K.name: (448, 0, 1, 0, 16),
+    DRAUGHTS_64K.name: (448, 4, 1, 0, 16),
+    HASAMI_64K.name: (448, 4, 1, 0, 8),
 }
 MIXED_BENCH_CFG = (128, 0, 1, 1, 0)
 
