@@ -176,10 +176,10 @@ def _head(node):
 
 # productions of the grammar that exist but that no kernel family implements
 _GRAMMAR_ONLY = {
-    "move", "hop", "slide", "step", "pattern", "promote", "extra_turn", "region", "regions",
-    "prev_move", "hopped", "captured", "promoted", "corner_custodial", "action_was",
-    "can_move_again", "last_move_in", "set_forward", "edgesNoCorners", "corners", "edges",
+    "pattern", "region", "regions", "prev_move", "hopped", "captured", "promoted", "edgesNoCorners", "corners",
+    "edges",
 }
+MOVE_TYPES = ("hop", "slide", "step")
 
 PLAYERS = ("P1", "P2")
 MOVERS = ("mover", "opponent")
@@ -278,15 +278,24 @@ class _Elab:
             self.err(path, f"unexpected form after (rules ...): {_fmt(node[6])}")
         if len(node) == 6:
             self.expect_form(node[5], path + "/rendering", "rendering")
-        return {"name": name, "players": players, "board": board, "pieces": pieces, **rules}
+        return {"name": name, "players": players, "forward": dict(self.forward), "board": board, "pieces": pieces,
+                **rules}
 
     def players(self, node, path):
         self.expect_form(node, path, "players")
         if len(node) not in (2, 3):
             self.err(path, "expected (players n (set_forward ...)?)")
         n = self.integer(node[1], path, 1)
+        self.forward = {"P1": "up", "P2": "down"}  # reading: P1 starts at the bottom
         if len(node) == 3:
-            self.expect_form(node[2], path, "set_forward")
+            fw = node[2]
+            self.expect_form(fw, path + "/set_forward", "set_forward")
+            if len(fw) != 3:
+                self.err(path + "/set_forward", "expected (set_forward (P1 dir) (P2 dir))")
+            for who, a in zip(PLAYERS, fw[1:]):
+                if not (isinstance(a, list) and len(a) == 2 and a[0] == Sym(who)):
+                    self.err(path + "/set_forward", f"expected ({who} up|down|left|right), found {_fmt(a)}")
+                self.forward[who] = self.sym(a[1], path + "/set_forward", ("up", "down", "left", "right"))
         return n
 
     def equipment(self, node, path):
@@ -387,7 +396,7 @@ class _Elab:
     def mechanic(self, node, path):
         h = self.expect_form(node, path, "place", "move")
         if h == "move":
-            self.unsupported(path, node)
+            return self.move(node, path)
         if len(node) < 3:
             self.err(path, "expected (place \"piece\" mover? (destination ...) (result ...)? (effects ...)?)")
         piece = self.piece(node[1], path)
@@ -419,6 +428,43 @@ class _Elab:
             self.err(path, f"unexpected {_fmt(rest[0])}")
         return ("place", piece, mover, dest, result, effects)
 
+    def move(self, node, path):
+        if len(node) not in (2, 3):
+            self.err(path, "expected (move <hop|slide|step or (or ...)> (effects ...)?)")
+        spec = node[1]
+        forms = spec[1:] if _head(spec) == "or" else [spec]
+        if not forms:
+            self.err(path, "(or) needs move types")
+        types = tuple(sorted((self.move_type(f, f"{path}/{_head(f)}") for f in forms), key=repr))
+        effects = ()
+        if len(node) == 3:
+            self.expect_form(node[2], path + "/effects", "effects")
+            if len(node[2]) < 2:
+                self.err(path + "/effects", "(effects ...) is empty")
+            effects = tuple(self.effect(e, f"{path}/effects[{i}]") for i, e in enumerate(node[2][1:]))
+        return ("move", types, effects)
+
+    def move_type(self, node, path):
+        h = self.expect_form(node, path, *MOVE_TYPES)
+        pos, kw = self.split(node, path, 1)
+        if len(pos) != 1:
+            self.err(path, f"({h} \"piece\" ...) takes one piece")
+        piece = self.piece(pos[0], path)
+        dirs = self.directions(kw.get("direction"), path)
+        prio = self.integer(kw["priority"], path) if "priority" in kw else 0
+        if h == "hop":
+            self.no_extra(kw, path, ("direction", "piece", "hop_over", "capture", "priority"))
+            over = self.sym(kw["hop_over"], path, PLAYERS + MOVERS) if "hop_over" in kw else "any"
+            cap = self.boolean(kw["capture"], path) if "capture" in kw else False
+            target = self.piece(kw["piece"], path) if "piece" in kw else None
+            return ("hop", piece, dirs, target, over, cap, prio)
+        if h == "slide":
+            self.no_extra(kw, path, ("direction", "distance", "priority"))
+            dist = self.integer(kw["distance"], path, 1) if "distance" in kw else None
+            return ("slide", piece, dirs, dist, prio)
+        self.no_extra(kw, path, ("direction", "priority"))
+        return ("step", piece, dirs, prio)
+
     # ---- effects
     def effect(self, node, path):
         h = self.expect_form(node, path)
@@ -444,6 +490,20 @@ class _Elab:
             if len(node) != 3:
                 self.err(path, f"expected ({h} mover|opponent <function>)")
             return (h, self.sym(node[1], path, MOVERS), self.function(node[2], path))
+        if h == "promote":
+            pos, kw = self.split(node, path, 3)
+            self.no_extra(kw, path, ("mover",))
+            if len(pos) != 3:
+                self.err(path, "expected (promote \"from\" \"to\" <mask> mover: ...)")
+            who = self.sym(kw["mover"], path, MOVERS + ("both",)) if "mover" in kw else "mover"
+            return ("promote", self.piece(pos[0], path), self.piece(pos[1], path), self.mask(pos[2], path), who)
+        if h == "extra_turn":
+            pos, kw = self.split(node, path, 1)
+            self.no_extra(kw, path, ("same_piece",))
+            if len(pos) != 1:
+                self.err(path, "expected (extra_turn mover|opponent same_piece: ...)")
+            same = self.boolean(kw["same_piece"], path) if "same_piece" in kw else False
+            return ("extra_turn", self.sym(pos[0], path, MOVERS), same)
         if h in _GRAMMAR_ONLY:
             self.unsupported(path, node)
         self.err(path, f"unknown effect {_fmt(node)}")
@@ -494,6 +554,13 @@ class _Elab:
             who = self.sym(kw["mover"], path, MOVERS + ("both",)) if "mover" in kw else "mover"
             orient = self.sym(kw["orientation"], path, ORIENTATIONS) if "orientation" in kw else "any"
             return ("custodial", piece, n, who, orient)
+        if h == "corner_custodial":
+            pos, kw = self.split(node, path, 1)
+            self.no_extra(kw, path, ("mover",))
+            if len(pos) != 1:
+                self.err(path, "expected (corner_custodial \"piece\" mover: ...)")
+            who = self.sym(kw["mover"], path, MOVERS + ("both",)) if "mover" in kw else "mover"
+            return ("corner_custodial", self.piece(pos[0], path), who)
         if h == "line":
             self.err(path, f"(line ...) as a mask of cells is not implemented by any kernel family: {_fmt(node)}")
         if h in _GRAMMAR_ONLY:
@@ -524,9 +591,8 @@ class _Elab:
             orient = self.sym(kw["orientation"], path, ORIENTATIONS) if "orientation" in kw else "any"
             exact = self.boolean(kw["exact"], path) if "exact" in kw else False
             who = self.sym(kw["player"], path, PLAYERS + MOVERS) if "player" in kw else "mover"
-            if "exclude" in kw:
-                self.err(path, "line with exclude: is not implemented by any kernel family")
-            return ("line", piece, n, orient, exact, who)
+            excl = self.multi_mask(kw["exclude"], path + "/exclude") if "exclude" in kw else ()
+            return ("line", piece, n, orient, exact, who, excl)
         if h == "connected":
             pos, kw = self.split(node, path, 2)
             self.no_extra(kw, path, ("mover", "direction"))
@@ -592,6 +658,18 @@ class _Elab:
             if len(node) != 2:
                 self.err(path, "expected (mover_is P1|P2)")
             return ("mover_is", self.sym(node[1], path, PLAYERS))
+        if h == "last_move_in":
+            if len(node) != 2:
+                self.err(path, "expected (last_move_in <mask>)")
+            return ("last_move_in", self.mask(node[1], path + "/last_move_in"))
+        if h == "action_was":
+            if len(node) != 3:
+                self.err(path, "expected (action_was mover|opponent hop|slide|step)")
+            return ("action_was", self.sym(node[1], path, MOVERS), self.sym(node[2], path, MOVE_TYPES))
+        if h == "can_move_again":
+            if len(node) != 2:
+                self.err(path, "expected (can_move_again hop|slide|step)")
+            return ("can_move_again", self.sym(node[1], path, MOVE_TYPES))
         if h == "exists":
             if len(node) != 2:
                 self.err(path, "expected (exists <mask>)")
@@ -677,8 +755,8 @@ FULL_DRAW = (("full_board",), ("draw",))
 def _line_pred(p):
     """(n, exact) if p is 'the mover has a line of n, any orientation'."""
     if p[0] == "ge" and p[2] == ("const", 1) and p[1][0] == "line":
-        _, _piece, n, orient, exact, who = p[1]
-        if orient == "any" and who == "mover":
+        _, _piece, n, orient, exact, who, excl = p[1]
+        if orient == "any" and who == "mover" and not excl:
             return n, exact
     return None
 
@@ -835,7 +913,7 @@ def _lower_pente(g):
         _fail("rules/play/phase[1]", "Pente's second phase alternates from P2, places on (empty) cells and "
               "captures (custodial \"piece\" 2) with increment_score: true")
     end = g["end"]
-    want = [(("ge", ("line", m2[1], 5, "any", False, "mover"), ("const", 1)), ("win", "mover")),
+    want = [(("ge", ("line", m2[1], 5, "any", False, "mover", ()), ("const", 1)), ("win", "mover")),
             (("ge", ("score", "mover"), ("const", 10)), ("win", "mover")), FULL_DRAW]
     if len(end) != 3 or end[2] != FULL_DRAW or sorted(end[:2], key=repr) != sorted(want[:2], key=repr):
         _fail("rules/end", "the Pente kernel implements: a line of five or a score of 10 wins, then a full "
@@ -843,10 +921,125 @@ def _lower_pente(g):
     return _spec(g["name"], GAME_PENTE, 19, 19)
 
 
+FWD_DIAGONALS = (("forward_left", "forward_right"),)
+WIN = ("win", "mover")
+NO_MOVES_WIN = (("no_legal_actions",), WIN)
+
+
+def _dark_cells(rows):
+    return tuple(r * 8 + c for r in rows for c in range(8) if (r + c) % 2 == 1)
+
+
+def _forward_ok(g, path):
+    if g["forward"] != {"P1": "up", "P2": "down"}:
+        _fail(path, "the move-game kernels take P1 moving up and P2 down: (set_forward (P1 up) (P2 down))")
+
+
+def _single_move_phase(g, path="rules/play"):
+    play = g["play"]
+    if len(play) != 1:
+        _fail(path, "the move-game kernels take a single (repeat (P1 P2) (move ...)) phase")
+    kind, order, mech, force_pass = play[0]
+    if kind != "repeat" or order != ("P1", "P2"):
+        _fail(path, "players must alternate with P1 first: (repeat (P1 P2) ...)")
+    if mech[0] != "move" or force_pass:
+        _fail(path, "the move-game kernels take one (move ...) mechanic and no pass")
+    return mech[1], mech[2]   # move types, effects
+
+
+def _lower_wolf_sheep(g):
+    sheep = [k for k, v in g["pieces"].items() if v == "P1"]
+    wolf = [k for k, v in g["pieces"].items() if v == "P2"]
+    if len(sheep) != 1 or len(wolf) != 1 or len(g["pieces"]) != 2:
+        _fail("equipment/pieces", "Wolf and Sheep has one piece type of P1 (sheep) and one of P2 (wolf)")
+    a, b = sheep[0], wolf[0]
+    if g["start"] != tuple(sorted([(a, "P1", (56, 58, 60, 62)), (b, "P2", (3,))])):
+        _fail("rules/start", "the Wolf and Sheep kernel starts with sheep on 56 58 60 62 and the wolf on 3")
+    types, effects = _single_move_phase(g)
+    fwd = [("step", a, d, 0) for d in (("forward_left", "forward_right"), ("up_left", "up_right"))]
+    ok = any(types == tuple(sorted([f, ("step", b, ("diagonal",), 0)], key=repr)) for f in fwd)
+    if not ok or effects:
+        _fail("rules/play", "Wolf and Sheep: sheep step diagonally forward, the wolf diagonally, no effects")
+    bottom = (("and", tuple(sorted([("mover_is", "P2"), ("last_move_in", ("edge", "bottom"))], key=repr))), WIN)
+    if tuple(g["end"]) not in ((bottom, NO_MOVES_WIN), (NO_MOVES_WIN, bottom)):
+        _fail("rules/end", "Wolf and Sheep ends when the wolf reaches the bottom edge or a side cannot move")
+    return _spec(g["name"], GAME_WOLF_SHEEP, 8, 8)
+
+
+def _lower_draughts(g):
+    if len(g["pieces"]) != 2 or set(g["pieces"].values()) != {"both"}:
+        _fail("equipment/pieces", "Draughts has two piece types of both players (a man and a king)")
+    types, effects = _single_move_phase(g)
+    men = [t[1] for t in types if t[0] == "step" and t[2] == ("forward_left", "forward_right")]
+    if len(men) != 1:
+        _fail("rules/play", "Draughts: men step diagonally forward (forward_left forward_right)")
+    m = men[0]
+    k = [x for x in g["pieces"] if x != m][0]
+    fwd, diag = ("forward_left", "forward_right"), ("diagonal",)
+    want = tuple(sorted([("hop", m, fwd, None, "opponent", True, 0), ("hop", k, diag, None, "opponent", True, 0),
+                         ("step", m, fwd, 1), ("step", k, diag, 1)], key=repr))
+    if types != want:
+        _fail("rules/play", "Draughts: hops over an opponent (capture, priority 0) before steps (priority 1), men "
+              "forward, kings diagonally")
+    if g["start"] != tuple(sorted([(m, "P1", _dark_cells((5, 6, 7))), (m, "P2", _dark_cells((0, 1, 2)))])):
+        _fail("rules/start", "the Draughts kernel starts with men on the dark cells of rows 5-7 (P1) and 0-2 (P2)")
+    again = ("and", tuple(sorted([("action_was", "mover", "hop"), ("can_move_again", "hop")], key=repr)))
+    if effects != (("promote", m, k, ("edge", "forward"), "mover"), ("if", again, ("extra_turn", "mover", True))):
+        _fail("rules/play/effects", "Draughts: promote men on the forward edge, then an extra turn for the same "
+              "piece after a hop that can be continued")
+    if tuple(g["end"]) != (NO_MOVES_WIN,):
+        _fail("rules/end", "Draughts ends when the player to move has no legal action")
+    return _spec(g["name"], GAME_DRAUGHTS, 8, 8)
+
+
+def _lower_hasami(g):
+    if len(g["pieces"]) != 1 or set(g["pieces"].values()) != {"both"}:
+        _fail("equipment/pieces", "Dai Hasami Shogi uses one piece type of both players")
+    p = next(iter(g["pieces"]))
+    if g["start"] != tuple(sorted([(p, "P1", tuple(range(63, 81))), (p, "P2", tuple(range(0, 18)))])):
+        _fail("rules/start", "the Dai Hasami Shogi kernel starts with P1 on rows 7-8 and P2 on rows 0-1")
+    types, effects = _single_move_phase(g)
+    orth = ("orthogonal",)
+    slide = ("slide", p, orth, None, 0)
+    hops = [tuple(sorted([slide, ("hop", p, orth, None, "any", False, 0)], key=repr)),
+            tuple(sorted([slide, ("hop", p, orth, None, "mover", False, 0), ("hop", p, orth, None, "opponent", False, 0)],
+                         key=repr))]
+    if types not in hops:
+        _fail("rules/play", "Dai Hasami Shogi: orthogonal slides and hops over one piece of either side (no capture)")
+    caps = {("capture", ("custodial", p, "any", "mover", "orthogonal"), "mover", False),
+            ("capture", ("corner_custodial", p, "mover"), "mover", False)}
+    if set(effects) != caps or len(effects) != 2:
+        _fail("rules/play/effects", "Dai Hasami Shogi captures custodially (any length, orthogonal) and in corners")
+
+    def five(who, rows):
+        line = ("ge", ("line", p, 5, "orthogonal", False, "mover", tuple(sorted((("row", r) for r in rows), key=repr))),
+                ("const", 1))
+        return (("and", tuple(sorted([("mover_is", who), line], key=repr))), WIN)
+
+    r1, r2 = five("P1", (7, 8)), five("P2", (0, 1))
+    if tuple(g["end"]) not in ((r1, r2, NO_MOVES_WIN), (r2, r1, NO_MOVES_WIN)):
+        _fail("rules/end", "Dai Hasami Shogi: five in a row (orthogonal) outside the mover's home rows wins, then a "
+              "side without a move loses")
+    return _spec(g["name"], GAME_HASAMI_SHOGI, 9, 9)
+
+
+def _lower_move_game(g):
+    _forward_ok(g, "players")
+    shape = g["board"]
+    if shape == ("square", 9):
+        return _lower_hasami(g)
+    if shape != ("square", 8):
+        _fail("equipment/board", "the move-game kernels take (square 8) (Wolf and Sheep, Draughts) or (square 9)")
+    owners = set(g["pieces"].values())
+    return _lower_draughts(g) if owners == {"both"} else _lower_wolf_sheep(g)
+
+
 def lower(g: dict, specialize: bool = True) -> GameSpec:
     """Match a normalised game against the kernel families."""
     if g["players"] != 2:
         _fail("players", "every kernel family is a two-player game")
+    if any(ph[2][0] == "move" for ph in g["play"]):
+        return _lower_move_game(g)
     owners = set(g["pieces"].values())
     if len(g["pieces"]) != 1 or owners != {"both"}:
         _fail("equipment/pieces", "every kernel family uses one piece type shared by both players (\"name\" both)")

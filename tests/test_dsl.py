@@ -43,6 +43,9 @@ EXPECTED = {
     "misere_tic_tac_toe": LUDAX_DESC_LINE(3, 3, 3, dsl.LINE_MISERE),
     "connect_five_9x12": LUDAX_DESC_LINE(9, 12, 5, dsl.LINE_EXACT | dsl.LINE_GRAVITY),
     "tic_tac_four_5x5": LUDAX_DESC_LINE(5, 5, 4, 0),
+    "wolf_and_sheep": W.desc(8, 8, 8),
+    "english_draughts": W.desc(9, 8, 8),
+    "dai_hasami_shogi": W.desc(10, 9, 9),
 }
 
 
@@ -78,7 +81,9 @@ def test_specialised_and_generic_descriptors_play_identically(name, seed):
 def test_library_runs_through_the_oracle_mixed_batch():
     d = np.array([EXPECTED[k] for k in sorted(EXPECTED)] * 50, np.int32)
     o, p = G.rollout_mixed(d, 17)
-    assert ((o >= 0) & (o <= 2)).all() and (p > 0).all()
+    move = np.isin(d & 0xFF, (8, 9, 10))
+    assert ((o >= 0) & (o <= 2)).all() or ((o == 3) <= move).all()   # only move games stop at their 200-ply cap
+    assert ((o >= 0) & (o <= 3)).all() and (p > 0).all() and (p[o == 3] == 200).all()
 
 
 # ----------------------------------------------------------- normalisation --
@@ -161,7 +166,7 @@ def test_mnk_family(rows, cols, L, exact, misere):
 # ------------------------------------------------------------- rejections --
 @pytest.mark.parametrize("text,path,words", [
     (mk(dest='(empty)').replace('(place "s" (destination (empty)))', '(move (step "s" direction: up))'),
-     "game/rules/play/phase[0]/move", "no kernel family implements"),
+     "equipment/board", "move-game kernels"),
     (mk(end='(if (pattern "s" (square 2)) (mover win)) (if (full_board) (draw))'),
      "game/rules/end/if[0]", "no kernel family implements"),
     (mk(end='(if (line "t" 3) (mover win)) (if (full_board) (draw))'), "game/rules/end/if[0]", "not declared"),
@@ -176,8 +181,8 @@ def test_mnk_family(rows, cols, L, exact, misere):
     (mk(dest="(frobnicate)"), "game/rules/play/phase[0]/place/destination", "unknown mask"),
     (mk().replace("(players 2)", "(players 3)"), "players", "two-player"),
     (mk().replace("(repeat (P1 P2)", "(repeat (P2 P1)"), "rules/play", "P1 first"),
-    (mk(end='(if (line "s" 3 exclude: (edge top)) (mover win)) (if (full_board) (draw))'), "game/rules/end/if[0]",
-     "exclude"),
+    (mk(end='(if (line "s" 3 exclude: (edge top)) (mover win)) (if (full_board) (draw))'), "rules/end/if[0]",
+     "every orientation"),
     (mk(end='(if (line "s" 3) (mover win) extra) (if (full_board) (draw))'), "game/rules/end/if[0]", "expected (if"),
     (LIB["reversi"].replace("(28 35)", "(27 35)"), "rules/start", "28 and 35"),
     (LIB["reversi"].replace("(force_pass)", ""), "rules/play", "force_pass"),
@@ -191,3 +196,52 @@ def test_rejections_name_the_node(text, path, words):
     with pytest.raises(dsl.DslError) as ei:
         dsl.compile_game(text)
     assert ei.value.path == path and words in str(ei.value), str(ei.value)
+
+
+# ------------------------------------------------------------ move games --
+def test_move_game_equivalent_forms():
+    ws = LIB["wolf_and_sheep"]
+    # the sheep's forward diagonals written absolutely; the end rules in the other order
+    alt = ws.replace("(step \"sheep\" direction: (forward_left forward_right))",
+                     "(step \"sheep\" direction: (up_right up_left))")
+    alt = alt.replace("""            (if (and (mover_is P2) (last_move_in (edge bottom))) (mover win))
+            (if (no_legal_actions) (mover win))""", """            (if (no_legal_actions) (mover win))
+            (if (and (last_move_in (edge bottom)) (mover_is P2)) (mover win))""")
+    assert alt != ws and dsl.descriptor(alt) == W.desc(8, 8, 8)
+    # one hop over any piece is the same as hops over the mover's and the opponent's
+    hs = LIB["dai_hasami_shogi"].replace("""                        (hop "piece" direction: orthogonal hop_over: mover)
+                        (hop "piece" direction: orthogonal hop_over: opponent))""",
+                                         """                        (hop "piece" direction: orthogonal))""")
+    assert hs != LIB["dai_hasami_shogi"] and dsl.descriptor(hs) == W.desc(10, 9, 9)
+    # no set_forward: P1 moves up by default
+    dr = LIB["english_draughts"].replace("(players 2 (set_forward (P1 up) (P2 down)))", "(players 2)")
+    assert dsl.descriptor(dr) == W.desc(9, 8, 8)
+
+
+@pytest.mark.parametrize("name,old,new,path,words", [
+    ("english_draughts", '(promote "man" "king" (edge forward))', '(promote "man" "king" (edge backward))',
+     "rules/play/effects", "promote"),
+    ("english_draughts", "priority: 1", "priority: 0", "rules/play", "priority"),
+    ("english_draughts", "(set_forward (P1 up) (P2 down))", "(set_forward (P1 down) (P2 up))", "players",
+     "set_forward"),
+    ("wolf_and_sheep", '(place "wolf" P2 (3))', '(place "wolf" P2 (5))', "rules/start", "wolf on 3"),
+    ("dai_hasami_shogi", "hop_over: mover)", "hop_over: mover capture: true)", "rules/play", "no capture"),
+    ("dai_hasami_shogi", "((row 7) (row 8))", "((row 6) (row 7))", "rules/end", "home rows"),
+    ("dai_hasami_shogi", '(capture (corner_custodial "piece"))', '(capture (custodial "piece" 1))',
+     "rules/play/effects", "corners"),
+])
+def test_move_game_rejections(name, old, new, path, words):
+    text = LIB[name]
+    assert old in text
+    with pytest.raises(dsl.DslError) as ei:
+        dsl.compile_game(text.replace(old, new, 1))
+    assert ei.value.path == path and words in str(ei.value), str(ei.value)
+
+
+def test_move_mechanics_parse_into_the_normal_form():
+    g = dsl.elaborate(dsl.read(LIB["english_draughts"]))
+    kind, order, mech, force_pass = g["play"][0]
+    assert mech[0] == "move" and len(mech[1]) == 4 and not force_pass
+    assert ("hop", "man", ("forward_left", "forward_right"), None, "opponent", True, 0) in mech[1]
+    assert mech[2][0] == ("promote", "man", "king", ("edge", "forward"), "mover")
+    assert g["forward"] == {"P1": "up", "P2": "down"}
