@@ -31,7 +31,9 @@ namespace {
 constexpr int TM = 128, TN = 256, TK = 64, TSTAGES = 4, UMMA_THREADS = 192;
 constexpr int A_TILE = TM * TK * 2, B_TILE = TN * TK * 2, STAGE = A_TILE + B_TILE;
 constexpr int TMEM_COLS = 2 * TN;  // two accumulators
-constexpr size_t UMMA_SMEM = (size_t)TSTAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
+constexpr int MAX_N = 4096;        // the bias row is staged in shared memory
+constexpr size_t UMMA_SMEM =
+    (size_t)TSTAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */ + sizeof(float) * MAX_N /* bias */;
 constexpr long long kWaitLimit = 2000000000ll;  // clock cycles (~1 s at 2 GHz)
 
 static __device__ int g_umma_error;  // nonzero after a wait expired
@@ -98,7 +100,8 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+// 32 columns of this warp's 32 TMEM lanes into r (asynchronous: tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
@@ -107,7 +110,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+// waits for the outstanding TMEM loads; r (the registers they fill) are
+// read-write operands, so no use of them is moved before the wait
+__device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
@@ -120,8 +134,10 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     uint64_t* acc_full = empty + TSTAGES;  // [2] MMA -> epilogue
     uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    float* sbias = reinterpret_cast<float*>(smem + TSTAGES * STAGE + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ktiles = K / TK, ntn = N / TN, ntiles = (M / TM) * ntn;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sbias[i] = bias[i];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TSTAGES; ++s) {
@@ -197,22 +213,29 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             const int row = (t / ntn) * TM + q * 32 + lane, n0 = (t % ntn) * TN;
             __nv_bfloat16* orow = out + (size_t)row * ldo + n0;
             const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
+            // two register sets: the load of chunk c + 1 is in flight while chunk c is converted
+            uint32_t r[2][32];
+            tmem_ld32_async(base, r[0]);
+            tmem_wait_ld(r[0]);
+#pragma unroll
             for (int c = 0; c < TN / 32; ++c) {
-                uint32_t r[32];
-                tmem_ld32(base + (uint32_t)(c * 32), r);
+                if (c + 1 < TN / 32) tmem_ld32_async(base + (uint32_t)((c + 1) * 32), r[(c + 1) & 1]);
+                const uint32_t* x = r[c & 1];
+                const float4* bb = reinterpret_cast<const float4*>(sbias + n0 + c * 32);
                 __align__(16) __nv_bfloat162 v[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c * 32 + 2 * j;
-                    float x0 = fmaxf(__uint_as_float(r[2 * j]) + __ldg(bias + col), 0.f);
-                    float x1 = fmaxf(__uint_as_float(r[2 * j + 1]) + __ldg(bias + col + 1), 0.f);
-                    v[j] = __floats2bfloat162_rn(x0, x1);
+                for (int j = 0; j < 8; ++j) {
+                    const float4 b4 = bb[j];
+                    v[2 * j] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j]) + b4.x, 0.f),
+                                                     fmaxf(__uint_as_float(x[4 * j + 1]) + b4.y, 0.f));
+                    v[2 * j + 1] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j + 2]) + b4.z, 0.f),
+                                                         fmaxf(__uint_as_float(x[4 * j + 3]) + b4.w, 0.f));
                 }
                 uint4* dst = reinterpret_cast<uint4*>(orow + c * 32);
                 const uint4* src = reinterpret_cast<const uint4*>(v);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) dst[k] = src[k];
+                if (c + 1 < TN / 32) tmem_wait_ld(r[(c + 1) & 1]);
             }
             tc_fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
@@ -260,7 +283,9 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows
 
 namespace ludax {
 
-bool umma_dense_supported(int M, int N, int K) { return M > 0 && N > 0 && K > 0 && M % TM == 0 && N % TN == 0 && K % TK == 0; }
+bool umma_dense_supported(int M, int N, int K) {
+    return M > 0 && N > 0 && K > 0 && M % TM == 0 && N % TN == 0 && K % TK == 0 && N <= MAX_N;
+}
 
 int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, int M, int N, int K, int ldo,
                     cudaStream_t s) {
