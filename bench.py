@@ -64,6 +64,8 @@ def parse():
                                                         "line_c5", "wolf_sheep", "draughts", "hasami_shogi", "mixed",
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
+    p.add_argument("--only", choices=["dense_layer", "gavel_library"], default=None,
+                   help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
     p.add_argument("--cpu-seconds", type=float, default=8.0, help="target wall time of the CPU-baseline sample")
@@ -479,6 +481,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     peaks, peak_kind = measured_peaks()
     flush_buf = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB
+    if args.only:
+        res = bench_dense(L, peaks, flush_buf) if args.only == "dense_layer" else bench_gavel()
+        if rank == 0:
+            print(json.dumps({args.only: res}), flush=True)
+        return 0
 
     cfg = workload_cfg(args.workload) if args.workload not in ("mixed", "step_c4") else None
     with ClockSampler(local) as clk:

@@ -12,9 +12,14 @@
 //               accumulators in TMEM, frees ring stages with tcgen05.commit
 //               and signals the finished accumulator;
 //   warps 2-5 : epilogue -- drain the finished accumulator with tcgen05.ld
-//               (each warp its quarter of the 128 TMEM lanes = rows), add the
-//               bias, ReLU, round to BF16, store; then hand the accumulator
-//               back, so the epilogue of tile i overlaps the MMAs of tile i+1.
+//               (each warp its quarter of the 128 TMEM lanes = rows; the load
+//               of the next 32 columns is in flight while the current ones
+//               are converted), add the bias (staged in shared memory),
+//               ReLU, round to BF16 into a 32 x 64 shared-memory box in the
+//               128-byte-swizzle layout (conflict-free), and store each box
+//               with one bulk tensor store (cp.async.bulk.tensor); then hand
+//               the accumulator back, so the epilogue of tile i overlaps the
+//               MMAs of tile i+1.
 // Every mbarrier wait is bounded (about a second of clock); on expiry the
 // kernel records an error in a device word and stops issuing work, so a
 // fault in the pipeline surfaces as a status instead of a hang.
@@ -31,9 +36,12 @@ namespace {
 constexpr int TM = 128, TN = 256, TK = 64, TSTAGES = 4, UMMA_THREADS = 192;
 constexpr int A_TILE = TM * TK * 2, B_TILE = TN * TK * 2, STAGE = A_TILE + B_TILE;
 constexpr int TMEM_COLS = 2 * TN;  // two accumulators
-constexpr int MAX_N = 4096;        // the bias row is staged in shared memory
-constexpr size_t UMMA_SMEM =
-    (size_t)TSTAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */ + sizeof(float) * MAX_N /* bias */;
+constexpr int MAX_N = 1024;        // the bias row is staged in shared memory
+constexpr int OUT_BOX = 64;        // output columns per TMA store box (128 bytes of BF16)
+constexpr int STAGING = 32 * OUT_BOX * 2;  // one 32-row box per epilogue warp, 128-byte swizzle
+constexpr int RING = TSTAGES * STAGE;
+constexpr size_t UMMA_SMEM = 1024 /* alignment */ + (size_t)RING + 4 * STAGING + 256 /* barriers */ +
+                             sizeof(float) * MAX_N /* bias */;
 constexpr long long kWaitLimit = 2000000000ll;  // clock cycles (~1 s at 2 GHz)
 
 static __device__ int g_umma_error;  // nonzero after a wait expired
@@ -70,6 +78,18 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1)
         : "memory");
 }
+
+// bulk tensor store of a shared-memory box to global memory (bulk async-group)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(map),
+                 "r"(saddr(src)), "r"(c0), "r"(c1)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+// the shared-memory sources of this thread's bulk stores may be overwritten
+__device__ __forceinline__ void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
@@ -125,16 +145,18 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
 }
 
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
-    umma_dense_relu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-                           int N, int K, const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, int ldo) {
+    umma_dense_relu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                           const __grid_constant__ CUtensorMap tmOut, int M, int N, int K,
+                           const float* __restrict__ bias) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + TSTAGES * STAGE);
+    uint8_t* staging = smem + RING;  // 1024-byte aligned: the 128-byte swizzle pattern repeats every 1024 bytes
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING + 4 * STAGING);
     uint64_t* empty = full + TSTAGES;
     uint64_t* acc_full = empty + TSTAGES;  // [2] MMA -> epilogue
     uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
-    float* sbias = reinterpret_cast<float*>(smem + TSTAGES * STAGE + 256);
+    float* sbias = reinterpret_cast<float*>(smem + RING + 4 * STAGING + 256);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ktiles = K / TK, ntn = N / TN, ntiles = (M / TM) * ntn;
     for (int i = threadIdx.x; i < N; i += blockDim.x) sbias[i] = bias[i];
@@ -210,8 +232,9 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
             if (!ok) break;
             tc_fence_after();
-            const int row = (t / ntn) * TM + q * 32 + lane, n0 = (t % ntn) * TN;
-            __nv_bfloat16* orow = out + (size_t)row * ldo + n0;
+            const int row0 = (t / ntn) * TM + q * 32, n0 = (t % ntn) * TN;
+            uint8_t* box = staging + q * STAGING;
+            uint8_t* myrow = box + lane * (OUT_BOX * 2);
             const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
             // two register sets: the load of chunk c + 1 is in flight while chunk c is converted
             uint32_t r[2][32];
@@ -231,10 +254,22 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                     v[2 * j + 1] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j + 2]) + b4.z, 0.f),
                                                          fmaxf(__uint_as_float(x[4 * j + 3]) + b4.w, 0.f));
                 }
-                uint4* dst = reinterpret_cast<uint4*>(orow + c * 32);
+                const int half = c & 1;  // which 64-byte half of the box row
+                if (half == 0) {         // the box's previous store must have read the staging buffer
+                    if (lane == 0) tma_store_wait_read();
+                    __syncwarp();
+                }
                 const uint4* src = reinterpret_cast<const uint4*>(v);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) dst[k] = src[k];
+                for (int k = 0; k < 4; ++k) {  // 16-byte chunk 4*half+k of the row, swizzled with the row
+                    const int chunk = (4 * half + k) ^ (lane & 7);
+                    *reinterpret_cast<uint4*>(myrow + chunk * 16) = src[k];
+                }
+                if (half == 1) {  // box complete: hand it to the TMA engine
+                    fence_async_shared();
+                    __syncwarp();
+                    if (lane == 0) tma_store_2d(&tmOut, box, n0 + (c - 1) * 32, row0);
+                }
                 if (c + 1 < TN / 32) tmem_wait_ld(r[(c + 1) & 1]);
             }
             tc_fence_before();
@@ -242,6 +277,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
         }
     }
     if (!ok) atomicOr(&g_umma_error, 1);
+    if (warp >= 2 && lane == 0) tma_store_wait_all();  // the epilogue's bulk stores have landed
     tc_fence_before();
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
@@ -265,14 +301,14 @@ EncodeTiled encode_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor map over a row-major [rows][cols] matrix with a box of
-// box_rows x 64 columns and 128-byte swizzle.
-bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows) {
+// 2-D BF16 tensor map over a row-major [rows][cols] matrix (row pitch ld
+// elements) with a box of box_rows x 64 columns and 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows, int ld) {
     EncodeTiled fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};  // 64 BF16 = the 128-byte swizzle span
     cuuint32_t estr[2] = {1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -291,8 +327,9 @@ int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, 
                     cudaStream_t s) {
     if (!umma_dense_supported(M, N, K) || ldo % 8 || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)out % 16))
         return LUDAX_ERR_SIZE;
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, M, K, TM) || !make_map(&mb, B, N, K, TN)) return LUDAX_ERR_CUDA;
+    CUtensorMap ma, mb, mo;
+    if (!make_map(&ma, A, M, K, TM, K) || !make_map(&mb, B, N, K, TN, K) || !make_map(&mo, out, M, N, 32, ldo))
+        return LUDAX_ERR_CUDA;
     static bool attr = false;
     if (!attr) {
         if (cudaFuncSetAttribute(umma_dense_relu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UMMA_SMEM) !=
@@ -309,8 +346,7 @@ int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, 
     }
     const int ntiles = (M / TM) * (N / TN);
     const int grid = ntiles < sms ? ntiles : sms;
-    umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, M, N, K, bias,
-                                                                 reinterpret_cast<__nv_bfloat16*>(out), ldo);
+    umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
