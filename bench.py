@@ -532,8 +532,10 @@ def main():
                     "median_launch_ms": round(med, 5)}
     if ops_per_launch:
         achieved = ops_per_launch / (med / 1e3) / 1e12
+        alu_pipe = peak_ops / 2  # logic/shift/add run on the ALU pipe: 64 lanes per clock per SM
         roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_ops / 1e12, 3),
                     "unit": "Tops/s (32-bit integer)", "frac": round(achieved / (peak_ops / 1e12), 4),
+                    "alu_pipe_peak": round(alu_pipe / 1e12, 3), "alu_pipe_frac": round(achieved / (alu_pipe / 1e12), 4),
                     "traffic": NCU_TRAFFIC_BYTES.get(wl_name),
                     "peak_source": f"{sms} SMs x 128 int32 lanes x {max_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
                     "alg_ops_per_step": ALG_OPS_PER_STEP[game_key(cfg)], "median_launch_ms": round(med, 5)}

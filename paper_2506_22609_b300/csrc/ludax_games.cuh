@@ -45,6 +45,9 @@
 #pragma once
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace ludax {
 
 constexpr int kOngoing = -1, kDraw = 0, kWin1 = 1, kWin2 = 2, kCapped = 3;
@@ -230,7 +233,7 @@ struct C4 {
     __device__ __forceinline__ void place(int b) {
         own |= 1ull << b;
         if (line4(own)) outcome = side + 1;
-        else if ((own | opp) == kValid) outcome = kDraw;
+        else if (ply + 1 == kCells) outcome = kDraw;  // discs are never removed: full at ply 42
         ++ply;
         uint64_t t = own; own = opp; opp = t;
         side ^= 1;
@@ -917,6 +920,28 @@ __device__ __forceinline__ int cells_of(const G& g) {
     else return G::kCells;
 }
 
+// Games that keep derived data with their state (C4's next legal cells,
+// Draughts' legal count) rebuild it with refresh() after a position is
+// loaded; the others have nothing to rebuild.
+template <class G, class = void>
+struct HasRefresh : std::false_type {};
+template <class G>
+struct HasRefresh<G, std::void_t<decltype(std::declval<G&>().refresh())>> : std::true_type {};
+template <class G>
+__device__ __forceinline__ void refresh_of(G& g) {
+    if constexpr (HasRefresh<G>::value) g.refresh();
+}
+// number of legal actions in the mask m = g.legal()
+template <class G, class = void>
+struct HasLegalCount : std::false_type {};
+template <class G>
+struct HasLegalCount<G, std::void_t<decltype(std::declval<const G&>().legal_count())>> : std::true_type {};
+template <class G>
+__device__ __forceinline__ uint32_t legal_count_of(const G& g, const typename G::Mask& m) {
+    if constexpr (HasLegalCount<G>::value) return g.legal_count();
+    else return popc(m);
+}
+
 // ---------------------------------------------------------- one random ply --
 // Uniform-random policy: n legal cells, k-th in ascending cell id with
 // k = umulhi(top32(sm(key ^ ply)), n); a forced pass draws nothing.
@@ -926,7 +951,7 @@ __device__ __forceinline__ void random_ply(G& g, uint64_t key) {
     if (G::kHasPass && !any(m)) {
         g.pass();
     } else {
-        uint32_t k = draw_index(key, (uint32_t)g.ply, popc(m));
+        uint32_t k = draw_index(key, (uint32_t)g.ply, legal_count_of(g, m));
         g.place(select_bit(m, k));
     }
     if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
@@ -946,7 +971,7 @@ __device__ __forceinline__ void random_ply_pre(G& g, uint64_t key, uint32_t& rhi
     if (G::kHasPass && !any(m)) {
         g.pass();
     } else {
-        g.place(select_bit(m, __umulhi(rhi, popc(m))));
+        g.place(select_bit(m, __umulhi(rhi, legal_count_of(g, m))));
     }
     if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
     rhi = rnext;

@@ -85,7 +85,6 @@ __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
         for (int k = 0; k < G::kPlanes; ++k) w[k] = d.planes[(int64_t)k * d.n + e];
         g.planes_in(w);
         g.set_extra((int)((meta >> 24) & 0xFF));
-        g.refresh();
     } else if constexpr (WideW<G>::value != 0) {
         constexpr int W = WideW<G>::value;
         typename G::Mask p1, p2;
@@ -120,6 +119,7 @@ __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
         g.oppA = p1 ? a2 : a1;
         g.oppB = p1 ? b2 : b1;
     }
+    refresh_of(g);
 }
 
 template <class G>
