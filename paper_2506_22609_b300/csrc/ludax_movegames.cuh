@@ -232,11 +232,26 @@ struct Draughts {
     __device__ __forceinline__ uint64_t dests(int i, bool cap) const { return cap ? hops_of(i) : steps_of(i); }
     // the position's legal-action count and capture mode, kept with the state
     // (the count is also the end test of the previous ply)
+    // For one direction the destinations of different pieces are distinct
+    // (each destination has one source cell), so the count is a popcount per
+    // direction over all movers at once.
     __device__ __forceinline__ void refresh() {
-        capcache = pending >= 0 || any_hop();
+        const uint64_t e = empty(), o = opp();
+        uint64_t hop[4], step[4];
+        bool cap = false;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            const uint64_t fwd = (side == 0) == (d < 2);
+            const uint64_t mv = pending >= 0 ? (1ull << pending) & (fwd ? own() : kings_own) : (fwd ? own() : kings_own);
+            hop[d] = diag_step(diag_step(mv, d) & o, d) & e;
+            step[d] = diag_step(mv, d) & e;
+            cap = cap || hop[d] != 0;
+        }
+        capcache = pending >= 0 || cap;
         int n = 0;
-        for (uint64_t m = movers(); m; m &= m - 1) n += __popcll(dests(lowest(m), capcache));
-        ncache = n;
+#pragma unroll
+        for (int d = 0; d < 4; ++d) n += __popcll(capcache ? hop[d] : step[d]);
+        ncache = outcome == kOngoing ? n : 0;
     }
     __device__ __forceinline__ bool capture_mode() const { return capcache; }
     __device__ __forceinline__ int count() const { return ncache; }
@@ -401,6 +416,7 @@ struct HasamiShogi {
     using Mask = BitsW<5>;  // ordinals: at most 18 pieces x 16 destinations = 288 legal actions
     B128 own, opp;          // relative to the side to move
     int side, ply, passes, outcome;
+    int ncache;             // legal actions of the position (refresh(); also the end test of a ply)
 
     __device__ __forceinline__ static B128 valid() { return B128{grid_word(9, 9, 10, false, 0), grid_word(9, 9, 10, false, 1)}; }
     __device__ __forceinline__ void reset() {
@@ -408,6 +424,7 @@ struct HasamiShogi {
         opp = B128{kHasamiRows01Lo, kHasamiRows01Hi};  // P2 on rows 0-1
         side = ply = passes = 0;
         outcome = kOngoing;
+        ncache = 54;                                   // 9 pieces x 5 slides up + 9 hops
     }
     // one orthogonal step (and two, four): 0 up, 1 down, 2 left, 3 right
     __device__ __forceinline__ static B128 ortho(B128 b, int d) {
@@ -452,19 +469,28 @@ struct HasamiShogi {
         }
         return r;
     }
-    __device__ __forceinline__ int count() const {
+    // The legal-action count of the mover, for all pieces at once: along one
+    // direction the slide destinations of different pieces are disjoint (an
+    // empty cell has one nearest piece behind it), and so are the hop
+    // destinations, so each direction is one occluded fill and two popcounts.
+    __device__ __forceinline__ int count_all() const {
+        const B128 occ = own | opp, e = valid() & ~occ;
         int n = 0;
-        for (uint64_t m = own.lo; m; m &= m - 1) n += (int)popc(dests(lowest(m)));
-        for (uint64_t m = own.hi; m; m &= m - 1) n += (int)popc(dests(64 + lowest(m)));
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            B128 g = own, p = e;
+            g = g | (p & ortho(g, d));
+            p = p & ortho(p, d);
+            g = g | (p & ortho2(g, d));
+            p = p & ortho2(p, d);
+            g = g | (p & ortho4(g, d));
+            n += (int)popc(ortho(g, d) & e);
+            n += (int)popc(ortho(ortho(own, d) & occ, d) & e);
+        }
         return n;
     }
-    __device__ __forceinline__ bool any_move() const {
-        for (uint64_t m = own.lo; m; m &= m - 1)
-            if (any(dests(lowest(m)))) return true;
-        for (uint64_t m = own.hi; m; m &= m - 1)
-            if (any(dests(64 + lowest(m)))) return true;
-        return false;
-    }
+    __device__ __forceinline__ void refresh() { ncache = outcome == kOngoing ? count_all() : 0; }
+    __device__ __forceinline__ int count() const { return ncache; }
     __device__ __forceinline__ Mask legal() const { return ordinalsW<5>(count()); }
     __device__ __forceinline__ void find(int k, int& from, int& to) const {
         from = to = -1;
@@ -520,8 +546,8 @@ struct HasamiShogi {
         opp = x;
         ++ply;
         side ^= 1;
-        if (won) outcome = p + 1;
-        else if (!any_move()) outcome = p + 1;
+        ncache = count_all();  // the next player's legal actions
+        if (won || ncache == 0) outcome = p + 1;
     }
     __device__ __forceinline__ void pass() {}
     __device__ __forceinline__ static int canon_cell(int b) { return (b / kStride) * kCols + b % kStride; }
@@ -569,7 +595,6 @@ struct HasamiShogi {
     }
     __device__ __forceinline__ int extra() const { return 0; }
     __device__ __forceinline__ void set_extra(int) {}
-    __device__ __forceinline__ void refresh() {}
     __device__ __forceinline__ void planes_out(uint64_t* w) const {  // P1 lo, hi, P2 lo, hi
         const B128 a = side == 0 ? own : opp, b = side == 0 ? opp : own;
         w[0] = a.lo;
@@ -594,6 +619,7 @@ struct HasamiShogi {
         own = B128{w[0], w[1]};
         opp = B128{w[2], w[3]};
         unpack_small(w[4], ply, passes, side, outcome);
+        refresh();
     }
 };
 template <>

@@ -97,8 +97,8 @@ BENCH_CFGS = {
     YAVALATH_64K.name: (448, 0, 1, 0, 16),
     CONNECT5_9X12_64K.name: (448, 0, 1, 0, 16),
     WOLF_SHEEP_64K.name: (448, 0, 1, 0, 16),
-    DRAUGHTS_64K.name: (448, 4, 1, 0, 16),
-    HASAMI_64K.name: (448, 4, 1, 0, 8),
+    DRAUGHTS_64K.name: (448, 0, 1, 0, 16),
+    HASAMI_64K.name: (448, 2, 1, 0, 16),
 }
 MIXED_BENCH_CFG = (128, 0, 1, 1, 0)
 
