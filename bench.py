@@ -64,7 +64,7 @@ def parse():
                                                         "line_c5", "wolf_sheep", "draughts", "hasami_shogi", "mixed",
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--only", choices=["dense_layer", "gavel_library"], default=None,
+    p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep"], default=None,
                    help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
@@ -293,6 +293,31 @@ def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
     return ms, total
 
 
+SWEEP_GAMES = ("ttt", "c4", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5", "wolf_sheep", "draughts",
+               "hasami_shogi")
+
+
+def bench_batch_sweep(L, W, flush_buf, sizes=tuple(1 << k for k in range(10, 23, 2)), steps=8, warmup=2):
+    """Throughput against batch size (Fig. 2's log-scale batch axis): fused
+    playouts from the start position of every single-game workload at 2^10 ..
+    2^22 envs, each timed as the median of `steps` launches after `warmup`,
+    with the workload's launch shape and the L2 flushed between launches."""
+    import dataclasses
+
+    out = {}
+    for name in SWEEP_GAMES:
+        base = workload_cfg(name)
+        row = {}
+        for n in sizes:
+            cfg = dataclasses.replace(base, num_envs=n, name=base.name)
+            env, lc, ms, spl = bench_rollout_config(L, W, cfg, steps, warmup, flush_buf)
+            env.close()
+            m = statistics.median(ms)
+            row[str(n)] = {"env_steps_per_s": round(spl / (m / 1e3), 1), "median_launch_ms": round(m, 5)}
+        out[name] = row
+    return out
+
+
 def bench_compiled_library(L, steps, warmup, flush_buf, n=1 << 20, seed=3):
     """A mixed batch of every game description in the package's library,
     compiled to descriptors (env e plays library game e mod G), through the
@@ -482,7 +507,12 @@ def main():
     peaks, peak_kind = measured_peaks()
     flush_buf = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")  # 256 MiB
     if args.only:
-        res = bench_dense(L, peaks, flush_buf) if args.only == "dense_layer" else bench_gavel()
+        if args.only == "dense_layer":
+            res = bench_dense(L, peaks, flush_buf)
+        elif args.only == "gavel_library":
+            res = bench_gavel()
+        else:
+            res = bench_batch_sweep(L, W, flush_buf)
         if rank == 0:
             print(json.dumps({args.only: res}), flush=True)
         return 0
