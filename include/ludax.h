@@ -256,9 +256,12 @@ const char* ludax_status_string(int status);
 /* ---------------------------------------------------------------------------
  * Mixed-game batches: one persistent launch over envs of different games and
  * board sizes, each env's game given by an int32 descriptor
- *   desc = game | rows << 8 | cols << 16
- * (LUDAX_DESC(g, r, c)).  Results match per-game ludax_rollout calls from the
- * start position with the same (seed, global env index) bit for bit.       */
+ *   desc = game | rows << 8 | cols << 16   (LUDAX_DESC(g, r, c))
+ *   desc = LUDAX_GAME_LINE | rows << 8 | cols << 16 | line << 24 | flags << 28
+ *          (LUDAX_DESC_LINE(r, c, line, flags))
+ * for any game and board size ludax_env_create accepts.  Results match
+ * per-game ludax_rollout calls from the start position with the same (seed,
+ * global env index) bit for bit.                                           */
 #define LUDAX_DESC(g, r, c) ((int32_t)((g) | ((r) << 8) | ((c) << 16)))
 /* descriptor of the parametric line game: line length in bits 24-27, flags in 28-30 */
 #define LUDAX_DESC_LINE(r, c, line, flags) \

@@ -1,11 +1,13 @@
 // ludax_mixed.cu -- mixed-game batches in one persistent launch, the CUDA
 // graph plan that replays it, and the launch-shape autotuner.
 //
-// Each env carries an int32 descriptor game | rows << 8 | cols << 16.  At plan
-// creation the env ids are grouped by game ("buckets": Tic-Tac-Toe, Connect
-// Four, Reversi, Hex 2..11) into a work queue, so consecutive queue positions
-// -- and therefore the 32 lanes of a warp -- play the same game and branch
-// together.  The persistent kernel hands out queue positions with a
+// Each env carries an int32 descriptor game | rows << 8 | cols << 16 (plus
+// line << 24 | flags << 28 for the line game).  At plan creation the env ids
+// are grouped by kernel instance ("buckets": Tic-Tac-Toe, Connect Four,
+// Reversi, Hex 2..11, Gomoku, Pente, Yavalath, the parametric line game, Wolf
+// and Sheep, Draughts, Dai Hasami Shogi) into a work queue, so consecutive
+// queue positions -- and therefore the 32 lanes of a warp -- play the same
+// game and branch together.  The persistent kernel hands out queue positions with a
 // warp-aggregated atomic cursor; a lane whose game ends writes its 3 bytes of
 // output and claims the next position, staying inside its game's playout
 // loop while the claimed env has the same game.
