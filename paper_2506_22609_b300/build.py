@@ -51,14 +51,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
-    objs = []
-    log = []
-    for src in sources():
+
+    def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
         cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
+        return src, obj, r
+
+    # the translation units are independent: compile them side by side
+    from concurrent.futures import ThreadPoolExecutor
+
+    srcs = sources()
+    with ThreadPoolExecutor(max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        results = list(ex.map(compile_one, srcs))
+    objs, log = [], []
+    for src, obj, r in results:
         log.append(r.stdout + r.stderr)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
