@@ -183,6 +183,7 @@ struct Draughts {
     int side, ply, passes, outcome, pending;           // pending: cell of the piece that must hop again, -1 if none
     int ncache;                                        // legal actions of the position (refresh())
     bool capcache;                                     // whether they are hops
+    uint64_t src[4];                                   // per direction, the movers that have that move (refresh())
 
     __device__ __forceinline__ void reset() {
         men_own = 0x55AA550000000000ull;  // P1: dark cells of rows 5-7
@@ -250,30 +251,51 @@ struct Draughts {
         capcache = pending >= 0 || cap;
         int n = 0;
 #pragma unroll
-        for (int d = 0; d < 4; ++d) n += __popcll(capcache ? hop[d] : step[d]);
+        for (int d = 0; d < 4; ++d) {
+            const uint64_t dst = capcache ? hop[d] : step[d];
+            n += __popcll(dst);
+            // a destination minus the direction's step is its source
+            const int back = (d == 0 ? 9 : d == 1 ? 7 : d == 2 ? -7 : -9) * (capcache ? 2 : 1);
+            src[d] = back > 0 ? shl64c(dst, (uint32_t)back) : shr64c(dst, (uint32_t)-back);
+        }
         ncache = outcome == kOngoing ? n : 0;
     }
     __device__ __forceinline__ bool capture_mode() const { return capcache; }
     __device__ __forceinline__ int count() const { return ncache; }
     __device__ __forceinline__ Mask legal() const { return ordinals64(ncache); }
+    // The moves of piece i are the directions whose source set holds i
+    // (ascending direction = ascending destination); every mover is counted
+    // (no early exit) and the one holding the k-th move noted on the way.
     __device__ __forceinline__ void find(int k, int& from, int& to) const {
-        const bool cap = capture_mode();
-        from = to = -1;
+        int acc = 0, sel = -1, kk = 0;
+        uint32_t dirs = 0;
         for (uint64_t m = movers(); m; m &= m - 1) {
             const int i = lowest(m);
-            const uint64_t d = dests(i, cap);
-            const int c = __popcll(d);
-            if (k < c) {
-                from = i;
-                to = select_bit(d, (uint32_t)k);
-                return;
-            }
-            k -= c;
+            const uint32_t g = ((uint32_t)(src[0] >> i) & 1u) | (((uint32_t)(src[1] >> i) & 1u) << 1) |
+                               (((uint32_t)(src[2] >> i) & 1u) << 2) | (((uint32_t)(src[3] >> i) & 1u) << 3);
+            const int n = __popc(g);
+            const bool hit = sel < 0 && k < acc + n;
+            sel = hit ? i : sel;
+            kk = hit ? k - acc : kk;
+            dirs = hit ? g : dirs;
+            acc += n;
         }
+        from = sel;
+        if (sel < 0) {
+            to = -1;
+            return;
+        }
+        const int d = select_bit(dirs, (uint32_t)kk);
+        to = sel + (d == 0 ? -9 : d == 1 ? -7 : d == 2 ? 7 : 9) * (capture_mode() ? 2 : 1);
     }
     __device__ __forceinline__ void place(int k) {
         int f, t;
         find(k, f, t);
+        apply(f, t);
+    }
+    // move the mover's piece from cell f to t, then capture, crowning, the
+    // extra turn and the end test
+    __device__ __forceinline__ void apply(int f, int t) {
         const int p = side;
         const uint64_t fb = 1ull << f, tb = 1ull << t;
         const bool king = (kings_own >> f) & 1;
@@ -401,6 +423,17 @@ constexpr uint64_t kHasamiRows01Lo = hasami_rows(0, 1, 0), kHasamiRows01Hi = has
 constexpr uint64_t kHasamiRows78Lo = hasami_rows(7, 8, 0), kHasamiRows78Hi = hasami_rows(7, 8, 1);
 constexpr uint64_t kHasamiRows06Lo = hasami_rows(0, 6, 0), kHasamiRows06Hi = hasami_rows(0, 6, 1);
 constexpr uint64_t kHasamiRows28Lo = hasami_rows(2, 8, 0), kHasamiRows28Hi = hasami_rows(2, 8, 1);
+// word w of the transposed layout (bit 10 * column + row) holding rows r0..r1
+__host__ __device__ constexpr uint64_t hasami_cols(int r0, int r1, int w) {
+    uint64_t m = 0;
+    for (int b = 0; b < 64; ++b) {
+        const int i = w * 64 + b, c = i / 10, r = i % 10;
+        if (r >= r0 && r <= r1 && r < 9 && c < 9) m |= 1ull << b;
+    }
+    return m;
+}
+constexpr uint64_t kHasamiStartTLo = hasami_cols(0, 1, 0) | hasami_cols(7, 8, 0);
+constexpr uint64_t kHasamiStartTHi = hasami_cols(0, 1, 1) | hasami_cols(7, 8, 1);
 
 // 9x9 in two words with a row stride of 10 (the empty tenth column stops
 // horizontal runs from wrapping).  P1 fills rows 7-8, P2 rows 0-1.  A piece
@@ -415,6 +448,7 @@ struct HasamiShogi {
     static constexpr bool kHasPass = false;
     using Mask = BitsW<5>;  // ordinals: at most 18 pieces x 16 destinations = 288 legal actions
     B128 own, opp;          // relative to the side to move
+    B128 occT;              // occupied cells transposed (bit 10 * column + row): columns as 10-bit windows
     int side, ply, passes, outcome;
     int ncache;             // legal actions of the position (refresh(); also the end test of a ply)
 
@@ -422,6 +456,7 @@ struct HasamiShogi {
     __device__ __forceinline__ void reset() {
         own = B128{kHasamiRows78Lo, kHasamiRows78Hi};  // P1 on rows 7-8
         opp = B128{kHasamiRows01Lo, kHasamiRows01Hi};  // P2 on rows 0-1
+        occT = B128{kHasamiStartTLo, kHasamiStartTHi};
         side = ply = passes = 0;
         outcome = kOngoing;
         ncache = 54;                                   // 9 pieces x 5 slides up + 9 hops
@@ -489,24 +524,84 @@ struct HasamiShogi {
         }
         return n;
     }
-    __device__ __forceinline__ void refresh() { ncache = outcome == kOngoing ? count_all() : 0; }
+    __device__ __forceinline__ static int transposed(int i) { return 10 * (i % 10) + i / 10; }
+    __device__ __forceinline__ void refresh() {
+        occT = B128{0, 0};
+        for (int w = 0; w < 2; ++w)
+            for (uint64_t m = w ? (own.hi | opp.hi) : (own.lo | opp.lo); m; m &= m - 1)
+                occT = occT | bit128(transposed(64 * w + lowest(m)));
+        ncache = outcome == kOngoing ? count_all() : 0;
+    }
     __device__ __forceinline__ int count() const { return ncache; }
     __device__ __forceinline__ Mask legal() const { return ordinalsW<5>(count()); }
+    // bits at..at+8 of b: one row of the board (at = 10 * row) or one column
+    // of the transpose (at = 10 * column); one funnel shift of two 32-bit words
+    __device__ __forceinline__ static uint32_t field9(B128 b, int at) {
+        const uint32_t w0 = (uint32_t)b.lo, w1 = (uint32_t)(b.lo >> 32), w2 = (uint32_t)b.hi, w3 = (uint32_t)(b.hi >> 32);
+        const int q = at >> 5;
+        const uint32_t x = q == 0 ? w0 : (q == 1 ? w1 : w2), y = q == 0 ? w1 : (q == 1 ? w2 : w3);
+        return __funnelshift_r(x, y, (uint32_t)at & 31u) & 0x1FFu;
+    }
+    // the blocked cells of a row or column as a window: cell j at bit j + 2,
+    // and two set bits past each end (the edge stops runs and hops as a
+    // piece does)
+    __device__ __forceinline__ static uint32_t window(B128 occ, int at) { return (field9(occ, at) << 2) | 0x1803u; }
+    // The moves of one piece without forming its destination set: in the
+    // window of its row (column) the slide to the right (down) is the run of
+    // clear bits above it and to the left (up) the run below it; a hop needs
+    // the adjacent cell blocked by a piece and the cell beyond it clear.
+    struct Runs {
+        int up, left, right, down;
+        int hup, hleft, hright, hdown;
+        __device__ __forceinline__ int total() const { return up + left + right + down + hup + hleft + hright + hdown; }
+    };
+    __device__ __forceinline__ static void axis(uint32_t w, int j, int& lo, int& hi, int& hlo, int& hhi) {
+        const uint32_t a = w >> (j + 3);                        // bit 0: the cell after j
+        hi = __ffs(a) - 1;
+        lo = j - 30 + __clz(w & ((1u << (j + 2)) - 1u));        // nearest blocked bit below j
+        hhi = (int)(a & ~(a >> 1) & 1u);
+        hlo = (int)((w >> (j + 1)) & ~(w >> j) & 1u);
+    }
+    __device__ __forceinline__ static Runs runs_of(uint32_t row, uint32_t col, int r, int c) {
+        Runs x;
+        axis(row, c, x.left, x.right, x.hleft, x.hright);
+        axis(col, r, x.up, x.down, x.hup, x.hdown);
+        return x;
+    }
+    // the k-th destination of piece i in ascending cell order: cells above
+    // it, then left of it, right of it, below it
+    __device__ __forceinline__ static int dest_of(int i, const Runs& x, int k) {
+        const int nu = x.up + x.hup, nl = x.left + x.hleft, nr = x.right + x.hright;
+        if (k < nu) return x.hup ? i - 20 : i - 10 * (x.up - k);
+        k -= nu;
+        if (k < nl) return x.hleft ? i - 2 : i - (x.left - k);
+        k -= nl;
+        if (k < nr) return x.hright ? i + 2 : i + 1 + k;
+        k -= nr;
+        return x.hdown ? i + 20 : i + 10 * (1 + k);
+    }
+    __device__ __forceinline__ Runs runs_at(B128 occ, int i) const {
+        const int r = i / 10, c = i - 10 * r;
+        return runs_of(window(occ, 10 * r), window(occT, 10 * c), r, c);
+    }
+    // Every piece is counted (no early exit): the counts do not depend on k,
+    // so their latencies overlap, and the piece holding the k-th move is
+    // noted on the way.
     __device__ __forceinline__ void find(int k, int& from, int& to) const {
-        from = to = -1;
+        const B128 occ = own | opp;
+        int acc = 0, sel = -1, kk = 0;
         for (int w = 0; w < 2; ++w) {
             for (uint64_t m = w ? own.hi : own.lo; m; m &= m - 1) {
                 const int i = 64 * w + lowest(m);
-                const B128 d = dests(i);
-                const int c = (int)popc(d);
-                if (k < c) {
-                    from = i;
-                    to = select_bit(d, (uint32_t)k);
-                    return;
-                }
-                k -= c;
+                const int n = runs_at(occ, i).total();
+                const bool hit = sel < 0 && k < acc + n;
+                sel = hit ? i : sel;
+                kk = hit ? k - acc : kk;
+                acc += n;
             }
         }
+        from = sel;
+        to = sel < 0 ? -1 : dest_of(sel, runs_at(occ, sel), kk);
     }
     __device__ __forceinline__ bool five() const {  // the mover, outside its starting rows
         const B128 m = own & (side == 0 ? B128{kHasamiRows06Lo, kHasamiRows06Hi} : B128{kHasamiRows28Lo, kHasamiRows28Hi});
@@ -517,18 +612,30 @@ struct HasamiShogi {
     __device__ __forceinline__ void place(int k) {
         int f, t;
         find(k, f, t);
+        apply(f, t);
+    }
+    // move the mover's piece from internal cell f to t, then captures and end test
+    __device__ __forceinline__ void apply(int f, int t) {
         const int p = side;
-        const B128 tb = bit128(t);
+        const B128 tb = bit128(t), tT = bit128(transposed(t));
         own = (own & ~bit128(f)) | tb;
+        occT = (occT & ~bit128(transposed(f))) | tT;
         // custodial captures along the four directions from the moved piece
+        // (walked in both layouts: a row of the board is a column of the transpose)
 #pragma unroll
         for (int d = 0; d < 4; ++d) {
-            B128 run{0, 0}, x = ortho(tb, d);
+            const int dT = d ^ 2;
+            B128 run{0, 0}, runT{0, 0}, x = ortho(tb, d), xT = ortho(tT, dT);
             for (int s = 0; s < 8 && any(x & opp); ++s) {
                 run = run | x;
+                runT = runT | xT;
                 x = ortho(x, d);
+                xT = ortho(xT, dT);
             }
-            if (any(x & own)) opp = opp & ~run;
+            if (any(x & own)) {
+                opp = opp & ~run;
+                occT = occT & ~runT;
+            }
         }
         // corner captures: an opposing corner piece whose two neighbours are
         // now the mover's, one of them the moved piece
@@ -537,8 +644,10 @@ struct HasamiShogi {
             const int corner = c == 0 ? 0 : (c == 1 ? 8 : (c == 2 ? 80 : 88));
             const int n1 = c == 0 ? 10 : (c == 1 ? 18 : (c == 2 ? 70 : 78));
             const int n2 = c == 0 ? 1 : (c == 1 ? 7 : (c == 2 ? 81 : 87));
-            if (any(opp & bit128(corner)) && any(own & bit128(n1)) && any(own & bit128(n2)) && (t == n1 || t == n2))
+            if (any(opp & bit128(corner)) && any(own & bit128(n1)) && any(own & bit128(n2)) && (t == n1 || t == n2)) {
                 opp = opp & ~bit128(corner);
+                occT = occT & ~bit128(c == 0 ? 0 : (c == 1 ? 80 : (c == 2 ? 8 : 88)));
+            }
         }
         const bool won = five();
         const B128 x = own;
@@ -607,19 +716,22 @@ struct HasamiShogi {
         own = side == 0 ? a : b;
         opp = side == 0 ? b : a;
     }
-    static constexpr int kWords = 5;
+    static constexpr int kWords = 7;
     __device__ __forceinline__ void save(uint64_t* w) const {
         w[0] = own.lo;
         w[1] = own.hi;
         w[2] = opp.lo;
         w[3] = opp.hi;
         w[4] = pack_small(ply, passes, side, outcome);
+        w[5] = occT.lo;
+        w[6] = occT.hi;
     }
     __device__ __forceinline__ void load(const uint64_t* w) {
         own = B128{w[0], w[1]};
         opp = B128{w[2], w[3]};
         unpack_small(w[4], ply, passes, side, outcome);
-        refresh();
+        occT = B128{w[5], w[6]};
+        ncache = outcome == kOngoing ? count_all() : 0;
     }
 };
 template <>
