@@ -64,7 +64,7 @@ def parse():
                                                         "line_c5", "wolf_sheep", "draughts", "hasami_shogi", "mixed",
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep"], default=None,
+    p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net"], default=None,
                    help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
@@ -500,7 +500,7 @@ def bench_valuenet():
                      "reference_noise_mae": ev["reference_noise_mae"], "target_mae": ev["target_mae"],
                      "final_val_mae": r["history"][-1]["val_mae"], "train_seconds": round(r["train_seconds"], 3),
                      "train_steps": r["train_steps"], "data_seconds": round(r["data_seconds"], 3),
-                     "n_train": r["n_train"], "n_eval": r["n_eval"],
+                     "n_train": r["n_train"], "n_eval": r["n_eval"], "inference_rows": ev["inference_rows"],
                      "all_truncated": ev["truncated"], "all_full": ev["full_playouts"]}
     return out
 
@@ -537,6 +537,8 @@ def main():
             res = bench_dense(L, peaks, flush_buf)
         elif args.only == "gavel_library":
             res = bench_gavel()
+        elif args.only == "value_net":
+            res = bench_valuenet()
         else:
             res = bench_batch_sweep(L, W, flush_buf)
         if rank == 0:

@@ -98,5 +98,11 @@ __host__ __device__ inline int desc_bucket(int32_t d) {
 bool umma_dense_supported(int M, int N, int K);
 int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, int M, int N, int K, int ldo,
                     cudaStream_t s);
+// The same layer with row pitches lda / ldb (K may be a prefix of the rows:
+// columns past K are not read) and, with w3 non-null (N BF16 weights), the
+// head fused into the epilogue: instead of storing the rows, zpart[m * (N /
+// 256) + j] = sum over the j-th 256 columns of bf16(relu(.))[m][n] * w3[n].
+int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const float* bias, void* out, int ldo,
+                       const void* w3, float* zpart, int M, int N, int K, cudaStream_t s);
 
 }  // namespace ludax

@@ -454,9 +454,32 @@ int dense_layer(ludax_net* n, const __nv_bfloat16* A, const __nv_bfloat16* W, co
     return launch_gemm<true, true, EPI_BIAS_RELU>(a, 1, n->stream);
 }
 
+// p[row] from the head partials of the fused second layer
+__global__ void head_finish_kernel(const float* zpart, int parts, const float* b3, int B, float* p_out) {
+    int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= B) return;
+    float z = 0.f;
+    for (int i = 0; i < parts; ++i) z += zpart[(size_t)row * parts + i];
+    p_out[row] = 0.5f * (tanhf(z + b3[0]) + 1.f);
+}
+
 // Forward pass to p (and, with labels y, the per-row gradient g3 of the loss).
-int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, const float* y) {
+// kuse <= kpad: the input columns the first layer reads (the rest must be zero).
+// Without labels (inference) and on the tcgen05 path, the head is fused into
+// the second layer's epilogue, so its rows are never stored.
+int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, const float* y, int kuse = 0) {
     cudaStream_t s = n->stream;
+    if (kuse <= 0) kuse = n->kpad;
+    if (!y && p && n->use_tcgen05 && umma_dense_supported((int)B, kH, kuse) && umma_dense_supported((int)B, kH, kH)) {
+        int st = umma_dense_relu_ex(X, n->kpad, n->W1b, n->kpad, n->p + n->ob1, n->H1, kH, nullptr, nullptr, (int)B, kH,
+                                    kuse, s);
+        if (st) return st;
+        float* zpart = n->g3;  // 2 floats per row: g3 and sqerr are unused without labels
+        if ((st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, nullptr, 0, n->w3b, zpart, (int)B, kH, kH, s)))
+            return st;
+        head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, kH / 256, n->p + n->ob3, (int)B, p);
+        return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    }
     int st = dense_layer(n, X, n->W1b, n->p + n->ob1, n->H1, B, n->kpad);
     if (st) return st;
     if ((st = dense_layer(n, n->H1, n->W2b, n->p + n->ob2, n->H2, B, kH))) return st;
@@ -675,7 +698,9 @@ int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K
                 return LUDAX_ERR_CUDA;
             leaf_kernel<G><<<blocks_for(rows, 128), 128, 0, env->stream>>>(d, e0, nc, K, seed, plies, n->Xleaf,
                                                                              n->kpad, n->score, n->done);
-            int st = net_forward(n, n->Xleaf, rows_pad, n->pout, nullptr);
+            // the leaf rows are zero past the 2 * cells + 1 inputs: the first
+            // layer reads only the 64-column blocks that hold them
+            int st = net_forward(n, n->Xleaf, rows_pad, n->pout, nullptr, ((n->kin + 63) / 64) * 64);
             if (st) return st;
             combine_kernel<<<blocks_for(nc, 256), 256, 0, env->stream>>>(e0, nc, K, n->score, n->done, n->pout, value_dev);
         }

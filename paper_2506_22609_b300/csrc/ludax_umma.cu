@@ -41,7 +41,7 @@ constexpr int OUT_BOX = 64;        // output columns per TMA store box (128 byte
 constexpr int STAGING = 32 * OUT_BOX * 2;  // one 32-row box per epilogue warp, 128-byte swizzle
 constexpr int RING = TSTAGES * STAGE;
 constexpr size_t UMMA_SMEM = 1024 /* alignment */ + (size_t)RING + 4 * STAGING + 256 /* barriers */ +
-                             sizeof(float) * MAX_N /* bias */;
+                             2 * sizeof(float) * MAX_N /* bias, head weights */;
 constexpr long long kWaitLimit = 2000000000ll;  // clock cycles (~1 s at 2 GHz)
 
 static __device__ int g_umma_error;  // nonzero after a wait expired
@@ -147,7 +147,8 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
     umma_dense_relu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                            const __grid_constant__ CUtensorMap tmOut, int M, int N, int K,
-                           const float* __restrict__ bias) {
+                           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ w3,
+                           float* __restrict__ zpart) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + RING;  // 1024-byte aligned: the 128-byte swizzle pattern repeats every 1024 bytes
@@ -157,9 +158,14 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
     float* sbias = reinterpret_cast<float*>(smem + RING + 4 * STAGING + 256);
+    float* sw3 = sbias + MAX_N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ktiles = K / TK, ntn = N / TN, ntiles = (M / TM) * ntn;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) sbias[i] = bias[i];
+    const bool head = w3 != nullptr;  // fused head: per-row dot products with w3 instead of stored rows
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        sbias[i] = bias[i];
+        sw3[i] = head ? __bfloat162float(w3[i]) : 0.f;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TSTAGES; ++s) {
@@ -238,6 +244,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
             // two register sets: the load of chunk c + 1 is in flight while chunk c is converted
             uint32_t r[2][32];
+            float z = 0.f;  // fused head: this row's dot product over the tile's columns
             tmem_ld32_async(base, r[0]);
             tmem_wait_ld(r[0]);
 #pragma unroll
@@ -253,6 +260,20 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                                                      fmaxf(__uint_as_float(x[4 * j + 1]) + b4.y, 0.f));
                     v[2 * j + 1] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j + 2]) + b4.z, 0.f),
                                                          fmaxf(__uint_as_float(x[4 * j + 3]) + b4.w, 0.f));
+                }
+                if (head) {  // the BF16 activations, as a stored row would hold them, times w3
+                    const float4* ww = reinterpret_cast<const float4*>(sw3 + n0 + c * 32);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 w4 = ww[j];
+                        const float2 f0 = __bfloat1622float2(v[2 * j]), f1 = __bfloat1622float2(v[2 * j + 1]);
+                        z = fmaf(f0.x, w4.x, z);
+                        z = fmaf(f0.y, w4.y, z);
+                        z = fmaf(f1.x, w4.z, z);
+                        z = fmaf(f1.y, w4.w, z);
+                    }
+                    if (c + 1 < TN / 32) tmem_wait_ld(r[(c + 1) & 1]);
+                    continue;
                 }
                 const int half = c & 1;  // which 64-byte half of the box row
                 if (half == 0) {         // the box's previous store must have read the staging buffer
@@ -272,6 +293,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                 }
                 if (c + 1 < TN / 32) tmem_wait_ld(r[(c + 1) & 1]);
             }
+            if (head) zpart[(size_t)(row0 + lane) * ntn + (t % ntn)] = z;
             tc_fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
         }
@@ -325,10 +347,20 @@ bool umma_dense_supported(int M, int N, int K) {
 
 int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, int M, int N, int K, int ldo,
                     cudaStream_t s) {
-    if (!umma_dense_supported(M, N, K) || ldo % 8 || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)out % 16))
+    return umma_dense_relu_ex(A, K, B, K, bias, out, ldo, nullptr, nullptr, M, N, K, s);
+}
+
+int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const float* bias, void* out, int ldo,
+                       const void* w3, float* zpart, int M, int N, int K, cudaStream_t s) {
+    const bool head = w3 != nullptr;
+    if (!umma_dense_supported(M, N, K) || lda < K || ldb < K || lda % 8 || ldb % 8 || ((uintptr_t)A % 16) ||
+        ((uintptr_t)B % 16))
         return LUDAX_ERR_SIZE;
+    if (head ? !zpart : (!out || ldo % 8 || ((uintptr_t)out % 16))) return LUDAX_ERR_SIZE;
     CUtensorMap ma, mb, mo;
-    if (!make_map(&ma, A, M, K, TM, K) || !make_map(&mb, B, N, K, TN, K) || !make_map(&mo, out, M, N, 32, ldo))
+    // in head mode nothing is stored: the output map is a valid placeholder over A
+    if (!make_map(&ma, A, M, K, TM, lda) || !make_map(&mb, B, N, K, TN, ldb) ||
+        !(head ? make_map(&mo, A, M, K, 32, lda) : make_map(&mo, out, M, N, 32, ldo)))
         return LUDAX_ERR_CUDA;
     static bool attr = false;
     if (!attr) {
@@ -346,7 +378,8 @@ int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, 
     }
     const int ntiles = (M / TM) * (N / TN);
     const int grid = ntiles < sms ? ntiles : sms;
-    umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias);
+    umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias,
+                                                                  static_cast<const __nv_bfloat16*>(w3), zpart);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 

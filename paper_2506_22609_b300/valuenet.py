@@ -109,9 +109,23 @@ def predict(net, x):
     return torch.cat(out)
 
 
+def inference_net(net, rows):
+    """A copy of the trained net whose buffers hold `rows` rows (rounded up to
+    128, at most 2^21), so an estimate over all positions is one batch:
+    every continuation of every position goes through the dense layers as one
+    large GEMM instead of max_batch-sized chunks."""
+    rows = min(1 << 21, ((int(rows) + 127) // 128) * 128)
+    if rows <= net.max_batch:
+        return net, False
+    big = L.Net(net.cells, rows)
+    big.set_params(net.get_params())
+    return big, True
+
+
 def evaluate(env, net, ref, seed, Ms=(4, 8, 16, 32, 64, 128), Ks=(1, 2, 4, 8, 16), plies=8, target=0.05):
     n = env.num_envs
     res = {"full_playouts": [], "truncated": []}
+    net, owned = inference_net(net, n * max(Ks))
     for M in Ms:
         v, dt = cuda_time(lambda: env.rollout_value(seed + 100000 * M, M))
         res["full_playouts"].append({"M": M, "mae": float((v - ref).abs().mean().item()),
@@ -124,6 +138,9 @@ def evaluate(env, net, ref, seed, Ms=(4, 8, 16, 32, 64, 128), Ks=(1, 2, 4, 8, 16
                                  "estimates_per_s": n / dt, "seconds": dt})
     pnet = predict(net, pack(env, net.in_pad))
     res["net_only_mae"] = float((pnet - ref).abs().mean().item())
+    res["inference_rows"] = net.max_batch
+    if owned:
+        net.close()
     # noise of the reference itself: sd of a 256-sample mean, as an expected absolute value
     r = ref.double()
     res["reference_noise_mae"] = float((torch.sqrt(r * (1 - r) / 256) * (2 / np.pi) ** 0.5).mean().item())
