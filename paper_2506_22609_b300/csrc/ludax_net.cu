@@ -368,30 +368,78 @@ __global__ void pack_inputs_kernel(EnvDev d, __nv_bfloat16* X, int ld) {
     write_input_row(g, X + (size_t)e * ld, ld);
 }
 
+// The same input row as bits (bit c = column c) in four words: P1's stones
+// in canonical cell order, then P2's shifted up by `cells`, then the
+// P1-to-move bit at 2 * cells (at most 255 columns).
+template <class G>
+__device__ __forceinline__ void input_bits(const G& g, uint64_t x[4]) {
+    const int cells = cells_of(g);
+    const typename G::Mask& p1 = g.side == 0 ? g.own : g.opp;
+    const typename G::Mask& p2 = g.side == 0 ? g.opp : g.own;
+    const uint64_t a0 = canon_mask_word(g, p1, 0), a1 = cells > 64 ? canon_mask_word(g, p1, 1) : 0ull;
+    const uint64_t b0 = canon_mask_word(g, p2, 0), b1 = cells > 64 ? canon_mask_word(g, p2, 1) : 0ull;
+    const uint32_t r = (uint32_t)cells & 63u;  // P2 starts in word cells / 64 (0 or 1) at bit r
+    const uint64_t lo = shl64c(b0, r), mid = shl64c(b1, r) | shr64c(b0, 64u - r), hi = shr64c(b1, 64u - r);
+    const bool up = cells >= 64;
+    x[0] = a0 | (up ? 0ull : lo);
+    x[1] = a1 | (up ? lo : mid);
+    x[2] = up ? mid : hi;
+    x[3] = up ? hi : 0ull;
+    const int s = 2 * cells;
+    const uint64_t side_bit = g.side == 0 ? (1ull << (s & 63)) : 0ull;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) x[w] |= (s >> 6) == w ? side_bit : 0ull;  // no run-time index into x
+}
+
+// bits t0, t0+1 of v as two BF16 values (1.0 = 0x3F80) in one 32-bit word
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t v) { return ((v & 1u) | ((v & 2u) << 15)) * 0x3F80u; }
+
 // Continuation j of env e0+i (i < n_chunk): up to `plies` uniform-random plies
 // from the stored state with the draws of playout seed + j, then either the
-// final result (score, done = 1) or the leaf's input row (done = 0).
+// final result (score, done = 1) or the leaf's input row (done = 0).  The rows
+// are written by the whole warp together: each lane's bits go to shared memory,
+// then row by row every lane expands one byte (8 columns) into one 16-byte
+// store, so a row is one contiguous write.  Only the first kuse columns are
+// written (the layer that reads them takes no more).
+constexpr int LEAF_THREADS = 128;
 template <class G>
-__global__ void leaf_kernel(EnvDev d, long long e0, long long n_chunk, int K, uint64_t seed, int plies,
-                            __nv_bfloat16* X, int ld, float* score, uint8_t* done) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_chunk * K) return;
-    long long e = e0 + t / K;
-    int j = (int)(t % K);
-    G g;
-    set_table(g, nullptr);
-    load_state(g, d, e);
-    uint64_t key = env_key(splitmix64(seed + (uint64_t)j), (uint64_t)(d.env_offset + e));
-    int stop = g.ply + plies;
-    uint32_t rhi = draw_hi(key, (uint32_t)g.ply);
-    while (g.outcome == kOngoing && g.ply < stop) random_ply_pre(g, key, rhi);
-    if (g.outcome != kOngoing) {
-        score[t] = p1_score(g.outcome);
-        done[t] = 1;
-    } else {
-        done[t] = 0;
+__global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(EnvDev d, long long e0, long long n_chunk, int K,
+                                                             uint64_t seed, int plies, __nv_bfloat16* X, int ld,
+                                                             int kuse, float* score, uint8_t* done) {
+    __shared__ uint64_t bits[LEAF_THREADS / 32][32][4];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x, total = n_chunk * K;
+    uint64_t x[4] = {0ull, 0ull, 0ull, 0ull};
+    if (t < total) {
+        const long long e = e0 + t / K;
+        const int j = (int)(t % K);
+        G g;
+        set_table(g, nullptr);
+        load_state(g, d, e);
+        uint64_t key = env_key(splitmix64(seed + (uint64_t)j), (uint64_t)(d.env_offset + e));
+        int stop = g.ply + plies;
+        uint32_t rhi = draw_hi(key, (uint32_t)g.ply);
+        while (g.outcome == kOngoing && g.ply < stop) random_ply_pre(g, key, rhi);
+        if (g.outcome != kOngoing) {
+            score[t] = p1_score(g.outcome);
+            done[t] = 1;
+        } else {
+            done[t] = 0;
+        }
+        input_bits(g, x);
     }
-    write_input_row(g, X + (size_t)t * ld, ld);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) bits[wib][lane][w] = x[w];
+    __syncwarp();
+    const long long t0 = t - lane;
+    const uint8_t* rb = reinterpret_cast<const uint8_t*>(&bits[wib][0][0]);
+    if (8 * lane < kuse) {
+        for (int r = 0; r < 32 && t0 + r < total; ++r) {
+            const uint32_t v = rb[r * 32 + lane];  // columns 8 * lane .. 8 * lane + 7 of row t0 + r
+            const uint4 o = make_uint4(bf16_pair(v), bf16_pair(v >> 2), bf16_pair(v >> 4), bf16_pair(v >> 6));
+            *reinterpret_cast<uint4*>(X + (size_t)(t0 + r) * ld + 8 * lane) = o;
+        }
+    }
 }
 
 // value[e0+i] = mean over j of (done ? score : p_net)
@@ -696,11 +744,12 @@ int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K
                 cudaMemsetAsync(n->Xleaf + (size_t)rows * n->kpad, 0,
                                 sizeof(__nv_bfloat16) * (size_t)(rows_pad - rows) * n->kpad, env->stream) != cudaSuccess)
                 return LUDAX_ERR_CUDA;
-            leaf_kernel<G><<<blocks_for(rows, 128), 128, 0, env->stream>>>(d, e0, nc, K, seed, plies, n->Xleaf,
-                                                                             n->kpad, n->score, n->done);
-            // the leaf rows are zero past the 2 * cells + 1 inputs: the first
-            // layer reads only the 64-column blocks that hold them
-            int st = net_forward(n, n->Xleaf, rows_pad, n->pout, nullptr, ((n->kin + 63) / 64) * 64);
+            // the first layer reads only the 64-column blocks that hold the
+            // 2 * cells + 1 inputs; the leaf rows are written that far
+            const int kuse = ((n->kin + 63) / 64) * 64;
+            leaf_kernel<G><<<blocks_for(rows, LEAF_THREADS), LEAF_THREADS, 0, env->stream>>>(
+                d, e0, nc, K, seed, plies, n->Xleaf, n->kpad, kuse, n->score, n->done);
+            int st = net_forward(n, n->Xleaf, rows_pad, n->pout, nullptr, kuse);
             if (st) return st;
             combine_kernel<<<blocks_for(nc, 256), 256, 0, env->stream>>>(e0, nc, K, n->score, n->done, n->pout, value_dev);
         }

@@ -74,6 +74,18 @@ def cuda_time(fn):
     return out, a.elapsed_time(b) / 1e3
 
 
+def cuda_time_median(fn, warmup=2, reps=5):
+    """fn's result and its median time over `reps` timed calls after `warmup`
+    untimed ones (the first call of a shape also pays one-time setup)."""
+    for _ in range(warmup):
+        fn()
+    times = []
+    for _ in range(reps):
+        out, dt = cuda_time(fn)
+        times.append(dt)
+    return out, float(np.median(times))
+
+
 def train(net, x, y, batch, epochs, lr, seed, x_val=None, y_val=None, log=None):
     n = x.shape[0]
     nb = n // batch
@@ -127,13 +139,13 @@ def evaluate(env, net, ref, seed, Ms=(4, 8, 16, 32, 64, 128), Ks=(1, 2, 4, 8, 16
     res = {"full_playouts": [], "truncated": []}
     net, owned = inference_net(net, n * max(Ks))
     for M in Ms:
-        v, dt = cuda_time(lambda: env.rollout_value(seed + 100000 * M, M))
+        v, dt = cuda_time_median(lambda: env.rollout_value(seed + 100000 * M, M))
         res["full_playouts"].append({"M": M, "mae": float((v - ref).abs().mean().item()),
                                      "estimates_per_s": n / dt, "seconds": dt})
     for K in Ks:
         val = torch.empty(n, dtype=torch.float32, device="cuda")
-        _, dt = cuda_time(lambda: L.ludax_truncated_value(env.handle, net.handle, seed + 7777 + 1000 * K, K, plies,
-                                                          val))
+        _, dt = cuda_time_median(lambda: L.ludax_truncated_value(env.handle, net.handle, seed + 7777 + 1000 * K, K,
+                                                                 plies, val))
         res["truncated"].append({"K": K, "plies": plies, "mae": float((val - ref).abs().mean().item()),
                                  "estimates_per_s": n / dt, "seconds": dt})
     pnet = predict(net, pack(env, net.in_pad))
