@@ -104,5 +104,14 @@ int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, 
 // 256) + j] = sum over the j-th 256 columns of bf16(relu(.))[m][n] * w3[n].
 int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const float* bias, void* out, int ldo,
                        const void* w3, float* zpart, int M, int N, int K, cudaStream_t s);
+// Both hidden layers (512 wide) and the head in one launch for inference:
+// zpart[m * 4 + j] = sum over columns 128 j .. 128 j + 127 of
+// bf16(relu(bf16(relu(X W1^T + b1)) W2^T + b2))[m][n] * w3[n].  X [M][ldx]
+// (first K1 columns read), W1 [512][ldw1], W2 [512][512]; scratch holds
+// umma_mlp_scratch_rows() rows of 512 BF16 (layer 1's rows pass through it).
+int umma_mlp_scratch_rows();
+int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
+                  const float* b2, const void* w3, float* zpart, void* scratch, int scratch_rows, int M,
+                  cudaStream_t s);
 
 }  // namespace ludax

@@ -473,6 +473,9 @@ struct ludax_net {
     float *pout, *g3, *sqerr, *part, *score;
     uint8_t* done;
     long long part_floats;
+    __nv_bfloat16* mlp_scratch;  // layer-1 rows of the fused inference kernel (allocated on first use)
+    float* mlp_z;                // its head partials, 4 per row
+    int mlp_rows;
 };
 
 namespace {
@@ -519,13 +522,34 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
     cudaStream_t s = n->stream;
     if (kuse <= 0) kuse = n->kpad;
     if (!y && p && n->use_tcgen05 && umma_dense_supported((int)B, kH, kuse) && umma_dense_supported((int)B, kH, kH)) {
-        int st = umma_dense_relu_ex(X, n->kpad, n->W1b, n->kpad, n->p + n->ob1, n->H1, kH, nullptr, nullptr, (int)B, kH,
+        if (!n->mlp_scratch) {
+            const int rows = umma_mlp_scratch_rows();
+            if (rows > 0 && cudaMalloc(&n->mlp_scratch, sizeof(__nv_bfloat16) * (size_t)rows * kH) == cudaSuccess &&
+                cudaMalloc(&n->mlp_z, sizeof(float) * 4 * (size_t)n->max_batch) == cudaSuccess) {
+                n->mlp_rows = rows;
+            } else {  // no scratch: the two-launch form below
+                cudaGetLastError();
+                cudaFree(n->mlp_scratch);
+                n->mlp_scratch = nullptr;
+            }
+        }
+        int st, parts;
+        float* zpart;
+        if (n->mlp_scratch) {  // both layers and the head in one launch, layer 1's rows through L2
+            zpart = n->mlp_z;
+            parts = 4;
+            st = umma_mlp_head(X, n->kpad, kuse, n->W1b, n->kpad, n->p + n->ob1, n->W2b, n->p + n->ob2, n->w3b, zpart,
+                               n->mlp_scratch, n->mlp_rows, (int)B, s);
+        } else {
+            zpart = n->g3;  // 2 floats per row: g3 and sqerr are unused without labels
+            parts = kH / 256;
+            st = umma_dense_relu_ex(X, n->kpad, n->W1b, n->kpad, n->p + n->ob1, n->H1, kH, nullptr, nullptr, (int)B, kH,
                                     kuse, s);
+            if (!st)
+                st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, nullptr, 0, n->w3b, zpart, (int)B, kH, kH, s);
+        }
         if (st) return st;
-        float* zpart = n->g3;  // 2 floats per row: g3 and sqerr are unused without labels
-        if ((st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, nullptr, 0, n->w3b, zpart, (int)B, kH, kH, s)))
-            return st;
-        head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, kH / 256, n->p + n->ob3, (int)B, p);
+        head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, parts, n->p + n->ob3, (int)B, p);
         return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
     }
     int st = dense_layer(n, X, n->W1b, n->p + n->ob1, n->H1, B, n->kpad);
@@ -644,6 +668,8 @@ int ludax_net_destroy(ludax_net* n) {
     cudaFree(n->H1);
     cudaFree(n->pout);
     cudaFree(n->done);
+    if (n->mlp_scratch) cudaFree(n->mlp_scratch);
+    if (n->mlp_z) cudaFree(n->mlp_z);
     delete n;
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }

@@ -5,17 +5,18 @@
 // Persistent, warp-specialised kernel: one CTA per SM walks 128 x 256 output
 // tiles (tile t covers rows 128*(t / (N/256)) and columns 256*(t % (N/256))).
 //   warp 0    : TMA producer -- streams 128x64 (A) and 256x64 (B) K-slices
-//               (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage
+//               (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage
 //               shared-memory ring guarded by full/empty mbarriers;
 //   warp 1    : MMA issuer -- one thread issues tcgen05.mma (kind::f16,
 //               M=128, N=256, K=16) into one of two 256-column FP32
 //               accumulators in TMEM, frees ring stages with tcgen05.commit
 //               and signals the finished accumulator;
 //   warps 2-5 : epilogue -- drain the finished accumulator with tcgen05.ld
-//               (each warp its quarter of the 128 TMEM lanes = rows; the load
-//               of the next 32 columns is in flight while the current ones
+//               (each warp its quarter of the 128 TMEM lanes = rows; the loads
+//               of the next 64 columns are in flight while the current ones
 //               are converted), add the bias (staged in shared memory),
-//               ReLU, round to BF16 into a 32 x 64 shared-memory box in the
+//               ReLU, round to BF16 into 32 x 64 shared-memory boxes (two per warp,
+//               alternating, so one fills while the other drains) in the
 //               128-byte-swizzle layout (conflict-free), and store each box
 //               with one bulk tensor store (cp.async.bulk.tensor); then hand
 //               the accumulator back, so the epilogue of tile i overlaps the
@@ -33,14 +34,15 @@
 
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 64, TSTAGES = 4, UMMA_THREADS = 192;
+constexpr int TM = 128, TN = 256, TK = 64, UMMA_THREADS = 192;
 constexpr int A_TILE = TM * TK * 2, B_TILE = TN * TK * 2, STAGE = A_TILE + B_TILE;
 constexpr int TMEM_COLS = 2 * TN;  // two accumulators
 constexpr int MAX_N = 1024;        // the bias row is staged in shared memory
 constexpr int OUT_BOX = 64;        // output columns per TMA store box (128 bytes of BF16)
-constexpr int STAGING = 32 * OUT_BOX * 2;  // one 32-row box per epilogue warp, 128-byte swizzle
-constexpr int RING = TSTAGES * STAGE;
-constexpr size_t UMMA_SMEM = 1024 /* alignment */ + (size_t)RING + 4 * STAGING + 256 /* barriers */ +
+constexpr int BOX_BYTES = 32 * OUT_BOX * 2;  // one 32-row x 64-column BF16 box, 128-byte swizzle
+constexpr int DENSE_STAGES = 4;              // dense layer: ring depth; one staging box per epilogue warp
+constexpr int RING = DENSE_STAGES * STAGE;
+constexpr size_t UMMA_SMEM = 1024 /* alignment */ + (size_t)RING + 4 * BOX_BYTES + 256 /* barriers */ +
                              2 * sizeof(float) * MAX_N /* bias, head weights */;
 constexpr long long kWaitLimit = 2000000000ll;  // clock cycles (~1 s at 2 GHz)
 
@@ -86,8 +88,9 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }
-// the shared-memory sources of this thread's bulk stores may be overwritten
-__device__ __forceinline__ void tma_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// the shared-memory sources of this thread's bulk stores (all, or all but the most recent) may be overwritten
+__device__ __forceinline__ void tma_store_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_store_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory"); }
 __device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
@@ -144,6 +147,84 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t* r) {
                  : "memory");
 }
 
+// Drains NCH 32-column chunks, from chunk c0 on, of one accumulator (this
+// warp's 32 TMEM lanes = rows): the load of the next chunk is in flight
+// while the current one is converted.  For each chunk c, fn(c, v) gets this
+// lane's 32 values of relu(acc + bias) as 16 BF16 pairs.
+template <int NCH, class F>
+__device__ __forceinline__ void drain_accumulator(uint32_t base, int c0, const float* bias_n0, F&& fn) {
+    uint32_t r[2][32];
+    tmem_ld32_async(base + (uint32_t)(c0 * 32), r[0]);
+    tmem_wait_ld(r[0]);
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) {
+        const int c = c0 + i;
+        if (i + 1 < NCH) tmem_ld32_async(base + (uint32_t)((c + 1) * 32), r[(i + 1) & 1]);
+        const uint32_t* x = r[i & 1];
+        const float4* bb = reinterpret_cast<const float4*>(bias_n0 + c * 32);
+        __align__(16) __nv_bfloat162 v[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float4 b4 = bb[j];
+            v[2 * j] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j]) + b4.x, 0.f),
+                                             fmaxf(__uint_as_float(x[4 * j + 1]) + b4.y, 0.f));
+            v[2 * j + 1] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j + 2]) + b4.z, 0.f),
+                                                 fmaxf(__uint_as_float(x[4 * j + 3]) + b4.w, 0.f));
+        }
+        fn(c, v);
+        if (i + 1 < NCH) tmem_wait_ld(r[(i + 1) & 1]);
+    }
+}
+
+// <v, w[0..31]> over one chunk of BF16 activations (four partial sums, so
+// the multiply-adds are not one dependent chain)
+__device__ __forceinline__ float dot_chunk(const __nv_bfloat162* v, const float* w) {
+    const float4* ww = reinterpret_cast<const float4*>(w);
+    float z0 = 0.f, z1 = 0.f, z2 = 0.f, z3 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 w4 = ww[j];
+        const float2 f0 = __bfloat1622float2(v[2 * j]), f1 = __bfloat1622float2(v[2 * j + 1]);
+        z0 = fmaf(f0.x, w4.x, z0);
+        z1 = fmaf(f0.y, w4.y, z1);
+        z2 = fmaf(f1.x, w4.z, z2);
+        z3 = fmaf(f1.y, w4.w, z3);
+    }
+    return (z0 + z1) + (z2 + z3);
+}
+
+// One 32-column chunk of BF16 values into this lane's row of a 32 x 64
+// staging box (128-byte swizzle), and the box to global memory by TMA once
+// both of its chunks are in.  With BOXES = 2 the warp's two boxes alternate
+// (box of chunk c = (c / 2) % 2), so a box fills while the store of the
+// other is still reading it out: before a box is refilled, at most one store
+// (the other box's) may be pending.
+template <int BOXES>
+__device__ __forceinline__ void stage_chunk(int c, const __nv_bfloat162* v, uint8_t* staging_warp, int lane,
+                                            const CUtensorMap* map, int col_base, int row0) {
+    uint8_t* box = staging_warp + (BOXES == 2 ? ((c >> 1) & 1) * BOX_BYTES : 0);
+    uint8_t* myrow = box + lane * (OUT_BOX * 2);
+    const int half = c & 1;
+    if (half == 0) {
+        if (lane == 0) {
+            if (BOXES == 2) tma_store_wait_read1();
+            else tma_store_wait_read0();
+        }
+        __syncwarp();
+    }
+    const uint4* src = reinterpret_cast<const uint4*>(v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // 16-byte chunk 4*half+k of the row, swizzled with the row
+        const int chunk = (4 * half + k) ^ (lane & 7);
+        *reinterpret_cast<uint4*>(myrow + chunk * 16) = src[k];
+    }
+    if (half == 1) {  // box complete: hand it to the TMA engine
+        fence_async_shared();
+        __syncwarp();
+        if (lane == 0) tma_store_2d(map, box, col_base + (c - 1) * 32, row0);
+    }
+}
+
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
     umma_dense_relu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                            const __grid_constant__ CUtensorMap tmOut, int M, int N, int K,
@@ -152,12 +233,12 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + RING;  // 1024-byte aligned: the 128-byte swizzle pattern repeats every 1024 bytes
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING + 4 * STAGING);
-    uint64_t* empty = full + TSTAGES;
-    uint64_t* acc_full = empty + TSTAGES;  // [2] MMA -> epilogue
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + RING + 4 * BOX_BYTES);
+    uint64_t* empty = full + DENSE_STAGES;
+    uint64_t* acc_full = empty + DENSE_STAGES;  // [2] MMA -> epilogue
     uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
-    float* sbias = reinterpret_cast<float*>(smem + RING + 4 * STAGING + 256);
+    float* sbias = reinterpret_cast<float*>(smem + RING + 4 * BOX_BYTES + 256);
     float* sw3 = sbias + MAX_N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ktiles = K / TK, ntn = N / TN, ntiles = (M / TM) * ntn;
@@ -168,7 +249,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     }
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TSTAGES; ++s) {
+        for (int s = 0; s < DENSE_STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -195,8 +276,8 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const int m0 = (t / ntn) * TM, n0 = (t % ntn) * TN;
                 for (int kt = 0; kt < ktiles && ok; ++kt, ++it) {
-                    const int s = it % TSTAGES;
-                    if (it >= TSTAGES) ok = mbar_wait(&empty[s], (uint32_t)(((it / TSTAGES) & 1) ^ 1));
+                    const int s = it % DENSE_STAGES;
+                    if (it >= DENSE_STAGES) ok = mbar_wait(&empty[s], (uint32_t)(((it / DENSE_STAGES) & 1) ^ 1));
                     if (!ok) break;
                     uint8_t* st = smem + s * STAGE;
                     mbar_expect_tx(&full[s], STAGE);
@@ -215,8 +296,8 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(a * TN);
                 for (int kt = 0; kt < ktiles && ok; ++kt, ++it) {
-                    const int s = it % TSTAGES;
-                    ok = mbar_wait(&full[s], (uint32_t)((it / TSTAGES) & 1));
+                    const int s = it % DENSE_STAGES;
+                    ok = mbar_wait(&full[s], (uint32_t)((it / DENSE_STAGES) & 1));
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t sa = saddr(smem + s * STAGE);
@@ -239,60 +320,13 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             if (!ok) break;
             tc_fence_after();
             const int row0 = (t / ntn) * TM + q * 32, n0 = (t % ntn) * TN;
-            uint8_t* box = staging + q * STAGING;
-            uint8_t* myrow = box + lane * (OUT_BOX * 2);
+            uint8_t* box = staging + q * BOX_BYTES;
             const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
-            // two register sets: the load of chunk c + 1 is in flight while chunk c is converted
-            uint32_t r[2][32];
             float z = 0.f;  // fused head: this row's dot product over the tile's columns
-            tmem_ld32_async(base, r[0]);
-            tmem_wait_ld(r[0]);
-#pragma unroll
-            for (int c = 0; c < TN / 32; ++c) {
-                if (c + 1 < TN / 32) tmem_ld32_async(base + (uint32_t)((c + 1) * 32), r[(c + 1) & 1]);
-                const uint32_t* x = r[c & 1];
-                const float4* bb = reinterpret_cast<const float4*>(sbias + n0 + c * 32);
-                __align__(16) __nv_bfloat162 v[16];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float4 b4 = bb[j];
-                    v[2 * j] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j]) + b4.x, 0.f),
-                                                     fmaxf(__uint_as_float(x[4 * j + 1]) + b4.y, 0.f));
-                    v[2 * j + 1] = __floats2bfloat162_rn(fmaxf(__uint_as_float(x[4 * j + 2]) + b4.z, 0.f),
-                                                         fmaxf(__uint_as_float(x[4 * j + 3]) + b4.w, 0.f));
-                }
-                if (head) {  // the BF16 activations, as a stored row would hold them, times w3
-                    const float4* ww = reinterpret_cast<const float4*>(sw3 + n0 + c * 32);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float4 w4 = ww[j];
-                        const float2 f0 = __bfloat1622float2(v[2 * j]), f1 = __bfloat1622float2(v[2 * j + 1]);
-                        z = fmaf(f0.x, w4.x, z);
-                        z = fmaf(f0.y, w4.y, z);
-                        z = fmaf(f1.x, w4.z, z);
-                        z = fmaf(f1.y, w4.w, z);
-                    }
-                    if (c + 1 < TN / 32) tmem_wait_ld(r[(c + 1) & 1]);
-                    continue;
-                }
-                const int half = c & 1;  // which 64-byte half of the box row
-                if (half == 0) {         // the box's previous store must have read the staging buffer
-                    if (lane == 0) tma_store_wait_read();
-                    __syncwarp();
-                }
-                const uint4* src = reinterpret_cast<const uint4*>(v);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {  // 16-byte chunk 4*half+k of the row, swizzled with the row
-                    const int chunk = (4 * half + k) ^ (lane & 7);
-                    *reinterpret_cast<uint4*>(myrow + chunk * 16) = src[k];
-                }
-                if (half == 1) {  // box complete: hand it to the TMA engine
-                    fence_async_shared();
-                    __syncwarp();
-                    if (lane == 0) tma_store_2d(&tmOut, box, n0 + (c - 1) * 32, row0);
-                }
-                if (c + 1 < TN / 32) tmem_wait_ld(r[(c + 1) & 1]);
-            }
+            drain_accumulator<TN / 32>(base, 0, sbias + n0, [&](int c, const __nv_bfloat162* v) {
+                if (head) z += dot_chunk(v, sw3 + n0 + c * 32);  // the BF16 activations times w3
+                else stage_chunk<1>(c, v, box, lane, &tmOut, n0, row0);
+            });
             if (head) zpart[(size_t)(row0 + lane) * ntn + (t % ntn)] = z;
             tc_fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
@@ -300,6 +334,189 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     }
     if (!ok) atomicOr(&g_umma_error, 1);
     if (warp >= 2 && lane == 0) tma_store_wait_all();  // the epilogue's bulk stores have landed
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// --------------------------------------------- fused inference MLP --
+// Both hidden layers (N = 512) and the head for 128-row blocks in one
+// persistent launch.  For block i of this CTA, layer 1 (two 256-column
+// halves, K1 input columns) writes its BF16 rows to this CTA's scratch slot
+// i % 2 in global memory -- reused block after block, so it stays in L2 and
+// never reaches HBM -- and one block later, while the stores drain behind the
+// next block's layer 1, layer 2 reads them back through TMA and the head
+// takes each row's dot product with w3.  Jobs in order: L1(0), L1(1), L2(0),
+// L1(2), L2(1), ..., L2(nb - 1); each job is one 128 x 256 tile through a
+// 3-stage ring and two TMEM accumulators.  Draining an accumulator is the
+// slow part of a job (a 128 x 256 drain took ~2.4 us with four epilogue
+// warps, against ~1.1 us of MMAs for a K = 192 layer-1 tile), so eight
+// epilogue warps split it: warps w and w + 4 share TMEM lane quarter w % 4
+// and take one 128-column half each; a row's head therefore has four
+// partials, zpart[m * 4 + 2 * (column half of the tile) + (half of it)].
+constexpr int MLP_N = 512;
+constexpr int MLP_STAGES = 3, MLP_EPI_WARPS = 8, MLP_THREADS = 32 * (2 + MLP_EPI_WARPS);
+constexpr int MLP_STAGING = 2 * BOX_BYTES;  // per epilogue warp: two alternating boxes
+constexpr size_t MLP_SMEM = 1024 /* alignment */ + (size_t)MLP_STAGES * STAGE + MLP_EPI_WARPS * MLP_STAGING +
+                            256 /* barriers */ + 3 * sizeof(float) * MLP_N /* b1, b2, w3 */;
+
+struct MlpJob {
+    int phase, blk, h;  // layer 1 or 2, this CTA's block index, column half
+};
+__device__ __forceinline__ MlpJob mlp_job(int j, int nb) {
+    const int p = j >> 1;
+    MlpJob r;
+    r.h = j & 1;
+    if (p == 0) {
+        r.phase = 1, r.blk = 0;
+    } else if (p == 2 * nb - 1) {
+        r.phase = 2, r.blk = nb - 1;
+    } else if (p & 1) {
+        r.phase = 1, r.blk = (p + 1) >> 1;
+    } else {
+        r.phase = 2, r.blk = (p >> 1) - 1;
+    }
+    return r;
+}
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(MLP_THREADS, 1)
+    umma_mlp_head_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
+                         const __grid_constant__ CUtensorMap tmHst, const __grid_constant__ CUtensorMap tmHld,
+                         const __grid_constant__ CUtensorMap tmW2, int M, int K1, const float* __restrict__ b1,
+                         const float* __restrict__ b2, const __nv_bfloat16* __restrict__ w3,
+                         float* __restrict__ zpart) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* staging = smem + MLP_STAGES * STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + MLP_STAGES * STAGE + MLP_EPI_WARPS * MLP_STAGING);
+    uint64_t* empty = full + MLP_STAGES;
+    uint64_t* acc_full = empty + MLP_STAGES;  // [2] MMA -> epilogue
+    uint64_t* acc_empty = acc_full + 2;    // [2] epilogue -> MMA
+    uint64_t* h1_ready = acc_empty + 2;    // [2] epilogue -> producer: a scratch slot's rows are stored
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(h1_ready + 2);
+    float* sb1 = reinterpret_cast<float*>(smem + MLP_STAGES * STAGE + MLP_EPI_WARPS * MLP_STAGING + 256);
+    float* sb2 = sb1 + MLP_N;
+    float* sw3 = sb2 + MLP_N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nblk = M / TM;
+    const int nb = (int)blockIdx.x < nblk ? (nblk - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int njobs = 4 * nb, k1t = K1 / TK, k2t = MLP_N / TK;
+    for (int i = threadIdx.x; i < MLP_N; i += blockDim.x) {
+        sb1[i] = b1[i];
+        sb2[i] = b2[i];
+        sw3[i] = __bfloat162float(w3[i]);
+    }
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < MLP_STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 32 * MLP_EPI_WARPS);  // every epilogue thread arrives
+            mbar_init(&h1_ready[a], MLP_EPI_WARPS);         // lane 0 of each epilogue warp, once its stores are complete
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int scratch0 = (int)blockIdx.x * 2 * TM;  // this CTA's two slots of 128 rows
+    bool ok = true;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            int it = 0;
+            for (int j = 0; j < njobs && ok; ++j) {
+                const MlpJob jb = mlp_job(j, nb);
+                const int gblk = (int)blockIdx.x + jb.blk * (int)gridDim.x;
+                if (jb.phase == 2 && jb.h == 0) {  // layer 1's rows of this block must be in global memory
+                    ok = mbar_wait(&h1_ready[jb.blk & 1], (uint32_t)((jb.blk >> 1) & 1));
+                    if (!ok) break;
+                    fence_proxy_async_global();
+                }
+                const int kt_n = jb.phase == 1 ? k1t : k2t;
+                for (int kt = 0; kt < kt_n && ok; ++kt, ++it) {
+                    const int st = it % MLP_STAGES;
+                    if (it >= MLP_STAGES) ok = mbar_wait(&empty[st], (uint32_t)(((it / MLP_STAGES) & 1) ^ 1));
+                    if (!ok) break;
+                    uint8_t* dst = smem + st * STAGE;
+                    mbar_expect_tx(&full[st], STAGE);
+                    if (jb.phase == 1) {
+                        tma_load_2d(dst, &tmX, &full[st], kt * TK, gblk * TM);
+                        tma_load_2d(dst + A_TILE, &tmW1, &full[st], kt * TK, jb.h * TN);
+                    } else {
+                        tma_load_2d(dst, &tmHld, &full[st], kt * TK, scratch0 + (jb.blk & 1) * TM);
+                        tma_load_2d(dst + A_TILE, &tmW2, &full[st], kt * TK, jb.h * TN);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int it = 0;
+            for (int j = 0; j < njobs && ok; ++j) {
+                const int a = j & 1;
+                if (j >= 2) ok = mbar_wait(&acc_empty[a], (uint32_t)(((j >> 1) & 1) ^ 1));
+                if (!ok) break;
+                tc_fence_after();
+                const int kt_n = mlp_job(j, nb).phase == 1 ? k1t : k2t;
+                const uint32_t d = tmem + (uint32_t)(a * TN);
+                for (int kt = 0; kt < kt_n && ok; ++kt, ++it) {
+                    const int st = it % MLP_STAGES;
+                    ok = mbar_wait(&full[st], (uint32_t)((it / MLP_STAGES) & 1));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t sa = saddr(smem + st * STAGE);
+                    const uint64_t ad = sw128_desc(sa), bd = sw128_desc(sa + A_TILE);
+#pragma unroll
+                    for (int kk = 0; kk < TK / 16; ++kk) umma_bf16(d, ad + 2 * kk, bd + 2 * kk, (kt | kk) != 0);
+                    umma_commit(&empty[st]);
+                }
+                umma_commit(&acc_full[a]);
+            }
+        }
+    } else {  // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        for (int j = 0; j < njobs; ++j) {
+            const int a = j & 1;
+            if (ok) ok = mbar_wait(&acc_full[a], (uint32_t)((j >> 1) & 1));
+            ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            const MlpJob jb = mlp_job(j, nb);
+            const int gblk = (int)blockIdx.x + jb.blk * (int)gridDim.x;
+            const int n0 = jb.h * TN;
+            const bool l1 = jb.phase == 1;
+            const float* sbias = l1 ? sb1 : sb2;
+            const int srow0 = scratch0 + (jb.blk & 1) * TM + q * 32;  // layer 1's rows of this warp in scratch
+            uint8_t* box = staging + (warp - 2) * MLP_STAGING;
+            const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
+            float z = 0.f;
+            drain_accumulator<TN / 64>(base, half * (TN / 64), sbias + n0, [&](int c, const __nv_bfloat162* v) {
+                if (l1) stage_chunk<2>(c, v, box, lane, &tmHst, n0, srow0);  // layer 1: rows to scratch
+                else z += dot_chunk(v, sw3 + n0 + c * 32);                   // layer 2: the head's dot product
+            });
+            if (!l1) zpart[((size_t)gblk * TM + q * 32 + lane) * 4 + jb.h * 2 + half] = z;
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
+            if (l1 && jb.h == 1 && lane == 0) {  // both halves of this warp's rows are in global memory
+                tma_store_wait_all();
+                fence_proxy_async_global();
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&h1_ready[jb.blk & 1]))
+                             : "memory");
+            }
+        }
+    }
+    if (!ok) atomicOr(&g_umma_error, 1);
+    if (warp >= 2 && lane == 0) tma_store_wait_all();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
@@ -380,6 +597,45 @@ int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const flo
     const int grid = ntiles < sms ? ntiles : sms;
     umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias,
                                                                   static_cast<const __nv_bfloat16*>(w3), zpart);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+int umma_mlp_scratch_rows() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms * 2 * TM;
+}
+
+int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
+                  const float* b2, const void* w3, float* zpart, void* scratch, int scratch_rows, int M,
+                  cudaStream_t s) {
+    if (M <= 0 || M % TM || K1 <= 0 || K1 % TK || K1 > ldx || K1 > ldw1 || ldx % 8 || ldw1 % 8 || !zpart ||
+        !scratch || ((uintptr_t)X % 16) || ((uintptr_t)W1 % 16) || ((uintptr_t)W2 % 16) || ((uintptr_t)scratch % 16))
+        return LUDAX_ERR_SIZE;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return LUDAX_ERR_CUDA;
+    }
+    const int nblk = M / TM, grid = nblk < sms ? nblk : sms;
+    if (scratch_rows < grid * 2 * TM) return LUDAX_ERR_SIZE;
+    CUtensorMap mx, mw1, mhs, mhl, mw2;
+    if (!make_map(&mx, X, M, K1, TM, ldx) || !make_map(&mw1, W1, MLP_N, K1, TN, ldw1) ||
+        !make_map(&mhs, scratch, scratch_rows, MLP_N, 32, MLP_N) || !make_map(&mhl, scratch, scratch_rows, MLP_N, TM, MLP_N) ||
+        !make_map(&mw2, W2, MLP_N, MLP_N, TN, MLP_N))
+        return LUDAX_ERR_CUDA;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(umma_mlp_head_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM) !=
+            cudaSuccess)
+            return LUDAX_ERR_CUDA;
+        attr = true;
+    }
+    umma_mlp_head_kernel<<<grid, MLP_THREADS, MLP_SMEM, s>>>(mx, mw1, mhs, mhl, mw2, M, K1, b1, b2,
+                                                              static_cast<const __nv_bfloat16*>(w3), zpart);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 

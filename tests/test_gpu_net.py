@@ -180,3 +180,64 @@ def test_truncated_value_matches_oracle(L, name, game, rows, cols):
         want += np.where(t.outcome >= 0, res, p)
     want /= Kc
     assert np.abs(val - want).max() < 5e-4
+
+
+def subset(s, idx):
+    """The positions idx of a States batch, as a new batch."""
+    t = G.States(s.game, s.rows, s.cols, len(idx))
+    for k in ("board", "to_move", "ply", "passes", "outcome"):
+        setattr(t, k, np.ascontiguousarray(getattr(s, k)[idx]))
+    return t
+
+
+@pytest.mark.parametrize("cells", [64, 121])
+def test_forward_large_batch_sampled(L, cells):
+    """Inference at a batch where every CTA of the persistent launch runs
+    several 128-row blocks (595 blocks over at most 148 SMs, a ragged last
+    round): sampled rows from every part of the batch against the oracle."""
+    B = 595 * 128
+    K = W.net_in_pad(cells)
+    theta = W.init_params(cells, 11)
+    theta[M.num_params(K) - 1] = -0.05
+    rng = np.random.default_rng(cells + 1)
+    X = np.zeros((B, K), np.float32)
+    X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
+    net = L.Net(cells, B)
+    net.set_params(torch.from_numpy(theta).cuda())
+    p = net.forward(bf16_bits(X)).cpu().numpy()
+    assert L.ludax_device_error() == 0
+    idx = np.unique(np.concatenate([np.arange(0, B, 211), np.arange(B - 128, B), np.arange(148 * 128, 150 * 128)]))
+    ref = forward_bf16(theta, X[idx].astype(np.float64), K)
+    assert np.abs(p[idx] - ref).max() < 5e-4
+    assert np.isfinite(p).all() and (p > 0).all() and (p < 1).all()
+
+
+def test_truncated_value_large_batch_sampled(L):
+    """The truncated estimator with K * n rows spanning many blocks per CTA
+    (Othello: only the first 192 input columns are read): sampled positions
+    against the oracle, each replayed with its own env index."""
+    game, rows, cols, n, Kc, plies, seed = G.OTHELLO, 8, 8, 24000, 4, 8, 123
+    cells = rows * cols
+    K = W.net_in_pad(cells)
+    s = positions(game, rows, cols, n, 6)
+    env = L.Env(game, rows, cols, n, env_offset=3)
+    env.set_state(*(torch.from_numpy(x) for x in (s.board, s.to_move, s.ply, s.passes, s.outcome)))
+    theta = W.init_params(cells, 12)
+    net = L.Net(cells, n * Kc)
+    net.set_params(torch.from_numpy(theta).cuda())
+    val = torch.empty(n, dtype=torch.float32, device="cuda")
+    L.ludax_truncated_value(env.handle, net.handle, seed, Kc, plies, val)
+    val = val.cpu().numpy()
+    assert L.ludax_device_error() == 0
+    idx = np.unique(np.concatenate([np.arange(0, n, 397), np.arange(n - 8, n)]))
+    want = np.zeros(len(idx))
+    for j in range(Kc):
+        for r, e in enumerate(idx):
+            t = subset(s, [e])
+            G.rollout_from(t, seed=seed + j, env_offset=3 + int(e), stop_ply=(t.ply + plies).astype(np.int16))
+            if t.outcome[0] >= 0:
+                want[r] += 1.0 if t.outcome[0] == 1 else (0.0 if t.outcome[0] == 2 else 0.5)
+            else:
+                want[r] += forward_bf16(theta, M.encode(t.board, t.to_move, K), K)[0]
+    want /= Kc
+    assert np.abs(val[idx] - want).max() < 5e-4
