@@ -5,18 +5,17 @@
 // Persistent, warp-specialised kernel: one CTA per SM walks 128 x 256 output
 // tiles (tile t covers rows 128*(t / (N/256)) and columns 256*(t % (N/256))).
 //   warp 0    : TMA producer -- streams 128x64 (A) and 256x64 (B) K-slices
-//               (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage
+//               (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage
 //               shared-memory ring guarded by full/empty mbarriers;
 //   warp 1    : MMA issuer -- one thread issues tcgen05.mma (kind::f16,
 //               M=128, N=256, K=16) into one of two 256-column FP32
 //               accumulators in TMEM, frees ring stages with tcgen05.commit
 //               and signals the finished accumulator;
 //   warps 2-5 : epilogue -- drain the finished accumulator with tcgen05.ld
-//               (each warp its quarter of the 128 TMEM lanes = rows; the loads
-//               of the next 64 columns are in flight while the current ones
+//               (each warp its quarter of the 128 TMEM lanes = rows; the load
+//               of the next 32 columns is in flight while the current ones
 //               are converted), add the bias (staged in shared memory),
-//               ReLU, round to BF16 into 32 x 64 shared-memory boxes (two per warp,
-//               alternating, so one fills while the other drains) in the
+//               ReLU, round to BF16 into a 32 x 64 shared-memory box in the
 //               128-byte-swizzle layout (conflict-free), and store each box
 //               with one bulk tensor store (cp.async.bulk.tensor); then hand
 //               the accumulator back, so the epilogue of tile i overlaps the
