@@ -64,7 +64,8 @@ def parse():
                                                         "line_c5", "wolf_sheep", "draughts", "hasami_shogi", "mixed",
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net"], default=None,
+    p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net", "value_estimator"],
+                   default=None,
                    help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-valuenet", action="store_true", help="skip the value-net (config 5) extra")
@@ -505,6 +506,35 @@ def bench_valuenet():
     return out
 
 
+def bench_value_estimator(n=100_000):
+    """The truncated estimator alone (8 random plies, then the net; Othello
+    K = 8, Hex 11 K = 1, the continuation counts that reach MAE 0.05 with the
+    trained net) on n sampled positions with an untrained net of the same
+    shape: its speed does not depend on the weights.  A small case for
+    profilers; value_net measures the same path after training."""
+    import torch
+
+    from paper_2506_22609_b300 import ludax as L
+    from paper_2506_22609_b300 import valuenet as V
+    from paper_2506_22609_b300 import workloads as W
+
+    out = {}
+    for game, K in (("othello", 8), ("hex11", 1)):
+        g, rows, cols = V.GAMES[game]
+        env, _ = V.sample_positions(g, rows, cols, n, 5, 0)
+        net = L.Net(rows * cols, 65536)
+        net.set_params(torch.from_numpy(W.init_params(rows * cols, 5)).cuda())
+        inet, owned = V.inference_net(net, n * K)
+        val = torch.empty(n, dtype=torch.float32, device="cuda")
+        _, dt = V.cuda_time_median(lambda: L.ludax_truncated_value(env.handle, inet.handle, 77, K, 8, val))
+        out[game] = {"K": K, "plies": 8, "positions": n, "rows": n * K, "seconds": dt, "estimates_per_s": n / dt}
+        if owned:
+            inet.close()
+        net.close()
+        env.close()
+    return out
+
+
 # ------------------------------------------------------------------ main --
 def main():
     args = parse()
@@ -539,6 +569,8 @@ def main():
             res = bench_gavel()
         elif args.only == "value_net":
             res = bench_valuenet()
+        elif args.only == "value_estimator":
+            res = bench_value_estimator()
         else:
             res = bench_batch_sweep(L, W, flush_buf)
         if rank == 0:
