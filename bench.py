@@ -475,12 +475,11 @@ def bench_dense(L, peaks, flush_buf, M=65536, N=512, K=512):
     net = L.Net(64, M)
     x = torch.zeros(M, net.in_pad, dtype=torch.int16, device="cuda")
     flops = 2.0 * M * (net.in_pad * 512 + 512 * 512 + 512)
-    for path in (True, False):
+    for path, name in ((1, "tcgen05_one_launch"), (2, "tcgen05_two_launches"), (0, "mma_sync")):
         net.set_tensor_path(path)
         msf = time_steps(lambda: net.forward(x), 10, 2, flush_buf, torch.cuda.current_stream())
         tf = statistics.median(msf) / 1e3
-        res["net_forward_" + ("tcgen05" if path else "mma_sync")] = {"median_ms": round(tf * 1e3, 4),
-                                                                    "tflops": round(flops / tf / 1e12, 1)}
+        res["net_forward_" + name] = {"median_ms": round(tf * 1e3, 4), "tflops": round(flops / tf / 1e12, 1)}
     net.close()
     return res
 

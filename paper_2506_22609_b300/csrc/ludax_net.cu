@@ -461,7 +461,7 @@ unsigned blocks_for(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 struct ludax_net {
     int cells, kin, kpad;
-    int use_tcgen05;  // forward layers on tcgen05 (1, default) or mma.sync (0)
+    int use_tcgen05;  // forward layers on tcgen05 (1, default; 2: never the one-launch MLP) or mma.sync (0)
     long long max_batch;
     cudaStream_t stream;
     long long nparams;
@@ -522,7 +522,7 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
     cudaStream_t s = n->stream;
     if (kuse <= 0) kuse = n->kpad;
     if (!y && p && n->use_tcgen05 && umma_dense_supported((int)B, kH, kuse) && umma_dense_supported((int)B, kH, kH)) {
-        if (!n->mlp_scratch) {
+        if (!n->mlp_scratch && n->use_tcgen05 == 1) {
             const int rows = umma_mlp_scratch_rows();
             if (rows > 0 && cudaMalloc(&n->mlp_scratch, sizeof(__nv_bfloat16) * (size_t)rows * kH) == cudaSuccess &&
                 cudaMalloc(&n->mlp_z, sizeof(float) * 4 * (size_t)n->max_batch) == cudaSuccess) {
@@ -535,7 +535,7 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
         }
         int st, parts;
         float* zpart;
-        if (n->mlp_scratch) {  // both layers and the head in one launch, layer 1's rows through L2
+        if (n->mlp_scratch && n->use_tcgen05 == 1) {  // both layers and the head in one launch, layer 1's rows through L2
             zpart = n->mlp_z;
             parts = 4;
             st = umma_mlp_head(X, n->kpad, kuse, n->W1b, n->kpad, n->p + n->ob1, n->W2b, n->p + n->ob2, n->w3b, zpart,
@@ -692,7 +692,7 @@ int ludax_net_set_params(ludax_net* n, const float* params_dev) {
 }
 
 int ludax_net_set_tensor_path(ludax_net* n, int32_t use_tcgen05) {
-    if (!n || (use_tcgen05 != 0 && use_tcgen05 != 1)) return LUDAX_ERR_ARG;
+    if (!n || use_tcgen05 < 0 || use_tcgen05 > 2) return LUDAX_ERR_ARG;
     n->use_tcgen05 = use_tcgen05;
     return LUDAX_OK;
 }

@@ -426,8 +426,11 @@ class Net:
     def set_params(self, params):
         ludax_net_set_params(self.handle, params.to(torch.float32).contiguous())
 
-    def set_tensor_path(self, use_tcgen05: bool):
-        _check(lib().ludax_net_set_tensor_path(self.handle, 1 if use_tcgen05 else 0), "ludax_net_set_tensor_path")
+    def set_tensor_path(self, use_tcgen05):
+        """True / 1: tcgen05 (one-launch MLP for inference), 2: tcgen05 as two
+        layer launches, False / 0: mma.sync."""
+        mode = int(use_tcgen05) if not isinstance(use_tcgen05, bool) else (1 if use_tcgen05 else 0)
+        _check(lib().ludax_net_set_tensor_path(self.handle, mode), "ludax_net_set_tensor_path")
 
     def get_params(self):
         p = torch.empty(self.num_params, dtype=torch.float32, device="cuda")

@@ -83,8 +83,8 @@ def test_forward_matches_oracle(L, cells, B):
     net.set_params(torch.from_numpy(theta).cuda())
     ref = forward_bf16(theta, X, K)
     exact, _ = M.forward(theta.astype(np.float64), X, K)
-    for tcgen05 in (True, False):
-        net.set_tensor_path(tcgen05)
+    for path in (1, 2, 0):  # one-launch tcgen05 MLP, tcgen05 layer by layer, mma.sync
+        net.set_tensor_path(path)
         p = net.forward(bf16_bits(X)).cpu().numpy()
         assert np.abs(p - ref).max() < 5e-4
         assert np.abs(p - exact).max() < 2e-2
@@ -204,12 +204,15 @@ def test_forward_large_batch_sampled(L, cells):
     X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
     net = L.Net(cells, B)
     net.set_params(torch.from_numpy(theta).cuda())
-    p = net.forward(bf16_bits(X)).cpu().numpy()
-    assert L.ludax_device_error() == 0
     idx = np.unique(np.concatenate([np.arange(0, B, 211), np.arange(B - 128, B), np.arange(148 * 128, 150 * 128)]))
     ref = forward_bf16(theta, X[idx].astype(np.float64), K)
-    assert np.abs(p[idx] - ref).max() < 5e-4
-    assert np.isfinite(p).all() and (p > 0).all() and (p < 1).all()
+    xb = bf16_bits(X)
+    for path in (1, 2):  # one launch with layer 1 through L2; two layer launches
+        net.set_tensor_path(path)
+        p = net.forward(xb).cpu().numpy()
+        assert L.ludax_device_error() == 0
+        assert np.abs(p[idx] - ref).max() < 5e-4
+        assert np.isfinite(p).all() and (p > 0).all() and (p < 1).all()
 
 
 def test_truncated_value_large_batch_sampled(L):
