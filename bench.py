@@ -64,7 +64,8 @@ def parse():
                                                         "line_c5", "wolf_sheep", "draughts", "hasami_shogi", "mixed",
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
-    p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net", "value_estimator"],
+    p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net", "value_estimator",
+                                      "int_peak"],
                    default=None,
                    help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -505,6 +506,40 @@ def bench_valuenet():
     return out
 
 
+def bench_int_peak(L, iters=1 << 16):
+    """What a stream of one integer op reaches (LOP3, IADD, SHF; 8 independent
+    chains per thread, every SM fully occupied), against the issue peak (4
+    warp instructions per clock per SM) and the ALU pipe's half of it: the
+    denominators of the playouts' roofline."""
+    import torch
+
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    out = {}
+    with ClockSampler(dev) as clk:
+        for kind in ("lop3", "iadd", "shf"):
+            ms = []
+            for i in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ops = L.ludax_int_peak(kind, iters)
+                b.record()
+                torch.cuda.synchronize()
+                if i:
+                    ms.append(a.elapsed_time(b))
+            t = statistics.median(ms) / 1e3
+            out[kind] = {"tops": round(ops / t / 1e12, 3), "ms": round(t * 1e3, 3), "ops": ops}
+    rec = clk.record()
+    mhz = rec["sm_mhz"] or rec["sm_max_mhz"] or 2032
+    issue = props.multi_processor_count * 128 * mhz * 1e6 / 1e12
+    out["clocks"] = rec
+    out["issue_peak_tops"] = round(issue, 3)
+    out["alu_pipe_peak_tops"] = round(issue / 2, 3)
+    for kind in ("lop3", "iadd", "shf"):
+        out[kind]["frac_of_issue_peak"] = round(out[kind]["tops"] / issue, 3)
+    return out
+
+
 def bench_value_estimator(n=100_000):
     """The truncated estimator alone (8 random plies, then the net; Othello
     K = 8, Hex 11 K = 1, the continuation counts that reach MAE 0.05 with the
@@ -570,6 +605,8 @@ def main():
             res = bench_valuenet()
         elif args.only == "value_estimator":
             res = bench_value_estimator()
+        elif args.only == "int_peak":
+            res = bench_int_peak(L)
         else:
             res = bench_batch_sweep(L, W, flush_buf)
         if rank == 0:

@@ -477,6 +477,14 @@ int ludax_dense_bf16_relu(const uint16_t* a_dev, const uint16_t* b_dev, const fl
  * an internal wait since the last call; error_out (nullable) gets the word. */
 int ludax_device_error(int32_t* error_out);
 
+/* Integer-issue microbenchmark behind the playouts' roofline: one launch
+ * over every SM at full occupancy in which each thread issues `iters` x 8
+ * independent 32-bit ops of one kind -- 0 LOP3 (3-input logic), 1 IADD
+ * (add.u32), 2 SHF (funnel shift) -- as inline PTX.  ops_out (host,
+ * nullable) gets the number of thread-level ops; time the launch on
+ * `stream` (asynchronous).  iters in 1 .. 2^30; LUDAX_ERR_ARG otherwise. */
+int ludax_int_peak(int32_t kind, int64_t iters, int64_t* ops_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

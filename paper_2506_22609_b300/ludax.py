@@ -123,6 +123,7 @@ def lib() -> ctypes.CDLL:
         "ludax_truncated_value": [vp, vp, u64, i32, i32, vp],
         "ludax_dense_bf16_relu": [vp, vp, vp, vp, i32, i32, i32, i32, vp],
         "ludax_device_error": [P(i32)],
+        "ludax_int_peak": [i32, i64, P(i64), vp],
         "ludax_mcts_reserve": [vp, i32, ctypes.c_double],
         "ludax_mcts_search": [vp, u64, i32, ctypes.c_double, vp, vp, vp],
         "ludax_mcts_play": [vp, u64, u32, i32, i32, ctypes.c_double, vp, vp, vp, vp],
@@ -402,6 +403,16 @@ def ludax_device_error():
     e = ctypes.c_int32()
     lib().ludax_device_error(ctypes.byref(e))
     return e.value
+
+
+INT_PEAK_KINDS = {"lop3": 0, "iadd": 1, "shf": 2}
+
+
+def ludax_int_peak(kind: str, iters: int, stream=None) -> int:
+    """Launch the integer-issue microbenchmark; returns the number of ops."""
+    ops = ctypes.c_int64()
+    _check(lib().ludax_int_peak(INT_PEAK_KINDS[kind], iters, ctypes.byref(ops), _stream(stream)), "ludax_int_peak")
+    return ops.value
 
 
 class Net:

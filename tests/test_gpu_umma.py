@@ -51,3 +51,14 @@ def test_dense_relu_rejects_unsupported_shapes(L):
     with pytest.raises(L.LudaxError) as ei:
         L.ludax_dense_bf16_relu(a, b, torch.zeros(256, device="cuda"), out)
     assert ei.value.status == -3
+
+
+@pytest.mark.parametrize("kind", ["lop3", "iadd", "shf"])
+def test_int_peak_microbenchmark_runs(L, kind):
+    """The integer-issue microbenchmark counts its ops exactly and finishes."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ops = L.ludax_int_peak(kind, 64)
+    torch.cuda.synchronize()
+    assert ops == sms * 8 * 256 * 8 * 64
+    with pytest.raises(L.LudaxError):
+        L.ludax_int_peak(kind, 0)
