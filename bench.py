@@ -194,6 +194,41 @@ def cpu_oracle_rate(cfg, seconds, desc=None):
     return steps / dt, cores, f"first {n} of {total_envs} envs (global ids 0..{n - 1}), {cores} threads, {dt:.2f} s"
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_single_thread(cfg, seconds, desc=None):
+    """The same oracle on one host thread (about `seconds`): steps/s and sample."""
+    import numpy as np
+
+    from oracle import games as OG
+
+    def run(n):
+        if desc is not None:
+            _, p = OG.rollout_mixed(desc[:n], cfg.seed, env_offset=0)
+        else:
+            gid = cfg.game if cfg.game != 7 else 7 | (cfg.line << 8) | (cfg.flags << 12)
+            _, p, _ = OG.rollout_start(gid, cfg.rows, cfg.cols, n, cfg.seed, env_offset=0)
+        return int(p.astype(np.int64).sum())
+
+    t0 = time.perf_counter()
+    run(128)
+    per_env = max((time.perf_counter() - t0) / 128, 1e-7)
+    n = int(min(cfg.num_envs, max(128, seconds / per_env)))
+    t0 = time.perf_counter()
+    steps = run(n)
+    dt = time.perf_counter() - t0
+    return steps / dt, f"first {n} envs, 1 thread, {dt:.2f} s"
+
+
 # ------------------------------------------------------------- GPU parts --
 def D_shard(rank, n):
     from paper_2506_22609_b300 import dist as D
@@ -685,16 +720,20 @@ def main():
                                "-> pinned host outcome/plies; two streams alternate so step i+1's upload overlaps "
                                "step i's playouts; wall clock over all steps"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        desc = None
         if args.workload == "step_c4":
-            v, cores, sample = cpu_oracle_rate(W.C4_64K, args.cpu_seconds)
-            sample = "Connect Four playouts: " + sample
+            ccfg = W.C4_64K
         elif cfg is not None:
-            v, cores, sample = cpu_oracle_rate(cfg, args.cpu_seconds)
+            ccfg = cfg
         else:
-            v, cores, sample = cpu_oracle_rate(W_mixed_cfg(W), args.cpu_seconds,
-                                               desc=W.mixed_descriptors(W.MIXED_ENVS, "block"))
+            ccfg, desc = W_mixed_cfg(W), W.mixed_descriptors(W.MIXED_ENVS, "block")
+        v, cores, sample = cpu_oracle_rate(ccfg, args.cpu_seconds, desc=desc)
+        v1, sample1 = cpu_oracle_single_thread(ccfg, min(2.0, args.cpu_seconds / 4), desc=desc)
+        if args.workload == "step_c4":
+            sample = "Connect Four playouts: " + sample
         line["cpu_baseline"] = {"value": round(v, 1), "unit": "env steps/s", "cores": cores, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "cpu_model": cpu_model(),
+                                "single_thread": {"value": round(v1, 1), "sample": sample1}}
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {}
         for name in ("ttt", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5", "wolf_sheep", "draughts",
