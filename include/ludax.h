@@ -227,6 +227,22 @@ int ludax_random_step(ludax_env* env, uint64_t seed, float* rewards_dev, uint8_t
 int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* stop_ply_dev, int8_t* outcome_dev,
                   int16_t* plies_dev, const ludax_launch_cfg* cfg);
 
+/* ludax_rollout_host: ludax_rollout for positions held on the host -- the
+ * whole round trip in one call.  Enqueues on the env's stream, in order: the
+ * copy of the packed state (planes_host uint64 [words_per_env][num_envs],
+ * meta_host uint32 [num_envs]; the layout of ludax_get_state_bits) to device
+ * staging owned by the env, loading it as ludax_set_state_bits does, the
+ * playout of every env to its end (seed, launch shape cfg, nullable), and the
+ * copies of outcome_host int8 [num_envs] and plies_host int16 [num_envs] back;
+ * returns without waiting (ludax_sync, or the stream, tells when the outputs
+ * are in place).  Host buffers should be page-locked for the copies to run
+ * asynchronously.  The staging (num_envs x (8 x words_per_env + 7) bytes)
+ * is allocated on the first call and kept until ludax_env_destroy; growing
+ * it synchronises the stream.  The env's state afterwards is the loaded
+ * positions (the playouts do not write back). */
+int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32_t* meta_host, uint64_t seed,
+                       int8_t* outcome_host, int16_t* plies_host, const ludax_launch_cfg* cfg);
+
 /* ludax_rollout_value: for every env, R independent uniform-random playouts
  * from its current state; playout j (0 <= j < R) draws with seed + j.
  *   value_dev float32 [num_envs]: mean result from P1's view (win 1, draw
@@ -240,6 +256,25 @@ int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_d
  * form (bitboards, Hex edge-connected sets) from the cell values.          */
 int ludax_get_state(ludax_env* env, const ludax_state_view* dst);
 int ludax_set_state(ludax_env* env, const ludax_state_view* src);
+
+/* Packed form of the same canonical state, for moving many positions at
+ * two bits per cell instead of a byte (a library interface; the paper's
+ * environments hold the board as arrays):
+ *   planes_dev uint64 [words_per_env][num_envs] (plane-major across envs):
+ *              V planes, one per nonzero cell value v = 1 .. V (V = 4 for
+ *              Draughts -- men 1/2, kings 3/4 -- else 2), each W =
+ *              ceil(cells / 64) words in canonical cell order: bit c % 64 of
+ *              word (v - 1) * W + c / 64 is set iff cell c holds v
+ *   meta_dev   uint32 [num_envs]: ply (bits 0-15) | (to_move - 1) << 16 |
+ *              the state view's passes byte << 17 | (outcome + 1) << 25
+ * words_per_env = V * W (ludax_state_bits_words).  set_state_bits ignores
+ * bits past the last cell and, like set_state, validates nothing about
+ * reachability; both are asynchronous on the env's stream.  LUDAX_ERR_ARG
+ * on null pointers, LUDAX_ERR_ALIGN unless planes are 8- and meta 4-byte
+ * aligned. */
+int ludax_state_bits_words(const ludax_env* env, int32_t* words_per_env);
+int ludax_get_state_bits(ludax_env* env, uint64_t* planes_dev, uint32_t* meta_dev);
+int ludax_set_state_bits(ludax_env* env, const uint64_t* planes_dev, const uint32_t* meta_dev);
 
 /* ludax_counters: host-visible totals since creation (synchronises the
  * env's stream): illegal actions seen by ludax_step, envs that hit the ply

@@ -203,6 +203,108 @@ __global__ void set_state_kernel(EnvDev d, ludax_state_view v) {
     }
 }
 
+// ------------------------------------------------- packed state view --
+// Per env: V planes (cell value v = 1 .. V; V = 2, or 4 with Draughts'
+// kings) of W = ceil(cells / 64) words each in canonical cell order, stored
+// plane-major across envs (word w of plane v - 1 of env e at
+// planes[((v - 1) * W + w) * n + e]), and one meta word:
+// ply | (to_move - 1) << 16 | passes byte << 17 | (outcome + 1) << 25.
+__device__ __forceinline__ uint32_t pack_state_meta(int ply, int side, int passes_byte, int outcome) {
+    return (uint32_t)(ply & 0xFFFF) | ((uint32_t)(side & 1) << 16) | ((uint32_t)(passes_byte & 0xFF) << 17) |
+           ((uint32_t)((outcome + 1) & 7) << 25);
+}
+
+template <class G>
+__global__ void get_state_bits_kernel(EnvDev d, uint64_t* planes, uint32_t* meta, int W, int V) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    load_state(g, d, e);
+    int pb = g.passes;
+    if constexpr (IsMove<G>::value) {
+        for (int v = 1; v <= V; ++v)
+            for (int w = 0; w < W; ++w) {
+                uint64_t x = 0;
+                for (int j = 0; j < 64 && 64 * w + j < d.cells; ++j)
+                    if (g.cell_value(64 * w + j) == v) x |= 1ull << j;
+                planes[((int64_t)(v - 1) * W + w) * d.n + e] = x;
+            }
+        pb = g.extra();
+    } else {
+        const typename G::Mask& p1 = g.side == 0 ? g.own : g.opp;
+        const typename G::Mask& p2 = g.side == 0 ? g.opp : g.own;
+        for (int w = 0; w < W; ++w) {
+            planes[(int64_t)w * d.n + e] = canon_mask_word(g, p1, w);
+            planes[(int64_t)(W + w) * d.n + e] = canon_mask_word(g, p2, w);
+        }
+        if constexpr (G::kGame == Pente::kGame) {
+            const int c1 = g.side == 0 ? g.caps_own : g.caps_opp, c2 = g.side == 0 ? g.caps_opp : g.caps_own;
+            pb = (c1 & 15) | ((c2 & 15) << 4);
+        }
+    }
+    meta[e] = pack_state_meta(g.ply, g.side, pb, g.outcome);
+}
+
+template <class G>
+__global__ void set_state_bits_kernel(EnvDev d, const uint64_t* planes, const uint32_t* meta, int W, int V) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    const uint32_t m = meta[e];
+    const int ply = (int)(m & 0xFFFF), side = (int)((m >> 16) & 1), pb = (int)((m >> 17) & 0xFF);
+    const int outcome = (int)((m >> 25) & 7) - 1;
+    G g;
+    set_table(g, nullptr);
+    configure(g, d.desc);
+    if constexpr (IsMove<G>::value) {
+        g.reset();
+        g.clear();
+        g.side = side;  // the pieces are kept relative to the side to move
+        for (int v = 1; v <= V; ++v)
+            for (int w = 0; w < W; ++w)
+                for (uint64_t x = planes[((int64_t)(v - 1) * W + w) * d.n + e]; x; x &= x - 1) {
+                    const int c = 64 * w + __ffsll((long long)x) - 1;
+                    if (c < d.cells) g.set_cell(c, v);
+                }
+        g.ply = ply;
+        g.passes = 0;
+        g.outcome = outcome;
+        g.set_extra(pb);
+        g.refresh();
+    } else {
+        typename G::Mask p1{}, p2{};
+        for (int w = 0; w < W; ++w) {
+            for (uint64_t x = planes[(int64_t)w * d.n + e]; x; x &= x - 1) {
+                const int c = 64 * w + __ffsll((long long)x) - 1;
+                if (c < d.cells) set_bit(p1, g.bit_of(c));
+            }
+            for (uint64_t x = planes[(int64_t)(W + w) * d.n + e]; x; x &= x - 1) {
+                const int c = 64 * w + __ffsll((long long)x) - 1;
+                if (c < d.cells) set_bit(p2, g.bit_of(c));
+            }
+        }
+        g.side = side;
+        g.ply = ply;
+        g.passes = pb;
+        g.outcome = outcome;
+        g.own = side == 0 ? p1 : p2;
+        g.opp = side == 0 ? p2 : p1;
+        if constexpr (G::kGame == Pente::kGame) {
+            g.passes = 0;
+            g.caps_own = side == 0 ? (pb & 15) : (pb >> 4);
+            g.caps_opp = side == 0 ? (pb >> 4) : (pb & 15);
+        }
+        if constexpr (HexN<G>::value != 0) g.rebuild();
+    }
+    store_state(g, d, e);
+}
+
+// words per plane and planes of the packed state view
+void state_bits_shape(const ludax_env* env, int* W, int* V) {
+    *W = (env->cells + 63) / 64;
+    *V = env->game == LUDAX_GAME_DRAUGHTS ? 4 : 2;
+}
+
 // ----------------------------------------------------- fused playouts --
 struct RolloutArgs {
     EnvDev d;
@@ -570,6 +672,7 @@ int ludax_env_destroy(ludax_env* env) {
     cudaFree(env->d_counters);
     cudaFree(env->d_tree);
     cudaFree(env->d_ucb);
+    cudaFree(env->d_stage);
     delete env;
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
@@ -652,6 +755,41 @@ int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* 
     });
 }
 
+int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32_t* meta_host, uint64_t seed,
+                       int8_t* outcome_host, int16_t* plies_host, const ludax_launch_cfg* cfg) {
+    if (!env || !planes_host || !meta_host || !outcome_host || !plies_host) return LUDAX_ERR_ARG;
+    int W, V;
+    state_bits_shape(env, &W, &V);
+    const size_t n = (size_t)env->n, pbytes = (size_t)W * V * n * 8;
+    // staging: planes (8-byte aligned), meta, plies (2-byte aligned), outcome
+    const size_t need = pbytes + 4 * n + 2 * n + n;
+    if (env->stage_bytes < need) {
+        if (cudaStreamSynchronize(env->stream) != cudaSuccess) return LUDAX_ERR_CUDA;  // a previous call may still use it
+        cudaFree(env->d_stage);
+        env->d_stage = nullptr;
+        env->stage_bytes = 0;
+        if (cudaMalloc(&env->d_stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return LUDAX_ERR_NOMEM;
+        }
+        env->stage_bytes = need;
+    }
+    uint64_t* dp = reinterpret_cast<uint64_t*>(env->d_stage);
+    uint32_t* dm = reinterpret_cast<uint32_t*>(env->d_stage + pbytes);
+    int16_t* dpl = reinterpret_cast<int16_t*>(env->d_stage + pbytes + 4 * n);
+    int8_t* dout = reinterpret_cast<int8_t*>(env->d_stage + pbytes + 6 * n);
+    if (cudaMemcpyAsync(dp, planes_host, pbytes, cudaMemcpyHostToDevice, env->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dm, meta_host, 4 * n, cudaMemcpyHostToDevice, env->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    int st = ludax_set_state_bits(env, dp, dm);
+    if (st) return st;
+    if ((st = ludax_rollout(env, seed, 0, nullptr, dout, dpl, cfg))) return st;
+    if (cudaMemcpyAsync(outcome_host, dout, n, cudaMemcpyDeviceToHost, env->stream) != cudaSuccess ||
+        cudaMemcpyAsync(plies_host, dpl, 2 * n, cudaMemcpyDeviceToHost, env->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    return LUDAX_OK;
+}
+
 int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_dev, const ludax_launch_cfg* cfg) {
     if (!env || !value_dev || R < 1) return LUDAX_ERR_ARG;
     if (!aligned(value_dev, 4)) return LUDAX_ERR_ALIGN;
@@ -689,6 +827,38 @@ int ludax_set_state(ludax_env* env, const ludax_state_view* src) {
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         set_state_kernel<G><<<grid_for(env->n, 128), 128, 0, env->stream>>>(dev_of(env), v);
+        return launch_status();
+    });
+}
+
+int ludax_state_bits_words(const ludax_env* env, int32_t* words_per_env) {
+    if (!env || !words_per_env) return LUDAX_ERR_ARG;
+    int W, V;
+    state_bits_shape(env, &W, &V);
+    *words_per_env = W * V;
+    return LUDAX_OK;
+}
+
+int ludax_get_state_bits(ludax_env* env, uint64_t* planes_dev, uint32_t* meta_dev) {
+    if (!env || !planes_dev || !meta_dev) return LUDAX_ERR_ARG;
+    if (!aligned(planes_dev, 8) || !aligned(meta_dev, 4)) return LUDAX_ERR_ALIGN;
+    int W, V;
+    state_bits_shape(env, &W, &V);
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        get_state_bits_kernel<G><<<grid_for(env->n, 128), 128, 0, env->stream>>>(dev_of(env), planes_dev, meta_dev, W, V);
+        return launch_status();
+    });
+}
+
+int ludax_set_state_bits(ludax_env* env, const uint64_t* planes_dev, const uint32_t* meta_dev) {
+    if (!env || !planes_dev || !meta_dev) return LUDAX_ERR_ARG;
+    if (!aligned(planes_dev, 8) || !aligned(meta_dev, 4)) return LUDAX_ERR_ALIGN;
+    int W, V;
+    state_bits_shape(env, &W, &V);
+    return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
+        using G = typename decltype(tag)::type;
+        set_state_bits_kernel<G><<<grid_for(env->n, 128), 128, 0, env->stream>>>(dev_of(env), planes_dev, meta_dev, W, V);
         return launch_status();
     });
 }

@@ -20,6 +20,8 @@ struct ludax_env {
     double* d_ucb;                   // UCB1 table T[m] = c * sqrt(ln m)
     int ucb_len;
     double ucb_c;
+    uint8_t* d_stage;                // device staging of ludax_rollout_host (grown on demand)
+    size_t stage_bytes;
 };
 
 namespace ludax {

@@ -100,6 +100,10 @@ def lib() -> ctypes.CDLL:
         "ludax_rollout_value": [vp, u64, i32, vp, P(ludax_launch_cfg)],
         "ludax_get_state": [vp, P(ludax_state_view)],
         "ludax_set_state": [vp, P(ludax_state_view)],
+        "ludax_state_bits_words": [vp, P(i32)],
+        "ludax_rollout_host": [vp, vp, vp, u64, vp, vp, P(ludax_launch_cfg)],
+        "ludax_get_state_bits": [vp, vp, vp],
+        "ludax_set_state_bits": [vp, vp, vp],
         "ludax_counters": [vp, P(i64), P(i64)],
         "ludax_sync": [vp, i64],
         "ludax_rollout_mixed": [vp, i64, i64, u64, vp, vp, P(ludax_launch_cfg), vp],
@@ -232,6 +236,53 @@ def ludax_set_state(h, board, to_move, ply, passes, outcome):
         _ptr(t)
     v = _view(board, to_move, ply, passes, outcome)
     _check(lib().ludax_set_state(h, ctypes.byref(v)), "ludax_set_state")
+
+
+def ludax_state_bits_words(h) -> int:
+    w = ctypes.c_int32()
+    _check(lib().ludax_state_bits_words(h, ctypes.byref(w)), "ludax_state_bits_words")
+    return w.value
+
+
+def ludax_get_state_bits(h, planes, meta):
+    """planes int64 [words_per_env][n] (uint64 bits), meta int32 [n] (uint32 bits)."""
+    _check(lib().ludax_get_state_bits(h, _ptr(planes), _ptr(meta)), "ludax_get_state_bits")
+
+
+def ludax_set_state_bits(h, planes, meta):
+    _check(lib().ludax_set_state_bits(h, _ptr(planes), _ptr(meta)), "ludax_set_state_bits")
+
+
+def pack_state_bits(board, to_move, ply, passes, outcome, planes_count):
+    """The packed state (numpy, host) of a canonical state view: planes
+    uint64 [planes_count * W][n] and meta uint32 [n], as ludax_get_state_bits
+    writes them."""
+    import numpy as np
+
+    board = np.asarray(board)
+    n, cells = board.shape
+    W = (cells + 63) // 64
+    planes = np.zeros((planes_count * W, n), np.uint64)
+    for v in range(1, planes_count + 1):
+        for c in range(cells):
+            hit = (board[:, c] == v).astype(np.uint64)
+            planes[(v - 1) * W + c // 64] |= hit << np.uint64(c % 64)
+    meta = (np.asarray(ply).astype(np.uint32) & 0xFFFF) | ((np.asarray(to_move).astype(np.uint32) - 1) & 1) << 16 | \
+        (np.asarray(passes).astype(np.uint8).astype(np.uint32) << 17) | \
+        (((np.asarray(outcome).astype(np.int32) + 1) & 7).astype(np.uint32) << 25)
+    return planes, meta.astype(np.uint32)
+
+
+def ludax_rollout_host(h, planes_host, meta_host, seed, outcome_host, plies_host, cfg=None):
+    """Host tensors (pinned for asynchronous copies): planes int64
+    [words_per_env][n], meta int32 [n] in; outcome int8 [n], plies int16 [n]
+    out, valid once the env's stream has reached this call."""
+    for t in (planes_host, meta_host, outcome_host, plies_host):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("ludax_rollout_host takes contiguous host tensors")
+    _check(lib().ludax_rollout_host(h, planes_host.data_ptr(), meta_host.data_ptr(), seed, outcome_host.data_ptr(),
+                                    plies_host.data_ptr(), ctypes.byref(cfg) if cfg is not None else None),
+           "ludax_rollout_host")
 
 
 def ludax_counters(h):
@@ -566,6 +617,21 @@ class Env:
     def set_state(self, board, to_move, ply, passes, outcome):
         ts = [t.to(self.device).contiguous() for t in (board, to_move, ply, passes, outcome)]
         ludax_set_state(self.handle, *ts)
+        ludax_sync(self.handle)  # the temporaries in ts must outlive the copy
+
+    def state_bits_words(self):
+        return ludax_state_bits_words(self.handle)
+
+    def get_state_bits(self):
+        """(planes int64 [words_per_env][n], meta int32 [n]): the packed state."""
+        planes = self._empty((self.state_bits_words(), self.num_envs), torch.int64)
+        meta = self._empty((self.num_envs,), torch.int32)
+        ludax_get_state_bits(self.handle, planes, meta)
+        return planes, meta
+
+    def set_state_bits(self, planes, meta):
+        ts = [t.to(self.device).contiguous() for t in (planes, meta)]
+        ludax_set_state_bits(self.handle, *ts)
         ludax_sync(self.handle)  # the temporaries in ts must outlive the copy
 
     def counters(self):

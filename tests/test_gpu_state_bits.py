@@ -1,0 +1,114 @@
+"""GPU: the packed state view (two bits per cell) against the byte view and
+the oracle, for every game family.
+
+Oracle positions at random plies go in through one view and out through the
+other, bit-exact; the same positions loaded through either view then play
+identical playouts (the engine's derived state -- Hex edge sets, Draughts
+capture caches, Hasami Shogi's transposed occupancy -- is rebuilt the same).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import games as G
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("ttt", G.TTT, 3, 3), ("c4", G.C4, 6, 7), ("othello", G.OTHELLO, 8, 8), ("hex5", G.HEX, 5, 5),
+         ("hex11", G.HEX, 11, 11), ("gomoku", G.GOMOKU, 15, 15), ("pente", G.PENTE, 19, 19),
+         ("yavalath", G.YAVALATH, 9, 9), ("wolf_sheep", G.WOLF_SHEEP, 8, 8), ("draughts", G.DRAUGHTS, 8, 8),
+         ("hasami_shogi", G.HASAMI_SHOGI, 9, 9)]
+
+
+@pytest.fixture(scope="module")
+def L(cuda_device):
+    from paper_2506_22609_b300 import build
+
+    build.build()
+    from paper_2506_22609_b300 import ludax
+
+    ludax.lib()
+    return ludax
+
+
+def positions(game, rows, cols, n, seed):
+    s = G.reset(game, rows, cols, n)
+    cells = G.num_cells(game, rows, cols)
+    rng = np.random.default_rng(seed)
+    stop = rng.integers(0, max(2, cells), n).astype(np.int16)
+    G.rollout_from(s, seed=seed, stop_ply=stop)
+    return s
+
+
+@pytest.mark.parametrize("name,game,rows,cols", CASES, ids=[c[0] for c in CASES])
+def test_packed_view_round_trips(L, name, game, rows, cols):
+    n = 333  # two 128-thread tiles and a ragged tail
+    s = positions(game, rows, cols, n, 17)
+    view = (s.board, s.to_move, s.ply, s.passes, s.outcome)
+    planes_count = 4 if game == G.DRAUGHTS else 2
+    want_p, want_m = L.pack_state_bits(*view, planes_count)
+
+    a = L.Env(game, rows, cols, n, env_offset=5)
+    a.set_state(*(torch.from_numpy(x) for x in view))
+    assert a.state_bits_words() == want_p.shape[0]
+    p, m = a.get_state_bits()
+    torch.cuda.synchronize()
+    assert (p.cpu().numpy().view(np.uint64) == want_p).all()
+    assert (m.cpu().numpy().view(np.uint32) == want_m).all()
+
+    b = L.Env(game, rows, cols, n, env_offset=5)
+    b.set_state_bits(torch.from_numpy(want_p.view(np.int64)), torch.from_numpy(want_m.view(np.int32)))
+    got = [t.cpu().numpy() for t in b.get_state()]
+    for g_, w_ in zip(got, view):
+        assert (g_ == w_).all()
+
+    oa, pa = a.rollout(42, from_start=False)
+    ob, pb = b.rollout(42, from_start=False)
+    torch.cuda.synchronize()
+    assert (oa.cpu().numpy() == ob.cpu().numpy()).all() and (pa.cpu().numpy() == pb.cpu().numpy()).all()
+    t = s.copy()
+    G.rollout_from(t, seed=42, env_offset=5)
+    assert (oa.cpu().numpy() == t.outcome).all()
+    for e in (a, b):
+        e.close()
+
+
+def test_packed_view_ignores_bits_past_the_board(L):
+    n = 64
+    s = positions(G.C4, 6, 7, n, 3)
+    p, m = L.pack_state_bits(s.board, s.to_move, s.ply, s.passes, s.outcome, 2)
+    junk = p.copy()
+    junk |= np.uint64(0xFFFFFC0000000000)  # bits 42..63: no such cells
+    env = L.Env(G.C4, 6, 7, n)
+    env.set_state_bits(torch.from_numpy(junk.view(np.int64)), torch.from_numpy(m.view(np.int32)))
+    got = env.get_state()[0].cpu().numpy()
+    assert (got == s.board).all()
+    env.close()
+
+
+@pytest.mark.parametrize("name,game,rows,cols", [CASES[1], CASES[4], CASES[9]], ids=["c4", "hex11", "draughts"])
+def test_rollout_host_matches_device_path(L, name, game, rows, cols):
+    """One call with host buffers: the same outcomes and plies as loading the
+    packed state on the device and playing it out, and as the oracle."""
+    n = 1000
+    s = positions(game, rows, cols, n, 23)
+    planes_count = 4 if game == G.DRAUGHTS else 2
+    p, m = L.pack_state_bits(s.board, s.to_move, s.ply, s.passes, s.outcome, planes_count)
+    hp = torch.from_numpy(p.view(np.int64)).pin_memory()
+    hm = torch.from_numpy(m.view(np.int32)).pin_memory()
+    ho = torch.empty(n, dtype=torch.int8).pin_memory()
+    hpl = torch.empty(n, dtype=torch.int16).pin_memory()
+    env = L.Env(game, rows, cols, n, env_offset=9)
+    for _ in range(2):  # the second call reuses the staging
+        L.ludax_rollout_host(env.handle, hp, hm, 77, ho, hpl)
+        env.sync()
+    ref = L.Env(game, rows, cols, n, env_offset=9)
+    ref.set_state_bits(torch.from_numpy(p.view(np.int64)), torch.from_numpy(m.view(np.int32)))
+    o, pl = ref.rollout(77, from_start=False)
+    torch.cuda.synchronize()
+    assert (ho.numpy() == o.cpu().numpy()).all() and (hpl.numpy() == pl.cpu().numpy()).all()
+    t = s.copy()
+    G.rollout_from(t, seed=77, env_offset=9)
+    assert (ho.numpy() == t.outcome).all() and (hpl.numpy() == t.ply).all()
+    for e in (env, ref):
+        e.close()
