@@ -7,10 +7,12 @@
 // Reversi, Hex 2..11, Gomoku, Pente, Yavalath, the parametric line game, Wolf
 // and Sheep, Draughts, Dai Hasami Shogi) into a work queue, so consecutive
 // queue positions -- and therefore the 32 lanes of a warp -- play the same
-// game and branch together.  The persistent kernel hands out queue positions with a
-// warp-aggregated atomic cursor; a lane whose game ends writes its 3 bytes of
-// output and claims the next position, staying inside its game's playout
-// loop while the claimed env has the same game.
+// game and branch together.  With a thread per env the hardware's block
+// scheduler hands out the work; a persistent launch (fewer threads than
+// envs) gives each bucket its own warp-aggregated atomic cursor: a warp
+// stays inside one bucket, a lane whose game ends writes its 3 bytes of
+// output and claims that bucket's next position, and once the bucket is
+// drained the warp moves on to the next bucket with work.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,11 +57,48 @@ __device__ __forceinline__ int bucket_at(const MixedArgs& a, long long q) {
     return b;
 }
 
-// Plays queue positions of one bucket until the lane claims a position
-// outside it; returns that position (>= n when the queue is exhausted).
+// Non-persistent launches (a thread per env, the hardware's block scheduler
+// refilling the SMs): plays the env at queue
+// position q to its end.
 template <class G>
-__device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q, long long end, long long slots,
-                                                bool refill, const B128* table) {
+__device__ __forceinline__ void play_one(const MixedArgs& a, long long q, const B128* table) {
+    G g;
+    set_table(g, table);
+    const long long e = a.queue[q];
+    configure(g, a.desc[e]);
+    g.reset();
+    const uint64_t key = env_key(a.seed_key, (uint64_t)(a.env_offset + e));
+    uint32_t rhi = draw_hi(key, 0u);
+    while (g.outcome == kOngoing) random_ply_pre(g, key, rhi);
+    a.outcome[e] = (int8_t)g.outcome;
+    a.plies[e] = (int16_t)g.ply;
+}
+
+// Persistent launches: a warp stays inside one bucket (one game, so its
+// lanes branch together) and its lanes take that bucket's positions from the
+// bucket's own cursor, one new env per finished lane, until the bucket is
+// drained; then the warp moves on to the next bucket with work.  (A single
+// cursor over the whole queue would let the lanes of a warp drift into
+// different games.)
+__device__ __forceinline__ long long bucket_begin(const MixedArgs& a, int b) { return b == 0 ? 0 : a.bucket_end[b - 1]; }
+
+// positions for the lanes in `want` from bucket b's cursor (warp-aggregated);
+// a result >= the bucket's end means the bucket is drained
+__device__ __forceinline__ long long claim_in_bucket(const MixedArgs& a, int b, bool want) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (m && lane == leader) base = atomicAdd(&a.cursor[b], (unsigned long long)__popc(m));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader < 0 ? 0 : leader);
+    return bucket_begin(a, b) + (long long)(base + __popc(m & ((1u << lane) - 1u)));
+}
+
+// One lane plays positions of bucket b, from its first claim q, taking the
+// next position from the bucket's cursor when a game ends (the lanes that
+// finish together claim with one atomic), until the bucket is drained.
+template <class G>
+__device__ __forceinline__ void drain_bucket(const MixedArgs& a, int b, long long q, const B128* table) {
+    const long long begin = bucket_begin(a, b), end = a.bucket_end[b];
     G g;
     set_table(g, table);
     long long e = a.queue[q];
@@ -74,8 +113,8 @@ __device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q,
         }
         a.outcome[e] = (int8_t)g.outcome;
         a.plies[e] = (int16_t)g.ply;
-        q = refill ? slots + claim_next(a.cursor) : a.n;
-        if (q >= end) return q;
+        q = begin + claim_next(&a.cursor[b]);
+        if (q >= end) return;
         e = a.queue[q];
         configure(g, a.desc[e]);
         g.reset();
@@ -84,10 +123,30 @@ __device__ __forceinline__ long long run_bucket(const MixedArgs& a, long long q,
     }
 }
 
-template <int N, bool TABLE>
-__device__ __forceinline__ long long run_hex(const MixedArgs& a, long long q, long long end, long long slots,
-                                             bool refill, const B128* tables) {
-    return run_bucket<Hex<N>>(a, q, end, slots, refill, TABLE ? tables + hex_table_offset(N) : nullptr);
+template <bool TABLE>
+__device__ __forceinline__ void drain_any(const MixedArgs& a, int b, long long q, const B128* tables) {
+    switch (b) {
+    case 0: drain_bucket<TTT>(a, b, q, nullptr); break;
+    case 1: drain_bucket<C4>(a, b, q, nullptr); break;
+    case 2: drain_bucket<Othello>(a, b, q, nullptr); break;
+    case 3: drain_bucket<Hex<2>>(a, b, q, TABLE ? tables + hex_table_offset(2) : nullptr); break;
+    case 4: drain_bucket<Hex<3>>(a, b, q, TABLE ? tables + hex_table_offset(3) : nullptr); break;
+    case 5: drain_bucket<Hex<4>>(a, b, q, TABLE ? tables + hex_table_offset(4) : nullptr); break;
+    case 6: drain_bucket<Hex<5>>(a, b, q, TABLE ? tables + hex_table_offset(5) : nullptr); break;
+    case 7: drain_bucket<Hex<6>>(a, b, q, TABLE ? tables + hex_table_offset(6) : nullptr); break;
+    case 8: drain_bucket<Hex<7>>(a, b, q, TABLE ? tables + hex_table_offset(7) : nullptr); break;
+    case 9: drain_bucket<Hex<8>>(a, b, q, TABLE ? tables + hex_table_offset(8) : nullptr); break;
+    case 10: drain_bucket<Hex<9>>(a, b, q, TABLE ? tables + hex_table_offset(9) : nullptr); break;
+    case 11: drain_bucket<Hex<10>>(a, b, q, TABLE ? tables + hex_table_offset(10) : nullptr); break;
+    case 12: drain_bucket<Hex<11>>(a, b, q, TABLE ? tables + hex_table_offset(11) : nullptr); break;
+    case 13: drain_bucket<Gomoku>(a, b, q, nullptr); break;
+    case 14: drain_bucket<Pente>(a, b, q, nullptr); break;
+    case 15: drain_bucket<Yavalath>(a, b, q, nullptr); break;
+    case 16: drain_bucket<LineGame>(a, b, q, nullptr); break;
+    case 17: drain_bucket<WolfSheep>(a, b, q, nullptr); break;
+    case 18: drain_bucket<Draughts>(a, b, q, nullptr); break;
+    default: drain_bucket<HasamiShogi>(a, b, q, nullptr); break;
+    }
 }
 
 template <bool TABLE>
@@ -106,34 +165,64 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         hex_fill_table<11>(tables + hex_table_offset(11));
         __syncthreads();
     }
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= a.n) return;
+    const B128* t = tables;
+    switch (bucket_at(a, q)) {
+    case 0: play_one<TTT>(a, q, nullptr); break;
+    case 1: play_one<C4>(a, q, nullptr); break;
+    case 2: play_one<Othello>(a, q, nullptr); break;
+    case 3: play_one<Hex<2>>(a, q, TABLE ? t + hex_table_offset(2) : nullptr); break;
+    case 4: play_one<Hex<3>>(a, q, TABLE ? t + hex_table_offset(3) : nullptr); break;
+    case 5: play_one<Hex<4>>(a, q, TABLE ? t + hex_table_offset(4) : nullptr); break;
+    case 6: play_one<Hex<5>>(a, q, TABLE ? t + hex_table_offset(5) : nullptr); break;
+    case 7: play_one<Hex<6>>(a, q, TABLE ? t + hex_table_offset(6) : nullptr); break;
+    case 8: play_one<Hex<7>>(a, q, TABLE ? t + hex_table_offset(7) : nullptr); break;
+    case 9: play_one<Hex<8>>(a, q, TABLE ? t + hex_table_offset(8) : nullptr); break;
+    case 10: play_one<Hex<9>>(a, q, TABLE ? t + hex_table_offset(9) : nullptr); break;
+    case 11: play_one<Hex<10>>(a, q, TABLE ? t + hex_table_offset(10) : nullptr); break;
+    case 12: play_one<Hex<11>>(a, q, TABLE ? t + hex_table_offset(11) : nullptr); break;
+    case 13: play_one<Gomoku>(a, q, nullptr); break;
+    case 14: play_one<Pente>(a, q, nullptr); break;
+    case 15: play_one<Yavalath>(a, q, nullptr); break;
+    case 16: play_one<LineGame>(a, q, nullptr); break;
+    case 17: play_one<WolfSheep>(a, q, nullptr); break;
+    case 18: play_one<Draughts>(a, q, nullptr); break;
+    default: play_one<HasamiShogi>(a, q, nullptr); break;
+    }
+}
+
+// Persistent launches (fewer threads than envs): warps drain buckets,
+// starting spread over the queue in proportion to the buckets' sizes.
+template <bool TABLE>
+__global__ void __launch_bounds__(512, 1) mixed_persistent_kernel(MixedArgs a) {
+    __shared__ B128 tables[TABLE ? kHexTableCells : 1];
+    if constexpr (TABLE) {
+        hex_fill_table<2>(tables + hex_table_offset(2));
+        hex_fill_table<3>(tables + hex_table_offset(3));
+        hex_fill_table<4>(tables + hex_table_offset(4));
+        hex_fill_table<5>(tables + hex_table_offset(5));
+        hex_fill_table<6>(tables + hex_table_offset(6));
+        hex_fill_table<7>(tables + hex_table_offset(7));
+        hex_fill_table<8>(tables + hex_table_offset(8));
+        hex_fill_table<9>(tables + hex_table_offset(9));
+        hex_fill_table<10>(tables + hex_table_offset(10));
+        hex_fill_table<11>(tables + hex_table_offset(11));
+        __syncthreads();
+    }
     const long long slots = (long long)gridDim.x * blockDim.x;
-    const bool refill = slots < a.n;
-    long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    while (q < a.n) {
-        int b = bucket_at(a, q);
-        long long end = a.bucket_end[b];
-        switch (b) {
-        case 0: q = run_bucket<TTT>(a, q, end, slots, refill, nullptr); break;
-        case 1: q = run_bucket<C4>(a, q, end, slots, refill, nullptr); break;
-        case 2: q = run_bucket<Othello>(a, q, end, slots, refill, nullptr); break;
-        case 3: q = run_hex<2, TABLE>(a, q, end, slots, refill, tables); break;
-        case 4: q = run_hex<3, TABLE>(a, q, end, slots, refill, tables); break;
-        case 5: q = run_hex<4, TABLE>(a, q, end, slots, refill, tables); break;
-        case 6: q = run_hex<5, TABLE>(a, q, end, slots, refill, tables); break;
-        case 7: q = run_hex<6, TABLE>(a, q, end, slots, refill, tables); break;
-        case 8: q = run_hex<7, TABLE>(a, q, end, slots, refill, tables); break;
-        case 9: q = run_hex<8, TABLE>(a, q, end, slots, refill, tables); break;
-        case 10: q = run_hex<9, TABLE>(a, q, end, slots, refill, tables); break;
-        case 11: q = run_hex<10, TABLE>(a, q, end, slots, refill, tables); break;
-        case 12: q = run_hex<11, TABLE>(a, q, end, slots, refill, tables); break;
-        case 13: q = run_bucket<Gomoku>(a, q, end, slots, refill, nullptr); break;
-        case 14: q = run_bucket<Pente>(a, q, end, slots, refill, nullptr); break;
-        case 15: q = run_bucket<Yavalath>(a, q, end, slots, refill, nullptr); break;
-        case 16: q = run_bucket<LineGame>(a, q, end, slots, refill, nullptr); break;
-        case 17: q = run_bucket<WolfSheep>(a, q, end, slots, refill, nullptr); break;
-        case 18: q = run_bucket<Draughts>(a, q, end, slots, refill, nullptr); break;
-        default: q = run_bucket<HasamiShogi>(a, q, end, slots, refill, nullptr); break;
+    const long long warps = slots >> 5, w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int b = bucket_at(a, w * a.n / warps);
+    for (int idle = 0; idle < kBuckets; b = (b + 1) % kBuckets) {
+        const long long q = claim_in_bucket(a, b, true);  // the whole warp enters bucket b together
+        const bool mine = q < a.bucket_end[b];
+        if (__any_sync(0xFFFFFFFFu, mine)) {
+            idle = 0;
+            if (mine) drain_any<TABLE>(a, b, q, tables);
+        } else {
+            ++idle;
         }
+        __syncwarp();  // lanes leave the bucket together
     }
 }
 
@@ -183,8 +272,14 @@ int build_queue(const int32_t* desc_dev, long long n, std::vector<int32_t>& queu
 int launch_mixed(const MixedArgs& a, const ludax_launch_cfg& c, int num_sms, cudaStream_t s) {
     int grid = mixed_grid(a.n, c, num_sms);
     if (cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long) * kBuckets, s) != cudaSuccess) return LUDAX_ERR_CUDA;
-    if (c.hex_nbr_table) mixed_rollout_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
-    else mixed_rollout_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
+    if ((long long)grid * c.block_threads < a.n) {  // persistent
+        if (c.hex_nbr_table) mixed_persistent_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
+        else mixed_persistent_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
+    } else if (c.hex_nbr_table) {
+        mixed_rollout_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
+    } else {
+        mixed_rollout_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
+    }
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
