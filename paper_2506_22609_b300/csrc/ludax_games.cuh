@@ -957,6 +957,29 @@ __device__ __forceinline__ void random_ply(G& g, uint64_t key) {
     if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
 }
 
+// The same ply taken by all 32 lanes of a warp that hold the same position
+// (the UCT kernel, where a warp owns one search): games with a warp form of
+// the move lookup (place_warp) share its work across the lanes; the others
+// compute it in every lane.  Every lane ends with the same state.
+template <class G, class = void>
+struct HasWarpPlace : std::false_type {};
+template <class G>
+struct HasWarpPlace<G, std::void_t<decltype(std::declval<G&>().place_warp(0, 0))>> : std::true_type {};
+template <class G>
+__device__ __forceinline__ void random_ply_warp(G& g, uint64_t key, int lane) {
+    if constexpr (HasWarpPlace<G>::value) {
+        typename G::Mask m = g.legal();
+        if (G::kHasPass && !any(m)) {
+            g.pass();
+        } else {
+            g.place_warp((int)draw_index(key, (uint32_t)g.ply, legal_count_of(g, m)), lane);
+        }
+        if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
+    } else {
+        random_ply(g, key);
+    }
+}
+
 // The same ply with the draw software-pipelined: rhi holds the top 32 bits of
 // this ply's draw (computed one ply ahead); the next ply's draw is started
 // here, independent of the board work, and handed back through rhi.  The

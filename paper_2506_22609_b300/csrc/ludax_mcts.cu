@@ -20,9 +20,11 @@
 // round: every lane replays the round's expansion draws (cheap), takes its
 // own iteration's child, plays its playout, and writes its node exactly where
 // the sequential search would have (node index, sibling link, N = 1, W); the
-// root then adds the round's visits.  Iterations that descend by UCB1 run on
-// lane 0 alone.  Every loop is bounded by the iteration count and the game's
-// ply cap.
+// root then adds the round's visits.  Iterations that descend by UCB1 run in
+// all lanes on the same data (lane 0 alone writes the tree); their playouts
+// share each ply of a move game -- one piece per lane for the move lookup --
+// and are computed redundantly otherwise.  Every loop is bounded by the
+// iteration count and the game's ply cap.
 #include <cmath>
 #include <vector>
 
@@ -126,10 +128,13 @@ __device__ __forceinline__ M mask_without(M m, int b) {
 }
 
 // One sequential iteration (traversal by UCB1, expansion, playout, update)
-// with the iteration key ki; count = nodes in use.
+// with the iteration key ki; count = nodes in use.  All 32 lanes of the warp
+// run it on the same data: the traversal and the playout are computed in
+// every lane (a move game's playout shares each ply's move lookup across the
+// lanes), and lane 0 alone writes the tree.
 template <class G>
 __device__ void uct_iteration(const G& root, uint64_t ki, const double* __restrict__ T, TNode* nd, uint64_t* mk,
-                              int& count) {
+                              int& count, int lane) {
     using M = typename G::Mask;
     constexpr int MW = MaskWords<M>::value;
     G g = root;
@@ -139,9 +144,11 @@ __device__ void uct_iteration(const G& root, uint64_t ki, const double* __restri
         if (G::kHasPass && !any(legal)) {  // the forced pass is the only action
             if (nd[x].first_child < 0) {
                 const int y = count++;
-                nd[y] = make_node(x, -1, -1, -1, 0u, 0u, g.side);
-                mask_zero(mk + (size_t)y * MW, MW);
-                nd[x].first_child = (int16_t)y;
+                if (lane == 0) {
+                    nd[y] = make_node(x, -1, -1, -1, 0u, 0u, g.side);
+                    mask_zero(mk + (size_t)y * MW, MW);
+                    nd[x].first_child = (int16_t)y;
+                }
                 play(g, -1);
                 x = y;
                 break;
@@ -157,11 +164,13 @@ __device__ void uct_iteration(const G& root, uint64_t ki, const double* __restri
             const uint32_t k = __umulhi((uint32_t)(splitmix64(~ki) >> 32), popc(untried));
             const int b = select_bit(untried, k);
             mask_add(tried, b);
-            mask_put(mk + (size_t)x * MW, tried);
             const int y = count++;
-            nd[y] = make_node(x, b, -1, nd[x].first_child, 0u, 0u, g.side);
-            mask_zero(mk + (size_t)y * MW, MW);
-            nd[x].first_child = (int16_t)y;
+            if (lane == 0) {
+                mask_put(mk + (size_t)x * MW, tried);
+                nd[y] = make_node(x, b, -1, nd[x].first_child, 0u, 0u, g.side);
+                mask_zero(mk + (size_t)y * MW, MW);
+                nd[x].first_child = (int16_t)y;
+            }
             play(g, b);
             x = y;
             break;
@@ -182,12 +191,14 @@ __device__ void uct_iteration(const G& root, uint64_t ki, const double* __restri
         play(g, best_a);
         x = best;
     }
-    while (g.outcome == kOngoing) random_ply(g, ki);
-    for (int y = x; y > 0; y = nd[y].parent) {
-        nd[y].N = (uint16_t)(nd[y].N + 1u);
-        nd[y].W = (uint16_t)(nd[y].W + half_points(g.outcome, nd[y].mover));
+    while (g.outcome == kOngoing) random_ply_warp(g, ki, lane);
+    if (lane == 0) {  // the new node's links were written by this lane
+        for (int y = x; y > 0; y = nd[y].parent) {
+            nd[y].N = (uint16_t)(nd[y].N + 1u);
+            nd[y].W = (uint16_t)(nd[y].W + half_points(g.outcome, nd[y].mover));
+        }
+        nd[0].N = (uint16_t)(nd[0].N + 1u);
     }
-    nd[0].N = (uint16_t)(nd[0].N + 1u);
 }
 
 // the move: most visits, then largest W, then smallest action
@@ -257,8 +268,7 @@ __device__ int uct_search_warp(const G& root, uint64_t key, int iters, const dou
             count += R;
             i += R;
         } else {
-            if (lane == 0) uct_iteration(root, splitmix64(key ^ (uint64_t)i), T, nd, mk, count);
-            count = __shfl_sync(0xffffffffu, count, 0);
+            uct_iteration(root, splitmix64(key ^ (uint64_t)i), T, nd, mk, count, lane);
             ++i;
         }
         __syncwarp();

@@ -288,6 +288,41 @@ struct Draughts {
         const int d = select_bit(dirs, (uint32_t)kk);
         to = sel + (d == 0 ? -9 : d == 1 ? -7 : d == 2 ? 7 : 9) * (capture_mode() ? 2 : 1);
     }
+    // The same lookup by the 32 lanes of a warp that all hold this position:
+    // lane j reads the moves of the j-th mover (at most 12), a prefix sum over
+    // the lanes finds the one holding move k.
+    __device__ __forceinline__ void find_warp(int k, int& from, int& to, int lane) const {
+        const uint64_t mv = movers();
+        const int np = __popcll(mv);
+        int i = -1, c = 0;
+        uint32_t g = 0;
+        if (lane < np) {
+            i = select_bit(mv, (uint32_t)lane);
+            g = ((uint32_t)(src[0] >> i) & 1u) | (((uint32_t)(src[1] >> i) & 1u) << 1) |
+                (((uint32_t)(src[2] >> i) & 1u) << 2) | (((uint32_t)(src[3] >> i) & 1u) << 3);
+            c = __popc(g);
+        }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const bool hit = lane < np && k >= incl - c && k < incl;
+        const int srcl = __ffs(__ballot_sync(0xFFFFFFFFu, hit)) - 1;
+        int t = -1;
+        if (hit) {
+            const int d = select_bit(g, (uint32_t)(k - (incl - c)));
+            t = i + (d == 0 ? -9 : d == 1 ? -7 : d == 2 ? 7 : 9) * (capture_mode() ? 2 : 1);
+        }
+        from = __shfl_sync(0xFFFFFFFFu, i, srcl < 0 ? 0 : srcl);
+        to = __shfl_sync(0xFFFFFFFFu, t, srcl < 0 ? 0 : srcl);
+    }
+    __device__ __forceinline__ void place_warp(int k, int lane) {
+        int f, t;
+        find_warp(k, f, t, lane);
+        apply(f, t);
+    }
     __device__ __forceinline__ void place(int k) {
         int f, t;
         find(k, f, t);
@@ -602,6 +637,37 @@ struct HasamiShogi {
         }
         from = sel;
         to = sel < 0 ? -1 : dest_of(sel, runs_at(occ, sel), kk);
+    }
+    // The same lookup by the 32 lanes of a warp that all hold this position:
+    // lane j counts the moves of the j-th piece (at most 18), a prefix sum
+    // over the lanes finds the piece holding move k, and its lane forms the
+    // destination.
+    __device__ __forceinline__ void find_warp(int k, int& from, int& to, int lane) const {
+        const B128 occ = own | opp;
+        const int np = (int)popc(own);
+        int i = -1, c = 0;
+        Runs x{};
+        if (lane < np) {
+            i = select_bit(own, (uint32_t)lane);
+            x = runs_at(occ, i);
+            c = x.total();
+        }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const bool hit = lane < np && k >= incl - c && k < incl;
+        const int src = __ffs(__ballot_sync(0xFFFFFFFFu, hit)) - 1;
+        const int t = hit ? dest_of(i, x, k - (incl - c)) : -1;
+        from = __shfl_sync(0xFFFFFFFFu, i, src < 0 ? 0 : src);
+        to = __shfl_sync(0xFFFFFFFFu, t, src < 0 ? 0 : src);
+    }
+    __device__ __forceinline__ void place_warp(int k, int lane) {
+        int f, t;
+        find_warp(k, f, t, lane);
+        apply(f, t);
     }
     __device__ __forceinline__ bool five() const {  // the mover, outside its starting rows
         const B128 m = own & (side == 0 ? B128{kHasamiRows06Lo, kHasamiRows06Hi} : B128{kHasamiRows28Lo, kHasamiRows28Hi});
