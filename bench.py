@@ -1,7 +1,10 @@
 """Benchmark: env steps/s of uniform-random playouts on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload c4|ttt|othello|hex11|mixed] [--no-extras] [--no-cpu-baseline]
+                    [--workload c4|ttt|othello|hex11|gomoku|pente|yavalath|line_c5|wolf_sheep|
+                                draughts|hasami_shogi|mixed|step_c4]
+                    [--no-extras] [--no-cpu-baseline] [--only dense_layer|gavel_library|
+                     batch_sweep|value_net|value_estimator|int_peak]
 
 One step = one fused playout launch over the whole batch: every env of the
 workload is reset to the start position and played to the end of its game
@@ -12,9 +15,10 @@ The default workload is Connect Four 6x7, 65,536 envs, seed 1.
 
 Metric: env steps per second = total plies played (passes included) / time.
 `value` is device time (CUDA events on the launching stream) with L2 flushed
-between steps; `e2e` goes through the public API with host buffers: start
-positions copied from pinned host memory and loaded with ludax_set_state,
-the playout, and outcome + game length copied back to pinned host memory.
+between steps; `e2e` goes through the C-ABI call with host buffers
+(ludax_rollout_host): start positions in the packed state view copied from
+pinned host memory and loaded, the playout, and outcome + game length copied
+back to pinned host memory.
 
 Under torchrun (N > 1) each rank plays its own disjoint range of global env
 ids (weak scaling, no collective on the data path); the step time is the
