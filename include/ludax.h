@@ -511,6 +511,13 @@ int ludax_dense_bf16_relu(const uint16_t* a_dev, const uint16_t* b_dev, const fl
  * (synchronising): LUDAX_OK, or LUDAX_ERR_TIMEOUT when a kernel gave up on
  * an internal wait since the last call; error_out (nullable) gets the word. */
 int ludax_device_error(int32_t* error_out);
+/* Self-test of that failure path, without a fault: launches one thread that
+ * waits on an mbarrier nothing arrives at, gives up after limit_cycles
+ * (1 .. 2e9 clock cycles) and sets bit 2 of the device error word, as a
+ * tensor-core kernel does when an internal wait expires.  The next
+ * ludax_device_error then returns LUDAX_ERR_TIMEOUT, and the context stays
+ * usable.  Asynchronous on `stream`. */
+int ludax_selftest_wait(int64_t limit_cycles, void* stream);
 
 /* Integer-issue microbenchmark behind the playouts' roofline: one launch
  * over every SM at full occupancy in which each thread issues `iters` x 8

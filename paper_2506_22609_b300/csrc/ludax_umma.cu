@@ -521,6 +521,26 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ------------------------------------------------------ wait self-test --
+// The failure path of the bounded waits, exercised without a fault: one
+// thread waits on an mbarrier that nothing will ever arrive at, gives up
+// after `limit` clock cycles and records the expiry in the device error word
+// (bit 2), exactly as the GEMM kernels do when a pipeline stage never lands.
+__global__ void wait_selftest_kernel(long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const long long t0 = clock64();
+    bool done = false;
+    while (!(done = mbar_try_wait(&bar, 0u)))
+        if (clock64() - t0 > limit) break;
+    if (!done) atomicOr(&g_umma_error, 2);
+}
+
 // ------------------------------------------------------------ host side --
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -646,6 +666,12 @@ int ludax_dense_bf16_relu(const uint16_t* a_dev, const uint16_t* b_dev, const fl
                           int32_t M, int32_t N, int32_t K, int32_t ld_out, void* stream) {
     if (!a_dev || !b_dev || !bias_dev || !out_dev) return LUDAX_ERR_ARG;
     return ludax::umma_dense_relu(a_dev, b_dev, bias_dev, out_dev, M, N, K, ld_out, (cudaStream_t)stream);
+}
+
+int ludax_selftest_wait(int64_t limit_cycles, void* stream) {
+    if (limit_cycles < 1 || limit_cycles > kWaitLimit) return LUDAX_ERR_ARG;
+    wait_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((long long)limit_cycles);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
 int ludax_device_error(int32_t* error_out) {

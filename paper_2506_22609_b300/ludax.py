@@ -128,6 +128,7 @@ def lib() -> ctypes.CDLL:
         "ludax_dense_bf16_relu": [vp, vp, vp, vp, i32, i32, i32, i32, vp],
         "ludax_device_error": [P(i32)],
         "ludax_int_peak": [i32, i64, P(i64), vp],
+        "ludax_selftest_wait": [i64, vp],
         "ludax_mcts_reserve": [vp, i32, ctypes.c_double],
         "ludax_mcts_search": [vp, u64, i32, ctypes.c_double, vp, vp, vp],
         "ludax_mcts_play": [vp, u64, u32, i32, i32, ctypes.c_double, vp, vp, vp, vp],
@@ -454,6 +455,11 @@ def ludax_device_error():
     e = ctypes.c_int32()
     lib().ludax_device_error(ctypes.byref(e))
     return e.value
+
+
+def ludax_selftest_wait(limit_cycles: int, stream=None):
+    """Make a bounded device wait expire (see ludax_device_error)."""
+    _check(lib().ludax_selftest_wait(limit_cycles, _stream(stream)), "ludax_selftest_wait")
 
 
 INT_PEAK_KINDS = {"lop3": 0, "iadd": 1, "shf": 2}

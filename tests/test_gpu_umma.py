@@ -62,3 +62,23 @@ def test_int_peak_microbenchmark_runs(L, kind):
     assert ops == sms * 8 * 256 * 8 * 64
     with pytest.raises(L.LudaxError):
         L.ludax_int_peak(kind, 0)
+
+
+def test_bounded_wait_expires_and_reports(L):
+    """A device wait that nothing completes gives up after its limit, the
+    expiry reaches the host as LUDAX_ERR_TIMEOUT through the error word, the
+    word is cleared by reading it, and the context keeps working."""
+    assert L.ludax_device_error() == 0
+    L.ludax_selftest_wait(2_000_000)  # about a millisecond of clock
+    torch.cuda.synchronize()
+    assert L.ludax_device_error() == 2
+    assert L.ludax_device_error() == 0
+    a = torch.ones(128, 64, dtype=torch.bfloat16, device="cuda")
+    b = torch.ones(256, 64, dtype=torch.bfloat16, device="cuda")
+    out = torch.empty(128, 256, dtype=torch.int16, device="cuda")
+    L.ludax_dense_bf16_relu(a.view(torch.int16), b.view(torch.int16), torch.zeros(256, device="cuda"), out)
+    torch.cuda.synchronize()
+    assert (out.view(torch.bfloat16).float() == 64.0).all()
+    assert L.ludax_device_error() == 0
+    with pytest.raises(L.LudaxError):
+        L.ludax_selftest_wait(0)
