@@ -112,3 +112,28 @@ def test_rollout_host_matches_device_path(L, name, game, rows, cols):
     assert (ho.numpy() == t.outcome).all() and (hpl.numpy() == t.ply).all()
     for e in (env, ref):
         e.close()
+
+
+@pytest.mark.parametrize("rows,cols,line,flags", [(9, 12, 5, 0), (8, 9, 5, 3), (10, 11, 4, 2)])
+def test_packed_view_line_games(L, rows, cols, line, flags):
+    """The parametric line game (run-time board shape, up to 110 cells here: two
+    words per plane) through both views."""
+    n = 257
+    gid = 7 | (line << 8) | (flags << 12)
+    s = positions(gid, rows, cols, n, 29)
+    view = (s.board, s.to_move, s.ply, s.passes, s.outcome)
+    want_p, want_m = L.pack_state_bits(*view, 2)
+    a = L.Env("line", rows, cols, n, env_offset=2, line=line, flags=flags)
+    a.set_state(*(torch.from_numpy(x) for x in view))
+    p, m = a.get_state_bits()
+    torch.cuda.synchronize()
+    assert (p.cpu().numpy().view(np.uint64) == want_p).all() and (m.cpu().numpy().view(np.uint32) == want_m).all()
+    b = L.Env("line", rows, cols, n, env_offset=2, line=line, flags=flags)
+    b.set_state_bits(torch.from_numpy(want_p.view(np.int64)), torch.from_numpy(want_m.view(np.int32)))
+    for g_, w_ in zip((t.cpu().numpy() for t in b.get_state()), view):
+        assert (g_ == w_).all()
+    oa, _ = a.rollout(5, from_start=False)
+    ob, _ = b.rollout(5, from_start=False)
+    assert (oa.cpu().numpy() == ob.cpu().numpy()).all()
+    for e in (a, b):
+        e.close()
