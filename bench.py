@@ -399,9 +399,10 @@ def bench_compiled_library(L, steps, warmup, flush_buf, n=1 << 20, seed=3):
 def bench_gavel(matches=100, iters=100, weak_iters=50):
     """App. F's GAVEL-like evaluation of every game in the package's library
     (matches between UCT agents: equal agents, then the stronger agent in
-    each seat against a weaker one), all games in one launch; beside it the
-    oracle's time for one Connect Four match between the same agents (one
-    host thread, a bounded sample of 4 matches)."""
+    each seat against a weaker one), all games in one launch; beside it, as
+    this measurement's CPU baseline, the oracle's time for one Connect Four
+    match between the same agents (one host thread, a bounded sample of 4
+    matches)."""
     from oracle import games as OG
     from paper_2506_22609_b300 import dsl, gavel
 
@@ -419,8 +420,9 @@ def bench_gavel(matches=100, iters=100, weak_iters=50):
             "iterations_per_s_lower_bound": round(searches * weak_iters / secs, 1), "gavel_scores": scores,
             "median_gavel_score": round(float(statistics.median(scores.values())), 3),
             "interesting": sorted(k for k, v in r.items() if v["interesting"]),
-            "cpu_oracle": {"connect_four_seconds_per_match": round(cpu_c4, 4), "threads": 1,
-                           "sample": "4 Connect Four matches between 100-iteration agents"}}
+            "cpu_baseline": {"kind": "oracle", "unit": "s per Connect Four match",
+                             "value": round(cpu_c4, 4), "cores": 1,
+                             "sample": "4 Connect Four matches between 100-iteration agents, one host thread"}}
 
 
 # algorithmic bytes of one env step in step-per-launch mode: read two planes
