@@ -236,12 +236,20 @@ int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* 
  * copies of outcome_host int8 [num_envs] and plies_host int16 [num_envs] back;
  * returns without waiting (ludax_sync, or the stream, tells when the outputs
  * are in place).  Host buffers should be page-locked for the copies to run
- * asynchronously.  The staging (num_envs x (8 x words_per_env + 7) bytes)
- * is allocated on the first call and kept until ludax_env_destroy; growing
- * it synchronises the stream.  The env's state afterwards is the loaded
- * positions (the playouts do not write back). */
+ * asynchronously.  The playout kernel loads the packed positions itself; the
+ * env's stored state is not changed.  The staging (num_envs x (8 x
+ * words_per_env + 8) bytes at most) is allocated on the first call and kept
+ * until ludax_env_destroy; growing it synchronises the stream. */
 int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32_t* meta_host, uint64_t seed,
                        int8_t* outcome_host, int16_t* plies_host, const ludax_launch_cfg* cfg);
+/* The same with one host buffer each way (one copy each way):
+ *   in_host  planes (8 x words_per_env x num_envs bytes, the layout above)
+ *            followed by meta (4 x num_envs bytes)
+ *   out_host outcome (num_envs bytes), one pad byte when num_envs is odd,
+ *            then plies (2 x num_envs bytes)
+ * Both 8-byte aligned, page-locked for asynchronous copies. */
+int ludax_rollout_host_packed(ludax_env* env, const void* in_host, void* out_host, uint64_t seed,
+                              const ludax_launch_cfg* cfg);
 
 /* ludax_rollout_value: for every env, R independent uniform-random playouts
  * from its current state; playout j (0 <= j < R) draws with seed + j.

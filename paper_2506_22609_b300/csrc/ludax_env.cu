@@ -246,15 +246,14 @@ __global__ void get_state_bits_kernel(EnvDev d, uint64_t* planes, uint32_t* meta
     meta[e] = pack_state_meta(g.ply, g.side, pb, g.outcome);
 }
 
+// Builds env e's engine state from the packed view (the state's meta word and
+// its V x W plane words); no store.
 template <class G>
-__global__ void set_state_bits_kernel(EnvDev d, const uint64_t* planes, const uint32_t* meta, int W, int V) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= d.n) return;
+__device__ __forceinline__ void load_bits(G& g, const EnvDev& d, const uint64_t* planes, const uint32_t* meta,
+                                          int64_t e, int W, int V) {
     const uint32_t m = meta[e];
     const int ply = (int)(m & 0xFFFF), side = (int)((m >> 16) & 1), pb = (int)((m >> 17) & 0xFF);
     const int outcome = (int)((m >> 25) & 7) - 1;
-    G g;
-    set_table(g, nullptr);
     configure(g, d.desc);
     if constexpr (IsMove<G>::value) {
         g.reset();
@@ -296,6 +295,15 @@ __global__ void set_state_bits_kernel(EnvDev d, const uint64_t* planes, const ui
         }
         if constexpr (HexN<G>::value != 0) g.rebuild();
     }
+}
+
+template <class G>
+__global__ void set_state_bits_kernel(EnvDev d, const uint64_t* planes, const uint32_t* meta, int W, int V) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.n) return;
+    G g;
+    set_table(g, nullptr);
+    load_bits(g, d, planes, meta, e, W, V);
     store_state(g, d, e);
 }
 
@@ -313,6 +321,9 @@ struct RolloutArgs {
     int8_t* outcome;
     int16_t* plies;
     int from_start, write_back;
+    const uint64_t* bits;        // non-null: start each env from this packed view instead
+    const uint32_t* bits_meta;
+    int bits_w, bits_v;
 };
 
 // One persistent kernel: each thread holds EPT envs in registers and advances
@@ -346,7 +357,8 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
     auto init = [&](int i) {
         const int64_t e = env[i];
         configure(g[i], a.d.desc);
-        if (a.from_start) g[i].reset();
+        if (a.bits) load_bits(g[i], a.d, a.bits, a.bits_meta, e, a.bits_w, a.bits_v);
+        else if (a.from_start) g[i].reset();
         else load_state(g[i], a.d, e);
         key[i] = env_key(a.seed_key, (uint64_t)(a.d.env_offset + e));
         rhi[i] = draw_hi(key[i], (uint32_t)g[i].ply);
@@ -439,7 +451,8 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
     bool active = env < n;
     auto init = [&]() {
         configure(g, a.d.desc);
-        if (a.from_start) g.reset();
+        if (a.bits) load_bits(g, a.d, a.bits, a.bits_meta, env, a.bits_w, a.bits_v);
+        else if (a.from_start) g.reset();
         else load_state(g, a.d, env);
         key = env_key(a.seed_key, (uint64_t)(a.d.env_offset + env));
         rhi = draw_hi(key, (uint32_t)g.ply);
@@ -733,8 +746,11 @@ int ludax_random_step(ludax_env* env, uint64_t seed, float* rewards_dev, uint8_t
     });
 }
 
-int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* stop_ply_dev, int8_t* outcome_dev,
-                  int16_t* plies_dev, const ludax_launch_cfg* cfg) {
+// the playouts of ludax_rollout; with bits non-null every env starts from the
+// packed view (bits, bits_meta) instead of its stored or start state
+static int rollout_impl(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* stop_ply_dev,
+                        int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg, const uint64_t* bits,
+                        const uint32_t* bits_meta) {
     if (!env) return LUDAX_ERR_ARG;
     if (flags & ~(uint32_t)(LUDAX_ROLLOUT_FROM_START | LUDAX_ROLLOUT_WRITE_BACK)) return LUDAX_ERR_ARG;
     if ((stop_ply_dev && !aligned(stop_ply_dev, 2)) || (plies_dev && !aligned(plies_dev, 2))) return LUDAX_ERR_ALIGN;
@@ -749,20 +765,26 @@ int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* 
     a.plies = plies_dev;
     a.from_start = (flags & LUDAX_ROLLOUT_FROM_START) ? 1 : 0;
     a.write_back = (flags & LUDAX_ROLLOUT_WRITE_BACK) ? 1 : 0;
+    a.bits = bits;
+    a.bits_meta = bits_meta;
+    state_bits_shape(env, &a.bits_w, &a.bits_v);
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         return launch_rollout<G>(env, a, c);
     });
 }
 
-int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32_t* meta_host, uint64_t seed,
-                       int8_t* outcome_host, int16_t* plies_host, const ludax_launch_cfg* cfg) {
-    if (!env || !planes_host || !meta_host || !outcome_host || !plies_host) return LUDAX_ERR_ARG;
-    int W, V;
-    state_bits_shape(env, &W, &V);
-    const size_t n = (size_t)env->n, pbytes = (size_t)W * V * n * 8;
-    // staging: planes (8-byte aligned), meta, plies (2-byte aligned), outcome
-    const size_t need = pbytes + 4 * n + 2 * n + n;
+int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* stop_ply_dev, int8_t* outcome_dev,
+                  int16_t* plies_dev, const ludax_launch_cfg* cfg) {
+    return rollout_impl(env, seed, flags, stop_ply_dev, outcome_dev, plies_dev, cfg, nullptr, nullptr);
+}
+
+// device staging of the host-buffer playouts: planes, meta, outcome, plies
+static int host_stage(ludax_env* env, size_t pbytes, size_t* out_at, size_t* plies_at) {
+    const size_t n = (size_t)env->n;
+    *out_at = pbytes + 4 * n;
+    *plies_at = *out_at + n + (n & 1);
+    const size_t need = *plies_at + 2 * n;
     if (env->stage_bytes < need) {
         if (cudaStreamSynchronize(env->stream) != cudaSuccess) return LUDAX_ERR_CUDA;  // a previous call may still use it
         cudaFree(env->d_stage);
@@ -774,18 +796,49 @@ int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32
         }
         env->stage_bytes = need;
     }
+    return LUDAX_OK;
+}
+
+int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32_t* meta_host, uint64_t seed,
+                       int8_t* outcome_host, int16_t* plies_host, const ludax_launch_cfg* cfg) {
+    if (!env || !planes_host || !meta_host || !outcome_host || !plies_host) return LUDAX_ERR_ARG;
+    int W, V;
+    state_bits_shape(env, &W, &V);
+    const size_t n = (size_t)env->n, pbytes = (size_t)W * V * n * 8;
+    size_t out_at, plies_at;
+    int st = host_stage(env, pbytes, &out_at, &plies_at);
+    if (st) return st;
     uint64_t* dp = reinterpret_cast<uint64_t*>(env->d_stage);
     uint32_t* dm = reinterpret_cast<uint32_t*>(env->d_stage + pbytes);
-    int16_t* dpl = reinterpret_cast<int16_t*>(env->d_stage + pbytes + 4 * n);
-    int8_t* dout = reinterpret_cast<int8_t*>(env->d_stage + pbytes + 6 * n);
+    int8_t* dout = reinterpret_cast<int8_t*>(env->d_stage + out_at);
+    int16_t* dpl = reinterpret_cast<int16_t*>(env->d_stage + plies_at);
     if (cudaMemcpyAsync(dp, planes_host, pbytes, cudaMemcpyHostToDevice, env->stream) != cudaSuccess ||
         cudaMemcpyAsync(dm, meta_host, 4 * n, cudaMemcpyHostToDevice, env->stream) != cudaSuccess)
         return LUDAX_ERR_CUDA;
-    int st = ludax_set_state_bits(env, dp, dm);
-    if (st) return st;
-    if ((st = ludax_rollout(env, seed, 0, nullptr, dout, dpl, cfg))) return st;
+    // the playouts load the packed positions themselves (no separate load launch)
+    if ((st = rollout_impl(env, seed, 0, nullptr, dout, dpl, cfg, dp, dm))) return st;
     if (cudaMemcpyAsync(outcome_host, dout, n, cudaMemcpyDeviceToHost, env->stream) != cudaSuccess ||
         cudaMemcpyAsync(plies_host, dpl, 2 * n, cudaMemcpyDeviceToHost, env->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    return LUDAX_OK;
+}
+
+int ludax_rollout_host_packed(ludax_env* env, const void* in_host, void* out_host, uint64_t seed,
+                              const ludax_launch_cfg* cfg) {
+    if (!env || !in_host || !out_host) return LUDAX_ERR_ARG;
+    int W, V;
+    state_bits_shape(env, &W, &V);
+    const size_t n = (size_t)env->n, pbytes = (size_t)W * V * n * 8;
+    size_t out_at, plies_at;
+    int st = host_stage(env, pbytes, &out_at, &plies_at);
+    if (st) return st;
+    uint64_t* dp = reinterpret_cast<uint64_t*>(env->d_stage);
+    uint32_t* dm = reinterpret_cast<uint32_t*>(env->d_stage + pbytes);
+    int8_t* dout = reinterpret_cast<int8_t*>(env->d_stage + out_at);
+    int16_t* dpl = reinterpret_cast<int16_t*>(env->d_stage + plies_at);
+    if (cudaMemcpyAsync(dp, in_host, out_at, cudaMemcpyHostToDevice, env->stream) != cudaSuccess) return LUDAX_ERR_CUDA;
+    if ((st = rollout_impl(env, seed, 0, nullptr, dout, dpl, cfg, dp, dm))) return st;
+    if (cudaMemcpyAsync(out_host, dout, plies_at + 2 * n - out_at, cudaMemcpyDeviceToHost, env->stream) != cudaSuccess)
         return LUDAX_ERR_CUDA;
     return LUDAX_OK;
 }

@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
         "ludax_set_state": [vp, P(ludax_state_view)],
         "ludax_state_bits_words": [vp, P(i32)],
         "ludax_rollout_host": [vp, vp, vp, u64, vp, vp, P(ludax_launch_cfg)],
+        "ludax_rollout_host_packed": [vp, vp, vp, u64, P(ludax_launch_cfg)],
         "ludax_get_state_bits": [vp, vp, vp],
         "ludax_set_state_bits": [vp, vp, vp],
         "ludax_counters": [vp, P(i64), P(i64)],
@@ -284,6 +285,17 @@ def ludax_rollout_host(h, planes_host, meta_host, seed, outcome_host, plies_host
     _check(lib().ludax_rollout_host(h, planes_host.data_ptr(), meta_host.data_ptr(), seed, outcome_host.data_ptr(),
                                     plies_host.data_ptr(), ctypes.byref(cfg) if cfg is not None else None),
            "ludax_rollout_host")
+
+
+def ludax_rollout_host_packed(h, in_host, out_host, seed, cfg=None):
+    """in_host uint8 host tensor: planes then meta; out_host uint8: outcome,
+    a pad byte when n is odd, then plies."""
+    for t in (in_host, out_host):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("ludax_rollout_host_packed takes contiguous host tensors")
+    _check(lib().ludax_rollout_host_packed(h, in_host.data_ptr(), out_host.data_ptr(), seed,
+                                           ctypes.byref(cfg) if cfg is not None else None),
+           "ludax_rollout_host_packed")
 
 
 def ludax_counters(h):

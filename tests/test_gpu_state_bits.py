@@ -102,6 +102,16 @@ def test_rollout_host_matches_device_path(L, name, game, rows, cols):
     for _ in range(2):  # the second call reuses the staging
         L.ludax_rollout_host(env.handle, hp, hm, 77, ho, hpl)
         env.sync()
+    # the same with one buffer each way (ludax_rollout_host_packed)
+    pb = p.size * 8
+    hin = torch.empty(pb + 4 * n, dtype=torch.uint8).pin_memory()
+    hin[:pb] = torch.from_numpy(p.view(np.uint8).reshape(-1))
+    hin[pb:] = torch.from_numpy(m.view(np.uint8))
+    hout = torch.empty(n + (n & 1) + 2 * n, dtype=torch.uint8).pin_memory()
+    ho1, hpl1 = hout[:n].view(torch.int8), hout[n + (n & 1):].view(torch.int16)
+    L.ludax_rollout_host_packed(env.handle, hin, hout, 77)
+    env.sync()
+    assert (ho1.numpy() == ho.numpy()).all() and (hpl1.numpy() == hpl.numpy()).all()
     ref = L.Env(game, rows, cols, n, env_offset=9)
     ref.set_state_bits(torch.from_numpy(p.view(np.int64)), torch.from_numpy(m.view(np.int32)))
     o, pl = ref.rollout(77, from_start=False)
