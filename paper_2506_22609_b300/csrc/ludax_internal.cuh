@@ -116,4 +116,14 @@ int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, cons
                   const float* b2, const void* w3, float* zpart, void* scratch, int scratch_rows, int M,
                   cudaStream_t s);
 
+// The value net's backward contractions on tcgen05 (ludax_umma.cu).
+// umma_grad_mask: out[m][n] = bf16(mask[m][n] > 0 ? sum_k A[m][k] B[k][n] : 0)
+// with A [M][K], B [K][N], mask and out [M][N], all row-major BF16.
+int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, cudaStream_t s);
+// umma_grad_weights: part[p][m][n] = FP32 sum over the p-th of *splits_out
+// contiguous K ranges of A[k][m] B[k][n]; A [K][lda], B [K][ldb] row-major
+// BF16; part holds part_floats floats (the split count is capped by it).
+int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* part,
+                      long long part_floats, int* splits_out, cudaStream_t s);
+
 }  // namespace ludax

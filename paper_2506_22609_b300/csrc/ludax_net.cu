@@ -571,24 +571,37 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, float* loss_
     reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pb2, chunks, kH, n->g + n->ob2);
     reduce_parts_kernel<<<1, 32, 0, s>>>(pb3, chunks, 1, n->g + n->ob3);
     // dZ1 = (dZ2 . W2) * [H1 > 0]
-    GemmArgs a{};
-    a.A = n->dZ2; a.B = n->W2b; a.M = (int)B; a.N = kH; a.K = kH; a.lda = kH; a.ldb = kH;
-    a.mask = n->H1; a.out = n->dZ1; a.ldo = kH;
-    int st = launch_gemm<true, false, EPI_MASK>(a, 1, s);
+    const bool tc = n->use_tcgen05 && umma_dense_supported((int)B, kH, kH);
+    int st;
+    if (tc) {
+        st = umma_grad_mask(n->dZ2, n->W2b, n->H1, n->dZ1, (int)B, kH, kH, s);
+    } else {
+        GemmArgs a{};
+        a.A = n->dZ2; a.B = n->W2b; a.M = (int)B; a.N = kH; a.K = kH; a.lda = kH; a.ldb = kH;
+        a.mask = n->H1; a.out = n->dZ1; a.ldo = kH;
+        st = launch_gemm<true, false, EPI_MASK>(a, 1, s);
+    }
     if (st) return st;
     colsum_kernel<<<chunks, 256, 0, s>>>(n->dZ1, (int)B, pw3);
     reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pw3, chunks, kH, n->g + n->ob1);
-    // dW2 = dZ2^T . H1 and dW1 = dZ1^T . X, split over the batch
-    int splits = (int)std::min<long long>(32, B / BKT);
-    while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
-    a = GemmArgs{};
-    a.A = n->dZ2; a.B = n->H1; a.M = kH; a.N = kH; a.K = (int)B; a.lda = kH; a.ldb = kH; a.partial = n->part;
-    if ((st = launch_gemm<false, false, EPI_PARTIAL>(a, splits, s))) return st;
-    reduce_parts_kernel<<<blocks_for((long long)kH * kH, 256), 256, 0, s>>>(n->part, splits, kH * kH, n->g + n->oW2);
-    a.A = n->dZ1; a.B = X; a.N = n->kpad; a.ldb = n->kpad;
-    if ((st = launch_gemm<false, false, EPI_PARTIAL>(a, splits, s))) return st;
-    reduce_parts_kernel<<<blocks_for((long long)kH * n->kpad, 256), 256, 0, s>>>(n->part, splits, kH * n->kpad,
-                                                                                 n->g + n->oW1);
+    // dW2 = dZ2^T . H1 and dW1 = dZ1^T . X, split over the batch into partial sums
+    auto weight_grad = [&](const __nv_bfloat16* A, const __nv_bfloat16* Bm, int N, int ldb, float* out) -> int {
+        int splits = 0, r;
+        if (tc && umma_dense_supported(kH, N, (int)B)) {
+            r = umma_grad_weights(A, kH, Bm, ldb, kH, N, (int)B, n->part, n->part_floats, &splits, s);
+        } else {
+            splits = (int)std::min<long long>(32, B / BKT);
+            while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
+            GemmArgs a{};
+            a.A = A; a.B = Bm; a.M = kH; a.N = N; a.K = (int)B; a.lda = kH; a.ldb = ldb; a.partial = n->part;
+            r = launch_gemm<false, false, EPI_PARTIAL>(a, splits, s);
+        }
+        if (r) return r;
+        reduce_parts_kernel<<<blocks_for((long long)kH * N, 256), 256, 0, s>>>(n->part, splits, kH * N, out);
+        return LUDAX_OK;
+    };
+    if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->g + n->oW2))) return st;
+    if ((st = weight_grad(n->dZ1, X, n->kpad, n->kpad, n->g + n->oW1))) return st;
     if (loss_out) sum_kernel<<<1, 1024, 0, s>>>(n->sqerr, (int)B, 1.f / (float)B, loss_out);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }

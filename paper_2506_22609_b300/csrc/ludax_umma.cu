@@ -521,6 +521,246 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
+// ------------------------------------------------------ backward GEMMs --
+// The value net's backward contractions on the same pipeline (one TMA
+// producer warp, one MMA warp, four epilogue warps, two TMEM accumulators),
+// with operands that are K-major as above or MN-major: stored as K rows of M
+// (or N) contiguous elements, which is how activations and gradients
+// [batch][unit] look when the contraction runs over the batch.
+//   GRAD_MASK    : out = bf16(mask > 0 ? A . B : 0) -- dZ1 = (dZ2 . W2) *
+//                  [H1 > 0] with A = dZ2 K-major and B = W2 MN-major;
+//   GRAD_PARTIAL : part[split][m][n] = FP32 sum over the split's share of K
+//                  of A[k][m] B[k][n] -- dW2 = dZ2^T . H1 and dW1 = dZ1^T . X,
+//                  both operands MN-major; the batch is split so that
+//                  (tiles x splits) work units fill the SMs, and the host sums
+//                  the partials in a fixed order.
+// An MN-major operand tile arrives as 64 x 64 boxes (64 K rows of 128
+// bytes, 128-byte swizzle), box h holding elements 64 h .. 64 h + 63 along M
+// (or N): in its shared-memory descriptor the leading byte offset is the
+// 8 KB step between those 64-element blocks and the stride byte offset the
+// 1 KB step between 8-row groups along K; each K = 16 MMA step moves the
+// start by two groups.  GRAD_MASK stages the mask tile of each epilogue warp
+// (its 32 rows x 256 columns) in shared memory with cp.async while the
+// tile's MMAs run, rows XOR-swizzled by 16-byte chunk so the per-row reads
+// are conflict-free; with that buffer the ring has three stages.
+enum { GRAD_MASK = 0, GRAD_PARTIAL = 1 };
+constexpr int MN_BOX = 64 * TK * 2;  // one 64 (M or N) x 64 (K) BF16 box
+constexpr int MASK_WARP_BYTES = 32 * TN * 2;
+template <int EPI>
+struct GradCfg {
+    static constexpr int stages = EPI == GRAD_MASK ? 3 : DENSE_STAGES;
+    static constexpr size_t smem = 1024 + (size_t)stages * STAGE + 4 * BOX_BYTES + 256 +
+                                   (EPI == GRAD_MASK ? 4 * (size_t)MASK_WARP_BYTES : 0);
+};
+
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)(MN_BOX >> 4) << 16;                // leading byte offset: next 64-element block along M / N
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: next 8-row group along K
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+template <bool A_MN, bool B_MN>
+__device__ __forceinline__ void umma_bf16_major(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    // bits 15 / 16 of the instruction descriptor: A / B MN-major
+    constexpr uint32_t idesc = kIdesc | (A_MN ? (1u << 15) : 0u) | (B_MN ? (1u << 16) : 0u);
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32-column chunks c0 .. c0 + NCH - 1 of one accumulator as raw FP32 bits:
+// fn(c, x) with this lane's 32 values; the next chunk's load is in flight
+// while fn runs.
+template <int NCH, class F>
+__device__ __forceinline__ void drain_raw(uint32_t base, F&& fn) {
+    uint32_t r[2][32];
+    tmem_ld32_async(base, r[0]);
+    tmem_wait_ld(r[0]);
+#pragma unroll
+    for (int i = 0; i < NCH; ++i) {
+        if (i + 1 < NCH) tmem_ld32_async(base + (uint32_t)((i + 1) * 32), r[(i + 1) & 1]);
+        fn(i, r[i & 1]);
+        if (i + 1 < NCH) tmem_wait_ld(r[(i + 1) & 1]);
+    }
+}
+
+__device__ __forceinline__ void cp_async16_shared(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+template <bool A_MN, bool B_MN, int EPI>
+__global__ void __launch_bounds__(UMMA_THREADS, 1)
+    umma_grad_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmOut, int M, int N, int kblocks, int splits,
+                     const __nv_bfloat16* __restrict__ mask, int ldm, float* __restrict__ part) {
+    constexpr int NS = GradCfg<EPI>::stages;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* staging = smem + NS * STAGE;
+    uint8_t* smask = staging + 4 * BOX_BYTES;  // GRAD_MASK: four warps' mask tiles
+    uint64_t* full = reinterpret_cast<uint64_t*>(smask + (EPI == GRAD_MASK ? 4 * MASK_WARP_BYTES : 0));
+    uint64_t* empty = full + NS;
+    uint64_t* acc_full = empty + NS;    // [2] MMA -> epilogue
+    uint64_t* acc_empty = acc_full + 2;  // [2] epilogue -> MMA
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntn = N / TN, tiles = (M / TM) * ntn, units = tiles * splits;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 128);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(tmem_slot)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+    // work unit u: tile u % tiles over K blocks [kb0, kb1) of split u / tiles
+    auto unit = [&](int u, int& m0, int& n0, int& sp, int& kb0, int& kb1) {
+        const int tile = u % tiles;
+        sp = u / tiles;
+        m0 = (tile / ntn) * TM;
+        n0 = (tile % ntn) * TN;
+        kb0 = (int)((long long)sp * kblocks / splits);
+        kb1 = (int)((long long)(sp + 1) * kblocks / splits);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            int it = 0;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                int m0, n0, sp, kb0, kb1;
+                unit(u, m0, n0, sp, kb0, kb1);
+                for (int kt = kb0; kt < kb1 && ok; ++kt, ++it) {
+                    const int s = it % NS;
+                    if (it >= NS) ok = mbar_wait(&empty[s], (uint32_t)(((it / NS) & 1) ^ 1));
+                    if (!ok) break;
+                    uint8_t* st = smem + s * STAGE;
+                    mbar_expect_tx(&full[s], STAGE);
+                    if (A_MN) {
+#pragma unroll
+                        for (int h = 0; h < TM / 64; ++h) tma_load_2d(st + h * MN_BOX, &tmA, &full[s], m0 + 64 * h, kt * TK);
+                    } else {
+                        tma_load_2d(st, &tmA, &full[s], kt * TK, m0);
+                    }
+                    if (B_MN) {
+#pragma unroll
+                        for (int h = 0; h < TN / 64; ++h)
+                            tma_load_2d(st + A_TILE + h * MN_BOX, &tmB, &full[s], n0 + 64 * h, kt * TK);
+                    } else {
+                        tma_load_2d(st + A_TILE, &tmB, &full[s], kt * TK, n0);
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int it = 0, local = 0;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++local) {
+                int m0, n0, sp, kb0, kb1;
+                unit(u, m0, n0, sp, kb0, kb1);
+                const int a = local & 1;
+                if (local >= 2) ok = mbar_wait(&acc_empty[a], (uint32_t)(((local >> 1) & 1) ^ 1));
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * TN);
+                for (int kt = kb0; kt < kb1 && ok; ++kt, ++it) {
+                    const int s = it % NS;
+                    ok = mbar_wait(&full[s], (uint32_t)((it / NS) & 1));
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t sa = saddr(smem + s * STAGE);
+                    const uint64_t ad = A_MN ? sw128_mn_desc(sa) : sw128_desc(sa);
+                    const uint64_t bd = B_MN ? sw128_mn_desc(sa + A_TILE) : sw128_desc(sa + A_TILE);
+                    constexpr uint64_t astep = A_MN ? (2048 >> 4) : 2, bstep = B_MN ? (2048 >> 4) : 2;
+#pragma unroll
+                    for (int kk = 0; kk < TK / 16; ++kk)
+                        umma_bf16_major<A_MN, B_MN>(d, ad + astep * kk, bd + bstep * kk, (kt != kb0 || kk) ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                umma_commit(&acc_full[a]);
+            }
+        }
+    } else {  // epilogue warps 2..5: TMEM lane quarter = warp % 4
+        const int q = warp & 3;
+        uint8_t* wmask = smask + q * MASK_WARP_BYTES;
+        int local = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x, ++local) {
+            int m0, n0, sp, kb0, kb1;
+            unit(u, m0, n0, sp, kb0, kb1);
+            const int row0 = m0 + q * 32;
+            if (EPI == GRAD_MASK) {  // this warp's 32 mask rows, 16 bytes per lane per row, while the MMAs run
+                __syncwarp();        // every lane is done reading the previous tile's rows
+                const uint32_t wm = saddr(wmask);
+                for (int r = 0; r < 32; ++r)
+                    cp_async16_shared(wm + (uint32_t)(r * (TN * 2) + ((lane ^ (r & 7)) * 16)),
+                                      mask + (size_t)(row0 + r) * ldm + n0 + lane * 8);
+                asm volatile("cp.async.commit_group;\n" ::: "memory");
+            }
+            const int a = local & 1;
+            if (ok) ok = mbar_wait(&acc_full[a], (uint32_t)((local >> 1) & 1));
+            ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            if (EPI == GRAD_MASK) {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                __syncwarp();
+            }
+            const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
+            drain_raw<TN / 32>(base, [&](int c, const uint32_t* x) {
+                if (EPI == GRAD_PARTIAL) {
+                    float4* dst = reinterpret_cast<float4*>(part + ((size_t)sp * M + row0 + lane) * N + n0 + c * 32);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        dst[j] = make_float4(__uint_as_float(x[4 * j]), __uint_as_float(x[4 * j + 1]),
+                                             __uint_as_float(x[4 * j + 2]), __uint_as_float(x[4 * j + 3]));
+                } else {
+                    __align__(16) __nv_bfloat162 v[16];
+                    const uint8_t* myrow = wmask + lane * (TN * 2);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {  // 16-byte chunk 4 c + j of this lane's mask row
+                        const uint4 m4 = *reinterpret_cast<const uint4*>(myrow + (((4 * c + j) ^ (lane & 7)) * 16));
+                        const __nv_bfloat162* mk = reinterpret_cast<const __nv_bfloat162*>(&m4);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 mf = __bfloat1622float2(mk[e]);
+                            const int i = 8 * j + 2 * e;
+                            v[4 * j + e] = __floats2bfloat162_rn(mf.x > 0.f ? __uint_as_float(x[i]) : 0.f,
+                                                                 mf.y > 0.f ? __uint_as_float(x[i + 1]) : 0.f);
+                        }
+                    }
+                    stage_chunk<1>(c, v, staging + q * BOX_BYTES, lane, &tmOut, n0, row0);
+                }
+            });
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
+        }
+        if (EPI == GRAD_MASK) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // nothing in flight at exit
+    }
+    if (!ok) atomicOr(&g_umma_error, 1);
+    if (warp >= 2 && lane == 0) tma_store_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
 // ------------------------------------------------------ wait self-test --
 // The failure path of the bounded waits, exercised without a fault: one
 // thread waits on an mbarrier that nothing will ever arrive at, gives up
@@ -617,6 +857,65 @@ int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const flo
     umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias,
                                                                   static_cast<const __nv_bfloat16*>(w3), zpart);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+template <bool A_MN, bool B_MN, int EPI>
+static int launch_grad(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mo, int M, int N, int kblocks,
+                       int splits, const void* mask, int ldm, float* part, int sms, cudaStream_t s) {
+    auto k = umma_grad_kernel<A_MN, B_MN, EPI>;
+    static bool attr = false;  // per instantiation
+    if (!attr) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradCfg<EPI>::smem) != cudaSuccess)
+            return LUDAX_ERR_CUDA;
+        attr = true;
+    }
+    const int units = (M / TM) * (N / TN) * splits;
+    k<<<units < sms ? units : sms, UMMA_THREADS, GradCfg<EPI>::smem, s>>>(
+        ma, mb, mo, M, N, kblocks, splits, static_cast<const __nv_bfloat16*>(mask), ldm, part);
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+}
+
+static int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+    }
+    return sms;
+}
+
+int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, cudaStream_t s) {
+    if (!umma_dense_supported(M, N, K) || !A || !B || !mask || !out || N % 8 || K % 8 || ((uintptr_t)A % 16) ||
+        ((uintptr_t)B % 16) || ((uintptr_t)mask % 16) || ((uintptr_t)out % 16))
+        return LUDAX_ERR_SIZE;
+    const int sms = sm_count();
+    if (!sms) return LUDAX_ERR_CUDA;
+    CUtensorMap ma, mb, mo;
+    // A [M][K] K-major; B [K][N] MN-major (64 x 64 boxes); out [M][N] in 32-row boxes
+    if (!make_map(&ma, A, M, K, TM, K) || !make_map(&mb, B, K, N, 64, N) || !make_map(&mo, out, M, N, 32, N))
+        return LUDAX_ERR_CUDA;
+    return launch_grad<false, true, GRAD_MASK>(ma, mb, mo, M, N, K / TK, 1, mask, N, nullptr, sms, s);
+}
+
+int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* part,
+                      long long part_floats, int* splits_out, cudaStream_t s) {
+    if (!umma_dense_supported(M, N, K) || !A || !B || !part || !splits_out || lda < M || ldb < N || lda % 8 ||
+        ldb % 8 || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)part % 16))
+        return LUDAX_ERR_SIZE;
+    const int sms = sm_count();
+    if (!sms) return LUDAX_ERR_CUDA;
+    const int tiles = (M / TM) * (N / TN), kblocks = K / TK;
+    long long splits = sms / tiles;
+    if (splits > kblocks) splits = kblocks;  // every split gets at least one K block
+    if (splits > part_floats / ((long long)M * N)) splits = part_floats / ((long long)M * N);
+    if (splits < 1) return LUDAX_ERR_SIZE;
+    CUtensorMap ma, mb;
+    // A [K][M] and B [K][N], both MN-major (64 x 64 boxes); nothing is stored through a tensor map
+    if (!make_map(&ma, A, K, M, 64, lda) || !make_map(&mb, B, K, N, 64, ldb)) return LUDAX_ERR_CUDA;
+    *splits_out = (int)splits;
+    return launch_grad<true, true, GRAD_PARTIAL>(ma, mb, ma, M, N, kblocks, (int)splits, nullptr, 0, part, sms, s);
 }
 
 int umma_mlp_scratch_rows() {

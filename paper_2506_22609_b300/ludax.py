@@ -507,8 +507,8 @@ class Net:
         ludax_net_set_params(self.handle, params.to(torch.float32).contiguous())
 
     def set_tensor_path(self, use_tcgen05):
-        """True / 1: tcgen05 (one-launch MLP for inference), 2: tcgen05 as two
-        layer launches, False / 0: mma.sync."""
+        """True / 1: tcgen05 (one-launch MLP for inference; tcgen05 backward),
+        2: tcgen05 as two layer launches, False / 0: mma.sync everywhere."""
         mode = int(use_tcgen05) if not isinstance(use_tcgen05, bool) else (1 if use_tcgen05 else 0)
         _check(lib().ludax_net_set_tensor_path(self.handle, mode), "ludax_net_set_tensor_path")
 

@@ -92,30 +92,89 @@ def test_forward_matches_oracle(L, cells, B):
     assert np.allclose(net.get_params().cpu().numpy(), theta)
 
 
-@pytest.mark.parametrize("cells,B", [(64, 512), (121, 256)])
-def test_gradient_matches_oracle(L, cells, B):
+def grad_bf16(theta, X, y, K):
+    """fp64 gradient with the kernels' rounding points: BF16 weights, BF16
+    hidden activations, and the hidden-layer gradients dZ2 and dZ1 rounded to
+    BF16 before the contractions that read them (db2 sums dZ2 unrounded)."""
+    P = M.unflatten(rounded_theta(theta, K), K)
+    B = X.shape[0]
+    h1 = M.bf16_round(np.maximum(X @ P["W1"].T + P["b1"], 0))
+    h2 = M.bf16_round(np.maximum(h1 @ P["W2"].T + P["b2"], 0))
+    v = np.tanh(h2 @ P["w3"] + P["b3"][0])
+    g3 = 2.0 * (0.5 * (v + 1) - y) / B * 0.5 * (1 - v * v)
+    dz2 = np.outer(g3, P["w3"]) * (h2 > 0)
+    dz2b = M.bf16_round(dz2)
+    dz1 = M.bf16_round((dz2b @ P["W2"]) * (h1 > 0))
+    g = {"W1": dz1.T @ X, "b1": dz1.sum(0), "W2": dz2b.T @ h1, "b2": dz2.sum(0), "w3": h2.T @ g3,
+         "b3": np.array([g3.sum()])}
+    return M.flatten(g, K)
+
+
+def blocks_close(g, want, K, rel_tol, cos_tol):
+    G_, Wt = M.unflatten(g, K), M.unflatten(want, K)
+    for name, _ in M.param_shapes(K):
+        a, b = G_[name].ravel(), Wt[name].ravel()
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+        assert rel < rel_tol and cos > cos_tol, (name, rel, cos)
+
+
+def check_gradient(g, theta, X, y, K, cells, loss=None):
+    """g (flat, from the kernels), per parameter block: within FP32
+    accumulation order of the fp64 gradient taken with the kernels' BF16
+    rounding points, and within the BF16 rounding error (a few percent at
+    small batches, where few rows average it out) of the plain fp64 gradient
+    of the same BF16 weights."""
+    th = rounded_theta(theta, K)
+    if loss is not None:
+        assert abs(loss - M.loss(th, X, y, K)) < 1e-3 * max(1.0, M.loss(th, X, y, K))
+    blocks_close(g, grad_bf16(theta, X, y, K), K, 2e-3, 0.99999)
+    blocks_close(g, M.grad(th, X, y, K), K, 6e-2, 0.998)
+    # padded input columns never receive gradient
+    assert np.abs(M.unflatten(g, K)["W1"][:, 2 * cells + 1:]).max() == 0.0
+
+
+# B = 128: two K blocks, so two splits of the weight gradients; B = 4736 =
+# 37 x 128: 74 K blocks over 18 (dW2) and 37 (dW1) splits, unequal in size.
+@pytest.mark.parametrize("cells,B", [(64, 512), (121, 256), (64, 128), (64, 4736)])
+@pytest.mark.parametrize("path", [1, 0])  # tcgen05 backward, mma.sync backward
+def test_gradient_matches_oracle(L, cells, B, path):
     K = W.net_in_pad(cells)
     theta = W.init_params(cells, 3)
     rng = np.random.default_rng(5)
     X = np.zeros((B, K))
     X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
     y = rng.random(B)
-    net = L.Net(cells, 1024)
+    net = L.Net(cells, max(1024, B))
     net.set_params(torch.from_numpy(theta).cuda())
+    net.set_tensor_path(path)
     g, loss = net.grad(bf16_bits(X), torch.from_numpy(y.astype(np.float32)).cuda())
-    g = g.cpu().numpy().astype(np.float64)
-    th = rounded_theta(theta, K)
-    want = M.grad(th, X, y, K)
-    assert abs(loss.item() - M.loss(th, X, y, K)) < 1e-3 * max(1.0, M.loss(th, X, y, K))
-    G_ = M.unflatten(g, K)
-    Wt = M.unflatten(want, K)
-    for name, _ in M.param_shapes(K):
-        a, b = G_[name].ravel(), Wt[name].ravel()
-        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
-        cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
-        assert rel < 3e-2 and cos > 0.999, (name, rel, cos)
-    # padded input columns never receive gradient
-    assert np.abs(G_["W1"][:, 2 * cells + 1:]).max() == 0.0
+    assert L.ludax_device_error() == 0
+    check_gradient(g.cpu().numpy().astype(np.float64), theta, X, y, K, cells, loss.item())
+
+
+def test_gradient_training_batch(L):
+    """The training batch (65,536 rows of Othello inputs): the tcgen05
+    backward against the fp64 oracle, and against the mma.sync backward."""
+    cells, B = 64, 65536
+    K = W.net_in_pad(cells)
+    theta = W.init_params(cells, 9)
+    rng = np.random.default_rng(8)
+    X = np.zeros((B, K))
+    X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
+    y = rng.random(B)
+    net = L.Net(cells, B)
+    net.set_params(torch.from_numpy(theta).cuda())
+    xb, yb = bf16_bits(X), torch.from_numpy(y.astype(np.float32)).cuda()
+    grads = {}
+    for path in (1, 0):
+        net.set_tensor_path(path)
+        g, _ = net.grad(xb, yb)
+        grads[path] = g.cpu().numpy().astype(np.float64)
+    assert L.ludax_device_error() == 0
+    check_gradient(grads[1], theta, X, y, K, cells)
+    a, b = grads[1], grads[0]
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-2
 
 
 def test_adam_step_matches_oracle(L):
