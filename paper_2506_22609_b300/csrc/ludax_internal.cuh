@@ -102,8 +102,9 @@ int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, 
                     cudaStream_t s);
 // The same layer with row pitches lda / ldb (K may be a prefix of the rows:
 // columns past K are not read) and, with w3 non-null (N BF16 weights), the
-// head fused into the epilogue: instead of storing the rows, zpart[m * (N /
-// 256) + j] = sum over the j-th 256 columns of bf16(relu(.))[m][n] * w3[n].
+// head fused into the epilogue: zpart[m * (N / 256) + j] = sum over the j-th
+// 256 columns of bf16(relu(.))[m][n] * w3[n]; the rows are stored as well
+// when out is non-null (at least one of out and w3 must be given).
 int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const float* bias, void* out, int ldo,
                        const void* w3, float* zpart, int M, int N, int K, cudaStream_t s);
 // Both hidden layers (512 wide) and the head in one launch for inference:

@@ -244,59 +244,182 @@ __global__ void head_forward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16
     }
 }
 
-// dZ2[b][j] = g3[b] w3[j] [H2[b][j] > 0] (stored bf16), plus per-chunk column
-// partials of dw3 = sum_b g3 H2 and db2 = sum_b dZ2, and of db3 = sum_b g3.
-constexpr int HB_ROWS = 256;
-__global__ void head_backward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16* w3, const float* g3, int B,
-                                     __nv_bfloat16* dZ2, float* part_w3, float* part_b2, float* part_b3) {
-    const int j = threadIdx.x * 2;  // 256 threads x 2 columns
-    const int r0 = blockIdx.x * HB_ROWS;
-    float2 w = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(w3 + j));
-    float aw0 = 0, aw1 = 0, ab0 = 0, ab1 = 0, ag = 0;
-    for (int r = r0; r < min(r0 + HB_ROWS, B); ++r) {
-        float gr = g3[r];
-        float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(H2 + (size_t)r * kH + j));
-        float d0 = h.x > 0.f ? gr * w.x : 0.f, d1 = h.y > 0.f ? gr * w.y : 0.f;
-        *reinterpret_cast<__nv_bfloat162*>(dZ2 + (size_t)r * kH + j) = __floats2bfloat162_rn(d0, d1);
-        aw0 = fmaf(gr, h.x, aw0);
-        aw1 = fmaf(gr, h.y, aw1);
-        ab0 += d0;
-        ab1 += d1;
-        ag += gr;
+// Row-chunk kernels over [B][kH] BF16 matrices: a 256-thread block takes
+// HB_ROWS rows; its thread t covers columns 8 (t % 64) .. 8 (t % 64) + 7 of
+// rows r0 + t / 64, r0 + t / 64 + 4, ... (16-byte loads, four rows in
+// flight), and the four row groups' sums are added in a fixed order.
+constexpr int HB_ROWS = 128, HB_GROUPS = 4;
+constexpr int HB_COLS = 2 * kH + 2;  // head partials per chunk: db2 | dw3 | db3 | squared error
+
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float* f) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float2 x = __bfloat1622float2(h[e]);
+        f[2 * e] = x.x;
+        f[2 * e + 1] = x.y;
     }
-    part_w3[(size_t)blockIdx.x * kH + j] = aw0;
-    part_w3[(size_t)blockIdx.x * kH + j + 1] = aw1;
-    part_b2[(size_t)blockIdx.x * kH + j] = ab0;
-    part_b2[(size_t)blockIdx.x * kH + j + 1] = ab1;
-    if (threadIdx.x == 0) part_b3[blockIdx.x] = ag;
 }
 
-// per-chunk column sums of a [B][kH] bf16 matrix (db1 = sum_b dZ1)
-__global__ void colsum_kernel(const __nv_bfloat16* X, int B, float* part) {
-    const int j = threadIdx.x * 2;
-    const int r0 = blockIdx.x * HB_ROWS;
-    float a0 = 0, a1 = 0;
-    for (int r = r0; r < min(r0 + HB_ROWS, B); ++r) {
-        float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(X + (size_t)r * kH + j));
-        a0 += v.x;
-        a1 += v.y;
+// dZ2[b][j] = g3[b] w3[j] [H2[b][j] > 0] (stored bf16), plus the chunk's
+// partials in row blockIdx.x of part[chunks][HB_COLS]: db2 = sum_b dZ2
+// (unrounded), dw3 = sum_b g3 H2, db3 = sum_b g3 and the summed squared
+// error -- b2, w3, b3 in the order the gradient vector stores them.
+__global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16* w3,
+                                                            const float* g3, const float* sqerr, int B,
+                                                            __nv_bfloat16* dZ2, float* part) {
+    __shared__ float sh[HB_GROUPS - 1][HB_COLS];
+    const int grp = threadIdx.x >> 6, j0 = (threadIdx.x & 63) * 8;
+    const bool first = (threadIdx.x & 63) == 0;
+    float w[8], ab[8], aw[8], ag = 0.f, al = 0.f;
+    load8(w3 + j0, w);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) ab[e] = aw[e] = 0.f;
+    const int r0 = blockIdx.x * HB_ROWS, r1 = min(r0 + HB_ROWS, B);
+#pragma unroll 4
+    for (int r = r0 + grp; r < r1; r += HB_GROUPS) {
+        const float gr = g3[r];
+        float h[8];
+        load8(H2 + (size_t)r * kH + j0, h);
+        __align__(16) __nv_bfloat162 d[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float d0 = h[2 * e] > 0.f ? gr * w[2 * e] : 0.f, d1 = h[2 * e + 1] > 0.f ? gr * w[2 * e + 1] : 0.f;
+            d[e] = __floats2bfloat162_rn(d0, d1);
+            ab[2 * e] += d0;
+            ab[2 * e + 1] += d1;
+            aw[2 * e] = fmaf(gr, h[2 * e], aw[2 * e]);
+            aw[2 * e + 1] = fmaf(gr, h[2 * e + 1], aw[2 * e + 1]);
+        }
+        *reinterpret_cast<uint4*>(dZ2 + (size_t)r * kH + j0) = *reinterpret_cast<const uint4*>(d);
+        if (first) {
+            ag += gr;
+            al += sqerr[r];
+        }
     }
-    part[(size_t)blockIdx.x * kH + j] = a0;
-    part[(size_t)blockIdx.x * kH + j + 1] = a1;
+    if (grp > 0) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            sh[grp - 1][j0 + e] = ab[e];
+            sh[grp - 1][kH + j0 + e] = aw[e];
+        }
+        if (first) {
+            sh[grp - 1][2 * kH] = ag;
+            sh[grp - 1][2 * kH + 1] = al;
+        }
+    }
+    __syncthreads();
+    if (grp == 0) {
+        float* out = part + (size_t)blockIdx.x * HB_COLS;
+        for (int g = 0; g < HB_GROUPS - 1; ++g) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                ab[e] += sh[g][j0 + e];
+                aw[e] += sh[g][kH + j0 + e];
+            }
+            if (first) {
+                ag += sh[g][2 * kH];
+                al += sh[g][2 * kH + 1];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            out[j0 + e] = ab[e];
+            out[kH + j0 + e] = aw[e];
+        }
+        if (first) {
+            out[2 * kH] = ag;
+            out[2 * kH + 1] = al;
+        }
+    }
 }
 
-// out[i] = sum_s part[s*n + i] (in a fixed order)
-__global__ void reduce_parts_kernel(const float* part, int splits, int n, float* out) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// the chunk's column sums of a [B][kH] BF16 matrix into row blockIdx.x of
+// part[chunks][kH] (db1 = sum_b dZ1)
+__global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* X, int B, float* part) {
+    __shared__ float sh[HB_GROUPS - 1][kH];
+    const int grp = threadIdx.x >> 6, j0 = (threadIdx.x & 63) * 8;
+    float a[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) a[e] = 0.f;
+    const int r0 = blockIdx.x * HB_ROWS, r1 = min(r0 + HB_ROWS, B);
+#pragma unroll 4
+    for (int r = r0 + grp; r < r1; r += HB_GROUPS) {
+        float v[8];
+        load8(X + (size_t)r * kH + j0, v);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a[e] += v[e];
+    }
+    if (grp > 0)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) sh[grp - 1][j0 + e] = a[e];
+    __syncthreads();
+    if (grp == 0) {
+        for (int g = 0; g < HB_GROUPS - 1; ++g)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) a[e] += sh[g][j0 + e];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) part[(size_t)blockIdx.x * kH + j0 + e] = a[e];
+    }
+}
+
+// out[i] = scale * sum over p < parts of part[p * ld + i], i < n, for many
+// parts and few columns: a 1024-thread block takes 32 columns, thread
+// (tx, ty) sums parts ty, ty + 32, ... of column tx, and the 32 sums are
+// added in a fixed order.
+__global__ void __launch_bounds__(1024) reduce_cols_kernel(const float* part, int parts, int ld, int n, float scale,
+                                                           float* out) {
+    __shared__ float sh[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + tx;
     float a = 0.f;
-    for (int s = 0; s < splits; ++s) a += part[(size_t)s * n + i];
-    out[i] = a;
+    if (i < n) {
+#pragma unroll 8
+        for (int p = ty; p < parts; p += 32) a += part[(size_t)p * ld + i];
+    }
+    sh[ty][tx] = a;
+    __syncthreads();
+    if (ty == 0 && i < n) {
+        float t = 0.f;
+        for (int k = 0; k < 32; ++k) t += sh[k][tx];
+        out[i] = t * scale;
+    }
+}
+
+// out[i] = sum_s part[s*n + i] (in a fixed order), four columns per thread
+// (n % 4 == 0): few parts, many columns (the split weight gradients).  part
+// is 16-byte aligned; out (a block of the flat gradient vector) is only
+// 4-byte aligned, so it is written one float at a time.
+__global__ void reduce_parts_kernel(const float* part, int splits, int n, float* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * i >= n) return;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+    for (int s = 0; s < splits; ++s) {
+        const float4 v = *reinterpret_cast<const float4*>(part + (size_t)s * n + 4 * i);
+        a.x += v.x;
+        a.y += v.y;
+        a.z += v.z;
+        a.w += v.w;
+    }
+    out[4 * i] = a.x;
+    out[4 * i + 1] = a.y;
+    out[4 * i + 2] = a.z;
+    out[4 * i + 3] = a.w;
 }
 
 // Adam (Kingma & Ba, Algorithm 1) on the flat FP32 parameters, then the BF16
 // copies the GEMMs read.  bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
-__global__ void adam_kernel(float* p, float* m, float* v, const float* g, long long n, float lr, float bc1, float bc2) {
+// The updated weights also go to their BF16 copies: W1 | W2 | w3 back to
+// back in bf, the flat vector's layout W1 | b1 | W2 | b2 | w3 | b3 without
+// the biases (each bias is kH long; b3 is last).
+struct BfCopy {
+    __nv_bfloat16* bf;
+    long long ob1, oW2, ob2, ow3, ob3;
+};
+__global__ void adam_kernel(float* p, float* m, float* v, const float* g, long long n, float lr, float bc1, float bc2,
+                            BfCopy c) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -305,28 +428,16 @@ __global__ void adam_kernel(float* p, float* m, float* v, const float* g, long l
     float vi = b2 * v[i] + (1.f - b2) * gi * gi;
     m[i] = mi;
     v[i] = vi;
-    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    p[i] = pi;
+    if (i < c.ob1) c.bf[i] = __float2bfloat16_rn(pi);
+    else if (i >= c.oW2 && i < c.ob2) c.bf[i - kH] = __float2bfloat16_rn(pi);
+    else if (i >= c.ow3 && i < c.ob3) c.bf[i - 2 * kH] = __float2bfloat16_rn(pi);
 }
 
 __global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, long long n) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
-}
-
-__global__ void sum_kernel(const float* x, int n, float scale, float* out) {
-    __shared__ float sh[32];
-    float a = 0.f;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        a = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-        if (threadIdx.x == 0) *out = a * scale;
-    }
 }
 
 // ---------------------------------------------------------- env -> input --
@@ -505,13 +616,21 @@ int dense_layer(ludax_net* n, const __nv_bfloat16* A, const __nv_bfloat16* W, co
     return launch_gemm<true, true, EPI_BIAS_RELU>(a, 1, n->stream);
 }
 
-// p[row] from the head partials of the fused second layer
-__global__ void head_finish_kernel(const float* zpart, int parts, const float* b3, int B, float* p_out) {
+// p[row] from the head partials of the fused second layer; with labels also
+// g3[row] = dL/dz for L = mean (p - y)^2 and the row's squared error
+__global__ void head_finish_kernel(const float* zpart, int parts, const float* b3, int B, float* p_out,
+                                   const float* y, float* g3, float* sqerr) {
     int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= B) return;
     float z = 0.f;
     for (int i = 0; i < parts; ++i) z += zpart[(size_t)row * parts + i];
-    p_out[row] = 0.5f * (tanhf(z + b3[0]) + 1.f);
+    const float v = tanhf(z + b3[0]), p = 0.5f * (v + 1.f);
+    if (p_out) p_out[row] = p;
+    if (y) {
+        const float d = p - y[row];
+        g3[row] = d * (1.f - v * v) / (float)B;  // 2 (p-y)/B * (1/2) (1 - v^2)
+        sqerr[row] = d * d;
+    }
 }
 
 // Forward pass to p (and, with labels y, the per-row gradient g3 of the loss).
@@ -549,11 +668,24 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
                 st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, nullptr, 0, n->w3b, zpart, (int)B, kH, kH, s);
         }
         if (st) return st;
-        head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, parts, n->p + n->ob3, (int)B, p);
+        head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, parts, n->p + n->ob3, (int)B, p, nullptr,
+                                                               nullptr, nullptr);
         return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
     }
     int st = dense_layer(n, X, n->W1b, n->p + n->ob1, n->H1, B, n->kpad);
     if (st) return st;
+    if (n->use_tcgen05 && umma_dense_supported((int)B, kH, kH)) {
+        // training forward: the second layer stores its rows for the backward
+        // pass and takes the head's dot products in the same epilogue (two
+        // partials per row, in the backward pass's not yet used buffer)
+        float* zpart = n->part;
+        if ((st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, n->H2, kH, n->w3b, zpart, (int)B, kH, kH,
+                                     s)))
+            return st;
+        head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, kH / 256, n->p + n->ob3, (int)B, p, y, n->g3,
+                                                               n->sqerr);
+        return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    }
     if ((st = dense_layer(n, n->H1, n->W2b, n->p + n->ob2, n->H2, B, kH))) return st;
     head_forward_kernel<<<blocks_for(B, 8), 256, 0, s>>>(n->H2, n->w3b, n->p + n->ob3, (int)B, p, y, n->g3, n->sqerr);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
@@ -563,13 +695,11 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
 int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, float* loss_out) {
     cudaStream_t s = n->stream;
     const int chunks = (int)((B + HB_ROWS - 1) / HB_ROWS);
-    float* pw3 = n->part;
-    float* pb2 = pw3 + (size_t)chunks * kH;
-    float* pb3 = pb2 + (size_t)chunks * kH;
-    head_backward_kernel<<<chunks, 256, 0, s>>>(n->H2, n->w3b, n->g3, (int)B, n->dZ2, pw3, pb2, pb3);
-    reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pw3, chunks, kH, n->g + n->ow3);
-    reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pb2, chunks, kH, n->g + n->ob2);
-    reduce_parts_kernel<<<1, 32, 0, s>>>(pb3, chunks, 1, n->g + n->ob3);
+    float* hpart = n->part;  // [chunks][HB_COLS]
+    head_backward_kernel<<<chunks, 256, 0, s>>>(n->H2, n->w3b, n->g3, n->sqerr, (int)B, n->dZ2, hpart);
+    // db2 | dw3 | db3 land where the gradient vector keeps b2, w3, b3; then the mean loss
+    reduce_cols_kernel<<<(2 * kH + 1 + 31) / 32, 1024, 0, s>>>(hpart, chunks, HB_COLS, 2 * kH + 1, 1.f, n->g + n->ob2);
+    if (loss_out) reduce_cols_kernel<<<1, 1024, 0, s>>>(hpart + 2 * kH + 1, chunks, HB_COLS, 1, 1.f / (float)B, loss_out);
     // dZ1 = (dZ2 . W2) * [H1 > 0]
     const bool tc = n->use_tcgen05 && umma_dense_supported((int)B, kH, kH);
     int st;
@@ -582,8 +712,8 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, float* loss_
         st = launch_gemm<true, false, EPI_MASK>(a, 1, s);
     }
     if (st) return st;
-    colsum_kernel<<<chunks, 256, 0, s>>>(n->dZ1, (int)B, pw3);
-    reduce_parts_kernel<<<blocks_for(kH, 256), 256, 0, s>>>(pw3, chunks, kH, n->g + n->ob1);
+    colsum_kernel<<<chunks, 256, 0, s>>>(n->dZ1, (int)B, n->part);
+    reduce_cols_kernel<<<kH / 32, 1024, 0, s>>>(n->part, chunks, kH, kH, 1.f, n->g + n->ob1);
     // dW2 = dZ2^T . H1 and dW1 = dZ1^T . X, split over the batch into partial sums
     auto weight_grad = [&](const __nv_bfloat16* A, const __nv_bfloat16* Bm, int N, int ldb, float* out) -> int {
         int splits = 0, r;
@@ -597,12 +727,11 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, float* loss_
             r = launch_gemm<false, false, EPI_PARTIAL>(a, splits, s);
         }
         if (r) return r;
-        reduce_parts_kernel<<<blocks_for((long long)kH * N, 256), 256, 0, s>>>(n->part, splits, kH * N, out);
+        reduce_parts_kernel<<<blocks_for((long long)kH * N / 4, 256), 256, 0, s>>>(n->part, splits, kH * N, out);
         return LUDAX_OK;
     };
     if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->g + n->oW2))) return st;
     if ((st = weight_grad(n->dZ1, X, n->kpad, n->kpad, n->g + n->oW1))) return st;
-    if (loss_out) sum_kernel<<<1, 1024, 0, s>>>(n->sqerr, (int)B, 1.f / (float)B, loss_out);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
@@ -743,9 +872,9 @@ int ludax_net_train_step(ludax_net* n, const uint16_t* x_dev, const float* y_dev
     if (st) return st;
     n->t += 1;
     const float bc1 = 1.f - powf(0.9f, (float)n->t), bc2 = 1.f - powf(0.999f, (float)n->t);
-    adam_kernel<<<blocks_for(n->nparams, 256), 256, 0, n->stream>>>(n->p, n->m, n->v, n->g, n->nparams, lr, bc1, bc2);
-    if (cudaGetLastError() != cudaSuccess) return LUDAX_ERR_CUDA;
-    return refresh_bf16(n);
+    adam_kernel<<<blocks_for(n->nparams, 256), 256, 0, n->stream>>>(
+        n->p, n->m, n->v, n->g, n->nparams, lr, bc1, bc2, BfCopy{n->W1b, n->ob1, n->oW2, n->ob2, n->ow3, n->ob3});
+    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
 int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld) {

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     umma_dense_relu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                            const __grid_constant__ CUtensorMap tmOut, int M, int N, int K,
                            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ w3,
-                           float* __restrict__ zpart) {
+                           float* __restrict__ zpart, int store) {
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + RING;  // 1024-byte aligned: the 128-byte swizzle pattern repeats every 1024 bytes
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     float* sw3 = sbias + MAX_N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ktiles = K / TK, ntn = N / TN, ntiles = (M / TM) * ntn;
-    const bool head = w3 != nullptr;  // fused head: per-row dot products with w3 instead of stored rows
+    const bool head = w3 != nullptr;  // fused head: per-row dot products with w3 (and the rows stored if store)
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         sbias[i] = bias[i];
         sw3[i] = head ? __bfloat162float(w3[i]) : 0.f;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             float z = 0.f;  // fused head: this row's dot product over the tile's columns
             drain_accumulator<TN / 32>(base, 0, sbias + n0, [&](int c, const __nv_bfloat162* v) {
                 if (head) z += dot_chunk(v, sw3 + n0 + c * 32);  // the BF16 activations times w3
-                else stage_chunk<1>(c, v, box, lane, &tmOut, n0, row0);
+                if (store) stage_chunk<1>(c, v, box, lane, &tmOut, n0, row0);
             });
             if (head) zpart[(size_t)(row0 + lane) * ntn + (t % ntn)] = z;
             tc_fence_before();
@@ -828,15 +828,15 @@ int umma_dense_relu(const void* A, const void* B, const float* bias, void* out, 
 
 int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const float* bias, void* out, int ldo,
                        const void* w3, float* zpart, int M, int N, int K, cudaStream_t s) {
-    const bool head = w3 != nullptr;
+    const bool head = w3 != nullptr, store = out != nullptr;
     if (!umma_dense_supported(M, N, K) || lda < K || ldb < K || lda % 8 || ldb % 8 || ((uintptr_t)A % 16) ||
         ((uintptr_t)B % 16))
         return LUDAX_ERR_SIZE;
-    if (head ? !zpart : (!out || ldo % 8 || ((uintptr_t)out % 16))) return LUDAX_ERR_SIZE;
+    if ((!head && !store) || (head && !zpart) || (store && (ldo % 8 || ((uintptr_t)out % 16)))) return LUDAX_ERR_SIZE;
     CUtensorMap ma, mb, mo;
-    // in head mode nothing is stored: the output map is a valid placeholder over A
+    // with nothing stored the output map is a valid placeholder over A
     if (!make_map(&ma, A, M, K, TM, lda) || !make_map(&mb, B, N, K, TN, ldb) ||
-        !(head ? make_map(&mo, A, M, K, 32, lda) : make_map(&mo, out, M, N, 32, ldo)))
+        !(store ? make_map(&mo, out, M, N, 32, ldo) : make_map(&mo, A, M, K, 32, lda)))
         return LUDAX_ERR_CUDA;
     static bool attr = false;
     if (!attr) {
@@ -855,7 +855,8 @@ int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const flo
     const int ntiles = (M / TM) * (N / TN);
     const int grid = ntiles < sms ? ntiles : sms;
     umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias,
-                                                                  static_cast<const __nv_bfloat16*>(w3), zpart);
+                                                                  static_cast<const __nv_bfloat16*>(w3), zpart,
+                                                                  store ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
