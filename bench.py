@@ -4,7 +4,7 @@
                     [--workload c4|ttt|othello|hex11|gomoku|pente|yavalath|line_c5|wolf_sheep|
                                 draughts|hasami_shogi|mixed|step_c4]
                     [--no-extras] [--no-cpu-baseline] [--only dense_layer|gavel_library|
-                     batch_sweep|value_net|value_estimator|int_peak]
+                     batch_sweep|value_net|value_estimator|int_peak|train_step]
 
 One step = one fused playout launch over the whole batch: every env of the
 workload is reset to the start position and played to the end of its game
@@ -69,7 +69,7 @@ def parse():
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net", "value_estimator",
-                                      "int_peak"],
+                                      "int_peak", "train_step"],
                    default=None,
                    help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -511,6 +511,40 @@ def bench_dense(L, peaks, flush_buf, M=65536, N=512, K=512):
     return res
 
 
+def bench_train_step(L, peaks, flush_buf, steps=20, warmup=3, B=65536):
+    """One Adam step of the value net (forward with labels, backward, Adam)
+    on a 65,536-row batch of Othello (129 inputs) and Hex 11 (243 inputs)
+    rows, on the tcgen05 path and on the mma.sync path; the rows hold a
+    stone in 30% of the cells.  FLOPs per step: the forward, dZ1 and the two
+    weight gradients, 2 B (2 * in_pad * 512 + 3 * 512 * 512 + 512)."""
+    import torch
+
+    from paper_2506_22609_b300 import workloads as W
+
+    out = {}
+    g = torch.Generator(device="cuda").manual_seed(3)
+    for game, cells in (("othello", 64), ("hex11", 121)):
+        net = L.Net(cells, B)
+        net.set_params(torch.from_numpy(W.init_params(cells, 1)).cuda())
+        x = (torch.rand(B, net.in_pad, device="cuda", generator=g) < 0.3).to(torch.bfloat16)
+        x[:, 2 * cells + 1:] = 0
+        xb, yb = x.view(torch.int16), torch.rand(B, device="cuda", generator=g)
+        flops = 2.0 * B * (2 * net.in_pad * 512 + 3 * 512 * 512 + 512)
+        res = {"batch": B, "in_pad": net.in_pad, "gflop_per_step": round(flops / 1e9, 2)}
+        for path, name in ((1, "tcgen05"), (0, "mma_sync")):
+            net.set_tensor_path(path)
+            ms = time_steps(lambda: net.train_step(xb, yb, 1e-3), steps, warmup, flush_buf,
+                            torch.cuda.current_stream())
+            t = statistics.median(ms) / 1e3
+            tf = flops / t / 1e12
+            res[name] = {"median_ms": round(t * 1e3, 4), "steps_per_s": round(1 / t, 1), "tflops": round(tf, 1),
+                         "frac_of_bf16_peak": round(tf / float(peaks.get("bf16_tflops", 1800.0)), 4)}
+        res["device_error"] = L.ludax_device_error()
+        net.close()
+        out[game] = res
+    return out
+
+
 def bench_valuenet():
     """The learned part: 2M training positions per game, 100k held-out
     positions; value estimates/s of the truncated estimator (8 random plies,
@@ -633,6 +667,8 @@ def main():
             res = bench_value_estimator()
         elif args.only == "int_peak":
             res = bench_int_peak(L)
+        elif args.only == "train_step":
+            res = bench_train_step(L, peaks, flush_buf, max(args.steps, 5), args.warmup)
         else:
             res = bench_batch_sweep(L, W, flush_buf)
         if rank == 0:
@@ -749,6 +785,7 @@ def main():
             sm["hbm_frac"] = round(sm["gbs"] / float(peaks.get("hbm_gbs", 6400.0)), 4)
             extras["step_mode_" + gname] = sm
         extras["dense_layer"] = bench_dense(L, peaks, flush_buf)
+        extras["train_step"] = bench_train_step(L, peaks, flush_buf)
         extras["gavel_library"] = bench_gavel()
         if not args.no_valuenet:
             extras["value_net"] = bench_valuenet()
