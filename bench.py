@@ -326,9 +326,32 @@ def e2e_rollout(L, cfg, steps, warmup, rank=0):
         times.append((time.perf_counter() - t0) / steps)
     dt = statistics.median(times)
     steps_per_launch = int(slots[(steps - 1) % depth][5].numpy().astype(np.int64).sum())
+    # the host link alone: the same four copies per step (two up, two down), each direction timed
+    # by CUDA events on its own, median of 10 after 3 warm-ups
+    stream, _, h_planes, h_meta, h_out, h_plies = slots[0]
+    d_planes, d_meta = torch.empty_like(h_planes, device="cuda"), torch.empty_like(h_meta, device="cuda")
+    d_out, d_plies = torch.empty_like(h_out, device="cuda"), torch.empty_like(h_plies, device="cuda")
+
+    def copy_time(fn):
+        ts = []
+        for i in range(13):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record()
+                fn()
+                b.record()
+            b.synchronize()
+            if i >= 3:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    link = {"h2d_ms": copy_time(lambda: (d_planes.copy_(h_planes, non_blocking=True),
+                                         d_meta.copy_(h_meta, non_blocking=True))),
+            "d2h_ms": copy_time(lambda: (h_out.copy_(d_out, non_blocking=True),
+                                         h_plies.copy_(d_plies, non_blocking=True)))}
     for sl in slots:
         sl[1].close()
-    return steps_per_launch / dt, total, n * 1 + n * 2, dt, cells
+    return steps_per_launch / dt, total, n * 1 + n * 2, dt, cells, link, steps_per_launch
 
 
 def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
@@ -740,9 +763,17 @@ def main():
             "gpu_launches": args.steps * (2 if args.workload == "mixed" else 1)}
 
     if rank == 0 and cfg is not None and args.workload != "step_c4":
-        e2e_val, h2d, d2h, dt, _ = e2e_rollout(L, cfg, max(3, min(args.steps, 100)), 3, rank)
+        e2e_val, h2d, d2h, dt, _, link, spl = e2e_rollout(L, cfg, max(3, min(args.steps, 100)), 3, rank)
+        # with the copies of one step overlapping another's playouts, a step costs at least the
+        # slowest of: its uploads, its downloads, its playout launch
+        t_bound = max(link["h2d_ms"], link["d2h_ms"], roofline["median_launch_ms"]) / 1e3
         line["e2e"] = {"value": round(e2e_val * world, 1), "unit": "env steps/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4),
+                       "link": {"h2d_ms": round(link["h2d_ms"], 4), "d2h_ms": round(link["d2h_ms"], 4),
+                                "h2d_gbs": round(h2d / link["h2d_ms"] / 1e6, 2),
+                                "d2h_gbs": round(d2h / link["d2h_ms"] / 1e6, 2),
+                                "bound_env_steps_per_s": round(spl / t_bound, 1),
+                                "frac": round(e2e_val / (spl / t_bound), 4)},
                        "path": "ludax_rollout_host per step: pinned host start positions in the packed state view "
                                "(2 bits per cell + a meta word per env) -> device -> playouts -> pinned host "
                                "outcome/plies; six envs on six streams rotate so one step's copies overlap "
