@@ -135,8 +135,10 @@ def check_gradient(g, theta, X, y, K, cells, loss=None):
 
 
 # B = 128: two K blocks, so two splits of the weight gradients; B = 4736 =
-# 37 x 128: 74 K blocks over 18 (dW2) and 37 (dW1) splits, unequal in size.
-@pytest.mark.parametrize("cells,B", [(64, 512), (121, 256), (64, 128), (64, 4736)])
+# 37 x 128: 74 K blocks over 18 (dW2) and 37 (dW1) splits, unequal in size;
+# 42 cells: 85 inputs padded to 128 columns, so dW1 (N = 128, not a multiple
+# of the 256-column tile) stays on mma.sync while the rest runs on tcgen05.
+@pytest.mark.parametrize("cells,B", [(64, 512), (121, 256), (64, 128), (64, 4736), (42, 384)])
 @pytest.mark.parametrize("path", [1, 0])  # tcgen05 backward, mma.sync backward
 def test_gradient_matches_oracle(L, cells, B, path):
     K = W.net_in_pad(cells)
