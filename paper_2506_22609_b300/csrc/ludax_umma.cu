@@ -908,10 +908,11 @@ int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int
     const int sms = sm_count();
     if (!sms) return LUDAX_ERR_CUDA;
     const int tiles = (M / TM) * (N / TN), kblocks = K / TK;
-    long long splits = sms / tiles;
+    long long splits = sms / tiles;          // enough work units to fill the SMs (one when the tiles already do)
     if (splits > kblocks) splits = kblocks;  // every split gets at least one K block
     if (splits > part_floats / ((long long)M * N)) splits = part_floats / ((long long)M * N);
-    if (splits < 1) return LUDAX_ERR_SIZE;
+    if (splits < 1) splits = 1;
+    if ((long long)M * N > part_floats) return LUDAX_ERR_SIZE;  // not even one partial fits
     CUtensorMap ma, mb;
     // A [K][M] and B [K][N], both MN-major (64 x 64 boxes); nothing is stored through a tensor map
     if (!make_map(&ma, A, K, M, 64, lda) || !make_map(&mb, B, K, N, 64, ldb)) return LUDAX_ERR_CUDA;
