@@ -590,9 +590,10 @@ def bench_valuenet():
 
 
 def bench_int_peak(L, iters=1 << 16):
-    """What a stream of one integer op reaches (LOP3, IADD, SHF; 8 independent
-    chains per thread, every SM fully occupied), against the issue peak (4
-    warp instructions per clock per SM) and the ALU pipe's half of it: the
+    """What a stream of one integer op reaches (LOP3, IADD, SHF, IMAD,
+    IMAD.HI, and LOP3 + IMAD on alternate chains; 8 independent chains per
+    thread, every SM fully occupied), against the issue peak (4 warp
+    instructions per clock per SM) and the ALU pipe's half of it: the
     denominators of the playouts' roofline."""
     import torch
 
@@ -600,7 +601,7 @@ def bench_int_peak(L, iters=1 << 16):
     props = torch.cuda.get_device_properties(dev)
     out = {}
     with ClockSampler(dev) as clk:
-        for kind in ("lop3", "iadd", "shf"):
+        for kind in ("lop3", "iadd", "shf", "imad", "imad_hi", "lop3_imad"):
             ms = []
             for i in range(5):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -618,7 +619,7 @@ def bench_int_peak(L, iters=1 << 16):
     out["clocks"] = rec
     out["issue_peak_tops"] = round(issue, 3)
     out["alu_pipe_peak_tops"] = round(issue / 2, 3)
-    for kind in ("lop3", "iadd", "shf"):
+    for kind in ("lop3", "iadd", "shf", "imad", "imad_hi", "lop3_imad"):
         out[kind]["frac_of_issue_peak"] = round(out[kind]["tops"] / issue, 3)
     return out
 

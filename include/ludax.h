@@ -534,9 +534,11 @@ int ludax_selftest_wait(int64_t limit_cycles, void* stream);
 /* Integer-issue microbenchmark behind the playouts' roofline: one launch
  * over every SM at full occupancy in which each thread issues `iters` x 8
  * independent 32-bit ops of one kind -- 0 LOP3 (3-input logic), 1 IADD
- * (add.u32), 2 SHF (funnel shift) -- as inline PTX.  ops_out (host,
- * nullable) gets the number of thread-level ops; time the launch on
- * `stream` (asynchronous).  iters in 1 .. 2^30; LUDAX_ERR_ARG otherwise. */
+ * (add.u32), 2 SHF (funnel shift), 3 IMAD (mad.lo.u32), 4 IMAD.HI
+ * (mul.hi.u32), 5 LOP3 and IMAD on alternate chains -- as inline PTX.
+ * ops_out (host, nullable) gets the number of thread-level ops; time the
+ * launch on `stream` (asynchronous).  kind in 0 .. 5 and iters in
+ * 1 .. 2^30; LUDAX_ERR_ARG otherwise. */
 int ludax_int_peak(int32_t kind, int64_t iters, int64_t* ops_out, void* stream);
 
 #ifdef __cplusplus

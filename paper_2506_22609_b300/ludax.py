@@ -474,7 +474,7 @@ def ludax_selftest_wait(limit_cycles: int, stream=None):
     _check(lib().ludax_selftest_wait(limit_cycles, _stream(stream)), "ludax_selftest_wait")
 
 
-INT_PEAK_KINDS = {"lop3": 0, "iadd": 1, "shf": 2}
+INT_PEAK_KINDS = {"lop3": 0, "iadd": 1, "shf": 2, "imad": 3, "imad_hi": 4, "lop3_imad": 5}
 
 
 def ludax_int_peak(kind: str, iters: int, stream=None) -> int:

@@ -53,7 +53,7 @@ def test_dense_relu_rejects_unsupported_shapes(L):
     assert ei.value.status == -3
 
 
-@pytest.mark.parametrize("kind", ["lop3", "iadd", "shf"])
+@pytest.mark.parametrize("kind", ["lop3", "iadd", "shf", "imad", "imad_hi", "lop3_imad"])
 def test_int_peak_microbenchmark_runs(L, kind):
     """The integer-issue microbenchmark counts its ops exactly and finishes."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
