@@ -157,6 +157,27 @@ def test_random_step_reproduces_rollout(L, name, game, rows, cols):
     assert (np_(final_rew) == want).all()
 
 
+def test_step_mode_full_size_sampled(L):
+    """The step-per-launch benchmark configuration: 16,777,216 Connect Four
+    envs, reset, then five ludax_random_step launches over the whole batch;
+    sampled envs against the oracle's playout stopped after five plies, and
+    at any size: no game ends before ply 7, so every reward and flag is 0."""
+    n, seed, plies = 1 << 24, 1, 5
+    env = L.Env(G.C4, 6, 7, n)
+    for _ in range(plies):
+        rew, term = env.random_step(seed)
+    assert bool((rew == 0).all()) and bool((term == 0).all())
+    b, tm, ply, ps, oc = env.get_state()
+    idx = torch.from_numpy(W.sample_envs(n, 2000, 7)).cuda()
+    b, tm, ply, ps, oc = (np_(t[idx]) for t in (b, tm, ply, ps, oc))
+    assert (ply == plies).all() and (oc == -1).all()
+    for i, e in enumerate(np_(idx)):
+        s = G.reset(G.C4, 6, 7, 1)
+        G.rollout_from(s, seed, env_offset=int(e), stop_ply=np.array([plies], np.int16))
+        assert (s.board[0] == b[i]).all() and s.to_move[0] == tm[i] and s.ply[0] == ply[i], int(e)
+    env.close()
+
+
 def _canon_legal(mask_words, A, cells):
     bits = np.zeros((mask_words.shape[0], A), np.uint8)
     w = mask_words.view(np.uint64)
