@@ -95,6 +95,12 @@ __host__ __device__ inline int desc_bucket(int32_t d) {
     }
 }
 
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per (kernel, device); LUDAX_OK or LUDAX_ERR_CUDA.
+int ensure_smem_limit(const void* kernel, size_t bytes);
+// SMs of the current device (0 on error).
+int device_sms();
+
 // dense BF16 layer on tcgen05 tensor cores (ludax_umma.cu):
 // out = bf16(relu(A . B^T + bias)), A [M][K], B [N][K] row-major
 bool umma_dense_supported(int M, int N, int K);

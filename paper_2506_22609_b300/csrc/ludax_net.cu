@@ -193,12 +193,7 @@ template <bool AK, bool BK_, int EPI>
 int launch_gemm(const GemmArgs& a, int splits, cudaStream_t s) {
     if (a.M % BM || a.N % BN || a.K % (BKT * splits) || a.lda % 8 || a.ldb % 8) return LUDAX_ERR_SIZE;
     auto k = gemm_bf16_kernel<AK, BK_, EPI>;
-    static bool attr = false;  // per instantiation
-    if (!attr) {
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM) != cudaSuccess)
-            return LUDAX_ERR_CUDA;
-        attr = true;
-    }
+    if (ensure_smem_limit((const void*)k, GEMM_SMEM)) return LUDAX_ERR_CUDA;
     GemmArgs g = a;
     g.k_per_split = a.K / splits;
     dim3 grid(a.N / BN, a.M / BM, splits);

@@ -28,6 +28,8 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include "ludax_internal.cuh"
 
@@ -817,6 +819,29 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int box_rows
 
 namespace ludax {
 
+// A kernel's dynamic shared-memory limit is an attribute of the function on
+// the current device: set once per (kernel, device), under a lock.
+int ensure_smem_limit(const void* kernel, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LUDAX_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return LUDAX_OK;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    done.insert({kernel, dev});
+    return LUDAX_OK;
+}
+
+// SMs of the current device (0 on error)
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
 bool umma_dense_supported(int M, int N, int K) {
     return M > 0 && N > 0 && K > 0 && M % TM == 0 && N % TN == 0 && K % TK == 0 && N <= MAX_N;
 }
@@ -838,20 +863,8 @@ int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const flo
     if (!make_map(&ma, A, M, K, TM, lda) || !make_map(&mb, B, N, K, TN, ldb) ||
         !(store ? make_map(&mo, out, M, N, 32, ldo) : make_map(&mo, A, M, K, 32, lda)))
         return LUDAX_ERR_CUDA;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(umma_dense_relu_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)UMMA_SMEM) !=
-            cudaSuccess)
-            return LUDAX_ERR_CUDA;
-        attr = true;
-    }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return LUDAX_ERR_CUDA;
-    }
+    const int sms = device_sms();
+    if (!sms || ensure_smem_limit((const void*)umma_dense_relu_kernel, UMMA_SMEM)) return LUDAX_ERR_CUDA;
     const int ntiles = (M / TM) * (N / TN);
     const int grid = ntiles < sms ? ntiles : sms;
     umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias,
@@ -864,34 +877,18 @@ template <bool A_MN, bool B_MN, int EPI>
 static int launch_grad(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mo, int M, int N, int kblocks,
                        int splits, const void* mask, int ldm, float* part, int sms, cudaStream_t s) {
     auto k = umma_grad_kernel<A_MN, B_MN, EPI>;
-    static bool attr = false;  // per instantiation
-    if (!attr) {
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GradCfg<EPI>::smem) != cudaSuccess)
-            return LUDAX_ERR_CUDA;
-        attr = true;
-    }
+    if (ensure_smem_limit((const void*)k, GradCfg<EPI>::smem)) return LUDAX_ERR_CUDA;
     const int units = (M / TM) * (N / TN) * splits;
     k<<<units < sms ? units : sms, UMMA_THREADS, GradCfg<EPI>::smem, s>>>(
         ma, mb, mo, M, N, kblocks, splits, static_cast<const __nv_bfloat16*>(mask), ldm, part);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
-static int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return 0;
-    }
-    return sms;
-}
-
 int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, cudaStream_t s) {
     if (!umma_dense_supported(M, N, K) || !A || !B || !mask || !out || N % 8 || K % 8 || ((uintptr_t)A % 16) ||
         ((uintptr_t)B % 16) || ((uintptr_t)mask % 16) || ((uintptr_t)out % 16))
         return LUDAX_ERR_SIZE;
-    const int sms = sm_count();
+    const int sms = device_sms();
     if (!sms) return LUDAX_ERR_CUDA;
     CUtensorMap ma, mb, mo;
     // A [M][K] K-major; B [K][N] MN-major (64 x 64 boxes); out [M][N] in 32-row boxes
@@ -905,7 +902,7 @@ int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int
     if (!umma_dense_supported(M, N, K) || !A || !B || !part || !splits_out || lda < M || ldb < N || lda % 8 ||
         ldb % 8 || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)part % 16))
         return LUDAX_ERR_SIZE;
-    const int sms = sm_count();
+    const int sms = device_sms();
     if (!sms) return LUDAX_ERR_CUDA;
     const int tiles = (M / TM) * (N / TN), kblocks = K / TK;
     long long splits = sms / tiles;          // enough work units to fill the SMs (one when the tiles already do)
@@ -920,12 +917,7 @@ int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int
     return launch_grad<true, true, GRAD_PARTIAL>(ma, mb, ma, M, N, kblocks, (int)splits, nullptr, 0, part, sms, s);
 }
 
-int umma_mlp_scratch_rows() {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 0;
-    return sms * 2 * TM;
-}
+int umma_mlp_scratch_rows() { return device_sms() * 2 * TM; }
 
 int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
                   const float* b2, const void* w3, float* zpart, void* scratch, int scratch_rows, int M,
@@ -933,13 +925,8 @@ int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, cons
     if (M <= 0 || M % TM || K1 <= 0 || K1 % TK || K1 > ldx || K1 > ldw1 || ldx % 8 || ldw1 % 8 || !zpart ||
         !scratch || ((uintptr_t)X % 16) || ((uintptr_t)W1 % 16) || ((uintptr_t)W2 % 16) || ((uintptr_t)scratch % 16))
         return LUDAX_ERR_SIZE;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return LUDAX_ERR_CUDA;
-    }
+    const int sms = device_sms();
+    if (!sms) return LUDAX_ERR_CUDA;
     const int nblk = M / TM, grid = nblk < sms ? nblk : sms;
     if (scratch_rows < grid * 2 * TM) return LUDAX_ERR_SIZE;
     CUtensorMap mx, mw1, mhs, mhl, mw2;
@@ -947,13 +934,7 @@ int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, cons
         !make_map(&mhs, scratch, scratch_rows, MLP_N, 32, MLP_N) || !make_map(&mhl, scratch, scratch_rows, MLP_N, TM, MLP_N) ||
         !make_map(&mw2, W2, MLP_N, MLP_N, TN, MLP_N))
         return LUDAX_ERR_CUDA;
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(umma_mlp_head_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MLP_SMEM) !=
-            cudaSuccess)
-            return LUDAX_ERR_CUDA;
-        attr = true;
-    }
+    if (ensure_smem_limit((const void*)umma_mlp_head_kernel, MLP_SMEM)) return LUDAX_ERR_CUDA;
     umma_mlp_head_kernel<<<grid, MLP_THREADS, MLP_SMEM, s>>>(mx, mw1, mhs, mhl, mw2, M, K1, b1, b2,
                                                               static_cast<const __nv_bfloat16*>(w3), zpart);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
