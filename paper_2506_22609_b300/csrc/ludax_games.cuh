@@ -423,7 +423,12 @@ struct Hex {
         if (ta && tb) {
             outcome = side + 1;
         } else if (ta || tb) {
-            B128 c = flood(x, own & ~(ownA | ownB));
+            // the stones newly joined to the touched edge set: x's component
+            // among the mover's stones outside both sets, started from x and
+            // its neighbours there (nx is at hand), flooded only if there are any
+            const B128 stones = own & ~(ownA | ownB), first = nx & stones;
+            B128 c = x | first;
+            if (any(first)) c = flood(c, stones);
             if (ta) ownA = ownA | c;
             else ownB = ownB | c;
         }
