@@ -767,7 +767,7 @@ def main():
         e2e_val, h2d, d2h, dt, _, link, spl = e2e_rollout(L, cfg, max(3, min(args.steps, 100)), 3, rank)
         # with the copies of one step overlapping another's playouts, a step costs at least the
         # slowest of: its uploads, its downloads, its playout launch
-        t_bound = max(link["h2d_ms"], link["d2h_ms"], roofline["median_launch_ms"]) / 1e3
+        t_bound = max(link["h2d_ms"], link["d2h_ms"], med) / 1e3
         line["e2e"] = {"value": round(e2e_val * world, 1), "unit": "env steps/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4),
                        "link": {"h2d_ms": round(link["h2d_ms"], 4), "d2h_ms": round(link["d2h_ms"], 4),

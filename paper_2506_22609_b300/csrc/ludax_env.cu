@@ -461,10 +461,21 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
     if (active) init();
     for (;;) {
         if (active) {
+            if constexpr (HexN<G>::value != 0) {
+                // two plies per loop body: the six board words that trade roles
+                // every ply are renamed instead of moved (Hex 11: ~3% faster;
+                // other games measured slower or unchanged)
+#pragma unroll 2
+                for (int r = 0; r < R; ++r) {
+                    if (g.outcome != kOngoing || g.ply >= stop) break;
+                    random_ply_pre(g, key, rhi);
+                }
+            } else {
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) {
-                if (g.outcome != kOngoing || g.ply >= stop) break;
-                random_ply_pre(g, key, rhi);
+                for (int r = 0; r < R; ++r) {
+                    if (g.outcome != kOngoing || g.ply >= stop) break;
+                    random_ply_pre(g, key, rhi);
+                }
             }
             if (g.outcome != kOngoing || g.ply >= stop) {
                 if (a.outcome) a.outcome[env] = (int8_t)g.outcome;
