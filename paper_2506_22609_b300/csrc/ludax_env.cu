@@ -329,7 +329,9 @@ struct RolloutArgs {
 // One persistent kernel: each thread holds EPT envs in registers and advances
 // each by one ply per loop trip; a finished env is written out and replaced
 // by the next unclaimed env (claim_next).  Work index w < n maps to env w.
-template <class G, int EPT, bool TABLE>
+// BITS: the envs start from the packed view in a.bits (the host-buffer path);
+// a separate instantiation, so the other launches carry none of its code.
+template <class G, int EPT, bool TABLE, bool BITS = false>
 __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
     extern __shared__ B128 smem_table[];
     const B128* table = nullptr;
@@ -357,7 +359,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
     auto init = [&](int i) {
         const int64_t e = env[i];
         configure(g[i], a.d.desc);
-        if (a.bits) load_bits(g[i], a.d, a.bits, a.bits_meta, e, a.bits_w, a.bits_v);
+        if constexpr (BITS) load_bits(g[i], a.d, a.bits, a.bits_meta, e, a.bits_w, a.bits_v);
         else if (a.from_start) g[i].reset();
         else load_state(g[i], a.d, e);
         key[i] = env_key(a.seed_key, (uint64_t)(a.d.env_offset + e));
@@ -424,7 +426,7 @@ __device__ __forceinline__ void slot_load(const uint64_t* buf, int stride, int p
     stop = (int)(x >> 32);
 }
 
-template <class G, bool TABLE>
+template <class G, bool TABLE, bool BITS = false>
 __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int R) {
     extern __shared__ __align__(16) uint64_t smem64[];
     const int B = blockDim.x;
@@ -451,7 +453,7 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
     bool active = env < n;
     auto init = [&]() {
         configure(g, a.d.desc);
-        if (a.bits) load_bits(g, a.d, a.bits, a.bits_meta, env, a.bits_w, a.bits_v);
+        if constexpr (BITS) load_bits(g, a.d, a.bits, a.bits_meta, env, a.bits_w, a.bits_v);
         else if (a.from_start) g.reset();
         else load_state(g, a.d, env);
         key = env_key(a.seed_key, (uint64_t)(a.d.env_offset + env));
@@ -552,10 +554,10 @@ __global__ void __launch_bounds__(512) rollout_value_kernel(EnvDev d, uint64_t s
     value[e] = R > 0 ? acc / (float)R : 0.f;
 }
 
-template <class G>
-int launch_rollout(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& cfg) {
+template <class G, bool BITS>
+int launch_rollout_as(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& cfg) {
     const int block = cfg.block_threads;
-    const int ept = cfg.envs_per_thread;
+    const int ept = BITS ? 1 : cfg.envs_per_thread;  // the packed-view path has one env per thread
     int64_t need = (env->n + (int64_t)block * ept - 1) / ((int64_t)block * ept);
     int64_t grid = need;
     if (cfg.blocks_per_sm > 0) {
@@ -571,26 +573,31 @@ int launch_rollout(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg&
     if (cfg.compact_every > 0) {
         size_t cs = sizeof(uint64_t) * (G::kWords + 2) * block + 32 * sizeof(int) + smem;
         if (table) {
-            auto k = rollout_compact_kernel<G, true>;
+            auto k = rollout_compact_kernel<G, true, BITS>;
             if (cs > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs) != cudaSuccess)
                 return LUDAX_ERR_CUDA;
             k<<<(unsigned)grid, block, cs, env->stream>>>(a, cfg.compact_every);
         } else {
-            auto k = rollout_compact_kernel<G, false>;
+            auto k = rollout_compact_kernel<G, false, BITS>;
             if (cs > 48 * 1024 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs) != cudaSuccess)
                 return LUDAX_ERR_CUDA;
             k<<<(unsigned)grid, block, cs, env->stream>>>(a, cfg.compact_every);
         }
         return launch_status();
     }
-    if (ept == 2) {
+    if (!BITS && ept == 2) {
         if (table) rollout_kernel<G, 2, true><<<(unsigned)grid, block, smem, env->stream>>>(a);
         else rollout_kernel<G, 2, false><<<(unsigned)grid, block, 0, env->stream>>>(a);
     } else {
-        if (table) rollout_kernel<G, 1, true><<<(unsigned)grid, block, smem, env->stream>>>(a);
-        else rollout_kernel<G, 1, false><<<(unsigned)grid, block, 0, env->stream>>>(a);
+        if (table) rollout_kernel<G, 1, true, BITS><<<(unsigned)grid, block, smem, env->stream>>>(a);
+        else rollout_kernel<G, 1, false, BITS><<<(unsigned)grid, block, 0, env->stream>>>(a);
     }
     return launch_status();
+}
+
+template <class G>
+int launch_rollout(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& cfg) {
+    return a.bits ? launch_rollout_as<G, true>(env, a, cfg) : launch_rollout_as<G, false>(env, a, cfg);
 }
 
 ludax_launch_cfg default_cfg() { return ludax_launch_cfg{256, 0, 1, 0, 0}; }
