@@ -54,8 +54,8 @@ ALG_OPS_PER_STEP = {"ttt": 75, "c4": 112, "othello": 437, "hex": 180, "gomoku": 
 
 # DRAM bytes per launch of the benchmarked kernel, from the committed ncu
 # captures (profiles/); None once the kernel changes until it is captured again.
-NCU_TRAFFIC_BYTES = {"connect4_6x7_65536env_seed1": 17920,
-                     "connect4_6x7_16777216env_random_step_seed1": 335567104 + 426962432}
+NCU_TRAFFIC_BYTES = {"connect4_6x7_65536env_seed1": 13568,
+                     "connect4_6x7_16777216env_random_step_seed1": 335567360 + 426561280}
 
 
 def parse():
