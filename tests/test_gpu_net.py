@@ -276,18 +276,24 @@ def test_forward_large_batch_sampled(L, cells):
         assert np.isfinite(p).all() and (p > 0).all() and (p < 1).all()
 
 
-def test_truncated_value_large_batch_sampled(L):
+# 24,000 x 4 rows; and the value benchmark's own configurations: 100,000
+# positions with K = 8 (Othello, 800,000 rows in one launch of the fused MLP)
+# and K = 1 (Hex 11)
+@pytest.mark.parametrize("game,rows,cols,n,Kc", [(G.OTHELLO, 8, 8, 24000, 4), (G.OTHELLO, 8, 8, 100000, 8),
+                                                 (G.HEX, 11, 11, 100000, 1)], ids=["othello_24k_k4", "othello_100k_k8",
+                                                                                  "hex11_100k_k1"])
+def test_truncated_value_large_batch_sampled(L, game, rows, cols, n, Kc):
     """The truncated estimator with K * n rows spanning many blocks per CTA
-    (Othello: only the first 192 input columns are read): sampled positions
-    against the oracle, each replayed with its own env index."""
-    game, rows, cols, n, Kc, plies, seed = G.OTHELLO, 8, 8, 24000, 4, 8, 123
+    (only the input columns the first layer needs are read): sampled
+    positions against the oracle, each replayed with its own env index."""
+    plies, seed = 8, 123
     cells = rows * cols
     K = W.net_in_pad(cells)
     s = positions(game, rows, cols, n, 6)
     env = L.Env(game, rows, cols, n, env_offset=3)
     env.set_state(*(torch.from_numpy(x) for x in (s.board, s.to_move, s.ply, s.passes, s.outcome)))
     theta = W.init_params(cells, 12)
-    net = L.Net(cells, n * Kc)
+    net = L.Net(cells, (n * Kc + 127) // 128 * 128)  # row capacity: a multiple of 128
     net.set_params(torch.from_numpy(theta).cuda())
     val = torch.empty(n, dtype=torch.float32, device="cuda")
     L.ludax_truncated_value(env.handle, net.handle, seed, Kc, plies, val)
