@@ -127,6 +127,23 @@ def test_benchmark_configs_sampled(L, cfg):
         assert (out != 0).all()
 
 
+@pytest.mark.parametrize("cfg", [W.CONNECT5_9X12_64K, W.WOLF_SHEEP_64K, W.DRAUGHTS_64K, W.HASAMI_64K],
+                         ids=lambda c: c.name)
+def test_benchmark_extra_configs_sampled(L, cfg):
+    """The other playout workloads bench.py times, at their size and in their
+    launch shape: sampled envs against the oracle, each replayed with its own
+    env index (outcome and length, including games ended by the ply cap)."""
+    env = L.Env(cfg.game, cfg.rows, cfg.cols, cfg.num_envs, line=cfg.line, flags=cfg.flags)
+    out, plies = env.rollout(cfg.seed, cfg=L.make_cfg(*W.bench_cfg(cfg)))
+    out, plies = np_(out), np_(plies)
+    gid = line_gid(cfg.line, cfg.flags) if cfg.line else cfg.game
+    for e in W.sample_envs(cfg.num_envs, 400, 9):
+        o, p, _ = G.rollout_start(gid, cfg.rows, cfg.cols, 1, cfg.seed, env_offset=int(e))
+        assert o[0] == out[e] and p[0] == plies[e], e
+    assert plies.min() >= 1 and plies.max() <= G.ply_cap(gid, cfg.rows, cfg.cols)
+    env.close()
+
+
 # ------------------------------------------------------ step-per-launch --
 @pytest.mark.parametrize("name,game,rows,cols", GAMES, ids=GAME_IDS)
 def test_random_step_reproduces_rollout(L, name, game, rows, cols):
