@@ -46,3 +46,36 @@ def test_compiled_library_mixed_batch_matches_oracle(cuda_device):
     finally:
         L.ludax_mixed_plan_destroy(plan)
     assert (out.cpu().numpy() == o).all() and (plies.cpu().numpy() == p).all()
+
+
+def test_gavel_library_launch_sampled(cuda_device):
+    """The GAVEL-like evaluation in the configuration bench.py times: the 13
+    library games, each with 100 matches between equal 100-iteration agents,
+    50 with the 100-iteration agent moving first against a 50-iteration one
+    and 50 the other way round, all 2,600 in one ludax_mcts_play_mixed
+    launch; one match per game (the pairings taken in turn) against the
+    oracle's match with the same global index."""
+    from paper_2506_22609_b300 import ludax as L
+
+    desc, iters, spans = [], [], []
+    for name in sorted(LIB):
+        spec = dsl.compile_game(LIB[name])
+        for n, i1, i2 in ((100, 100, 100), (50, 100, 50), (50, 50, 100)):
+            spans.append((name, spec, len(desc), n, i1, i2))
+            desc += [spec.desc] * n
+            iters += [(i1, i2)] * n
+    n, seed = len(desc), 0
+    assert n == 2600
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies, agency, cov = (torch.empty(n, dtype=torch.int16, device="cuda") for _ in range(3))
+    L.ludax_mcts_play_mixed(np.array(desc, np.int32), np.array(iters, np.int32), 0, seed, 2 ** 0.5, out, plies,
+                            agency, cov)
+    torch.cuda.synchronize()
+    got = [t.cpu().numpy() for t in (out, plies, agency, cov)]
+    rng = np.random.default_rng(17)
+    for g in range(len(LIB)):
+        name, spec, first, k, i1, i2 = spans[3 * g + g % 3]
+        e = first + int(rng.integers(0, k))
+        want = G.mcts_play(oracle_gid(spec), spec.rows, spec.cols, 1, seed, i1, i2, env_offset=e)
+        for g_arr, w_arr in zip(got, want):
+            assert g_arr[e] == w_arr[0], (name, e)
