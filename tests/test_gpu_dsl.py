@@ -79,3 +79,29 @@ def test_gavel_library_launch_sampled(cuda_device):
         want = G.mcts_play(oracle_gid(spec), spec.rows, spec.cols, 1, seed, i1, i2, env_offset=e)
         for g_arr, w_arr in zip(got, want):
             assert g_arr[e] == w_arr[0], (name, e)
+
+
+def test_compiled_library_full_batch_sampled(cuda_device):
+    """The compiled-library mix in the configuration bench.py times: 2^20 envs,
+    env e playing library game e mod 13, through the autotuned, graph-captured
+    mixed plan; sampled envs against the oracle, each with its own index."""
+    from paper_2506_22609_b300 import ludax as L
+    from paper_2506_22609_b300 import workloads as W
+
+    descs = [dsl.descriptor(t) for t in LIB.values()]
+    n, seed = 1 << 20, 3
+    d_host = np.array(descs, np.int32)[np.arange(n) % len(descs)]
+    d = torch.from_numpy(d_host).cuda()
+    cfg, _, _ = L.ludax_autotune(d, seed, reps=1)
+    plan = L.ludax_mixed_plan_create(d, 0, cfg)
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies = torch.empty(n, dtype=torch.int16, device="cuda")
+    try:
+        L.ludax_mixed_plan_launch(plan, seed, out, plies)
+        torch.cuda.synchronize()
+    finally:
+        L.ludax_mixed_plan_destroy(plan)
+    out, plies = out.cpu().numpy(), plies.cpu().numpy()
+    for e in W.sample_envs(n, 650, 23):
+        o, p = G.rollout_mixed(d_host[e:e + 1], seed, env_offset=int(e))
+        assert o[0] == out[e] and p[0] == plies[e], (int(e), int(d_host[e]))
