@@ -25,8 +25,9 @@ def bf16(x):
     return torch.from_numpy(np.asarray(x, np.float32)).to(torch.bfloat16)
 
 
+# the last shape is the one bench.py times (every element checked)
 @pytest.mark.parametrize("Mr,N,K", [(128, 256, 64), (256, 512, 256), (384, 512, 512), (2048, 512, 128),
-                                    (16384, 512, 512)])
+                                    (16384, 512, 512), (65536, 512, 512)])
 def test_dense_relu_matches_fp64(L, Mr, N, K):
     rng = np.random.default_rng(Mr + N + K)
     a = bf16(rng.normal(0, 1, (Mr, K)))
