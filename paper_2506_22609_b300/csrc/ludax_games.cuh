@@ -947,11 +947,24 @@ __device__ __forceinline__ uint32_t legal_count_of(const G& g, const typename G:
     else return popc(m);
 }
 
+// Games whose legal mask is ordinal (kOrdinal: bits 0 .. count() - 1, one
+// per legal action in action order): the k-th legal action is k itself, so
+// a random ply needs only the count, not the mask.
+template <class G, class = void>
+struct IsOrdinal : std::false_type {};
+template <class G>
+struct IsOrdinal<G, std::enable_if_t<G::kOrdinal>> : std::true_type {};
+
 // ---------------------------------------------------------- one random ply --
 // Uniform-random policy: n legal cells, k-th in ascending cell id with
 // k = umulhi(top32(sm(key ^ ply)), n); a forced pass draws nothing.
 template <class G>
 __device__ __forceinline__ void random_ply(G& g, uint64_t key) {
+    if constexpr (IsOrdinal<G>::value) {  // no pass in these games; called only while the game is on
+        g.place((int)draw_index(key, (uint32_t)g.ply, (uint32_t)g.count()));
+        if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
+        return;
+    }
     typename G::Mask m = g.legal();
     if (G::kHasPass && !any(m)) {
         g.pass();
@@ -972,7 +985,10 @@ template <class G>
 struct HasWarpPlace<G, std::void_t<decltype(std::declval<G&>().place_warp(0, 0))>> : std::true_type {};
 template <class G>
 __device__ __forceinline__ void random_ply_warp(G& g, uint64_t key, int lane) {
-    if constexpr (HasWarpPlace<G>::value) {
+    if constexpr (HasWarpPlace<G>::value && IsOrdinal<G>::value) {
+        g.place_warp((int)draw_index(key, (uint32_t)g.ply, (uint32_t)g.count()), lane);
+        if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
+    } else if constexpr (HasWarpPlace<G>::value) {
         typename G::Mask m = g.legal();
         if (G::kHasPass && !any(m)) {
             g.pass();
@@ -995,11 +1011,15 @@ __device__ __forceinline__ uint32_t draw_hi(uint64_t key, uint32_t ply) {
 template <class G>
 __device__ __forceinline__ void random_ply_pre(G& g, uint64_t key, uint32_t& rhi) {
     const uint32_t rnext = draw_hi(key, (uint32_t)g.ply + 1u);
-    typename G::Mask m = g.legal();
-    if (G::kHasPass && !any(m)) {
-        g.pass();
+    if constexpr (IsOrdinal<G>::value) {
+        g.place((int)__umulhi(rhi, (uint32_t)g.count()));
     } else {
-        g.place(select_bit(m, __umulhi(rhi, legal_count_of(g, m))));
+        typename G::Mask m = g.legal();
+        if (G::kHasPass && !any(m)) {
+            g.pass();
+        } else {
+            g.place(select_bit(m, __umulhi(rhi, legal_count_of(g, m))));
+        }
     }
     if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
     rhi = rnext;

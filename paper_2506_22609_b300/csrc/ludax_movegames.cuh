@@ -56,6 +56,7 @@ __device__ __forceinline__ uint64_t diag_step(uint64_t b, int d) {
 struct WolfSheep {
     static constexpr int kGame = 8, kRows = 8, kCols = 8, kCells = 64, kCap = 200, kPlanes = 2, kActions = 4096;
     static constexpr bool kHasPass = false;
+    static constexpr bool kOrdinal = true;  // legal() holds the ordinals 0 .. count() - 1
     using Mask = uint32_t;  // ordinals: at most 8 legal actions
     uint64_t own, opp;      // pieces of the side to move / of the other side
     int side, ply, passes, outcome;
@@ -178,6 +179,7 @@ struct IsMove<WolfSheep> {
 struct Draughts {
     static constexpr int kGame = 9, kRows = 8, kCols = 8, kCells = 64, kCap = 200, kPlanes = 4, kActions = 4096;
     static constexpr bool kHasPass = false;
+    static constexpr bool kOrdinal = true;  // legal() holds the ordinals 0 .. count() - 1
     using Mask = uint64_t;  // ordinals: at most 48 legal actions (12 pieces x 4 directions)
     uint64_t men_own, kings_own, men_opp, kings_opp;  // relative to the side to move
     int side, ply, passes, outcome, pending;           // pending: cell of the piece that must hop again, -1 if none
@@ -481,6 +483,7 @@ struct HasamiShogi {
     static constexpr int kGame = 10, kRows = 9, kCols = 9, kCells = 81, kCap = 200, kPlanes = 4, kActions = 6561;
     static constexpr int kStride = 10;
     static constexpr bool kHasPass = false;
+    static constexpr bool kOrdinal = true;  // legal() holds the ordinals 0 .. count() - 1
     using Mask = BitsW<5>;  // ordinals: at most 18 pieces x 16 destinations = 288 legal actions
     B128 own, opp;          // relative to the side to move
     B128 occT;              // occupied cells transposed (bit 10 * column + row): columns as 10-bit windows
