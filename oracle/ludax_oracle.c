@@ -35,7 +35,7 @@
  * board draws) covers Tic-Tac-Toe, Connect Four and their variants on any
  * board of up to 128 padded cells.
  *
- * Readings where the paper is silent (they are listed in the design doc):
+ * Readings where the paper is silent:
  *   Hex neighbours of (r,c): (r-1,c) (r+1,c) (r,c-1) (r,c+1) (r-1,c+1) (r+1,c-1);
  *   Reversi: P1 = black moves first; white on D4,E5 = cells 27,36, black on
  *   D5,E4 = cells 35,28 (algebraic rows counted from the top); a pass is the
@@ -921,7 +921,7 @@ void oracle_ttt_enumerate(uint64_t* counts /* [10*3] */) {
  * iterations per move, each = traversal, expansion, random rollout).
  *
  * The paper leaves the details open; this is the definition both sides
- * implement (the readings are listed in the design doc):
+ * implement:
  *   - a node holds N (visits) and W (reward in half points, for the player
  *     who made the move into the node: win 2, draw or capped 1, loss 0);
  *   - iteration i of a search with key K: key_i = sm(K ^ i); from the root,
