@@ -23,6 +23,24 @@ def test_splitmix64_published_sequence():
         assert G.sm(state) == int(hexval, 16)
 
 
+def test_draw_key_derivation_known_answers():
+    # the policy's draw keyed on (seed, global env, ply): key = sm(sm(seed) ^ env),
+    # r = sm(key ^ ply), k = multiply-shift of r's top 32 bits.  Known answers
+    # come from tests/golden/make_splitmix64_keys.py (published splitmix64,
+    # no oracle code); the first three are also the survey's key(0,0),
+    # r(0,0,0) and r(0,0,1).  Slips such as sm(seed ^ env), sm(seed) ^ env or
+    # r = sm(key + ply) fail here.
+    rows = golden("splitmix64_keys.txt")
+    assert len(rows) >= 10
+    for seed, env, ply, n, key_hex, r_hex, k in rows:
+        seed, env, ply, n = int(seed), int(env), int(ply), int(n)
+        assert G.sm(G.sm(seed) ^ env) == int(key_hex, 16)
+        r = G.draw(seed, env, ply)
+        assert r == int(r_hex, 16), (seed, env, ply)
+        assert G.pick(r, n) == int(k)
+    assert G.draw(0, 0, 0) == 0x238275BC38FCBE91 and G.draw(0, 0, 1) == 0x2F32A78496C67C60
+
+
 def test_pick_is_uniform_multiply_shift():
     # k = floor(u * n / 2^32) for the top 32 bits u of the draw: check the
     # extreme draws and that every index in [0, n) is reachable and balanced.
