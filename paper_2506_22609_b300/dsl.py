@@ -20,12 +20,16 @@ Pipeline:
    flattened and their operands sorted, a bare function used as a
    predicate rewritten to ``(>= f 1)`` (App. B, predicate_function),
    ``(opponent win)`` rewritten to ``(mover lose)`` and vice versa.
-   Productions of the grammar that no kernel family implements (move,
-   hop, slide, step, pattern, promote, extra_turn, regions, ...) are
-   recognised and rejected with the path of the offending node.
+   The move mechanics (``move`` with ``hop`` / ``slide`` / ``step``,
+   priorities, ``promote``, ``extra_turn``) are elaborated like the
+   placement rules.  Productions of the grammar that no kernel family
+   implements (``pattern``, ``region`` / ``regions``, ``prev_move``,
+   ``hopped``, ``captured``, ``promoted``, the edge and corner masks, ...)
+   are recognised and rejected with the path of the offending node.
 3. ``lower`` -- matches the normalised game against the kernel families
    (the m,n,k line family with exact / gravity / misere end rules, Reversi,
-   Hex, Yavalath, Pente) and returns a ``GameSpec``.  Like the paper's
+   Hex, Yavalath, Pente, and the move games Wolf and Sheep, English
+   Draughts and Dai Hasami Shogi) and returns a ``GameSpec``.  Like the paper's
    parse-time precomputation (Sec. 4), everything that depends only on the
    description (board size, line length, rule variant) is fixed here and
    passed to the kernels as constants.  With ``specialize=True`` a line game

@@ -255,26 +255,6 @@ def ludax_set_state_bits(h, planes, meta):
     _check(lib().ludax_set_state_bits(h, _ptr(planes), _ptr(meta)), "ludax_set_state_bits")
 
 
-def pack_state_bits(board, to_move, ply, passes, outcome, planes_count):
-    """The packed state (numpy, host) of a canonical state view: planes
-    uint64 [planes_count * W][n] and meta uint32 [n], as ludax_get_state_bits
-    writes them."""
-    import numpy as np
-
-    board = np.asarray(board)
-    n, cells = board.shape
-    W = (cells + 63) // 64
-    planes = np.zeros((planes_count * W, n), np.uint64)
-    for v in range(1, planes_count + 1):
-        for c in range(cells):
-            hit = (board[:, c] == v).astype(np.uint64)
-            planes[(v - 1) * W + c // 64] |= hit << np.uint64(c % 64)
-    meta = (np.asarray(ply).astype(np.uint32) & 0xFFFF) | ((np.asarray(to_move).astype(np.uint32) - 1) & 1) << 16 | \
-        (np.asarray(passes).astype(np.uint8).astype(np.uint32) << 17) | \
-        (((np.asarray(outcome).astype(np.int32) + 1) & 7).astype(np.uint32) << 25)
-    return planes, meta.astype(np.uint32)
-
-
 def ludax_rollout_host(h, planes_host, meta_host, seed, outcome_host, plies_host, cfg=None):
     """Host tensors (pinned for asynchronous copies): planes int64
     [words_per_env][n], meta int32 [n] in; outcome int8 [n], plies int16 [n]

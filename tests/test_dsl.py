@@ -219,7 +219,7 @@ def test_move_game_equivalent_forms():
 
 
 @pytest.mark.parametrize("name,old,new,path,words", [
-    ("english_draughts", '(promote "man" "king" (edge forward))', '(promote "man" "king" (edge backward))',
+    ("english_draughts", '(promote "pawn" "king" (edge forward))', '(promote "pawn" "king" (edge backward))',
      "rules/play/effects", "promote"),
     ("english_draughts", "priority: 1", "priority: 0", "rules/play", "priority"),
     ("english_draughts", "(set_forward (P1 up) (P2 down))", "(set_forward (P1 down) (P2 up))", "players",
@@ -242,6 +242,6 @@ def test_move_mechanics_parse_into_the_normal_form():
     g = dsl.elaborate(dsl.read(LIB["english_draughts"]))
     kind, order, mech, force_pass = g["play"][0]
     assert mech[0] == "move" and len(mech[1]) == 4 and not force_pass
-    assert ("hop", "man", ("forward_left", "forward_right"), None, "opponent", True, 0) in mech[1]
-    assert mech[2][0] == ("promote", "man", "king", ("edge", "forward"), "mover")
+    assert ("hop", "pawn", ("forward_left", "forward_right"), None, "opponent", True, 0) in mech[1]
+    assert mech[2][0] == ("promote", "pawn", "king", ("edge", "forward"), "mover")
     assert g["forward"] == {"P1": "up", "P2": "down"}

@@ -12,6 +12,25 @@ import torch
 
 from oracle import games as G
 
+
+def pack_state_bits(board, to_move, ply, passes, outcome, planes_count):
+    """Test-side encoder of the packed state (numpy, host) of a canonical
+    state view: planes uint64 [planes_count * W][n] and meta uint32 [n], as
+    ludax_get_state_bits writes them."""
+    board = np.asarray(board)
+    n, cells = board.shape
+    W = (cells + 63) // 64
+    planes = np.zeros((planes_count * W, n), np.uint64)
+    for v in range(1, planes_count + 1):
+        for c in range(cells):
+            hit = (board[:, c] == v).astype(np.uint64)
+            planes[(v - 1) * W + c // 64] |= hit << np.uint64(c % 64)
+    meta = (np.asarray(ply).astype(np.uint32) & 0xFFFF) | ((np.asarray(to_move).astype(np.uint32) - 1) & 1) << 16 | \
+        (np.asarray(passes).astype(np.uint8).astype(np.uint32) << 17) | \
+        (((np.asarray(outcome).astype(np.int32) + 1) & 7).astype(np.uint32) << 25)
+    return planes, meta.astype(np.uint32)
+
+
 pytestmark = pytest.mark.gpu
 
 CASES = [("ttt", G.TTT, 3, 3), ("c4", G.C4, 6, 7), ("othello", G.OTHELLO, 8, 8), ("hex5", G.HEX, 5, 5),
@@ -46,7 +65,7 @@ def test_packed_view_round_trips(L, name, game, rows, cols):
     s = positions(game, rows, cols, n, 17)
     view = (s.board, s.to_move, s.ply, s.passes, s.outcome)
     planes_count = 4 if game == G.DRAUGHTS else 2
-    want_p, want_m = L.pack_state_bits(*view, planes_count)
+    want_p, want_m = pack_state_bits(*view, planes_count)
 
     a = L.Env(game, rows, cols, n, env_offset=5)
     a.set_state(*(torch.from_numpy(x) for x in view))
@@ -76,7 +95,7 @@ def test_packed_view_round_trips(L, name, game, rows, cols):
 def test_packed_view_ignores_bits_past_the_board(L):
     n = 64
     s = positions(G.C4, 6, 7, n, 3)
-    p, m = L.pack_state_bits(s.board, s.to_move, s.ply, s.passes, s.outcome, 2)
+    p, m = pack_state_bits(s.board, s.to_move, s.ply, s.passes, s.outcome, 2)
     junk = p.copy()
     junk |= np.uint64(0xFFFFFC0000000000)  # bits 42..63: no such cells
     env = L.Env(G.C4, 6, 7, n)
@@ -93,7 +112,7 @@ def test_rollout_host_matches_device_path(L, name, game, rows, cols):
     n = 1000
     s = positions(game, rows, cols, n, 23)
     planes_count = 4 if game == G.DRAUGHTS else 2
-    p, m = L.pack_state_bits(s.board, s.to_move, s.ply, s.passes, s.outcome, planes_count)
+    p, m = pack_state_bits(s.board, s.to_move, s.ply, s.passes, s.outcome, planes_count)
     hp = torch.from_numpy(p.view(np.int64)).pin_memory()
     hm = torch.from_numpy(m.view(np.int32)).pin_memory()
     ho = torch.empty(n, dtype=torch.int8).pin_memory()
@@ -132,7 +151,7 @@ def test_packed_view_line_games(L, rows, cols, line, flags):
     gid = 7 | (line << 8) | (flags << 12)
     s = positions(gid, rows, cols, n, 29)
     view = (s.board, s.to_move, s.ply, s.passes, s.outcome)
-    want_p, want_m = L.pack_state_bits(*view, 2)
+    want_p, want_m = pack_state_bits(*view, 2)
     a = L.Env("line", rows, cols, n, env_offset=2, line=line, flags=flags)
     a.set_state(*(torch.from_numpy(x) for x in view))
     p, m = a.get_state_bits()
