@@ -332,25 +332,29 @@ int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_o
                         int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg, void* stream);
 
 /* Allocation-free variant of ludax_rollout_mixed, for callers that cannot
- * allocate device memory: code running while a CUDA graph is being captured,
- * where cudaMalloc is not permitted, or serving loops and embedders where
- * cudaMalloc/cudaFree would synchronise the device, stall other streams or
- * break a fixed memory budget.  (The paper has no counterpart: this is a
- * deployment entry point of this library.)
+ * allocate device memory: plugins running inside a host framework whose
+ * memory pool already owns the device's memory (a cudaMalloc of ours could
+ * fail or fragment that pool), and serving loops where cudaFree would
+ * synchronise the whole device and stall every other stream.  (The paper has
+ * no counterpart: this is a deployment entry point of this library.)
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  *     Its scratch -- the game-grouped work queue and the claim cursors -- is a
  *     static device array of 4 MiB plus 1 KiB, held by every GPU that
  *     loads this library until the process exits.
  *   - num_envs at most 1,048,576 (2^20): larger batches return LUDAX_ERR_SIZE
  *     before anything is launched.
- *   - The first call on a device looks up the array's device address (which
- *     may load the library's device code); make that first call before any
- *     stream capture on the device.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (which may load the library's device code) and
+ *     keeps it for the process; make that first call before any stream
+ *     capture on the device.  The kept address is not refreshed, so do not
+ *     use this entry point on a device after cudaDeviceReset.
  *   - Every call shares the one array: the call resets the counters it needs
  *     and overwrites the queue, so calls whose work overlaps on the GPU (other
  *     streams or threads) race and must be serialised by the caller.
- *   - Blocks until the descriptors are validated (one small device-to-host
- *     read); the playout itself stays asynchronous on `stream`.
+ *   - Blocks until the descriptors are validated: it synchronises `stream`
+ *     after a small device-to-host read of the bucket counts (and one more
+ *     read of the bad descriptor when there is one); the playout itself
+ *     stays asynchronous on `stream`.
  * Arguments, results and errors as ludax_rollout_mixed; bad_index (nullable)
  * receives the index of the first invalid descriptor, else -1.            */
 int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,

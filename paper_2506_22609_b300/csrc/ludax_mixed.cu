@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -531,11 +533,12 @@ int ludax_autotune(const int32_t* desc_dev, int64_t num_envs, uint64_t seed, int
 // ===================================================== allocation-free path ==
 // ludax_rollout_mixed_noalloc: the same mixed-batch playout as
 // ludax_rollout_mixed, for callers that must not allocate device memory --
-// for example code that runs while another thread captures work into a CUDA
-// graph, or a serving loop where cudaMalloc/cudaFree would synchronise the
-// device and stall other streams.  Its scratch (the game-grouped work queue
-// and the claim cursors) lives in the static device array below, which every
-// GPU that loads this library keeps until the process exits.
+// a plugin running inside a host framework that owns the device's memory
+// budget (its pool has reserved the memory, so a cudaMalloc of ours could
+// fail or fragment it), or a serving loop where cudaFree would synchronise
+// the device and stall every other stream.  Its scratch (the game-grouped
+// work queue and the claim cursors) lives in the static device array below,
+// which every GPU that loads this library keeps until the process exits.
 namespace {
 
 constexpr long long kNoAllocMaxEnvs = 1ll << 20;  // 4 MiB of queue entries
@@ -546,7 +549,26 @@ constexpr int kCtrCount = 32, kCtrPos = 64, kCtrBad = 96;
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocMaxEnvs + 2 * kNoAllocCounterWords];
 
 constexpr int kMaxDevices = 64;
-void* g_noalloc_ptr[kMaxDevices] = {nullptr};
+// the array's device address per device, looked up once under the lock
+std::atomic<void*> g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+int noalloc_scratch_address(int dev, void** out) {
+    void* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return LUDAX_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return LUDAX_OK;
+}
 
 __device__ __forceinline__ int bucket_of_desc_dev(int32_t d) { return desc_bucket(d); }
 
@@ -613,12 +635,9 @@ extern "C" int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LUDAX_ERR_CUDA;
     if ((st = num_sms_current(&sms)) != LUDAX_OK) return st;
     // once per device, with that device current: the scratch array's device address
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LUDAX_ERR_CUDA;
-        g_noalloc_ptr[dev] = p;
-    }
-    uint32_t* base = static_cast<uint32_t*>(g_noalloc_ptr[dev]);
+    void* scratch = nullptr;
+    if ((st = noalloc_scratch_address(dev, &scratch)) != LUDAX_OK) return st;
+    uint32_t* base = static_cast<uint32_t*>(scratch);
     int32_t* queue = reinterpret_cast<int32_t*>(base);
     unsigned long long* ctr = reinterpret_cast<unsigned long long*>(base + kNoAllocMaxEnvs);
     cudaStream_t s = (cudaStream_t)stream;
@@ -634,7 +653,9 @@ extern "C" int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_
         long long e = (long long)h[kCtrBad];
         int32_t d = 0;
         if (bad_index) *bad_index = e;
-        if (cudaMemcpy(&d, desc_dev + e, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess) return LUDAX_ERR_CUDA;
+        if (cudaMemcpyAsync(&d, desc_dev + e, sizeof(d), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return LUDAX_ERR_CUDA;
         return bucket_of_desc(d) == -2 ? LUDAX_ERR_SIZE : LUDAX_ERR_GAME;
     }
     if (bad_index) *bad_index = -1;

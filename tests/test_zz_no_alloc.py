@@ -1,12 +1,14 @@
 """The allocation-free mixed-batch playout (ludax_rollout_mixed_noalloc).
 
-It exists for callers that cannot allocate device memory -- for instance code
-running while a CUDA graph is captured, or a serving loop that must not let
-cudaMalloc/cudaFree synchronise the device.  Its scratch is a static device
-array shared by every call, so this test calls it twice in a row (the second
-call must not see the first call's queue or counters) and checks each result
-against the allocating entry point ludax_rollout_mixed, exactly: outcomes and
-game lengths are integers.  This file is collected last on purpose.
+It exists for callers that cannot allocate device memory -- a plugin inside a
+host framework whose memory pool owns the device's memory, or a serving loop
+that must not let cudaFree synchronise the device.  Its scratch is a static
+device array shared by every call, so this test calls it twice in a row (the
+second call must not see the first call's queue or counters) and checks each
+result against the allocating entry point ludax_rollout_mixed, exactly:
+outcomes and game lengths are integers.  It also checks that the device's
+free memory does not move across calls once the kernels are loaded.  This
+file is collected last on purpose.
 """
 import pytest
 import torch
@@ -76,3 +78,20 @@ def test_noalloc_rejects_oversized_and_bad_batches(L):
     good = torch.from_numpy(W.mixed_descriptors(640, "interleave")).cuda()
     (ro, rp), (oo, op) = run_both(L, good, 0, 5)
     assert torch.equal(oo, ro) and torch.equal(op, rp)
+
+
+def test_noalloc_leaves_device_memory_unchanged(L):
+    # after one warm-up call (which loads the kernels it launches), further
+    # calls must not change the device's free memory: no allocation, no free
+    n = 1 << 20
+    d = torch.from_numpy(W.mixed_descriptors(n, "block")).cuda()
+    o = torch.empty(n, dtype=torch.int8, device="cuda")
+    p = torch.empty(n, dtype=torch.int16, device="cuda")
+    cfg = L.make_cfg(*W.mixed_bench_cfg())
+    L.ludax_rollout_mixed_noalloc(d, 0, 7, o, p, cfg)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for seed in (8, 9, 10):
+        L.ludax_rollout_mixed_noalloc(d, 0, seed, o, p, cfg)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
