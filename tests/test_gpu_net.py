@@ -92,10 +92,14 @@ def test_forward_matches_oracle(L, cells, B):
     assert np.allclose(net.get_params().cpu().numpy(), theta)
 
 
-def grad_bf16(theta, X, y, K):
+def grad_bf16(theta, X, y, K, with_bounds=False):
     """fp64 gradient with the kernels' rounding points: BF16 weights, BF16
     hidden activations, and the hidden-layer gradients dZ2 and dZ1 rounded to
-    BF16 before the contractions that read them (db2 sums dZ2 unrounded)."""
+    BF16 before the contractions that read them (db2 sums dZ2 unrounded).
+    With with_bounds, also each parameter block's element-wise error scales
+    (S, m): every gradient element is a sum over the batch of products a_b c_b
+    of a row factor and a column factor; S = sum_b |a_b| |c_b| and m =
+    max_b |a_b| * max_b |c_b| (a bound on the largest single term)."""
     P = M.unflatten(rounded_theta(theta, K), K)
     B = X.shape[0]
     h1 = M.bf16_round(np.maximum(X @ P["W1"].T + P["b1"], 0))
@@ -107,7 +111,20 @@ def grad_bf16(theta, X, y, K):
     dz1 = M.bf16_round((dz2b @ P["W2"]) * (h1 > 0))
     g = {"W1": dz1.T @ X, "b1": dz1.sum(0), "W2": dz2b.T @ h1, "b2": dz2.sum(0), "w3": h2.T @ g3,
          "b3": np.array([g3.sum()])}
-    return M.flatten(g, K)
+    if not with_bounds:
+        return M.flatten(g, K)
+    one = np.ones((B, 1))
+    factors = {"W1": (dz1, X), "b1": (dz1, one), "W2": (dz2b, h1), "b2": (dz2, one), "w3": (g3[:, None], h2),
+               "b3": (g3[:, None], one)}
+    bounds = {}
+    for name, (a, c) in factors.items():
+        a, c = np.abs(a), np.abs(c)
+        S = a.T @ c
+        m = np.outer(a.max(0), c.max(0))
+        if name == "w3":  # w3's element j is sum_b g3_b h2[b, j]: a column vector, like g["w3"]
+            S, m = S.ravel(), m.ravel()
+        bounds[name] = (S.reshape(g[name].shape), m.reshape(g[name].shape))
+    return M.flatten(g, K), bounds
 
 
 def blocks_close(g, want, K, rel_tol, cos_tol):
@@ -119,16 +136,48 @@ def blocks_close(g, want, K, rel_tol, cos_tol):
         assert rel < rel_tol and cos > cos_tol, (name, rel, cos)
 
 
+U_BF16, U_FP32 = 2.0 ** -8, 2.0 ** -24
+
+
+def elements_close(g, want, bounds, K, B):
+    """Every element of every block: |g - ref| <= 2^-8 |ref| + 8 sqrt(B) 2^-24 S + 2^-5 m.
+
+    The three terms: (1) one BF16 rounding of the result's dominant factor,
+    relative to the element; (2) FP32 accumulation of the B products in any
+    order and split, at the probabilistic rate sqrt(B) u (Higham and Mary,
+    2019) with a factor 8 of margin, relative to the sum of the products'
+    magnitudes S; (3) a BF16 intermediate (hidden activation, dZ2, dZ1) that
+    the kernel rounds to the neighbouring BF16 value because its FP32 input
+    sat next to a rounding boundary: each such factor moves its term by at
+    most 2^-8 of it (2^-7 for the two factors of a term), and up to four such
+    terms per element are allowed, each bounded by m.  A wrong sign costs
+    2 |ref| and a dropped row one whole term, far above the bound."""
+    G_, Wt = M.unflatten(g, K), M.unflatten(want, K)
+    worst = {}
+    for name, _ in M.param_shapes(K):
+        S, m = bounds[name]
+        err = np.abs(G_[name] - Wt[name])
+        tol = U_BF16 * np.abs(Wt[name]) + 8 * np.sqrt(B) * U_FP32 * S + 4 * 2 * U_BF16 * m
+        # where every product is zero (padded columns, units that never fire) the bound is 0: exact zeros
+        ratio = np.where(tol > 0, err / np.where(tol > 0, tol, 1.0), np.where(err > 0, np.inf, 0.0))
+        k = np.unravel_index(np.argmax(ratio), ratio.shape)
+        worst[name] = float(ratio[k])
+        assert ratio[k] <= 1.0, (name, k, float(G_[name][k]), float(Wt[name][k]), float(tol[k]))
+    return worst
+
+
 def check_gradient(g, theta, X, y, K, cells, loss=None):
-    """g (flat, from the kernels), per parameter block: within FP32
-    accumulation order of the fp64 gradient taken with the kernels' BF16
-    rounding points, and within the BF16 rounding error (a few percent at
-    small batches, where few rows average it out) of the plain fp64 gradient
-    of the same BF16 weights."""
+    """g (flat, from the kernels): element by element within the bound of
+    elements_close of the fp64 gradient taken with the kernels' BF16 rounding
+    points; per parameter block within 2e-3 of it in relative L2 norm; and
+    within the BF16 rounding error (a few percent at small batches, where few
+    rows average it out) of the plain fp64 gradient of the same BF16 weights."""
     th = rounded_theta(theta, K)
     if loss is not None:
         assert abs(loss - M.loss(th, X, y, K)) < 1e-3 * max(1.0, M.loss(th, X, y, K))
-    blocks_close(g, grad_bf16(theta, X, y, K), K, 2e-3, 0.99999)
+    want, bounds = grad_bf16(theta, X, y, K, with_bounds=True)
+    elements_close(g, want, bounds, K, X.shape[0])
+    blocks_close(g, want, K, 2e-3, 0.99999)
     blocks_close(g, M.grad(th, X, y, K), K, 6e-2, 0.998)
     # padded input columns never receive gradient
     assert np.abs(M.unflatten(g, K)["W1"][:, 2 * cells + 1:]).max() == 0.0
