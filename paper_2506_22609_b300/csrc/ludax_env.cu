@@ -382,7 +382,10 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
             const int64_t e = env[i];
             if (a.outcome) a.outcome[e] = (int8_t)g[i].outcome;
             if (a.plies) a.plies[e] = (int16_t)g[i].ply;
-            if (a.write_back) store_state(g[i], a.d, e);
+            if (a.write_back) {
+                settle_of(g[i]);
+                store_state(g[i], a.d, e);
+            }
             if (g[i].outcome == kCapped) atomicAdd(&a.d.counters[2], 1ull);
             if (refill) {
                 env[i] = slots + claim_next(&a.d.counters[0]);
@@ -482,7 +485,10 @@ __global__ void __launch_bounds__(512) rollout_compact_kernel(RolloutArgs a, int
             if (g.outcome != kOngoing || g.ply >= stop) {
                 if (a.outcome) a.outcome[env] = (int8_t)g.outcome;
                 if (a.plies) a.plies[env] = (int16_t)g.ply;
-                if (a.write_back) store_state(g, a.d, env);
+                if (a.write_back) {
+                    settle_of(g);
+                    store_state(g, a.d, env);
+                }
                 if (g.outcome == kCapped) atomicAdd(&a.d.counters[2], 1ull);
                 active = false;
             }

@@ -36,7 +36,12 @@
 //                the stones not yet connected to any edge that it links are
 //                added to that set by a flood fill.  This is the incremental
 //                connected-component update of Sec. 4 ("Dynamic State
-//                Attributes") in bitboard form.
+//                Attributes") in bitboard form.  The fused playouts spread
+//                that flood one layer per loop step instead (place_spread /
+//                spread): every lane runs the same one-layer dilation each
+//                step, and an env plays its next ply only once its flood has
+//                stopped, so the lanes of a warp no longer wait for the
+//                longest flood of the warp at every ply.
 //   Gomoku 15x15 / Pente 19x19 / Yavalath: W-word bitboards (BitsW) with one
 //                empty padding column per row (strides 16, 20 and 10), so
 //                shifted line and capture patterns cannot wrap across rows;
@@ -379,10 +384,14 @@ struct Hex {
     B128 own, opp;        // stones
     B128 ownA, ownB;      // own stones connected to own's edge A / edge B
     B128 oppA, oppB;
+    B128 front;           // outer layer of the last mover's group still spreading (fused playouts), or empty
     int side, ply, passes, outcome;
     const B128* nbr_table;  // per-cell neighbour masks in shared memory, or nullptr
 
     __device__ __forceinline__ static B128 board() { return {kBoardLo, kBoardHi}; }
+    // a value known to lie on the board: on boards of at most 64 cells the
+    // high word is the constant 0, so the compiler drops every high-word op
+    __device__ __forceinline__ static B128 fit(B128 a) { return {a.lo, kBoardHi ? a.hi : 0ull}; }
     __device__ __forceinline__ static B128 nbrs(B128 s) {
         const B128 notc0 = {kBoardLo & ~kCol0Lo, kBoardHi & ~kCol0Hi};
         const B128 notcl = {kBoardLo & ~kColLLo, kBoardHi & ~kColLHi};
@@ -409,7 +418,7 @@ struct Hex {
         return c;
     }
     __device__ __forceinline__ void reset() {
-        own = opp = ownA = ownB = oppA = oppB = B128{0, 0};
+        own = opp = ownA = ownB = oppA = oppB = front = B128{0, 0};
         side = ply = passes = 0;
         outcome = kOngoing;
     }
@@ -439,28 +448,83 @@ struct Hex {
         side ^= 1;
     }
     __device__ __forceinline__ void pass() {}
+    // The same placement with the flood left to spread(): the stone and its
+    // neighbours among the mover's stones outside both edge sets join the
+    // touched set now, and `front` keeps those neighbours, the layer from
+    // which the group goes on growing.  The edge sets are exact again once
+    // spread() has returned false; until then no ply may be played.
+    __device__ __forceinline__ void place_spread(int b) {
+        const B128 x = fit(bit128(b));
+        const B128 nx = fit(nbr_table ? nbr_table[b] : nbrs(x));
+        const bool ta = any((x & edgeA(side)) | (nx & ownA));
+        const bool tb = any((x & edgeB(side)) | (nx & ownB));
+        own = fit(own) | x;
+        if (ta && tb) {
+            outcome = side + 1;
+        } else if (ta || tb) {
+            const B128 first = nx & own & ~(ownA | ownB);
+            const B128 c = x | first;
+            if (ta) ownA = ownA | c;
+            else ownB = ownB | c;
+            front = first;
+        }
+        ++ply;
+        B128 t = own; own = opp; opp = t;
+        t = ownA; ownA = oppA; oppA = t;
+        t = ownB; ownB = oppB; oppB = t;
+        side ^= 1;
+    }
+    // One layer of the last mover's (now opp's) spreading group: the
+    // neighbours of `front` among its stones outside both edge sets join the
+    // set that `front` belongs to and become the new front.  The same
+    // instructions run whether or not anything is spreading (an empty front
+    // adds nothing).  Returns true while the group is still growing.
+    __device__ __forceinline__ bool spread() {
+        const B128 f = fit(front), a = fit(oppA), b = fit(oppB);
+        const bool to_a = any(f & a);
+        const B128 nw = nbrs(f) & fit(opp) & ~(a | b);
+        const B128 z = {0ull, 0ull};
+        oppA = a | (to_a ? nw : z);
+        oppB = b | (to_a ? z : nw);
+        front = nw;
+        return any(nw);
+    }
+    // k-th legal cell; on boards of at most 64 cells only the low word exists
+    __device__ __forceinline__ static int pick(B128 m, uint32_t k) {
+        if constexpr (kBoardHi == 0) return select_bit(m.lo, k);
+        else return select_bit(m, k);
+    }
+    // finish a spreading group (before the state leaves the registers)
+    __device__ __forceinline__ void settle() {
+#pragma unroll 1
+        while (spread()) {
+        }
+    }
     // rebuild the edge-connected sets of both players from the stones
     __device__ __forceinline__ void rebuild() {
         ownA = flood(own & edgeA(side), own);
         ownB = flood(own & edgeB(side), own);
         oppA = flood(opp & edgeA(side ^ 1), opp);
         oppB = flood(opp & edgeB(side ^ 1), opp);
+        front = B128{0, 0};
     }
     __device__ __forceinline__ static int canon_of(int b) { return b; }
     __device__ __forceinline__ static int bit_of(int cell) { return cell; }
     __device__ __forceinline__ static uint64_t canon_word(Mask m, int w) { return w == 0 ? m.lo : m.hi; }
-    static constexpr int kWords = 13;
+    static constexpr int kWords = 15;
     __device__ __forceinline__ void save(uint64_t* w) const {
         w[0] = own.lo; w[1] = own.hi; w[2] = opp.lo; w[3] = opp.hi;
         w[4] = ownA.lo; w[5] = ownA.hi; w[6] = ownB.lo; w[7] = ownB.hi;
         w[8] = oppA.lo; w[9] = oppA.hi; w[10] = oppB.lo; w[11] = oppB.hi;
         w[12] = pack_small(ply, passes, side, outcome);
+        w[13] = front.lo; w[14] = front.hi;
     }
     __device__ __forceinline__ void load(const uint64_t* w) {
         own = {w[0], w[1]}; opp = {w[2], w[3]};
         ownA = {w[4], w[5]}; ownB = {w[6], w[7]};
         oppA = {w[8], w[9]}; oppB = {w[10], w[11]};
         unpack_small(w[12], ply, passes, side, outcome);
+        front = {w[13], w[14]};
     }
 };
 
@@ -955,6 +1019,18 @@ struct IsOrdinal : std::false_type {};
 template <class G>
 struct IsOrdinal<G, std::enable_if_t<G::kOrdinal>> : std::true_type {};
 
+// Games whose placement can leave a flood to spread over later loop steps
+// (Hex in the fused playouts): place_spread(), spread(), settle().
+template <class G, class = void>
+struct HasSpread : std::false_type {};
+template <class G>
+struct HasSpread<G, std::void_t<decltype(std::declval<G&>().spread())>> : std::true_type {};
+// bring a state whose flood may still be spreading to its exact form
+template <class G>
+__device__ __forceinline__ void settle_of(G& g) {
+    if constexpr (HasSpread<G>::value) g.settle();
+}
+
 // ---------------------------------------------------------- one random ply --
 // Uniform-random policy: n legal cells, k-th in ascending cell id with
 // k = umulhi(top32(sm(key ^ ply)), n); a forced pass draws nothing.
@@ -1008,8 +1084,20 @@ __device__ __forceinline__ void random_ply_warp(G& g, uint64_t key, int lane) {
 __device__ __forceinline__ uint32_t draw_hi(uint64_t key, uint32_t ply) {
     return (uint32_t)(splitmix64(key ^ (uint64_t)ply) >> 32);
 }
+// Games with a spreading flood (HasSpread) first grow it by one layer; while
+// it still grows the env plays no ply this step (its edge sets are not yet
+// exact), so every ply sees the same state as with the eager flood.
 template <class G>
 __device__ __forceinline__ void random_ply_pre(G& g, uint64_t key, uint32_t& rhi) {
+    if constexpr (HasSpread<G>::value) {
+        if (g.spread()) return;
+        const uint32_t rnext = draw_hi(key, (uint32_t)g.ply + 1u);
+        const typename G::Mask m = g.legal();
+        g.place_spread(G::pick(m, __umulhi(rhi, popc(m))));
+        if (g.outcome == kOngoing && g.ply >= G::kCap) g.outcome = kCapped;
+        rhi = rnext;
+        return;
+    }
     const uint32_t rnext = draw_hi(key, (uint32_t)g.ply + 1u);
     if constexpr (IsOrdinal<G>::value) {
         g.place((int)__umulhi(rhi, (uint32_t)g.count()));

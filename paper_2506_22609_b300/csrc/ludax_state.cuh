@@ -118,6 +118,7 @@ __device__ __forceinline__ void load_state(G& g, const EnvDev& d, int64_t e) {
         g.ownB = p1 ? b1 : b2;
         g.oppA = p1 ? a2 : a1;
         g.oppB = p1 ? b2 : b1;
+        g.front = B128{0, 0};  // a stored state is settled
     }
     refresh_of(g);
 }
