@@ -11,14 +11,17 @@ workload is reset to the start position and played to the end of its game
 with the counter-based uniform-random policy (legal mask, draw, select,
 apply with captures/flips/gravity, terminal and win detection, all in
 registers), and each env's outcome and game length are written to HBM.
-The default workload is Connect Four 6x7, 65,536 envs, seed 1.
+The default workload is the mixed batch: 1,048,576 envs split evenly over
+Tic-Tac-Toe, Connect Four, Reversi and Hex 7x7 / 9x9 / 11x11, seed 3, one
+graph-captured launch per step (the largest single-GPU configuration).
 
 Metric: env steps per second = total plies played (passes included) / time.
 `value` is device time (CUDA events on the launching stream) with L2 flushed
 between steps; `e2e` goes through the C-ABI call with host buffers
-(ludax_rollout_host): start positions in the packed state view copied from
-pinned host memory and loaded, the playout, and outcome + game length copied
-back to pinned host memory.
+(ludax_mixed_plan_launch_host for the mixed batch: descriptors copied from
+pinned host memory, the work queue rebuilt on the device, the playouts, and
+outcome + game length copied back; ludax_rollout_host for a single game:
+start positions in the packed state view in, the same results out).
 
 Under torchrun (N > 1) each rank plays its own disjoint range of global env
 ids (weak scaling, no collective on the data path); the step time is the
@@ -51,11 +54,21 @@ METRIC = "env steps/sec on 1 B300 (random playouts); value estimates/sec at stat
 # shifts) 248, outcome and turn 9.
 ALG_OPS_PER_STEP = {"ttt": 75, "c4": 112, "othello": 437, "hex": 180, "gomoku": 330, "pente": 700,
                     "yavalath": 150, "line": 334}
+# The survey's estimates of the same work (its measurement section): TTT ~40,
+# C4 ~80, Reversi ~350-500 (our 437 lies inside), Hex ~100 + ~40 per flood
+# round; a random Hex game needs 0.27-0.29 flood rounds per ply on 7x7 to
+# 11x11 boards (the incremental edge-set update), so Hex ~112.
+SURVEY_OPS_PER_STEP = {"ttt": 40, "c4": 80, "othello": 437, "hex": 112}
+# game id of a descriptor (low byte) -> key of the tables above
+GAME_KEYS = {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente", 6: "yavalath", 7: "line"}
 
 # DRAM bytes per launch of the benchmarked kernel, from the committed ncu
 # captures (profiles/); None once the kernel changes until it is captured again.
 NCU_TRAFFIC_BYTES = {"connect4_6x7_65536env_seed1": 13568,
                      "connect4_6x7_16777216env_random_step_seed1": 335567360 + 426561280}
+# thread instructions ncu counts executed per env step (smsp__thread_inst_executed.sum
+# / plies of the launch), from the same captures; None until re-captured
+NCU_THREAD_INST_PER_STEP = {}
 
 
 def parse():
@@ -64,7 +77,7 @@ def parse():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="c4", choices=["c4", "ttt", "othello", "hex11", "gomoku", "pente", "yavalath",
+    p.add_argument("--workload", default="mixed", choices=["c4", "ttt", "othello", "hex11", "gomoku", "pente", "yavalath",
                                                         "line_c5", "wolf_sheep", "draughts", "hasami_shogi", "mixed",
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
@@ -163,6 +176,21 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle --
+def sample_ranges(cfg, n, desc=None):
+    """(offset, count) env ranges of a CPU sample of n envs: the first n envs of
+    a single-game batch; for a mixed batch laid out in game blocks, an equal
+    share from the start of every block, so every game is in the sample in
+    its batch proportion."""
+    if desc is None:
+        return [(0, n)]
+    import numpy as np
+
+    starts = [0] + [int(i) for i in np.nonzero(desc[1:] != desc[:-1])[0] + 1]
+    ends = starts[1:] + [len(desc)]
+    k = max(1, n // len(starts))
+    return [(a, min(k, b - a)) for a, b in zip(starts, ends)]
+
+
 def cpu_oracle_rate(cfg, seconds, desc=None):
     """The CPU oracle as it stands (plain C, -O2), all host cores via threads
     (ctypes releases the GIL), on a sample of the workload's envs sized to
@@ -175,7 +203,9 @@ def cpu_oracle_rate(cfg, seconds, desc=None):
 
     cores = len(os.sched_getaffinity(0))
 
-    def run(n, off):
+    def run(off, n):
+        if n <= 0:
+            return 0
         if desc is not None:
             _, p = OG.rollout_mixed(desc[off:off + n], cfg.seed, env_offset=off)
         else:
@@ -184,18 +214,26 @@ def cpu_oracle_rate(cfg, seconds, desc=None):
         return int(p.astype(np.int64).sum())
 
     total_envs = cfg.num_envs
-    # calibrate on one core
-    n0 = 256
+    # calibrate on one core with a small sample of the same composition
+    n0 = 256 if desc is None else 64 * len(sample_ranges(cfg, 64, desc))
     t0 = time.perf_counter()
-    run(n0, 0)
+    for off, k in sample_ranges(cfg, n0, desc):
+        run(off, k)
     per_env = max((time.perf_counter() - t0) / n0, 1e-7)
     n = int(min(total_envs, max(cores * 64, seconds * cores / per_env)))
-    chunk = (n + cores - 1) // cores
+    chunks = []
+    for off, k in sample_ranges(cfg, n, desc):
+        step = (k + cores - 1) // cores
+        chunks += [(off + i, min(step, k - i)) for i in range(0, k, step)]
     t0 = time.perf_counter()
     with ThreadPoolExecutor(cores) as ex:
-        steps = sum(ex.map(lambda i: run(min(chunk, n - i * chunk), i * chunk), range(cores)))
+        steps = sum(ex.map(lambda c: run(*c), chunks))
     dt = time.perf_counter() - t0
-    return steps / dt, cores, f"first {n} of {total_envs} envs (global ids 0..{n - 1}), {cores} threads, {dt:.2f} s"
+    ranges = sample_ranges(cfg, n, desc)
+    where = (f"first {n} of {total_envs} envs (global ids 0..{n - 1})" if desc is None else
+             f"{sum(k for _, k in ranges)} of {total_envs} envs: the first {ranges[0][1]} of each of the "
+             f"{len(ranges)} game blocks")
+    return steps / dt, cores, f"{where}, {cores} threads, {dt:.2f} s"
 
 
 def cpu_model():
@@ -216,21 +254,24 @@ def cpu_oracle_single_thread(cfg, seconds, desc=None):
     from oracle import games as OG
 
     def run(n):
-        if desc is not None:
-            _, p = OG.rollout_mixed(desc[:n], cfg.seed, env_offset=0)
-        else:
-            gid = cfg.game if cfg.game != 7 else 7 | (cfg.line << 8) | (cfg.flags << 12)
-            _, p, _ = OG.rollout_start(gid, cfg.rows, cfg.cols, n, cfg.seed, env_offset=0)
-        return int(p.astype(np.int64).sum())
+        steps = 0
+        for off, k in sample_ranges(cfg, n, desc):
+            if desc is not None:
+                _, p = OG.rollout_mixed(desc[off:off + k], cfg.seed, env_offset=off)
+            else:
+                gid = cfg.game if cfg.game != 7 else 7 | (cfg.line << 8) | (cfg.flags << 12)
+                _, p, _ = OG.rollout_start(gid, cfg.rows, cfg.cols, k, cfg.seed, env_offset=off)
+            steps += int(p.astype(np.int64).sum())
+        return steps
 
     t0 = time.perf_counter()
-    run(128)
-    per_env = max((time.perf_counter() - t0) / 128, 1e-7)
+    run(128 if desc is None else 384)
+    per_env = max((time.perf_counter() - t0) / (128 if desc is None else 384), 1e-7)
     n = int(min(cfg.num_envs, max(128, seconds / per_env)))
     t0 = time.perf_counter()
     steps = run(n)
     dt = time.perf_counter() - t0
-    return steps / dt, f"first {n} envs, 1 thread, {dt:.2f} s"
+    return steps / dt, f"{n} envs as in the multi-thread sample, 1 thread, {dt:.2f} s"
 
 
 # ------------------------------------------------------------- GPU parts --
@@ -355,6 +396,8 @@ def e2e_rollout(L, cfg, steps, warmup, rank=0):
 
 
 def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
+    """The graph-captured mixed plan over the 2^20-env six-game batch; returns
+    the per-launch times, the plies of one launch and those plies per game id."""
     import torch
 
     d = torch.from_numpy(W.mixed_descriptors(W.MIXED_ENVS, "block")).cuda()
@@ -364,8 +407,72 @@ def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
     fn = lambda: L.ludax_mixed_plan_launch(plan, W.MIXED_SEED, out, plies)  # noqa: E731
     ms = time_steps(fn, steps, warmup, flush_buf, torch.cuda.current_stream())
     total = int(plies.to(torch.int64).sum().item())
+    per_game = torch.bincount((d & 0xFF).long(), weights=plies.double()).cpu().tolist()
     L.ludax_mixed_plan_destroy(plan)
-    return ms, total
+    return ms, total, {g: int(v) for g, v in enumerate(per_game) if v}
+
+
+def e2e_mixed(L, W, steps, warmup, rank=0, depth=4):
+    """Public-API path with host buffers, every step: one
+    ludax_mixed_plan_launch_host call -- the 2^20 descriptors copied from
+    pinned host memory, the game-grouped queue rebuilt on the device, the
+    playouts, outcome and plies copied back to pinned host memory.  `depth`
+    plans on their own streams rotate, so one step's copies overlap another's
+    playouts; the host waits for step i - depth + 1 after issuing step i."""
+    import numpy as np
+    import torch
+
+    n = W.MIXED_ENVS
+    d = W.mixed_descriptors(n, "block")
+    dd = torch.from_numpy(d).cuda()
+    slots = []
+    for _ in range(depth):
+        stream = torch.cuda.Stream()
+        plan = L.ludax_mixed_plan_create(dd, D_shard(rank, n), L.make_cfg(*W.mixed_bench_cfg()), stream=stream)
+        slots.append((stream, plan, torch.from_numpy(d.copy()).pin_memory(),
+                      torch.empty(n, dtype=torch.int8).pin_memory(), torch.empty(n, dtype=torch.int16).pin_memory()))
+
+    def run(k):
+        for i in range(k):
+            _, plan, h_desc, h_out, h_plies = slots[i % depth]
+            L.ludax_mixed_plan_launch_host(plan, W.MIXED_SEED, h_desc, h_out, h_plies)
+            if i >= depth - 1:
+                L.ludax_mixed_plan_sync(slots[(i - depth + 1) % depth][1])
+        for sl in slots:
+            L.ludax_mixed_plan_sync(sl[1])
+
+    run(warmup)
+    times = []
+    for _ in range(3):  # the host and its link are shared: the median of three blocks of `steps`
+        t0 = time.perf_counter()
+        run(steps)
+        times.append((time.perf_counter() - t0) / steps)
+    dt = statistics.median(times)
+    spl = int(slots[(steps - 1) % depth][4].numpy().astype(np.int64).sum())
+    # the host link alone: the same three copies, each direction timed by CUDA events
+    stream, _, h_desc, h_out, h_plies = slots[0]
+    d_desc = torch.empty_like(h_desc, device="cuda")
+    d_out, d_plies = torch.empty_like(h_out, device="cuda"), torch.empty_like(h_plies, device="cuda")
+
+    def copy_time(fn):
+        ts = []
+        for i in range(13):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record()
+                fn()
+                b.record()
+            b.synchronize()
+            if i >= 3:
+                ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    link = {"h2d_ms": copy_time(lambda: d_desc.copy_(h_desc, non_blocking=True)),
+            "d2h_ms": copy_time(lambda: (h_out.copy_(d_out, non_blocking=True),
+                                         h_plies.copy_(d_plies, non_blocking=True)))}
+    for sl in slots:
+        L.ludax_mixed_plan_destroy(sl[1])
+    return spl / dt, 4 * n, 3 * n, dt, link, spl, [round(t * 1e3, 4) for t in times]
 
 
 SWEEP_GAMES = ("ttt", "c4", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5", "wolf_sheep", "draughts",
@@ -712,7 +819,7 @@ def main():
             wl_name, n_envs, seed = cfg.name, cfg.num_envs, cfg.seed
             launch = lc.as_dict()
         else:
-            ms, steps_per_launch = bench_mixed(L, W, args.steps, args.warmup, flush_buf, rank)
+            ms, steps_per_launch, plies_per_game = bench_mixed(L, W, args.steps, args.warmup, flush_buf, rank)
             wl_name, n_envs, seed = "mixed6_1048576env_seed3_graph", W.MIXED_ENVS, W.MIXED_SEED
             launch = dict(zip(("block_threads", "blocks_per_sm", "envs_per_thread", "hex_nbr_table",
                                "compact_every"), W.mixed_bench_cfg()))
@@ -728,8 +835,15 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_ops = sms * 128 * max_mhz * 1e6  # 32-bit lanes x clock
+    ops_survey = None
     if cfg is not None and game_key(cfg) in ALG_OPS_PER_STEP:
         ops_per_launch = ALG_OPS_PER_STEP[game_key(cfg)] * steps_per_launch
+        if game_key(cfg) in SURVEY_OPS_PER_STEP:
+            ops_survey = SURVEY_OPS_PER_STEP[game_key(cfg)] * steps_per_launch
+    elif args.workload == "mixed":
+        # the sum over the mix's games of (ops per step x that game's plies in the launch)
+        ops_per_launch = sum(ALG_OPS_PER_STEP[GAME_KEYS[g]] * v for g, v in plies_per_game.items())
+        ops_survey = sum(SURVEY_OPS_PER_STEP[GAME_KEYS[g]] * v for g, v in plies_per_game.items())
     else:
         ops_per_launch = None
     med = statistics.median(ms)
@@ -743,14 +857,27 @@ def main():
                     "peak_source": f"hbm_gbs ({peak_kind})", "alg_bytes_per_env_step": bytes_per,
                     "median_launch_ms": round(med, 5)}
     if ops_per_launch:
-        achieved = ops_per_launch / (med / 1e3) / 1e12
+        # frac uses the survey's op counts where it gives them; the builder's own
+        # counts of the bitboard algorithm and ncu's executed count sit beside it
         alu_pipe = peak_ops / 2  # logic/shift/add run on the ALU pipe: 64 lanes per clock per SM
+        achieved_b = ops_per_launch / (med / 1e3) / 1e12
+        achieved = (ops_survey or ops_per_launch) / (med / 1e3) / 1e12
+        if cfg is not None:
+            per_step = {"builder": ALG_OPS_PER_STEP[game_key(cfg)],
+                        "survey": SURVEY_OPS_PER_STEP.get(game_key(cfg))}
+        else:
+            per_step = {"builder": {GAME_KEYS[g]: ALG_OPS_PER_STEP[GAME_KEYS[g]] for g in plies_per_game},
+                        "survey": {GAME_KEYS[g]: SURVEY_OPS_PER_STEP[GAME_KEYS[g]] for g in plies_per_game},
+                        "plies_per_game": {GAME_KEYS[g]: v for g, v in plies_per_game.items()}}
         roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_ops / 1e12, 3),
                     "unit": "Tops/s (32-bit integer)", "frac": round(achieved / (peak_ops / 1e12), 4),
+                    "counts": "survey" if ops_survey else "builder",
                     "alu_pipe_peak": round(alu_pipe / 1e12, 3), "alu_pipe_frac": round(achieved / (alu_pipe / 1e12), 4),
+                    "frac_builder_counts": round(achieved_b / (peak_ops / 1e12), 4),
+                    "ncu_thread_instructions_per_step": NCU_THREAD_INST_PER_STEP.get(wl_name),
                     "traffic": NCU_TRAFFIC_BYTES.get(wl_name),
                     "peak_source": f"{sms} SMs x 128 int32 lanes x {max_mhz:.0f} MHz (sm_max_mhz, {peak_kind})",
-                    "alg_ops_per_step": ALG_OPS_PER_STEP[game_key(cfg)], "median_launch_ms": round(med, 5)}
+                    "alg_ops_per_step": per_step, "median_launch_ms": round(med, 5)}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "env steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 5),
@@ -761,7 +888,7 @@ def main():
                        "timing": "CUDA events around each launch on the launching stream, summed over steps",
                        "env_steps_per_launch": steps_per_launch, "episodes_per_launch": n_envs},
             "roofline": roofline, "clocks": clocks,
-            "gpu_launches": args.steps * (2 if args.workload == "mixed" else 1)}
+            "gpu_launches": args.steps}
 
     if rank == 0 and cfg is not None and args.workload != "step_c4":
         e2e_val, h2d, d2h, dt, _, link, spl = e2e_rollout(L, cfg, max(3, min(args.steps, 100)), 3, rank)
@@ -779,6 +906,20 @@ def main():
                                "(2 bits per cell + a meta word per env) -> device -> playouts -> pinned host "
                                "outcome/plies; six envs on six streams rotate so one step's copies overlap "
                                "another's playouts; wall clock over blocks of steps, median of 5 blocks"}
+    if rank == 0 and args.workload == "mixed":
+        e2e_val, h2d, d2h, dt, link, spl, blocks = e2e_mixed(L, W, max(3, min(args.steps, 50)), 3, rank)
+        t_bound = max(link["h2d_ms"], link["d2h_ms"], med) / 1e3
+        line["e2e"] = {"value": round(e2e_val * world, 1), "unit": "env steps/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 4), "ms_per_step_blocks": blocks,
+                       "link": {"h2d_ms": round(link["h2d_ms"], 4), "d2h_ms": round(link["d2h_ms"], 4),
+                                "h2d_gbs": round(h2d / link["h2d_ms"] / 1e6, 2),
+                                "d2h_gbs": round(d2h / link["d2h_ms"] / 1e6, 2),
+                                "bound_env_steps_per_s": round(spl / t_bound, 1),
+                                "frac": round(e2e_val / (spl / t_bound), 4)},
+                       "path": "ludax_mixed_plan_launch_host per step: pinned host descriptors (int32 per env) -> "
+                               "device -> work queue rebuilt on the device -> playouts -> pinned host outcome/plies; "
+                               "four plans on four streams rotate so one step's copies overlap another's playouts; "
+                               "wall clock over blocks of steps, median of 3 blocks"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         desc = None
         if args.workload == "step_c4":
@@ -796,8 +937,10 @@ def main():
                                 "single_thread": {"value": round(v1, 1), "sample": sample1}}
     if rank == 0 and world == 1 and not args.no_extras:
         extras = {}
-        for name in ("ttt", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5", "wolf_sheep", "draughts",
-                     "hasami_shogi"):
+        for name in ("ttt", "c4", "othello", "hex11", "gomoku", "pente", "yavalath", "line_c5", "wolf_sheep",
+                     "draughts", "hasami_shogi"):
+            if name == args.workload:
+                continue
             c = workload_cfg(name)
             e, lc, ms2, spl = bench_rollout_config(L, W, c, 20, 3, flush_buf)
             m2 = statistics.median(ms2)
@@ -807,10 +950,11 @@ def main():
                               "alu_frac": (round(ALG_OPS_PER_STEP[game_key(c)] * rate / peak_ops, 4)
                                            if game_key(c) in ALG_OPS_PER_STEP else None)}
             e.close()
-        ms3, tot = bench_mixed(L, W, 10, 2, flush_buf)
-        m3 = statistics.median(ms3)
-        extras["mixed6_1048576env_seed3_graph"] = {"env_steps_per_s": round(tot / (m3 / 1e3), 1),
-                                                   "median_launch_ms": round(m3, 4), "env_steps_per_launch": tot}
+        if args.workload != "mixed":
+            ms3, tot, _ = bench_mixed(L, W, 10, 2, flush_buf)
+            m3 = statistics.median(ms3)
+            extras["mixed6_1048576env_seed3_graph"] = {"env_steps_per_s": round(tot / (m3 / 1e3), 1),
+                                                       "median_launch_ms": round(m3, 4), "env_steps_per_launch": tot}
         extras["compiled_library_1048576env_seed3"] = bench_compiled_library(L, 10, 2, flush_buf)
         for gname in ("c4", "othello"):
             sm = bench_step_mode(L, 10, flush_buf, gname, 1 << 24 if gname == "c4" else 1 << 22)

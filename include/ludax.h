@@ -325,6 +325,26 @@ int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int
 /* Replay the captured graph with a new seed and output buffers:
  * outcome_dev int8 [num_envs], plies_dev int16 [num_envs].                */
 int ludax_mixed_plan_launch(ludax_mixed_plan* plan, uint64_t seed, int8_t* outcome_dev, int16_t* plies_dev);
+/* The plan's playout with the batch in HOST memory (the end-to-end form of
+ * the mixed-batch benchmark of Sec. 6): desc_host int32 [num_envs] (any
+ * descriptors, not only those the plan was built from) is copied to the
+ * device, the game-grouped work queue is rebuilt there (no host round trip),
+ * the envs are played with the plan's launch shape and env_offset, and
+ * outcome_host int8 [num_envs] and plies_host int16 [num_envs] are copied
+ * back -- all asynchronously on the plan's stream, so the host buffers must
+ * stay valid until the stream reaches this call (pinned memory lets the
+ * copies overlap other streams' work).  The plan's first host-buffer call
+ * allocates its device staging (11 bytes per env + 1 KiB) and one pinned
+ * word.  An env whose descriptor is invalid is not played (outcome -1,
+ * plies 0); ludax_mixed_plan_sync reports it.  Calls on one plan are ordered
+ * by its stream; the replayed graph (ludax_mixed_plan_launch) keeps its own
+ * queue and is unaffected.                                                 */
+int ludax_mixed_plan_launch_host(ludax_mixed_plan* plan, uint64_t seed, const int32_t* desc_host,
+                                 int8_t* outcome_host, int16_t* plies_host);
+/* Wait for the plan's stream; if the last host-buffer launch met an invalid
+ * descriptor, return LUDAX_ERR_GAME or LUDAX_ERR_SIZE for the first one and
+ * its index through bad_index (nullable; -1 when none).                    */
+int ludax_mixed_plan_sync(ludax_mixed_plan* plan, int64_t* bad_index);
 int ludax_mixed_plan_destroy(ludax_mixed_plan* plan);
 
 /* Same work without a graph: one direct launch (used to validate the graph). */

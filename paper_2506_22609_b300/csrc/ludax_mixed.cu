@@ -47,15 +47,23 @@ struct MixedArgs {
     uint64_t seed_key;
     int8_t* outcome;
     int16_t* plies;
-    unsigned long long* cursor;      // claim cursor (word 0), zeroed before each launch
+    unsigned long long* cursor;      // per-bucket claim cursors, zeroed before each launch
+    const long long* bucket_end_dev; // non-null: the bucket ends were built on the device (host-buffer path)
 };
 // The mixed kernel takes exactly one parameter (MixedArgs): the graph plan
 // rewrites that single parameter before each replay.
 
-__device__ __forceinline__ int bucket_at(const MixedArgs& a, long long q) {
+// Every block first copies the bucket ends into shared memory (from the
+// kernel parameter, or from device memory when the queue was built on the
+// device), and the helpers below read them there.
+__device__ __forceinline__ void load_bucket_ends(const MixedArgs& a, long long* be) {
+    if (threadIdx.x < kBuckets) be[threadIdx.x] = a.bucket_end_dev ? a.bucket_end_dev[threadIdx.x] : a.bucket_end[threadIdx.x];
+}
+
+__device__ __forceinline__ int bucket_at(const long long* be, long long q) {
     int b = 0;
 #pragma unroll
-    for (int k = 0; k < kBuckets - 1; ++k) b += q >= a.bucket_end[k];
+    for (int k = 0; k < kBuckets - 1; ++k) b += q >= be[k];
     return b;
 }
 
@@ -82,25 +90,26 @@ __device__ __forceinline__ void play_one(const MixedArgs& a, long long q, const 
 // drained; then the warp moves on to the next bucket with work.  (A single
 // cursor over the whole queue would let the lanes of a warp drift into
 // different games.)
-__device__ __forceinline__ long long bucket_begin(const MixedArgs& a, int b) { return b == 0 ? 0 : a.bucket_end[b - 1]; }
+__device__ __forceinline__ long long bucket_begin(const long long* be, int b) { return b == 0 ? 0 : be[b - 1]; }
 
 // positions for the lanes in `want` from bucket b's cursor (warp-aggregated);
 // a result >= the bucket's end means the bucket is drained
-__device__ __forceinline__ long long claim_in_bucket(const MixedArgs& a, int b, bool want) {
+__device__ __forceinline__ long long claim_in_bucket(const MixedArgs& a, const long long* be, int b, bool want) {
     const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
     const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
     unsigned long long base = 0;
     if (m && lane == leader) base = atomicAdd(&a.cursor[b], (unsigned long long)__popc(m));
     base = __shfl_sync(0xFFFFFFFFu, base, leader < 0 ? 0 : leader);
-    return bucket_begin(a, b) + (long long)(base + __popc(m & ((1u << lane) - 1u)));
+    return bucket_begin(be, b) + (long long)(base + __popc(m & ((1u << lane) - 1u)));
 }
 
 // One lane plays positions of bucket b, from its first claim q, taking the
 // next position from the bucket's cursor when a game ends (the lanes that
 // finish together claim with one atomic), until the bucket is drained.
 template <class G>
-__device__ __forceinline__ void drain_bucket(const MixedArgs& a, int b, long long q, const B128* table) {
-    const long long begin = bucket_begin(a, b), end = a.bucket_end[b];
+__device__ __forceinline__ void drain_bucket(const MixedArgs& a, const long long* be, int b, long long q,
+                                             const B128* table) {
+    const long long begin = bucket_begin(be, b), end = be[b];
     G g;
     set_table(g, table);
     long long e = a.queue[q];
@@ -126,28 +135,29 @@ __device__ __forceinline__ void drain_bucket(const MixedArgs& a, int b, long lon
 }
 
 template <bool TABLE>
-__device__ __forceinline__ void drain_any(const MixedArgs& a, int b, long long q, const B128* tables) {
+__device__ __forceinline__ void drain_any(const MixedArgs& a, const long long* be, int b, long long q,
+                                          const B128* tables) {
     switch (b) {
-    case 0: drain_bucket<TTT>(a, b, q, nullptr); break;
-    case 1: drain_bucket<C4>(a, b, q, nullptr); break;
-    case 2: drain_bucket<Othello>(a, b, q, nullptr); break;
-    case 3: drain_bucket<Hex<2>>(a, b, q, TABLE ? tables + hex_table_offset(2) : nullptr); break;
-    case 4: drain_bucket<Hex<3>>(a, b, q, TABLE ? tables + hex_table_offset(3) : nullptr); break;
-    case 5: drain_bucket<Hex<4>>(a, b, q, TABLE ? tables + hex_table_offset(4) : nullptr); break;
-    case 6: drain_bucket<Hex<5>>(a, b, q, TABLE ? tables + hex_table_offset(5) : nullptr); break;
-    case 7: drain_bucket<Hex<6>>(a, b, q, TABLE ? tables + hex_table_offset(6) : nullptr); break;
-    case 8: drain_bucket<Hex<7>>(a, b, q, TABLE ? tables + hex_table_offset(7) : nullptr); break;
-    case 9: drain_bucket<Hex<8>>(a, b, q, TABLE ? tables + hex_table_offset(8) : nullptr); break;
-    case 10: drain_bucket<Hex<9>>(a, b, q, TABLE ? tables + hex_table_offset(9) : nullptr); break;
-    case 11: drain_bucket<Hex<10>>(a, b, q, TABLE ? tables + hex_table_offset(10) : nullptr); break;
-    case 12: drain_bucket<Hex<11>>(a, b, q, TABLE ? tables + hex_table_offset(11) : nullptr); break;
-    case 13: drain_bucket<Gomoku>(a, b, q, nullptr); break;
-    case 14: drain_bucket<Pente>(a, b, q, nullptr); break;
-    case 15: drain_bucket<Yavalath>(a, b, q, nullptr); break;
-    case 16: drain_bucket<LineGame>(a, b, q, nullptr); break;
-    case 17: drain_bucket<WolfSheep>(a, b, q, nullptr); break;
-    case 18: drain_bucket<Draughts>(a, b, q, nullptr); break;
-    default: drain_bucket<HasamiShogi>(a, b, q, nullptr); break;
+    case 0: drain_bucket<TTT>(a, be, b, q, nullptr); break;
+    case 1: drain_bucket<C4>(a, be, b, q, nullptr); break;
+    case 2: drain_bucket<Othello>(a, be, b, q, nullptr); break;
+    case 3: drain_bucket<Hex<2>>(a, be, b, q, TABLE ? tables + hex_table_offset(2) : nullptr); break;
+    case 4: drain_bucket<Hex<3>>(a, be, b, q, TABLE ? tables + hex_table_offset(3) : nullptr); break;
+    case 5: drain_bucket<Hex<4>>(a, be, b, q, TABLE ? tables + hex_table_offset(4) : nullptr); break;
+    case 6: drain_bucket<Hex<5>>(a, be, b, q, TABLE ? tables + hex_table_offset(5) : nullptr); break;
+    case 7: drain_bucket<Hex<6>>(a, be, b, q, TABLE ? tables + hex_table_offset(6) : nullptr); break;
+    case 8: drain_bucket<Hex<7>>(a, be, b, q, TABLE ? tables + hex_table_offset(7) : nullptr); break;
+    case 9: drain_bucket<Hex<8>>(a, be, b, q, TABLE ? tables + hex_table_offset(8) : nullptr); break;
+    case 10: drain_bucket<Hex<9>>(a, be, b, q, TABLE ? tables + hex_table_offset(9) : nullptr); break;
+    case 11: drain_bucket<Hex<10>>(a, be, b, q, TABLE ? tables + hex_table_offset(10) : nullptr); break;
+    case 12: drain_bucket<Hex<11>>(a, be, b, q, TABLE ? tables + hex_table_offset(11) : nullptr); break;
+    case 13: drain_bucket<Gomoku>(a, be, b, q, nullptr); break;
+    case 14: drain_bucket<Pente>(a, be, b, q, nullptr); break;
+    case 15: drain_bucket<Yavalath>(a, be, b, q, nullptr); break;
+    case 16: drain_bucket<LineGame>(a, be, b, q, nullptr); break;
+    case 17: drain_bucket<WolfSheep>(a, be, b, q, nullptr); break;
+    case 18: drain_bucket<Draughts>(a, be, b, q, nullptr); break;
+    default: drain_bucket<HasamiShogi>(a, be, b, q, nullptr); break;
     }
 }
 
@@ -167,10 +177,13 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         hex_fill_table<11>(tables + hex_table_offset(11));
         __syncthreads();
     }
+    __shared__ long long be[kBuckets];
+    load_bucket_ends(a, be);
+    __syncthreads();
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= a.n) return;
+    if (q >= be[kBuckets - 1]) return;  // past the last valid queue position
     const B128* t = tables;
-    switch (bucket_at(a, q)) {
+    switch (bucket_at(be, q)) {
     case 0: play_one<TTT>(a, q, nullptr); break;
     case 1: play_one<C4>(a, q, nullptr); break;
     case 2: play_one<Othello>(a, q, nullptr); break;
@@ -212,15 +225,18 @@ __global__ void __launch_bounds__(512, 1) mixed_persistent_kernel(MixedArgs a) {
         hex_fill_table<11>(tables + hex_table_offset(11));
         __syncthreads();
     }
+    __shared__ long long be[kBuckets];
+    load_bucket_ends(a, be);
+    __syncthreads();
     const long long slots = (long long)gridDim.x * blockDim.x;
     const long long warps = slots >> 5, w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int b = bucket_at(a, w * a.n / warps);
+    int b = bucket_at(be, w * be[kBuckets - 1] / warps);
     for (int idle = 0; idle < kBuckets; b = (b + 1) % kBuckets) {
-        const long long q = claim_in_bucket(a, b, true);  // the whole warp enters bucket b together
-        const bool mine = q < a.bucket_end[b];
+        const long long q = claim_in_bucket(a, be, b, true);  // the whole warp enters bucket b together
+        const bool mine = q < be[b];
         if (__any_sync(0xFFFFFFFFu, mine)) {
             idle = 0;
-            if (mine) drain_any<TABLE>(a, b, q, tables);
+            if (mine) drain_any<TABLE>(a, be, b, q, tables);
         } else {
             ++idle;
         }
@@ -296,6 +312,79 @@ ludax_launch_cfg default_mixed_cfg() { return ludax_launch_cfg{256, 0, 1, 0, 0};
 
 }  // namespace
 
+// Host-buffer launches (ludax_mixed_plan_launch_host) build the work queue on
+// the device from the uploaded descriptors: a histogram of the buckets (and
+// the first invalid descriptor), one block turning it into bucket ends, and a
+// scatter of the env ids; the playout kernel then reads the bucket ends from
+// device memory.  Counter words: [0, 20) claim cursors, [20, 40) bucket
+// counts, [40, 60) fill positions, [60] first invalid index (all ones: none).
+namespace {
+constexpr int kHostCtrWords = 64, kHostCount = 20, kHostFill = 40, kHostBad = 60;
+static_assert(kBuckets <= 20, "counter layout holds 20 buckets");
+
+__global__ void hq_init_kernel(unsigned long long* ctr) {
+    if (threadIdx.x < kHostCtrWords) ctr[threadIdx.x] = threadIdx.x == kHostBad ? ~0ull : 0ull;
+}
+
+// bucket histogram (block-local, one atomic per bucket per block); an env
+// with an invalid descriptor is not played: its outcome is written as -1
+// (ongoing) and its length as 0, and the smallest such index is kept
+__global__ void hq_count_kernel(const int32_t* desc, long long n, unsigned long long* ctr, int8_t* outcome,
+                                int16_t* plies) {
+    __shared__ unsigned int hist[kBuckets];
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) {
+        const int b = desc_bucket(desc[e]);
+        if (b < 0) {
+            atomicMin(&ctr[kHostBad], (unsigned long long)e);
+            outcome[e] = -1;
+            plies[e] = 0;
+        } else {
+            atomicAdd(&hist[b], 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kBuckets && hist[threadIdx.x])
+        atomicAdd(&ctr[kHostCount + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+}
+
+// bucket ends = inclusive prefix sums of the counts (one thread: 20 values)
+__global__ void hq_scan_kernel(const unsigned long long* ctr, long long* bucket_end) {
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int b = 0; b < kBuckets; ++b) {
+            acc += (long long)ctr[kHostCount + b];
+            bucket_end[b] = acc;
+        }
+    }
+}
+
+// queue[begin(b) + k] = the env ids of bucket b (the order inside a bucket
+// follows the blocks' reservations; results do not depend on it: every draw
+// is keyed by the env's global index)
+__global__ void hq_scatter_kernel(const int32_t* desc, long long n, const long long* bucket_end,
+                                  unsigned long long* ctr, int32_t* queue) {
+    __shared__ unsigned int hist[kBuckets];
+    __shared__ unsigned long long base[kBuckets];
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int b = -1;
+    unsigned int rank = 0;
+    if (e < n) {
+        b = desc_bucket(desc[e]);
+        if (b >= 0) rank = atomicAdd(&hist[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kBuckets && hist[threadIdx.x])
+        base[threadIdx.x] = atomicAdd(&ctr[kHostFill + threadIdx.x], (unsigned long long)hist[threadIdx.x]);
+    __syncthreads();
+    if (b >= 0) queue[(b == 0 ? 0 : bucket_end[b - 1]) + (long long)base[b] + rank] = (int32_t)e;
+}
+}  // namespace
+
 struct ludax_mixed_plan {
     long long n, env_offset;
     int num_sms;
@@ -309,6 +398,10 @@ struct ludax_mixed_plan {
     cudaGraphNode_t kernel_node;
     cudaKernelNodeParams kparams;
     MixedArgs args;  // kernel parameter block updated before each replay
+    // host-buffer path (allocated by its first call)
+    uint8_t* d_host;           // descriptors, queue, outcome, plies, counters, bucket ends
+    unsigned long long* h_bad;  // pinned: first invalid index of the last host-buffer launch
+    bool host_used;
 };
 
 extern "C" {
@@ -451,6 +544,90 @@ int ludax_mixed_plan_launch(ludax_mixed_plan* p, uint64_t seed, int8_t* outcome_
     return LUDAX_OK;
 }
 
+namespace {
+// byte offsets of the host-buffer path's device scratch (each 256-byte aligned)
+struct HostLayout {
+    size_t desc, queue, out, plies, ctr, end, total;
+    explicit HostLayout(long long n) {
+        auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+        desc = 0;
+        queue = up(desc + 4 * (size_t)n);
+        out = up(queue + 4 * (size_t)n);
+        plies = up(out + (size_t)n);
+        ctr = up(plies + 2 * (size_t)n);
+        end = up(ctr + 8 * (size_t)kHostCtrWords);
+        total = up(end + 8 * (size_t)kBuckets);
+    }
+};
+}  // namespace
+
+int ludax_mixed_plan_launch_host(ludax_mixed_plan* p, uint64_t seed, const int32_t* desc_host, int8_t* outcome_host,
+                                 int16_t* plies_host) {
+    if (!p || !desc_host || !outcome_host || !plies_host) return LUDAX_ERR_ARG;
+    const long long n = p->n;
+    const HostLayout L(n);
+    if (!p->d_host) {
+        if (cudaMalloc(&p->d_host, L.total) != cudaSuccess) {
+            p->d_host = nullptr;
+            cudaGetLastError();
+            return LUDAX_ERR_NOMEM;
+        }
+        if (cudaMallocHost(&p->h_bad, sizeof(unsigned long long)) != cudaSuccess) {
+            p->h_bad = nullptr;
+            cudaGetLastError();
+            return LUDAX_ERR_NOMEM;
+        }
+    }
+    uint8_t* base = p->d_host;
+    int32_t* d_desc = reinterpret_cast<int32_t*>(base + L.desc);
+    int32_t* d_queue = reinterpret_cast<int32_t*>(base + L.queue);
+    int8_t* d_out = reinterpret_cast<int8_t*>(base + L.out);
+    int16_t* d_plies = reinterpret_cast<int16_t*>(base + L.plies);
+    unsigned long long* d_ctr = reinterpret_cast<unsigned long long*>(base + L.ctr);
+    long long* d_end = reinterpret_cast<long long*>(base + L.end);
+    cudaStream_t s = p->stream;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (cudaMemcpyAsync(d_desc, desc_host, 4 * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    hq_init_kernel<<<1, kHostCtrWords, 0, s>>>(d_ctr);
+    hq_count_kernel<<<grid, 256, 0, s>>>(d_desc, n, d_ctr, d_out, d_plies);
+    hq_scan_kernel<<<1, 32, 0, s>>>(d_ctr, d_end);
+    hq_scatter_kernel<<<grid, 256, 0, s>>>(d_desc, n, d_end, d_ctr, d_queue);
+    if (cudaGetLastError() != cudaSuccess) return LUDAX_ERR_CUDA;
+    MixedArgs a = p->args;
+    a.queue = d_queue;
+    a.desc = d_desc;
+    a.bucket_end_dev = d_end;
+    a.seed_key = splitmix64(seed);
+    a.outcome = d_out;
+    a.plies = d_plies;
+    a.cursor = d_ctr;  // words [0, kBuckets): zeroed by launch_mixed
+    int st = launch_mixed(a, p->cfg, p->num_sms, s);
+    if (st != LUDAX_OK) return st;
+    if (cudaMemcpyAsync(outcome_host, d_out, (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(plies_host, d_plies, 2 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(p->h_bad, d_ctr + kHostBad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    p->host_used = true;
+    return LUDAX_OK;
+}
+
+int ludax_mixed_plan_sync(ludax_mixed_plan* p, int64_t* bad_index) {
+    if (!p) return LUDAX_ERR_ARG;
+    if (bad_index) *bad_index = -1;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return LUDAX_ERR_CUDA;
+    if (!p->host_used || *p->h_bad == ~0ull) return LUDAX_OK;
+    const long long e = (long long)*p->h_bad;
+    if (bad_index) *bad_index = e;
+    int32_t d = 0;
+    const int32_t* d_desc = reinterpret_cast<const int32_t*>(p->d_host + HostLayout(p->n).desc);
+    if (cudaMemcpyAsync(&d, d_desc + e, sizeof(d), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess ||
+        cudaStreamSynchronize(p->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    return desc_bucket(d) == -2 ? LUDAX_ERR_SIZE : LUDAX_ERR_GAME;
+}
+
 int ludax_mixed_plan_destroy(ludax_mixed_plan* p) {
     if (!p) return LUDAX_OK;
     cudaStreamSynchronize(p->stream);
@@ -458,6 +635,8 @@ int ludax_mixed_plan_destroy(ludax_mixed_plan* p) {
     if (p->graph) cudaGraphDestroy(p->graph);
     cudaFree(p->d_queue);
     cudaFree(p->d_cursor);
+    cudaFree(p->d_host);
+    if (p->h_bad) cudaFreeHost(p->h_bad);
     delete p;
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }

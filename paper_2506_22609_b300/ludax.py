@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
         "ludax_mixed_plan_create": [P(vp), vp, i64, i64, P(ludax_launch_cfg), vp, P(i64)],
         "ludax_rollout_mixed_noalloc": [vp, i64, i64, u64, vp, vp, P(ludax_launch_cfg), vp, P(i64)],
         "ludax_mixed_plan_launch": [vp, u64, vp, vp],
+        "ludax_mixed_plan_launch_host": [vp, u64, vp, vp, vp],
+        "ludax_mixed_plan_sync": [vp, P(i64)],
         "ludax_mixed_plan_destroy": [vp],
         "ludax_autotune": [vp, i64, u64, i32, vp, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
         "ludax_autotune_env": [vp, u64, i32, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
@@ -356,6 +358,26 @@ def ludax_mixed_plan_create(desc, env_offset: int = 0, cfg=None, stream=None):
 
 def ludax_mixed_plan_launch(plan, seed: int, outcome, plies):
     _check(lib().ludax_mixed_plan_launch(plan, seed, _ptr(outcome), _ptr(plies)), "ludax_mixed_plan_launch")
+
+
+def ludax_mixed_plan_launch_host(plan, seed: int, desc_host, outcome_host, plies_host):
+    """Host tensors (pinned for asynchronous copies): desc int32 [n] in,
+    outcome int8 [n] and plies int16 [n] out, valid once the plan's stream
+    has reached this call (ludax_mixed_plan_sync)."""
+    for t in (desc_host, outcome_host, plies_host):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("ludax_mixed_plan_launch_host takes contiguous host tensors")
+    _check(lib().ludax_mixed_plan_launch_host(plan, seed, desc_host.data_ptr(), outcome_host.data_ptr(),
+                                              plies_host.data_ptr()), "ludax_mixed_plan_launch_host")
+
+
+def ludax_mixed_plan_sync(plan):
+    bad = ctypes.c_int64(-1)
+    st = lib().ludax_mixed_plan_sync(plan, ctypes.byref(bad))
+    if st != 0:
+        err = LudaxError(st, f"ludax_mixed_plan_sync (first bad descriptor index {bad.value})")
+        err.bad_index = bad.value
+        raise err
 
 
 def ludax_mixed_plan_destroy(plan):

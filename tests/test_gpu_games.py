@@ -345,6 +345,47 @@ def test_mixed_full_config_sampled(L):
     L.ludax_mixed_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("cfg", [(128, 0, 1, 1, 0), (128, 2, 1, 1, 0)])
+def test_mixed_host_buffers_match_oracle(L, cfg):
+    # the plan's host-buffer launch: descriptors uploaded, queue rebuilt on the
+    # device, results copied back; any batch of the plan's size, including ones
+    # the plan was not built from, and invalid descriptors reported by sync
+    n, off = 3001, 55
+    d0 = W.mixed_descriptors(n, "block")
+    plan = L.ludax_mixed_plan_create(torch.from_numpy(d0).cuda(), off, L.make_cfg(*cfg))
+    h_out = torch.empty(n, dtype=torch.int8).pin_memory()
+    h_plies = torch.empty(n, dtype=torch.int16).pin_memory()
+    for k, (d, seed) in enumerate(((W.random_descriptors(n, 5), 3), (W.mixed_descriptors(n, "interleave"), 4),
+                                   (d0, 5))):
+        h_desc = torch.from_numpy(d).pin_memory()
+        L.ludax_mixed_plan_launch_host(plan, seed, h_desc, h_out, h_plies)
+        L.ludax_mixed_plan_sync(plan)
+        o, p = G.rollout_mixed(d, seed, env_offset=off)
+        assert (h_out.numpy() == o).all() and (h_plies.numpy() == p).all(), k
+    # the captured graph keeps its own queue
+    out = torch.empty(n, dtype=torch.int8, device="cuda")
+    plies = torch.empty(n, dtype=torch.int16, device="cuda")
+    L.ludax_mixed_plan_launch(plan, 5, out, plies)
+    torch.cuda.synchronize()
+    assert (np_(out) == h_out.numpy()).all() and (np_(plies) == h_plies.numpy()).all()
+    bad = W.mixed_descriptors(n, "interleave")
+    bad[2500], bad[1999] = W.desc(3, 12, 12), W.desc(11, 3, 3)
+    L.ludax_mixed_plan_launch_host(plan, 6, torch.from_numpy(bad).pin_memory(), h_out, h_plies)
+    with pytest.raises(L.LudaxError) as ei:
+        L.ludax_mixed_plan_sync(plan)
+    assert ei.value.status == -2 and ei.value.bad_index == 1999
+    good = np.ones(n, bool)
+    good[[1999, 2500]] = False
+    # the valid envs are played as usual (their draws are keyed by their own index)
+    idx = np.nonzero(good)[0]
+    for j in W.sample_envs(len(idx), 200, 3):
+        e = int(idx[j])
+        oe, pe = G.rollout_mixed(bad[e:e + 1], 6, env_offset=off + e)
+        assert h_out.numpy()[e] == oe[0] and h_plies.numpy()[e] == pe[0]
+    assert h_out.numpy()[1999] == -1 and h_plies.numpy()[2500] == 0
+    L.ludax_mixed_plan_destroy(plan)
+
+
 def test_mixed_rejects_bad_descriptors(L):
     d = W.mixed_descriptors(100, "block")
     d[37] = W.desc(3, 12, 12)
