@@ -65,10 +65,11 @@ GAME_KEYS = {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente",
 # DRAM bytes per launch of the benchmarked kernel, from the committed ncu
 # captures (profiles/); None once the kernel changes until it is captured again.
 NCU_TRAFFIC_BYTES = {"connect4_6x7_65536env_seed1": 13568,
-                     "connect4_6x7_16777216env_random_step_seed1": 335567360 + 426561280}
-# thread instructions ncu counts executed per env step (smsp__thread_inst_executed.sum
-# / plies of the launch), from the same captures; None until re-captured
-NCU_THREAD_INST_PER_STEP = {}
+                     "connect4_6x7_16777216env_random_step_seed1": 335567360 + 426561280,
+                     "mixed6_1048576env_seed3_graph": 4276480}
+# thread instructions ncu counts executed per env step (warp instructions x
+# active lanes per instruction / plies of the launch), from the same captures
+NCU_THREAD_INST_PER_STEP = {"mixed6_1048576env_seed3_graph": round(725478758 * 24.41 / 54553274, 1)}
 
 
 def parse():
@@ -675,24 +676,41 @@ def bench_train_step(L, peaks, flush_buf, steps=20, warmup=3, B=65536):
     return out
 
 
-def bench_valuenet():
-    """The learned part: 2M training positions per game, 100k held-out
-    positions; value estimates/s of the truncated estimator (8 random plies,
-    then the net) and of full playouts at MAE <= 0.05 against a 256-playout
-    reference."""
+def bench_valuenet(seeds=(5, 6, 7)):
+    """The learned part: 2M training positions per game, 65,536 validation
+    positions (which choose the epoch, K and M) and 100k held-out positions
+    (evaluated once); value estimates/s of the truncated estimator (8 random
+    plies, then the net) and of full playouts at MAE <= 0.05 against a
+    256-playout reference, over several seeds (mean and sd of each seed's
+    held-out numbers)."""
     from paper_2506_22609_b300 import valuenet as V
+
+    def spread(xs):
+        return {"mean": round(statistics.mean(xs), 5), "sd": round(statistics.stdev(xs), 5) if len(xs) > 1 else 0.0,
+                "values": [round(x, 5) for x in xs]}
 
     out = {}
     for game in ("othello", "hex11"):
-        r = V.run(game)
-        ev = r["eval"]
-        out[game] = {"truncated_at_target": ev["truncated_at_target"], "full_at_target": ev["full_at_target"],
-                     "gain_estimates_per_s": ev.get("gain_estimates_per_s"), "net_only_mae": ev["net_only_mae"],
-                     "reference_noise_mae": ev["reference_noise_mae"], "target_mae": ev["target_mae"],
-                     "final_val_mae": r["history"][-1]["val_mae"], "train_seconds": round(r["train_seconds"], 3),
-                     "train_steps": r["train_steps"], "data_seconds": round(r["data_seconds"], 3),
-                     "n_train": r["n_train"], "n_eval": r["n_eval"], "inference_rows": ev["inference_rows"],
-                     "all_truncated": ev["truncated"], "all_full": ev["full_playouts"]}
+        runs = [V.run(game, seed=sd) for sd in seeds]
+        ev = [r["eval"] for r in runs]
+        out[game] = {
+            "seeds": list(seeds),
+            "selected_K": [r["validation"]["K"] for r in runs], "selected_M": [r["validation"]["M"] for r in runs],
+            "epoch_kept": [r["epoch_kept"] for r in runs],
+            "truncated_mae": spread([e["truncated_selected"]["mae"] for e in ev]),
+            "truncated_estimates_per_s": spread([e["truncated_selected"]["estimates_per_s"] for e in ev]),
+            "full_mae": spread([e["full_selected"]["mae"] for e in ev]),
+            "full_estimates_per_s": spread([e["full_selected"]["estimates_per_s"] for e in ev]),
+            "gain_estimates_per_s": spread([e["gain_estimates_per_s"] for e in ev]),
+            "equal_mae": ev[0]["equal_mae"], "equal_time": ev[0]["equal_time"],
+            "net_only_mae": spread([e["net_only_mae"] for e in ev]),
+            "reference_noise_mae": round(ev[0]["reference_noise_mae"], 5), "target_mae": ev[0]["target_mae"],
+            "validation_truncated": runs[0]["validation"]["truncated"],
+            "all_truncated": ev[0]["truncated"], "all_full": ev[0]["full_playouts"],
+            "train_seconds": [round(r["train_seconds"], 3) for r in runs],
+            "train_steps": [r["train_steps"] for r in runs], "data_seconds": round(runs[0]["data_seconds"], 3),
+            "n_train": runs[0]["n_train"], "n_val": runs[0]["n_val"], "n_eval": runs[0]["n_eval"],
+            "inference_rows": ev[0]["inference_rows"]}
     return out
 
 
