@@ -1,6 +1,6 @@
 """Learned value estimates: data, training and evaluation of the value net.
 
-    python -m paper_2506_22609_b300.valuenet --game othello [--n-train 2000000] [--epochs 30]
+    python -m paper_2506_22609_b300.valuenet --game othello [--n-train 2000000] [--epochs 100]
 
 Pipeline (every compute step is a libludax kernel; this module only moves
 handles, sizes and seeds around):
@@ -10,12 +10,19 @@ handles, sizes and seeds around):
   2. labels: the fraction of 64 uniform-random playouts from the position
      that P1 wins, draws counting one half (ludax_rollout_value);
   3. training: batches of 65,536 positions, Adam at lr 1e-3
-     (ludax_net_train_step), the batch order shuffled each epoch;
-  4. evaluation on held-out positions against a 256-playout reference
-     estimate: the truncated estimator (K continuations of 8 random plies,
-     then the net: ludax_truncated_value) and the full-playout estimator with
-     M playouts (ludax_rollout_value), each as mean absolute error and
-     estimates per second.
+     (ludax_net_train_step), the batch order shuffled each epoch, for up to
+     max_epochs epochs; the epoch kept is the one whose net is closest (mean
+     absolute error) to a 256-playout reference of the VALIDATION positions;
+  4. selection on the validation positions, never on the held-out ones: the
+     smallest number K of truncated continuations (8 random plies, then the
+     net: ludax_truncated_value) and the smallest number M of full playouts
+     (ludax_rollout_value) whose mean absolute error against the validation
+     reference is at most the target;
+  5. evaluation, once, on held-out positions against their own 256-playout
+     reference: every K and M (mean absolute error and estimates per second),
+     the selected K and M, and the comparison at an equal time budget (the
+     full-playout estimator with the largest M that fits in the selected
+     truncated estimator's time).
 """
 from __future__ import annotations
 
@@ -86,28 +93,41 @@ def cuda_time_median(fn, warmup=2, reps=5):
     return out, float(np.median(times))
 
 
-def train(net, x, y, batch, epochs, lr, seed, x_val=None, y_val=None, log=None):
+def train(net, x, y, batch, epochs, lr, seed, x_val=None, y_val=None, log=None, keep_best=False):
+    """Adam over shuffled batches; with x_val, each epoch's validation MAE
+    is recorded, and with keep_best the parameters of the epoch with the
+    smallest one are restored at the end.  Returns (history, seconds of
+    training steps, steps, the epoch kept)."""
     n = x.shape[0]
     nb = n // batch
     rng = np.random.default_rng(seed)
     hist = []
-    t0 = time.perf_counter()
+    t_train = 0.0
     steps = 0
+    best, best_ep, best_params = float("inf"), epochs, None
     for ep in range(epochs):
         losses = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         for b in rng.permutation(nb):
             loss = net.train_step(x[b * batch:(b + 1) * batch], y[b * batch:(b + 1) * batch], lr)
             losses.append(loss)
             steps += 1
+        torch.cuda.synchronize()
+        t_train += time.perf_counter() - t0
         rec = {"epoch": ep + 1, "train_loss": float(torch.stack(losses).mean().item())}
         if x_val is not None:
             p = predict(net, x_val)
             rec["val_mae"] = float((p - y_val).abs().mean().item())
+            if keep_best and rec["val_mae"] < best:
+                best, best_ep, best_params = rec["val_mae"], ep + 1, net.get_params()
         hist.append(rec)
         if log:
             log(rec)
+    if keep_best and best_params is not None:
+        net.set_params(best_params)
     torch.cuda.synchronize()
-    return hist, time.perf_counter() - t0, steps
+    return hist, t_train, steps, best_ep
 
 
 def predict(net, x):
@@ -134,20 +154,41 @@ def inference_net(net, rows):
     return big, True
 
 
-def evaluate(env, net, ref, seed, Ms=(4, 8, 16, 32, 64, 128), Ks=(1, 2, 4, 8, 16), plies=8, target=0.05):
+def estimator_table(env, net, ref, seed, Ms, Ks, plies, timed=True):
+    """MAE against ref (and estimates/s) of full playouts for every M and of
+    the truncated estimator for every K on the positions of env."""
     n = env.num_envs
-    res = {"full_playouts": [], "truncated": []}
-    net, owned = inference_net(net, n * max(Ks))
+    full, trunc = [], []
     for M in Ms:
-        v, dt = cuda_time_median(lambda: env.rollout_value(seed + 100000 * M, M))
-        res["full_playouts"].append({"M": M, "mae": float((v - ref).abs().mean().item()),
-                                     "estimates_per_s": n / dt, "seconds": dt})
+        fn = lambda: env.rollout_value(seed + 100000 * M, M)  # noqa: E731
+        v, dt = cuda_time_median(fn) if timed else (fn(), None)
+        full.append({"M": M, "mae": float((v - ref).abs().mean().item()),
+                     "estimates_per_s": n / dt if dt else None, "seconds": dt})
     for K in Ks:
         val = torch.empty(n, dtype=torch.float32, device="cuda")
-        _, dt = cuda_time_median(lambda: L.ludax_truncated_value(env.handle, net.handle, seed + 7777 + 1000 * K, K,
-                                                                 plies, val))
-        res["truncated"].append({"K": K, "plies": plies, "mae": float((val - ref).abs().mean().item()),
-                                 "estimates_per_s": n / dt, "seconds": dt})
+        fn = lambda: L.ludax_truncated_value(env.handle, net.handle, seed + 7777 + 1000 * K, K, plies, val)  # noqa: E731
+        _, dt = cuda_time_median(fn) if timed else (fn(), None)
+        trunc.append({"K": K, "plies": plies, "mae": float((val - ref).abs().mean().item()),
+                      "estimates_per_s": n / dt if dt else None, "seconds": dt})
+    return full, trunc
+
+
+def first_at(rows, target):
+    ok = [x for x in rows if x["mae"] <= target]
+    return ok[0] if ok else rows[-1]
+
+
+def evaluate(env, net, ref, seed, Ms=(1, 2, 4, 8, 16, 32, 64, 128), Ks=(1, 2, 4, 8, 16), plies=8, target=0.05,
+             K_sel=None, M_sel=None, M_eq=None):
+    """The held-out evaluation: every estimator's MAE against the reference
+    and its speed; K_sel / M_sel are the counts chosen on the validation
+    positions for the target, M_eq the full-playout count that matched the
+    selected truncated estimator's validation MAE (this function never
+    chooses a count from its own errors)."""
+    n = env.num_envs
+    net, owned = inference_net(net, n * max(Ks))
+    full, trunc = estimator_table(env, net, ref, seed, Ms, Ks, plies)
+    res = {"full_playouts": full, "truncated": trunc}
     pnet = predict(net, pack(env, net.in_pad))
     res["net_only_mae"] = float((pnet - ref).abs().mean().item())
     res["inference_rows"] = net.max_batch
@@ -156,18 +197,29 @@ def evaluate(env, net, ref, seed, Ms=(4, 8, 16, 32, 64, 128), Ks=(1, 2, 4, 8, 16
     # noise of the reference itself: sd of a 256-sample mean, as an expected absolute value
     r = ref.double()
     res["reference_noise_mae"] = float((torch.sqrt(r * (1 - r) / 256) * (2 / np.pi) ** 0.5).mean().item())
-    ok_m = [x for x in res["full_playouts"] if x["mae"] <= target]
-    ok_k = [x for x in res["truncated"] if x["mae"] <= target]
     res["target_mae"] = target
-    res["full_at_target"] = ok_m[0] if ok_m else None
-    res["truncated_at_target"] = ok_k[0] if ok_k else None
-    if ok_m and ok_k:
-        res["gain_estimates_per_s"] = ok_k[0]["estimates_per_s"] / ok_m[0]["estimates_per_s"]
+    if K_sel is not None:
+        t = next(x for x in trunc if x["K"] == K_sel)
+        f = next(x for x in full if x["M"] == M_sel)
+        res["truncated_selected"], res["full_selected"] = t, f
+        res["gain_estimates_per_s"] = t["estimates_per_s"] / f["estimates_per_s"]
+        if M_eq is not None:
+            fe = next(x for x in full if x["M"] == M_eq)
+            res["equal_mae"] = {"truncated_K": K_sel, "truncated_mae": t["mae"],
+                                "truncated_estimates_per_s": t["estimates_per_s"], "full_M": M_eq,
+                                "full_mae": fe["mae"], "full_estimates_per_s": fe["estimates_per_s"],
+                                "gain": t["estimates_per_s"] / fe["estimates_per_s"]}
+        # equal time budget: the most full playouts per position that fit in the truncated estimator's time
+        fit = [x for x in full if x["seconds"] <= t["seconds"]]
+        res["equal_time"] = {"truncated_K": K_sel, "truncated_mae": t["mae"], "seconds": t["seconds"],
+                             "full_M": fit[-1]["M"] if fit else 0,
+                             "full_mae": fit[-1]["mae"] if fit else float((0.5 - ref).abs().mean().item())}
     return res
 
 
-def run(game="othello", n_train=2_000_000, n_val=65_536, n_eval=100_000, batch=65_536, epochs=30, lr=1e-3,
-        label_R=64, ref_R=256, seed=5, log=None):
+def run(game="othello", n_train=2_000_000, n_val=65_536, n_eval=100_000, batch=65_536, epochs=100, lr=1e-3,
+        label_R=64, ref_R=256, seed=5, target=0.05, Ks=(1, 2, 4, 8, 16), Ms=(1, 2, 4, 8, 16, 32, 64, 128),
+        log=None):
     g, rows, cols = GAMES[game]
     cells = rows * cols
     torch.cuda.synchronize()
@@ -176,7 +228,7 @@ def run(game="othello", n_train=2_000_000, n_val=65_536, n_eval=100_000, batch=6
     env_va, off = sample_positions(g, rows, cols, n_val, seed + 1, off)
     env_ev, off = sample_positions(g, rows, cols, n_eval, seed + 2, off)
     y_tr, t_lab = cuda_time(lambda: env_tr.rollout_value(seed * 7919 + 1, label_R))
-    y_va = env_va.rollout_value(seed * 7919 + 2, label_R)
+    ref_va = env_va.rollout_value(seed * 7919 + 2, ref_R)
     ref = env_ev.rollout_value(seed * 7919 + 3, ref_R)
     in_pad = W.net_in_pad(cells)
     x_tr, x_va = pack(env_tr, in_pad), pack(env_va, in_pad)
@@ -184,13 +236,24 @@ def run(game="othello", n_train=2_000_000, n_val=65_536, n_eval=100_000, batch=6
     t_data = time.perf_counter() - t0
     net = L.Net(cells, batch)
     net.set_params(torch.from_numpy(W.init_params(cells, seed)).cuda())
-    untrained_val_mae = float((predict(net, x_va) - y_va).abs().mean().item())
-    hist, t_train, steps = train(net, x_tr, y_tr, batch, epochs, lr, seed, x_va, y_va, log)
-    ev = evaluate(env_ev, net, ref, seed * 31 + 17)
+    untrained_val_mae = float((predict(net, x_va) - ref_va).abs().mean().item())
+    hist, t_train, steps, kept = train(net, x_tr, y_tr, batch, epochs, lr, seed, x_va, ref_va, log, keep_best=True)
+    # K and M chosen on the validation positions against their own reference
+    vnet, owned = inference_net(net, n_val * max(Ks))
+    vfull, vtrunc = estimator_table(env_va, vnet, ref_va, seed * 31 + 5, Ms, Ks, 8, timed=False)
+    if owned:
+        vnet.close()
+    t_sel = first_at(vtrunc, target)
+    K_sel, M_sel = t_sel["K"], first_at(vfull, target)["M"]
+    M_eq = first_at(vfull, t_sel["mae"])["M"]  # full playouts as accurate as the selected truncated estimator
+    ev = evaluate(env_ev, net, ref, seed * 31 + 17, Ms=Ms, Ks=Ks, target=target, K_sel=K_sel, M_sel=M_sel,
+                  M_eq=M_eq)
     out = {"game": game, "n_train": n_train, "n_val": n_val, "n_eval": n_eval, "batch": batch, "epochs": epochs,
-           "lr": lr, "label_playouts": label_R, "reference_playouts": ref_R, "data_seconds": t_data,
-           "label_playouts_per_s": n_train * label_R / t_lab, "train_seconds": t_train, "train_steps": steps,
-           "untrained_val_mae": untrained_val_mae, "history": hist, "eval": ev}
+           "epoch_kept": kept, "lr": lr, "label_playouts": label_R, "reference_playouts": ref_R,
+           "data_seconds": t_data, "label_playouts_per_s": n_train * label_R / t_lab, "train_seconds": t_train,
+           "train_steps": steps, "untrained_val_mae": untrained_val_mae, "history": hist,
+           "validation": {"truncated": vtrunc, "full_playouts": vfull, "K": K_sel, "M": M_sel, "M_equal_mae": M_eq},
+           "eval": ev}
     for e in (env_tr, env_va, env_ev):
         e.close()
     net.close()
@@ -202,7 +265,7 @@ def main():
     ap.add_argument("--game", default="othello", choices=sorted(GAMES))
     ap.add_argument("--n-train", type=int, default=2_000_000)
     ap.add_argument("--n-eval", type=int, default=100_000)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=100)
     ap.add_argument("--seed", type=int, default=5)
     a = ap.parse_args()
     res = run(a.game, n_train=a.n_train, n_eval=a.n_eval, epochs=a.epochs, seed=a.seed,
