@@ -150,6 +150,12 @@ typedef struct {
                                 its unfinished envs into its lowest warps through shared
                                 memory (idle warps stop issuing) and refills the freed
                                 slots from the queue; needs envs_per_thread 1         */
+    int32_t threads_per_env; /* lanes cooperating on one env: 0 or 1 = one lane per env
+                                (every game and path); 2 or 4 = Hex single-game
+                                ludax_rollout only (the board's four 32-bit words split
+                                across the lanes, draws and end tests shared by warp
+                                shuffles; same results bit for bit); needs
+                                envs_per_thread 1 and compact_every 0                 */
 } ludax_launch_cfg;
 
 /* ---------------------------------------------------------------------------
@@ -394,10 +400,15 @@ int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out);
 
 /* Autotuner for ludax_rollout on one env batch (from the start position, no
  * write-back; the env's stored state is not touched): walks block_threads x
- * blocks_per_sm x envs_per_thread (x hex_nbr_table for Hex), timing each
- * like ludax_autotune.  ms_table_out (nullable) needs room for 512 floats. */
+ * blocks_per_sm x envs_per_thread x compact_every, and for Hex also
+ * hex_nbr_table and threads_per_env 2 and 4 (the candidates of
+ * ludax_autotune_env_candidates, in that order), timing each like
+ * ludax_autotune.  ms_table_out (nullable) needs room for 512 floats.      */
 int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
                        float* ms_table_out, int32_t* n_candidates_out);
+/* The candidate list ludax_autotune_env walks for this env's game (host
+ * memory, at most max_out written, the full count returned).              */
+int ludax_autotune_env_candidates(const ludax_env* env, ludax_launch_cfg* out, int32_t max_out);
 
 /* ---------------------------------------------------------------------------
  * Value network that truncates playouts (the learned part built on the

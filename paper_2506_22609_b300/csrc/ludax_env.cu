@@ -13,6 +13,7 @@
 #include <thread>
 
 #include "../../include/ludax.h"
+#include "ludax_hex_lanes.cuh"
 #include "ludax_internal.cuh"
 
 using namespace ludax;
@@ -560,8 +561,141 @@ __global__ void __launch_bounds__(512) rollout_value_kernel(EnvDev d, uint64_t s
     value[e] = R > 0 ? acc / (float)R : 0.f;
 }
 
+// Hex with TPE lanes per env (threads_per_env 2 or 4): a group of TPE
+// consecutive lanes plays one env (HexLanes: the board's words split across
+// the lanes) and takes the next unclaimed env when its game ends.  Work index
+// w < n maps to env w, as in rollout_kernel.
+template <int N, int TPE>
+__device__ __forceinline__ void load_lanes(HexLanes<N, TPE>& g, const EnvDev& d, int64_t e) {
+    int passes;
+    unpack_meta(d.meta[e], g.ply, passes, g.side, g.outcome);
+    const uint64_t* P = d.planes;
+    const int64_t n = d.n;
+    const bool p1 = g.side == 0;
+    uint32_t s1[HexLanes<N, TPE>::WPL], s2[HexLanes<N, TPE>::WPL], a1[HexLanes<N, TPE>::WPL],
+        b1[HexLanes<N, TPE>::WPL], a2[HexLanes<N, TPE>::WPL], b2[HexLanes<N, TPE>::WPL];
+    g.words_of(P[0 * n + e], P[1 * n + e], s1);
+    g.words_of(P[2 * n + e], P[3 * n + e], s2);
+    g.words_of(P[4 * n + e], P[5 * n + e], a1);
+    g.words_of(P[6 * n + e], P[7 * n + e], b1);
+    g.words_of(P[8 * n + e], P[9 * n + e], a2);
+    g.words_of(P[10 * n + e], P[11 * n + e], b2);
+#pragma unroll
+    for (int j = 0; j < HexLanes<N, TPE>::WPL; ++j) {
+        g.own[j] = p1 ? s1[j] : s2[j];
+        g.opp[j] = p1 ? s2[j] : s1[j];
+        g.ownA[j] = p1 ? a1[j] : a2[j];
+        g.ownB[j] = p1 ? b1[j] : b2[j];
+        g.oppA[j] = p1 ? a2[j] : a1[j];
+        g.oppB[j] = p1 ? b2[j] : b1[j];
+        g.front[j] = 0u;
+    }
+}
+template <int N, int TPE>
+__device__ __forceinline__ void store_lanes(const HexLanes<N, TPE>& g, const EnvDev& d, int64_t e) {
+    const bool p1 = g.side == 0;
+    uint64_t w[12];
+    w[0] = g.plane_word(p1 ? g.own : g.opp, 0);
+    w[1] = g.plane_word(p1 ? g.own : g.opp, 1);
+    w[2] = g.plane_word(p1 ? g.opp : g.own, 0);
+    w[3] = g.plane_word(p1 ? g.opp : g.own, 1);
+    w[4] = g.plane_word(p1 ? g.ownA : g.oppA, 0);
+    w[5] = g.plane_word(p1 ? g.ownA : g.oppA, 1);
+    w[6] = g.plane_word(p1 ? g.ownB : g.oppB, 0);
+    w[7] = g.plane_word(p1 ? g.ownB : g.oppB, 1);
+    w[8] = g.plane_word(p1 ? g.oppA : g.ownA, 0);
+    w[9] = g.plane_word(p1 ? g.oppA : g.ownA, 1);
+    w[10] = g.plane_word(p1 ? g.oppB : g.ownB, 0);
+    w[11] = g.plane_word(p1 ? g.oppB : g.ownB, 1);
+    if (g.r == 0) {
+        d.meta[e] = pack_meta(g.ply, 0, g.side, g.outcome, 0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) d.planes[(int64_t)k * d.n + e] = w[k];
+    }
+}
+
+template <int N, int TPE, bool TABLE>
+__global__ void __launch_bounds__(512) rollout_lanes_kernel(RolloutArgs a) {
+    __shared__ uint32_t table[TABLE ? N * N * 4 : 1];
+    if constexpr (TABLE) {
+        for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+            const B128 m = Hex<N>::nbrs(bit128(i));
+            table[4 * i + 0] = (uint32_t)m.lo;
+            table[4 * i + 1] = (uint32_t)(m.lo >> 32);
+            table[4 * i + 2] = (uint32_t)m.hi;
+            table[4 * i + 3] = (uint32_t)(m.hi >> 32);
+        }
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, r = lane % TPE;
+    const unsigned gmask = ((1u << TPE) - 1u) << (lane - r);
+    const int64_t n = a.d.n;
+    const int64_t groups = (int64_t)gridDim.x * blockDim.x / TPE;
+    const bool refill = groups < n;
+    HexLanes<N, TPE> g;
+    g.init_lane(r, gmask, TABLE ? table : nullptr);
+    int64_t env = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / TPE;
+    bool active = env < n;
+    uint64_t key = 0;
+    uint32_t rhi = 0;
+    int stop = 0;
+    auto init = [&]() {
+        if (a.from_start) g.reset();
+        else load_lanes(g, a.d, env);
+        key = env_key(a.seed_key, (uint64_t)(a.d.env_offset + env));
+        rhi = draw_hi(key, (uint32_t)g.ply);
+        stop = a.stop ? (int)a.stop[env] : 0x7FFF;
+    };
+    if (active) init();
+    while (active) {  // uniform within a group
+        if (g.outcome == kOngoing && g.ply < stop) {
+            g.step(key, rhi);
+            continue;
+        }
+        if (a.write_back) {
+            g.settle();
+            store_lanes(g, a.d, env);
+        }
+        if (r == 0) {
+            if (a.outcome) a.outcome[env] = (int8_t)g.outcome;
+            if (a.plies) a.plies[env] = (int16_t)g.ply;
+            if (g.outcome == kCapped) atomicAdd(&a.d.counters[2], 1ull);
+        }
+        if (!refill) break;
+        long long next = 0;
+        if (r == 0) next = (long long)atomicAdd(&a.d.counters[0], 1ull);
+        next = __shfl_sync(gmask, next, lane - r);
+        env = groups + next;
+        active = env < n;
+        if (active) init();
+    }
+}
+
+template <int N>
+int launch_lanes(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& cfg) {
+    const int block = cfg.block_threads, tpe = cfg.threads_per_env;
+    const int64_t per_block = block / tpe;
+    int64_t grid = (env->n + per_block - 1) / per_block;
+    if (cfg.blocks_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)env->num_sms * cfg.blocks_per_sm);
+    if (grid * per_block < env->n &&
+        cudaMemsetAsync(env->d_counters, 0, sizeof(unsigned long long), env->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    const unsigned gd = (unsigned)grid;
+    if (tpe == 2) {
+        if (cfg.hex_nbr_table) rollout_lanes_kernel<N, 2, true><<<gd, block, 0, env->stream>>>(a);
+        else rollout_lanes_kernel<N, 2, false><<<gd, block, 0, env->stream>>>(a);
+    } else {
+        if (cfg.hex_nbr_table) rollout_lanes_kernel<N, 4, true><<<gd, block, 0, env->stream>>>(a);
+        else rollout_lanes_kernel<N, 4, false><<<gd, block, 0, env->stream>>>(a);
+    }
+    return launch_status();
+}
+
 template <class G, bool BITS>
 int launch_rollout_as(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& cfg) {
+    if constexpr (HexN<G>::value != 0 && !BITS) {
+        if (cfg.threads_per_env > 1) return launch_lanes<HexN<G>::value>(env, a, cfg);
+    }
     const int block = cfg.block_threads;
     const int ept = BITS ? 1 : cfg.envs_per_thread;  // the packed-view path has one env per thread
     int64_t need = (env->n + (int64_t)block * ept - 1) / ((int64_t)block * ept);
@@ -615,6 +749,8 @@ int check_cfg(const ludax_launch_cfg& c) {
     if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
     if (c.compact_every < 0 || c.compact_every > 256) return LUDAX_ERR_ARG;
     if (c.compact_every > 0 && c.envs_per_thread != 1) return LUDAX_ERR_ARG;
+    if (c.threads_per_env < 0 || c.threads_per_env == 3 || c.threads_per_env > 4) return LUDAX_ERR_ARG;
+    if (c.threads_per_env > 1 && (c.envs_per_thread != 1 || c.compact_every != 0)) return LUDAX_ERR_ARG;
     return LUDAX_OK;
 }
 
@@ -781,6 +917,8 @@ static int rollout_impl(ludax_env* env, uint64_t seed, uint32_t flags, const int
     ludax_launch_cfg c = cfg ? *cfg : default_cfg();
     int st = check_cfg(c);
     if (st != LUDAX_OK) return st;
+    // several lanes per env: Hex playouts from the env's own or start state only
+    if (c.threads_per_env > 1 && (env->game != LUDAX_GAME_HEX || bits)) return LUDAX_ERR_ARG;
     RolloutArgs a;
     a.d = dev_of(env);
     a.seed_key = splitmix64(seed);
@@ -873,6 +1011,7 @@ int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_d
     ludax_launch_cfg c = cfg ? *cfg : default_cfg();
     int st = check_cfg(c);
     if (st != LUDAX_OK) return st;
+    if (c.threads_per_env > 1) return LUDAX_ERR_ARG;  // one lane per env here
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         const bool table = c.hex_nbr_table != 0 && HexN<G>::value != 0;
@@ -966,17 +1105,50 @@ int ludax_sync(ludax_env* env, int64_t timeout_ms) {
     }
 }
 
+int ludax_autotune_env_candidates(const ludax_env* env, ludax_launch_cfg* out, int32_t max_out) {
+    if (!env) return LUDAX_ERR_ARG;
+    static const int blocks[] = {64, 128, 192, 256, 384, 448, 512};
+    static const int bps[] = {0, 2, 4, 8, 16};
+    static const int compacts[] = {0, 4, 8, 16};
+    const bool hex = env->game == LUDAX_GAME_HEX;
+    int k = 0;
+    auto put = [&](ludax_launch_cfg c) {
+        if (out && k < max_out) out[k] = c;
+        ++k;
+    };
+    for (int t = 0; t < (hex ? 2 : 1); ++t) {
+        for (int ce : compacts)
+            for (int ept = 1; ept <= 2; ++ept)
+                for (int b : blocks)
+                    for (int s : bps) {
+                        if (s > 0 && b * s > 2048) continue;
+                        if (ce > 0 && ept != 1) continue;
+                        put(ludax_launch_cfg{b, s, ept, t, ce, 1});
+                    }
+        if (hex)  // several lanes per env
+            for (int tpe : {2, 4})
+                for (int b : blocks)
+                    for (int s : bps) {
+                        if (s > 0 && b * s > 2048) continue;
+                        put(ludax_launch_cfg{b, s, 1, t, 0, tpe});
+                    }
+    }
+    return k;
+}
+
 int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
                        float* ms_table_out, int32_t* n_candidates_out) {
     if (!env || !best_out || reps < 1) return LUDAX_ERR_ARG;
-    static const int blocks[] = {64, 128, 192, 256, 384, 448, 512};
-    static const int bps[] = {0, 2, 4, 8, 16};
-    const int tables = env->game == LUDAX_GAME_HEX ? 2 : 1;
+    const int nc = ludax_autotune_env_candidates(env, nullptr, 0);
+    ludax_launch_cfg* cands = new (std::nothrow) ludax_launch_cfg[(size_t)nc];
+    if (!cands) return LUDAX_ERR_NOMEM;
+    ludax_autotune_env_candidates(env, cands, nc);
     int8_t* d_out = nullptr;
     int16_t* d_plies = nullptr;
     if (cudaMalloc(&d_out, env->n) != cudaSuccess || cudaMalloc(&d_plies, 2 * env->n) != cudaSuccess) {
         cudaFree(d_out);
         cudaGetLastError();
+        delete[] cands;
         return LUDAX_ERR_NOMEM;
     }
     cudaEvent_t e0, e1;
@@ -984,40 +1156,33 @@ int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch
     cudaEventCreate(&e1);
     int st = LUDAX_OK, k = 0;
     float best = 1e30f;
-    static const int compacts[] = {0, 4, 8, 16};
-    for (int t = 0; t < tables && st == LUDAX_OK; ++t)
-        for (int ce : compacts)
-        for (int ept = 1; ept <= 2 && st == LUDAX_OK; ++ept)
-            for (int b : blocks)
-                for (int s : bps) {
-                    if (st != LUDAX_OK) break;
-                    if (s > 0 && b * s > 2048) continue;
-                    if (ce > 0 && ept != 1) continue;
-                    ludax_launch_cfg c{b, s, ept, t, ce};
-                    float ts[64];
-                    int nt = 0;
-                    for (int r = 0; r < reps + 2 && st == LUDAX_OK; ++r) {
-                        cudaEventRecord(e0, env->stream);
-                        st = ludax_rollout(env, seed + (uint64_t)r, LUDAX_ROLLOUT_FROM_START, nullptr, d_out, d_plies, &c);
-                        cudaEventRecord(e1, env->stream);
-                        if (cudaEventSynchronize(e1) != cudaSuccess) st = LUDAX_ERR_CUDA;
-                        float ms = 0;
-                        cudaEventElapsedTime(&ms, e0, e1);
-                        if (r >= 2 && nt < 64) ts[nt++] = ms;
-                    }
-                    if (st != LUDAX_OK) break;
-                    for (int i = 1; i < nt; ++i)
-                        for (int j = i; j > 0 && ts[j] < ts[j - 1]; --j) {
-                            float x = ts[j]; ts[j] = ts[j - 1]; ts[j - 1] = x;
-                        }
-                    float med = ts[nt / 2];
-                    if (ms_table_out && k < 512) ms_table_out[k] = med;
-                    ++k;
-                    if (med < best) {
-                        best = med;
-                        *best_out = c;
-                    }
-                }
+    for (int i = 0; i < nc && st == LUDAX_OK; ++i) {
+        const ludax_launch_cfg c = cands[i];
+        float ts[64];
+        int nt = 0;
+        for (int r = 0; r < reps + 2 && st == LUDAX_OK; ++r) {
+            cudaEventRecord(e0, env->stream);
+            st = ludax_rollout(env, seed + (uint64_t)r, LUDAX_ROLLOUT_FROM_START, nullptr, d_out, d_plies, &c);
+            cudaEventRecord(e1, env->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = LUDAX_ERR_CUDA;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r >= 2 && nt < 64) ts[nt++] = ms;
+        }
+        if (st != LUDAX_OK) break;
+        for (int a = 1; a < nt; ++a)
+            for (int j = a; j > 0 && ts[j] < ts[j - 1]; --j) {
+                float x = ts[j]; ts[j] = ts[j - 1]; ts[j - 1] = x;
+            }
+        const float med = ts[nt / 2];
+        if (ms_table_out && k < 512) ms_table_out[k] = med;
+        ++k;
+        if (med < best) {
+            best = med;
+            *best_out = c;
+        }
+    }
+    delete[] cands;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(d_out);

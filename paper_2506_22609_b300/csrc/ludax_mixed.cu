@@ -256,6 +256,7 @@ int check_mixed_cfg(const ludax_launch_cfg& c) {
     if (c.envs_per_thread != 1) return LUDAX_ERR_ARG;  // the mixed kernel runs one env per lane
     if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
     if (c.compact_every != 0) return LUDAX_ERR_ARG;  // compaction is a single-game option
+    if (c.threads_per_env > 1 || c.threads_per_env < 0) return LUDAX_ERR_ARG;  // one lane per env
     return LUDAX_OK;
 }
 

@@ -61,7 +61,7 @@ class ludax_state_view(ctypes.Structure):
 class ludax_launch_cfg(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("envs_per_thread", ctypes.c_int32), ("hex_nbr_table", ctypes.c_int32),
-                ("compact_every", ctypes.c_int32)]
+                ("compact_every", ctypes.c_int32), ("threads_per_env", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,8 +70,10 @@ class ludax_launch_cfg(ctypes.Structure):
         return f"ludax_launch_cfg({self.as_dict()})"
 
 
-def make_cfg(block_threads=256, blocks_per_sm=0, envs_per_thread=1, hex_nbr_table=0, compact_every=0):
-    return ludax_launch_cfg(block_threads, blocks_per_sm, envs_per_thread, hex_nbr_table, compact_every)
+def make_cfg(block_threads=256, blocks_per_sm=0, envs_per_thread=1, hex_nbr_table=0, compact_every=0,
+             threads_per_env=1):
+    return ludax_launch_cfg(block_threads, blocks_per_sm, envs_per_thread, hex_nbr_table, compact_every,
+                            threads_per_env)
 
 
 _lib = None
@@ -117,6 +119,7 @@ def lib() -> ctypes.CDLL:
         "ludax_autotune": [vp, i64, u64, i32, vp, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
         "ludax_autotune_env": [vp, u64, i32, P(ludax_launch_cfg), P(ctypes.c_float), vp, P(i32)],
         "ludax_autotune_candidates": [P(ludax_launch_cfg), i32],
+        "ludax_autotune_env_candidates": [vp, P(ludax_launch_cfg), i32],
         "ludax_net_create": [P(vp), i32, i64, vp],
         "ludax_net_destroy": [vp],
         "ludax_net_sizes": [vp, P(i32), P(i32), P(i64)],
@@ -403,15 +406,23 @@ def ludax_autotune(desc, seed: int = 0, reps: int = 5, stream=None):
     return best, best_ms.value, list(zip(cands, list(table)))
 
 
+def ludax_autotune_env_candidates(h):
+    n = lib().ludax_autotune_env_candidates(h, None, 0)
+    arr = (ludax_launch_cfg * n)()
+    lib().ludax_autotune_env_candidates(h, arr, n)
+    return list(arr)
+
+
 def ludax_autotune_env(h, seed: int = 0, reps: int = 5):
-    """Autotunes ludax_rollout (from the start position) for one env batch."""
+    """Autotunes ludax_rollout (from the start position) for one env batch:
+    (best config, its median ms, [(candidate, median ms), ...])."""
     cands_n = ctypes.c_int32()
     best = ludax_launch_cfg()
     best_ms = ctypes.c_float()
     table = (ctypes.c_float * 512)()
     _check(lib().ludax_autotune_env(h, seed, reps, ctypes.byref(best), ctypes.byref(best_ms), table,
                                     ctypes.byref(cands_n)), "ludax_autotune_env")
-    return best, best_ms.value, list(table)[: cands_n.value]
+    return best, best_ms.value, list(zip(ludax_autotune_env_candidates(h), list(table)[: cands_n.value]))
 
 
 def ludax_net_create(cells: int, max_batch: int, stream=None):
