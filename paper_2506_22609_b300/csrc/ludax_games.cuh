@@ -390,13 +390,24 @@ struct Hex {
 
     __device__ __forceinline__ static B128 board() { return {kBoardLo, kBoardHi}; }
     // a value known to lie on the board: on boards of at most 64 cells the
-    // high word is the constant 0, so the compiler drops every high-word op
-    __device__ __forceinline__ static B128 fit(B128 a) { return {a.lo, kBoardHi ? a.hi : 0ull}; }
+    // high word is the constant 0, and on 9x9 its upper half is, so the
+    // compiler drops every instruction on those words
+    __device__ __forceinline__ static B128 fit(B128 a) {
+        if constexpr (kBoardHi == 0) return {a.lo, 0ull};
+        else if constexpr ((kBoardHi >> 32) == 0) return {a.lo, a.hi & kBoardHi};
+        else return a;
+    }
+    // the six neighbours of the cells of s: (r±1, c), (r, c±1), (r-1, c+1),
+    // (r+1, c-1).  A shift by n-1 after a shift by 1 is a shift by n, so the
+    // row neighbours ride along with the anti-diagonal ones: four shifts.
+    // Shifting by +1 wraps column n-1 onto column 0 of the next row and by -1
+    // column 0 onto column n-1, so those results are masked after the shift.
     __device__ __forceinline__ static B128 nbrs(B128 s) {
         const B128 notc0 = {kBoardLo & ~kCol0Lo, kBoardHi & ~kCol0Hi};
         const B128 notcl = {kBoardLo & ~kColLLo, kBoardHi & ~kColLHi};
-        B128 a = s & notcl, b = s & notc0;
-        B128 r = shl<N>(s) | shr<N>(s) | shl<1>(a) | shr<1>(b) | shr<N - 1>(a) | shl<N - 1>(b);
+        const B128 s1 = shl<1>(s), t1 = shr<1>(s);
+        const B128 u = s1 | (s & notc0), v = t1 | (s & notcl);
+        B128 r = shl<N - 1>(u) | shr<N - 1>(v) | (s1 & notc0) | (t1 & notcl);
         return r & board();
     }
     // edge A / B of the player on `side`: P1 rows 0 and n-1, P2 columns 0 and n-1
@@ -455,9 +466,21 @@ struct Hex {
     // spread() has returned false; until then no ply may be played.
     __device__ __forceinline__ void place_spread(int b) {
         const B128 x = fit(bit128(b));
-        const B128 nx = fit(nbr_table ? nbr_table[b] : nbrs(x));
-        const bool ta = any((x & edgeA(side)) | (nx & ownA));
-        const bool tb = any((x & edgeB(side)) | (nx & ownB));
+        bool ea, eb;
+        B128 nx;
+        if (nbr_table) {
+            const B128 raw = nbr_table[b];
+            const uint32_t fl = (uint32_t)(raw.hi >> 60);
+            ea = ((side ? fl >> 2 : fl) & 1u) != 0u;
+            eb = ((side ? fl >> 3 : fl >> 1) & 1u) != 0u;
+            nx = fit(raw);
+        } else {
+            nx = fit(nbrs(x));
+            ea = any(x & edgeA(side));
+            eb = any(x & edgeB(side));
+        }
+        const bool ta = ea || any(nx & ownA);
+        const bool tb = eb || any(nx & ownB);
         own = fit(own) | x;
         if (ta && tb) {
             outcome = side + 1;
@@ -467,6 +490,7 @@ struct Hex {
             if (ta) ownA = ownA | c;
             else ownB = ownB | c;
             front = first;
+            passes = ta;  // the set the front joins (kept through the compaction slots with the state)
         }
         ++ply;
         B128 t = own; own = opp; opp = t;
@@ -481,7 +505,7 @@ struct Hex {
     // adds nothing).  Returns true while the group is still growing.
     __device__ __forceinline__ bool spread() {
         const B128 f = fit(front), a = fit(oppA), b = fit(oppB);
-        const bool to_a = any(f & a);
+        const bool to_a = passes != 0;  // Hex has no passes: the field says which set the front joins
         const B128 nw = nbrs(f) & fit(opp) & ~(a | b);
         const B128 z = {0ull, 0ull};
         oppA = a | (to_a ? nw : z);
@@ -489,16 +513,29 @@ struct Hex {
         front = nw;
         return any(nw);
     }
-    // k-th legal cell; on boards of at most 64 cells only the low word exists
+    // k-th legal cell; on boards of at most 64 cells only the low word
+    // exists; otherwise the 32-bit word holding it is found from the words'
+    // counts (independent of each other) and the bit inside it by the SWAR
+    // search of select_bit
     __device__ __forceinline__ static int pick(B128 m, uint32_t k) {
-        if constexpr (kBoardHi == 0) return select_bit(m.lo, k);
-        else return select_bit(m, k);
+        if constexpr (kBoardHi == 0) {
+            return select_bit(m.lo, k);
+        } else {
+            const uint32_t w0 = (uint32_t)m.lo, w1 = (uint32_t)(m.lo >> 32), w2 = (uint32_t)m.hi, w3 = (uint32_t)(m.hi >> 32);
+            const uint32_t p1 = __popc(w0), p2 = p1 + __popc(w1), p3 = p2 + __popc(w2);
+            const bool g1 = k >= p1, g2 = k >= p2, g3 = k >= p3;
+            const uint32_t w = g3 ? w3 : (g2 ? w2 : (g1 ? w1 : w0));
+            const uint32_t base = g3 ? p3 : (g2 ? p2 : (g1 ? p1 : 0u));
+            const int at = (g1 + g2 + g3) * 32;
+            return at + select_bit(w, k - base);
+        }
     }
     // finish a spreading group (before the state leaves the registers)
     __device__ __forceinline__ void settle() {
 #pragma unroll 1
         while (spread()) {
         }
+        passes = 0;
     }
     // rebuild the edge-connected sets of both players from the stones
     __device__ __forceinline__ void rebuild() {
@@ -529,10 +566,19 @@ struct Hex {
 };
 
 // Fill a shared-memory table of per-cell neighbour masks for Hex<N>
-// (cooperatively by the block; caller synchronises).
+// (cooperatively by the block; caller synchronises).  The four top bits of
+// an entry (bits 124..127, never cells: n*n <= 121) say whether the cell is
+// on row 0, row n-1, column 0, column n-1 -- the players' edges -- so a
+// placement reads its edge contacts with its neighbours.
 template <int N>
 __device__ __forceinline__ void hex_fill_table(B128* table) {
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) table[i] = Hex<N>::nbrs(bit128(i));
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        B128 m = Hex<N>::nbrs(bit128(i));
+        const int r = i / N, c = i % N;
+        m.hi |= ((uint64_t)(r == 0) << 60) | ((uint64_t)(r == N - 1) << 61) | ((uint64_t)(c == 0) << 62) |
+                ((uint64_t)(c == N - 1) << 63);
+        table[i] = m;
+    }
 }
 
 // ------------------------------------------------- multi-word bitboards --
