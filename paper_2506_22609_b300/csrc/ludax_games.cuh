@@ -136,19 +136,13 @@ __device__ __forceinline__ uint32_t swar_select(const Swar32& s, uint32_t k) {
     return pos + (k >= c ? 1u : 0u);
 }
 __device__ __forceinline__ int select_bit(uint32_t m, uint32_t k) { return (int)swar_select(swar32(m), k); }
-// the SWAR counts of both 32-bit halves do not depend on k, so they are
-// formed while k is still being drawn; one search runs in the chosen half
+// the half that holds the k-th bit is chosen by the low half's count, then
+// one SWAR search runs in it
 __device__ __forceinline__ int select_bit(uint64_t m, uint32_t k) {
     const uint32_t lo = (uint32_t)m, hi = (uint32_t)(m >> 32);
     const uint32_t nlo = __popc(lo);
-    const Swar32 sl = swar32(lo), sh = swar32(hi);
     const bool low = k < nlo;
-    Swar32 s;
-    s.w = low ? sl.w : sh.w;
-    s.a = low ? sl.a : sh.a;
-    s.b = low ? sl.b : sh.b;
-    s.p = low ? sl.p : sh.p;
-    return (int)((low ? 0u : 32u) + swar_select(s, low ? k : k - nlo));
+    return (int)((low ? 0u : 32u) + swar_select(swar32(low ? lo : hi), low ? k : k - nlo));
 }
 __device__ __forceinline__ int select_bit(B128 m, uint32_t k) {
     const uint32_t c = __popcll(m.lo);
