@@ -86,6 +86,9 @@ def test_null_handles_are_rejected(L):
     assert L.ludax_env_destroy(None) == 0
     assert L.ludax_mixed_plan_destroy(None) == 0
     assert L.ludax_rollout_mixed(None, 10, 0, 0, None, None, None, None) == -1
+    assert L.ludax_mixed_plan_launch_host(None, 0, None, None, None) == -1
+    assert L.ludax_mixed_plan_sync(None, None) == -1
+    assert L.ludax_autotune_env_candidates(None, None, 0) == -1
 
 
 def test_autotune_candidates_are_valid(L):
@@ -97,6 +100,7 @@ def test_autotune_candidates_are_valid(L):
         assert 32 <= c.block_threads <= 512 and c.block_threads % 32 == 0
         assert c.blocks_per_sm == 0 or c.block_threads * c.blocks_per_sm <= 2048
         assert c.envs_per_thread == 1 and c.hex_nbr_table in (0, 1)
+        assert c.threads_per_env in (0, 1)  # the mixed kernel runs one lane per env
 
 
 def test_binding_refuses_host_tensors(L):
