@@ -1015,7 +1015,8 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": "env steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int8 cells", "data": "synthetic",
-            "config": {"workload": cfg.name, "num_envs_per_gpu": cfg.num_envs, "seed": cfg.seed},
+            "config": {"workload": cfg.name + ("_graph" if args.workload == "mixed" else ""),
+                       "num_envs_per_gpu": cfg.num_envs, "seed": cfg.seed},
             "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": round(value, 1),
                              "unit": "env steps/s"},
             "e2e": {"value": round(value, 1), "unit": "env steps/s", "h2d_bytes_per_step": 0,
