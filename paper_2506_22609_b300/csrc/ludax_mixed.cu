@@ -28,6 +28,14 @@ using namespace ludax;
 namespace {
 
 constexpr int kBuckets = kDescBuckets;
+// Buckets in decreasing order of the time one env takes to play out (single-
+// game launches of 65,536 envs: Dai Hasami Shogi, Pente, Draughts, Gomoku,
+// Hex 11, the line game, Reversi, Hex 10, Hex 9, Wolf and Sheep, ...,
+// Tic-Tac-Toe, Hex 3, Hex 2).  The one-env-per-thread launch starts the
+// buckets in this order (six-game mix 0.851 -> 0.812 ms, the 13 library
+// games 4.61 ms persistent -> 3.97 ms).
+__device__ constexpr int kLongestFirst[kBuckets] = {19, 14, 18, 13, 12, 16, 2, 11, 10, 17,
+                                                    9, 8, 15, 7, 1, 6, 5, 0, 4, 3};
 constexpr int kHexTableCells = 505;  // sum of n*n for n = 2..11
 
 __host__ __device__ constexpr int hex_table_offset(int n) {
@@ -68,8 +76,7 @@ __device__ __forceinline__ int bucket_at(const long long* be, long long q) {
 }
 
 // Non-persistent launches (a thread per env, the hardware's block scheduler
-// refilling the SMs): plays the env at queue
-// position q to its end.
+// refilling the SMs): plays the env at queue position q to its end.
 template <class G>
 __device__ __forceinline__ void play_one(const MixedArgs& a, long long q, const B128* table) {
     G g;
@@ -177,11 +184,31 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         hex_fill_table<11>(tables + hex_table_offset(11));
         __syncthreads();
     }
-    __shared__ long long be[kBuckets];
+    __shared__ long long be[kBuckets], seg_end[kBuckets], seg_q[kBuckets];
     load_bucket_ends(a, be);
     __syncthreads();
-    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= be[kBuckets - 1]) return;  // past the last valid queue position
+    // Blocks are handed out in index order, so thread position q0 walks the
+    // buckets in kLongestFirst order: the games that take longest start first
+    // and the short ones fill the tail of the launch (longest-first
+    // scheduling).  seg_end[i] = positions covered by the first i + 1 buckets
+    // of that order, seg_q[i] = queue offset of segment i.
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int i = 0; i < kBuckets; ++i) {
+            const int b = kLongestFirst[i];
+            const long long beg = b == 0 ? 0 : be[b - 1];
+            seg_q[i] = beg - acc;
+            acc += be[b] - beg;
+            seg_end[i] = acc;
+        }
+    }
+    __syncthreads();
+    const long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q0 >= be[kBuckets - 1]) return;  // past the last valid queue position
+    int si = 0;
+#pragma unroll
+    for (int k = 0; k < kBuckets - 1; ++k) si += q0 >= seg_end[k];
+    const long long q = q0 + seg_q[si];
     const B128* t = tables;
     switch (bucket_at(be, q)) {
     case 0: play_one<TTT>(a, q, nullptr); break;

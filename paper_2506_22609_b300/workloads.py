@@ -100,7 +100,7 @@ BENCH_CFGS = {
     DRAUGHTS_64K.name: (448, 0, 1, 0, 16),
     HASAMI_64K.name: (448, 2, 1, 0, 16),
 }
-MIXED_BENCH_CFG = (128, 0, 1, 1, 0)
+MIXED_BENCH_CFG = (256, 0, 1, 1, 0)
 
 
 def bench_cfg(cfg: Config) -> tuple:
