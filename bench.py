@@ -659,15 +659,24 @@ def bench_train_step(L, peaks, flush_buf, steps=20, warmup=3, B=65536):
         x[:, 2 * cells + 1:] = 0
         xb, yb = x.view(torch.int16), torch.rand(B, device="cuda", generator=g)
         flops = 2.0 * B * (2 * net.in_pad * 512 + 3 * 512 * 512 + 512)
-        res = {"batch": B, "in_pad": net.in_pad, "gflop_per_step": round(flops / 1e9, 2)}
+        # algorithmic HBM bytes of the step's dataflow: X read by layer 1 and dW1; H1 written and
+        # read by layer 2, the dZ1 mask and dW2; H2 written and read by the head's backward; dZ2
+        # written and read by dZ1 and dW2; dZ1 written and read by the bias sum and dW1 (BF16);
+        # Adam reads and writes parameters and both moments and reads the gradient (FP32)
+        nbytes = 2.0 * B * (2 * net.in_pad + 512 * (4 + 2 + 3 + 3)) + 4.0 * 7 * net.num_params
+        res = {"batch": B, "in_pad": net.in_pad, "gflop_per_step": round(flops / 1e9, 2),
+               "alg_mbytes_per_step": round(nbytes / 1e6, 1),
+               "arithmetic_intensity_flop_per_byte": round(flops / nbytes, 1)}
         for path, name in ((1, "tcgen05"), (0, "mma_sync")):
             net.set_tensor_path(path)
             ms = time_steps(lambda: net.train_step(xb, yb, 1e-3), steps, warmup, flush_buf,
                             torch.cuda.current_stream())
             t = statistics.median(ms) / 1e3
             tf = flops / t / 1e12
+            gbs = nbytes / t / 1e9
             res[name] = {"median_ms": round(t * 1e3, 4), "steps_per_s": round(1 / t, 1), "tflops": round(tf, 1),
-                         "frac_of_bf16_peak": round(tf / float(peaks.get("bf16_tflops", 1800.0)), 4)}
+                         "frac_of_bf16_peak": round(tf / float(peaks.get("bf16_tflops", 1800.0)), 4),
+                         "hbm_gbs": round(gbs, 1), "frac_of_hbm": round(gbs / float(peaks.get("hbm_gbs", 6400.0)), 4)}
         res["device_error"] = L.ludax_device_error()
         net.close()
         out[game] = res
