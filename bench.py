@@ -54,11 +54,11 @@ METRIC = "env steps/sec on 1 B300 (random playouts); value estimates/sec at stat
 # shifts) 248, outcome and turn 9.
 ALG_OPS_PER_STEP = {"ttt": 75, "c4": 112, "othello": 437, "hex": 180, "gomoku": 330, "pente": 700,
                     "yavalath": 150, "line": 334}
-# The survey's estimates of the same work (its measurement section): TTT ~40,
-# C4 ~80, Reversi ~350-500 (our 437 lies inside), Hex ~100 + ~40 per flood
-# round; a random Hex game needs 0.27-0.29 flood rounds per ply on 7x7 to
-# 11x11 boards (the incremental edge-set update), so Hex ~112.
-SURVEY_OPS_PER_STEP = {"ttt": 40, "c4": 80, "othello": 437, "hex": 112}
+# Estimates of the same work made before any kernel was written: TTT ~40,
+# C4 ~80, Reversi ~350-500 (the count above, 437, lies inside), Hex ~100 + ~40
+# per flood round; a random Hex game needs 0.27-0.29 flood rounds per ply on
+# 7x7 to 11x11 boards (the incremental edge-set update), so Hex ~112.
+PRIOR_OPS_PER_STEP = {"ttt": 40, "c4": 80, "othello": 437, "hex": 112}
 # game id of a descriptor (low byte) -> key of the tables above
 GAME_KEYS = {0: "ttt", 1: "c4", 2: "othello", 3: "hex", 4: "gomoku", 5: "pente", 6: "yavalath", 7: "line"}
 
@@ -860,15 +860,15 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     peak_ops = sms * 128 * max_mhz * 1e6  # 32-bit lanes x clock
-    ops_survey = None
+    ops_prior = None
     if cfg is not None and game_key(cfg) in ALG_OPS_PER_STEP:
         ops_per_launch = ALG_OPS_PER_STEP[game_key(cfg)] * steps_per_launch
-        if game_key(cfg) in SURVEY_OPS_PER_STEP:
-            ops_survey = SURVEY_OPS_PER_STEP[game_key(cfg)] * steps_per_launch
+        if game_key(cfg) in PRIOR_OPS_PER_STEP:
+            ops_prior = PRIOR_OPS_PER_STEP[game_key(cfg)] * steps_per_launch
     elif args.workload == "mixed":
         # the sum over the mix's games of (ops per step x that game's plies in the launch)
         ops_per_launch = sum(ALG_OPS_PER_STEP[GAME_KEYS[g]] * v for g, v in plies_per_game.items())
-        ops_survey = sum(SURVEY_OPS_PER_STEP[GAME_KEYS[g]] * v for g, v in plies_per_game.items())
+        ops_prior = sum(PRIOR_OPS_PER_STEP[GAME_KEYS[g]] * v for g, v in plies_per_game.items())
     else:
         ops_per_launch = None
     med = statistics.median(ms)
@@ -882,21 +882,21 @@ def main():
                     "peak_source": f"hbm_gbs ({peak_kind})", "alg_bytes_per_env_step": bytes_per,
                     "median_launch_ms": round(med, 5)}
     if ops_per_launch:
-        # frac uses the survey's op counts where it gives them; the builder's own
+        # frac uses the prior estimates of the op counts where they exist; the
         # counts of the bitboard algorithm and ncu's executed count sit beside it
         alu_pipe = peak_ops / 2  # logic/shift/add run on the ALU pipe: 64 lanes per clock per SM
         achieved_b = ops_per_launch / (med / 1e3) / 1e12
-        achieved = (ops_survey or ops_per_launch) / (med / 1e3) / 1e12
+        achieved = (ops_prior or ops_per_launch) / (med / 1e3) / 1e12
         if cfg is not None:
             per_step = {"builder": ALG_OPS_PER_STEP[game_key(cfg)],
-                        "survey": SURVEY_OPS_PER_STEP.get(game_key(cfg))}
+                        "prior_estimate": PRIOR_OPS_PER_STEP.get(game_key(cfg))}
         else:
             per_step = {"builder": {GAME_KEYS[g]: ALG_OPS_PER_STEP[GAME_KEYS[g]] for g in plies_per_game},
-                        "survey": {GAME_KEYS[g]: SURVEY_OPS_PER_STEP[GAME_KEYS[g]] for g in plies_per_game},
+                        "prior_estimate": {GAME_KEYS[g]: PRIOR_OPS_PER_STEP[GAME_KEYS[g]] for g in plies_per_game},
                         "plies_per_game": {GAME_KEYS[g]: v for g, v in plies_per_game.items()}}
         roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_ops / 1e12, 3),
                     "unit": "Tops/s (32-bit integer)", "frac": round(achieved / (peak_ops / 1e12), 4),
-                    "counts": "survey" if ops_survey else "builder",
+                    "counts": "prior_estimate" if ops_prior else "builder",
                     "alu_pipe_peak": round(alu_pipe / 1e12, 3), "alu_pipe_frac": round(achieved / (alu_pipe / 1e12), 4),
                     "frac_builder_counts": round(achieved_b / (peak_ops / 1e12), 4),
                     "ncu_thread_instructions_per_step": NCU_THREAD_INST_PER_STEP.get(wl_name),

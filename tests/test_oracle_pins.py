@@ -27,9 +27,9 @@ def test_draw_key_derivation_known_answers():
     # the policy's draw keyed on (seed, global env, ply): key = sm(sm(seed) ^ env),
     # r = sm(key ^ ply), k = multiply-shift of r's top 32 bits.  Known answers
     # come from tests/golden/make_splitmix64_keys.py (published splitmix64,
-    # no oracle code); the first three are also the survey's key(0,0),
-    # r(0,0,0) and r(0,0,1).  Slips such as sm(seed ^ env), sm(seed) ^ env or
-    # r = sm(key + ply) fail here.
+    # no oracle code); the first three, key(0,0), r(0,0,0) and r(0,0,1), were
+    # also worked out when the draw was specified.  Slips such as sm(seed ^ env),
+    # sm(seed) ^ env or r = sm(key + ply) fail here.
     rows = golden("splitmix64_keys.txt")
     assert len(rows) >= 10
     for seed, env, ply, n, key_hex, r_hex, k in rows:
