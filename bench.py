@@ -4,7 +4,7 @@
                     [--workload c4|ttt|othello|hex11|gomoku|pente|yavalath|line_c5|wolf_sheep|
                                 draughts|hasami_shogi|mixed|step_c4]
                     [--no-extras] [--no-cpu-baseline] [--only dense_layer|gavel_library|
-                     batch_sweep|value_net|value_estimator|int_peak|train_step]
+                     batch_sweep|value_net|value_estimator|int_peak|train_step|threads_per_env]
 
 One step = one fused playout launch over the whole batch: every env of the
 workload is reset to the start position and played to the end of its game
@@ -81,7 +81,7 @@ def parse():
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net", "value_estimator",
-                                      "int_peak", "train_step"],
+                                      "int_peak", "train_step", "threads_per_env"],
                    default=None,
                    help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -721,6 +721,28 @@ def bench_valuenet(seeds=(5, 6, 7)):
     return out
 
 
+def bench_threads_per_env(L, sizes=(7, 9, 11), batches=(1024, 4096, 16384, 65536, 174763), seed=4, reps=3):
+    """The single-game autotuner over Hex boards and batch sizes, reduced to
+    the fastest launch shape for each threads-per-env value (1, 2, 4): ms
+    per launch from the start position and env steps per second."""
+    out = {}
+    for size in sizes:
+        for n in batches:
+            env = L.Env("hex", size, size, n)
+            best, best_ms, table = L.ludax_autotune_env(env.handle, seed, reps=reps)
+            per = {}
+            for c, ms in table:
+                t = max(1, c.threads_per_env)
+                if t not in per or ms < per[t][1]:
+                    per[t] = (c.as_dict(), ms)
+            _, plies = env.rollout(seed, cfg=best)
+            spl = int(plies.to(dtype=__import__("torch").int64).sum().item())
+            out[f"hex{size}_{n}env"] = {str(t): {"ms": round(v[1], 4), "env_steps_per_s": round(spl / (v[1] / 1e3), 1),
+                                                 "launch": v[0]} for t, v in sorted(per.items())}
+            env.close()
+    return out
+
+
 def bench_int_peak(L, iters=1 << 16):
     """What a stream of one integer op reaches (LOP3, IADD, SHF, IMAD,
     IMAD.HI, and LOP3 + IMAD on alternate chains; 8 independent chains per
@@ -825,6 +847,8 @@ def main():
             res = bench_int_peak(L)
         elif args.only == "train_step":
             res = bench_train_step(L, peaks, flush_buf, max(args.steps, 5), args.warmup)
+        elif args.only == "threads_per_env":
+            res = bench_threads_per_env(L)
         else:
             res = bench_batch_sweep(L, W, flush_buf)
         if rank == 0:
