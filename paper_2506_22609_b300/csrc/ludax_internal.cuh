@@ -125,12 +125,45 @@ int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, cons
 
 // The value net's backward contractions on tcgen05 (ludax_umma.cu).
 // umma_grad_mask: out[m][n] = bf16(mask[m][n] > 0 ? sum_k A[m][k] B[k][n] : 0)
-// with A [M][K], B [K][N], mask and out [M][N], all row-major BF16.
-int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, cudaStream_t s);
+// with A [M][K], B [K][N], mask and out [M][N], all row-major BF16.  With
+// colpart non-null it also leaves the column sums of out (the stored BF16
+// values, summed in FP32) as umma_grad_colrows(M, N) partial rows of N
+// floats: every row of out is counted in exactly one of them, and each
+// partial row is written in full.
+int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, float* colpart,
+                   cudaStream_t s);
+int umma_grad_colrows(int M, int N);  // 0 on error; at most 4 * SMs
 // umma_grad_weights: part[p][m][n] = FP32 sum over the p-th of *splits_out
 // contiguous K ranges of A[k][m] B[k][n]; A [K][lda], B [K][ldb] row-major
 // BF16; part holds part_floats floats (the split count is capped by it).
 int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* part,
                       long long part_floats, int* splits_out, cudaStream_t s);
+
+// Programmatic dependent launch.  A kernel started with launch_dependent is
+// scheduled as the CTAs of the kernel before it on the stream exit (each
+// exit counts as that CTA's trigger), so its CTAs fill the SMs the previous
+// kernel's tail leaves idle, and run up to their pdl_wait(), which returns
+// once that kernel (and so everything before it) has completed and its
+// memory is visible: it must come before the kernel's first global load or
+// store.  For an ordinary launch it is a no-op.  (Triggering at the start of
+// a kernel instead let the next kernel's waiting CTAs take SM resources
+// early and made the training step slower.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                             Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 }  // namespace ludax

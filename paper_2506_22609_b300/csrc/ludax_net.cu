@@ -261,10 +261,24 @@ __device__ __forceinline__ void load8(const __nv_bfloat16* p, float* f) {
 // partials in row blockIdx.x of part[chunks][HB_COLS]: db2 = sum_b dZ2
 // (unrounded), dw3 = sum_b g3 H2, db3 = sum_b g3 and the summed squared
 // error -- b2, w3, b3 in the order the gradient vector stores them.
+// With zpart given (the second layer's fused head: two partial dot products
+// per row) the row's g3 and squared error are formed here from z, y and b3,
+// as head_finish_kernel does; otherwise they are read from g3 / sqerr.
+__device__ __forceinline__ void head_row(const float* zpart, const float* y, const float* b3, int B, int r,
+                                         float& g, float& se) {
+    float z = 0.f;
+    for (int i = 0; i < kH / 256; ++i) z += zpart[(size_t)r * (kH / 256) + i];
+    const float v = tanhf(z + b3[0]), p = 0.5f * (v + 1.f), d = p - y[r];
+    g = d * (1.f - v * v) / (float)B;  // 2 (p-y)/B * (1/2) (1 - v^2)
+    se = d * d;
+}
 __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16* w3,
-                                                            const float* g3, const float* sqerr, int B,
+                                                            const float* g3, const float* sqerr, const float* zpart,
+                                                            const float* y, const float* b3, int B,
                                                             __nv_bfloat16* dZ2, float* part) {
+    pdl_wait();
     __shared__ float sh[HB_GROUPS - 1][HB_COLS];
+    __shared__ float sg[HB_ROWS], ss[HB_ROWS];  // the chunk's rows: g3 and squared error
     const int grp = threadIdx.x >> 6, j0 = (threadIdx.x & 63) * 8;
     const bool first = (threadIdx.x & 63) == 0;
     float w[8], ab[8], aw[8], ag = 0.f, al = 0.f;
@@ -272,9 +286,17 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
 #pragma unroll
     for (int e = 0; e < 8; ++e) ab[e] = aw[e] = 0.f;
     const int r0 = blockIdx.x * HB_ROWS, r1 = min(r0 + HB_ROWS, B);
+    for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) {  // each row's loss gradient once
+        float gr, se;
+        if (zpart) head_row(zpart, y, b3, B, r0 + i, gr, se);
+        else gr = g3[r0 + i], se = sqerr[r0 + i];
+        sg[i] = gr;
+        ss[i] = se;
+    }
+    __syncthreads();
 #pragma unroll 4
     for (int r = r0 + grp; r < r1; r += HB_GROUPS) {
-        const float gr = g3[r];
+        const float gr = sg[r - r0], se = ss[r - r0];
         float h[8];
         load8(H2 + (size_t)r * kH + j0, h);
         __align__(16) __nv_bfloat162 d[4];
@@ -290,7 +312,7 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
         *reinterpret_cast<uint4*>(dZ2 + (size_t)r * kH + j0) = *reinterpret_cast<const uint4*>(d);
         if (first) {
             ag += gr;
-            al += sqerr[r];
+            al += se;
         }
     }
     if (grp > 0) {
@@ -359,51 +381,6 @@ __global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* X, int
     }
 }
 
-// out[i] = scale * sum over p < parts of part[p * ld + i], i < n, for many
-// parts and few columns: a 1024-thread block takes 32 columns, thread
-// (tx, ty) sums parts ty, ty + 32, ... of column tx, and the 32 sums are
-// added in a fixed order.
-__global__ void __launch_bounds__(1024) reduce_cols_kernel(const float* part, int parts, int ld, int n, float scale,
-                                                           float* out) {
-    __shared__ float sh[32][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int i = blockIdx.x * 32 + tx;
-    float a = 0.f;
-    if (i < n) {
-#pragma unroll 8
-        for (int p = ty; p < parts; p += 32) a += part[(size_t)p * ld + i];
-    }
-    sh[ty][tx] = a;
-    __syncthreads();
-    if (ty == 0 && i < n) {
-        float t = 0.f;
-        for (int k = 0; k < 32; ++k) t += sh[k][tx];
-        out[i] = t * scale;
-    }
-}
-
-// out[i] = sum_s part[s*n + i] (in a fixed order), four columns per thread
-// (n % 4 == 0): few parts, many columns (the split weight gradients).  part
-// is 16-byte aligned; out (a block of the flat gradient vector) is only
-// 4-byte aligned, so it is written one float at a time.
-__global__ void reduce_parts_kernel(const float* part, int splits, int n, float* out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (4 * i >= n) return;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-    for (int s = 0; s < splits; ++s) {
-        const float4 v = *reinterpret_cast<const float4*>(part + (size_t)s * n + 4 * i);
-        a.x += v.x;
-        a.y += v.y;
-        a.z += v.z;
-        a.w += v.w;
-    }
-    out[4 * i] = a.x;
-    out[4 * i + 1] = a.y;
-    out[4 * i + 2] = a.z;
-    out[4 * i + 3] = a.w;
-}
-
 // Adam (Kingma & Ba, Algorithm 1) on the flat FP32 parameters, then the BF16
 // copies the GEMMs read.  bc1 = 1 - beta1^t, bc2 = 1 - beta2^t.
 // The updated weights also go to their BF16 copies: W1 | W2 | w3 back to
@@ -413,21 +390,105 @@ struct BfCopy {
     __nv_bfloat16* bf;
     long long ob1, oW2, ob2, ow3, ob3;
 };
-__global__ void adam_kernel(float* p, float* m, float* v, const float* g, long long n, float lr, float bc1, float bc2,
-                            BfCopy c) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+
+// The backward pass's last launch: each parameter's gradient from the
+// partial sums the earlier kernels left, then either the gradient stored
+// in g (adam == 0) or one Adam step applied in place (p, m, v and the BF16
+// copies).  Partials:
+//   w1p [s1][kH * kpad], w2p [s2][kH * kH]  split-K sums of dW1, dW2;
+//   cp  [crows][kH]                         row-group sums of db1;
+//   hp  [hrows][HB_COLS]                    row-chunk sums of db2 | dw3 |
+//                                           db3 | squared error.
+// Blocks [0, nwide) take W1 and W2, four elements per thread, adding the
+// splits in order; each later block takes 32 columns of cp, then of hp:
+// its 32 warps stride down the rows (lane = column) and the 32 warp sums
+// are added in a fixed order.  The loss is the squared-error column / B.
+struct FinishArgs {
+    const float *w1p, *w2p, *cp, *hp;
+    int s1, s2, crows, hrows;
+    long long n1, n2;  // kH * kpad, kH * kH
+    int nwide;
+    float* g;
+    float *p, *m, *v;
+    float lr, bc1, bc2;
+    BfCopy c;
+    float* loss;
+    float inv_b;
+    int adam;
+};
+
+__device__ __forceinline__ void apply_grad(const FinishArgs& a, long long i, float gi) {
+    if (!a.adam) {
+        a.g[i] = gi;
+        return;
+    }
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    float gi = g[i];
-    float mi = b1 * m[i] + (1.f - b1) * gi;
-    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
-    p[i] = pi;
+    const float mi = b1 * a.m[i] + (1.f - b1) * gi;
+    const float vi = b2 * a.v[i] + (1.f - b2) * gi * gi;
+    a.m[i] = mi;
+    a.v[i] = vi;
+    const float pi = a.p[i] - a.lr * (mi / a.bc1) / (sqrtf(vi / a.bc2) + eps);
+    a.p[i] = pi;
+    const BfCopy& c = a.c;
     if (i < c.ob1) c.bf[i] = __float2bfloat16_rn(pi);
     else if (i >= c.oW2 && i < c.ob2) c.bf[i - kH] = __float2bfloat16_rn(pi);
     else if (i >= c.ow3 && i < c.ob3) c.bf[i - 2 * kH] = __float2bfloat16_rn(pi);
+}
+
+constexpr int FIN_THREADS = 1024;
+
+__global__ void __launch_bounds__(FIN_THREADS) finish_kernel(FinishArgs a) {
+    pdl_wait();
+    if ((int)blockIdx.x < a.nwide) {
+        const long long t = (long long)blockIdx.x * FIN_THREADS + threadIdx.x, e = 4 * t;
+        if (e >= a.n1 + a.n2) return;
+        const bool w1 = e < a.n1;
+        const float* src = w1 ? a.w1p + e : a.w2p + (e - a.n1);
+        const long long stride = w1 ? a.n1 : a.n2, flat = w1 ? e : a.c.oW2 + (e - a.n1);
+        const int splits = w1 ? a.s1 : a.s2;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int s0 = 0; s0 < splits; s0 += 8) {  // eight loads in flight, then added in split order
+            float4 x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                x[k] = s0 + k < splits ? *reinterpret_cast<const float4*>(src + (size_t)(s0 + k) * stride)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                acc.x += x[k].x;
+                acc.y += x[k].y;
+                acc.z += x[k].z;
+                acc.w += x[k].w;
+            }
+        }
+        apply_grad(a, flat, acc.x);
+        apply_grad(a, flat + 1, acc.y);
+        apply_grad(a, flat + 2, acc.z);
+        apply_grad(a, flat + 3, acc.w);
+        return;
+    }
+    __shared__ float sh[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int blk = (int)blockIdx.x - a.nwide;
+    const bool bias1 = blk < kH / 32;
+    if (!bias1) blk -= kH / 32;
+    const int col = blk * 32 + lane, ncols = bias1 ? kH : HB_COLS, rows = bias1 ? a.crows : a.hrows;
+    const float* src = bias1 ? a.cp : a.hp;
+    float x = 0.f;
+    if (col < ncols) {
+#pragma unroll 4
+        for (int r = w; r < rows; r += 32) x += src[(size_t)r * ncols + col];
+    }
+    sh[w][lane] = x;
+    __syncthreads();
+    if (w != 0 || col >= ncols) return;
+    float t = 0.f;
+    for (int k = 0; k < 32; ++k) t += sh[k][lane];
+    if (bias1) apply_grad(a, a.c.ob1 + col, t);
+    else if (col < kH) apply_grad(a, a.c.ob2 + col, t);
+    else if (col < 2 * kH) apply_grad(a, a.c.ow3 + (col - kH), t);
+    else if (col == 2 * kH) apply_grad(a, a.c.ob3, t);
+    else if (a.loss) a.loss[0] = t * a.inv_b;
 }
 
 __global__ void to_bf16_kernel(const float* src, __nv_bfloat16* dst, long long n) {
@@ -576,9 +637,13 @@ struct ludax_net {
     float *p, *m, *v, *g;
     __nv_bfloat16 *W1b, *W2b, *w3b;
     __nv_bfloat16 *H1, *H2, *dZ2, *dZ1, *Xleaf;
-    float *pout, *g3, *sqerr, *part, *score;
+    float *pout, *g3, *sqerr, *score;
+    // backward partial sums (see finish_kernel): the second layer's head
+    // partials [B][2], the head's row-chunk sums, db1's row-group sums and the
+    // split-K sums of dW2 and dW1
+    float *zp, *hp, *cp, *w2p, *w1p;
+    long long cp_rows, w2_floats, w1_floats;
     uint8_t* done;
-    long long part_floats;
     __nv_bfloat16* mlp_scratch;  // layer-1 rows of the fused inference kernel (allocated on first use)
     float* mlp_z;                // its head partials, 4 per row
     int mlp_rows;
@@ -628,7 +693,15 @@ __global__ void head_finish_kernel(const float* zpart, int parts, const float* b
     }
 }
 
-// Forward pass to p (and, with labels y, the per-row gradient g3 of the loss).
+// Training runs both hidden layers and the backward contractions on
+// tcgen05 for these batches; otherwise on the mma.sync kernel.
+bool tc_layers(const ludax_net* n, long long B) {
+    return n->use_tcgen05 && umma_dense_supported((int)B, kH, kH);
+}
+
+// Forward pass to p (and, with labels y, the per-row gradient g3 of the loss,
+// or on the tcgen05 training path the head partials it is formed from; p is
+// then not written).
 // kuse <= kpad: the input columns the first layer reads (the rest must be zero).
 // Without labels (inference) and on the tcgen05 path, the head is fused into
 // the second layer's epilogue, so its rows are never stored.
@@ -667,67 +740,92 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
                                                                nullptr, nullptr);
         return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
     }
-    int st = dense_layer(n, X, n->W1b, n->p + n->ob1, n->H1, B, n->kpad);
-    if (st) return st;
-    if (n->use_tcgen05 && umma_dense_supported((int)B, kH, kH)) {
-        // training forward: the second layer stores its rows for the backward
+    int st;
+    if (tc_layers(n, B)) {
+        // training forward: layer 1 reads the input columns up to the next
+        // multiple of 64 past the last used one (the rest are zero by the
+        // input contract); the second layer stores its rows for the backward
         // pass and takes the head's dot products in the same epilogue (two
-        // partials per row, in the backward pass's not yet used buffer)
-        float* zpart = n->part;
-        if ((st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, n->H2, kH, n->w3b, zpart, (int)B, kH, kH,
-                                     s)))
+        // partials per row), from which the backward pass's first kernel
+        // forms the loss gradient
+        const int k1 = std::min(n->kpad, (n->kin + 63) / 64 * 64);
+        if ((st = umma_dense_relu_ex(X, n->kpad, n->W1b, n->kpad, n->p + n->ob1, n->H1, kH, nullptr, nullptr, (int)B,
+                                     kH, k1, s)))
             return st;
-        head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, kH / 256, n->p + n->ob3, (int)B, p, y, n->g3,
-                                                               n->sqerr);
-        return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+        return umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, n->H2, kH, n->w3b, n->zp, (int)B, kH, kH, s);
     }
+    if ((st = dense_layer(n, X, n->W1b, n->p + n->ob1, n->H1, B, n->kpad))) return st;
     if ((st = dense_layer(n, n->H1, n->W2b, n->p + n->ob2, n->H2, B, kH))) return st;
     head_forward_kernel<<<blocks_for(B, 8), 256, 0, s>>>(n->H2, n->w3b, n->p + n->ob3, (int)B, p, y, n->g3, n->sqerr);
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
 
-// Full gradient into n->g (flat, FP32) and the mean loss into loss_out (nullable).
-int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, float* loss_out) {
+struct AdamStep {
+    float lr, bc1, bc2;
+};
+
+// Backward pass after net_forward with labels y: the gradient into n->g
+// (adam == nullptr) or one Adam step applied to the parameters, and the mean
+// loss into loss_out (nullable).  Launches: the head's backward (dZ2 and its
+// bias / weight sums), dZ1 with db1's column sums, the two weight gradients
+// as split-K partials, and finish_kernel, which reduces every partial and
+// stores or applies the gradient.
+int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float* y, float* loss_out,
+                 const AdamStep* adam) {
     cudaStream_t s = n->stream;
     const int chunks = (int)((B + HB_ROWS - 1) / HB_ROWS);
-    float* hpart = n->part;  // [chunks][HB_COLS]
-    head_backward_kernel<<<chunks, 256, 0, s>>>(n->H2, n->w3b, n->g3, n->sqerr, (int)B, n->dZ2, hpart);
-    // db2 | dw3 | db3 land where the gradient vector keeps b2, w3, b3; then the mean loss
-    reduce_cols_kernel<<<(2 * kH + 1 + 31) / 32, 1024, 0, s>>>(hpart, chunks, HB_COLS, 2 * kH + 1, 1.f, n->g + n->ob2);
-    if (loss_out) reduce_cols_kernel<<<1, 1024, 0, s>>>(hpart + 2 * kH + 1, chunks, HB_COLS, 1, 1.f / (float)B, loss_out);
-    // dZ1 = (dZ2 . W2) * [H1 > 0]
-    const bool tc = n->use_tcgen05 && umma_dense_supported((int)B, kH, kH);
-    int st;
+    const bool tc = tc_layers(n, B);
+    if (launch_dependent(head_backward_kernel, (unsigned)chunks, 256, 0, s, (const __nv_bfloat16*)n->H2,
+                         (const __nv_bfloat16*)n->w3b, (const float*)n->g3, (const float*)n->sqerr,
+                         (const float*)(tc ? n->zp : nullptr), y, (const float*)(n->p + n->ob3), (int)B, n->dZ2,
+                         n->hp) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    // dZ1 = (dZ2 . W2) * [H1 > 0], and db1 = its column sums as partial rows
+    int st, crows;
     if (tc) {
-        st = umma_grad_mask(n->dZ2, n->W2b, n->H1, n->dZ1, (int)B, kH, kH, s);
+        crows = umma_grad_colrows((int)B, kH);
+        if (crows <= 0 || crows > n->cp_rows) return LUDAX_ERR_CUDA;
+        st = umma_grad_mask(n->dZ2, n->W2b, n->H1, n->dZ1, (int)B, kH, kH, n->cp, s);
     } else {
         GemmArgs a{};
         a.A = n->dZ2; a.B = n->W2b; a.M = (int)B; a.N = kH; a.K = kH; a.lda = kH; a.ldb = kH;
         a.mask = n->H1; a.out = n->dZ1; a.ldo = kH;
         st = launch_gemm<true, false, EPI_MASK>(a, 1, s);
+        if (!st) colsum_kernel<<<chunks, 256, 0, s>>>(n->dZ1, (int)B, n->cp);
+        crows = chunks;
     }
     if (st) return st;
-    colsum_kernel<<<chunks, 256, 0, s>>>(n->dZ1, (int)B, n->part);
-    reduce_cols_kernel<<<kH / 32, 1024, 0, s>>>(n->part, chunks, kH, kH, 1.f, n->g + n->ob1);
     // dW2 = dZ2^T . H1 and dW1 = dZ1^T . X, split over the batch into partial sums
-    auto weight_grad = [&](const __nv_bfloat16* A, const __nv_bfloat16* Bm, int N, int ldb, float* out) -> int {
-        int splits = 0, r;
-        if (tc && umma_dense_supported(kH, N, (int)B)) {
-            r = umma_grad_weights(A, kH, Bm, ldb, kH, N, (int)B, n->part, n->part_floats, &splits, s);
-        } else {
-            splits = (int)std::min<long long>(32, B / BKT);
-            while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
-            GemmArgs a{};
-            a.A = A; a.B = Bm; a.M = kH; a.N = N; a.K = (int)B; a.lda = kH; a.ldb = ldb; a.partial = n->part;
-            r = launch_gemm<false, false, EPI_PARTIAL>(a, splits, s);
-        }
-        if (r) return r;
-        reduce_parts_kernel<<<blocks_for((long long)kH * N / 4, 256), 256, 0, s>>>(n->part, splits, kH * N, out);
-        return LUDAX_OK;
+    auto weight_grad = [&](const __nv_bfloat16* A, const __nv_bfloat16* Bm, int N, int ldb, float* part,
+                           long long cap, int& splits) -> int {
+        if (tc && umma_dense_supported(kH, N, (int)B))
+            return umma_grad_weights(A, kH, Bm, ldb, kH, N, (int)B, part, cap, &splits, s);
+        splits = (int)std::min<long long>(32, B / BKT);
+        while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
+        GemmArgs a{};
+        a.A = A; a.B = Bm; a.M = kH; a.N = N; a.K = (int)B; a.lda = kH; a.ldb = ldb; a.partial = part;
+        return launch_gemm<false, false, EPI_PARTIAL>(a, splits, s);
     };
-    if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->g + n->oW2))) return st;
-    if ((st = weight_grad(n->dZ1, X, n->kpad, n->kpad, n->g + n->oW1))) return st;
-    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    int s2 = 0, s1 = 0;
+    if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->w2p, n->w2_floats, s2))) return st;
+    if ((st = weight_grad(n->dZ1, X, n->kpad, n->kpad, n->w1p, n->w1_floats, s1))) return st;
+    FinishArgs f{};
+    f.w1p = n->w1p; f.w2p = n->w2p; f.cp = n->cp; f.hp = n->hp;
+    f.s1 = s1; f.s2 = s2; f.crows = crows; f.hrows = chunks;
+    f.n1 = (long long)kH * n->kpad; f.n2 = (long long)kH * kH;
+    f.nwide = (int)blocks_for((f.n1 + f.n2) / 4, FIN_THREADS);
+    f.g = n->g; f.p = n->p; f.m = n->m; f.v = n->v;
+    if (adam) {
+        f.adam = 1;
+        f.lr = adam->lr; f.bc1 = adam->bc1; f.bc2 = adam->bc2;
+    }
+    f.c = BfCopy{n->W1b, n->ob1, n->oW2, n->ob2, n->ow3, n->ob3};
+    f.loss = loss_out;
+    f.inv_b = 1.f / (float)B;
+    return launch_dependent(finish_kernel, (unsigned)(f.nwide + kH / 32 + (HB_COLS + 31) / 32), FIN_THREADS, 0, s, f) ==
+                   cudaSuccess
+               ? LUDAX_OK
+               : LUDAX_ERR_CUDA;
 }
 
 }  // namespace
@@ -754,9 +852,18 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
     n->ob3 = n->ow3 + kH;
     n->nparams = n->ob3 + 1;
     const long long B = max_batch;
-    const int max_splits = 32;
-    n->part_floats = std::max<long long>((long long)max_splits * kH * std::max(kH, n->kpad),
-                                         3ll * ((B + HB_ROWS - 1) / HB_ROWS) * kH + 64);
+    const int max_splits = 32, sms = device_sms();
+    if (sms <= 0) {
+        delete n;
+        return LUDAX_ERR_CUDA;
+    }
+    const long long chunks = (B + HB_ROWS - 1) / HB_ROWS;
+    auto up4 = [](long long x) { return (x + 3) / 4 * 4; };  // regions start 16-byte aligned
+    n->cp_rows = std::max<long long>(chunks, 4ll * sms);      // colsum_kernel's chunks or the tcgen05 row groups
+    n->w2_floats = (long long)max_splits * kH * kH;
+    n->w1_floats = (long long)max_splits * kH * n->kpad;
+    const long long zp_f = 2 * B, hp_f = up4(chunks * HB_COLS), cp_f = n->cp_rows * kH;
+    const long long part_floats = zp_f + hp_f + cp_f + n->w2_floats + n->w1_floats;
     bool ok = cudaMalloc(&n->p, 4 * n->nparams * sizeof(float)) == cudaSuccess;
     if (ok) {
         n->m = n->p + n->nparams;
@@ -775,12 +882,16 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
         n->dZ1 = n->dZ2 + (size_t)B * kH;
         n->Xleaf = n->dZ1 + (size_t)B * kH;
     }
-    ok = ok && cudaMalloc(&n->pout, sizeof(float) * (4 * (size_t)B + n->part_floats)) == cudaSuccess;
+    ok = ok && cudaMalloc(&n->pout, sizeof(float) * (4 * (size_t)B + part_floats)) == cudaSuccess;
     if (ok) {
         n->g3 = n->pout + B;
         n->sqerr = n->g3 + B;
         n->score = n->sqerr + B;
-        n->part = n->score + B;
+        n->zp = n->score + B;
+        n->hp = n->zp + zp_f;
+        n->cp = n->hp + hp_f;
+        n->w2p = n->cp + cp_f;
+        n->w1p = n->w2p + n->w2_floats;
     }
     ok = ok && cudaMalloc(&n->done, (size_t)B) == cudaSuccess;
     if (!ok) {
@@ -856,20 +967,24 @@ int ludax_net_grad(ludax_net* n, const uint16_t* x_dev, const float* y_dev, int6
     if ((uintptr_t)x_dev % 16) return LUDAX_ERR_ALIGN;
     const __nv_bfloat16* X = reinterpret_cast<const __nv_bfloat16*>(x_dev);
     if ((st = net_forward(n, X, B, n->pout, y_dev))) return st;
-    if ((st = net_backward(n, X, B, loss_dev))) return st;
+    if ((st = net_backward(n, X, B, y_dev, loss_dev, nullptr))) return st;
     if (grad_dev && cudaMemcpyAsync(grad_dev, n->g, sizeof(float) * n->nparams, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess)
         return LUDAX_ERR_CUDA;
     return LUDAX_OK;
 }
 
 int ludax_net_train_step(ludax_net* n, const uint16_t* x_dev, const float* y_dev, int64_t B, float lr, float* loss_dev) {
-    int st = ludax_net_grad(n, x_dev, y_dev, B, nullptr, loss_dev);
+    int st = net_check(n, B);
     if (st) return st;
-    n->t += 1;
-    const float bc1 = 1.f - powf(0.9f, (float)n->t), bc2 = 1.f - powf(0.999f, (float)n->t);
-    adam_kernel<<<blocks_for(n->nparams, 256), 256, 0, n->stream>>>(
-        n->p, n->m, n->v, n->g, n->nparams, lr, bc1, bc2, BfCopy{n->W1b, n->ob1, n->oW2, n->ob2, n->ow3, n->ob3});
-    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    if (!x_dev || !y_dev) return LUDAX_ERR_ARG;
+    if ((uintptr_t)x_dev % 16) return LUDAX_ERR_ALIGN;
+    const __nv_bfloat16* X = reinterpret_cast<const __nv_bfloat16*>(x_dev);
+    const int t = n->t + 1;
+    const AdamStep adam{lr, 1.f - powf(0.9f, (float)t), 1.f - powf(0.999f, (float)t)};
+    if ((st = net_forward(n, X, B, n->pout, y_dev))) return st;
+    if ((st = net_backward(n, X, B, y_dev, loss_dev, &adam))) return st;
+    n->t = t;
+    return LUDAX_OK;
 }
 
 int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld) {

@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                            const __grid_constant__ CUtensorMap tmOut, int M, int N, int K,
                            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ w3,
                            float* __restrict__ zpart, int store) {
+    ludax::pdl_wait();
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + RING;  // 1024-byte aligned: the 128-byte swizzle pattern repeats every 1024 bytes
@@ -530,7 +531,14 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
 // (or N) contiguous elements, which is how activations and gradients
 // [batch][unit] look when the contraction runs over the batch.
 //   GRAD_MASK    : out = bf16(mask > 0 ? A . B : 0) -- dZ1 = (dZ2 . W2) *
-//                  [H1 > 0] with A = dZ2 K-major and B = W2 MN-major;
+//                  [H1 > 0] with A = dZ2 K-major and B = W2 MN-major; with
+//                  colpart given, also the column sums of the stored values
+//                  (db1 = sum_b dZ1): each epilogue warp reads every staging
+//                  box it fills back column-wise (lane l: columns 2l, 2l+1),
+//                  keeps those running sums over all its tiles (the grid is a
+//                  multiple of N / 256, so a CTA's tiles share their
+//                  columns) and writes them once, as row (CTA / (N / 256)) *
+//                  4 + warp of colpart [rows][N];
 //   GRAD_PARTIAL : part[split][m][n] = FP32 sum over the split's share of K
 //                  of A[k][m] B[k][n] -- dW2 = dZ2^T . H1 and dW1 = dZ1^T . X,
 //                  both operands MN-major; the batch is split so that
@@ -575,6 +583,21 @@ __device__ __forceinline__ void umma_bf16_major(uint32_t d_tmem, uint64_t adesc,
         : "memory");
 }
 
+// Column sums of a completed 32-row x 64-column BF16 staging box (the
+// 128-byte-swizzle layout stage_chunk writes): lane l adds columns 2l and
+// 2l + 1 down the 32 rows into a0, a1, in row order.  Each row is one
+// 4-byte shared load per lane; a row's 16-byte chunks sit at chunk ^ (row
+// % 8), so the 32 lanes of a row read 32 distinct banks.
+__device__ __forceinline__ void box_colsum(const uint8_t* box, int lane, float& a0, float& a1) {
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) {
+        const uint32_t u =
+            *reinterpret_cast<const uint32_t*>(box + r * (OUT_BOX * 2) + (((lane >> 2) ^ (r & 7)) * 16) + (lane & 3) * 4);
+        a0 += __uint_as_float(u << 16);
+        a1 += __uint_as_float(u & 0xFFFF0000u);
+    }
+}
+
 // 32-column chunks c0 .. c0 + NCH - 1 of one accumulator as raw FP32 bits:
 // fn(c, x) with this lane's 32 values; the next chunk's load is in flight
 // while fn runs.
@@ -599,7 +622,9 @@ template <bool A_MN, bool B_MN, int EPI>
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
     umma_grad_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmOut, int M, int N, int kblocks, int splits,
-                     const __nv_bfloat16* __restrict__ mask, int ldm, float* __restrict__ part) {
+                     const __nv_bfloat16* __restrict__ mask, int ldm, float* __restrict__ part,
+                     float* __restrict__ colpart) {
+    ludax::pdl_wait();
     constexpr int NS = GradCfg<EPI>::stages;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -703,6 +728,9 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     } else {  // epilogue warps 2..5: TMEM lane quarter = warp % 4
         const int q = warp & 3;
         uint8_t* wmask = smask + q * MASK_WARP_BYTES;
+        float csum[TN / 32];  // GRAD_MASK with colpart: columns 64 b + 2 lane, + 1 of box b, summed over the tiles
+#pragma unroll
+        for (int c = 0; c < TN / 32; ++c) csum[c] = 0.f;
         int local = 0;
         for (int u = blockIdx.x; u < units; u += gridDim.x, ++local) {
             int m0, n0, sp, kb0, kb1;
@@ -749,12 +777,22 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                         }
                     }
                     stage_chunk<1>(c, v, staging + q * BOX_BYTES, lane, &tmOut, n0, row0);
+                    // a full box (its store just issued reads it too; the box is
+                    // refilled only after the store has read it and this warp moved on)
+                    if (colpart && (c & 1)) box_colsum(staging + q * BOX_BYTES, lane, csum[c - 1], csum[c]);
                 }
             });
             tc_fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
         }
-        if (EPI == GRAD_MASK) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // nothing in flight at exit
+        if (EPI == GRAD_MASK) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // nothing in flight at exit
+            if (colpart) {
+                float* dst = colpart + (size_t)((blockIdx.x / ntn) * 4 + q) * N + (blockIdx.x % ntn) * TN + 2 * lane;
+#pragma unroll
+                for (int b = 0; b < TN / 64; ++b) *reinterpret_cast<float2*>(dst + b * 64) = make_float2(csum[2 * b], csum[2 * b + 1]);
+            }
+        }
     }
     if (!ok) atomicOr(&g_umma_error, 1);
     if (warp >= 2 && lane == 0) tma_store_wait_all();
@@ -867,24 +905,42 @@ int umma_dense_relu_ex(const void* A, int lda, const void* B, int ldb, const flo
     if (!sms || ensure_smem_limit((const void*)umma_dense_relu_kernel, UMMA_SMEM)) return LUDAX_ERR_CUDA;
     const int ntiles = (M / TM) * (N / TN);
     const int grid = ntiles < sms ? ntiles : sms;
-    umma_dense_relu_kernel<<<grid, UMMA_THREADS, UMMA_SMEM, s>>>(ma, mb, mo, M, N, K, bias,
-                                                                  static_cast<const __nv_bfloat16*>(w3), zpart,
-                                                                  store ? 1 : 0);
-    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    return launch_dependent(umma_dense_relu_kernel, (unsigned)grid, UMMA_THREADS, UMMA_SMEM, s, ma, mb, mo, M, N, K,
+                            bias, static_cast<const __nv_bfloat16*>(w3), zpart, store ? 1 : 0) == cudaSuccess
+               ? LUDAX_OK
+               : LUDAX_ERR_CUDA;
+}
+
+// grid of a backward launch: one CTA per SM at most, a multiple of the
+// column tiles N / 256 (so a persistent CTA's tiles all cover the same
+// columns; there are always at least that many units)
+static int grad_grid(int units, int ntn, int sms) {
+    int g = units < sms ? units : sms;
+    g -= g % ntn;
+    return g < ntn ? ntn : g;
 }
 
 template <bool A_MN, bool B_MN, int EPI>
 static int launch_grad(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mo, int M, int N, int kblocks,
-                       int splits, const void* mask, int ldm, float* part, int sms, cudaStream_t s) {
+                       int splits, const void* mask, int ldm, float* part, float* colpart, int sms, cudaStream_t s) {
     auto k = umma_grad_kernel<A_MN, B_MN, EPI>;
     if (ensure_smem_limit((const void*)k, GradCfg<EPI>::smem)) return LUDAX_ERR_CUDA;
     const int units = (M / TM) * (N / TN) * splits;
-    k<<<units < sms ? units : sms, UMMA_THREADS, GradCfg<EPI>::smem, s>>>(
-        ma, mb, mo, M, N, kblocks, splits, static_cast<const __nv_bfloat16*>(mask), ldm, part);
-    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    return launch_dependent(k, (unsigned)grad_grid(units, N / TN, sms), UMMA_THREADS, GradCfg<EPI>::smem, s, ma, mb,
+                            mo, M, N, kblocks, splits, static_cast<const __nv_bfloat16*>(mask), ldm, part,
+                            colpart) == cudaSuccess
+               ? LUDAX_OK
+               : LUDAX_ERR_CUDA;
 }
 
-int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, cudaStream_t s) {
+int umma_grad_colrows(int M, int N) {
+    const int sms = device_sms();
+    if (!sms || !umma_dense_supported(M, N, TK)) return 0;
+    return grad_grid((M / TM) * (N / TN), N / TN, sms) / (N / TN) * 4;
+}
+
+int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, float* colpart,
+                   cudaStream_t s) {
     if (!umma_dense_supported(M, N, K) || !A || !B || !mask || !out || N % 8 || K % 8 || ((uintptr_t)A % 16) ||
         ((uintptr_t)B % 16) || ((uintptr_t)mask % 16) || ((uintptr_t)out % 16))
         return LUDAX_ERR_SIZE;
@@ -894,7 +950,8 @@ int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, in
     // A [M][K] K-major; B [K][N] MN-major (64 x 64 boxes); out [M][N] in 32-row boxes
     if (!make_map(&ma, A, M, K, TM, K) || !make_map(&mb, B, K, N, 64, N) || !make_map(&mo, out, M, N, 32, N))
         return LUDAX_ERR_CUDA;
-    return launch_grad<false, true, GRAD_MASK>(ma, mb, mo, M, N, K / TK, 1, mask, N, nullptr, sms, s);
+    if (colpart && ((uintptr_t)colpart % 8)) return LUDAX_ERR_SIZE;
+    return launch_grad<false, true, GRAD_MASK>(ma, mb, mo, M, N, K / TK, 1, mask, N, nullptr, colpart, sms, s);
 }
 
 int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* part,
@@ -914,7 +971,8 @@ int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int
     // A [K][M] and B [K][N], both MN-major (64 x 64 boxes); nothing is stored through a tensor map
     if (!make_map(&ma, A, K, M, 64, lda) || !make_map(&mb, B, K, N, 64, ldb)) return LUDAX_ERR_CUDA;
     *splits_out = (int)splits;
-    return launch_grad<true, true, GRAD_PARTIAL>(ma, mb, ma, M, N, kblocks, (int)splits, nullptr, 0, part, sms, s);
+    return launch_grad<true, true, GRAD_PARTIAL>(ma, mb, ma, M, N, kblocks, (int)splits, nullptr, 0, part, nullptr,
+                                                 sms, s);
 }
 
 int umma_mlp_scratch_rows() { return device_sms() * 2 * TM; }
