@@ -122,6 +122,10 @@ int umma_mlp_scratch_rows();
 int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
                   const float* b2, const void* w3, float* zpart, void* scratch, int scratch_rows, int M,
                   cudaStream_t s);
+// The same launch for training: layer 1's rows kept in H1 [M][512] and layer
+// 2's in H2 [M][512] (BF16), zpart as above (four partials per row).
+int umma_mlp_train(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
+                   const float* b2, const void* w3, float* zpart, void* H1, void* H2, int M, cudaStream_t s);
 
 // The value net's backward contractions on tcgen05 (ludax_umma.cu).
 // umma_grad_mask: out[m][n] = bf16(mask[m][n] > 0 ? sum_k A[m][k] B[k][n] : 0)

@@ -261,20 +261,21 @@ __device__ __forceinline__ void load8(const __nv_bfloat16* p, float* f) {
 // partials in row blockIdx.x of part[chunks][HB_COLS]: db2 = sum_b dZ2
 // (unrounded), dw3 = sum_b g3 H2, db3 = sum_b g3 and the summed squared
 // error -- b2, w3, b3 in the order the gradient vector stores them.
-// With zpart given (the second layer's fused head: two partial dot products
-// per row) the row's g3 and squared error are formed here from z, y and b3,
+// With zpart given (the training forward's fused head: zparts partial dot
+// products per row) the row's g3 and squared error are formed here from z, y and b3,
 // as head_finish_kernel does; otherwise they are read from g3 / sqerr.
-__device__ __forceinline__ void head_row(const float* zpart, const float* y, const float* b3, int B, int r,
-                                         float& g, float& se) {
+constexpr int ZPARTS = 4;  // head partials per row of the one-launch training forward (umma_mlp_train)
+__device__ __forceinline__ void head_row(const float* zpart, int parts, const float* y, const float* b3, int B,
+                                         int r, float& g, float& se) {
     float z = 0.f;
-    for (int i = 0; i < kH / 256; ++i) z += zpart[(size_t)r * (kH / 256) + i];
+    for (int i = 0; i < parts; ++i) z += zpart[(size_t)r * parts + i];
     const float v = tanhf(z + b3[0]), p = 0.5f * (v + 1.f), d = p - y[r];
     g = d * (1.f - v * v) / (float)B;  // 2 (p-y)/B * (1/2) (1 - v^2)
     se = d * d;
 }
 __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16* w3,
                                                             const float* g3, const float* sqerr, const float* zpart,
-                                                            const float* y, const float* b3, int B,
+                                                            int zparts, const float* y, const float* b3, int B,
                                                             __nv_bfloat16* dZ2, float* part) {
     pdl_wait();
     __shared__ float sh[HB_GROUPS - 1][HB_COLS];
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
     const int r0 = blockIdx.x * HB_ROWS, r1 = min(r0 + HB_ROWS, B);
     for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) {  // each row's loss gradient once
         float gr, se;
-        if (zpart) head_row(zpart, y, b3, B, r0 + i, gr, se);
+        if (zpart) head_row(zpart, zparts, y, b3, B, r0 + i, gr, se);
         else gr = g3[r0 + i], se = sqerr[r0 + i];
         sg[i] = gr;
         ss[i] = se;
@@ -638,11 +639,12 @@ struct ludax_net {
     __nv_bfloat16 *W1b, *W2b, *w3b;
     __nv_bfloat16 *H1, *H2, *dZ2, *dZ1, *Xleaf;
     float *pout, *g3, *sqerr, *score;
-    // backward partial sums (see finish_kernel): the second layer's head
-    // partials [B][2], the head's row-chunk sums, db1's row-group sums and the
-    // split-K sums of dW2 and dW1
+    // backward partial sums (see finish_kernel): the training forward's head
+    // partials [B][ZPARTS], the head's row-chunk sums, db1's row-group sums
+    // and the split-K sums of dW2 and dW1
     float *zp, *hp, *cp, *w2p, *w1p;
     long long cp_rows, w2_floats, w1_floats;
+    int zparts;  // head partials per row the last training forward left in zp
     uint8_t* done;
     __nv_bfloat16* mlp_scratch;  // layer-1 rows of the fused inference kernel (allocated on first use)
     float* mlp_z;                // its head partials, 4 per row
@@ -742,13 +744,21 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
     }
     int st;
     if (tc_layers(n, B)) {
-        // training forward: layer 1 reads the input columns up to the next
-        // multiple of 64 past the last used one (the rest are zero by the
-        // input contract); the second layer stores its rows for the backward
-        // pass and takes the head's dot products in the same epilogue (two
-        // partials per row), from which the backward pass's first kernel
-        // forms the loss gradient
+        // training forward: both layers in one launch (layer 1's rows pass
+        // through L2 on their way to layer 2 and are kept, as are layer 2's;
+        // tensor path 2 keeps two launches);
+        // layer 1 reads the input columns up to the next multiple of 64 past
+        // the last used one (the rest are zero by the input contract); the
+        // head's dot products come out as four partials per row, from which
+        // the backward pass's first kernel forms the loss gradient
         const int k1 = std::min(n->kpad, (n->kin + 63) / 64 * 64);
+        if (n->use_tcgen05 == 1) {
+            n->zparts = ZPARTS;
+            return umma_mlp_train(X, n->kpad, k1, n->W1b, n->kpad, n->p + n->ob1, n->W2b, n->p + n->ob2, n->w3b,
+                                  n->zp, n->H1, n->H2, (int)B, s);
+        }
+        // the two-launch form (tensor path 2): the second layer's epilogue takes two head partials per row
+        n->zparts = kH / 256;
         if ((st = umma_dense_relu_ex(X, n->kpad, n->W1b, n->kpad, n->p + n->ob1, n->H1, kH, nullptr, nullptr, (int)B,
                                      kH, k1, s)))
             return st;
@@ -777,7 +787,7 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
     const bool tc = tc_layers(n, B);
     if (launch_dependent(head_backward_kernel, (unsigned)chunks, 256, 0, s, (const __nv_bfloat16*)n->H2,
                          (const __nv_bfloat16*)n->w3b, (const float*)n->g3, (const float*)n->sqerr,
-                         (const float*)(tc ? n->zp : nullptr), y, (const float*)(n->p + n->ob3), (int)B, n->dZ2,
+                         (const float*)(tc ? n->zp : nullptr), n->zparts, y, (const float*)(n->p + n->ob3), (int)B, n->dZ2,
                          n->hp) != cudaSuccess)
         return LUDAX_ERR_CUDA;
     // dZ1 = (dZ2 . W2) * [H1 > 0], and db1 = its column sums as partial rows
@@ -862,7 +872,7 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
     n->cp_rows = std::max<long long>(chunks, 4ll * sms);      // colsum_kernel's chunks or the tcgen05 row groups
     n->w2_floats = (long long)max_splits * kH * kH;
     n->w1_floats = (long long)max_splits * kH * n->kpad;
-    const long long zp_f = 2 * B, hp_f = up4(chunks * HB_COLS), cp_f = n->cp_rows * kH;
+    const long long zp_f = ZPARTS * B, hp_f = up4(chunks * HB_COLS), cp_f = n->cp_rows * kH;
     const long long part_floats = zp_f + hp_f + cp_f + n->w2_floats + n->w1_floats;
     bool ok = cudaMalloc(&n->p, 4 * n->nparams * sizeof(float)) == cudaSuccess;
     if (ok) {

@@ -356,6 +356,10 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
 // epilogue warps split it: warps w and w + 4 share TMEM lane quarter w % 4
 // and take one 128-column half each; a row's head therefore has four
 // partials, zpart[m * 4 + 2 * (column half of the tile) + (half of it)].
+// Training form (train != 0): layer 1's rows go to the block's own rows of
+// H1 (tmHst / tmHld over H1) instead of a scratch slot -- read back one block
+// later while still in L2, and kept for the backward pass -- and layer 2's
+// epilogue stores its rows to H2 (tmH2) besides the head's partials.
 constexpr int MLP_N = 512;
 constexpr int MLP_STAGES = 3, MLP_EPI_WARPS = 8, MLP_THREADS = 32 * (2 + MLP_EPI_WARPS);
 constexpr int MLP_STAGING = 2 * BOX_BYTES;  // per epilogue warp: two alternating boxes
@@ -385,9 +389,10 @@ __device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence
 __global__ void __launch_bounds__(MLP_THREADS, 1)
     umma_mlp_head_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
                          const __grid_constant__ CUtensorMap tmHst, const __grid_constant__ CUtensorMap tmHld,
-                         const __grid_constant__ CUtensorMap tmW2, int M, int K1, const float* __restrict__ b1,
-                         const float* __restrict__ b2, const __nv_bfloat16* __restrict__ w3,
-                         float* __restrict__ zpart) {
+                         const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH2, int M,
+                         int K1, const float* __restrict__ b1, const float* __restrict__ b2,
+                         const __nv_bfloat16* __restrict__ w3, float* __restrict__ zpart, int train) {
+    ludax::pdl_wait();
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + MLP_STAGES * STAGE;
@@ -455,7 +460,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
                         tma_load_2d(dst, &tmX, &full[st], kt * TK, gblk * TM);
                         tma_load_2d(dst + A_TILE, &tmW1, &full[st], kt * TK, jb.h * TN);
                     } else {
-                        tma_load_2d(dst, &tmHld, &full[st], kt * TK, scratch0 + (jb.blk & 1) * TM);
+                        tma_load_2d(dst, &tmHld, &full[st], kt * TK, train ? gblk * TM : scratch0 + (jb.blk & 1) * TM);
                         tma_load_2d(dst + A_TILE, &tmW2, &full[st], kt * TK, jb.h * TN);
                     }
                 }
@@ -498,13 +503,19 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
             const int n0 = jb.h * TN;
             const bool l1 = jb.phase == 1;
             const float* sbias = l1 ? sb1 : sb2;
-            const int srow0 = scratch0 + (jb.blk & 1) * TM + q * 32;  // layer 1's rows of this warp in scratch
+            // layer 1's rows of this warp: in scratch, or (training) in H1, where layer 2's rows go to H2 too
+            const int grow0 = gblk * TM + q * 32;
+            const int srow0 = train ? grow0 : scratch0 + (jb.blk & 1) * TM + q * 32;
             uint8_t* box = staging + (warp - 2) * MLP_STAGING;
             const uint32_t base = tmem + (uint32_t)(a * TN) + ((uint32_t)(q * 32) << 16);
             float z = 0.f;
             drain_accumulator<TN / 64>(base, half * (TN / 64), sbias + n0, [&](int c, const __nv_bfloat162* v) {
-                if (l1) stage_chunk<2>(c, v, box, lane, &tmHst, n0, srow0);  // layer 1: rows to scratch
-                else z += dot_chunk(v, sw3 + n0 + c * 32);                   // layer 2: the head's dot product
+                if (l1) {
+                    stage_chunk<2>(c, v, box, lane, &tmHst, n0, srow0);  // layer 1: rows to scratch / H1
+                } else {
+                    z += dot_chunk(v, sw3 + n0 + c * 32);  // layer 2: the head's dot product
+                    if (train) stage_chunk<2>(c, v, box, lane, &tmH2, n0, grow0);
+                }
             });
             if (!l1) zpart[((size_t)gblk * TM + q * 32 + lane) * 4 + jb.h * 2 + half] = z;
             tc_fence_before();
@@ -993,9 +1004,32 @@ int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, cons
         !make_map(&mw2, W2, MLP_N, MLP_N, TN, MLP_N))
         return LUDAX_ERR_CUDA;
     if (ensure_smem_limit((const void*)umma_mlp_head_kernel, MLP_SMEM)) return LUDAX_ERR_CUDA;
-    umma_mlp_head_kernel<<<grid, MLP_THREADS, MLP_SMEM, s>>>(mx, mw1, mhs, mhl, mw2, M, K1, b1, b2,
-                                                              static_cast<const __nv_bfloat16*>(w3), zpart);
-    return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
+    // no H2 is stored: its map is a valid placeholder over the scratch
+    return launch_dependent(umma_mlp_head_kernel, (unsigned)grid, MLP_THREADS, MLP_SMEM, s, mx, mw1, mhs, mhl, mw2, mhs,
+                            M, K1, b1, b2, static_cast<const __nv_bfloat16*>(w3), zpart, 0) == cudaSuccess
+               ? LUDAX_OK
+               : LUDAX_ERR_CUDA;
+}
+
+int umma_mlp_train(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
+                   const float* b2, const void* w3, float* zpart, void* H1, void* H2, int M, cudaStream_t s) {
+    if (M <= 0 || M % TM || K1 <= 0 || K1 % TK || K1 > ldx || K1 > ldw1 || ldx % 8 || ldw1 % 8 || !zpart || !H1 ||
+        !H2 || ((uintptr_t)X % 16) || ((uintptr_t)W1 % 16) || ((uintptr_t)W2 % 16) || ((uintptr_t)H1 % 16) ||
+        ((uintptr_t)H2 % 16))
+        return LUDAX_ERR_SIZE;
+    const int sms = device_sms();
+    if (!sms) return LUDAX_ERR_CUDA;
+    const int nblk = M / TM, grid = nblk < sms ? nblk : sms;
+    CUtensorMap mx, mw1, mhs, mhl, mw2, mh2;
+    if (!make_map(&mx, X, M, K1, TM, ldx) || !make_map(&mw1, W1, MLP_N, K1, TN, ldw1) ||
+        !make_map(&mhs, H1, M, MLP_N, 32, MLP_N) || !make_map(&mhl, H1, M, MLP_N, TM, MLP_N) ||
+        !make_map(&mw2, W2, MLP_N, MLP_N, TN, MLP_N) || !make_map(&mh2, H2, M, MLP_N, 32, MLP_N))
+        return LUDAX_ERR_CUDA;
+    if (ensure_smem_limit((const void*)umma_mlp_head_kernel, MLP_SMEM)) return LUDAX_ERR_CUDA;
+    return launch_dependent(umma_mlp_head_kernel, (unsigned)grid, MLP_THREADS, MLP_SMEM, s, mx, mw1, mhs, mhl, mw2, mh2,
+                            M, K1, b1, b2, static_cast<const __nv_bfloat16*>(w3), zpart, 1) == cudaSuccess
+               ? LUDAX_OK
+               : LUDAX_ERR_CUDA;
 }
 
 }  // namespace ludax

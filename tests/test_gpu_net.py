@@ -188,7 +188,8 @@ def check_gradient(g, theta, X, y, K, cells, loss=None):
 # 42 cells: 85 inputs padded to 128 columns, so dW1 (N = 128, not a multiple
 # of the 256-column tile) stays on mma.sync while the rest runs on tcgen05.
 @pytest.mark.parametrize("cells,B", [(64, 512), (121, 256), (64, 128), (64, 4736), (42, 384)])
-@pytest.mark.parametrize("path", [1, 0])  # tcgen05 backward, mma.sync backward
+# tensor path 1: both forward layers in one launch; 2: one launch per layer; 0: mma.sync throughout
+@pytest.mark.parametrize("path", [1, 2, 0])
 def test_gradient_matches_oracle(L, cells, B, path):
     K = W.net_in_pad(cells)
     theta = W.init_params(cells, 3)
@@ -206,7 +207,8 @@ def test_gradient_matches_oracle(L, cells, B, path):
 
 def test_gradient_training_batch(L):
     """The training batch (65,536 rows of Othello inputs): the tcgen05
-    backward against the fp64 oracle, and against the mma.sync backward."""
+    forward and backward (one-launch and per-layer forward) against the fp64
+    oracle, and against the mma.sync path."""
     cells, B = 64, 65536
     K = W.net_in_pad(cells)
     theta = W.init_params(cells, 9)
@@ -218,12 +220,13 @@ def test_gradient_training_batch(L):
     net.set_params(torch.from_numpy(theta).cuda())
     xb, yb = bf16_bits(X), torch.from_numpy(y.astype(np.float32)).cuda()
     grads = {}
-    for path in (1, 0):
+    for path in (1, 2, 0):
         net.set_tensor_path(path)
         g, _ = net.grad(xb, yb)
         grads[path] = g.cpu().numpy().astype(np.float64)
     assert L.ludax_device_error() == 0
     check_gradient(grads[1], theta, X, y, K, cells)
+    check_gradient(grads[2], theta, X, y, K, cells)
     a, b = grads[1], grads[0]
     assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-2
 
