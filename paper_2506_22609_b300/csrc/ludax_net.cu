@@ -400,10 +400,11 @@ struct BfCopy {
 //   cp  [crows][kH]                         row-group sums of db1;
 //   hp  [hrows][HB_COLS]                    row-chunk sums of db2 | dw3 |
 //                                           db3 | squared error.
-// Blocks [0, nwide) take W1 and W2, four elements per thread, adding the
-// splits in order; each later block takes 32 columns of cp, then of hp:
-// its 32 warps stride down the rows (lane = column) and the 32 warp sums
-// are added in a fixed order.  The loss is the squared-error column / B.
+// The first FIN_LONG blocks take 32 columns each of cp, then of hp: their
+// warps stride down the rows (lane = column) and the warp sums are added in
+// a fixed order; the nwide blocks after them take W1 and W2, four elements
+// per thread, adding the splits in order.  The loss is the squared-error
+// column / B.
 struct FinishArgs {
     const float *w1p, *w2p, *cp, *hp;
     int s1, s2, crows, hrows;
@@ -436,55 +437,59 @@ __device__ __forceinline__ void apply_grad(const FinishArgs& a, long long i, flo
     else if (i >= c.ow3 && i < c.ob3) c.bf[i - 2 * kH] = __float2bfloat16_rn(pi);
 }
 
-constexpr int FIN_THREADS = 1024;
+constexpr int FIN_THREADS = 256, FIN_WARPS = FIN_THREADS / 32;
+constexpr int FIN_LONG = kH / 32 + (HB_COLS + 31) / 32;  // blocks of 32 bias / head columns
 
 __global__ void __launch_bounds__(FIN_THREADS) finish_kernel(FinishArgs a) {
     pdl_wait();
-    if ((int)blockIdx.x < a.nwide) {
-        const long long t = (long long)blockIdx.x * FIN_THREADS + threadIdx.x, e = 4 * t;
+    if ((int)blockIdx.x >= FIN_LONG) {  // W1 and W2: four elements per thread, 16 splits in flight
+        const long long t = (long long)(blockIdx.x - FIN_LONG) * FIN_THREADS + threadIdx.x, e = 4 * t;
         if (e >= a.n1 + a.n2) return;
         const bool w1 = e < a.n1;
         const float* src = w1 ? a.w1p + e : a.w2p + (e - a.n1);
         const long long stride = w1 ? a.n1 : a.n2, flat = w1 ? e : a.c.oW2 + (e - a.n1);
         const int splits = w1 ? a.s1 : a.s2;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int s0 = 0; s0 < splits; s0 += 8) {  // eight loads in flight, then added in split order
-            float4 x[8];
+        auto add = [&](const float4& x) {
+            acc.x += x.x;
+            acc.y += x.y;
+            acc.z += x.z;
+            acc.w += x.w;
+        };
+        int s0 = 0;
+        for (; s0 + 16 <= splits; s0 += 16) {  // 16 loads issued, then added in split order
+            float4 x[16];
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                x[k] = s0 + k < splits ? *reinterpret_cast<const float4*>(src + (size_t)(s0 + k) * stride)
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int k = 0; k < 16; ++k) x[k] = __ldcg(reinterpret_cast<const float4*>(src + (size_t)(s0 + k) * stride));
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                acc.x += x[k].x;
-                acc.y += x[k].y;
-                acc.z += x[k].z;
-                acc.w += x[k].w;
-            }
+            for (int k = 0; k < 16; ++k) add(x[k]);
         }
+        for (; s0 < splits; ++s0) add(__ldcg(reinterpret_cast<const float4*>(src + (size_t)s0 * stride)));
         apply_grad(a, flat, acc.x);
         apply_grad(a, flat + 1, acc.y);
         apply_grad(a, flat + 2, acc.z);
         apply_grad(a, flat + 3, acc.w);
         return;
     }
-    __shared__ float sh[32][33];
+    // 32 columns of the db1 row-group sums, then of the head's chunk sums: the
+    // warps stride down the rows (lane = column), eight rows in flight each
+    __shared__ float sh[FIN_WARPS][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int blk = (int)blockIdx.x - a.nwide;
+    int blk = (int)blockIdx.x;
     const bool bias1 = blk < kH / 32;
     if (!bias1) blk -= kH / 32;
     const int col = blk * 32 + lane, ncols = bias1 ? kH : HB_COLS, rows = bias1 ? a.crows : a.hrows;
     const float* src = bias1 ? a.cp : a.hp;
     float x = 0.f;
     if (col < ncols) {
-#pragma unroll 4
-        for (int r = w; r < rows; r += 32) x += src[(size_t)r * ncols + col];
+#pragma unroll 8
+        for (int r = w; r < rows; r += FIN_WARPS) x += src[(size_t)r * ncols + col];
     }
     sh[w][lane] = x;
     __syncthreads();
     if (w != 0 || col >= ncols) return;
     float t = 0.f;
-    for (int k = 0; k < 32; ++k) t += sh[k][lane];
+    for (int k = 0; k < FIN_WARPS; ++k) t += sh[k][lane];
     if (bias1) apply_grad(a, a.c.ob1 + col, t);
     else if (col < kH) apply_grad(a, a.c.ob2 + col, t);
     else if (col < 2 * kH) apply_grad(a, a.c.ow3 + (col - kH), t);
@@ -832,7 +837,7 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
     f.c = BfCopy{n->W1b, n->ob1, n->oW2, n->ob2, n->ow3, n->ob3};
     f.loss = loss_out;
     f.inv_b = 1.f / (float)B;
-    return launch_dependent(finish_kernel, (unsigned)(f.nwide + kH / 32 + (HB_COLS + 31) / 32), FIN_THREADS, 0, s, f) ==
+    return launch_dependent(finish_kernel, (unsigned)(FIN_LONG + f.nwide), FIN_THREADS, 0, s, f) ==
                    cudaSuccess
                ? LUDAX_OK
                : LUDAX_ERR_CUDA;
