@@ -644,8 +644,10 @@ def bench_train_step(L, peaks, flush_buf, steps=20, warmup=3, B=65536):
     """One Adam step of the value net (forward with labels, backward, Adam)
     on a 65,536-row batch of Othello (129 inputs) and Hex 11 (243 inputs)
     rows, on the tcgen05 path and on the mma.sync path; the rows hold a
-    stone in 30% of the cells.  FLOPs per step: the forward, dZ1 and the two
-    weight gradients, 2 B (2 * in_pad * 512 + 3 * 512 * 512 + 512)."""
+    stone in 30% of the cells.  FLOPs per step as the tcgen05 kernels run
+    them: layer 1 over the input columns up to the next multiple of 64 (k1:
+    Othello 192, Hex 11 256), layer 2, the head, dZ1, dW2 and dW1 (over all
+    in_pad columns): 2 B (512 (k1 + in_pad) + 3 * 512 * 512 + 512)."""
     import torch
 
     from paper_2506_22609_b300 import workloads as W
@@ -658,13 +660,16 @@ def bench_train_step(L, peaks, flush_buf, steps=20, warmup=3, B=65536):
         x = (torch.rand(B, net.in_pad, device="cuda", generator=g) < 0.3).to(torch.bfloat16)
         x[:, 2 * cells + 1:] = 0
         xb, yb = x.view(torch.int16), torch.rand(B, device="cuda", generator=g)
-        flops = 2.0 * B * (2 * net.in_pad * 512 + 3 * 512 * 512 + 512)
-        # algorithmic HBM bytes of the step's dataflow: X read by layer 1 and dW1; H1 written and
-        # read by layer 2, the dZ1 mask and dW2; H2 written and read by the head's backward; dZ2
-        # written and read by dZ1 and dW2; dZ1 written and read by the bias sum and dW1 (BF16);
-        # Adam reads and writes parameters and both moments and reads the gradient (FP32)
-        nbytes = 2.0 * B * (2 * net.in_pad + 512 * (4 + 2 + 3 + 3)) + 4.0 * 7 * net.num_params
-        res = {"batch": B, "in_pad": net.in_pad, "gflop_per_step": round(flops / 1e9, 2),
+        k1 = min(net.in_pad, (2 * cells + 1 + 63) // 64 * 64)
+        flops = 2.0 * B * (512 * (k1 + net.in_pad) + 3 * 512 * 512 + 512)
+        # HBM bytes of the step's dataflow (BF16 activations): X read by layer 1 (k1 columns) and
+        # dW1 (in_pad); H1 written by the forward (which reads it back for layer 2 from L2, within
+        # the launch) and read by the dZ1 mask and dW2; H2 written and read by the head's
+        # backward; dZ2 written and read by dZ1 and dW2; dZ1 written (its column sums are taken
+        # in the same epilogue) and read by dW1; the finish kernel reads and writes parameters and
+        # both Adam moments and writes the BF16 weight copies (~7 FP32 words per parameter)
+        nbytes = 2.0 * B * (k1 + net.in_pad + 512 * (3 + 2 + 3 + 2)) + 4.0 * 7 * net.num_params
+        res = {"batch": B, "in_pad": net.in_pad, "layer1_columns": k1, "gflop_per_step": round(flops / 1e9, 2),
                "alg_mbytes_per_step": round(nbytes / 1e6, 1),
                "arithmetic_intensity_flop_per_byte": round(flops / nbytes, 1)}
         for path, name in ((1, "tcgen05"), (0, "mma_sync")):

@@ -437,18 +437,19 @@ int ludax_net_sizes(const ludax_net* net, int32_t* in_pad, int32_t* hidden, int6
 int ludax_net_set_params(ludax_net* net, const float* params_dev);
 int ludax_net_get_params(ludax_net* net, float* params_dev);
 /* Which kernels run the hidden-layer contractions:
- *   1 (default) tcgen05/TMEM: a forward without labels (ludax_net_forward,
- *     ludax_truncated_value) runs both layers and the head in one launch
- *     whose layer-1 rows stay in an L2-resident scratch; a training forward
- *     runs the two layers of ludax_dense_bf16_relu and keeps their rows for
- *     the backward pass, whose three contractions (dZ1 = (dZ2 W2) * [H1 > 0]
- *     and the weight gradients over the batch, split into FP32 partial sums)
- *     run on tcgen05 too; an input width that is not a multiple of 256 keeps
- *     dW1 on the mma.sync kernel;
+ *   1 (default) tcgen05/TMEM: a forward runs both layers and the head in one
+ *     launch, layer 1's rows passing through L2 to layer 2 (without labels,
+ *     ludax_net_forward and ludax_truncated_value, through a scratch; in
+ *     training into H1, kept with layer 2's rows for the backward pass); the
+ *     backward pass's three contractions (dZ1 = (dZ2 W2) * [H1 > 0] and the
+ *     weight gradients over the batch, split into FP32 partial sums) run on
+ *     tcgen05 too, and one launch reduces the partials and applies Adam; an
+ *     input width that is not a multiple of 256 keeps dW1 on the mma.sync
+ *     kernel;
  *   2 tcgen05/TMEM, always as two layer launches (the head fused into the
- *     second one's epilogue when there are no labels): the form used when the
- *     scratch cannot be allocated, selectable for comparison; the backward
- *     pass as in 1;
+ *     second one's epilogue): the form used for inference when the scratch
+ *     cannot be allocated, selectable for comparison; the backward pass as
+ *     in 1;
  *   0 the mma.sync kernel for every contraction (kept for comparison).
  * Results agree to FP32 rounding order across the three. */
 int ludax_net_set_tensor_path(ludax_net* net, int32_t use_tcgen05);

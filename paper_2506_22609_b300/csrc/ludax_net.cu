@@ -867,7 +867,7 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
     n->ob3 = n->ow3 + kH;
     n->nparams = n->ob3 + 1;
     const long long B = max_batch;
-    const int max_splits = 32, sms = device_sms();
+    const int max_splits = 48, sms = device_sms();  // split-K partials: the SM count over the tiles (37 for dW1 on 148 SMs)
     if (sms <= 0) {
         delete n;
         return LUDAX_ERR_CUDA;
