@@ -4,7 +4,8 @@
                     [--workload c4|ttt|othello|hex11|gomoku|pente|yavalath|line_c5|wolf_sheep|
                                 draughts|hasami_shogi|mixed|step_c4]
                     [--no-extras] [--no-cpu-baseline] [--only dense_layer|gavel_library|
-                     batch_sweep|value_net|value_estimator|int_peak|train_step|threads_per_env]
+                     batch_sweep|value_net|value_estimator|int_peak|train_step|threads_per_env|
+                     lanes_per_warp]
 
 One step = one fused playout launch over the whole batch: every env of the
 workload is reset to the start position and played to the end of its game
@@ -81,7 +82,7 @@ def parse():
                                                         "step_c4"])
     p.add_argument("--no-extras", action="store_true")
     p.add_argument("--only", choices=["dense_layer", "gavel_library", "batch_sweep", "value_net", "value_estimator",
-                                      "int_peak", "train_step", "threads_per_env"],
+                                      "int_peak", "train_step", "threads_per_env", "lanes_per_warp"],
                    default=None,
                    help="run one extra measurement alone and print its JSON (a small case for profilers)")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -748,6 +749,35 @@ def bench_threads_per_env(L, sizes=(7, 9, 11), batches=(1024, 4096, 16384, 65536
     return out
 
 
+def bench_lanes_per_warp(L, batches=(1024, 4096, 16384, 65536), seed=4, reps=3):
+    """The single-game autotuner over games and small batch sizes, reduced to
+    the fastest one-lane-per-env shape for each lanes-per-warp value (32 =
+    full warps, 16, 8): ms per launch from the start position and env steps
+    per second."""
+    import torch
+
+    games = (("ttt", 3, 3), ("c4", 6, 7), ("othello", 8, 8), ("hex", 7, 7), ("hex", 11, 11))
+    out = {}
+    for game, rows, cols in games:
+        for n in batches:
+            env = L.Env(game, rows, cols, n)
+            best, best_ms, table = L.ludax_autotune_env(env.handle, seed, reps=reps)
+            per = {}
+            for c, ms in table:
+                if c.threads_per_env > 1:
+                    continue
+                lanes = c.lanes_per_warp or 32
+                if lanes not in per or ms < per[lanes][1]:
+                    per[lanes] = (c.as_dict(), ms)
+            _, plies = env.rollout(seed, cfg=best)
+            spl = int(plies.to(dtype=torch.int64).sum().item())
+            out[f"{game}{rows}x{cols}_{n}env"] = {
+                str(k): {"ms": round(v[1], 4), "env_steps_per_s": round(spl / (v[1] / 1e3), 1), "launch": v[0]}
+                for k, v in sorted(per.items(), reverse=True)}
+            env.close()
+    return out
+
+
 def bench_int_peak(L, iters=1 << 16):
     """What a stream of one integer op reaches (LOP3, IADD, SHF, IMAD,
     IMAD.HI, and LOP3 + IMAD on alternate chains; 8 independent chains per
@@ -854,6 +884,8 @@ def main():
             res = bench_train_step(L, peaks, flush_buf, max(args.steps, 5), args.warmup)
         elif args.only == "threads_per_env":
             res = bench_threads_per_env(L)
+        elif args.only == "lanes_per_warp":
+            res = bench_lanes_per_warp(L)
         else:
             res = bench_batch_sweep(L, W, flush_buf)
         if rank == 0:

@@ -159,6 +159,12 @@ typedef struct {
                                 across the lanes, draws and end tests shared by warp
                                 shuffles; same results bit for bit); needs
                                 envs_per_thread 1 and compact_every 0                 */
+    int32_t lanes_per_warp;  /* lanes of each warp that hold envs: 0 or 32 = all; 8 or
+                                16 = single-game ludax_rollout only, the rest of the
+                                warp idle (small, latency-bound batches: fewer envs
+                                share a warp's issue slots and divergent branches);
+                                needs compact_every 0 and one lane per env; envs per
+                                warp = lanes_per_warp x envs_per_thread                */
 } ludax_launch_cfg;
 
 /* ---------------------------------------------------------------------------

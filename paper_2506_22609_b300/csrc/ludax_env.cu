@@ -325,11 +325,14 @@ struct RolloutArgs {
     const uint64_t* bits;        // non-null: start each env from this packed view instead
     const uint32_t* bits_meta;
     int bits_w, bits_v;
+    int lanes;                   // rollout_kernel: lanes of each warp that hold envs (1..32)
 };
 
 // One persistent kernel: each thread holds EPT envs in registers and advances
 // each by one ply per loop trip; a finished env is written out and replaced
 // by the next unclaimed env (claim_next).  Work index w < n maps to env w.
+// Only the first a.lanes lanes of each warp hold envs (the others leave once
+// the block's table is built): slot = warp * a.lanes + lane.
 // BITS: the envs start from the packed view in a.bits (the host-buffer path);
 // a separate instantiation, so the other launches carry none of its code.
 template <class G, int EPT, bool TABLE, bool BITS = false>
@@ -342,8 +345,11 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
         table = smem_table;
     }
     const int64_t n = a.d.n;
-    const int64_t slots = (int64_t)gridDim.x * blockDim.x * EPT;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    if (lane >= a.lanes) return;
+    const int64_t round = (int64_t)gridDim.x * (blockDim.x >> 5) * a.lanes;  // env slots per EPT round
+    const int64_t slots = round * EPT;
+    const int64_t tid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * a.lanes + lane;
     const bool refill = slots < n;
     G g[EPT];
     uint64_t key[EPT];
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(RolloutArgs a) {
     bool active[EPT];
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
-        env[i] = tid + (int64_t)i * gridDim.x * blockDim.x;
+        env[i] = tid + (int64_t)i * round;
         active[i] = env[i] < n;
         set_table(g[i], table);
     }
@@ -692,13 +698,16 @@ int launch_lanes(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& c
 }
 
 template <class G, bool BITS>
-int launch_rollout_as(ludax_env* env, const RolloutArgs& a, const ludax_launch_cfg& cfg) {
+int launch_rollout_as(ludax_env* env, const RolloutArgs& a0, const ludax_launch_cfg& cfg) {
     if constexpr (HexN<G>::value != 0 && !BITS) {
-        if (cfg.threads_per_env > 1) return launch_lanes<HexN<G>::value>(env, a, cfg);
+        if (cfg.threads_per_env > 1) return launch_lanes<HexN<G>::value>(env, a0, cfg);
     }
+    RolloutArgs a = a0;
+    a.lanes = (cfg.lanes_per_warp > 0 && cfg.lanes_per_warp < 32) ? cfg.lanes_per_warp : 32;
     const int block = cfg.block_threads;
     const int ept = BITS ? 1 : cfg.envs_per_thread;  // the packed-view path has one env per thread
-    int64_t need = (env->n + (int64_t)block * ept - 1) / ((int64_t)block * ept);
+    const int64_t per_block = (int64_t)(block / 32) * a.lanes * ept;  // env slots of one block
+    int64_t need = (env->n + per_block - 1) / per_block;
     int64_t grid = need;
     if (cfg.blocks_per_sm > 0) {
         int64_t cap = (int64_t)env->num_sms * cfg.blocks_per_sm;
@@ -707,7 +716,7 @@ int launch_rollout_as(ludax_env* env, const RolloutArgs& a, const ludax_launch_c
     const bool table = cfg.hex_nbr_table != 0 && HexN<G>::value != 0;
     size_t smem = table ? sizeof(B128) * G::kCells : 0;
     // the refill cursor is only read when the grid holds fewer slots than envs
-    if (grid * block * ept < env->n &&
+    if (grid * per_block < env->n &&
         cudaMemsetAsync(env->d_counters, 0, sizeof(unsigned long long), env->stream) != cudaSuccess)
         return LUDAX_ERR_CUDA;
     if (cfg.compact_every > 0) {
@@ -751,6 +760,9 @@ int check_cfg(const ludax_launch_cfg& c) {
     if (c.compact_every > 0 && c.envs_per_thread != 1) return LUDAX_ERR_ARG;
     if (c.threads_per_env < 0 || c.threads_per_env == 3 || c.threads_per_env > 4) return LUDAX_ERR_ARG;
     if (c.threads_per_env > 1 && (c.envs_per_thread != 1 || c.compact_every != 0)) return LUDAX_ERR_ARG;
+    if (c.lanes_per_warp != 0 && c.lanes_per_warp != 8 && c.lanes_per_warp != 16 && c.lanes_per_warp != 32)
+        return LUDAX_ERR_ARG;
+    if (c.lanes_per_warp % 32 != 0 && (c.compact_every != 0 || c.threads_per_env > 1)) return LUDAX_ERR_ARG;
     return LUDAX_OK;
 }
 
@@ -1011,7 +1023,7 @@ int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_d
     ludax_launch_cfg c = cfg ? *cfg : default_cfg();
     int st = check_cfg(c);
     if (st != LUDAX_OK) return st;
-    if (c.threads_per_env > 1) return LUDAX_ERR_ARG;  // one lane per env here
+    if (c.threads_per_env > 1 || c.lanes_per_warp % 32 != 0) return LUDAX_ERR_ARG;  // one lane per env, full warps
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
         const bool table = c.hex_nbr_table != 0 && HexN<G>::value != 0;
@@ -1125,6 +1137,10 @@ int ludax_autotune_env_candidates(const ludax_env* env, ludax_launch_cfg* out, i
                         if (ce > 0 && ept != 1) continue;
                         put(ludax_launch_cfg{b, s, ept, t, ce, 1});
                     }
+        // part-filled warps (one thread per env, no persistence): for small batches
+        for (int lanes : {8, 16})
+            for (int ept = 1; ept <= 2; ++ept)
+                for (int b : blocks) put(ludax_launch_cfg{b, 0, ept, t, 0, 1, lanes});
         if (hex)  // several lanes per env
             for (int tpe : {2, 4})
                 for (int b : blocks)

@@ -296,6 +296,7 @@ int check_mixed_cfg(const ludax_launch_cfg& c) {
     if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
     if (c.compact_every != 0) return LUDAX_ERR_ARG;  // compaction is a single-game option
     if (c.threads_per_env > 1 || c.threads_per_env < 0) return LUDAX_ERR_ARG;  // one lane per env
+    if (c.lanes_per_warp != 0 && c.lanes_per_warp != 32) return LUDAX_ERR_ARG;  // full warps
     return LUDAX_OK;
 }
 

@@ -61,7 +61,8 @@ class ludax_state_view(ctypes.Structure):
 class ludax_launch_cfg(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("envs_per_thread", ctypes.c_int32), ("hex_nbr_table", ctypes.c_int32),
-                ("compact_every", ctypes.c_int32), ("threads_per_env", ctypes.c_int32)]
+                ("compact_every", ctypes.c_int32), ("threads_per_env", ctypes.c_int32),
+                ("lanes_per_warp", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -71,9 +72,9 @@ class ludax_launch_cfg(ctypes.Structure):
 
 
 def make_cfg(block_threads=256, blocks_per_sm=0, envs_per_thread=1, hex_nbr_table=0, compact_every=0,
-             threads_per_env=1):
+             threads_per_env=1, lanes_per_warp=0):
     return ludax_launch_cfg(block_threads, blocks_per_sm, envs_per_thread, hex_nbr_table, compact_every,
-                            threads_per_env)
+                            threads_per_env, lanes_per_warp)
 
 
 _lib = None

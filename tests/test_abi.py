@@ -111,7 +111,7 @@ def test_mixed_launch_shape_checked_before_touching_the_device(L):
 
     fake = ctypes.c_void_p(1 << 20)  # never dereferenced: the shape is refused first
     for bad in [(128, 2, 2, 0, 0), (128, 0, 3, 0, 0), (128, 0, 8, 0, 0), (100, 0, 1, 0, 0), (128, 0, 1, 0, 4),
-                (128, 0, 1, 0, 0, 2)]:
+                (128, 0, 1, 0, 0, 2), (128, 0, 1, 0, 0, 1, 8)]:  # mixed batches run full warps
         cfg = ludax.make_cfg(*bad)
         assert L.ludax_rollout_mixed(fake, 10, 0, 0, fake, fake, ctypes.byref(cfg), None) == -1, bad
 

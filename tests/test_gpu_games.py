@@ -91,12 +91,41 @@ def test_launch_shape_does_not_change_results(L, name, game, rows, cols, cfg):
         assert o[0] == np_(out)[e] and p[0] == np_(plies)[e]
 
 
+# part-filled warps: only the first 8 or 16 lanes of each warp hold envs, one
+# thread per env or persistent (refilling), one or two envs per thread
+@pytest.mark.parametrize("cfg", [(256, 0, 1, 0, 0, 1, 8), (128, 0, 2, 1, 0, 1, 16), (64, 2, 1, 1, 0, 1, 8),
+                                 (512, 1, 2, 0, 0, 1, 16), (32, 0, 1, 0, 0, 1, 16)],
+                         ids=lambda c: "b{}_bps{}_ept{}_tab{}_lanes{}".format(c[0], c[1], c[2], c[3], c[6]))
+@pytest.mark.parametrize("name,game,rows,cols", [GAMES[0], GAMES[1], GAMES[2], GAMES[8], GAMES[11]],
+                         ids=["ttt", "c4", "othello", "hex11", "yavalath"])
+def test_part_filled_warps_match_oracle(L, name, game, rows, cols, cfg):
+    n, seed, off = (700 if game in BIG else 3001), 9, 321
+    env = L.Env(game, rows, cols, n, env_offset=off)
+    out, plies = env.rollout(seed, from_start=True, write_back=True, cfg=L.make_cfg(*cfg))
+    o_out, o_plies, o_boards = G.rollout_start(game, rows, cols, n, seed, env_offset=off, want_boards=True)
+    assert (np_(out) == o_out).all() and (np_(plies) == o_plies).all()
+    b, tm, ply, ps, oc = gpu_state(env)
+    assert (b == o_boards).all() and (oc == o_out).all()
+    assert env.counters() == (0, 0)
+
+
+def test_part_filled_warps_argument_checks(L):
+    env = L.Env("hex", 7, 7, 64)
+    for bad in [(64, 0, 1, 0, 0, 1, 4), (64, 0, 1, 0, 0, 1, 24), (64, 0, 1, 0, 4, 1, 8), (64, 0, 1, 0, 0, 2, 8)]:
+        with pytest.raises(L.LudaxError) as ei:  # 8, 16 or 32 lanes; no compaction, one lane per env
+            env.rollout(1, cfg=L.make_cfg(*bad))
+        assert ei.value.status == -1
+    with pytest.raises(L.LudaxError):  # the value playouts run full warps
+        env.rollout_value(1, 4, cfg=L.make_cfg(64, 0, 1, 0, 0, 1, 8))
+    env.close()
+
+
 @pytest.mark.parametrize("n", [1, 31, 33, 257])
 def test_ragged_and_tiny_batches(L, n):
     for name, game, rows, cols in (GAMES[0], GAMES[1], GAMES[2], GAMES[8], GAMES[9], GAMES[11]):
         env = L.Env(game, rows, cols, n)
         o, p, _ = G.rollout_start(game, rows, cols, n, 11)
-        for cfg in [(64, 1, 2, 0, 0), (64, 1, 1, 0, 4), (32, 1, 1, 1, 2)]:
+        for cfg in [(64, 1, 2, 0, 0), (64, 1, 1, 0, 4), (32, 1, 1, 1, 2), (64, 0, 1, 0, 0, 1, 8)]:
             out, plies = env.rollout(11, cfg=L.make_cfg(*cfg))
             assert (np_(out) == o).all() and (np_(plies) == p).all()
 

@@ -111,6 +111,7 @@ def test_env_autotuner_walks_lanes_per_env(L):
     env = L.Env("hex", 9, 9, 4096)
     cands = L.ludax_autotune_env_candidates(env.handle)
     assert {c.threads_per_env for c in cands} == {1, 2, 4}
+    assert {c.lanes_per_warp for c in cands} == {0, 8, 16}  # part-filled warps (one lane per env)
     best, best_ms, table = L.ludax_autotune_env(env.handle, 1, reps=1)
     assert len(table) == len(cands) and best_ms == min(ms for _, ms in table)
     env.close()
