@@ -142,10 +142,8 @@ typedef struct {
     int32_t block_threads;   /* threads per block: 32..512, multiple of 32           */
     int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid, >= 1;
                                 0 = one thread per env (no persistence)               */
-    int32_t envs_per_thread; /* single-game playouts: envs each thread advances
-                                together (ILP), 1 or 2; mixed batches with
-                                blocks_per_sm 0: queue positions each lane plays
-                                one after another, 1, 2 or 4 (1 when persistent)    */
+    int32_t envs_per_thread; /* envs each thread advances together (ILP): 1 or 2
+                                (single-game playouts; 1 for mixed batches)          */
     int32_t hex_nbr_table;   /* Hex neighbour test: 0 = bit shifts, 1 = shared-memory
                                 table of per-cell neighbour masks                     */
     int32_t compact_every;   /* single-game playouts only (0 for mixed batches): 0 =

@@ -57,7 +57,6 @@ struct MixedArgs {
     int16_t* plies;
     unsigned long long* cursor;      // per-bucket claim cursors, zeroed before each launch
     const long long* bucket_end_dev; // non-null: the bucket ends were built on the device (host-buffer path)
-    int seq;                         // one-thread-per-env launch: queue positions each lane plays in turn (1, 2, 4)
 };
 // The mixed kernel takes exactly one parameter (MixedArgs): the graph plan
 // rewrites that single parameter before each replay.
@@ -204,14 +203,7 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         }
     }
     __syncthreads();
-    // a block covers a.seq * blockDim.x consecutive positions; in turn i its
-    // threads take the i-th run of blockDim.x of them, so a lane plays a.seq
-    // games one after another, nearly always of one game (a warp idles once its
-    // longest lane is done, and a lane's total over several games varies less
-    // than one game's length)
-    const long long base = (long long)blockIdx.x * blockDim.x * a.seq + threadIdx.x;
-    for (int i = 0; i < a.seq; ++i) {
-    const long long q0 = base + (long long)i * blockDim.x;
+    const long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q0 >= be[kBuckets - 1]) return;  // past the last valid queue position
     int si = 0;
 #pragma unroll
@@ -239,7 +231,6 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
     case 17: play_one<WolfSheep>(a, q, nullptr); break;
     case 18: play_one<Draughts>(a, q, nullptr); break;
     default: play_one<HasamiShogi>(a, q, nullptr); break;
-    }
     }
 }
 
@@ -281,8 +272,7 @@ __global__ void __launch_bounds__(512, 1) mixed_persistent_kernel(MixedArgs a) {
 }
 
 int mixed_grid(long long n, const ludax_launch_cfg& c, int num_sms) {
-    const long long per_block = (long long)c.block_threads * c.envs_per_thread;
-    long long need = (n + per_block - 1) / per_block;
+    long long need = (n + c.block_threads - 1) / c.block_threads;
     if (c.blocks_per_sm > 0) need = std::min<long long>(need, (long long)num_sms * c.blocks_per_sm);
     return (int)std::max<long long>(need, 1);
 }
@@ -290,9 +280,7 @@ int mixed_grid(long long n, const ludax_launch_cfg& c, int num_sms) {
 int check_mixed_cfg(const ludax_launch_cfg& c) {
     if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32) return LUDAX_ERR_ARG;
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return LUDAX_ERR_ARG;
-    // one env per lane at a time; a lane of the one-thread-per-env launch may play 2 or 4 in turn
-    if (c.envs_per_thread != 1 && c.envs_per_thread != 2 && c.envs_per_thread != 4) return LUDAX_ERR_ARG;
-    if (c.envs_per_thread != 1 && c.blocks_per_sm != 0) return LUDAX_ERR_ARG;
+    if (c.envs_per_thread != 1) return LUDAX_ERR_ARG;  // the mixed kernel runs one env per lane
     if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
     if (c.compact_every != 0) return LUDAX_ERR_ARG;  // compaction is a single-game option
     if (c.threads_per_env > 1 || c.threads_per_env < 0) return LUDAX_ERR_ARG;  // one lane per env
@@ -328,11 +316,10 @@ int build_queue(const int32_t* desc_dev, long long n, std::vector<int32_t>& queu
     return LUDAX_OK;
 }
 
-int launch_mixed(MixedArgs a, const ludax_launch_cfg& c, int num_sms, cudaStream_t s) {
+int launch_mixed(const MixedArgs& a, const ludax_launch_cfg& c, int num_sms, cudaStream_t s) {
     int grid = mixed_grid(a.n, c, num_sms);
-    a.seq = c.envs_per_thread;
     if (cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long) * kBuckets, s) != cudaSuccess) return LUDAX_ERR_CUDA;
-    if ((long long)grid * c.block_threads * c.envs_per_thread < a.n) {  // persistent
+    if ((long long)grid * c.block_threads < a.n) {  // persistent
         if (c.hex_nbr_table) mixed_persistent_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
         else mixed_persistent_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
     } else if (c.hex_nbr_table) {
@@ -533,7 +520,6 @@ int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int
     a.outcome = nullptr;
     a.plies = nullptr;
     a.cursor = p->d_cursor;
-    a.seq = c.envs_per_thread;  // as launch_mixed sets it (the replays rewrite this parameter block)
     // capture cursor reset + kernel on a private stream
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -690,12 +676,11 @@ int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out) {
     int k = 0;
     for (int t = 0; t < 2; ++t)
         for (int b : blocks)
-            for (int s : bps)
-                for (int ept : {1, 2, 4}) {                 // positions a lane plays in turn (one thread per env only)
-                    if (s > 0 && (b * s > 2048 || ept > 1)) continue;  // more than one SM's threads
-                    if (out && k < max_out) out[k] = ludax_launch_cfg{b, s, ept, t, 0};
-                    ++k;
-                }
+            for (int s : bps) {
+                if (s > 0 && b * s > 2048) continue;  // more than one SM's threads
+                if (out && k < max_out) out[k] = ludax_launch_cfg{b, s, 1, t, 0};
+                ++k;
+            }
     return k;
 }
 
