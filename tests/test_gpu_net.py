@@ -231,6 +231,35 @@ def test_gradient_training_batch(L):
     assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-2
 
 
+@pytest.mark.parametrize("path", [1, 2, 0])
+def test_training_is_deterministic(L, path):
+    """Every partial sum of the backward pass (split-K weight gradients, row
+    sums of the biases, the loss) is reduced in a fixed order, so the same
+    batch gives the same gradient, and the same Adam step the same
+    parameters, bit for bit (4,736 rows: unequal splits, a ragged last chunk)."""
+    cells, B = 64, 4736
+    K = W.net_in_pad(cells)
+    rng = np.random.default_rng(21)
+    X = np.zeros((B, K))
+    X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
+    xb, yb = bf16_bits(X), torch.from_numpy(rng.random(B).astype(np.float32)).cuda()
+    theta = torch.from_numpy(W.init_params(cells, 4)).cuda()
+    net = L.Net(cells, B)
+    net.set_tensor_path(path)
+    net.set_params(theta)
+    g1, l1 = net.grad(xb, yb)
+    g2, l2 = net.grad(xb, yb)
+    assert torch.equal(g1, g2) and torch.equal(l1, l2)
+    runs = []
+    for _ in range(2):
+        net.set_params(theta)  # also resets Adam's moments and step count
+        losses = [net.train_step(xb, yb, 1e-3).clone() for _ in range(3)]
+        runs.append((net.get_params().clone(), torch.cat(losses)))
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+    assert L.ludax_device_error() == 0
+    net.close()
+
+
 def test_adam_step_matches_oracle(L):
     cells, B = 64, 256
     K = W.net_in_pad(cells)
