@@ -143,7 +143,7 @@ typedef struct {
     int32_t blocks_per_sm;   /* resident blocks per SM for the persistent grid, >= 1;
                                 0 = one thread per env (no persistence)               */
     int32_t envs_per_thread; /* envs each thread advances together (ILP): 1 or 2
-                                (single-game playouts; 1 for mixed batches)          */
+                                (mixed batches: 2 only with blocks_per_sm 0)         */
     int32_t hex_nbr_table;   /* Hex neighbour test: 0 = bit shifts, 1 = shared-memory
                                 table of per-cell neighbour masks                     */
     int32_t compact_every;   /* single-game playouts only (0 for mixed batches): 0 =
@@ -158,11 +158,12 @@ typedef struct {
                                 shuffles; same results bit for bit); needs
                                 envs_per_thread 1 and compact_every 0                 */
     int32_t lanes_per_warp;  /* lanes of each warp that hold envs: 0 or 32 = all; 8 or
-                                16 = single-game ludax_rollout only, the rest of the
-                                warp idle (small, latency-bound batches: fewer envs
-                                share a warp's issue slots and divergent branches);
-                                needs compact_every 0 and one lane per env; envs per
-                                warp = lanes_per_warp x envs_per_thread                */
+                                16 = ludax_rollout and mixed batches with
+                                blocks_per_sm 0, the rest of the warp idle (small,
+                                latency-bound batches: fewer envs share a warp's issue
+                                slots and divergent branches); needs compact_every 0
+                                and one lane per env; envs per warp = lanes_per_warp x
+                                envs_per_thread                                        */
 } ludax_launch_cfg;
 
 /* ---------------------------------------------------------------------------

@@ -57,6 +57,7 @@ struct MixedArgs {
     int16_t* plies;
     unsigned long long* cursor;      // per-bucket claim cursors, zeroed before each launch
     const long long* bucket_end_dev; // non-null: the bucket ends were built on the device (host-buffer path)
+    int lanes;                       // one-thread-per-env launch: lanes of each warp that hold envs (8, 16, 32)
 };
 // The mixed kernel takes exactly one parameter (MixedArgs): the graph plan
 // rewrites that single parameter before each replay.
@@ -89,6 +90,78 @@ __device__ __forceinline__ void play_one(const MixedArgs& a, long long q, const 
     while (g.outcome == kOngoing) random_ply_pre(g, key, rhi);
     a.outcome[e] = (int8_t)g.outcome;
     a.plies[e] = (int16_t)g.ply;
+}
+
+// The same for two envs of one bucket per thread (queue positions q0 and
+// q1, q1 < 0 for none), interleaved ply by ply: two independent dependency
+// chains in each thread (the "unroll").
+template <class G>
+__device__ __forceinline__ void play_pair(const MixedArgs& a, long long q0, long long q1, const B128* table) {
+    G g[2];
+    uint64_t key[2];
+    uint32_t rhi[2];
+    long long e[2];
+    bool on[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const long long q = i ? q1 : q0;
+        set_table(g[i], table);
+        on[i] = q >= 0;
+        e[i] = on[i] ? a.queue[q] : 0;
+        if (on[i]) configure(g[i], a.desc[e[i]]);
+        g[i].reset();
+        key[i] = env_key(a.seed_key, (uint64_t)(a.env_offset + e[i]));
+        rhi[i] = draw_hi(key[i], 0u);
+    }
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            if (!on[i]) continue;
+            any = true;
+            if (g[i].outcome == kOngoing) {
+                random_ply_pre(g[i], key[i], rhi[i]);
+                continue;
+            }
+            a.outcome[e[i]] = (int8_t)g[i].outcome;
+            a.plies[e[i]] = (int16_t)g[i].ply;
+            on[i] = false;
+        }
+        if (!any) break;
+    }
+}
+
+template <class G, int EPT>
+__device__ __forceinline__ void play_n(const MixedArgs& a, long long q0, long long q1, const B128* table) {
+    if constexpr (EPT == 1) play_one<G>(a, q0, table);
+    else play_pair<G>(a, q0, q1, table);
+}
+
+// the game of bucket b, for the positions q0 (and q1 with EPT 2)
+template <bool TABLE, int EPT>
+__device__ __forceinline__ void play_bucket(const MixedArgs& a, int b, long long q0, long long q1, const B128* t) {
+    switch (b) {
+    case 0: play_n<TTT, EPT>(a, q0, q1, nullptr); break;
+    case 1: play_n<C4, EPT>(a, q0, q1, nullptr); break;
+    case 2: play_n<Othello, EPT>(a, q0, q1, nullptr); break;
+    case 3: play_n<Hex<2>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(2) : nullptr); break;
+    case 4: play_n<Hex<3>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(3) : nullptr); break;
+    case 5: play_n<Hex<4>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(4) : nullptr); break;
+    case 6: play_n<Hex<5>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(5) : nullptr); break;
+    case 7: play_n<Hex<6>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(6) : nullptr); break;
+    case 8: play_n<Hex<7>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(7) : nullptr); break;
+    case 9: play_n<Hex<8>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(8) : nullptr); break;
+    case 10: play_n<Hex<9>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(9) : nullptr); break;
+    case 11: play_n<Hex<10>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(10) : nullptr); break;
+    case 12: play_n<Hex<11>, EPT>(a, q0, q1, TABLE ? t + hex_table_offset(11) : nullptr); break;
+    case 13: play_n<Gomoku, EPT>(a, q0, q1, nullptr); break;
+    case 14: play_n<Pente, EPT>(a, q0, q1, nullptr); break;
+    case 15: play_n<Yavalath, EPT>(a, q0, q1, nullptr); break;
+    case 16: play_n<LineGame, EPT>(a, q0, q1, nullptr); break;
+    case 17: play_n<WolfSheep, EPT>(a, q0, q1, nullptr); break;
+    case 18: play_n<Draughts, EPT>(a, q0, q1, nullptr); break;
+    default: play_n<HasamiShogi, EPT>(a, q0, q1, nullptr); break;
+    }
 }
 
 // Persistent launches: a warp stays inside one bucket (one game, so its
@@ -168,7 +241,12 @@ __device__ __forceinline__ void drain_any(const MixedArgs& a, const long long* b
     }
 }
 
-template <bool TABLE>
+// One thread per env (EPT envs per thread, interleaved); only the first
+// a.lanes lanes of each warp hold envs.  A block covers EPT runs of
+// (blockDim / 32) * a.lanes consecutive positions; a thread takes its slot in
+// each run, so its envs are nearly always of one bucket (when they are not,
+// it plays them one after the other).
+template <bool TABLE, int EPT>
 __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
     __shared__ B128 tables[TABLE ? kHexTableCells : 1];
     if constexpr (TABLE) {
@@ -203,34 +281,32 @@ __global__ void __launch_bounds__(512) mixed_rollout_kernel(MixedArgs a) {
         }
     }
     __syncthreads();
-    const long long q0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q0 >= be[kBuckets - 1]) return;  // past the last valid queue position
-    int si = 0;
+    const int lane = threadIdx.x & 31;
+    if (lane >= a.lanes) return;
+    const long long run = (long long)(blockDim.x >> 5) * a.lanes;
+    const long long slot = (long long)(threadIdx.x >> 5) * a.lanes + lane;
+    long long q[EPT];
+    int b[EPT];
 #pragma unroll
-    for (int k = 0; k < kBuckets - 1; ++k) si += q0 >= seg_end[k];
-    const long long q = q0 + seg_q[si];
-    const B128* t = tables;
-    switch (bucket_at(be, q)) {
-    case 0: play_one<TTT>(a, q, nullptr); break;
-    case 1: play_one<C4>(a, q, nullptr); break;
-    case 2: play_one<Othello>(a, q, nullptr); break;
-    case 3: play_one<Hex<2>>(a, q, TABLE ? t + hex_table_offset(2) : nullptr); break;
-    case 4: play_one<Hex<3>>(a, q, TABLE ? t + hex_table_offset(3) : nullptr); break;
-    case 5: play_one<Hex<4>>(a, q, TABLE ? t + hex_table_offset(4) : nullptr); break;
-    case 6: play_one<Hex<5>>(a, q, TABLE ? t + hex_table_offset(5) : nullptr); break;
-    case 7: play_one<Hex<6>>(a, q, TABLE ? t + hex_table_offset(6) : nullptr); break;
-    case 8: play_one<Hex<7>>(a, q, TABLE ? t + hex_table_offset(7) : nullptr); break;
-    case 9: play_one<Hex<8>>(a, q, TABLE ? t + hex_table_offset(8) : nullptr); break;
-    case 10: play_one<Hex<9>>(a, q, TABLE ? t + hex_table_offset(9) : nullptr); break;
-    case 11: play_one<Hex<10>>(a, q, TABLE ? t + hex_table_offset(10) : nullptr); break;
-    case 12: play_one<Hex<11>>(a, q, TABLE ? t + hex_table_offset(11) : nullptr); break;
-    case 13: play_one<Gomoku>(a, q, nullptr); break;
-    case 14: play_one<Pente>(a, q, nullptr); break;
-    case 15: play_one<Yavalath>(a, q, nullptr); break;
-    case 16: play_one<LineGame>(a, q, nullptr); break;
-    case 17: play_one<WolfSheep>(a, q, nullptr); break;
-    case 18: play_one<Draughts>(a, q, nullptr); break;
-    default: play_one<HasamiShogi>(a, q, nullptr); break;
+    for (int i = 0; i < EPT; ++i) {
+        const long long q0 = (long long)blockIdx.x * run * EPT + i * run + slot;
+        q[i] = -1;
+        b[i] = -1;
+        if (q0 >= be[kBuckets - 1]) continue;  // past the last valid queue position
+        int si = 0;
+#pragma unroll
+        for (int k = 0; k < kBuckets - 1; ++k) si += q0 >= seg_end[k];
+        q[i] = q0 + seg_q[si];
+        b[i] = bucket_at(be, q[i]);
+    }
+    if (q[0] < 0) return;
+    if constexpr (EPT == 1) {
+        play_bucket<TABLE, 1>(a, b[0], q[0], -1, tables);
+    } else if (q[1] < 0 || b[1] == b[0]) {
+        play_bucket<TABLE, 2>(a, b[0], q[0], q[1], tables);
+    } else {  // a bucket boundary between the two: one after the other
+        play_bucket<TABLE, 2>(a, b[0], q[0], -1, tables);
+        play_bucket<TABLE, 2>(a, b[1], q[1], -1, tables);
     }
 }
 
@@ -271,8 +347,13 @@ __global__ void __launch_bounds__(512, 1) mixed_persistent_kernel(MixedArgs a) {
     }
 }
 
+int mixed_lanes(const ludax_launch_cfg& c) {
+    return (c.lanes_per_warp == 8 || c.lanes_per_warp == 16) ? c.lanes_per_warp : 32;
+}
+
 int mixed_grid(long long n, const ludax_launch_cfg& c, int num_sms) {
-    long long need = (n + c.block_threads - 1) / c.block_threads;
+    const long long per_block = (long long)(c.block_threads / 32) * mixed_lanes(c) * c.envs_per_thread;
+    long long need = (n + per_block - 1) / per_block;
     if (c.blocks_per_sm > 0) need = std::min<long long>(need, (long long)num_sms * c.blocks_per_sm);
     return (int)std::max<long long>(need, 1);
 }
@@ -280,11 +361,14 @@ int mixed_grid(long long n, const ludax_launch_cfg& c, int num_sms) {
 int check_mixed_cfg(const ludax_launch_cfg& c) {
     if (c.block_threads < 32 || c.block_threads > 512 || c.block_threads % 32) return LUDAX_ERR_ARG;
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 64) return LUDAX_ERR_ARG;
-    if (c.envs_per_thread != 1) return LUDAX_ERR_ARG;  // the mixed kernel runs one env per lane
+    if (c.envs_per_thread != 1 && c.envs_per_thread != 2) return LUDAX_ERR_ARG;
+    if (c.lanes_per_warp != 0 && c.lanes_per_warp != 8 && c.lanes_per_warp != 16 && c.lanes_per_warp != 32)
+        return LUDAX_ERR_ARG;
+    // two envs per thread and part-filled warps: one-thread-per-env launches only
+    if ((c.envs_per_thread != 1 || mixed_lanes(c) != 32) && c.blocks_per_sm != 0) return LUDAX_ERR_ARG;
     if (c.hex_nbr_table != 0 && c.hex_nbr_table != 1) return LUDAX_ERR_ARG;
     if (c.compact_every != 0) return LUDAX_ERR_ARG;  // compaction is a single-game option
     if (c.threads_per_env > 1 || c.threads_per_env < 0) return LUDAX_ERR_ARG;  // one lane per env
-    if (c.lanes_per_warp != 0 && c.lanes_per_warp != 32) return LUDAX_ERR_ARG;  // full warps
     return LUDAX_OK;
 }
 
@@ -316,16 +400,20 @@ int build_queue(const int32_t* desc_dev, long long n, std::vector<int32_t>& queu
     return LUDAX_OK;
 }
 
-int launch_mixed(const MixedArgs& a, const ludax_launch_cfg& c, int num_sms, cudaStream_t s) {
+int launch_mixed(MixedArgs a, const ludax_launch_cfg& c, int num_sms, cudaStream_t s) {
     int grid = mixed_grid(a.n, c, num_sms);
+    a.lanes = mixed_lanes(c);
     if (cudaMemsetAsync(a.cursor, 0, sizeof(unsigned long long) * kBuckets, s) != cudaSuccess) return LUDAX_ERR_CUDA;
-    if ((long long)grid * c.block_threads < a.n) {  // persistent
+    if ((long long)grid * c.block_threads < a.n) {  // persistent (full warps, one env per thread)
         if (c.hex_nbr_table) mixed_persistent_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
         else mixed_persistent_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
+    } else if (c.envs_per_thread == 2) {
+        if (c.hex_nbr_table) mixed_rollout_kernel<true, 2><<<grid, c.block_threads, 0, s>>>(a);
+        else mixed_rollout_kernel<false, 2><<<grid, c.block_threads, 0, s>>>(a);
     } else if (c.hex_nbr_table) {
-        mixed_rollout_kernel<true><<<grid, c.block_threads, 0, s>>>(a);
+        mixed_rollout_kernel<true, 1><<<grid, c.block_threads, 0, s>>>(a);
     } else {
-        mixed_rollout_kernel<false><<<grid, c.block_threads, 0, s>>>(a);
+        mixed_rollout_kernel<false, 1><<<grid, c.block_threads, 0, s>>>(a);
     }
     return cudaGetLastError() == cudaSuccess ? LUDAX_OK : LUDAX_ERR_CUDA;
 }
@@ -520,6 +608,7 @@ int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int
     a.outcome = nullptr;
     a.plies = nullptr;
     a.cursor = p->d_cursor;
+    a.lanes = mixed_lanes(c);  // as launch_mixed sets it (the replays rewrite this parameter block)
     // capture cursor reset + kernel on a private stream
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
@@ -674,13 +763,24 @@ int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out) {
     static const int blocks[] = {64, 128, 192, 256, 384, 448, 512};
     static const int bps[] = {0, 2, 4, 8, 16};
     int k = 0;
-    for (int t = 0; t < 2; ++t)
+    auto put = [&](ludax_launch_cfg c) {
+        if (out && k < max_out) out[k] = c;
+        ++k;
+    };
+    for (int t = 0; t < 2; ++t) {
         for (int b : blocks)
             for (int s : bps) {
                 if (s > 0 && b * s > 2048) continue;  // more than one SM's threads
-                if (out && k < max_out) out[k] = ludax_launch_cfg{b, s, 1, t, 0};
-                ++k;
+                put(ludax_launch_cfg{b, s, 1, t, 0});
             }
+        // one thread per env: two envs per thread (the unroll) and part-filled warps (envs per warp)
+        for (int b : blocks)
+            for (int ept = 1; ept <= 2; ++ept)
+                for (int lanes : {32, 16, 8}) {
+                    if (ept == 1 && lanes == 32) continue;  // above
+                    put(ludax_launch_cfg{b, 0, ept, t, 0, 1, lanes == 32 ? 0 : lanes});
+                }
+    }
     return k;
 }
 

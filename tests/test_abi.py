@@ -100,16 +100,19 @@ def test_autotune_candidates_are_valid(L):
         assert 32 <= c.block_threads <= 512 and c.block_threads % 32 == 0
         assert c.blocks_per_sm == 0 or c.block_threads * c.blocks_per_sm <= 2048
         assert c.hex_nbr_table in (0, 1)
-        assert c.envs_per_thread == 1  # one env per lane
+        # two envs per thread and part-filled warps only in one-thread-per-env launches
+        assert c.envs_per_thread in (1, 2) and c.lanes_per_warp in (0, 8, 16)
+        assert c.blocks_per_sm == 0 or (c.envs_per_thread == 1 and c.lanes_per_warp == 0)
         assert c.threads_per_env in (0, 1)  # the mixed kernel runs one lane per env
+    assert {c.envs_per_thread for c in cands} == {1, 2} and {c.lanes_per_warp for c in cands} == {0, 8, 16}
 
 
 def test_mixed_launch_shape_checked_before_touching_the_device(L):
     from paper_2506_22609_b300 import ludax
 
     fake = ctypes.c_void_p(1 << 20)  # never dereferenced: the shape is refused first
-    for bad in [(128, 2, 2, 0, 0), (128, 0, 2, 0, 0), (128, 0, 8, 0, 0), (100, 0, 1, 0, 0), (128, 0, 1, 0, 4),
-                (128, 0, 1, 0, 0, 2), (128, 0, 1, 0, 0, 1, 8)]:  # mixed batches run full warps
+    for bad in [(128, 2, 2, 0, 0), (128, 0, 4, 0, 0), (128, 0, 8, 0, 0), (100, 0, 1, 0, 0), (128, 0, 1, 0, 4),
+                (128, 0, 1, 0, 0, 2), (128, 2, 1, 0, 0, 1, 8), (128, 0, 1, 0, 0, 1, 4)]:
         cfg = ludax.make_cfg(*bad)
         assert L.ludax_rollout_mixed(fake, 10, 0, 0, fake, fake, ctypes.byref(cfg), None) == -1, bad
 

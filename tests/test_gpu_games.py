@@ -343,7 +343,9 @@ def test_mixed_batch_matches_oracle(L, layout):
     L.ludax_rollout_mixed(dd, off, seed, out, plies)
     torch.cuda.synchronize()
     assert (np_(out) == o_out).all() and (np_(plies) == o_plies).all()
-    for cfg in [(128, 2, 1, 1, 0), (64, 1, 1, 0, 0), (512, 0, 1, 1, 0), (256, 4, 1, 0, 0), (32, 1, 1, 1, 0)]:
+    # persistent shapes, one thread per env, two interleaved envs per thread, part-filled warps
+    for cfg in [(128, 2, 1, 1, 0), (64, 1, 1, 0, 0), (512, 0, 1, 1, 0), (256, 4, 1, 0, 0), (32, 1, 1, 1, 0),
+                (128, 0, 2, 1, 0), (64, 0, 1, 0, 0, 1, 16), (256, 0, 2, 1, 0, 1, 8), (96, 0, 2, 0, 0, 1, 16)]:
         plan = L.ludax_mixed_plan_create(dd, off, L.make_cfg(*cfg))
         for s2 in (seed, seed + 1):
             out2 = torch.full((n,), 99, dtype=torch.int8, device="cuda")
@@ -374,7 +376,7 @@ def test_mixed_full_config_sampled(L):
     L.ludax_mixed_plan_destroy(plan)
 
 
-@pytest.mark.parametrize("cfg", [(128, 0, 1, 1, 0), (128, 2, 1, 1, 0)])
+@pytest.mark.parametrize("cfg", [(128, 0, 1, 1, 0), (128, 2, 1, 1, 0), (256, 0, 2, 1, 0, 1, 16)])
 def test_mixed_host_buffers_match_oracle(L, cfg):
     # the plan's host-buffer launch: descriptors uploaded, queue rebuilt on the
     # device, results copied back; any batch of the plan's size, including ones
