@@ -396,7 +396,8 @@ int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_envs, int64
                                 int64_t* bad_index);
 
 /* Autotuner: times every candidate launch shape (block_threads x
- * blocks_per_sm x envs_per_thread x hex_nbr_table) on the given mixed batch
+ * blocks_per_sm x hex_nbr_table, and for one thread per env envs_per_thread
+ * x lanes_per_warp; ludax_autotune_candidates lists them) on the given mixed batch
  * with CUDA events (warm-up, then the median of `reps` launches) and returns
  * the fastest in best_out; best_ms_out (nullable) its median time.
  * ms_table_out (nullable, host) receives each candidate's median in
