@@ -121,6 +121,12 @@ def test_rollout_host_matches_device_path(L, name, game, rows, cols):
     for _ in range(2):  # the second call reuses the staging
         L.ludax_rollout_host(env.handle, hp, hm, 77, ho, hpl)
         env.sync()
+    # part-filled warps (8 or 16 lanes holding envs), one thread per env and persistent: the same results
+    for cfg in (L.make_cfg(128, 0, 1, 0, 0, 1, 8), L.make_cfg(64, 2, 1, 1, 0, 1, 16)):
+        ho2, hpl2 = torch.zeros_like(ho).pin_memory(), torch.zeros_like(hpl).pin_memory()
+        L.ludax_rollout_host(env.handle, hp, hm, 77, ho2, hpl2, cfg)
+        env.sync()
+        assert torch.equal(ho2, ho) and torch.equal(hpl2, hpl)
     # the same with one buffer each way (ludax_rollout_host_packed)
     pb = p.size * 8
     hin = torch.empty(pb + 4 * n, dtype=torch.uint8).pin_memory()
