@@ -445,6 +445,16 @@ int ludax_net_sizes(const ludax_net* net, int32_t* in_pad, int32_t* hidden, int6
  * and step count; get_params copies the FP32 masters out. */
 int ludax_net_set_params(ludax_net* net, const float* params_dev);
 int ludax_net_get_params(ludax_net* net, float* params_dev);
+/* The whole training state, for checkpoints: the FP32 parameters, Adam's
+ * first and second moments (each float [num_params], device memory, owned by
+ * the caller) and the number of Adam steps taken (host).  get copies them out
+ * on the net's stream (any pointer may be null to skip it); set restores all
+ * of them (none null; 0 <= steps < 2^31) and the BF16 weight copies, so that
+ * the next train step is the one that followed get.  LUDAX_ERR_ARG on a bad
+ * argument, LUDAX_ERR_CUDA if a copy fails. */
+int ludax_net_get_state(ludax_net* net, float* params_dev, float* m_dev, float* v_dev, int64_t* steps);
+int ludax_net_set_state(ludax_net* net, const float* params_dev, const float* m_dev, const float* v_dev,
+                        int64_t steps);
 /* Which kernels run the hidden-layer contractions:
  *   1 (default) tcgen05/TMEM: a forward runs both layers and the head in one
  *     launch, layer 1's rows passing through L2 to layer 2 (without labels,

@@ -967,6 +967,29 @@ int ludax_net_get_params(ludax_net* n, float* params_dev) {
                : LUDAX_ERR_CUDA;
 }
 
+int ludax_net_get_state(ludax_net* n, float* params_dev, float* m_dev, float* v_dev, int64_t* steps) {
+    if (!n) return LUDAX_ERR_ARG;
+    const size_t bytes = sizeof(float) * (size_t)n->nparams;
+    const float* src[3] = {n->p, n->m, n->v};
+    float* dst[3] = {params_dev, m_dev, v_dev};
+    for (int i = 0; i < 3; ++i)
+        if (dst[i] && cudaMemcpyAsync(dst[i], src[i], bytes, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess)
+            return LUDAX_ERR_CUDA;
+    if (steps) *steps = n->t;
+    return LUDAX_OK;
+}
+
+int ludax_net_set_state(ludax_net* n, const float* params_dev, const float* m_dev, const float* v_dev, int64_t steps) {
+    if (!n || !params_dev || !m_dev || !v_dev || steps < 0 || steps > 0x7FFFFFFF) return LUDAX_ERR_ARG;
+    const size_t bytes = sizeof(float) * (size_t)n->nparams;
+    if (cudaMemcpyAsync(n->p, params_dev, bytes, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess ||
+        cudaMemcpyAsync(n->m, m_dev, bytes, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess ||
+        cudaMemcpyAsync(n->v, v_dev, bytes, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess)
+        return LUDAX_ERR_CUDA;
+    n->t = (int)steps;
+    return refresh_bf16(n);  // the BF16 copies Adam leaves are the rounded parameters
+}
+
 int ludax_net_forward(ludax_net* n, const uint16_t* x_dev, int64_t B, float* p_dev) {
     int st = net_check(n, B);
     if (st) return st;

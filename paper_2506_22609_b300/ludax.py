@@ -126,6 +126,8 @@ def lib() -> ctypes.CDLL:
         "ludax_net_sizes": [vp, P(i32), P(i32), P(i64)],
         "ludax_net_set_params": [vp, vp],
         "ludax_net_get_params": [vp, vp],
+        "ludax_net_get_state": [vp, vp, vp, vp, P(i64)],
+        "ludax_net_set_state": [vp, vp, vp, vp, i64],
         "ludax_net_set_tensor_path": [vp, i32],
         "ludax_net_forward": [vp, vp, i64, vp],
         "ludax_net_grad": [vp, vp, vp, i64, vp, vp],
@@ -450,6 +452,18 @@ def ludax_net_get_params(h, params):
     _check(lib().ludax_net_get_params(h, _ptr(params)), "ludax_net_get_params")
 
 
+def ludax_net_get_state(h, params, m, v):
+    """Copies parameters and Adam's moments into the three device tensors;
+    returns the number of Adam steps taken."""
+    steps = ctypes.c_int64()
+    _check(lib().ludax_net_get_state(h, _ptr(params), _ptr(m), _ptr(v), ctypes.byref(steps)), "ludax_net_get_state")
+    return steps.value
+
+
+def ludax_net_set_state(h, params, m, v, steps):
+    _check(lib().ludax_net_set_state(h, _ptr(params), _ptr(m), _ptr(v), int(steps)), "ludax_net_set_state")
+
+
 def ludax_net_forward(h, x, p):
     _check(lib().ludax_net_forward(h, _ptr(x), x.shape[0], _ptr(p)), "ludax_net_forward")
 
@@ -530,6 +544,17 @@ class Net:
         p = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
         ludax_net_get_params(self.handle, p)
         return p
+
+    def get_state(self):
+        """(parameters, Adam m, Adam v, Adam steps taken): what set_state needs
+        to continue training exactly where this net stands."""
+        p, m, v = (torch.empty(self.num_params, dtype=torch.float32, device="cuda") for _ in range(3))
+        steps = ludax_net_get_state(self.handle, p, m, v)
+        return p, m, v, steps
+
+    def set_state(self, params, m, v, steps):
+        f = lambda t: t.to(device="cuda", dtype=torch.float32).contiguous()  # noqa: E731
+        ludax_net_set_state(self.handle, f(params), f(m), f(v), steps)
 
     def forward(self, x):
         p = torch.empty(x.shape[0], dtype=torch.float32, device="cuda")

@@ -23,11 +23,14 @@ handles, sizes and seeds around):
      the selected K and M, and the comparison at an equal time budget (the
      full-playout estimator with the largest M that fits in the selected
      truncated estimator's time).
+Checkpoints (save_checkpoint / load_checkpoint) hold the parameters, both
+Adam moments and the step count, so training resumes bit for bit.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 
 import numpy as np
@@ -258,6 +261,66 @@ def run(game="othello", n_train=2_000_000, n_val=65_536, n_eval=100_000, batch=6
         e.close()
     net.close()
     return out
+
+
+# --------------------------------------------------------------- checkpoints --
+# One little-endian file: the 8-byte magic b"LUDAXNET", six int64 -- format
+# version, cells, input width, hidden width, number of parameters, Adam steps
+# taken -- then the FP32 parameters and Adam's first and second moments,
+# num_params each.  Restoring it continues training exactly where it stood
+# (ludax_net_set_state).
+CKPT_MAGIC, CKPT_VERSION = b"LUDAXNET", 1
+
+
+def write_checkpoint(path, cells, in_pad, hidden, steps, params, m, v):
+    """Writes the arrays (float32, num_params each) under the header; the
+    file appears whole or not at all (written aside, then renamed)."""
+    arrays = [np.ascontiguousarray(a, dtype="<f4") for a in (params, m, v)]
+    n = arrays[0].size
+    if any(a.size != n for a in arrays):
+        raise ValueError("parameters and moments differ in length")
+    head = np.array([CKPT_VERSION, cells, in_pad, hidden, n, steps], dtype="<i8")
+    tmp = f"{path}.tmp"
+    with open(tmp, "wb") as f:
+        f.write(CKPT_MAGIC)
+        f.write(head.tobytes())
+        for a in arrays:
+            f.write(a.tobytes())
+    os.replace(tmp, path)
+
+
+def read_checkpoint(path):
+    """The header fields and the three arrays; ValueError if the file is not
+    a checkpoint of this format or is cut short."""
+    with open(path, "rb") as f:
+        data = f.read()
+    if data[:8] != CKPT_MAGIC or len(data) < 56:
+        raise ValueError(f"{path}: not a value-net checkpoint")
+    version, cells, in_pad, hidden, n, steps = (int(x) for x in np.frombuffer(data, "<i8", 6, 8))
+    if version != CKPT_VERSION:
+        raise ValueError(f"{path}: checkpoint format {version}, expected {CKPT_VERSION}")
+    if n < 1 or len(data) != 56 + 12 * n:
+        raise ValueError(f"{path}: {len(data)} bytes, expected {56 + 12 * n}")
+    arr = np.frombuffer(data, "<f4", 3 * n, 56).reshape(3, n)
+    return {"cells": cells, "in_pad": in_pad, "hidden": hidden, "steps": steps,
+            "params": arr[0].copy(), "m": arr[1].copy(), "v": arr[2].copy()}
+
+
+def save_checkpoint(net, path):
+    p, m, v, steps = net.get_state()
+    torch.cuda.synchronize()
+    write_checkpoint(path, net.cells, net.in_pad, net.hidden, steps, p.cpu().numpy(), m.cpu().numpy(),
+                     v.cpu().numpy())
+
+
+def load_checkpoint(net, path):
+    """Restores a checkpoint into a net of the same shape; returns the Adam steps it had taken."""
+    c = read_checkpoint(path)
+    if (c["cells"], c["in_pad"], c["hidden"], c["params"].size) != (net.cells, net.in_pad, net.hidden,
+                                                                      net.num_params):
+        raise ValueError(f"{path}: a net of {c['cells']} cells, {c['in_pad']} inputs, {c['hidden']} hidden units")
+    net.set_state(*(torch.from_numpy(c[k]) for k in ("params", "m", "v")), c["steps"])
+    return c["steps"]
 
 
 def main():

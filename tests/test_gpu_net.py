@@ -260,6 +260,43 @@ def test_training_is_deterministic(L, path):
     net.close()
 
 
+def test_checkpoint_resumes_training_exactly(L, tmp_path):
+    """Training interrupted by a checkpoint (parameters, both Adam moments,
+    the step count; written to a file and read back into a fresh net) goes on
+    exactly as if uninterrupted, and the restored net predicts the same."""
+    from paper_2506_22609_b300 import valuenet as V
+
+    cells, B = 64, 1024
+    K = W.net_in_pad(cells)
+    rng = np.random.default_rng(31)
+    X = np.zeros((B, K))
+    X[:, :2 * cells + 1] = rng.random((B, 2 * cells + 1)) < 0.3
+    xb, yb = bf16_bits(X), torch.from_numpy(rng.random(B).astype(np.float32)).cuda()
+    theta = torch.from_numpy(W.init_params(cells, 6)).cuda()
+    a = L.Net(cells, B)
+    a.set_params(theta)
+    for _ in range(3):
+        a.train_step(xb, yb, 1e-3)
+    path = str(tmp_path / "net.ckpt")
+    V.save_checkpoint(a, path)
+    for _ in range(4):
+        a.train_step(xb, yb, 1e-3)
+    b = L.Net(cells, B)
+    assert V.load_checkpoint(b, path) == 3
+    for _ in range(4):
+        b.train_step(xb, yb, 1e-3)
+    pa, ma, va, ta = a.get_state()
+    pb, mb, vb, tb = b.get_state()
+    assert ta == tb == 7
+    assert torch.equal(pa, pb) and torch.equal(ma, mb) and torch.equal(va, vb)
+    assert torch.equal(a.forward(xb), b.forward(xb))
+    c = L.Net(121, B)  # a net of another shape refuses it
+    with pytest.raises(ValueError):
+        V.load_checkpoint(c, path)
+    for n in (a, b, c):
+        n.close()
+
+
 def test_adam_step_matches_oracle(L):
     cells, B = 64, 256
     K = W.net_in_pad(cells)

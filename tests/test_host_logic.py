@@ -1,11 +1,13 @@
 """Host-side logic without a GPU: the CPU baseline's sampling of the mixed
-batch, the value net's selection of K and M on validation errors, and the
-known-answer fixture of the policy's draw (regenerated by its script)."""
+batch, the value net's selection of K and M on validation errors, the
+known-answer fixture of the policy's draw (regenerated by its script), and
+the value net's checkpoint file format."""
 import os
 import subprocess
 import sys
 
 import numpy as np
+import pytest
 
 from conftest import ROOT
 
@@ -44,3 +46,30 @@ def test_draw_fixture_is_what_its_script_writes(tmp_path):
     assert open(fixture).read() == before
     rows = [l.split() for l in before.splitlines() if l and not l.startswith("#")]
     assert len({(r[0], r[1]) for r in rows}) >= 10 and np.all([len(r) == 7 for r in rows])
+
+
+def test_value_net_checkpoint_file_round_trip(tmp_path):
+    """The checkpoint format on its own (host side): header fields and the
+    three arrays come back bit for bit; other files are refused."""
+    import numpy as np
+
+    from paper_2506_22609_b300 import valuenet as V
+
+    rng = np.random.default_rng(3)
+    n = 1000
+    p, m, v = (rng.standard_normal(n).astype(np.float32) for _ in range(3))
+    path = str(tmp_path / "net.ckpt")
+    V.write_checkpoint(path, 64, 256, 512, 17, p, m, v)
+    c = V.read_checkpoint(path)
+    assert (c["cells"], c["in_pad"], c["hidden"], c["steps"]) == (64, 256, 512, 17)
+    for k, a in (("params", p), ("m", m), ("v", v)):
+        assert c[k].dtype == np.float32 and (c[k].view(np.uint32) == a.view(np.uint32)).all()
+    data = open(path, "rb").read()
+    assert len(data) == 8 + 6 * 8 + 3 * 4 * n
+    bad = tmp_path / "bad.ckpt"
+    for blob in (b"NOTANET!" + data[8:], data[:-4], data[:8] + (2).to_bytes(8, "little") + data[16:]):
+        bad.write_bytes(blob)
+        with pytest.raises(ValueError):
+            V.read_checkpoint(str(bad))
+    with pytest.raises(ValueError):  # moments of another length
+        V.write_checkpoint(path, 64, 256, 512, 0, p, m[:-1], v)
