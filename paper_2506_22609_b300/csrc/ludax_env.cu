@@ -877,6 +877,7 @@ int ludax_env_sizes(const ludax_env* env, int32_t* num_actions, int32_t* mask_wo
 }
 
 int ludax_reset(ludax_env* env, const uint8_t* env_mask_dev) {
+    ludax::ApiRange api_range("ludax_reset");
     if (!env) return LUDAX_ERR_ARG;
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
         using G = typename decltype(tag)::type;
@@ -886,6 +887,7 @@ int ludax_reset(ludax_env* env, const uint8_t* env_mask_dev) {
 }
 
 int ludax_legal_mask(ludax_env* env, uint64_t* mask_dev, uint8_t* pass_legal_dev) {
+    ludax::ApiRange api_range("ludax_legal_mask");
     if (!env || !mask_dev) return LUDAX_ERR_ARG;
     if (!aligned(mask_dev, 8)) return LUDAX_ERR_ALIGN;
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
@@ -897,6 +899,7 @@ int ludax_legal_mask(ludax_env* env, uint64_t* mask_dev, uint8_t* pass_legal_dev
 }
 
 int ludax_step(ludax_env* env, const int32_t* actions_dev, float* rewards_dev, uint8_t* terminated_dev) {
+    ludax::ApiRange api_range("ludax_step");
     if (!env || !actions_dev || !rewards_dev || !terminated_dev) return LUDAX_ERR_ARG;
     if (!aligned(actions_dev, 4) || !aligned(rewards_dev, 8)) return LUDAX_ERR_ALIGN;
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
@@ -908,6 +911,7 @@ int ludax_step(ludax_env* env, const int32_t* actions_dev, float* rewards_dev, u
 }
 
 int ludax_random_step(ludax_env* env, uint64_t seed, float* rewards_dev, uint8_t* terminated_dev) {
+    ludax::ApiRange api_range("ludax_random_step");
     if (!env || !rewards_dev || !terminated_dev) return LUDAX_ERR_ARG;
     if (!aligned(rewards_dev, 8)) return LUDAX_ERR_ALIGN;
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
@@ -950,6 +954,7 @@ static int rollout_impl(ludax_env* env, uint64_t seed, uint32_t flags, const int
 
 int ludax_rollout(ludax_env* env, uint64_t seed, uint32_t flags, const int16_t* stop_ply_dev, int8_t* outcome_dev,
                   int16_t* plies_dev, const ludax_launch_cfg* cfg) {
+    ludax::ApiRange api_range("ludax_rollout");
     return rollout_impl(env, seed, flags, stop_ply_dev, outcome_dev, plies_dev, cfg, nullptr, nullptr);
 }
 
@@ -975,6 +980,7 @@ static int host_stage(ludax_env* env, size_t pbytes, size_t* out_at, size_t* pli
 
 int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32_t* meta_host, uint64_t seed,
                        int8_t* outcome_host, int16_t* plies_host, const ludax_launch_cfg* cfg) {
+    ludax::ApiRange api_range("ludax_rollout_host");
     if (!env || !planes_host || !meta_host || !outcome_host || !plies_host) return LUDAX_ERR_ARG;
     int W, V;
     state_bits_shape(env, &W, &V);
@@ -999,6 +1005,7 @@ int ludax_rollout_host(ludax_env* env, const uint64_t* planes_host, const uint32
 
 int ludax_rollout_host_packed(ludax_env* env, const void* in_host, void* out_host, uint64_t seed,
                               const ludax_launch_cfg* cfg) {
+    ludax::ApiRange api_range("ludax_rollout_host_packed");
     if (!env || !in_host || !out_host) return LUDAX_ERR_ARG;
     int W, V;
     state_bits_shape(env, &W, &V);
@@ -1018,6 +1025,7 @@ int ludax_rollout_host_packed(ludax_env* env, const void* in_host, void* out_hos
 }
 
 int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_dev, const ludax_launch_cfg* cfg) {
+    ludax::ApiRange api_range("ludax_rollout_value");
     if (!env || !value_dev || R < 1) return LUDAX_ERR_ARG;
     if (!aligned(value_dev, 4)) return LUDAX_ERR_ALIGN;
     ludax_launch_cfg c = cfg ? *cfg : default_cfg();
@@ -1038,6 +1046,7 @@ int ludax_rollout_value(ludax_env* env, uint64_t seed, int32_t R, float* value_d
 }
 
 int ludax_get_state(ludax_env* env, const ludax_state_view* dst) {
+    ludax::ApiRange api_range("ludax_get_state");
     if (!env || !dst || !dst->board || !dst->to_move || !dst->ply || !dst->passes || !dst->outcome) return LUDAX_ERR_ARG;
     if (!aligned(dst->ply, 2)) return LUDAX_ERR_ALIGN;
     ludax_state_view v = *dst;
@@ -1049,6 +1058,7 @@ int ludax_get_state(ludax_env* env, const ludax_state_view* dst) {
 }
 
 int ludax_set_state(ludax_env* env, const ludax_state_view* src) {
+    ludax::ApiRange api_range("ludax_set_state");
     if (!env || !src || !src->board || !src->to_move || !src->ply || !src->passes || !src->outcome) return LUDAX_ERR_ARG;
     if (!aligned(src->ply, 2)) return LUDAX_ERR_ALIGN;
     ludax_state_view v = *src;
@@ -1068,6 +1078,7 @@ int ludax_state_bits_words(const ludax_env* env, int32_t* words_per_env) {
 }
 
 int ludax_get_state_bits(ludax_env* env, uint64_t* planes_dev, uint32_t* meta_dev) {
+    ludax::ApiRange api_range("ludax_get_state_bits");
     if (!env || !planes_dev || !meta_dev) return LUDAX_ERR_ARG;
     if (!aligned(planes_dev, 8) || !aligned(meta_dev, 4)) return LUDAX_ERR_ALIGN;
     int W, V;
@@ -1080,6 +1091,7 @@ int ludax_get_state_bits(ludax_env* env, uint64_t* planes_dev, uint32_t* meta_de
 }
 
 int ludax_set_state_bits(ludax_env* env, const uint64_t* planes_dev, const uint32_t* meta_dev) {
+    ludax::ApiRange api_range("ludax_set_state_bits");
     if (!env || !planes_dev || !meta_dev) return LUDAX_ERR_ARG;
     if (!aligned(planes_dev, 8) || !aligned(meta_dev, 4)) return LUDAX_ERR_ALIGN;
     int W, V;
@@ -1154,6 +1166,7 @@ int ludax_autotune_env_candidates(const ludax_env* env, ludax_launch_cfg* out, i
 
 int ludax_autotune_env(ludax_env* env, uint64_t seed, int32_t reps, ludax_launch_cfg* best_out, float* best_ms_out,
                        float* ms_table_out, int32_t* n_candidates_out) {
+    ludax::ApiRange api_range("ludax_autotune_env");
     if (!env || !best_out || reps < 1) return LUDAX_ERR_ARG;
     const int nc = ludax_autotune_env_candidates(env, nullptr, 0);
     ludax_launch_cfg* cands = new (std::nothrow) ludax_launch_cfg[(size_t)nc];

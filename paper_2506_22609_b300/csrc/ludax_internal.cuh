@@ -2,6 +2,7 @@
 // translation units (the env handle and the game dispatcher).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ludax.h"
 #include "ludax_state.cuh"
@@ -169,5 +170,15 @@ cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned b
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
+
+// An NVTX range over one C-ABI call, named after it, so that a profiler or
+// tracer attributes the call's host work and launches to it; with no tool
+// attached a push or pop is one check of a function pointer.
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange&) = delete;
+    ApiRange& operator=(const ApiRange&) = delete;
+};
 
 }  // namespace ludax

@@ -504,6 +504,7 @@ int ludax_mcts_reserve(ludax_env* env, int32_t iterations, double c) {
 
 int ludax_mcts_search(ludax_env* env, uint64_t seed, int32_t iterations, double c, int32_t* action_dev,
                       uint32_t* visits_dev, uint32_t* wins_dev) {
+    ludax::ApiRange api_range("ludax_mcts_search");
     if (!env || !action_dev || iterations < 1 || iterations > LUDAX_MCTS_MAX_ITERS || !valid_c(c)) return LUDAX_ERR_ARG;
     if (!aligned(action_dev, 4) || (visits_dev && !aligned(visits_dev, 4)) || (wins_dev && !aligned(wins_dev, 4)))
         return LUDAX_ERR_ALIGN;
@@ -524,6 +525,7 @@ int ludax_mcts_search(ludax_env* env, uint64_t seed, int32_t iterations, double 
 
 int ludax_mcts_play(ludax_env* env, uint64_t seed, uint32_t flags, int32_t iters_p1, int32_t iters_p2, double c,
                     int8_t* outcome_dev, int16_t* plies_dev, int16_t* agency_dev, int16_t* coverage_dev) {
+    ludax::ApiRange api_range("ludax_mcts_play");
     if (!env || iters_p1 < 1 || iters_p2 < 1 || iters_p1 > LUDAX_MCTS_MAX_ITERS || iters_p2 > LUDAX_MCTS_MAX_ITERS ||
         !valid_c(c))
         return LUDAX_ERR_ARG;
@@ -554,6 +556,7 @@ int ludax_mcts_play(ludax_env* env, uint64_t seed, uint32_t flags, int32_t iters
 int ludax_mcts_play_mixed(const int32_t* desc_host, const int32_t* iters_host, int64_t n, int64_t env_offset,
                           uint64_t seed, double c, int8_t* outcome_dev, int16_t* plies_dev, int16_t* agency_dev,
                           int16_t* coverage_dev, void* stream, int64_t* bad_index) {
+    ludax::ApiRange api_range("ludax_mcts_play_mixed");
     if (bad_index) *bad_index = -1;
     if (!desc_host || !iters_host || n < 1 || n > 0x7FFFFFFFll || env_offset < 0 || !valid_c(c)) return LUDAX_ERR_ARG;
     if ((plies_dev && !aligned(plies_dev, 2)) || (agency_dev && !aligned(agency_dev, 2)) ||

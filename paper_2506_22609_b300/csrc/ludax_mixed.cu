@@ -525,6 +525,7 @@ extern "C" {
 
 int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,
                         int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg, void* stream) {
+    ludax::ApiRange api_range("ludax_rollout_mixed");
     if (!desc_dev || !outcome_dev || !plies_dev || num_envs < 1 || num_envs > 0x7FFFFFFFll || env_offset < 0)
         return LUDAX_ERR_ARG;
     if (((uintptr_t)desc_dev % 4) || ((uintptr_t)plies_dev % 2)) return LUDAX_ERR_ALIGN;
@@ -566,6 +567,7 @@ int ludax_rollout_mixed(const int32_t* desc_dev, int64_t num_envs, int64_t env_o
 
 int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int64_t num_envs, int64_t env_offset,
                             const ludax_launch_cfg* cfg, void* stream, int64_t* bad_index) {
+    ludax::ApiRange api_range("ludax_mixed_plan_create");
     if (!out || !desc_dev || num_envs < 1 || num_envs > 0x7FFFFFFFll || env_offset < 0) return LUDAX_ERR_ARG;
     *out = nullptr;
     if ((uintptr_t)desc_dev % 4) return LUDAX_ERR_ALIGN;
@@ -648,6 +650,7 @@ int ludax_mixed_plan_create(ludax_mixed_plan** out, const int32_t* desc_dev, int
 }
 
 int ludax_mixed_plan_launch(ludax_mixed_plan* p, uint64_t seed, int8_t* outcome_dev, int16_t* plies_dev) {
+    ludax::ApiRange api_range("ludax_mixed_plan_launch");
     if (!p || !outcome_dev || !plies_dev) return LUDAX_ERR_ARG;
     if ((uintptr_t)plies_dev % 2) return LUDAX_ERR_ALIGN;
     p->args.seed_key = splitmix64(seed);
@@ -681,6 +684,7 @@ struct HostLayout {
 
 int ludax_mixed_plan_launch_host(ludax_mixed_plan* p, uint64_t seed, const int32_t* desc_host, int8_t* outcome_host,
                                  int16_t* plies_host) {
+    ludax::ApiRange api_range("ludax_mixed_plan_launch_host");
     if (!p || !desc_host || !outcome_host || !plies_host) return LUDAX_ERR_ARG;
     const long long n = p->n;
     const HostLayout L(n);
@@ -786,6 +790,7 @@ int ludax_autotune_candidates(ludax_launch_cfg* out, int32_t max_out) {
 
 int ludax_autotune(const int32_t* desc_dev, int64_t num_envs, uint64_t seed, int32_t reps, void* stream,
                    ludax_launch_cfg* best_out, float* best_ms_out, float* ms_table_out, int32_t* n_candidates_out) {
+    ludax::ApiRange api_range("ludax_autotune");
     if (!desc_dev || !best_out || num_envs < 1 || reps < 1) return LUDAX_ERR_ARG;
     int nc = ludax_autotune_candidates(nullptr, 0);
     std::vector<ludax_launch_cfg> cands((size_t)nc);
@@ -933,6 +938,7 @@ __global__ void noalloc_scatter_kernel(const int32_t* desc, long long n, BucketB
 extern "C" int ludax_rollout_mixed_noalloc(const int32_t* desc_dev, int64_t num_envs, int64_t env_offset, uint64_t seed,
                                            int8_t* outcome_dev, int16_t* plies_dev, const ludax_launch_cfg* cfg,
                                            void* stream, int64_t* bad_index) {
+    ludax::ApiRange api_range("ludax_rollout_mixed_noalloc");
     if (!desc_dev || !outcome_dev || !plies_dev || num_envs < 1 || env_offset < 0) return LUDAX_ERR_ARG;
     if (num_envs > kNoAllocMaxEnvs) return LUDAX_ERR_SIZE;  // more envs than the static queue holds
     if (((uintptr_t)desc_dev % 4) || ((uintptr_t)plies_dev % 2)) return LUDAX_ERR_ALIGN;

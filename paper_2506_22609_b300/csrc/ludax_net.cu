@@ -991,6 +991,7 @@ int ludax_net_set_state(ludax_net* n, const float* params_dev, const float* m_de
 }
 
 int ludax_net_forward(ludax_net* n, const uint16_t* x_dev, int64_t B, float* p_dev) {
+    ludax::ApiRange api_range("ludax_net_forward");
     int st = net_check(n, B);
     if (st) return st;
     if (!x_dev || !p_dev) return LUDAX_ERR_ARG;
@@ -999,6 +1000,7 @@ int ludax_net_forward(ludax_net* n, const uint16_t* x_dev, int64_t B, float* p_d
 }
 
 int ludax_net_grad(ludax_net* n, const uint16_t* x_dev, const float* y_dev, int64_t B, float* grad_dev, float* loss_dev) {
+    ludax::ApiRange api_range("ludax_net_grad");
     int st = net_check(n, B);
     if (st) return st;
     if (!x_dev || !y_dev) return LUDAX_ERR_ARG;
@@ -1012,6 +1014,7 @@ int ludax_net_grad(ludax_net* n, const uint16_t* x_dev, const float* y_dev, int6
 }
 
 int ludax_net_train_step(ludax_net* n, const uint16_t* x_dev, const float* y_dev, int64_t B, float lr, float* loss_dev) {
+    ludax::ApiRange api_range("ludax_net_train_step");
     int st = net_check(n, B);
     if (st) return st;
     if (!x_dev || !y_dev) return LUDAX_ERR_ARG;
@@ -1026,6 +1029,7 @@ int ludax_net_train_step(ludax_net* n, const uint16_t* x_dev, const float* y_dev
 }
 
 int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld) {
+    ludax::ApiRange api_range("ludax_pack_inputs");
     if (!env || !x_dev || ld < 2 * env->cells + 1 || ld % 8) return LUDAX_ERR_ARG;
     if ((uintptr_t)x_dev % 16) return LUDAX_ERR_ALIGN;
     return dispatch_game(env->game, env->rows, env->cols, [&](auto tag) {
@@ -1042,6 +1046,7 @@ int ludax_pack_inputs(ludax_env* env, uint16_t* x_dev, int32_t ld) {
 }
 
 int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K, int32_t plies, float* value_dev) {
+    ludax::ApiRange api_range("ludax_truncated_value");
     if (!env || !n || !value_dev || K < 1 || plies < 0) return LUDAX_ERR_ARG;
     if (n->cells != env->cells) return LUDAX_ERR_SIZE;
     if (n->stream != env->stream) return LUDAX_ERR_ARG;

@@ -1038,6 +1038,7 @@ extern "C" {
 
 int ludax_dense_bf16_relu(const uint16_t* a_dev, const uint16_t* b_dev, const float* bias_dev, uint16_t* out_dev,
                           int32_t M, int32_t N, int32_t K, int32_t ld_out, void* stream) {
+    ludax::ApiRange api_range("ludax_dense_bf16_relu");
     if (!a_dev || !b_dev || !bias_dev || !out_dev) return LUDAX_ERR_ARG;
     return ludax::umma_dense_relu(a_dev, b_dev, bias_dev, out_dev, M, N, K, ld_out, (cudaStream_t)stream);
 }
