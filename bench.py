@@ -303,6 +303,40 @@ def time_steps(fn, steps, warmup, flush_buf, stream):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+# Outcome statistics of the last timed launch (set by bench_rollout_config and
+# bench_mixed, read into the JSON line): wins of P1 and P2, draws, capped
+# games (which a correct kernel never produces) and the mean game length.
+LAST_OUTCOMES = {}
+
+
+def note_outcomes(out, plies):
+    import torch
+
+    o = out.to(torch.int64)
+    n = o.numel()
+    LAST_OUTCOMES.clear()
+    LAST_OUTCOMES.update({"p1_wins": int((o == 1).sum().item()), "p2_wins": int((o == 2).sum().item()),
+                          "draws": int((o == 0).sum().item()), "other": int(((o < 0) | (o > 2)).sum().item()),
+                          "mean_plies": round(float(plies.to(torch.float64).mean().item()), 4), "games": n})
+
+
+def source_fingerprint():
+    """SHA-256 over the library's sources, the header, the Python package and
+    this script (the GPU machine's copy of the repository has no git history)."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2506_22609_b300", "csrc", "*")) +
+                   glob.glob(os.path.join(ROOT, "paper_2506_22609_b300", "*.py")) +
+                   [os.path.join(ROOT, "include", "ludax.h"), os.path.abspath(__file__)])
+    for f in files:
+        h.update(os.path.relpath(f, ROOT).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def bench_rollout_config(L, W, cfg, steps, warmup, flush_buf, rank=0):
     """Fused playout of one single-game config; returns a dict of numbers."""
     import torch
@@ -316,6 +350,7 @@ def bench_rollout_config(L, W, cfg, steps, warmup, flush_buf, rank=0):
     fn = lambda: L.ludax_rollout(env.handle, cfg.seed, L.LUDAX_ROLLOUT_FROM_START, None, out, plies, lc)  # noqa: E731
     ms = time_steps(fn, steps, warmup, flush_buf, stream)
     steps_per_launch = int(plies.to(torch.int64).sum().item())
+    note_outcomes(out, plies)
     return env, lc, ms, steps_per_launch
 
 
@@ -410,6 +445,7 @@ def bench_mixed(L, W, steps, warmup, flush_buf, rank=0):
     ms = time_steps(fn, steps, warmup, flush_buf, torch.cuda.current_stream())
     total = int(plies.to(torch.int64).sum().item())
     per_game = torch.bincount((d & 0xFF).long(), weights=plies.double()).cpu().tolist()
+    note_outcomes(out, plies)
     L.ludax_mixed_plan_destroy(plan)
     return ms, total, {g: int(v) for g, v in enumerate(per_game) if v}
 
@@ -976,7 +1012,10 @@ def main():
                        "timing": "CUDA events around each launch on the launching stream, summed over steps",
                        "env_steps_per_launch": steps_per_launch, "episodes_per_launch": n_envs},
             "roofline": roofline, "clocks": clocks,
-            "gpu_launches": args.steps}
+            "gpu_launches": args.steps,
+            "outcomes": dict(LAST_OUTCOMES),
+            "run": {"source_sha256": source_fingerprint(), "gpu": torch.cuda.get_device_name(),
+                    "cuda_runtime": torch.version.cuda, "torch": torch.__version__}}
 
     if rank == 0 and cfg is not None and args.workload != "step_c4":
         e2e_val, h2d, d2h, dt, _, link, spl = e2e_rollout(L, cfg, max(3, min(args.steps, 100)), 3, rank)
