@@ -782,8 +782,8 @@ struct AdamStep {
 // Backward pass after net_forward with labels y: the gradient into n->g
 // (adam == nullptr) or one Adam step applied to the parameters, and the mean
 // loss into loss_out (nullable).  Launches: the head's backward (dZ2 and its
-// bias / weight sums), dZ1 with db1's column sums, the two weight gradients
-// as split-K partials, and finish_kernel, which reduces every partial and
+// bias / weight sums), dW2 as split-K partials, dZ1 with db1's column sums,
+// dW1 as split-K partials, and finish_kernel, which reduces every partial and
 // stores or applies the gradient.
 int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float* y, float* loss_out,
                  const AdamStep* adam) {
@@ -795,8 +795,23 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
                          (const float*)(tc ? n->zp : nullptr), n->zparts, y, (const float*)(n->p + n->ob3), (int)B, n->dZ2,
                          n->hp) != cudaSuccess)
         return LUDAX_ERR_CUDA;
+    // dW2 = dZ2^T . H1 and dW1 = dZ1^T . X, split over the batch into partial sums.
+    // dW2 runs first, while the dZ2 rows just written are still in L2; dZ1
+    // then runs just before dW1, which reads the dZ1 rows it leaves in L2.
+    auto weight_grad = [&](const __nv_bfloat16* A, const __nv_bfloat16* Bm, int N, int ldb, float* part,
+                           long long cap, int& splits) -> int {
+        if (tc && umma_dense_supported(kH, N, (int)B))
+            return umma_grad_weights(A, kH, Bm, ldb, kH, N, (int)B, part, cap, &splits, s);
+        splits = (int)std::min<long long>(32, B / BKT);
+        while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
+        GemmArgs a{};
+        a.A = A; a.B = Bm; a.M = kH; a.N = N; a.K = (int)B; a.lda = kH; a.ldb = ldb; a.partial = part;
+        return launch_gemm<false, false, EPI_PARTIAL>(a, splits, s);
+    };
+    int st, s2 = 0, s1 = 0;
+    if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->w2p, n->w2_floats, s2))) return st;
     // dZ1 = (dZ2 . W2) * [H1 > 0], and db1 = its column sums as partial rows
-    int st, crows;
+    int crows;
     if (tc) {
         crows = umma_grad_colrows((int)B, kH);
         if (crows <= 0 || crows > n->cp_rows) return LUDAX_ERR_CUDA;
@@ -810,19 +825,6 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
         crows = chunks;
     }
     if (st) return st;
-    // dW2 = dZ2^T . H1 and dW1 = dZ1^T . X, split over the batch into partial sums
-    auto weight_grad = [&](const __nv_bfloat16* A, const __nv_bfloat16* Bm, int N, int ldb, float* part,
-                           long long cap, int& splits) -> int {
-        if (tc && umma_dense_supported(kH, N, (int)B))
-            return umma_grad_weights(A, kH, Bm, ldb, kH, N, (int)B, part, cap, &splits, s);
-        splits = (int)std::min<long long>(32, B / BKT);
-        while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
-        GemmArgs a{};
-        a.A = A; a.B = Bm; a.M = kH; a.N = N; a.K = (int)B; a.lda = kH; a.ldb = ldb; a.partial = part;
-        return launch_gemm<false, false, EPI_PARTIAL>(a, splits, s);
-    };
-    int s2 = 0, s1 = 0;
-    if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->w2p, n->w2_floats, s2))) return st;
     if ((st = weight_grad(n->dZ1, X, n->kpad, n->kpad, n->w1p, n->w1_floats, s1))) return st;
     FinishArgs f{};
     f.w1p = n->w1p; f.w2p = n->w2p; f.cp = n->cp; f.hp = n->hp;
