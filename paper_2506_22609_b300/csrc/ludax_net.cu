@@ -578,7 +578,8 @@ constexpr int LEAF_THREADS = 128;
 template <class G>
 __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(EnvDev d, long long e0, long long n_chunk, int K,
                                                              uint64_t seed, int plies, __nv_bfloat16* X, int ld,
-                                                             int kuse, float* score, uint8_t* done) {
+                                                             int kuse, float* score, uint8_t* done, long long rows_pad) {
+    pdl_wait();
     __shared__ uint64_t bits[LEAF_THREADS / 32][32][4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x, total = n_chunk * K;
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(LEAF_THREADS) leaf_kernel(EnvDev d, long long 
     const long long t0 = t - lane;
     const uint8_t* rb = reinterpret_cast<const uint8_t*>(&bits[wib][0][0]);
     if (8 * lane < kuse) {
-        for (int r = 0; r < 32 && t0 + r < total; ++r) {
+        for (int r = 0; r < 32 && t0 + r < rows_pad; ++r) {  // rows past the last continuation: zero
             const uint32_t v = rb[r * 32 + lane];  // columns 8 * lane .. 8 * lane + 7 of row t0 + r
             const uint4 o = make_uint4(bf16_pair(v), bf16_pair(v >> 2), bf16_pair(v >> 4), bf16_pair(v >> 6));
             *reinterpret_cast<uint4*>(X + (size_t)(t0 + r) * ld + 8 * lane) = o;
@@ -624,6 +625,28 @@ __global__ void combine_kernel(long long e0, long long n_chunk, int K, const flo
     for (int j = 0; j < K; ++j) {
         long long t = i * K + j;
         a += done[t] ? score[t] : p[t];
+    }
+    value[e0 + i] = a / (float)K;
+}
+
+// The same mean with each continuation's p formed here from its row's head
+// partials (as head_finish_kernel forms it): one launch instead of two.
+__global__ void combine_z_kernel(long long e0, long long n_chunk, int K, const float* score, const uint8_t* done,
+                                 const float* zpart, int parts, const float* b3, float* value) {
+    pdl_wait();
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_chunk) return;
+    float a = 0.f;
+    for (int j = 0; j < K; ++j) {
+        long long t = i * K + j;
+        if (done[t]) {
+            a += score[t];
+        } else {
+            float z = 0.f;
+            for (int q = 0; q < parts; ++q) z += zpart[(size_t)t * parts + q];
+            const float v = tanhf(z + b3[0]);
+            a += 0.5f * (v + 1.f);
+        }
     }
     value[e0 + i] = a / (float)K;
 }
@@ -706,6 +729,48 @@ bool tc_layers(const ludax_net* n, long long B) {
     return n->use_tcgen05 && umma_dense_supported((int)B, kH, kH);
 }
 
+// Inference runs on tcgen05 (the layers, with the head in the second one's
+// epilogue) for these batches and input widths.
+bool infer_tc(const ludax_net* n, long long B, int kuse) {
+    return n->use_tcgen05 && umma_dense_supported((int)B, kH, kuse) && umma_dense_supported((int)B, kH, kH);
+}
+
+// Both hidden layers and the head's dot products of an inference forward (no
+// labels): the partials of each row's z into *zpart, *parts per row -- from
+// the one-launch MLP (layer 1's rows through an L2-resident scratch), or from
+// two layer launches when the scratch cannot be had or tensor path 2 is set.
+int infer_head(ludax_net* n, const __nv_bfloat16* X, long long B, int kuse, const float** zpart_out, int* parts_out) {
+    cudaStream_t s = n->stream;
+    if (!n->mlp_scratch && n->use_tcgen05 == 1) {
+        const int rows = umma_mlp_scratch_rows();
+        if (rows > 0 && cudaMalloc(&n->mlp_scratch, sizeof(__nv_bfloat16) * (size_t)rows * kH) == cudaSuccess &&
+            cudaMalloc(&n->mlp_z, sizeof(float) * 4 * (size_t)n->max_batch) == cudaSuccess) {
+            n->mlp_rows = rows;
+        } else {  // no scratch: the two-launch form below
+            cudaGetLastError();
+            cudaFree(n->mlp_scratch);
+            n->mlp_scratch = nullptr;
+        }
+    }
+    int st;
+    float* zpart;
+    if (n->mlp_scratch && n->use_tcgen05 == 1) {  // both layers and the head in one launch, layer 1's rows through L2
+        zpart = n->mlp_z;
+        *parts_out = 4;
+        st = umma_mlp_head(X, n->kpad, kuse, n->W1b, n->kpad, n->p + n->ob1, n->W2b, n->p + n->ob2, n->w3b, zpart,
+                           n->mlp_scratch, n->mlp_rows, (int)B, s);
+    } else {
+        zpart = n->g3;  // 2 floats per row: g3 and sqerr are unused without labels
+        *parts_out = kH / 256;
+        st = umma_dense_relu_ex(X, n->kpad, n->W1b, n->kpad, n->p + n->ob1, n->H1, kH, nullptr, nullptr, (int)B, kH,
+                                kuse, s);
+        if (!st)
+            st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, nullptr, 0, n->w3b, zpart, (int)B, kH, kH, s);
+    }
+    *zpart_out = zpart;
+    return st;
+}
+
 // Forward pass to p (and, with labels y, the per-row gradient g3 of the loss,
 // or on the tcgen05 training path the head partials it is formed from; p is
 // then not written).
@@ -715,33 +780,10 @@ bool tc_layers(const ludax_net* n, long long B) {
 int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, const float* y, int kuse = 0) {
     cudaStream_t s = n->stream;
     if (kuse <= 0) kuse = n->kpad;
-    if (!y && p && n->use_tcgen05 && umma_dense_supported((int)B, kH, kuse) && umma_dense_supported((int)B, kH, kH)) {
-        if (!n->mlp_scratch && n->use_tcgen05 == 1) {
-            const int rows = umma_mlp_scratch_rows();
-            if (rows > 0 && cudaMalloc(&n->mlp_scratch, sizeof(__nv_bfloat16) * (size_t)rows * kH) == cudaSuccess &&
-                cudaMalloc(&n->mlp_z, sizeof(float) * 4 * (size_t)n->max_batch) == cudaSuccess) {
-                n->mlp_rows = rows;
-            } else {  // no scratch: the two-launch form below
-                cudaGetLastError();
-                cudaFree(n->mlp_scratch);
-                n->mlp_scratch = nullptr;
-            }
-        }
-        int st, parts;
-        float* zpart;
-        if (n->mlp_scratch && n->use_tcgen05 == 1) {  // both layers and the head in one launch, layer 1's rows through L2
-            zpart = n->mlp_z;
-            parts = 4;
-            st = umma_mlp_head(X, n->kpad, kuse, n->W1b, n->kpad, n->p + n->ob1, n->W2b, n->p + n->ob2, n->w3b, zpart,
-                               n->mlp_scratch, n->mlp_rows, (int)B, s);
-        } else {
-            zpart = n->g3;  // 2 floats per row: g3 and sqerr are unused without labels
-            parts = kH / 256;
-            st = umma_dense_relu_ex(X, n->kpad, n->W1b, n->kpad, n->p + n->ob1, n->H1, kH, nullptr, nullptr, (int)B, kH,
-                                    kuse, s);
-            if (!st)
-                st = umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, nullptr, 0, n->w3b, zpart, (int)B, kH, kH, s);
-        }
+    if (!y && p && infer_tc(n, B, kuse)) {
+        const float* zpart;
+        int parts;
+        const int st = infer_head(n, X, B, kuse, &zpart, &parts);
         if (st) return st;
         head_finish_kernel<<<blocks_for(B, 256), 256, 0, s>>>(zpart, parts, n->p + n->ob3, (int)B, p, nullptr,
                                                                nullptr, nullptr);
@@ -1063,15 +1105,27 @@ int ludax_truncated_value(ludax_env* env, ludax_net* n, uint64_t seed, int32_t K
         for (long long e0 = 0; e0 < env->n; e0 += chunk) {
             long long nc = std::min(chunk, env->n - e0);
             long long rows = nc * K, rows_pad = ((rows + BM - 1) / BM) * BM;
-            if (rows_pad > rows &&
-                cudaMemsetAsync(n->Xleaf + (size_t)rows * n->kpad, 0,
-                                sizeof(__nv_bfloat16) * (size_t)(rows_pad - rows) * n->kpad, env->stream) != cudaSuccess)
-                return LUDAX_ERR_CUDA;
             // the first layer reads only the 64-column blocks that hold the
-            // 2 * cells + 1 inputs; the leaf rows are written that far
+            // 2 * cells + 1 inputs; the leaf rows are written that far, and the
+            // padding rows up to a multiple of 128 as zeros
             const int kuse = ((n->kin + 63) / 64) * 64;
-            leaf_kernel<G><<<blocks_for(rows, LEAF_THREADS), LEAF_THREADS, 0, env->stream>>>(
-                d, e0, nc, K, seed, plies, n->Xleaf, n->kpad, kuse, n->score, n->done);
+            if (launch_dependent(leaf_kernel<G>, blocks_for(rows_pad, LEAF_THREADS), LEAF_THREADS, 0, env->stream, d,
+                                 e0, nc, K, seed, plies, n->Xleaf, (int)n->kpad, kuse, n->score, n->done,
+                                 rows_pad) != cudaSuccess)
+                return LUDAX_ERR_CUDA;
+            // with one or two continuations per position the mean takes each p from its head partials
+            // (one launch instead of two); with more, a thread per continuation forms p first
+            if (K <= 2 && infer_tc(n, rows_pad, kuse)) {
+                const float* zpart;
+                int parts;
+                int st = infer_head(n, n->Xleaf, rows_pad, kuse, &zpart, &parts);
+                if (st) return st;
+                if (launch_dependent(combine_z_kernel, blocks_for(nc, 256), 256, 0, env->stream, e0, nc, K,
+                                     (const float*)n->score, (const uint8_t*)n->done, zpart, parts,
+                                     (const float*)(n->p + n->ob3), value_dev) != cudaSuccess)
+                    return LUDAX_ERR_CUDA;
+                continue;
+            }
             int st = net_forward(n, n->Xleaf, rows_pad, n->pout, nullptr, kuse);
             if (st) return st;
             combine_kernel<<<blocks_for(nc, 256), 256, 0, env->stream>>>(e0, nc, K, n->score, n->done, n->pout, value_dev);

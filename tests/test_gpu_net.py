@@ -336,9 +336,12 @@ def test_training_fits_a_fixed_target(L):
     assert last < 0.1 * first and last < 0.1 * y.var()
 
 
+# K = 1, 2: the mean forms p from the head partials itself; K = 4: through the
+# head's finish; 200 positions leave padding rows up to 256 (zeroed by the leaf kernel)
+@pytest.mark.parametrize("Kc", [1, 2, 4])
 @pytest.mark.parametrize("name,game,rows,cols", [("othello", G.OTHELLO, 8, 8), ("hex7", G.HEX, 7, 7)])
-def test_truncated_value_matches_oracle(L, name, game, rows, cols):
-    n, Kc, plies, seed = 200, 4, 8, 99
+def test_truncated_value_matches_oracle(L, name, game, rows, cols, Kc):
+    n, plies, seed = 200, 8, 99
     cells = rows * cols
     K = W.net_in_pad(cells)
     s = positions(game, rows, cols, n, 4)
