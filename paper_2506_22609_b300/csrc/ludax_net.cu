@@ -242,8 +242,10 @@ __global__ void head_forward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16
 // Row-chunk kernels over [B][kH] BF16 matrices: a 256-thread block takes
 // HB_ROWS rows; its thread t covers columns 8 (t % 64) .. 8 (t % 64) + 7 of
 // rows r0 + t / 64, r0 + t / 64 + 4, ... (16-byte loads, four rows in
-// flight), and the four row groups' sums are added in a fixed order.
-constexpr int HB_ROWS = 128, HB_GROUPS = 4;
+// flight), and the four row groups' sums are added in a fixed order.  112
+// rows make a 65,536-row batch 586 chunks, one wave of four resident blocks
+// on each of 148 SMs (128 rows left 512 blocks spread 3 or 4 per SM).
+constexpr int HB_ROWS = 112, HB_GROUPS = 4;
 constexpr int HB_COLS = 2 * kH + 2;  // head partials per chunk: db2 | dw3 | db3 | squared error
 
 __device__ __forceinline__ void load8(const __nv_bfloat16* p, float* f) {
@@ -287,6 +289,15 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
 #pragma unroll
     for (int e = 0; e < 8; ++e) ab[e] = aw[e] = 0.f;
     const int r0 = blockIdx.x * HB_ROWS, r1 = min(r0 + HB_ROWS, B);
+    // the thread's first HB_PRE rows of H2 are fetched first, so that their
+    // loads overlap the loss-gradient phase below
+    constexpr int HB_PRE = 4;
+    uint4 pre[HB_PRE];
+#pragma unroll
+    for (int k = 0; k < HB_PRE; ++k) {
+        const int r = r0 + grp + k * HB_GROUPS;
+        if (r < r1) pre[k] = *reinterpret_cast<const uint4*>(H2 + (size_t)r * kH + j0);
+    }
     for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) {  // each row's loss gradient once
         float gr, se;
         if (zpart) head_row(zpart, zparts, y, b3, B, r0 + i, gr, se);
@@ -295,11 +306,17 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
         ss[i] = se;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int r = r0 + grp; r < r1; r += HB_GROUPS) {
+    // one row: dZ2 = g3 * w3 where H2 > 0, and the running sums
+    auto row = [&](int r, const uint4& raw) {
         const float gr = sg[r - r0], se = ss[r - r0];
         float h[8];
-        load8(H2 + (size_t)r * kH + j0, h);
+        const __nv_bfloat162* hb = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 x = __bfloat1622float2(hb[e]);
+            h[2 * e] = x.x;
+            h[2 * e + 1] = x.y;
+        }
         __align__(16) __nv_bfloat162 d[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -315,7 +332,15 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
             ag += gr;
             al += se;
         }
+    };
+#pragma unroll
+    for (int k = 0; k < HB_PRE; ++k) {
+        const int r = r0 + grp + k * HB_GROUPS;
+        if (r < r1) row(r, pre[k]);
     }
+#pragma unroll 4
+    for (int r = r0 + grp + HB_PRE * HB_GROUPS; r < r1; r += HB_GROUPS)
+        row(r, *reinterpret_cast<const uint4*>(H2 + (size_t)r * kH + j0));
     if (grp > 0) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -437,38 +462,73 @@ __device__ __forceinline__ void apply_grad(const FinishArgs& a, long long i, flo
     else if (i >= c.ow3 && i < c.ob3) c.bf[i - 2 * kH] = __float2bfloat16_rn(pi);
 }
 
-constexpr int FIN_THREADS = 256, FIN_WARPS = FIN_THREADS / 32;
+// the same for four consecutive weights (i a multiple of 4, inside W1 or
+// W2), with their Adam state m0, v0, p0 read before the gradient was formed
+__device__ __forceinline__ void adam4(const FinishArgs& a, long long i, const float4& g, const float4& m0,
+                                      const float4& v0, const float4& p0) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float gs[4] = {g.x, g.y, g.z, g.w}, ms[4] = {m0.x, m0.y, m0.z, m0.w}, vs[4] = {v0.x, v0.y, v0.z, v0.w},
+                ps[4] = {p0.x, p0.y, p0.z, p0.w};
+    float mo[4], vo[4], po[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        mo[k] = b1 * ms[k] + (1.f - b1) * gs[k];
+        vo[k] = b2 * vs[k] + (1.f - b2) * gs[k] * gs[k];
+        po[k] = ps[k] - a.lr * (mo[k] / a.bc1) / (sqrtf(vo[k] / a.bc2) + eps);
+    }
+    *reinterpret_cast<float4*>(a.m + i) = make_float4(mo[0], mo[1], mo[2], mo[3]);
+    *reinterpret_cast<float4*>(a.v + i) = make_float4(vo[0], vo[1], vo[2], vo[3]);
+    *reinterpret_cast<float4*>(a.p + i) = make_float4(po[0], po[1], po[2], po[3]);
+    const long long j = i < a.c.ob1 ? i : i - kH;  // W1 | W2 back to back in the BF16 copy
+    __align__(8) __nv_bfloat162 h[2] = {__floats2bfloat162_rn(po[0], po[1]), __floats2bfloat162_rn(po[2], po[3])};
+    *reinterpret_cast<uint2*>(a.c.bf + j) = *reinterpret_cast<const uint2*>(h);
+}
+
+constexpr int FIN_THREADS = 256, FIN_WARPS = FIN_THREADS / 32, FIN_BATCH = 10, FIN_ROWS = 16;
 constexpr int FIN_LONG = kH / 32 + (HB_COLS + 31) / 32;  // blocks of 32 bias / head columns
 
 __global__ void __launch_bounds__(FIN_THREADS) finish_kernel(FinishArgs a) {
     pdl_wait();
-    if ((int)blockIdx.x >= FIN_LONG) {  // W1 and W2: four elements per thread, 16 splits in flight
+    if ((int)blockIdx.x >= FIN_LONG) {  // W1 and W2: four elements per thread, FIN_BATCH splits in flight
         const long long t = (long long)(blockIdx.x - FIN_LONG) * FIN_THREADS + threadIdx.x, e = 4 * t;
         if (e >= a.n1 + a.n2) return;
         const bool w1 = e < a.n1;
         const float* src = w1 ? a.w1p + e : a.w2p + (e - a.n1);
         const long long stride = w1 ? a.n1 : a.n2, flat = w1 ? e : a.c.oW2 + (e - a.n1);
         const int splits = w1 ? a.s1 : a.s2;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        auto add = [&](const float4& x) {
-            acc.x += x.x;
-            acc.y += x.y;
-            acc.z += x.z;
-            acc.w += x.w;
-        };
-        int s0 = 0;
-        for (; s0 + 16 <= splits; s0 += 16) {  // 16 loads issued, then added in split order
-            float4 x[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) x[k] = __ldcg(reinterpret_cast<const float4*>(src + (size_t)(s0 + k) * stride));
-#pragma unroll
-            for (int k = 0; k < 16; ++k) add(x[k]);
+        float4 m0, v0, p0;  // the Adam state, fetched while the partials are
+        if (a.adam) {
+            m0 = *reinterpret_cast<const float4*>(a.m + flat);
+            v0 = *reinterpret_cast<const float4*>(a.v + flat);
+            p0 = *reinterpret_cast<const float4*>(a.p + flat);
         }
-        for (; s0 < splits; ++s0) add(__ldcg(reinterpret_cast<const float4*>(src + (size_t)s0 * stride)));
-        apply_grad(a, flat, acc.x);
-        apply_grad(a, flat + 1, acc.y);
-        apply_grad(a, flat + 2, acc.z);
-        apply_grad(a, flat + 3, acc.w);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        // every batch issues all its loads (those past the last split are
+        // predicated off) before adding them in split order, so a split count
+        // that is not a multiple of the batch costs no extra round trips
+        for (int s0 = 0; s0 < splits; s0 += FIN_BATCH) {
+            float4 x[FIN_BATCH];
+#pragma unroll
+            for (int k = 0; k < FIN_BATCH; ++k)
+                if (s0 + k < splits) x[k] = __ldcg(reinterpret_cast<const float4*>(src + (size_t)(s0 + k) * stride));
+#pragma unroll
+            for (int k = 0; k < FIN_BATCH; ++k) {
+                if (s0 + k < splits) {
+                    acc.x += x[k].x;
+                    acc.y += x[k].y;
+                    acc.z += x[k].z;
+                    acc.w += x[k].w;
+                }
+            }
+        }
+        if (a.adam) {
+            adam4(a, flat, acc, m0, v0, p0);
+        } else {
+            a.g[flat] = acc.x;
+            a.g[flat + 1] = acc.y;
+            a.g[flat + 2] = acc.z;
+            a.g[flat + 3] = acc.w;
+        }
         return;
     }
     // 32 columns of the db1 row-group sums, then of the head's chunk sums: the
@@ -481,9 +541,16 @@ __global__ void __launch_bounds__(FIN_THREADS) finish_kernel(FinishArgs a) {
     const int col = blk * 32 + lane, ncols = bias1 ? kH : HB_COLS, rows = bias1 ? a.crows : a.hrows;
     const float* src = bias1 ? a.cp : a.hp;
     float x = 0.f;
-    if (col < ncols) {
-#pragma unroll 8
-        for (int r = w; r < rows; r += FIN_WARPS) x += src[(size_t)r * ncols + col];
+    if (col < ncols) {  // FIN_ROWS rows of a warp in flight, added in row order
+        for (int r0 = w; r0 < rows; r0 += FIN_WARPS * FIN_ROWS) {
+            float v[FIN_ROWS];
+#pragma unroll
+            for (int k = 0; k < FIN_ROWS; ++k)
+                if (r0 + k * FIN_WARPS < rows) v[k] = __ldcg(src + (size_t)(r0 + k * FIN_WARPS) * ncols + col);
+#pragma unroll
+            for (int k = 0; k < FIN_ROWS; ++k)
+                if (r0 + k * FIN_WARPS < rows) x += v[k];
+        }
     }
     sh[w][lane] = x;
     __syncthreads();
@@ -923,11 +990,14 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
     n->w1_floats = (long long)max_splits * kH * n->kpad;
     const long long zp_f = ZPARTS * B, hp_f = up4(chunks * HB_COLS), cp_f = n->cp_rows * kH;
     const long long part_floats = zp_f + hp_f + cp_f + n->w2_floats + n->w1_floats;
-    bool ok = cudaMalloc(&n->p, 4 * n->nparams * sizeof(float)) == cudaSuccess;
+    // p, m, v and g each start on a 16-byte boundary (the finish kernel
+    // reads and writes the Adam state four weights at a time)
+    const long long pstride = up4(n->nparams);
+    bool ok = cudaMalloc(&n->p, 4 * pstride * sizeof(float)) == cudaSuccess;
     if (ok) {
-        n->m = n->p + n->nparams;
-        n->v = n->m + n->nparams;
-        n->g = n->v + n->nparams;
+        n->m = n->p + pstride;
+        n->v = n->m + pstride;
+        n->g = n->v + pstride;
     }
     ok = ok && cudaMalloc(&n->W1b, sizeof(__nv_bfloat16) * ((size_t)kH * n->kpad + (size_t)kH * kH + kH)) == cudaSuccess;
     if (ok) {
@@ -958,7 +1028,7 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
         ludax_net_destroy(n);
         return LUDAX_ERR_NOMEM;
     }
-    if (cudaMemsetAsync(n->p, 0, 4 * n->nparams * sizeof(float), n->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(n->p, 0, 4 * (size_t)(n->m - n->p) * sizeof(float), n->stream) != cudaSuccess ||
         refresh_bf16(n) != LUDAX_OK) {
         ludax_net_destroy(n);
         return LUDAX_ERR_CUDA;
@@ -992,7 +1062,8 @@ int ludax_net_sizes(const ludax_net* n, int32_t* in_pad, int32_t* hidden, int64_
 int ludax_net_set_params(ludax_net* n, const float* params_dev) {
     if (!n || !params_dev) return LUDAX_ERR_ARG;
     if (cudaMemcpyAsync(n->p, params_dev, sizeof(float) * n->nparams, cudaMemcpyDeviceToDevice, n->stream) != cudaSuccess ||
-        cudaMemsetAsync(n->m, 0, 2 * sizeof(float) * n->nparams, n->stream) != cudaSuccess)
+        cudaMemsetAsync(n->m, 0, sizeof(float) * n->nparams, n->stream) != cudaSuccess ||
+        cudaMemsetAsync(n->v, 0, sizeof(float) * n->nparams, n->stream) != cudaSuccess)
         return LUDAX_ERR_CUDA;
     n->t = 0;
     return refresh_bf16(n);
