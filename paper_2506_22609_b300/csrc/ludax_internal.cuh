@@ -124,9 +124,20 @@ int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, cons
                   const float* b2, const void* w3, float* zpart, void* scratch, int scratch_rows, int M,
                   cudaStream_t s);
 // The same launch for training: layer 1's rows kept in H1 [M][512] and layer
-// 2's in H2 [M][512] (BF16), zpart as above (four partials per row).
+// 2's in H2 [M][512] (BF16), zpart as above (four partials per row), and
+// (h1bits non-null) which of H1's values are non-zero as M * 16 words in the
+// layout h1bits_index below.
 int umma_mlp_train(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
-                   const float* b2, const void* w3, float* zpart, void* H1, void* H2, int M, cudaStream_t s);
+                   const float* b2, const void* w3, float* zpart, void* H1, void* H2, uint32_t* h1bits, int M,
+                   cudaStream_t s);
+// Index of the word of a bit mask over an [M][N] matrix (N a multiple of
+// 32) that holds row r, column j, as bit j % 32.  A 32-row group keeps its
+// rows' words for columns 32 w .. 32 w + 31 side by side (row r % 32 at
+// offset r % 32), so the 32 rows of a group read or write one column word as
+// 128 consecutive bytes.
+__host__ __device__ __forceinline__ long long h1bits_index(int r, int j, int N) {
+    return ((long long)(r >> 5) * (N >> 5) + (j >> 5)) * 32 + (r & 31);
+}
 
 // The value net's backward contractions on tcgen05 (ludax_umma.cu).
 // umma_grad_mask: out[m][n] = bf16(mask[m][n] > 0 ? sum_k A[m][k] B[k][n] : 0)
@@ -137,6 +148,11 @@ int umma_mlp_train(const void* X, int ldx, int K1, const void* W1, int ldw1, con
 // partial row is written in full.
 int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, int M, int N, int K, float* colpart,
                    cudaStream_t s);
+// The same with the mask given as bits (h1bits_index layout, bit set where
+// the value is non-zero): the mask then costs M * N / 8 bytes of reads
+// instead of M * N * 2.
+int umma_grad_maskbits(const void* A, const void* B, const uint32_t* maskbits, void* out, int M, int N, int K,
+                       float* colpart, cudaStream_t s);
 int umma_grad_colrows(int M, int N);  // 0 on error; at most 4 * SMs
 // umma_grad_weights: part[p][m][n] = FP32 sum over the p-th of *splits_out
 // contiguous K ranges of A[k][m] B[k][n]; A [K][lda], B [K][ldb] row-major

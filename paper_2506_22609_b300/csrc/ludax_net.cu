@@ -733,6 +733,8 @@ struct ludax_net {
     float *p, *m, *v, *g;
     __nv_bfloat16 *W1b, *W2b, *w3b;
     __nv_bfloat16 *H1, *H2, *dZ2, *dZ1, *Xleaf;
+    uint32_t* h1bits;  // which values of H1 are non-zero (h1bits_index layout), from the one-launch training forward
+    bool h1bits_set;   // the last training forward wrote h1bits
     float *pout, *g3, *sqerr, *score;
     // backward partial sums (see finish_kernel): the training forward's head
     // partials [B][ZPARTS], the head's row-chunk sums, db1's row-group sums
@@ -866,10 +868,11 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
         // head's dot products come out as four partials per row, from which
         // the backward pass's first kernel forms the loss gradient
         const int k1 = std::min(n->kpad, (n->kin + 63) / 64 * 64);
+        n->h1bits_set = n->use_tcgen05 == 1;
         if (n->use_tcgen05 == 1) {
             n->zparts = ZPARTS;
             return umma_mlp_train(X, n->kpad, k1, n->W1b, n->kpad, n->p + n->ob1, n->W2b, n->p + n->ob2, n->w3b,
-                                  n->zp, n->H1, n->H2, (int)B, s);
+                                  n->zp, n->H1, n->H2, n->h1bits, (int)B, s);
         }
         // the two-launch form (tensor path 2): the second layer's epilogue takes two head partials per row
         n->zparts = kH / 256;
@@ -878,6 +881,7 @@ int net_forward(ludax_net* n, const __nv_bfloat16* X, long long B, float* p, con
             return st;
         return umma_dense_relu_ex(n->H1, kH, n->W2b, kH, n->p + n->ob2, n->H2, kH, n->w3b, n->zp, (int)B, kH, kH, s);
     }
+    n->h1bits_set = false;
     if ((st = dense_layer(n, X, n->W1b, n->p + n->ob1, n->H1, B, n->kpad))) return st;
     if ((st = dense_layer(n, n->H1, n->W2b, n->p + n->ob2, n->H2, B, kH))) return st;
     head_forward_kernel<<<blocks_for(B, 8), 256, 0, s>>>(n->H2, n->w3b, n->p + n->ob3, (int)B, p, y, n->g3, n->sqerr);
@@ -924,7 +928,9 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
     if (tc) {
         crows = umma_grad_colrows((int)B, kH);
         if (crows <= 0 || crows > n->cp_rows) return LUDAX_ERR_CUDA;
-        st = umma_grad_mask(n->dZ2, n->W2b, n->H1, n->dZ1, (int)B, kH, kH, n->cp, s);
+        // the mask from H1's bits when the forward left them (4 MB instead of H1's 64 MB at 65,536 rows)
+        st = n->h1bits_set ? umma_grad_maskbits(n->dZ2, n->W2b, n->h1bits, n->dZ1, (int)B, kH, kH, n->cp, s)
+                           : umma_grad_mask(n->dZ2, n->W2b, n->H1, n->dZ1, (int)B, kH, kH, n->cp, s);
     } else {
         GemmArgs a{};
         a.A = n->dZ2; a.B = n->W2b; a.M = (int)B; a.N = kH; a.K = kH; a.lda = kH; a.ldb = kH;
@@ -1004,12 +1010,14 @@ int ludax_net_create(ludax_net** out, int32_t cells, int64_t max_batch, void* st
         n->W2b = n->W1b + (size_t)kH * n->kpad;
         n->w3b = n->W2b + (size_t)kH * kH;
     }
-    ok = ok && cudaMalloc(&n->H1, sizeof(__nv_bfloat16) * (size_t)B * (4 * kH + n->kpad)) == cudaSuccess;
+    // H1 | H2 | dZ2 | dZ1 | Xleaf, then H1's bit mask (kH / 32 words per row)
+    ok = ok && cudaMalloc(&n->H1, sizeof(__nv_bfloat16) * (size_t)B * (4 * kH + n->kpad + kH / 16)) == cudaSuccess;
     if (ok) {
         n->H2 = n->H1 + (size_t)B * kH;
         n->dZ2 = n->H2 + (size_t)B * kH;
         n->dZ1 = n->dZ2 + (size_t)B * kH;
         n->Xleaf = n->dZ1 + (size_t)B * kH;
+        n->h1bits = reinterpret_cast<uint32_t*>(n->Xleaf + (size_t)B * n->kpad);
     }
     ok = ok && cudaMalloc(&n->pout, sizeof(float) * (4 * (size_t)B + part_floats)) == cudaSuccess;
     if (ok) {

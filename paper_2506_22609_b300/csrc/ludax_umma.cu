@@ -226,6 +226,21 @@ __device__ __forceinline__ void stage_chunk(int c, const __nv_bfloat162* v, uint
     }
 }
 
+// Bit k of the result: value k of the 32 BF16 values v (non-negative, as
+// ReLU leaves them) is non-zero.  Per 32-bit word, adding 0x7FFF to each
+// half's magnitude carries into the half's top bit exactly when the half is
+// non-zero (a -0 from the ReLU counts as zero, as in a "> 0" test).
+__device__ __forceinline__ uint32_t nonzero_bits(const __nv_bfloat162* v) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(v);
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t t = ((w[k] & 0x7FFF7FFFu) + 0x7FFF7FFFu) & 0x80008000u;
+        m |= ((t >> 15) & 1u) << (2 * k) | (t >> 31) << (2 * k + 1);
+    }
+    return m;
+}
+
 __global__ void __launch_bounds__(UMMA_THREADS, 1)
     umma_dense_relu_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                            const __grid_constant__ CUtensorMap tmOut, int M, int N, int K,
@@ -391,7 +406,8 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
                          const __grid_constant__ CUtensorMap tmHst, const __grid_constant__ CUtensorMap tmHld,
                          const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmH2, int M,
                          int K1, const float* __restrict__ b1, const float* __restrict__ b2,
-                         const __nv_bfloat16* __restrict__ w3, float* __restrict__ zpart, int train) {
+                         const __nv_bfloat16* __restrict__ w3, float* __restrict__ zpart, int train,
+                         uint32_t* __restrict__ h1bits) {
     ludax::pdl_wait();
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -512,6 +528,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
             drain_accumulator<TN / 64>(base, half * (TN / 64), sbias + n0, [&](int c, const __nv_bfloat162* v) {
                 if (l1) {
                     stage_chunk<2>(c, v, box, lane, &tmHst, n0, srow0);  // layer 1: rows to scratch / H1
+                    if (h1bits) h1bits[ludax::h1bits_index(grow0 + lane, n0 + c * 32, MLP_N)] = nonzero_bits(v);
                 } else {
                     z += dot_chunk(v, sw3 + n0 + c * 32);  // layer 2: the head's dot product
                     if (train) stage_chunk<2>(c, v, box, lane, &tmH2, n0, grow0);
@@ -564,7 +581,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
 // (its 32 rows x 256 columns) in shared memory with cp.async while the
 // tile's MMAs run, rows XOR-swizzled by 16-byte chunk so the per-row reads
 // are conflict-free; with that buffer the ring has three stages.
-enum { GRAD_MASK = 0, GRAD_PARTIAL = 1 };
+enum { GRAD_MASK = 0, GRAD_PARTIAL = 1, GRAD_MASKBITS = 2 };
 constexpr int MN_BOX = 64 * TK * 2;  // one 64 (M or N) x 64 (K) BF16 box
 constexpr int MASK_WARP_BYTES = 32 * TN * 2;
 template <int EPI>
@@ -640,7 +657,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     extern __shared__ __align__(16) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t* staging = smem + NS * STAGE;
-    uint8_t* smask = staging + 4 * BOX_BYTES;  // GRAD_MASK: four warps' mask tiles
+    uint8_t* smask = staging + 4 * BOX_BYTES;  // GRAD_MASK: four warps' mask tiles (GRAD_MASKBITS: read from global)
     uint64_t* full = reinterpret_cast<uint64_t*>(smask + (EPI == GRAD_MASK ? 4 * MASK_WARP_BYTES : 0));
     uint64_t* empty = full + NS;
     uint64_t* acc_full = empty + NS;    // [2] MMA -> epilogue
@@ -755,6 +772,12 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                                       mask + (size_t)(row0 + r) * ldm + n0 + lane * 8);
                 asm volatile("cp.async.commit_group;\n" ::: "memory");
             }
+            uint32_t mw[TN / 32];  // GRAD_MASKBITS: this lane's mask word of each 32-column chunk, fetched before the wait
+            if (EPI == GRAD_MASKBITS) {
+                const uint32_t* bits = reinterpret_cast<const uint32_t*>(mask);
+#pragma unroll
+                for (int c = 0; c < TN / 32; ++c) mw[c] = bits[ludax::h1bits_index(row0 + lane, n0 + c * 32, N)];
+            }
             const int a = local & 1;
             if (ok) ok = mbar_wait(&acc_full[a], (uint32_t)((local >> 1) & 1));
             ok = __all_sync(0xFFFFFFFFu, ok);  // tcgen05.ld is warp-collective
@@ -774,17 +797,25 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                                              __uint_as_float(x[4 * j + 2]), __uint_as_float(x[4 * j + 3]));
                 } else {
                     __align__(16) __nv_bfloat162 v[16];
-                    const uint8_t* myrow = wmask + lane * (TN * 2);
+                    if (EPI == GRAD_MASKBITS) {
+                        const uint32_t m = mw[c];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {  // 16-byte chunk 4 c + j of this lane's mask row
-                        const uint4 m4 = *reinterpret_cast<const uint4*>(myrow + (((4 * c + j) ^ (lane & 7)) * 16));
-                        const __nv_bfloat162* mk = reinterpret_cast<const __nv_bfloat162*>(&m4);
+                        for (int k = 0; k < 16; ++k)
+                            v[k] = __floats2bfloat162_rn((m >> (2 * k)) & 1u ? __uint_as_float(x[2 * k]) : 0.f,
+                                                         (m >> (2 * k + 1)) & 1u ? __uint_as_float(x[2 * k + 1]) : 0.f);
+                    } else {
+                        const uint8_t* myrow = wmask + lane * (TN * 2);
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float2 mf = __bfloat1622float2(mk[e]);
-                            const int i = 8 * j + 2 * e;
-                            v[4 * j + e] = __floats2bfloat162_rn(mf.x > 0.f ? __uint_as_float(x[i]) : 0.f,
-                                                                 mf.y > 0.f ? __uint_as_float(x[i + 1]) : 0.f);
+                        for (int j = 0; j < 4; ++j) {  // 16-byte chunk 4 c + j of this lane's mask row
+                            const uint4 m4 = *reinterpret_cast<const uint4*>(myrow + (((4 * c + j) ^ (lane & 7)) * 16));
+                            const __nv_bfloat162* mk = reinterpret_cast<const __nv_bfloat162*>(&m4);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 mf = __bfloat1622float2(mk[e]);
+                                const int i = 8 * j + 2 * e;
+                                v[4 * j + e] = __floats2bfloat162_rn(mf.x > 0.f ? __uint_as_float(x[i]) : 0.f,
+                                                                     mf.y > 0.f ? __uint_as_float(x[i + 1]) : 0.f);
+                            }
                         }
                     }
                     stage_chunk<1>(c, v, staging + q * BOX_BYTES, lane, &tmOut, n0, row0);
@@ -796,8 +827,8 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
             tc_fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(&acc_empty[a])) : "memory");
         }
-        if (EPI == GRAD_MASK) {
-            asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // nothing in flight at exit
+        if (EPI == GRAD_MASK) asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // nothing in flight at exit
+        if (EPI != GRAD_PARTIAL) {
             if (colpart) {
                 float* dst = colpart + (size_t)((blockIdx.x / ntn) * 4 + q) * N + (blockIdx.x % ntn) * TN + 2 * lane;
 #pragma unroll
@@ -965,6 +996,21 @@ int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, in
     return launch_grad<false, true, GRAD_MASK>(ma, mb, mo, M, N, K / TK, 1, mask, N, nullptr, colpart, sms, s);
 }
 
+int umma_grad_maskbits(const void* A, const void* B, const uint32_t* maskbits, void* out, int M, int N, int K,
+                       float* colpart, cudaStream_t s) {
+    if (!umma_dense_supported(M, N, K) || !A || !B || !maskbits || !out || N % 8 || K % 8 || ((uintptr_t)A % 16) ||
+        ((uintptr_t)B % 16) || ((uintptr_t)maskbits % 4) || ((uintptr_t)out % 16))
+        return LUDAX_ERR_SIZE;
+    const int sms = device_sms();
+    if (!sms) return LUDAX_ERR_CUDA;
+    CUtensorMap ma, mb, mo;
+    if (!make_map(&ma, A, M, K, TM, K) || !make_map(&mb, B, K, N, 64, N) || !make_map(&mo, out, M, N, 32, N))
+        return LUDAX_ERR_CUDA;
+    if (colpart && ((uintptr_t)colpart % 8)) return LUDAX_ERR_SIZE;
+    return launch_grad<false, true, GRAD_MASKBITS>(ma, mb, mo, M, N, K / TK, 1, maskbits, N, nullptr, colpart, sms,
+                                                   s);
+}
+
 int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* part,
                       long long part_floats, int* splits_out, cudaStream_t s) {
     if (!umma_dense_supported(M, N, K) || !A || !B || !part || !splits_out || lda < M || ldb < N || lda % 8 ||
@@ -1006,13 +1052,15 @@ int umma_mlp_head(const void* X, int ldx, int K1, const void* W1, int ldw1, cons
     if (ensure_smem_limit((const void*)umma_mlp_head_kernel, MLP_SMEM)) return LUDAX_ERR_CUDA;
     // no H2 is stored: its map is a valid placeholder over the scratch
     return launch_dependent(umma_mlp_head_kernel, (unsigned)grid, MLP_THREADS, MLP_SMEM, s, mx, mw1, mhs, mhl, mw2, mhs,
-                            M, K1, b1, b2, static_cast<const __nv_bfloat16*>(w3), zpart, 0) == cudaSuccess
+                            M, K1, b1, b2, static_cast<const __nv_bfloat16*>(w3), zpart, 0,
+                            static_cast<uint32_t*>(nullptr)) == cudaSuccess
                ? LUDAX_OK
                : LUDAX_ERR_CUDA;
 }
 
 int umma_mlp_train(const void* X, int ldx, int K1, const void* W1, int ldw1, const float* b1, const void* W2,
-                   const float* b2, const void* w3, float* zpart, void* H1, void* H2, int M, cudaStream_t s) {
+                   const float* b2, const void* w3, float* zpart, void* H1, void* H2, uint32_t* h1bits, int M,
+                   cudaStream_t s) {
     if (M <= 0 || M % TM || K1 <= 0 || K1 % TK || K1 > ldx || K1 > ldw1 || ldx % 8 || ldw1 % 8 || !zpart || !H1 ||
         !H2 || ((uintptr_t)X % 16) || ((uintptr_t)W1 % 16) || ((uintptr_t)W2 % 16) || ((uintptr_t)H1 % 16) ||
         ((uintptr_t)H2 % 16))
@@ -1027,7 +1075,7 @@ int umma_mlp_train(const void* X, int ldx, int K1, const void* W1, int ldw1, con
         return LUDAX_ERR_CUDA;
     if (ensure_smem_limit((const void*)umma_mlp_head_kernel, MLP_SMEM)) return LUDAX_ERR_CUDA;
     return launch_dependent(umma_mlp_head_kernel, (unsigned)grid, MLP_THREADS, MLP_SMEM, s, mx, mw1, mhs, mhl, mw2, mh2,
-                            M, K1, b1, b2, static_cast<const __nv_bfloat16*>(w3), zpart, 1) == cudaSuccess
+                            M, K1, b1, b2, static_cast<const __nv_bfloat16*>(w3), zpart, 1, h1bits) == cudaSuccess
                ? LUDAX_OK
                : LUDAX_ERR_CUDA;
 }
