@@ -701,13 +701,15 @@ def bench_train_step(L, peaks, flush_buf, steps=20, warmup=3, B=65536):
         xb, yb = x.view(torch.int16), torch.rand(B, device="cuda", generator=g)
         k1 = min(net.in_pad, (2 * cells + 1 + 63) // 64 * 64)
         flops = 2.0 * B * (512 * (k1 + net.in_pad) + 3 * 512 * 512 + 512)
-        # HBM bytes of the step's dataflow (BF16 activations): X read by layer 1 (k1 columns) and
-        # dW1 (in_pad); H1 written by the forward (which reads it back for layer 2 from L2, within
-        # the launch) and read by the dZ1 mask and dW2; H2 written and read by the head's
+        # HBM bytes of the tcgen05 step's dataflow (BF16 activations): X read by layer 1 (k1
+        # columns) and dW1 (in_pad); H1 written by the forward (which reads it back for layer 2
+        # from L2, within the launch) and read by dW2, and its non-zero bits (64 B per row)
+        # written by the forward and read by dZ1 as its mask; H2 written and read by the head's
         # backward; dZ2 written and read by dZ1 and dW2; dZ1 written (its column sums are taken
         # in the same epilogue) and read by dW1; the finish kernel reads and writes parameters and
-        # both Adam moments and writes the BF16 weight copies (~7 FP32 words per parameter)
-        nbytes = 2.0 * B * (k1 + net.in_pad + 512 * (3 + 2 + 3 + 2)) + 4.0 * 7 * net.num_params
+        # both Adam moments and writes the BF16 weight copies (~7 FP32 words per parameter).  The
+        # mma.sync path reads H1 itself for the mask (another 1 KB per row).
+        nbytes = 2.0 * B * (k1 + net.in_pad + 512 * (2 + 2 + 3 + 2)) + 2.0 * 64 * B + 4.0 * 7 * net.num_params
         res = {"batch": B, "in_pad": net.in_pad, "layer1_columns": k1, "gflop_per_step": round(flops / 1e9, 2),
                "alg_mbytes_per_step": round(nbytes / 1e6, 1),
                "arithmetic_intensity_flop_per_byte": round(flops / nbytes, 1)}
