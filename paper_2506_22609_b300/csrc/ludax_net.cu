@@ -487,7 +487,10 @@ __device__ __forceinline__ void adam4(const FinishArgs& a, long long i, const fl
 constexpr int FIN_THREADS = 256, FIN_WARPS = FIN_THREADS / 32, FIN_BATCH = 10, FIN_ROWS = 16;
 constexpr int FIN_LONG = kH / 32 + (HB_COLS + 31) / 32;  // blocks of 32 bias / head columns
 
-__global__ void __launch_bounds__(FIN_THREADS) finish_kernel(FinishArgs a) {
+// at most 85 registers a thread: three 256-thread blocks per SM, so the 433
+// blocks of a 65,536-row step (W1 and W2 four weights a thread, plus the bias
+// columns) run in one wave on 148 SMs
+__global__ void __launch_bounds__(FIN_THREADS, 3) finish_kernel(FinishArgs a) {
     pdl_wait();
     if ((int)blockIdx.x >= FIN_LONG) {  // W1 and W2: four elements per thread, FIN_BATCH splits in flight
         const long long t = (long long)(blockIdx.x - FIN_LONG) * FIN_THREADS + threadIdx.x, e = 4 * t;
