@@ -567,6 +567,10 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
 //                  multiple of N / 256, so a CTA's tiles share their
 //                  columns) and writes them once, as row (CTA / (N / 256)) *
 //                  4 + warp of colpart [rows][N];
+//   GRAD_MASKBITS: the same with the mask given as bits (h1bits_index
+//                  layout): each epilogue lane loads its row's words of the
+//                  tile before waiting for the accumulator, no mask tile is
+//                  staged, and the ring has four stages;
 //   GRAD_PARTIAL : part[split][m][n] = FP32 sum over the split's share of K
 //                  of A[k][m] B[k][n] -- dW2 = dZ2^T . H1 and dW1 = dZ1^T . X,
 //                  both operands MN-major; the batch is split so that
