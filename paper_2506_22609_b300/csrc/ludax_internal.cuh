@@ -157,8 +157,11 @@ int umma_grad_colrows(int M, int N);  // 0 on error; at most 4 * SMs
 // umma_grad_weights: part[p][m][n] = FP32 sum over the p-th of *splits_out
 // contiguous K ranges of A[k][m] B[k][n]; A [K][lda], B [K][ldb] row-major
 // BF16; part holds part_floats floats (the split count is capped by it).
+// last_use: bit 0 / bit 1 -- A / B is read for the last time in the
+// training step (its lines are the first L2 gives up).  umma_grad_mask and
+// umma_grad_maskbits always treat A (dZ2) that way.
 int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* part,
-                      long long part_floats, int* splits_out, cudaStream_t s);
+                      long long part_floats, int* splits_out, cudaStream_t s, int last_use);
 
 // Programmatic dependent launch.  A kernel started with launch_dependent is
 // scheduled as the CTAs of the kernel before it on the stream exit (each

@@ -275,6 +275,19 @@ __device__ __forceinline__ void head_row(const float* zpart, int parts, const fl
     g = d * (1.f - v * v) / (float)B;  // 2 (p-y)/B * (1/2) (1 - v^2)
     se = d * d;
 }
+// A 16-byte global load whose line L2 may give up first: for data read for
+// the last time (H2 in the head's backward), so that the rows written next
+// (dZ2, read by the next two launches) keep their place.
+__device__ __forceinline__ uint4 ld_last_use(const void* a) {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    uint4 v;
+    asm volatile("ld.global.L2::cache_hint.v4.b32 {%0, %1, %2, %3}, [%4], %5;\n"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(a), "l"(pol)
+                 : "memory");
+    return v;
+}
 __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16* H2, const __nv_bfloat16* w3,
                                                             const float* g3, const float* sqerr, const float* zpart,
                                                             int zparts, const float* y, const float* b3, int B,
@@ -296,7 +309,7 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
 #pragma unroll
     for (int k = 0; k < HB_PRE; ++k) {
         const int r = r0 + grp + k * HB_GROUPS;
-        if (r < r1) pre[k] = *reinterpret_cast<const uint4*>(H2 + (size_t)r * kH + j0);
+        if (r < r1) pre[k] = ld_last_use(H2 + (size_t)r * kH + j0);
     }
     for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) {  // each row's loss gradient once
         float gr, se;
@@ -340,7 +353,7 @@ __global__ void __launch_bounds__(256) head_backward_kernel(const __nv_bfloat16*
     }
 #pragma unroll 4
     for (int r = r0 + grp + HB_PRE * HB_GROUPS; r < r1; r += HB_GROUPS)
-        row(r, *reinterpret_cast<const uint4*>(H2 + (size_t)r * kH + j0));
+        row(r, ld_last_use(H2 + (size_t)r * kH + j0));
     if (grp > 0) {
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -915,9 +928,9 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
     // dW2 runs first, while the dZ2 rows just written are still in L2; dZ1
     // then runs just before dW1, which reads the dZ1 rows it leaves in L2.
     auto weight_grad = [&](const __nv_bfloat16* A, const __nv_bfloat16* Bm, int N, int ldb, float* part,
-                           long long cap, int& splits) -> int {
+                           long long cap, int& splits, int last_use) -> int {
         if (tc && umma_dense_supported(kH, N, (int)B))
-            return umma_grad_weights(A, kH, Bm, ldb, kH, N, (int)B, part, cap, &splits, s);
+            return umma_grad_weights(A, kH, Bm, ldb, kH, N, (int)B, part, cap, &splits, s, last_use);
         splits = (int)std::min<long long>(32, B / BKT);
         while (splits > 1 && (B % ((long long)BKT * splits))) --splits;
         GemmArgs a{};
@@ -925,7 +938,8 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
         return launch_gemm<false, false, EPI_PARTIAL>(a, splits, s);
     };
     int st, s2 = 0, s1 = 0;
-    if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->w2p, n->w2_floats, s2))) return st;
+    // dW2's last use is of H1 (dZ2 is read again by dZ1), dW1's of dZ1
+    if ((st = weight_grad(n->dZ2, n->H1, kH, kH, n->w2p, n->w2_floats, s2, 2))) return st;
     // dZ1 = (dZ2 . W2) * [H1 > 0], and db1 = its column sums as partial rows
     int crows;
     if (tc) {
@@ -943,7 +957,7 @@ int net_backward(ludax_net* n, const __nv_bfloat16* X, long long B, const float*
         crows = chunks;
     }
     if (st) return st;
-    if ((st = weight_grad(n->dZ1, X, n->kpad, n->kpad, n->w1p, n->w1_floats, s1))) return st;
+    if ((st = weight_grad(n->dZ1, X, n->kpad, n->kpad, n->w1p, n->w1_floats, s1, 1))) return st;
     FinishArgs f{};
     f.w1p = n->w1p; f.w2p = n->w2p; f.cp = n->cp; f.hp = n->hp;
     f.s1 = s1; f.s2 = s2; f.crows = crows; f.hrows = chunks;

@@ -82,6 +82,27 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// The same load with an L2 eviction policy (createpolicy) for the lines it reads.
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+        "%4}], [%2], %5;\n" ::"r"(saddr(dst)),
+        "l"(map), "r"(saddr(bar)), "r"(c0), "r"(c1), "l"(policy)
+        : "memory");
+}
+// a policy under which L2 gives up the lines first (data read for the last time)
+__device__ __forceinline__ uint64_t l2_last_use_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_load_2d_pol(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                                uint64_t policy) {
+    if (policy) tma_load_2d_hint(dst, map, bar, c0, c1, policy);
+    else tma_load_2d(dst, map, bar, c0, c1);
+}
+
 // bulk tensor store of a shared-memory box to global memory (bulk async-group)
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int c0, int c1) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(map),
@@ -655,7 +676,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
     umma_grad_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                      const __grid_constant__ CUtensorMap tmOut, int M, int N, int kblocks, int splits,
                      const __nv_bfloat16* __restrict__ mask, int ldm, float* __restrict__ part,
-                     float* __restrict__ colpart) {
+                     float* __restrict__ colpart, int last_use) {
     ludax::pdl_wait();
     constexpr int NS = GradCfg<EPI>::stages;
     extern __shared__ __align__(16) uint8_t smem_raw[];
@@ -703,6 +724,9 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
+            // operands read for the last time in the step (last_use bit 0: A, bit 1: B) leave L2 first
+            const uint64_t pa = (last_use & 1) ? l2_last_use_policy() : 0ull;
+            const uint64_t pb = (last_use & 2) ? l2_last_use_policy() : 0ull;
             int it = 0;
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
                 int m0, n0, sp, kb0, kb1;
@@ -715,16 +739,17 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1)
                     mbar_expect_tx(&full[s], STAGE);
                     if (A_MN) {
 #pragma unroll
-                        for (int h = 0; h < TM / 64; ++h) tma_load_2d(st + h * MN_BOX, &tmA, &full[s], m0 + 64 * h, kt * TK);
+                        for (int h = 0; h < TM / 64; ++h)
+                            tma_load_2d_pol(st + h * MN_BOX, &tmA, &full[s], m0 + 64 * h, kt * TK, pa);
                     } else {
-                        tma_load_2d(st, &tmA, &full[s], kt * TK, m0);
+                        tma_load_2d_pol(st, &tmA, &full[s], kt * TK, m0, pa);
                     }
                     if (B_MN) {
 #pragma unroll
                         for (int h = 0; h < TN / 64; ++h)
-                            tma_load_2d(st + A_TILE + h * MN_BOX, &tmB, &full[s], n0 + 64 * h, kt * TK);
+                            tma_load_2d_pol(st + A_TILE + h * MN_BOX, &tmB, &full[s], n0 + 64 * h, kt * TK, pb);
                     } else {
-                        tma_load_2d(st + A_TILE, &tmB, &full[s], kt * TK, n0);
+                        tma_load_2d_pol(st + A_TILE, &tmB, &full[s], kt * TK, n0, pb);
                     }
                 }
             }
@@ -968,13 +993,14 @@ static int grad_grid(int units, int ntn, int sms) {
 
 template <bool A_MN, bool B_MN, int EPI>
 static int launch_grad(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mo, int M, int N, int kblocks,
-                       int splits, const void* mask, int ldm, float* part, float* colpart, int sms, cudaStream_t s) {
+                       int splits, const void* mask, int ldm, float* part, float* colpart, int sms, cudaStream_t s,
+                       int last_use) {
     auto k = umma_grad_kernel<A_MN, B_MN, EPI>;
     if (ensure_smem_limit((const void*)k, GradCfg<EPI>::smem)) return LUDAX_ERR_CUDA;
     const int units = (M / TM) * (N / TN) * splits;
     return launch_dependent(k, (unsigned)grad_grid(units, N / TN, sms), UMMA_THREADS, GradCfg<EPI>::smem, s, ma, mb,
                             mo, M, N, kblocks, splits, static_cast<const __nv_bfloat16*>(mask), ldm, part,
-                            colpart) == cudaSuccess
+                            colpart, last_use) == cudaSuccess
                ? LUDAX_OK
                : LUDAX_ERR_CUDA;
 }
@@ -997,7 +1023,7 @@ int umma_grad_mask(const void* A, const void* B, const void* mask, void* out, in
     if (!make_map(&ma, A, M, K, TM, K) || !make_map(&mb, B, K, N, 64, N) || !make_map(&mo, out, M, N, 32, N))
         return LUDAX_ERR_CUDA;
     if (colpart && ((uintptr_t)colpart % 8)) return LUDAX_ERR_SIZE;
-    return launch_grad<false, true, GRAD_MASK>(ma, mb, mo, M, N, K / TK, 1, mask, N, nullptr, colpart, sms, s);
+    return launch_grad<false, true, GRAD_MASK>(ma, mb, mo, M, N, K / TK, 1, mask, N, nullptr, colpart, sms, s, 1);
 }
 
 int umma_grad_maskbits(const void* A, const void* B, const uint32_t* maskbits, void* out, int M, int N, int K,
@@ -1012,11 +1038,11 @@ int umma_grad_maskbits(const void* A, const void* B, const uint32_t* maskbits, v
         return LUDAX_ERR_CUDA;
     if (colpart && ((uintptr_t)colpart % 8)) return LUDAX_ERR_SIZE;
     return launch_grad<false, true, GRAD_MASKBITS>(ma, mb, mo, M, N, K / TK, 1, maskbits, N, nullptr, colpart, sms,
-                                                   s);
+                                                   s, 1);
 }
 
 int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* part,
-                      long long part_floats, int* splits_out, cudaStream_t s) {
+                      long long part_floats, int* splits_out, cudaStream_t s, int last_use) {
     if (!umma_dense_supported(M, N, K) || !A || !B || !part || !splits_out || lda < M || ldb < N || lda % 8 ||
         ldb % 8 || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)part % 16))
         return LUDAX_ERR_SIZE;
@@ -1033,7 +1059,7 @@ int umma_grad_weights(const void* A, int lda, const void* B, int ldb, int M, int
     if (!make_map(&ma, A, K, M, 64, lda) || !make_map(&mb, B, K, N, 64, ldb)) return LUDAX_ERR_CUDA;
     *splits_out = (int)splits;
     return launch_grad<true, true, GRAD_PARTIAL>(ma, mb, ma, M, N, kblocks, (int)splits, nullptr, 0, part, nullptr,
-                                                 sms, s);
+                                                 sms, s, last_use);
 }
 
 int umma_mlp_scratch_rows() { return device_sms() * 2 * TM; }
