@@ -477,6 +477,7 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
+            const uint64_t x_policy = l2_last_use_policy();
             int it = 0;
             for (int j = 0; j < njobs && ok; ++j) {
                 const MlpJob jb = mlp_job(j, nb);
@@ -494,7 +495,8 @@ __global__ void __launch_bounds__(MLP_THREADS, 1)
                     uint8_t* dst = smem + st * STAGE;
                     mbar_expect_tx(&full[st], STAGE);
                     if (jb.phase == 1) {
-                        tma_load_2d(dst, &tmX, &full[st], kt * TK, gblk * TM);
+                        // inference reads its input rows once; training's are read again by dW1
+                        tma_load_2d_pol(dst, &tmX, &full[st], kt * TK, gblk * TM, train ? 0ull : x_policy);
                         tma_load_2d(dst + A_TILE, &tmW1, &full[st], kt * TK, jb.h * TN);
                     } else {
                         tma_load_2d(dst, &tmHld, &full[st], kt * TK, train ? gblk * TM : scratch0 + (jb.blk & 1) * TM);
