@@ -79,6 +79,10 @@ struct B128 {
     uint64_t lo, hi;
 };
 __host__ __device__ __forceinline__ B128 operator|(B128 a, B128 b) { return {a.lo | b.lo, a.hi | b.hi}; }
+// a | b for a and b with no bit in common, computed as adds (no carry can
+// arise): an add also issues to a second pipe, where the logic ops the
+// bitboard code is bound by have one
+__host__ __device__ __forceinline__ B128 add_disjoint(B128 a, B128 b) { return {a.lo + b.lo, a.hi + b.hi}; }
 __host__ __device__ __forceinline__ B128 operator&(B128 a, B128 b) { return {a.lo & b.lo, a.hi & b.hi}; }
 __host__ __device__ __forceinline__ B128 operator~(B128 a) { return {~a.lo, ~a.hi}; }
 __host__ __device__ __forceinline__ bool operator==(B128 a, B128 b) { return a.lo == b.lo && a.hi == b.hi; }
@@ -475,14 +479,14 @@ struct Hex {
         }
         const bool ta = ea || any(nx & ownA);
         const bool tb = eb || any(nx & ownB);
-        own = fit(own) | x;
+        own = add_disjoint(fit(own), x);
         if (ta && tb) {
             outcome = side + 1;
         } else if (ta || tb) {
             const B128 first = nx & own & ~(ownA | ownB);
             const B128 c = x | first;
-            if (ta) ownA = ownA | c;
-            else ownB = ownB | c;
+            if (ta) ownA = add_disjoint(ownA, c);
+            else ownB = add_disjoint(ownB, c);
             front = first;
             passes = ta;  // the set the front joins (kept through the compaction slots with the state)
         }
@@ -502,8 +506,8 @@ struct Hex {
         const bool to_a = passes != 0;  // Hex has no passes: the field says which set the front joins
         const B128 nw = nbrs(f) & fit(opp) & ~(a | b);
         const B128 z = {0ull, 0ull};
-        oppA = a | (to_a ? nw : z);
-        oppB = b | (to_a ? z : nw);
+        oppA = add_disjoint(a, to_a ? nw : z);
+        oppB = add_disjoint(b, to_a ? z : nw);
         front = nw;
         return any(nw);
     }
