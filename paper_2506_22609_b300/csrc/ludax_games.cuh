@@ -504,7 +504,7 @@ struct Hex {
     __device__ __forceinline__ bool spread() {
         const B128 f = fit(front), a = fit(oppA), b = fit(oppB);
         const bool to_a = passes != 0;  // Hex has no passes: the field says which set the front joins
-        const B128 nw = nbrs(f) & fit(opp) & ~(a | b);
+        const B128 nw = nbrs(f) & fit(opp) & ~add_disjoint(a, b);  // the two edge sets share no stone
         const B128 z = {0ull, 0ull};
         oppA = add_disjoint(a, to_a ? nw : z);
         oppB = add_disjoint(b, to_a ? z : nw);
